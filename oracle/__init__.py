@@ -1,0 +1,306 @@
+"""FP64 CPU oracle of the batched differentiable quadrotor environment step.
+
+TEST INFRASTRUCTURE ONLY.  Only the test suite, ``__graft_entry__.smoke()`` and
+the benchmark's CPU-baseline leg import this package.  It is independent of
+the CUDA library: it shares no source, header, helper or constant with it, and
+neither imports the other.  The arithmetic lives in ``diffsim_oracle.c`` (plain
+C, double precision); this module only marshals numpy arrays through ctypes.
+
+Parity status of each oracle function (what pins it, see tests/test_oracle_*):
+  dynamics (Eq. 1, Eq. 3)      closed forms: hover, free fall, lag, drag decay,
+                               constant body rate, tilted thrust; RK4 limit
+  point-mass attitude          orthonormality, heading/thrust alignment cases
+  ray casting (Sec. III-B)     closed-form hits, wall z-depth, SDF marching
+  collisions and rewards       hand-computed cases
+  adjoint (Eq. 5)              central finite differences of ``loss``
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "diffsim_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+
+_d = C.c_double
+_i = C.c_int32
+_pd = C.POINTER(C.c_double)
+_pi = C.POINTER(C.c_int32)
+_pu8 = C.POINTER(C.c_uint8)
+_pi8 = C.POINTER(C.c_int8)
+
+
+class OcConfig(C.Structure):
+    _fields_ = [
+        ("model", _i), ("n_env", _i), ("n_agent", _i), ("horizon", _i),
+        ("dt", _d), ("gravity", _d),
+        ("lam", _d), ("drag", _d), ("act_scale", _d), ("ema_alpha", _d),
+        ("mass", _d), ("inertia", _d * 3), ("k_rate", _d * 3), ("drag_body", _d * 3),
+        ("rate_scale", _d * 3),
+        ("cam_w", _i), ("cam_h", _i), ("cam_hfov", _d), ("cam_range", _d),
+        ("lid_ch", _i), ("lid_az", _i), ("lid_elev_lo", _d), ("lid_elev_hi", _d),
+        ("lid_range", _d),
+        ("pos_sq", _i), ("w_pos", _d), ("w_obs", _d), ("d_safe", _d), ("w_act", _d),
+        ("w_agent", _d), ("d_agent", _d), ("success_radius", _d), ("r_quad", _d),
+        ("bound_lo", _d * 3), ("bound_hi", _d * 3),
+        ("terminate", _i), ("pool_size", _i),
+    ]
+
+
+class OcScene(C.Structure):
+    _fields_ = [
+        ("spheres", _pd), ("sph_off", _pi), ("boxes", _pd), ("box_off", _pi),
+        ("env_map", _pi), ("n_maps", _i), ("targets", _pd), ("pool", _pd),
+        ("drag_env", _pd), ("lam_env", _pd),
+    ]
+
+
+def build(force=False):
+    """Compile the oracle with gcc (plain -O2, OpenMP over environments only,
+    no fast-math, no FMA contraction)."""
+    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
+        return _LIB
+    tmp = _LIB + ".tmp%d" % os.getpid()
+    subprocess.check_call(["gcc", "-O2", "-fopenmp", "-ffp-contract=off", "-std=gnu99",
+                           "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"])
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = C.CDLL(_LIB)
+        L.oc_ray_sphere.restype = _d
+        L.oc_ray_sphere.argtypes = [_pd, _pd, _pd]
+        L.oc_ray_box.restype = _d
+        L.oc_ray_box.argtypes = [_pd, _pd, _pd, _pi]
+        L.oc_sdf_sphere.restype = _d
+        L.oc_sdf_sphere.argtypes = [_pd, _pd]
+        L.oc_sdf_box.restype = _d
+        L.oc_sdf_box.argtypes = [_pd, _pd]
+        L.oc_pose.restype = C.c_int
+        L.oc_loss.restype = _d
+        L.oc_max_threads.restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def _p(a, ct=_pd):
+    if a is None:
+        return C.cast(None, ct)
+    return a.ctypes.data_as(ct)
+
+
+def _c64(a):
+    return None if a is None else np.ascontiguousarray(a, dtype=np.float64)
+
+
+def make_config(p):
+    """oc_config from a workload parameter dict (angles given in degrees)."""
+    c = OcConfig()
+    c.model = 1 if p["model"] == "rigid" else 0
+    c.n_env, c.n_agent, c.horizon = p["n_env"], p["n_agent"], p["horizon"]
+    c.dt, c.gravity = p["dt"], p["gravity"]
+    c.lam, c.drag, c.act_scale, c.ema_alpha = p["lam"], p["drag"], p["act_scale"], p["ema_alpha"]
+    c.mass = p["mass"]
+    for k in range(3):
+        c.inertia[k] = p["inertia"][k]
+        c.k_rate[k] = p["k_rate"][k]
+        c.drag_body[k] = p["drag_body"][k]
+        c.rate_scale[k] = p["rate_scale"][k]
+        c.bound_lo[k] = p["bound_lo"][k]
+        c.bound_hi[k] = p["bound_hi"][k]
+    if p["cam"] is not None:
+        c.cam_w, c.cam_h = p["cam"][0], p["cam"][1]
+        c.cam_hfov, c.cam_range = math.radians(p["cam"][2]), p["cam"][3]
+    if p["lidar"] is not None:
+        c.lid_ch, c.lid_az = p["lidar"][0], p["lidar"][1]
+        c.lid_elev_lo, c.lid_elev_hi = math.radians(p["lidar"][2]), math.radians(p["lidar"][3])
+        c.lid_range = p["lidar"][4]
+    c.pos_sq = int(p["pos_sq"])
+    c.w_pos, c.w_obs, c.d_safe, c.w_act = p["w_pos"], p["w_obs"], p["d_safe"], p["w_act"]
+    c.w_agent, c.d_agent = p["w_agent"], p["d_agent"]
+    c.success_radius, c.r_quad = p["success_radius"], p["r_quad"]
+    c.terminate, c.pool_size = int(p["terminate"]), p["pool_size"]
+    return c
+
+
+class Oracle:
+    """Oracle bound to one workload (parameters + scene)."""
+
+    def __init__(self, p, inp):
+        self.p = p
+        self.cfg = make_config(p)
+        self.D = 13 if p["model"] == "rigid" else 12
+        self.A = 4 if p["model"] == "rigid" else 3
+        self.N, self.M, self.T = p["n_env"], p["n_agent"], p["horizon"]
+        self.NM = self.N * self.M
+        self.Rc = p["cam"][0] * p["cam"][1] if p["cam"] is not None else 0
+        self.Rl = p["lidar"][0] * p["lidar"][1] if p["lidar"] is not None else 0
+        self._keep = dict(
+            spheres=_c64(inp["spheres"].reshape(-1, 4)),
+            sph_off=np.ascontiguousarray(inp["sph_off"], dtype=np.int32),
+            boxes=_c64(inp["boxes"].reshape(-1, 6)),
+            box_off=np.ascontiguousarray(inp["box_off"], dtype=np.int32),
+            env_map=np.ascontiguousarray(inp["env_map"], dtype=np.int32),
+            targets=_c64(inp["targets"]), pool=_c64(inp["pool"]),
+            drag_env=_c64(inp.get("drag_env")), lam_env=_c64(inp.get("lam_env")),
+        )
+        k = self._keep
+        self.scene = OcScene(_p(k["spheres"]), _p(k["sph_off"], _pi), _p(k["boxes"]),
+                             _p(k["box_off"], _pi), _p(k["env_map"], _pi),
+                             len(k["sph_off"]) - 1, _p(k["targets"]), _p(k["pool"]),
+                             _p(k["drag_env"]), _p(k["lam_env"]))
+
+    def with_horizon(self, T):
+        o = Oracle.__new__(Oracle)
+        o.__dict__.update(self.__dict__)
+        o.cfg = make_config(dict(self.p, horizon=T))
+        o.T = T
+        return o
+
+    def rollout(self, s0, actions, pool_k=None, n_threads=0):
+        """Run T steps from s0 [NM, D] with actions [T, NM, A].  Returns a dict:
+        states [T+1,NM,D], spre [T,NM,D], r_ctrl, r_goal, done [T,NM],
+        depth/hit_cam/amb_cam [T,NM,Rc], lidar/hit_lid/amb_lid [T,NM,Rl],
+        amb_step, sdf_id [T,NM], pool_k [N] (advanced)."""
+        T, NM, D = self.T, self.NM, self.D
+        s0 = _c64(s0).reshape(NM, D)
+        act = _c64(actions).reshape(T, NM, self.A)
+        pk = np.zeros(self.N, np.int32) if pool_k is None else np.array(pool_k, np.int32)
+        out = dict(
+            states=np.zeros((T + 1, NM, D)), spre=np.zeros((T, NM, D)),
+            r_ctrl=np.zeros((T, NM)), r_goal=np.zeros((T, NM), np.int8),
+            done=np.zeros((T, NM), np.uint8),
+            depth=np.zeros((T, NM, self.Rc)), lidar=np.zeros((T, NM, self.Rl)),
+            hit_cam=np.zeros((T, NM, self.Rc), np.int32), hit_lid=np.zeros((T, NM, self.Rl), np.int32),
+            amb_cam=np.zeros((T, NM, self.Rc), np.uint8), amb_lid=np.zeros((T, NM, self.Rl), np.uint8),
+            amb_step=np.zeros((T, NM), np.uint8), sdf_id=np.zeros((T, NM), np.int32),
+        )
+        o = out
+        lib().oc_rollout(C.byref(self.cfg), C.byref(self.scene), _p(s0), _p(pk, _pi), _p(act),
+                         _p(o["states"]), _p(o["spre"]), _p(o["r_ctrl"]), _p(o["r_goal"], _pi8),
+                         _p(o["done"], _pu8), _p(o["depth"]), _p(o["lidar"]),
+                         _p(o["hit_cam"], _pi), _p(o["hit_lid"], _pi), _p(o["amb_cam"], _pu8),
+                         _p(o["amb_lid"], _pu8), _p(o["amb_step"], _pu8), _p(o["sdf_id"], _pi),
+                         C.c_int(n_threads))
+        out["pool_k"] = pk
+        out["actions"] = act
+        return out
+
+    def backward(self, rec, g_r, g_depth=None, g_lidar=None, g_sT=None, n_threads=0):
+        """Adjoint of a recorded rollout.  Returns (g_a [T,NM,A], g_s0 [NM,D])."""
+        T, NM, D, A = self.T, self.NM, self.D, self.A
+        g_a = np.zeros((T, NM, A))
+        g_s0 = np.zeros((NM, D))
+        gr = _c64(g_r).reshape(T, NM)
+        gd = None if (g_depth is None or self.Rc == 0) else _c64(g_depth).reshape(T, NM, self.Rc)
+        gl = None if (g_lidar is None or self.Rl == 0) else _c64(g_lidar).reshape(T, NM, self.Rl)
+        gs = None if g_sT is None else _c64(g_sT).reshape(NM, D)
+        lib().oc_backward(C.byref(self.cfg), C.byref(self.scene), _p(rec["actions"]),
+                          _p(rec["states"]), _p(rec["spre"]), _p(rec["done"], _pu8),
+                          _p(rec["hit_cam"], _pi), _p(rec["hit_lid"], _pi), _p(gr), _p(gd),
+                          _p(gl), _p(gs), _p(g_a), _p(g_s0), C.c_int(n_threads))
+        return g_a, g_s0
+
+    def loss(self, s0, actions, g_r, g_depth=None, g_lidar=None, g_sT=None):
+        """L = <g_r, r_ctrl> + <g_depth, depth> + <g_lidar, lidar> + <g_sT, s_T>."""
+        T, NM = self.T, self.NM
+        gd = None if (g_depth is None or self.Rc == 0) else _c64(g_depth).reshape(T, NM, self.Rc)
+        gl = None if (g_lidar is None or self.Rl == 0) else _c64(g_lidar).reshape(T, NM, self.Rl)
+        gs = None if g_sT is None else _c64(g_sT).reshape(NM, self.D)
+        return lib().oc_loss(C.byref(self.cfg), C.byref(self.scene), _p(_c64(s0)),
+                             _p(_c64(actions)), _p(_c64(g_r)), _p(gd), _p(gl), _p(gs))
+
+    def render(self, s):
+        """Sensor outputs of states s [NM, D]: (depth, lidar, hit_cam, hit_lid, amb_cam, amb_lid)."""
+        NM = self.NM
+        s = _c64(s).reshape(NM, self.D)
+        dep, lid = np.zeros((NM, self.Rc)), np.zeros((NM, self.Rl))
+        hc, hl = np.zeros((NM, self.Rc), np.int32), np.zeros((NM, self.Rl), np.int32)
+        ac, al = np.zeros((NM, self.Rc), np.uint8), np.zeros((NM, self.Rl), np.uint8)
+        lib().oc_render(C.byref(self.cfg), C.byref(self.scene), _p(s), _p(dep), _p(lid),
+                        _p(hc, _pi), _p(hl, _pi), _p(ac, _pu8), _p(al, _pu8))
+        return dep, lid, hc, hl, ac, al
+
+
+# ----------------------------------------------------------- primitive calls
+def _v(x, n=None):
+    a = np.ascontiguousarray(x, dtype=np.float64)
+    return a
+
+
+def ray_sphere(o, d, sphere):
+    return lib().oc_ray_sphere(_p(_v(o)), _p(_v(d)), _p(_v(sphere)))
+
+
+def ray_box(o, d, box):
+    ax = np.zeros(1, np.int32)
+    t = lib().oc_ray_box(_p(_v(o)), _p(_v(d)), _p(_v(box)), _p(ax, _pi))
+    return t, int(ax[0])
+
+
+def sdf_sphere(p, sphere):
+    return lib().oc_sdf_sphere(_p(_v(p)), _p(_v(sphere)))
+
+
+def sdf_box(p, box):
+    return lib().oc_sdf_box(_p(_v(p)), _p(_v(box)))
+
+
+def quat_to_rot(q):
+    R = np.zeros(9)
+    lib().oc_quat_to_rot(_p(_v(q)), _p(R))
+    return R.reshape(3, 3)
+
+
+def pm_step(p, s, a, drag=None, lam=None):
+    cfg = make_config(p)
+    o = np.zeros(12)
+    lib().oc_pm_step(C.byref(cfg), _d(p["drag"] if drag is None else drag),
+                     _d(p["lam"] if lam is None else lam), _p(_v(s)), _p(_v(a)), _p(o))
+    return o
+
+
+def rb_step(p, s, a):
+    cfg = make_config(p)
+    o = np.zeros(13)
+    lib().oc_rb_step(C.byref(cfg), _p(_v(s)), _p(_v(a)), _p(o))
+    return o
+
+
+def pose(p, s):
+    cfg = make_config(p)
+    o, R = np.zeros(3), np.zeros(9)
+    f = lib().oc_pose(C.byref(cfg), _p(_v(s)), _p(o), _p(R))
+    return o, R.reshape(3, 3), f
+
+
+def cam_dirs(p):
+    cfg = make_config(p)
+    R = p["cam"][0] * p["cam"][1]
+    d, f = np.zeros((R, 3)), np.zeros(R)
+    lib().oc_cam_dirs(C.byref(cfg), _p(d), _p(f))
+    return d, f
+
+
+def lidar_dirs(p):
+    cfg = make_config(p)
+    R = p["lidar"][0] * p["lidar"][1]
+    d = np.zeros((R, 3))
+    lib().oc_lidar_dirs(C.byref(cfg), _p(d))
+    return d
+
+
+def max_threads():
+    return lib().oc_max_threads()

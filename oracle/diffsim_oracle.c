@@ -1,0 +1,1069 @@
+/*
+ * diffsim_oracle.c -- plain FP64 CPU oracle of the batched, differentiable
+ * quadrotor environment step of DiffAero (arXiv 2509.10247).
+ *
+ * TEST INFRASTRUCTURE.  Only the test suite, the package smoke check and the
+ * benchmark's CPU-baseline leg load this library.  The product (the CUDA
+ * library) never links, imports or calls it, and it shares no code with it.
+ *
+ * What it computes, in the paper's order and notation:
+ *   - continuous point-mass dynamics (Sec. III-A, Eq. 3) and full rigid-body
+ *     quadrotor dynamics (Sec. III-A, Eq. 1) with the body-rate part of the
+ *     geometric controller, integrated by explicit Euler with every right-hand
+ *     side taken at time t (the paper gives only the continuous equations);
+ *   - point-mass attitude from the thrust direction and the horizontal
+ *     projection of an exponential moving average of velocity (Sec. III-B);
+ *   - depth camera and LiDAR by ray casting against analytic spheres and
+ *     axis-aligned boxes (Sec. III-B), brute force over every primitive, no
+ *     field-of-view culling (culling only skips primitives no ray can hit);
+ *   - collisions, the dense differentiable reward R_ctrl and the sparse
+ *     reward R_goal (Sec. III-C, III-D, III-E), termination and reset;
+ *   - the reverse-mode adjoint of the whole rollout, i.e. the chain rule of
+ *     Eq. 5 taken one step at a time, written by hand.
+ * All arithmetic is double precision.  Where the paper is silent the reading
+ * taken is the one listed in the design notes (e.g. thrust along +z_B in a
+ * z-up world; lambda = 1/tau; z-depth output clamped at the camera range).
+ *
+ * Layouts (row-major, last index fastest):
+ *   state  [NM][D], D = 12 (point mass: p, v, a, ema_v) or 13 (rigid: p,
+ *          q=(w,x,y,z), v, omega); actions [T][NM][A], A = 3 or 4;
+ *   spheres [K][4] = (cx, cy, cz, r); boxes [K][6] = (min xyz, max xyz);
+ *   per-map CSR offsets; env_map [N]; targets [NM][3]; pool [P][NM][D].
+ *   Primitive ids within a map: spheres 0..Ks-1, then boxes Ks..Ks+Kb-1.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define OC_PM 0
+#define OC_RIGID 1
+#define OC_INF HUGE_VAL
+
+/* Ambiguity margins used to flag rays and steps where an FP32 evaluation may
+ * legitimately take another discrete branch than FP64 (see the design notes). */
+#define AMB_DISC 1e-5   /* sphere grazing: |b^2 - C| < AMB_DISC * max(b^2, 1)  */
+#define AMB_SLAB 1e-5   /* box grazing: |t_far - t_near| < AMB_SLAB (m)        */
+#define AMB_INSIDE 1e-5 /* origin within this distance of a primitive surface  */
+#define AMB_GAP 1e-4    /* second-nearest hit within this distance (m)         */
+#define AMB_RANGE 1e-4  /* hit within this distance of the range clamp (m)     */
+#define AMB_GRAZE 0.05  /* |n . d| below this: ill-conditioned gradient       */
+#define AMB_EDGE 1e-5   /* two slab entry times within this (relative)        */
+#define AMB_STEP 1e-5   /* thresholds of collision / success / bounds (m)     */
+
+typedef struct {
+    int32_t model, n_env, n_agent, horizon;
+    double dt, gravity;
+    /* point mass (Eq. 3) */
+    double lam, drag, act_scale, ema_alpha;
+    /* rigid body (Eq. 1) */
+    double mass, inertia[3], k_rate[3], drag_body[3], rate_scale[3];
+    /* depth camera; cam_w == 0 disables it.  Angles in radians. */
+    int32_t cam_w, cam_h;
+    double cam_hfov, cam_range;
+    /* lidar; lid_ch == 0 disables it */
+    int32_t lid_ch, lid_az;
+    double lid_elev_lo, lid_elev_hi, lid_range;
+    /* task and reward */
+    int32_t pos_sq;
+    double w_pos, w_obs, d_safe, w_act, w_agent, d_agent, success_radius, r_quad;
+    double bound_lo[3], bound_hi[3];
+    int32_t terminate, pool_size;
+} oc_config;
+
+typedef struct {
+    const double *spheres;
+    const int32_t *sph_off;
+    const double *boxes;
+    const int32_t *box_off;
+    const int32_t *env_map;
+    int32_t n_maps;
+    const double *targets;
+    const double *pool;
+    const double *drag_env; /* [N] or NULL */
+    const double *lam_env;  /* [N] or NULL */
+} oc_scene;
+
+/* ------------------------------------------------------------------ utils */
+int oc_state_dim(int model) { return model == OC_RIGID ? 13 : 12; }
+int oc_action_dim(int model) { return model == OC_RIGID ? 4 : 3; }
+
+static double clamp1(double x) { return x < -1.0 ? -1.0 : (x > 1.0 ? 1.0 : x); }
+static double dclamp1(double x) { return (x >= -1.0 && x <= 1.0) ? 1.0 : 0.0; }
+static double dot3(const double *a, const double *b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+static double norm3(const double *a) { return sqrt(dot3(a, a)); }
+static void cross3(const double *a, const double *b, double *o)
+{
+    double x = a[1] * b[2] - a[2] * b[1];
+    double y = a[2] * b[0] - a[0] * b[2];
+    double z = a[0] * b[1] - a[1] * b[0];
+    o[0] = x; o[1] = y; o[2] = z;
+}
+static double relu(double x) { return x > 0.0 ? x : 0.0; }
+
+/* R(q): rotation body -> world of the Hamilton unit quaternion q = (w, x, y, z),
+ * row-major R[3*i + j]. */
+void oc_quat_to_rot(const double *q, double *R)
+{
+    double w = q[0], x = q[1], y = q[2], z = q[3];
+    R[0] = 1 - 2 * (y * y + z * z); R[1] = 2 * (x * y - w * z);     R[2] = 2 * (x * z + w * y);
+    R[3] = 2 * (x * y + w * z);     R[4] = 1 - 2 * (x * x + z * z); R[5] = 2 * (y * z - w * x);
+    R[6] = 2 * (x * z - w * y);     R[7] = 2 * (y * z + w * x);     R[8] = 1 - 2 * (x * x + y * y);
+}
+
+/* cotangent of q from the cotangent of R(q) (the entries' partial derivatives
+ * of the polynomial map above). */
+static void quat_to_rot_vjp(const double *q, const double *gR, double *gq)
+{
+    double w = q[0], x = q[1], y = q[2], z = q[3];
+    const double dw[9] = {0, -z, y, z, 0, -x, -y, x, 0};
+    const double dx[9] = {0, y, z, y, -2 * x, -w, z, w, -2 * x};
+    const double dy[9] = {-2 * y, x, w, x, 0, z, -w, z, -2 * y};
+    const double dz[9] = {-2 * z, -w, x, w, -2 * z, y, x, y, 0};
+    double s[4] = {0, 0, 0, 0};
+    for (int k = 0; k < 9; ++k) {
+        s[0] += 2 * dw[k] * gR[k];
+        s[1] += 2 * dx[k] * gR[k];
+        s[2] += 2 * dy[k] * gR[k];
+        s[3] += 2 * dz[k] * gR[k];
+    }
+    for (int k = 0; k < 4; ++k) gq[k] += s[k];
+}
+
+/* Hamilton product a (x) b */
+static void quat_mul(const double *a, const double *b, double *o)
+{
+    double w = a[0] * b[0] - a[1] * b[1] - a[2] * b[2] - a[3] * b[3];
+    double x = a[0] * b[1] + a[1] * b[0] + a[2] * b[3] - a[3] * b[2];
+    double y = a[0] * b[2] - a[1] * b[3] + a[2] * b[0] + a[3] * b[1];
+    double z = a[0] * b[3] + a[1] * b[2] - a[2] * b[1] + a[3] * b[0];
+    o[0] = w; o[1] = x; o[2] = y; o[3] = z;
+}
+
+/* ------------------------------------------------------ dynamics (Sec. III-A) */
+
+/* Continuous point mass, Eq. 3: p' = v, v' = a + g - d v, a' = lambda (u - a),
+ * one explicit-Euler step of length dt; u = act_scale * clip(action, -1, 1) is
+ * the world-frame acceleration command.  The EMA of velocity used by the
+ * point-mass attitude (Sec. III-B) is advanced from the new velocity. */
+void oc_pm_step(const oc_config *c, double drag, double lam, const double *s,
+                const double *act, double *o)
+{
+    const double g[3] = {0.0, 0.0, -c->gravity};
+    double u[3], n[12];
+    for (int i = 0; i < 3; ++i) u[i] = c->act_scale * clamp1(act[i]);
+    for (int i = 0; i < 3; ++i) {
+        double p = s[i], v = s[3 + i], a = s[6 + i], e = s[9 + i];
+        n[i] = p + c->dt * v;
+        n[3 + i] = v + c->dt * (a + g[i] - drag * v);
+        n[6 + i] = a + c->dt * lam * (u[i] - a);
+        n[9 + i] = (1.0 - c->ema_alpha) * e + c->ema_alpha * n[3 + i];
+    }
+    memcpy(o, n, sizeof(n));
+}
+
+/* Full quadrotor, Eq. 1: p' = v, v' = g + c z_B - R D R^T v (thrust along +z_B,
+ * c = T/m), q' = 1/2 q (x) [0, omega], omega' = J^-1 (tau - omega x J omega).
+ * The controller takes a thrust command T = m g (1 + clip(a0)) and a body-rate
+ * command omega_c = rate_scale * clip(a1..3); its torque is the body-rate part
+ * of the geometric controller, tau = J K (omega_c - omega) + omega x J omega.
+ * One explicit-Euler step; the quaternion is renormalised after the update. */
+void oc_rb_step(const oc_config *c, const double *s, const double *act, double *o)
+{
+    const double *p = s, *q = s + 3, *v = s + 7, *w = s + 10;
+    const double *J = c->inertia;
+    double T = c->mass * c->gravity * (1.0 + clamp1(act[0]));
+    double wc[3], Jw[3], gy[3], tau[3], wd[3], R[9], vb[3], dw[3], vd[3];
+    for (int i = 0; i < 3; ++i) wc[i] = c->rate_scale[i] * clamp1(act[1 + i]);
+    for (int i = 0; i < 3; ++i) Jw[i] = J[i] * w[i];
+    cross3(w, Jw, gy);
+    for (int i = 0; i < 3; ++i) tau[i] = J[i] * c->k_rate[i] * (wc[i] - w[i]) + gy[i];
+    for (int i = 0; i < 3; ++i) wd[i] = (tau[i] - gy[i]) / J[i];
+    oc_quat_to_rot(q, R);
+    for (int j = 0; j < 3; ++j) vb[j] = R[0 + j] * v[0] + R[3 + j] * v[1] + R[6 + j] * v[2];
+    for (int j = 0; j < 3; ++j) vb[j] *= c->drag_body[j];
+    for (int i = 0; i < 3; ++i) dw[i] = R[3 * i] * vb[0] + R[3 * i + 1] * vb[1] + R[3 * i + 2] * vb[2];
+    const double g[3] = {0.0, 0.0, -c->gravity};
+    for (int i = 0; i < 3; ++i) vd[i] = g[i] + (T / c->mass) * R[3 * i + 2] - dw[i];
+    double qw[4] = {0.0, w[0], w[1], w[2]}, qd[4];
+    quat_mul(q, qw, qd);
+    double n[13], qt[4];
+    for (int i = 0; i < 3; ++i) n[i] = p[i] + c->dt * v[i];
+    for (int k = 0; k < 4; ++k) qt[k] = q[k] + c->dt * 0.5 * qd[k];
+    double nq = sqrt(qt[0] * qt[0] + qt[1] * qt[1] + qt[2] * qt[2] + qt[3] * qt[3]);
+    for (int k = 0; k < 4; ++k) n[3 + k] = qt[k] / nq;
+    for (int i = 0; i < 3; ++i) n[7 + i] = v[i] + c->dt * vd[i];
+    for (int i = 0; i < 3; ++i) n[10 + i] = w[i] + c->dt * wd[i];
+    memcpy(o, n, sizeof(n));
+}
+
+/* ------------------------------------------------------ attitude (Sec. III-B) */
+
+/* Sensor pose of one agent: origin = position, R = body->world rotation.
+ * Rigid body: R(q).  Point mass: z_B along the thrust acceleration a; x_B is
+ * the horizontal projection of the velocity EMA, made orthogonal to z_B;
+ * y_B = z_B x x_B.  Degenerate cases: |a| < 1e-6 -> z_B = +z; horizontal
+ * heading (after orthogonalisation) shorter than 1e-6 -> world +x is used as
+ * heading instead, then world +y.  Returns a flag word: bit 0 = |a| fallback,
+ * bit 1 = heading fallback, bit 2 = a decision within 1e-3 relative of its
+ * threshold (ambiguous in FP32). */
+int oc_pose(const oc_config *c, const double *s, double *o, double *R)
+{
+    o[0] = s[0]; o[1] = s[1]; o[2] = s[2];
+    if (c->model == OC_RIGID) {
+        oc_quat_to_rot(s + 3, R);
+        return 0;
+    }
+    int flags = 0;
+    const double *a = s + 6, *e = s + 9;
+    double z[3], x[3], y[3];
+    double na = norm3(a);
+    if (na < 1e-6) { z[0] = 0; z[1] = 0; z[2] = 1; flags |= 1; }
+    else { z[0] = a[0] / na; z[1] = a[1] / na; z[2] = a[2] / na; }
+    if (fabs(na - 1e-6) < 1e-9) flags |= 4;
+    double h[3] = {e[0], e[1], 0.0}, hp[3];
+    double hz = dot3(h, z);
+    for (int i = 0; i < 3; ++i) hp[i] = h[i] - hz * z[i];
+    double nh = norm3(hp);
+    if (fabs(nh - 1e-6) < 1e-9) flags |= 4;
+    if (nh < 1e-6) {
+        flags |= 2;
+        double hx[3] = {1, 0, 0};
+        hz = dot3(hx, z);
+        for (int i = 0; i < 3; ++i) hp[i] = hx[i] - hz * z[i];
+        nh = norm3(hp);
+        if (nh < 1e-6) {
+            double hy[3] = {0, 1, 0};
+            hz = dot3(hy, z);
+            for (int i = 0; i < 3; ++i) hp[i] = hy[i] - hz * z[i];
+            nh = norm3(hp);
+        }
+    }
+    for (int i = 0; i < 3; ++i) x[i] = hp[i] / nh;
+    cross3(z, x, y);
+    for (int i = 0; i < 3; ++i) { R[3 * i] = x[i]; R[3 * i + 1] = y[i]; R[3 * i + 2] = z[i]; }
+    return flags;
+}
+
+/* ------------------------------------------------------- sensors (Sec. III-B) */
+
+/* Depth-camera rays in the body frame: pinhole looking along +x_B, image
+ * column i to the right (-y_B), row j downwards (-z_B), pixel centres,
+ * horizontal field of view hfov and square pixels.  Ray index j * W + i.
+ * dir [R][3] unit vectors; fac [R] = cos of the angle to the optical axis,
+ * which turns ray distance into z-depth. */
+void oc_cam_dirs(const oc_config *c, double *dir, double *fac)
+{
+    int W = c->cam_w, H = c->cam_h;
+    double th = tan(0.5 * c->cam_hfov), tv = th * (double)H / (double)W;
+    for (int j = 0; j < H; ++j)
+        for (int i = 0; i < W; ++i) {
+            double u = (2.0 * (i + 0.5) / W - 1.0) * th;
+            double v = (2.0 * (j + 0.5) / H - 1.0) * tv;
+            double d[3] = {1.0, -u, -v};
+            double n = norm3(d);
+            int r = j * W + i;
+            for (int k = 0; k < 3; ++k) dir[3 * r + k] = d[k] / n;
+            fac[r] = 1.0 / n;
+        }
+}
+
+/* LiDAR rays in the body frame: C channels at elevations evenly spaced over
+ * [elev_lo, elev_hi] (inclusive), Az azimuths k * 360/Az degrees from +x_B
+ * towards +y_B.  Ray index ch * Az + k. */
+void oc_lidar_dirs(const oc_config *c, double *dir)
+{
+    int C = c->lid_ch, Az = c->lid_az;
+    for (int ch = 0; ch < C; ++ch) {
+        double el = C > 1 ? c->lid_elev_lo + ch * (c->lid_elev_hi - c->lid_elev_lo) / (C - 1)
+                          : 0.5 * (c->lid_elev_lo + c->lid_elev_hi);
+        for (int k = 0; k < Az; ++k) {
+            double az = 2.0 * M_PI * k / Az;
+            int r = ch * Az + k;
+            dir[3 * r + 0] = cos(el) * cos(az);
+            dir[3 * r + 1] = cos(el) * sin(az);
+            dir[3 * r + 2] = sin(el);
+        }
+    }
+}
+
+/* Ray vs sphere: smallest t >= 0 with |o + t d - c| = r, |d| = 1; 0 when the
+ * origin is inside or on the sphere; +inf on a miss. */
+double oc_ray_sphere(const double *o, const double *d, const double *sp)
+{
+    double oc[3] = {sp[0] - o[0], sp[1] - o[1], sp[2] - o[2]};
+    double C = dot3(oc, oc) - sp[3] * sp[3];
+    if (C <= 0.0) return 0.0;
+    double b = dot3(d, oc);
+    double disc = b * b - C;
+    if (disc < 0.0 || b <= 0.0) return OC_INF;
+    return b - sqrt(disc);
+}
+
+/* Ray vs axis-aligned box by slabs: entry t_n = max_i min(t1_i, t2_i), exit
+ * t_f = min_i max(t1_i, t2_i); hit iff t_n <= t_f and t_f >= 0; 0 when the
+ * origin is inside.  A direction component of exactly 0 keeps the slab only
+ * if the origin lies between its planes.  *axis receives the entry axis. */
+double oc_ray_box(const double *o, const double *d, const double *bx, int *axis)
+{
+    double tn = -OC_INF, tf = OC_INF;
+    int ax = -1;
+    for (int i = 0; i < 3; ++i) {
+        if (d[i] == 0.0) {
+            if (o[i] < bx[i] || o[i] > bx[3 + i]) return OC_INF;
+            continue;
+        }
+        double t1 = (bx[i] - o[i]) / d[i], t2 = (bx[3 + i] - o[i]) / d[i];
+        double lo = t1 < t2 ? t1 : t2, hi = t1 < t2 ? t2 : t1;
+        if (lo > tn) { tn = lo; ax = i; }
+        if (hi < tf) tf = hi;
+    }
+    if (axis) *axis = ax;
+    if (tn > tf || tf < 0.0) return OC_INF;
+    return tn > 0.0 ? tn : 0.0;
+}
+
+/* Signed distance from a point to a sphere and to a box (exact Euclidean). */
+double oc_sdf_sphere(const double *p, const double *sp)
+{
+    double d[3] = {p[0] - sp[0], p[1] - sp[1], p[2] - sp[2]};
+    return norm3(d) - sp[3];
+}
+
+double oc_sdf_box(const double *p, const double *bx)
+{
+    double q[3], out = 0.0, in = -OC_INF;
+    for (int i = 0; i < 3; ++i) {
+        double ctr = 0.5 * (bx[i] + bx[3 + i]), half = 0.5 * (bx[3 + i] - bx[i]);
+        q[i] = fabs(p[i] - ctr) - half;
+        out += relu(q[i]) * relu(q[i]);
+        if (q[i] > in) in = q[i];
+    }
+    return sqrt(out) + (in < 0.0 ? in : 0.0);
+}
+
+/* gradient of the box SDF w.r.t. the point */
+static void sdf_box_grad(const double *p, const double *bx, double *gp)
+{
+    double q[3], sg[3], out = 0.0;
+    int am = 0;
+    for (int i = 0; i < 3; ++i) {
+        double ctr = 0.5 * (bx[i] + bx[3 + i]), half = 0.5 * (bx[3 + i] - bx[i]);
+        sg[i] = p[i] - ctr >= 0.0 ? 1.0 : -1.0;
+        q[i] = fabs(p[i] - ctr) - half;
+        out += relu(q[i]) * relu(q[i]);
+        if (q[i] > q[am]) am = i;
+    }
+    if (out > 0.0) {
+        double n = sqrt(out);
+        for (int i = 0; i < 3; ++i) gp[i] = relu(q[i]) * sg[i] / n;
+    } else {
+        for (int i = 0; i < 3; ++i) gp[i] = (i == am) ? sg[i] : 0.0;
+    }
+}
+
+/* One ray cast against every primitive of a map, brute force.  Returns t*
+ * (+inf on a miss) and the hit id (lowest id among exact ties; -1 on a miss).
+ * amb receives the ambiguity flags of this ray (bit 0: value, bit 1: gradient)
+ * given the clamp distance tclamp in ray length. */
+static double cast_ray(const double *o, const double *d, const double *sph, int ns,
+                       const double *box, int nb, int *hit, double tclamp, int *amb)
+{
+    double best = OC_INF, second = OC_INF;
+    int id = -1, flags = 0;
+    for (int k = 0; k < ns; ++k) {
+        double t = oc_ray_sphere(o, d, sph + 4 * k);
+        if (t < best) { second = best; best = t; id = k; }
+        else if (t < second) second = t;
+    }
+    for (int k = 0; k < nb; ++k) {
+        double t = oc_ray_box(o, d, box + 6 * k, NULL);
+        if (t < best) { second = best; best = t; id = ns + k; }
+        else if (t < second) second = t;
+    }
+    /* near-degenerate decisions that could change the value in FP32 */
+    double reach = (best < tclamp ? best : tclamp) + 1e-3;
+    for (int k = 0; k < ns; ++k) {
+        const double *sp = sph + 4 * k;
+        double oc[3] = {sp[0] - o[0], sp[1] - o[1], sp[2] - o[2]};
+        double C = dot3(oc, oc) - sp[3] * sp[3];
+        double b = dot3(d, oc);
+        if (fabs(norm3(oc) - sp[3]) < AMB_INSIDE) flags |= 3;
+        double disc = b * b - C;
+        if (b > 0.0 && b < reach && fabs(disc) < AMB_DISC * (b * b > 1.0 ? b * b : 1.0)) flags |= 3;
+    }
+    for (int k = 0; k < nb; ++k) {
+        const double *bx = box + 6 * k;
+        if (fabs(oc_sdf_box(o, bx)) < AMB_INSIDE) flags |= 3;
+        double tn = -OC_INF, tf = OC_INF;
+        int ok = 1;
+        for (int i = 0; i < 3; ++i) {
+            if (d[i] == 0.0) { if (o[i] < bx[i] || o[i] > bx[3 + i]) ok = 0; continue; }
+            double t1 = (bx[i] - o[i]) / d[i], t2 = (bx[3 + i] - o[i]) / d[i];
+            double lo = t1 < t2 ? t1 : t2, hi = t1 < t2 ? t2 : t1;
+            if (lo > tn) tn = lo;
+            if (hi < tf) tf = hi;
+        }
+        if (ok && tn > 0.0 && tn < reach && fabs(tf - tn) < AMB_SLAB) flags |= 3;
+    }
+    /* gradient-only ambiguities: second hit close, range clamp, grazing,
+     * entry through an edge */
+    if (best < OC_INF) {
+        if (second - best < AMB_GAP) flags |= 2;
+        if (fabs(best - tclamp) < AMB_RANGE) flags |= 2;
+        if (best > 0.0 && best < tclamp) {
+            double n[3];
+            if (id < ns) {
+                const double *sp = sph + 4 * id;
+                for (int i = 0; i < 3; ++i) n[i] = (o[i] + best * d[i] - sp[i]) / sp[3];
+            } else {
+                const double *bx = box + 6 * (id - ns);
+                int ax = -1;
+                oc_ray_box(o, d, bx, &ax);
+                for (int i = 0; i < 3; ++i) n[i] = 0.0;
+                if (ax >= 0) n[ax] = d[ax] > 0 ? -1.0 : 1.0;
+                /* two slab entry times within AMB_EDGE: the ray enters at an edge */
+                double tl[3];
+                for (int i = 0; i < 3; ++i) {
+                    if (d[i] == 0.0) { tl[i] = -OC_INF; continue; }
+                    double t1 = (bx[i] - o[i]) / d[i], t2 = (bx[3 + i] - o[i]) / d[i];
+                    tl[i] = t1 < t2 ? t1 : t2;
+                }
+                for (int i = 0; i < 3; ++i)
+                    if (i != ax && fabs(tl[i] - best) < AMB_EDGE * (best > 1.0 ? best : 1.0)) flags |= 2;
+            }
+            if (fabs(dot3(n, d)) < AMB_GRAZE) flags |= 2;
+        }
+    }
+    *hit = id;
+    *amb = flags;
+    return best;
+}
+
+/* -------------------------------------------------- obstacles and collisions */
+
+/* Minimum signed distance from p to the map's primitives and the arg-min id
+ * (lowest id among exact ties; -1 and +inf for an empty map).  gap receives
+ * the distance between the two smallest values. */
+static double sdf_min(const double *p, const double *sph, int ns, const double *box, int nb,
+                      int *id, double *gap)
+{
+    double best = OC_INF, second = OC_INF;
+    int bi = -1;
+    for (int k = 0; k < ns; ++k) {
+        double s = oc_sdf_sphere(p, sph + 4 * k);
+        if (s < best) { second = best; best = s; bi = k; }
+        else if (s < second) second = s;
+    }
+    for (int k = 0; k < nb; ++k) {
+        double s = oc_sdf_box(p, box + 6 * k);
+        if (s < best) { second = best; best = s; bi = ns + k; }
+        else if (s < second) second = s;
+    }
+    *id = bi;
+    *gap = second - best;
+    return best;
+}
+
+static void sdf_grad(const double *p, const double *sph, int ns, const double *box, int id,
+                     double *gp)
+{
+    if (id < ns) {
+        const double *sp = sph + 4 * id;
+        double d[3] = {p[0] - sp[0], p[1] - sp[1], p[2] - sp[2]};
+        double n = norm3(d);
+        for (int i = 0; i < 3; ++i) gp[i] = n > 0.0 ? d[i] / n : 0.0;
+    } else {
+        sdf_box_grad(p, box + 6 * (id - ns), gp);
+    }
+}
+
+/* ------------------------------------------------------------ rollout state */
+
+typedef struct {
+    const oc_config *c;
+    const oc_scene *sc;
+    int D, A, NM, Rc, Rl;
+    double *cam_dir, *cam_fac, *lid_dir;
+} ctx_t;
+
+static void ctx_init(ctx_t *x, const oc_config *c, const oc_scene *sc)
+{
+    x->c = c; x->sc = sc;
+    x->D = oc_state_dim(c->model);
+    x->A = oc_action_dim(c->model);
+    x->NM = c->n_env * c->n_agent;
+    x->Rc = c->cam_w > 0 ? c->cam_w * c->cam_h : 0;
+    x->Rl = c->lid_ch > 0 ? c->lid_ch * c->lid_az : 0;
+    x->cam_dir = x->Rc ? malloc(sizeof(double) * 3 * x->Rc) : NULL;
+    x->cam_fac = x->Rc ? malloc(sizeof(double) * x->Rc) : NULL;
+    x->lid_dir = x->Rl ? malloc(sizeof(double) * 3 * x->Rl) : NULL;
+    if (x->Rc) oc_cam_dirs(c, x->cam_dir, x->cam_fac);
+    if (x->Rl) oc_lidar_dirs(c, x->lid_dir);
+}
+
+static void ctx_free(ctx_t *x)
+{
+    free(x->cam_dir); free(x->cam_fac); free(x->lid_dir);
+}
+
+static void map_of(const ctx_t *x, int env, const double **sph, int *ns, const double **box, int *nb)
+{
+    int m = x->sc->env_map[env];
+    *sph = x->sc->spheres + 4 * x->sc->sph_off[m];
+    *ns = x->sc->sph_off[m + 1] - x->sc->sph_off[m];
+    *box = x->sc->boxes + 6 * x->sc->box_off[m];
+    *nb = x->sc->box_off[m + 1] - x->sc->box_off[m];
+}
+
+static void dyn_step(const ctx_t *x, int env, const double *s, const double *a, double *o)
+{
+    if (x->c->model == OC_RIGID) { oc_rb_step(x->c, s, a, o); return; }
+    double drag = x->sc->drag_env ? x->sc->drag_env[env] : x->c->drag;
+    double lam = x->sc->lam_env ? x->sc->lam_env[env] : x->c->lam;
+    oc_pm_step(x->c, drag, lam, s, a, o);
+}
+
+/* Render one agent: world ray = R * body ray, origin = position.  Camera
+ * output is z-depth min(t* fac, range); lidar output is min(t*, range). */
+static void render_agent(const ctx_t *x, int env, const double *s, double *depth, double *lidar,
+                         int32_t *hc, int32_t *hl, uint8_t *ac, uint8_t *al)
+{
+    const double *sph, *box;
+    int ns, nb;
+    map_of(x, env, &sph, &ns, &box, &nb);
+    double o[3], R[9];
+    int pf = oc_pose(x->c, s, o, R);
+    for (int r = 0; r < x->Rc; ++r) {
+        const double *db = x->cam_dir + 3 * r;
+        double d[3];
+        for (int i = 0; i < 3; ++i) d[i] = R[3 * i] * db[0] + R[3 * i + 1] * db[1] + R[3 * i + 2] * db[2];
+        int id, amb;
+        double tcl = x->c->cam_range / x->cam_fac[r];
+        double t = cast_ray(o, d, sph, ns, box, nb, &id, tcl, &amb);
+        double z = t * x->cam_fac[r];
+        if (depth) depth[r] = z < x->c->cam_range ? z : x->c->cam_range;
+        hc[r] = id;
+        ac[r] = (uint8_t)(amb | ((pf & 4) ? 3 : 0));
+    }
+    for (int r = 0; r < x->Rl; ++r) {
+        const double *db = x->lid_dir + 3 * r;
+        double d[3];
+        for (int i = 0; i < 3; ++i) d[i] = R[3 * i] * db[0] + R[3 * i + 1] * db[1] + R[3 * i + 2] * db[2];
+        int id, amb;
+        double t = cast_ray(o, d, sph, ns, box, nb, &id, x->c->lid_range, &amb);
+        if (lidar) lidar[r] = t < x->c->lid_range ? t : x->c->lid_range;
+        hl[r] = id;
+        al[r] = (uint8_t)(amb | ((pf & 4) ? 3 : 0));
+    }
+}
+
+/* Render the sensors of given states [NM][D] (no dynamics): used for the
+ * observation of the initial state. */
+int oc_render(const oc_config *c, const oc_scene *sc, const double *s, double *depth,
+              double *lidar, int32_t *hit_cam, int32_t *hit_lid, uint8_t *amb_cam,
+              uint8_t *amb_lid)
+{
+    ctx_t x;
+    ctx_init(&x, c, sc);
+    int M = c->n_agent;
+    for (int i = 0; i < x.NM; ++i)
+        render_agent(&x, i / M, s + (size_t)i * x.D,
+                     depth ? depth + (size_t)i * x.Rc : NULL, lidar ? lidar + (size_t)i * x.Rl : NULL,
+                     hit_cam + (size_t)i * x.Rc, hit_lid + (size_t)i * x.Rl,
+                     amb_cam + (size_t)i * x.Rc, amb_lid + (size_t)i * x.Rl);
+    ctx_free(&x);
+    return 0;
+}
+
+/* One environment step for all agents of env (Sec. III-C, III-D):
+ * dynamics -> collision and rewards on the new state -> termination ->
+ * reset of the whole environment from the pool -> sensor rendering of the
+ * (possibly reset) new state.  Collision: obstacle SDF < r_quad, position
+ * outside [bound_lo, bound_hi], or another agent of the env closer than
+ * d_agent.  R_ctrl = -w_pos |e|^(1 or 2) - w_obs relu(d_safe - sdf)^2
+ *                    - w_act |action|^2 - w_agent sum_j relu(d_agent - d_ij)^2,
+ * R_goal = -1 on collision, +1 within success_radius of the target, else 0. */
+static void env_step(const ctx_t *x, int env, int t, const double *s_t, const double *act_t,
+                     int32_t *pool_k, double *s_next, double *spre, double *r_ctrl,
+                     int8_t *r_goal, uint8_t *done, double *depth, double *lidar,
+                     int32_t *hc, int32_t *hl, uint8_t *ac, uint8_t *al, uint8_t *amb_step,
+                     int32_t *sdf_id)
+{
+    const oc_config *c = x->c;
+    int M = c->n_agent, D = x->D, A = x->A;
+    const double *sph, *box;
+    int ns, nb;
+    map_of(x, env, &sph, &ns, &box, &nb);
+    int i0 = env * M;
+    int any = 0;
+    int *coll = calloc((size_t)M, sizeof(int));
+    for (int m = 0; m < M; ++m) {
+        int i = i0 + m;
+        dyn_step(x, env, s_t + (size_t)i * D, act_t + (size_t)i * A, spre + (size_t)i * D);
+    }
+    for (int m = 0; m < M; ++m) {
+        int i = i0 + m, id, flags = 0;
+        const double *p = spre + (size_t)i * D;
+        const double *a = act_t + (size_t)i * A;
+        double gap;
+        double sd = sdf_min(p, sph, ns, box, nb, &id, &gap);
+        sdf_id[i] = id;
+        int col = sd < c->r_quad;
+        if (fabs(sd - c->r_quad) < AMB_STEP) flags |= 1;
+        for (int k = 0; k < 3; ++k) {
+            if (p[k] < c->bound_lo[k] || p[k] > c->bound_hi[k]) col = 1;
+            if (fabs(p[k] - c->bound_lo[k]) < AMB_STEP || fabs(p[k] - c->bound_hi[k]) < AMB_STEP) flags |= 1;
+        }
+        double pair = 0.0;
+        for (int n = 0; n < M; ++n) {
+            if (n == m) continue;
+            const double *q = spre + (size_t)(i0 + n) * D;
+            double dd[3] = {p[0] - q[0], p[1] - q[1], p[2] - q[2]};
+            double dij = norm3(dd);
+            if (dij < c->d_agent) col = 1;
+            if (fabs(dij - c->d_agent) < AMB_STEP) flags |= 1;
+            pair += relu(c->d_agent - dij) * relu(c->d_agent - dij);
+        }
+        const double *tg = x->sc->targets + 3 * (size_t)i;
+        double e[3] = {p[0] - tg[0], p[1] - tg[1], p[2] - tg[2]};
+        double ne = norm3(e);
+        double pos = c->pos_sq ? ne * ne : ne;
+        double ob = (c->w_obs != 0.0 && sd < OC_INF) ? relu(c->d_safe - sd) : 0.0;
+        double aa = 0.0;
+        for (int k = 0; k < A; ++k) aa += a[k] * a[k];
+        r_ctrl[i] = -c->w_pos * pos - c->w_obs * ob * ob - c->w_act * aa - c->w_agent * pair;
+        r_goal[i] = (int8_t)(col ? -1 : (ne < c->success_radius ? 1 : 0));
+        if (fabs(ne - c->success_radius) < AMB_STEP) flags |= 1;
+        /* gradient kinks: arg-min tie of an active obstacle term, norm at 0,
+         * action clip boundary, box SDF on its medial axis */
+        if (ob > 0.0 && gap < AMB_STEP) flags |= 2;
+        if (!c->pos_sq && ne < 1e-6) flags |= 2;
+        for (int k = 0; k < A; ++k)
+            if (fabs(fabs(a[k]) - 1.0) < 1e-9) flags |= 2;
+        amb_step[i] = (uint8_t)flags;
+        coll[m] = col;
+        any |= col;
+    }
+    int dn = c->terminate && any;
+    for (int m = 0; m < M; ++m) {
+        int i = i0 + m;
+        done[i] = (uint8_t)dn;
+        if (dn && c->pool_size > 0) {
+            int k = pool_k[env] % c->pool_size;
+            memcpy(s_next + (size_t)i * D, x->sc->pool + ((size_t)k * x->NM + i) * D, sizeof(double) * D);
+        } else {
+            memcpy(s_next + (size_t)i * D, spre + (size_t)i * D, sizeof(double) * D);
+        }
+    }
+    if (dn) pool_k[env] += 1;
+    for (int m = 0; m < M; ++m) {
+        int i = i0 + m;
+        double o[3], R[9];
+        if (c->model == OC_PM && (oc_pose(c, s_next + (size_t)i * D, o, R) & 4)) amb_step[i] |= 4;
+        render_agent(x, env, s_next + (size_t)i * D,
+                     depth ? depth + (size_t)i * x->Rc : NULL, lidar ? lidar + (size_t)i * x->Rl : NULL,
+                     hc + (size_t)i * x->Rc, hl + (size_t)i * x->Rl,
+                     ac + (size_t)i * x->Rc, al + (size_t)i * x->Rl);
+    }
+    (void)t;
+    free(coll);
+}
+
+/* Rollout over the horizon.  states [T+1][NM][D] receives s_0..s_T (after
+ * resets), spre [T][NM][D] the states before reset.  pool_k [N] is the reset
+ * counter of each env, read and advanced.  depth/lidar and their hit ids and
+ * flags are [T][NM][R]; output t is the observation of s_{t+1}.  n_threads
+ * parallelises over environments only. */
+int oc_rollout(const oc_config *c, const oc_scene *sc, const double *s0, int32_t *pool_k,
+               const double *act, double *states, double *spre, double *r_ctrl, int8_t *r_goal,
+               uint8_t *done, double *depth, double *lidar, int32_t *hit_cam, int32_t *hit_lid,
+               uint8_t *amb_cam, uint8_t *amb_lid, uint8_t *amb_step, int32_t *sdf_id,
+               int n_threads)
+{
+    ctx_t x;
+    ctx_init(&x, c, sc);
+    int N = c->n_env, M = c->n_agent, T = c->horizon, D = x.D, A = x.A, NM = x.NM;
+    memcpy(states, s0, sizeof(double) * (size_t)NM * D);
+#ifdef _OPENMP
+    int nt = n_threads > 0 ? n_threads : omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nt)
+#endif
+    for (int env = 0; env < N; ++env) {
+        for (int t = 0; t < T; ++t) {
+            size_t sT = (size_t)t * NM;
+            env_step(&x, env, t, states + sT * D, act + sT * A, pool_k,
+                     states + (sT + NM) * D, spre + sT * D, r_ctrl + sT, r_goal + sT, done + sT,
+                     depth ? depth + sT * x.Rc : NULL, lidar ? lidar + sT * x.Rl : NULL,
+                     hit_cam + sT * x.Rc, hit_lid + sT * x.Rl, amb_cam + sT * x.Rc,
+                     amb_lid + sT * x.Rl, amb_step + sT, sdf_id + sT);
+        }
+    }
+    (void)M;
+    ctx_free(&x);
+    return 0;
+}
+
+/* ------------------------------------------------------------------ adjoint */
+
+/* VJP of the point-mass step (Eq. 3, explicit Euler): given the cotangent go of
+ * the new state, accumulate into gs (old state) and ga (raw action). */
+static void pm_step_vjp(const oc_config *c, double drag, double lam, const double *s,
+                        const double *act, const double *go, double *gs, double *ga)
+{
+    double al = c->ema_alpha, dt = c->dt;
+    for (int i = 0; i < 3; ++i) {
+        double gp = go[i], gv = go[3 + i], gA = go[6 + i], ge = go[9 + i];
+        gv += al * ge;                 /* ema' = (1-al) ema + al v' */
+        gs[9 + i] += (1.0 - al) * ge;
+        gs[i] += gp;                   /* p' = p + dt v */
+        gs[3 + i] += dt * gp;
+        gs[3 + i] += (1.0 - dt * drag) * gv; /* v' = v + dt (a + g - d v) */
+        gs[6 + i] += dt * gv;
+        gs[6 + i] += (1.0 - dt * lam) * gA;  /* a' = a + dt lam (u - a) */
+        double gu = dt * lam * gA;
+        ga[i] += c->act_scale * dclamp1(act[i]) * gu;
+    }
+    (void)s;
+}
+
+/* VJP of the rigid-body step (Eq. 1 with the rate controller, explicit Euler,
+ * quaternion renormalisation). */
+static void rb_step_vjp(const oc_config *c, const double *s, const double *act, const double *go,
+                        double *gs, double *ga)
+{
+    const double *q = s + 3, *v = s + 7, *w = s + 10;
+    const double *J = c->inertia;
+    double dt = c->dt, m = c->mass;
+    /* recompute the forward intermediates */
+    double T = m * c->gravity * (1.0 + clamp1(act[0]));
+    double R[9], vb[3], dvb[3], Jw[3], qw[4] = {0.0, w[0], w[1], w[2]}, qd[4], qt[4];
+    oc_quat_to_rot(q, R);
+    for (int j = 0; j < 3; ++j) vb[j] = R[0 + j] * v[0] + R[3 + j] * v[1] + R[6 + j] * v[2];
+    for (int j = 0; j < 3; ++j) dvb[j] = c->drag_body[j] * vb[j];
+    for (int i = 0; i < 3; ++i) Jw[i] = J[i] * w[i];
+    quat_mul(q, qw, qd);
+    for (int k = 0; k < 4; ++k) qt[k] = q[k] + dt * 0.5 * qd[k];
+    double nq = sqrt(qt[0] * qt[0] + qt[1] * qt[1] + qt[2] * qt[2] + qt[3] * qt[3]);
+    double qn[4] = {qt[0] / nq, qt[1] / nq, qt[2] / nq, qt[3] / nq};
+
+    const double *gp = go, *gqn = go + 3, *gvn = go + 7, *gwn = go + 10;
+    double *gsp = gs, *gsq = gs + 3, *gsv = gs + 7, *gsw = gs + 10;
+    /* p' = p + dt v */
+    for (int i = 0; i < 3; ++i) { gsp[i] += gp[i]; gsv[i] += dt * gp[i]; }
+    /* v' = v + dt vd */
+    double gvd[3];
+    for (int i = 0; i < 3; ++i) { gsv[i] += gvn[i]; gvd[i] = dt * gvn[i]; }
+    /* q' = qt / |qt|, qt = q + dt/2 qd */
+    double qg = qn[0] * gqn[0] + qn[1] * gqn[1] + qn[2] * gqn[2] + qn[3] * gqn[3];
+    double gqt[4], gqd[4];
+    for (int k = 0; k < 4; ++k) gqt[k] = (gqn[k] - qn[k] * qg) / nq;
+    for (int k = 0; k < 4; ++k) { gsq[k] += gqt[k]; gqd[k] = 0.5 * dt * gqt[k]; }
+    /* omega' = omega + dt wd */
+    double gwd[3];
+    for (int i = 0; i < 3; ++i) { gsw[i] += gwn[i]; gwd[i] = dt * gwn[i]; }
+    /* qd = q (x) (0, w): w-part -v.w, vector part q_w w + v x w */
+    {
+        double vq[3] = {q[1], q[2], q[3]}, gvec[3] = {gqd[1], gqd[2], gqd[3]}, t3[3];
+        gsq[0] += dot3(gvec, w);
+        cross3(w, gvec, t3);
+        for (int i = 0; i < 3; ++i) gsq[1 + i] += -gqd[0] * w[i] + t3[i];
+        cross3(gvec, vq, t3);
+        for (int i = 0; i < 3; ++i) gsw[i] += -gqd[0] * vq[i] + q[0] * gvec[i] + t3[i];
+    }
+    /* vd = g + (T/m) R e3 - R dvb, dvb = Dd (R^T v) */
+    double gR[9] = {0}, gT = 0.0, gdvb[3], gvb[3];
+    for (int i = 0; i < 3; ++i) {
+        gT += R[3 * i + 2] * gvd[i] / m;
+        gR[3 * i + 2] += (T / m) * gvd[i];
+        for (int j = 0; j < 3; ++j) gR[3 * i + j] += -gvd[i] * dvb[j];
+    }
+    for (int j = 0; j < 3; ++j) gdvb[j] = -(R[0 + j] * gvd[0] + R[3 + j] * gvd[1] + R[6 + j] * gvd[2]);
+    for (int j = 0; j < 3; ++j) gvb[j] = c->drag_body[j] * gdvb[j];
+    for (int i = 0; i < 3; ++i) {
+        gsv[i] += R[3 * i] * gvb[0] + R[3 * i + 1] * gvb[1] + R[3 * i + 2] * gvb[2];
+        for (int j = 0; j < 3; ++j) gR[3 * i + j] += v[i] * gvb[j];
+    }
+    quat_to_rot_vjp(q, gR, gsq);
+    /* wd = (tau - gy) / J; tau = J K (wc - w) + gy; gy = w x Jw */
+    double gtau[3], ggy[3], gwc[3], t3[3];
+    for (int i = 0; i < 3; ++i) { gtau[i] = gwd[i] / J[i]; ggy[i] = -gwd[i] / J[i]; }
+    for (int i = 0; i < 3; ++i) {
+        gwc[i] = J[i] * c->k_rate[i] * gtau[i];
+        gsw[i] += -J[i] * c->k_rate[i] * gtau[i];
+        ggy[i] += gtau[i];
+    }
+    cross3(Jw, ggy, t3);
+    for (int i = 0; i < 3; ++i) gsw[i] += t3[i];
+    cross3(ggy, w, t3);
+    for (int i = 0; i < 3; ++i) gsw[i] += J[i] * t3[i];
+    /* T = m g (1 + clip a0), wc = rate_scale clip(a1..3) */
+    ga[0] += m * c->gravity * dclamp1(act[0]) * gT;
+    for (int i = 0; i < 3; ++i) ga[1 + i] += c->rate_scale[i] * dclamp1(act[1 + i]) * gwc[i];
+}
+
+/* VJP of the sensor pose: gR (row-major) and go (origin) into gs. */
+static void pose_vjp(const oc_config *c, const double *s, const double *go, const double *gR,
+                     double *gs)
+{
+    for (int i = 0; i < 3; ++i) gs[i] += go[i];
+    if (c->model == OC_RIGID) { quat_to_rot_vjp(s + 3, gR, gs + 3); return; }
+    const double *a = s + 6, *e = s + 9;
+    double z[3], hp[3], x[3], h[3];
+    double na = norm3(a);
+    int zfb = na < 1e-6;
+    if (zfb) { z[0] = 0; z[1] = 0; z[2] = 1; }
+    else for (int i = 0; i < 3; ++i) z[i] = a[i] / na;
+    h[0] = e[0]; h[1] = e[1]; h[2] = 0.0;
+    double hz = dot3(h, z);
+    for (int i = 0; i < 3; ++i) hp[i] = h[i] - hz * z[i];
+    double nh = norm3(hp);
+    int hfb = 0;
+    if (nh < 1e-6) {
+        hfb = 1;
+        h[0] = 1; h[1] = 0; h[2] = 0;
+        hz = dot3(h, z);
+        for (int i = 0; i < 3; ++i) hp[i] = h[i] - hz * z[i];
+        nh = norm3(hp);
+        if (nh < 1e-6) {
+            h[0] = 0; h[1] = 1; h[2] = 0;
+            hz = dot3(h, z);
+            for (int i = 0; i < 3; ++i) hp[i] = h[i] - hz * z[i];
+            nh = norm3(hp);
+        }
+    }
+    for (int i = 0; i < 3; ++i) x[i] = hp[i] / nh;
+    double gx[3], gy[3], gz[3], t3[3];
+    for (int i = 0; i < 3; ++i) { gx[i] = gR[3 * i]; gy[i] = gR[3 * i + 1]; gz[i] = gR[3 * i + 2]; }
+    /* y = z x x */
+    cross3(x, gy, t3);
+    for (int i = 0; i < 3; ++i) gz[i] += t3[i];
+    cross3(gy, z, t3);
+    for (int i = 0; i < 3; ++i) gx[i] += t3[i];
+    /* x = hp / |hp| */
+    double xg = dot3(x, gx), ghp[3];
+    for (int i = 0; i < 3; ++i) ghp[i] = (gx[i] - x[i] * xg) / nh;
+    /* hp = h - (h.z) z */
+    double zg = dot3(z, ghp);
+    for (int i = 0; i < 3; ++i) gz[i] += -hz * ghp[i] - h[i] * zg;
+    if (!hfb) {
+        gs[9] += ghp[0] - z[0] * zg;
+        gs[10] += ghp[1] - z[1] * zg;
+    }
+    /* z = a / |a| */
+    if (!zfb) {
+        double zz = dot3(z, gz);
+        for (int i = 0; i < 3; ++i) gs[6 + i] += (gz[i] - z[i] * zz) / na;
+    }
+}
+
+/* VJP of one ray's output w.r.t. origin o and world direction d.  g is the
+ * cotangent of the output, fac the factor from t* to the output (z-depth
+ * factor or 1), clampv the output clamp.  Zero on a miss, a clamped output,
+ * or an origin inside a primitive (t* = 0).  The hit-point normal n gives
+ * dt/do = -n / (n.d) and dt/dd = -t n / (n.d). */
+static void ray_vjp(const double *o, const double *d, const double *sph, int ns, const double *box,
+                    int id, double g, double fac, double clampv, double *go, double *gd)
+{
+    if (id < 0 || g == 0.0) return;
+    double t, n[3];
+    if (id < ns) {
+        const double *sp = sph + 4 * id;
+        t = oc_ray_sphere(o, d, sp);
+        if (!(t > 0.0) || t * fac >= clampv) return;
+        for (int i = 0; i < 3; ++i) n[i] = (o[i] + t * d[i] - sp[i]) / sp[3];
+    } else {
+        int ax = -1;
+        t = oc_ray_box(o, d, box + 6 * (id - ns), &ax);
+        if (!(t > 0.0) || t * fac >= clampv || ax < 0) return;
+        for (int i = 0; i < 3; ++i) n[i] = 0.0;
+        n[ax] = d[ax] > 0.0 ? -1.0 : 1.0;
+    }
+    double nd = dot3(n, d);
+    double gt = g * fac;
+    for (int i = 0; i < 3; ++i) {
+        go[i] += gt * (-n[i] / nd);
+        gd[i] += gt * (-t * n[i] / nd);
+    }
+}
+
+/* render VJP of one agent: accumulates into gs (state cotangent). */
+static void render_vjp(const ctx_t *x, int env, const double *s, const int32_t *hc,
+                       const int32_t *hl, const double *gdep, const double *glid, double *gs)
+{
+    const double *sph, *box;
+    int ns, nb;
+    map_of(x, env, &sph, &ns, &box, &nb);
+    double o[3], R[9], go[3] = {0, 0, 0}, gR[9] = {0};
+    oc_pose(x->c, s, o, R);
+    for (int r = 0; gdep && r < x->Rc; ++r) {
+        const double *db = x->cam_dir + 3 * r;
+        double d[3], gd[3] = {0, 0, 0};
+        for (int i = 0; i < 3; ++i) d[i] = R[3 * i] * db[0] + R[3 * i + 1] * db[1] + R[3 * i + 2] * db[2];
+        ray_vjp(o, d, sph, ns, box, hc[r], gdep[r], x->cam_fac[r], x->c->cam_range, go, gd);
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) gR[3 * i + j] += gd[i] * db[j];
+    }
+    for (int r = 0; glid && r < x->Rl; ++r) {
+        const double *db = x->lid_dir + 3 * r;
+        double d[3], gd[3] = {0, 0, 0};
+        for (int i = 0; i < 3; ++i) d[i] = R[3 * i] * db[0] + R[3 * i + 1] * db[1] + R[3 * i + 2] * db[2];
+        ray_vjp(o, d, sph, ns, box, hl[r], glid[r], 1.0, x->c->lid_range, go, gd);
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) gR[3 * i + j] += gd[i] * db[j];
+    }
+    (void)nb;
+    pose_vjp(x->c, s, go, gR, gs);
+}
+
+/* Adjoint of the rollout (Eq. 5 applied step by step, reverse order).  Inputs
+ * are the actions and the records of oc_rollout; cotangents g_r [T][NM] of
+ * R_ctrl, g_depth / g_lidar [T][NM][R] (NULL = zero), g_sT [NM][D] of the
+ * final state (NULL = zero).  Outputs g_a [T][NM][A] and g_s0 [NM][D].
+ * A reset replaces the state, so no cotangent crosses it. */
+int oc_backward(const oc_config *c, const oc_scene *sc, const double *act, const double *states,
+                const double *spre, const uint8_t *done, const int32_t *hit_cam,
+                const int32_t *hit_lid, const double *g_r, const double *g_depth,
+                const double *g_lidar, const double *g_sT, double *g_a, double *g_s0,
+                int n_threads)
+{
+    ctx_t x;
+    ctx_init(&x, c, sc);
+    int N = c->n_env, M = c->n_agent, T = c->horizon, D = x.D, A = x.A, NM = x.NM;
+    memset(g_a, 0, sizeof(double) * (size_t)T * NM * A);
+#ifdef _OPENMP
+    int nt = n_threads > 0 ? n_threads : omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nt)
+#endif
+    for (int env = 0; env < N; ++env) {
+        const double *sph, *box;
+        int ns, nb;
+        map_of(&x, env, &sph, &ns, &box, &nb);
+        int i0 = env * M;
+        double *gs = calloc((size_t)M * D, sizeof(double));
+        double *gpre = calloc((size_t)M * D, sizeof(double));
+        if (g_sT) memcpy(gs, g_sT + (size_t)i0 * D, sizeof(double) * M * D);
+        for (int t = T - 1; t >= 0; --t) {
+            size_t sT = (size_t)t * NM;
+            int dn = done[sT + i0];
+            /* cotangent of s_{t+1} (after reset) -> before reset */
+            for (int m = 0; m < M; ++m) {
+                int i = i0 + m;
+                double *g = gs + (size_t)m * D;
+                if (!dn)
+                    render_vjp(&x, env, states + (sT + NM + i) * D,
+                               hit_cam + (sT + i) * x.Rc, hit_lid + (sT + i) * x.Rl,
+                               g_depth ? g_depth + (sT + i) * x.Rc : NULL,
+                               g_lidar ? g_lidar + (sT + i) * x.Rl : NULL, g);
+                for (int k = 0; k < D; ++k) gpre[(size_t)m * D + k] = dn ? 0.0 : g[k];
+            }
+            /* reward on the state before reset */
+            for (int m = 0; m < M; ++m) {
+                int i = i0 + m, id;
+                double gr = g_r[sT + i];
+                const double *p = spre + (sT + i) * D;
+                const double *a = act + (sT + i) * A;
+                double *gp = gpre + (size_t)m * D;
+                double *gaa = g_a + (sT + i) * A;
+                const double *tg = sc->targets + 3 * (size_t)i;
+                double e[3] = {p[0] - tg[0], p[1] - tg[1], p[2] - tg[2]};
+                double ne = norm3(e);
+                for (int k = 0; k < 3; ++k) {
+                    double dpos = c->pos_sq ? 2.0 * e[k] : (ne > 0.0 ? e[k] / ne : 0.0);
+                    gp[k] += -gr * c->w_pos * dpos;
+                }
+                if (c->w_obs != 0.0) {
+                    double gap;
+                    double sd = sdf_min(p, sph, ns, box, nb, &id, &gap);
+                    double ob = sd < OC_INF ? relu(c->d_safe - sd) : 0.0;
+                    if (ob > 0.0) {
+                        double gsd[3];
+                        sdf_grad(p, sph, ns, box, id, gsd);
+                        for (int k = 0; k < 3; ++k) gp[k] += gr * 2.0 * c->w_obs * ob * gsd[k];
+                    }
+                }
+                for (int k = 0; k < A; ++k) gaa[k] += -2.0 * c->w_act * gr * a[k];
+                for (int n = 0; n < M; ++n) {
+                    if (n == m) continue;
+                    const double *q = spre + (sT + i0 + n) * D;
+                    double dd[3] = {p[0] - q[0], p[1] - q[1], p[2] - q[2]};
+                    double dij = norm3(dd);
+                    double sv = relu(c->d_agent - dij);
+                    if (sv > 0.0 && dij > 0.0) {
+                        /* r_m and r_n both hold -w sv^2; d/dp_m of -w sv^2 = 2 w sv dd/dij */
+                        double gsum = gr + g_r[sT + i0 + n];
+                        for (int k = 0; k < 3; ++k) gp[k] += gsum * 2.0 * c->w_agent * sv * dd[k] / dij;
+                    }
+                }
+            }
+            /* dynamics */
+            for (int m = 0; m < M; ++m) {
+                int i = i0 + m;
+                double *g = gs + (size_t)m * D;
+                memset(g, 0, sizeof(double) * D);
+                const double *s = states + (sT + i) * D;
+                const double *a = act + (sT + i) * A;
+                if (c->model == OC_RIGID)
+                    rb_step_vjp(c, s, a, gpre + (size_t)m * D, g, g_a + (sT + i) * A);
+                else {
+                    double drag = sc->drag_env ? sc->drag_env[env] : c->drag;
+                    double lam = sc->lam_env ? sc->lam_env[env] : c->lam;
+                    pm_step_vjp(c, drag, lam, s, a, gpre + (size_t)m * D, g, g_a + (sT + i) * A);
+                }
+            }
+        }
+        memcpy(g_s0 + (size_t)i0 * D, gs, sizeof(double) * M * D);
+        free(gs);
+        free(gpre);
+    }
+    ctx_free(&x);
+    return 0;
+}
+
+/* Scalar loss of a recorded rollout with given cotangents, i.e. the linear
+ * functional whose gradient oc_backward returns:
+ *   L = sum g_r r_ctrl + sum g_depth depth + sum g_lidar lidar + g_sT . s_T.
+ * Used by the finite-difference checks. */
+double oc_loss(const oc_config *c, const oc_scene *sc, const double *s0, const double *act,
+               const double *g_r, const double *g_depth, const double *g_lidar,
+               const double *g_sT)
+{
+    ctx_t x;
+    ctx_init(&x, c, sc);
+    int N = c->n_env, T = c->horizon, D = x.D, NM = x.NM;
+    size_t ns = (size_t)(T + 1) * NM * D;
+    double *states = malloc(sizeof(double) * ns);
+    double *spre = malloc(sizeof(double) * (size_t)T * NM * D);
+    double *r = malloc(sizeof(double) * (size_t)T * NM);
+    int8_t *rg = malloc((size_t)T * NM);
+    uint8_t *dn = malloc((size_t)T * NM), *as = malloc((size_t)T * NM);
+    int32_t *sid = malloc(sizeof(int32_t) * (size_t)T * NM);
+    size_t nc = (size_t)T * NM * x.Rc, nl = (size_t)T * NM * x.Rl;
+    double *dep = malloc(sizeof(double) * (nc ? nc : 1)), *lid = malloc(sizeof(double) * (nl ? nl : 1));
+    int32_t *hc = malloc(sizeof(int32_t) * (nc ? nc : 1)), *hl = malloc(sizeof(int32_t) * (nl ? nl : 1));
+    uint8_t *ac = malloc(nc ? nc : 1), *al = malloc(nl ? nl : 1);
+    int32_t *pk = calloc((size_t)N, sizeof(int32_t));
+    oc_rollout(c, sc, s0, pk, act, states, spre, r, rg, dn, dep, lid, hc, hl, ac, al, as, sid, 1);
+    double L = 0.0;
+    for (size_t k = 0; k < (size_t)T * NM; ++k) L += g_r[k] * r[k];
+    if (g_depth) for (size_t k = 0; k < nc; ++k) L += g_depth[k] * dep[k];
+    if (g_lidar) for (size_t k = 0; k < nl; ++k) L += g_lidar[k] * lid[k];
+    if (g_sT) for (size_t k = 0; k < (size_t)NM * D; ++k) L += g_sT[k] * states[(size_t)T * NM * D + k];
+    free(states); free(spre); free(r); free(rg); free(dn); free(as); free(sid);
+    free(dep); free(lid); free(hc); free(hl); free(ac); free(al); free(pk);
+    ctx_free(&x);
+    return L;
+}
+
+/* Largest thread count OpenMP would use (for reporting). */
+int oc_max_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
