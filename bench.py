@@ -1,0 +1,378 @@
+#!/usr/bin/env python
+"""Benchmark of the fused, batched, differentiable quadrotor step on B300.
+
+One bench step = one pass of the whole hot path over one batch: a rollout of
+T = 64 steps of 16384 environments x 8 point-mass agents (8 obstacle maps of
+10..200 spheres/boxes, a 16x9 depth camera per agent, inter-agent collisions,
+resets) in one persistent launch, then its adjoint (BPTT, Eq. 5) with a
+reward cotangent and a depth cotangent.  `value` is environment steps per
+second (env-steps/s) over all ranks, inputs resident in HBM.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+`--impl reference` times the FP64 CPU oracle (the only other implementation of
+the method) on the host cores, on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "swarm_16384env_8agent_8maps_depth16x9"
+METRIC = "env-steps/s (fwd+adjoint, with depth) at 16k envs vs roofline; Grays/s"
+UNIT = "env-steps/s"
+# launch configuration timed by the bench (and used by the full-size parity test)
+BENCH_EXEC = dict(ckpt_every=16, tape_hits=1, cull=1)
+# algorithmic FP32 operations of one ray-primitive test:
+# sphere: b = d.oc (5), disc = b^2 - C (2), can-beat test (3); box: 6 slab
+# products, 6 per-axis min/max, 4 entry/exit min/max
+FLOP_SPHERE_TEST = 10
+FLOP_BOX_TEST = 16
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    return ap.parse_args()
+
+
+def workload_params(name):
+    from paper_2509_10247_b300 import synth
+    return synth.preset(name)
+
+
+def source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2509_10247_b300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def peak_fp32_tflops(num_sms, sm_mhz):
+    # FP32 FMA issue: 128 lanes per SM, 2 FLOP per FMA
+    return 2.0 * 128 * num_sms * sm_mhz * 1e6 / 1e12
+
+
+def config_of(p, extra=None):
+    c = {"workload": p["name"], "n_env": p["n_env"], "n_agent": p["n_agent"],
+         "horizon": p["horizon"], "model": p["model"],
+         "camera": None if p["cam"] is None else "%dx%d" % (p["cam"][0], p["cam"][1]),
+         "lidar": None if p["lidar"] is None else "%dx%d" % (p["lidar"][0], p["lidar"][1]),
+         "obstacles_per_map": [a + b for a, b in p["map_counts"]],
+         "global_batch": p["n_env"], "seq_len": p["horizon"], "parallelism": "replicas"}
+    if extra:
+        c.update(extra)
+    return c
+
+
+# ------------------------------------------------------------- CPU oracle
+def oracle_sample(p, inp, n_envs, threads=0):
+    """Oracle rollout + adjoint on the first n_envs environments (all maps
+    represented); returns (seconds, env_steps)."""
+    import oracle
+    from paper_2509_10247_b300 import synth
+    envs = np.arange(n_envs)
+    M = p["n_agent"]
+    rows = (envs[:, None] * M + np.arange(M)[None, :]).reshape(-1)
+    q = dict(p, n_env=n_envs)
+    sub = dict(inp)
+    sub["s0"], sub["targets"] = inp["s0"][rows], inp["targets"][rows]
+    sub["pool"], sub["actions"] = inp["pool"][:, rows], inp["actions"][:, rows]
+    sub["env_map"] = inp["env_map"][envs]
+    o = oracle.Oracle(q, sub)
+    cot = synth.cotangents(q, seed=1)
+    t0 = time.perf_counter()
+    rec = o.rollout(sub["s0"], sub["actions"], n_threads=threads)
+    o.backward(rec, cot["g_r"], cot.get("g_depth"), cot.get("g_lidar"), n_threads=threads)
+    return time.perf_counter() - t0, n_envs * p["horizon"]
+
+
+def cpu_rate(p, inp, target_s):
+    """env-steps/s of the oracle on a sample sized to about target_s seconds."""
+    import oracle
+    n = max(1, min(8, p["n_env"]))
+    dt, steps = oracle_sample(p, inp, n)
+    while dt < 0.3 * target_s and n < p["n_env"]:
+        n = min(p["n_env"], max(n + 1, int(n * min(8.0, target_s / max(dt, 1e-3)))))
+        dt, steps = oracle_sample(p, inp, n)
+    return steps / dt, n, dt, oracle.max_threads()
+
+
+# ------------------------------------------------------------- clocks
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------- reference arm
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    p = workload_params(args.workload)
+    from paper_2509_10247_b300 import synth
+    inp = synth.make_inputs(p, seed=args.seed)
+    import oracle
+    oracle.build()
+    # size the per-step sample to about 2 s of CPU work
+    n = max(1, min(8, p["n_env"]))
+    dt, _ = oracle_sample(p, inp, n)
+    n = int(max(1, min(p["n_env"], n * 2.0 / max(dt, 1e-3))))
+    for _ in range(args.warmup):
+        oracle_sample(p, inp, n)
+    times = []
+    for _ in range(args.steps):
+        dt, steps = oracle_sample(p, inp, n)
+        times.append(dt)
+    tot = sum(times)
+    value = n * p["horizon"] * args.steps / tot
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config_of(p),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.max_threads(),
+                             "kind": "oracle",
+                             "sample": "%d of %d envs (all maps), full horizon, rollout + adjoint per step"
+                                       % (n, p["n_env"])},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------- our arm
+def run_ours(args, rank, world):
+    import torch
+    from paper_2509_10247_b300 import build as B, synth
+    from paper_2509_10247_b300.binding import Simulator
+    if rank == 0 or world == 1:
+        B.build()
+    if world > 1:
+        torch.distributed.barrier()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    p = workload_params(args.workload)
+    inp = synth.make_inputs(p, seed=args.seed + rank)
+    sim = Simulator(p, inp, device=dev, **BENCH_EXEC)
+    T, NM, Rc = p["horizon"], sim.NM, sim.Rc
+    s0 = torch.as_tensor(inp["s0"], dtype=torch.float32, device=dev)
+    act = torch.as_tensor(inp["actions"], dtype=torch.float32, device=dev)
+    g = torch.Generator(device=dev)
+    g.manual_seed(1234 + rank)
+    g_r = torch.randn(T, NM, device=dev, generator=g)
+    g_d = torch.randn(T, NM, Rc, device=dev, generator=g) if Rc else None
+    out = dict(r_ctrl=torch.empty(T, NM, device=dev), r_goal=torch.empty(T, NM, dtype=torch.int8, device=dev),
+               done=torch.empty(T, NM, dtype=torch.uint8, device=dev),
+               depth=torch.empty(T, NM, Rc, device=dev) if Rc else None, lidar=None)
+    g_a = torch.empty(T, NM, sim.A, device=dev)
+    g_s0 = torch.empty(NM, sim.D, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(ev=None):
+        sim.reset(s0)
+        if ev:
+            ev[0].record(stream)
+        sim.rollout(act, out=out)
+        if ev:
+            ev[1].record(stream)
+        sim.backward(g_r, g_d, None, None, g_a, g_s0)
+        if ev:
+            ev[2].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    sim.counters(reset=True)
+    # one counted pass for the algorithmic work of a rollout launch
+    step()
+    cnt = sim.counters(reset=True)
+    if sim.status() != 0:
+        raise RuntimeError("device status flagged during warm-up")
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    clocks = Clocks(local) if rank == 0 else None
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for k in range(args.steps):
+        step(evs[k])
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    ck = clocks.stop() if clocks else None
+    ms = t_start.elapsed_time(t_end)
+    if world > 1:
+        tt = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        ms = tt.item()
+    fwd_ms = statistics.mean(e[0].elapsed_time(e[1]) for e in evs)
+    bwd_ms = statistics.mean(e[1].elapsed_time(e[2]) for e in evs)
+    if sim.status() != 0:
+        raise RuntimeError("device status flagged during the timed region")
+    env_steps = p["n_env"] * T * args.steps * world
+    value = env_steps / (ms / 1e3)
+    rays_per_step = NM * (Rc + sim.Rl) * T  # per rollout launch
+    grays = rays_per_step * args.steps * world / (ms / 1e3) / 1e9
+
+    if rank != 0:
+        return 0
+    # roofline of the dominant kernel (the forward rollout: FP32 ray casting)
+    props = torch.cuda.get_device_properties(dev)
+    flop = FLOP_SPHERE_TEST * cnt["sphere_tests"] + FLOP_BOX_TEST * cnt["box_tests"]
+    achieved = flop / (fwd_ms / 1e3) / 1e12
+    peak = peak_fp32_tflops(props.multi_processor_count, 2032.0)
+    traffic = None
+    tfile = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tfile):
+        tj = json.load(open(tfile))
+        if tj.get("source_hash") == source_hash() and tj.get("workload") == p["name"]:
+            traffic = tj.get("rollout_bytes_per_launch")
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": traffic,
+                "kernel": "k_rollout (forward rollout launch)", "kernel_ms": fwd_ms,
+                "adjoint_ms": bwd_ms, "peak_basis": "FP32 FMA issue, %d SMs x 128 lanes x 2 x 2032 MHz (derived)"
+                % props.multi_processor_count,
+                "tests_per_launch": cnt["sphere_tests"] + cnt["box_tests"]}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": config_of(p, {"l2": "inputs larger than L2: %.1f GB depth written and %.1f GB "
+                                          "depth cotangent read per step" % (4e-9 * T * NM * Rc,
+                                                                            4e-9 * T * NM * Rc),
+                                    "exec": BENCH_EXEC}),
+            "grays_per_s": grays, "agent_steps_per_s": value * p["n_agent"],
+            "roofline": roofline, "gpu_launches": 2 * args.steps * 1, "clocks": ck}
+    # end to end: host actions and initial state in, rewards and action gradients out
+    if not args.no_e2e:
+        line["e2e"] = run_e2e(args, sim, inp, dev, g_r, g_d, out, g_a, g_s0, p)
+    if world == 1 and not args.no_cpu:
+        rate, n, dt, cores = cpu_rate(p, inp, args.cpu_seconds)
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": "%d of %d envs (all maps), full horizon, rollout + adjoint, %.1f s"
+                                          % (n, p["n_env"], dt)}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_e2e(args, sim, inp, dev, g_r, g_d, out, g_a, g_s0, p):
+    import torch
+    T, NM = p["horizon"], sim.NM
+    act_h = torch.as_tensor(inp["actions"], dtype=torch.float32).pin_memory()
+    s0_h = torch.as_tensor(inp["s0"], dtype=torch.float32).pin_memory()
+    r_h = torch.empty(T, NM, dtype=torch.float32).pin_memory()
+    ga_h = torch.empty(T, NM, sim.A, dtype=torch.float32).pin_memory()
+    act_d = torch.empty_like(act_h, device=dev)
+    s0_d = torch.empty_like(s0_h, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        act_d.copy_(act_h, non_blocking=True)
+        s0_d.copy_(s0_h, non_blocking=True)
+        sim.reset(s0_d)
+        sim.rollout(act_d, out=out)
+        sim.backward(g_r, g_d, None, None, g_a, g_s0)
+        r_h.copy_(out["r_ctrl"], non_blocking=True)
+        ga_h.copy_(g_a, non_blocking=True)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    h2d = act_h.numel() * 4 + s0_h.numel() * 4
+    d2h = r_h.numel() * 4 + ga_h.numel() * 4
+    return {"value": p["n_env"] * T * args.steps / (ms / 1e3), "unit": UNIT,
+            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+            "what": "pinned host actions + initial state in; rewards + action gradients out; "
+                    "reward/depth cotangents device-resident"}
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "gloo" if args.impl == "reference" else "nccl"
+        if backend == "nccl":
+            torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        dist.init_process_group(backend)
+    try:
+        if args.impl == "reference":
+            return run_reference(args, rank, world)
+        return run_ours(args, rank, world)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    sys.exit(main())

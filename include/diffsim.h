@@ -1,0 +1,221 @@
+/*
+ * diffsim.h -- C ABI of the fused, batched, differentiable quadrotor
+ * environment step (DiffAero, arXiv 2509.10247), sm_103a CUDA.
+ *
+ * One handle simulates N environments of M agents each.  Per step it
+ * integrates the point-mass (Eq. 3) or rigid-body (Eq. 1) dynamics,
+ * ray-casts the depth camera and / or LiDAR against the environment's
+ * spheres and axis-aligned boxes (Sec. III-B), evaluates collisions, the
+ * differentiable reward R_ctrl and the sparse reward R_goal (Sec. III-C,
+ * III-D, III-E), terminates and resets environments, and renders the new
+ * observation.  A rollout of T steps runs in one persistent launch; its
+ * adjoint (backpropagation through time, Eq. 5) is hand-written.
+ *
+ * Conventions
+ *  - Every function returns SIM_OK (0) or a negative SIM_ERR_* code; no C++
+ *    exception crosses this boundary.  sim_strerror() names a code.
+ *  - "device" pointers are CUDA global memory of the handle's device, owned
+ *    by the caller, read or written asynchronously on the given stream; the
+ *    caller keeps them alive until the stream has passed the call.  "host"
+ *    pointers are read synchronously and may be freed on return.
+ *  - Floating point is FP32 everywhere on the device.  Layouts are row-major
+ *    with the last index fastest:
+ *      state    [NM][D]   NM = N*M; D = 12 point mass (p[3], v[3], a[3],
+ *                          ema_v[3]); D = 13 rigid (p[3], q[4] = (w,x,y,z),
+ *                          v[3], omega[3])
+ *      actions  [T][NM][A]  A = 3 point mass, 4 rigid (thrust, 3 body rates),
+ *                          each in [-1, 1] (clipped)
+ *      r_ctrl   [T][NM] float, r_goal [T][NM] int8, done [T][NM] uint8
+ *      depth    [T][NM][Rc], Rc = cam_w * cam_h, ray = row * cam_w + col
+ *      lidar    [T][NM][Rl], Rl = lid_ch * lid_az, ray = ch * lid_az + k
+ *    Output t of a rollout is the observation of the state after step t.
+ *  - A handle is not thread safe; calls on one handle must be ordered.
+ */
+#ifndef DIFFSIM_H
+#define DIFFSIM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* cudaStream_t-compatible opaque stream (NULL = legacy default stream) */
+typedef struct CUstream_st *sim_stream_t;
+typedef struct sim_handle sim_handle;
+
+enum {
+    SIM_OK = 0,
+    SIM_ERR_INVALID_ARG = -1, /* a value out of its documented range */
+    SIM_ERR_NULL_PTR = -2,    /* a required pointer is NULL */
+    SIM_ERR_SIZE = -3,        /* sizes inconsistent or beyond a limit */
+    SIM_ERR_CUDA = -4,        /* a CUDA runtime call failed */
+    SIM_ERR_NOT_READY = -5,   /* e.g. step before set_scene, backward before rollout */
+    SIM_ERR_NAN = -6,         /* a non-finite state was produced (status word) */
+    SIM_ERR_TIMEOUT = -7,     /* a bounded device wait gave up (status word) */
+    SIM_ERR_OOM = -8,         /* device allocation failed */
+    SIM_ERR_UNSUPPORTED = -9  /* no kernel for this configuration */
+};
+
+enum { SIM_MODEL_POINT_MASS = 0, SIM_MODEL_RIGID = 1 };
+
+/* Status bits accumulated on the device (sim_last_status). */
+enum { SIM_STATUS_NAN = 1, SIM_STATUS_TIMEOUT = 2 };
+
+/* Simulation parameters.  Paper symbols: Eq. 3 (lam, drag), Eq. 1 (mass,
+ * inertia J, drag_body D), Sec. III-B (sensors), Sec. III-C/D/E (task). */
+typedef struct sim_config {
+    int32_t model;        /* SIM_MODEL_* */
+    int32_t n_env;        /* N >= 1 */
+    int32_t n_agent;      /* M >= 1 agents per environment (swarm) */
+    int32_t horizon;      /* T >= 1 steps per rollout */
+    float dt;             /* step length (s) */
+    float gravity;        /* |g| (m/s^2), acting along world -z */
+    /* continuous point mass, Eq. 3 */
+    float lam;            /* command latency factor lambda (1/s) */
+    float drag;           /* drag coefficient d (1/s) */
+    float act_scale;      /* acceleration command u = act_scale * clip(a) (m/s^2) */
+    float ema_alpha;      /* velocity EMA weight of the point-mass heading */
+    /* rigid body, Eq. 1, with rate controller tau = J K (w_c - w) + w x J w */
+    float mass;           /* kg */
+    float inertia[3];     /* diagonal of J (kg m^2) */
+    float k_rate[3];      /* diagonal of K (1/s) */
+    float drag_body[3];   /* diagonal of D (1/s) */
+    float rate_scale[3];  /* body-rate command w_c = rate_scale * clip(a1..3) (rad/s) */
+    /* depth camera (cam_w = 0: none): pinhole along +x_B, z-depth output */
+    int32_t cam_w, cam_h;
+    float cam_hfov;       /* horizontal field of view (rad) */
+    float cam_range;      /* z-depth clamp (m) */
+    /* LiDAR (lid_ch = 0: none): range output */
+    int32_t lid_ch, lid_az;
+    float lid_elev_lo, lid_elev_hi; /* channel elevations (rad), inclusive */
+    float lid_range;      /* range clamp (m) */
+    /* task / reward */
+    int32_t pos_sq;       /* 1: -w_pos |e|^2 (position task); 0: -w_pos |e| */
+    float w_pos, w_obs, d_safe, w_act, w_agent, d_agent, success_radius, r_quad;
+    float bound_lo[3], bound_hi[3]; /* leaving this box is a collision (+-inf: none) */
+    int32_t terminate;    /* 1: a collision ends the env's episode and resets it */
+    int32_t pool_size;    /* P reset states per agent (sim_set_pool) */
+    /* execution */
+    int32_t ckpt_every;   /* K: rollout checkpoints every K steps (0: K = T) */
+    int32_t tape_hits;    /* 1: rollout stores ray hit ids, backward gathers them;
+                             0: backward re-casts the rays; -1: auto (tape if <= 8 GiB) */
+    int32_t cull;         /* 1: field-of-view culling (result-preserving); 0: off */
+    int32_t warps_per_cta;   /* 0: auto (8); else warps per CTA, 1..8 */
+    int32_t rays_per_thread; /* 0: auto; else one of 1, 2, 3, 4, 5, 6, 8 */
+    int32_t ctas_per_sm;     /* 0: occupancy limit; else cap of resident CTAs per SM */
+    int32_t reserved[6];     /* must be 0 */
+} sim_config;
+
+/* Library version string. */
+const char *sim_version(void);
+
+/* Human-readable name of an error code (static storage). */
+const char *sim_strerror(int code);
+
+/* State dimension D and action dimension A of a model; -1 for an unknown model. */
+int sim_state_dim(int model);
+int sim_action_dim(int model);
+
+/* Create a handle on the current CUDA device.  Validates cfg (every count
+ * positive, horizon >= 1, camera and LiDAR sizes, tape/cull flags, launch
+ * knobs) and allocates the state, checkpoints, tapes and ray tables.
+ * *out is NULL on failure.  The handle owns its device memory. */
+int sim_create(const sim_config *cfg, sim_handle **out);
+
+/* Free a handle and its device memory (synchronises the device first).
+ * NULL is a no-op. */
+int sim_destroy(sim_handle *h);
+
+/* Bytes of device memory the handle holds (state, checkpoints, tapes, scene). */
+int sim_workspace_bytes(const sim_handle *h, size_t *bytes);
+
+/* Obstacle scene (Sec. III-B, III-C), all HOST pointers, copied in
+ * synchronously:
+ *   spheres [Ks][4] = (cx, cy, cz, r), boxes [Kb][6] = (min xyz, max xyz);
+ *   sph_off, box_off [n_maps + 1]: map m owns spheres sph_off[m] ..
+ *   sph_off[m+1]-1 and boxes box_off[m] .. box_off[m+1]-1 (at most 32767
+ *   primitives per map; within a map spheres take ids 0..ns-1, boxes ns..);
+ *   env_map [N]: map of each environment; targets [NM][3]: goal positions.
+ * Errors: NULL_PTR, SIZE (offsets not non-decreasing, an env_map entry out
+ * of range, a map too large for shared memory), INVALID_ARG (radius or box
+ * extent negative, non-finite values). */
+int sim_set_scene(sim_handle *h, const float *spheres, const int32_t *sph_off,
+                  const float *boxes, const int32_t *box_off, int32_t n_maps,
+                  const int32_t *env_map, const float *targets);
+
+/* Reset pool [P][NM][D], HOST pointer, P = cfg.pool_size: on termination
+ * environment e takes entry (k_e mod P) for all its agents, k_e counting
+ * its resets.  Required when terminate = 1. */
+int sim_set_pool(sim_handle *h, const float *pool);
+
+/* Per-environment drag d and latency lambda (Sec. IV-D domain
+ * randomisation), HOST pointers [N] each, either may be NULL (= cfg value). */
+int sim_set_env_params(sim_handle *h, const float *drag, const float *lam);
+
+/* Set the current state from a DEVICE buffer [NM][D] and zero the reset
+ * counters.  state0 = NULL takes pool entry 0. */
+int sim_reset(sim_handle *h, const float *state0, sim_stream_t stream);
+
+/* Copy the current state to / from a DEVICE buffer [NM][D]. */
+int sim_get_state(const sim_handle *h, float *dst, sim_stream_t stream);
+int sim_set_state(sim_handle *h, const float *src, sim_stream_t stream);
+
+/* Sensor outputs of the current state (the initial observation): depth
+ * [NM][Rc] and lidar [NM][Rl], DEVICE, either NULL to skip. */
+int sim_render(sim_handle *h, float *depth, float *lidar, sim_stream_t stream);
+
+/* One step of the current state with actions [NM][A] (DEVICE).  Outputs
+ * (DEVICE, any may be NULL): depth [NM][Rc], lidar [NM][Rl], r_ctrl [NM],
+ * r_goal [NM], done [NM].  Advances the current state. */
+int sim_step(sim_handle *h, const float *actions, float *depth, float *lidar,
+             float *r_ctrl, int8_t *r_goal, uint8_t *done, sim_stream_t stream);
+
+/* T = cfg.horizon steps from the current state in one persistent launch.
+ * actions [T][NM][A]; outputs r_ctrl [T][NM], r_goal [T][NM], done [T][NM],
+ * depth [T][NM][Rc], lidar [T][NM][Rl] (DEVICE, any may be NULL).  Records
+ * checkpoints (and hit tapes) for sim_backward and advances the state. */
+int sim_rollout(sim_handle *h, const float *actions, float *r_ctrl, int8_t *r_goal,
+                uint8_t *done, float *depth, float *lidar, sim_stream_t stream);
+
+/* Adjoint of the last sim_rollout (Eq. 5): given cotangents g_r [T][NM] of
+ * r_ctrl, g_depth [T][NM][Rc], g_lidar [T][NM][Rl] and g_sT [NM][D] of the
+ * final state (DEVICE; g_depth, g_lidar, g_sT may be NULL = zero), writes
+ * g_a [T][NM][A] and g_s0 [NM][D] (g_s0 may be NULL).  No cotangent crosses
+ * a reset; kinks take the active branch's derivative.  The actions buffer
+ * given to sim_rollout must still hold the same values.
+ * Errors: NOT_READY without a preceding rollout. */
+int sim_backward(sim_handle *h, const float *g_r, const float *g_depth, const float *g_lidar,
+                 const float *g_sT, float *g_a, float *g_s0, sim_stream_t stream);
+
+/* Vector-Jacobian product of one step (closed-loop use): state s_t [NM][D],
+ * actions a_t [NM][A], done_t [NM] (the step's done output), cotangents
+ * g_s_next [NM][D] (may be NULL), g_r [NM], g_depth [NM][Rc], g_lidar
+ * [NM][Rl] (may be NULL); outputs g_a [NM][A], g_s [NM][D] (may be NULL).
+ * All DEVICE.  Re-casts the rays of the step; does not touch the current state. */
+int sim_step_backward(sim_handle *h, const float *s_t, const float *a_t, const uint8_t *done_t,
+                      const float *g_s_next, const float *g_r, const float *g_depth,
+                      const float *g_lidar, float *g_a, float *g_s, sim_stream_t stream);
+
+/* Device status word accumulated by the kernels since the last call
+ * (SIM_STATUS_* bits; synchronises the handle's last stream and clears it).
+ * per_env is reserved and must be NULL. */
+int sim_last_status(sim_handle *h, int32_t *status, int32_t *per_env);
+
+/* Work counters accumulated by the forward kernels since the last reset:
+ * out[0] ray-sphere tests, out[1] ray-box tests (both after field-of-view
+ * culling), out[2] rays cast, out[3] environment steps.  Synchronises the
+ * last stream.  reset != 0 zeroes the counters after reading. */
+int sim_counters(sim_handle *h, uint64_t *out, int32_t reset);
+
+/* Launch shape chosen for this handle: warps per CTA, rays per thread,
+ * grid size of the rollout kernel and its dynamic shared memory (bytes). */
+int sim_launch_info(const sim_handle *h, int32_t *warps_per_cta, int32_t *rays_per_thread,
+                    int32_t *grid, int32_t *smem_bytes);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DIFFSIM_H */

@@ -1,0 +1,354 @@
+"""ctypes binding of libdiffsim.so (include/diffsim.h).
+
+Argument marshalling only: every step of the simulation runs in the CUDA
+library.  torch supplies device memory (tensors) and streams.  The module-level
+functions carry the C names; ``Simulator`` is a thin owner of one handle.
+If the library is missing, loading raises: there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+
+import numpy as np
+import torch
+
+from . import synth
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libdiffsim.so")
+
+_i, _f = C.c_int32, C.c_float
+_vp = C.c_void_p
+
+SIM_OK = 0
+SIM_MODEL_POINT_MASS, SIM_MODEL_RIGID = 0, 1
+ERRORS = {0: "SIM_OK", -1: "SIM_ERR_INVALID_ARG", -2: "SIM_ERR_NULL_PTR", -3: "SIM_ERR_SIZE",
+          -4: "SIM_ERR_CUDA", -5: "SIM_ERR_NOT_READY", -6: "SIM_ERR_NAN", -7: "SIM_ERR_TIMEOUT",
+          -8: "SIM_ERR_OOM", -9: "SIM_ERR_UNSUPPORTED"}
+
+# every symbol include/diffsim.h declares
+SYMBOLS = ["sim_version", "sim_strerror", "sim_state_dim", "sim_action_dim", "sim_create",
+           "sim_destroy", "sim_workspace_bytes", "sim_set_scene", "sim_set_pool",
+           "sim_set_env_params", "sim_reset", "sim_get_state", "sim_set_state", "sim_render",
+           "sim_step", "sim_rollout", "sim_backward", "sim_step_backward", "sim_last_status",
+           "sim_launch_info", "sim_counters"]
+
+
+class SimError(RuntimeError):
+    def __init__(self, code, what):
+        self.code = code
+        super().__init__("%s failed: %s (%d)" % (what, ERRORS.get(code, "?"), code))
+
+
+class SimConfig(C.Structure):
+    _fields_ = [
+        ("model", _i), ("n_env", _i), ("n_agent", _i), ("horizon", _i),
+        ("dt", _f), ("gravity", _f),
+        ("lam", _f), ("drag", _f), ("act_scale", _f), ("ema_alpha", _f),
+        ("mass", _f), ("inertia", _f * 3), ("k_rate", _f * 3), ("drag_body", _f * 3),
+        ("rate_scale", _f * 3),
+        ("cam_w", _i), ("cam_h", _i), ("cam_hfov", _f), ("cam_range", _f),
+        ("lid_ch", _i), ("lid_az", _i), ("lid_elev_lo", _f), ("lid_elev_hi", _f), ("lid_range", _f),
+        ("pos_sq", _i), ("w_pos", _f), ("w_obs", _f), ("d_safe", _f), ("w_act", _f),
+        ("w_agent", _f), ("d_agent", _f), ("success_radius", _f), ("r_quad", _f),
+        ("bound_lo", _f * 3), ("bound_hi", _f * 3),
+        ("terminate", _i), ("pool_size", _i),
+        ("ckpt_every", _i), ("tape_hits", _i), ("cull", _i), ("warps_per_cta", _i),
+        ("rays_per_thread", _i), ("ctas_per_sm", _i), ("reserved", _i * 6),
+    ]
+
+
+_lib = None
+
+
+def lib():
+    """Load libdiffsim.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libdiffsim.so not found at %s: build it with "
+                               "`python -m paper_2509_10247_b300.build`" % LIB_PATH)
+        L = C.CDLL(LIB_PATH)
+        L.sim_version.restype = C.c_char_p
+        L.sim_strerror.restype = C.c_char_p
+        L.sim_strerror.argtypes = [C.c_int]
+        for name in SYMBOLS[2:]:
+            getattr(L, name).restype = C.c_int
+        L.sim_create.argtypes = [C.POINTER(SimConfig), C.POINTER(_vp)]
+        _lib = L
+    return _lib
+
+
+def _ck(rc, what):
+    if rc != SIM_OK:
+        raise SimError(rc, what)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    assert t.is_cuda and t.is_contiguous(), "device tensors must be contiguous CUDA tensors"
+    return _vp(t.data_ptr())
+
+
+def _host(a, dt):
+    return np.ascontiguousarray(a, dtype=dt)
+
+
+def _np_ptr(a):
+    return None if a is None else _vp(a.ctypes.data)
+
+
+def _stream(stream=None):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return _vp(s.cuda_stream)
+
+
+def make_config(p, **ex):
+    """sim_config from a workload parameter dict; `ex` sets the execution
+    fields (ckpt_every, tape_hits, cull, warps_per_cta, rays_per_thread,
+    ctas_per_sm)."""
+    c = SimConfig()
+    c.model = SIM_MODEL_RIGID if p["model"] == "rigid" else SIM_MODEL_POINT_MASS
+    c.n_env, c.n_agent, c.horizon = p["n_env"], p["n_agent"], p["horizon"]
+    c.dt, c.gravity = p["dt"], p["gravity"]
+    c.lam, c.drag, c.act_scale, c.ema_alpha = p["lam"], p["drag"], p["act_scale"], p["ema_alpha"]
+    c.mass = p["mass"]
+    for k in range(3):
+        c.inertia[k], c.k_rate[k] = p["inertia"][k], p["k_rate"][k]
+        c.drag_body[k], c.rate_scale[k] = p["drag_body"][k], p["rate_scale"][k]
+        c.bound_lo[k], c.bound_hi[k] = p["bound_lo"][k], p["bound_hi"][k]
+    if p["cam"] is not None:
+        c.cam_w, c.cam_h = p["cam"][0], p["cam"][1]
+        c.cam_hfov, c.cam_range = math.radians(p["cam"][2]), p["cam"][3]
+    if p["lidar"] is not None:
+        c.lid_ch, c.lid_az = p["lidar"][0], p["lidar"][1]
+        c.lid_elev_lo, c.lid_elev_hi = math.radians(p["lidar"][2]), math.radians(p["lidar"][3])
+        c.lid_range = p["lidar"][4]
+    c.pos_sq = int(p["pos_sq"])
+    c.w_pos, c.w_obs, c.d_safe, c.w_act = p["w_pos"], p["w_obs"], p["d_safe"], p["w_act"]
+    c.w_agent, c.d_agent = p["w_agent"], p["d_agent"]
+    c.success_radius, c.r_quad = p["success_radius"], p["r_quad"]
+    c.terminate, c.pool_size = int(p["terminate"]), p["pool_size"]
+    c.ckpt_every = ex.get("ckpt_every", p.get("ckpt_every", 16))
+    c.tape_hits = ex.get("tape_hits", -1)
+    c.cull = ex.get("cull", 1)
+    c.warps_per_cta = ex.get("warps_per_cta", 0)
+    c.rays_per_thread = ex.get("rays_per_thread", 0)
+    c.ctas_per_sm = ex.get("ctas_per_sm", 0)
+    return c
+
+
+# ------------------------------------------------------------ C-named calls
+def sim_version():
+    return lib().sim_version().decode()
+
+
+def sim_strerror(code):
+    return lib().sim_strerror(code).decode()
+
+
+def sim_state_dim(model):
+    return lib().sim_state_dim(model)
+
+
+def sim_action_dim(model):
+    return lib().sim_action_dim(model)
+
+
+def sim_create(cfg):
+    h = _vp()
+    _ck(lib().sim_create(C.byref(cfg), C.byref(h)), "sim_create")
+    return h
+
+
+def sim_destroy(h):
+    _ck(lib().sim_destroy(h), "sim_destroy")
+
+
+def sim_workspace_bytes(h):
+    n = C.c_size_t()
+    _ck(lib().sim_workspace_bytes(h, C.byref(n)), "sim_workspace_bytes")
+    return n.value
+
+
+def sim_set_scene(h, spheres, sph_off, boxes, box_off, env_map, targets):
+    sp = _host(spheres, np.float32).reshape(-1, 4)
+    bx = _host(boxes, np.float32).reshape(-1, 6)
+    so, bo = _host(sph_off, np.int32), _host(box_off, np.int32)
+    em, tg = _host(env_map, np.int32), _host(targets, np.float32)
+    _ck(lib().sim_set_scene(h, _np_ptr(sp), _np_ptr(so), _np_ptr(bx), _np_ptr(bo),
+                            _i(len(so) - 1), _np_ptr(em), _np_ptr(tg)), "sim_set_scene")
+
+
+def sim_set_pool(h, pool):
+    pl = _host(pool, np.float32)
+    _ck(lib().sim_set_pool(h, _np_ptr(pl)), "sim_set_pool")
+
+
+def sim_set_env_params(h, drag=None, lam=None):
+    d = None if drag is None else _host(drag, np.float32)
+    l = None if lam is None else _host(lam, np.float32)
+    _ck(lib().sim_set_env_params(h, _np_ptr(d), _np_ptr(l)), "sim_set_env_params")
+
+
+def sim_reset(h, state0=None, stream=None):
+    _ck(lib().sim_reset(h, _ptr(state0), _stream(stream)), "sim_reset")
+
+
+def sim_get_state(h, dst, stream=None):
+    _ck(lib().sim_get_state(h, _ptr(dst), _stream(stream)), "sim_get_state")
+
+
+def sim_set_state(h, src, stream=None):
+    _ck(lib().sim_set_state(h, _ptr(src), _stream(stream)), "sim_set_state")
+
+
+def sim_render(h, depth=None, lidar=None, stream=None):
+    _ck(lib().sim_render(h, _ptr(depth), _ptr(lidar), _stream(stream)), "sim_render")
+
+
+def sim_step(h, actions, depth=None, lidar=None, r_ctrl=None, r_goal=None, done=None, stream=None):
+    _ck(lib().sim_step(h, _ptr(actions), _ptr(depth), _ptr(lidar), _ptr(r_ctrl), _ptr(r_goal),
+                       _ptr(done), _stream(stream)), "sim_step")
+
+
+def sim_rollout(h, actions, r_ctrl=None, r_goal=None, done=None, depth=None, lidar=None, stream=None):
+    _ck(lib().sim_rollout(h, _ptr(actions), _ptr(r_ctrl), _ptr(r_goal), _ptr(done), _ptr(depth),
+                          _ptr(lidar), _stream(stream)), "sim_rollout")
+
+
+def sim_backward(h, g_r, g_depth, g_lidar, g_sT, g_a, g_s0=None, stream=None):
+    _ck(lib().sim_backward(h, _ptr(g_r), _ptr(g_depth), _ptr(g_lidar), _ptr(g_sT), _ptr(g_a),
+                           _ptr(g_s0), _stream(stream)), "sim_backward")
+
+
+def sim_step_backward(h, s_t, a_t, done_t, g_s_next, g_r, g_depth, g_lidar, g_a, g_s=None, stream=None):
+    _ck(lib().sim_step_backward(h, _ptr(s_t), _ptr(a_t), _ptr(done_t), _ptr(g_s_next), _ptr(g_r),
+                                _ptr(g_depth), _ptr(g_lidar), _ptr(g_a), _ptr(g_s),
+                                _stream(stream)), "sim_step_backward")
+
+
+def sim_last_status(h):
+    st = C.c_int32()
+    rc = lib().sim_last_status(h, C.byref(st), None)
+    if rc not in (SIM_OK, -6, -7):
+        _ck(rc, "sim_last_status")
+    return st.value
+
+
+def sim_counters(h, reset=True):
+    v = (C.c_uint64 * 4)()
+    _ck(lib().sim_counters(h, v, _i(1 if reset else 0)), "sim_counters")
+    return dict(sphere_tests=v[0], box_tests=v[1], rays=v[2], env_steps=v[3])
+
+
+def sim_launch_info(h):
+    w, r, g, s = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32()
+    _ck(lib().sim_launch_info(h, C.byref(w), C.byref(r), C.byref(g), C.byref(s)), "sim_launch_info")
+    return dict(warps_per_cta=w.value, rays_per_thread=r.value, grid=g.value, smem_bytes=s.value)
+
+
+# ------------------------------------------------------------ owner class
+class Simulator:
+    """One handle bound to a workload: parameters `p` (synth.preset/params) and
+    inputs `inp` (synth.make_inputs).  Device tensors are float32 on `device`."""
+
+    def __init__(self, p, inp, device="cuda", **ex):
+        self.p = p
+        self.device = torch.device(device)
+        self.N, self.M, self.T = p["n_env"], p["n_agent"], p["horizon"]
+        self.NM = self.N * self.M
+        self.D, self.A = synth.STATE_DIM[p["model"]], synth.ACTION_DIM[p["model"]]
+        self.Rc = p["cam"][0] * p["cam"][1] if p["cam"] is not None else 0
+        self.Rl = p["lidar"][0] * p["lidar"][1] if p["lidar"] is not None else 0
+        self.cfg = make_config(p, **ex)
+        with torch.cuda.device(self.device):
+            self.h = sim_create(self.cfg)
+            sim_set_scene(self.h, inp["spheres"], inp["sph_off"], inp["boxes"], inp["box_off"],
+                          inp["env_map"], inp["targets"])
+            if p["pool_size"] > 0:
+                sim_set_pool(self.h, inp["pool"])
+            if inp.get("drag_env") is not None or inp.get("lam_env") is not None:
+                sim_set_env_params(self.h, inp.get("drag_env"), inp.get("lam_env"))
+
+    def close(self):
+        if getattr(self, "h", None):
+            sim_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _empty(self, *shape, dtype=torch.float32):
+        return torch.empty(*shape, dtype=dtype, device=self.device)
+
+    def reset(self, s0=None):
+        sim_reset(self.h, None if s0 is None else s0.contiguous())
+
+    def get_state(self):
+        out = self._empty(self.NM, self.D)
+        sim_get_state(self.h, out)
+        return out
+
+    def set_state(self, s):
+        sim_set_state(self.h, s.contiguous())
+
+    def render(self):
+        depth = self._empty(self.NM, self.Rc) if self.Rc else None
+        lidar = self._empty(self.NM, self.Rl) if self.Rl else None
+        sim_render(self.h, depth, lidar)
+        return depth, lidar
+
+    def step(self, actions):
+        o = dict(r_ctrl=self._empty(self.NM), r_goal=self._empty(self.NM, dtype=torch.int8),
+                 done=self._empty(self.NM, dtype=torch.uint8),
+                 depth=self._empty(self.NM, self.Rc) if self.Rc else None,
+                 lidar=self._empty(self.NM, self.Rl) if self.Rl else None)
+        sim_step(self.h, actions.contiguous(), o["depth"], o["lidar"], o["r_ctrl"], o["r_goal"], o["done"])
+        return o
+
+    def rollout(self, actions, depth=True, lidar=True, out=None):
+        T, NM = self.T, self.NM
+        o = out if out is not None else dict(
+            r_ctrl=self._empty(T, NM), r_goal=self._empty(T, NM, dtype=torch.int8),
+            done=self._empty(T, NM, dtype=torch.uint8),
+            depth=self._empty(T, NM, self.Rc) if (self.Rc and depth) else None,
+            lidar=self._empty(T, NM, self.Rl) if (self.Rl and lidar) else None)
+        self._actions = actions.contiguous()
+        sim_rollout(self.h, self._actions, o["r_ctrl"], o["r_goal"], o["done"], o["depth"], o["lidar"])
+        return o
+
+    def backward(self, g_r, g_depth=None, g_lidar=None, g_sT=None, g_a=None, g_s0=None):
+        T, NM = self.T, self.NM
+        g_a = self._empty(T, NM, self.A) if g_a is None else g_a
+        g_s0 = self._empty(NM, self.D) if g_s0 is None else g_s0
+        sim_backward(self.h, g_r.contiguous(), None if g_depth is None else g_depth.contiguous(),
+                     None if g_lidar is None else g_lidar.contiguous(),
+                     None if g_sT is None else g_sT.contiguous(), g_a, g_s0)
+        return g_a, g_s0
+
+    def step_backward(self, s_t, a_t, done_t, g_s_next, g_r, g_depth=None, g_lidar=None):
+        g_a = self._empty(self.NM, self.A)
+        g_s = self._empty(self.NM, self.D)
+        c = lambda x: None if x is None else x.contiguous()
+        sim_step_backward(self.h, c(s_t), c(a_t), c(done_t), c(g_s_next), c(g_r), c(g_depth),
+                          c(g_lidar), g_a, g_s)
+        return g_a, g_s
+
+    def status(self):
+        return sim_last_status(self.h)
+
+    def launch_info(self):
+        return sim_launch_info(self.h)
+
+    def counters(self, reset=True):
+        return sim_counters(self.h, reset)
+
+    def workspace_bytes(self):
+        return sim_workspace_bytes(self.h)

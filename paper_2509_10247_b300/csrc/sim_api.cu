@@ -1,0 +1,652 @@
+// sim_api.cu -- C ABI (include/diffsim.h): handle, validation, scene layout,
+// launch-shape selection and the entry points of the fused step.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <numeric>
+#include <vector>
+
+#include "diffsim.h"
+#include "sim_kernels.cuh"
+
+namespace ds {
+bool rpt_supported(int rpt);
+cudaError_t launch_sim(bool adjoint, int rpt, const Args& a, int grid, int block, size_t smem, cudaStream_t st);
+cudaError_t occupancy_sim(bool adjoint, int rpt, int block, size_t smem, int* n);
+}  // namespace ds
+
+using ds::Args;
+
+struct sim_handle {
+    sim_config cfg;
+    int D = 0, A = 0, N = 0, M = 0, NM = 0, T = 0, K = 0, S = 0, Rc = 0, Rl = 0;
+    int device = 0, num_sms = 0;
+    bool tape = false;
+    // scene
+    bool have_scene = false, have_pool = false;
+    float4* d_prims = nullptr;
+    int *d_map_off = nullptr, *d_map_ns = nullptr, *d_map_nb = nullptr;
+    int *d_env_map = nullptr, *d_order = nullptr;
+    float* d_targets = nullptr;
+    float* d_pool = nullptr;
+    float *d_drag = nullptr, *d_lam = nullptr;
+    int ns_max = 0, nb_max = 0, n_maps = 0;
+    // sensors
+    float4 *d_cam = nullptr, *d_lid = nullptr;
+    ds::Sensor sen[ds::MAX_SENSORS];
+    // state and records
+    float* d_state = nullptr;
+    int* d_pool_k = nullptr;
+    float* d_ckpt = nullptr;
+    int* d_ckpt_k = nullptr;
+    uint8_t* d_done_tape = nullptr;
+    int16_t* d_sdf_tape = nullptr;
+    int16_t *d_tape_cam = nullptr, *d_tape_lid = nullptr;
+    int *d_work = nullptr, *d_status = nullptr;
+    unsigned long long* d_counters = nullptr;
+    size_t bytes = 0;
+    bool have_rollout = false;
+    const float* rollout_actions = nullptr;
+    cudaStream_t last_stream = nullptr;
+    // launch shape
+    int nw = 8, rpt = 4, grid_f = 1, grid_b = 1;
+    size_t smem_f = 0, smem_b = 0, smem_sb = 0;
+    ds::Smem sm_f{}, sm_b{}, sm_sb{};
+};
+
+namespace {
+
+const char* kErr[] = {"ok", "invalid argument", "null pointer", "size error", "CUDA error",
+                      "not ready", "non-finite state", "device wait timed out", "out of device memory",
+                      "unsupported configuration"};
+
+int cuda_err(cudaError_t e) {
+    if (e == cudaSuccess) return SIM_OK;
+    if (e == cudaErrorMemoryAllocation) return SIM_ERR_OOM;
+    return SIM_ERR_CUDA;
+}
+
+#define CK(x)                               \
+    do {                                    \
+        cudaError_t e_ = (x);               \
+        if (e_ != cudaSuccess) {            \
+            cudaGetLastError();             \
+            return cuda_err(e_);            \
+        }                                   \
+    } while (0)
+
+template <class T>
+int dalloc(sim_handle* h, T** p, size_t n) {
+    *p = nullptr;
+    if (n == 0) return SIM_OK;
+    CK(cudaMalloc((void**)p, n * sizeof(T)));
+    h->bytes += n * sizeof(T);
+    return SIM_OK;
+}
+
+template <class T>
+void dfree(T*& p) {
+    if (p) cudaFree(p);
+    p = nullptr;
+}
+
+bool finite_pos(float x) { return std::isfinite(x) && x > 0.f; }
+
+int validate(const sim_config* c) {
+    if (c->model != SIM_MODEL_POINT_MASS && c->model != SIM_MODEL_RIGID) return SIM_ERR_INVALID_ARG;
+    if (c->n_env < 1 || c->n_agent < 1 || c->horizon < 1) return SIM_ERR_SIZE;
+    if (c->n_agent > 32) return SIM_ERR_SIZE;
+    if ((long long)c->n_env * c->n_agent > (1LL << 30)) return SIM_ERR_SIZE;
+    if (!finite_pos(c->dt) || !std::isfinite(c->gravity)) return SIM_ERR_INVALID_ARG;
+    if (c->model == SIM_MODEL_POINT_MASS) {
+        if (!std::isfinite(c->lam) || !std::isfinite(c->drag) || !std::isfinite(c->act_scale)) return SIM_ERR_INVALID_ARG;
+        if (!(c->ema_alpha >= 0.f && c->ema_alpha <= 1.f)) return SIM_ERR_INVALID_ARG;
+    } else {
+        if (!finite_pos(c->mass)) return SIM_ERR_INVALID_ARG;
+        for (int i = 0; i < 3; ++i)
+            if (!finite_pos(c->inertia[i]) || !std::isfinite(c->k_rate[i]) || !std::isfinite(c->drag_body[i]) ||
+                !std::isfinite(c->rate_scale[i]))
+                return SIM_ERR_INVALID_ARG;
+    }
+    if (c->cam_w < 0 || c->cam_h < 0 || c->lid_ch < 0 || c->lid_az < 0) return SIM_ERR_SIZE;
+    if (c->cam_w > 0) {
+        if (c->cam_h < 1 || (long long)c->cam_w * c->cam_h > (1 << 20)) return SIM_ERR_SIZE;
+        if (!(c->cam_hfov > 0.f && c->cam_hfov < 3.1f) || !finite_pos(c->cam_range)) return SIM_ERR_INVALID_ARG;
+    }
+    if (c->lid_ch > 0) {
+        if (c->lid_az < 1 || (long long)c->lid_ch * c->lid_az > (1 << 20)) return SIM_ERR_SIZE;
+        if (!finite_pos(c->lid_range) || !(c->lid_elev_lo <= c->lid_elev_hi) || c->lid_elev_lo < -1.5707964f ||
+            c->lid_elev_hi > 1.5707964f)
+            return SIM_ERR_INVALID_ARG;
+    }
+    if (c->pool_size < 0 || c->ckpt_every < 0) return SIM_ERR_SIZE;
+    if (c->terminate != 0 && c->terminate != 1) return SIM_ERR_INVALID_ARG;
+    if (c->tape_hits < -1 || c->tape_hits > 1 || (c->cull != 0 && c->cull != 1)) return SIM_ERR_INVALID_ARG;
+    if (c->warps_per_cta < 0 || c->warps_per_cta > 8) return SIM_ERR_INVALID_ARG;
+    if (c->rays_per_thread != 0 && !ds::rpt_supported(c->rays_per_thread)) return SIM_ERR_INVALID_ARG;
+    if (c->ctas_per_sm < 0) return SIM_ERR_INVALID_ARG;
+    for (int i = 0; i < 6; ++i)
+        if (c->reserved[i] != 0) return SIM_ERR_INVALID_ARG;
+    return SIM_OK;
+}
+
+size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
+
+ds::Smem layout(const sim_handle* h, bool adjoint, bool lists) {
+    ds::Smem s{};
+    size_t o = 0;
+    const int L = h->M * h->S;
+    auto take = [&](int& field, size_t bytes) {
+        field = (int)o;
+        o = align16(o + bytes);
+    };
+    take(s.prim, (size_t)(h->ns_max + 2 * h->nb_max) * 16);
+    const int Ls = lists ? L : 0;
+    take(s.lsph, (size_t)Ls * h->ns_max * 16);
+    take(s.lbox, (size_t)Ls * h->nb_max * 32);
+    take(s.lr2, (size_t)Ls * h->ns_max * 4);
+    take(s.lid, (size_t)Ls * (h->ns_max + h->nb_max) * 2);
+    take(s.lmeta, (size_t)Ls * 16);
+    take(s.st, (size_t)h->M * 16 * 4);
+    take(s.spre, (size_t)h->M * 16 * 4);
+    take(s.pose, (size_t)h->M * 12 * 4);
+    take(s.aux, (size_t)h->M * 8 * 4);
+    long items = 0;
+    for (int k = 0; k < h->S; ++k) items += (long)h->M * ((h->sen[k].R + 32 * h->rpt - 1) / (32 * h->rpt));
+    take(s.gpose, adjoint ? (size_t)items * 12 * 4 : 0);
+    take(s.gs, adjoint ? (size_t)h->M * 16 * 4 : 0);
+    take(s.seg, adjoint ? (size_t)(h->K + 1) * h->M * 16 * 4 : 0);
+    take(s.mbar, 16);
+    s.total = (int)o;
+    return s;
+}
+
+// Rays per thread: best product of lane utilisation and warp balance.
+int pick_rpt(const sim_handle* h) {
+    if (h->cfg.rays_per_thread) return h->cfg.rays_per_thread;
+    if (h->S == 0) return 1;
+    const int cands[] = {8, 6, 5, 4, 3, 2, 1};
+    double best = -1.0;
+    int pick = 4;
+    for (int r : cands) {
+        long items = 0, rays = 0;
+        for (int s = 0; s < h->S; ++s) {
+            items += (long)h->M * ((h->sen[s].R + 32 * r - 1) / (32 * r));
+            rays += (long)h->M * h->sen[s].R;
+        }
+        double util = (double)rays / ((double)items * 32 * r);
+        long rounds = (items + h->nw - 1) / h->nw;
+        double bal = (double)items / (double)(rounds * h->nw);
+        double score = util * bal;
+        if (score > best + 1e-9) { best = score; pick = r; }
+    }
+    return pick;
+}
+
+int configure_launch(sim_handle* h) {
+    h->nw = h->cfg.warps_per_cta ? h->cfg.warps_per_cta : 8;
+    h->rpt = pick_rpt(h);
+    h->sm_f = layout(h, false, h->S > 0);
+    h->sm_b = layout(h, true, h->S > 0 && !h->tape);
+    h->smem_f = h->sm_f.total;
+    h->smem_b = h->sm_b.total;
+    {
+        // the single-step adjoint re-casts rays and keeps a one-step segment
+        const int K = h->K;
+        h->K = 1;
+        h->sm_sb = layout(h, true, h->S > 0);
+        h->K = K;
+        h->smem_sb = h->sm_sb.total;
+    }
+    int maxsm = 0;
+    CK(cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
+    if ((int)h->smem_f > maxsm || (int)h->smem_b > maxsm || (int)h->smem_sb > maxsm) return SIM_ERR_SIZE;
+    const int block = 32 * h->nw;
+    int occ_f = 0, occ_b = 0;
+    CK(ds::occupancy_sim(false, h->rpt, block, h->smem_f, &occ_f));
+    CK(ds::occupancy_sim(true, h->rpt, block, h->smem_b, &occ_b));
+    if (occ_f < 1 || occ_b < 1) return SIM_ERR_UNSUPPORTED;
+    if (h->cfg.ctas_per_sm) {
+        occ_f = std::min(occ_f, h->cfg.ctas_per_sm);
+        occ_b = std::min(occ_b, h->cfg.ctas_per_sm);
+    }
+    h->grid_f = (int)std::min<long>((long)occ_f * h->num_sms, h->N);
+    h->grid_b = (int)std::min<long>((long)occ_b * h->num_sms, h->N);
+    return SIM_OK;
+}
+
+Args base_args(const sim_handle* h) {
+    Args a;
+    memset(&a, 0, sizeof(a));
+    const sim_config& c = h->cfg;
+    a.c.model = c.model; a.c.M = h->M; a.c.D = h->D; a.c.A = h->A;
+    a.c.dt = c.dt; a.c.g = c.gravity; a.c.lam = c.lam; a.c.drag = c.drag;
+    a.c.act_scale = c.act_scale; a.c.ema_alpha = c.ema_alpha; a.c.mass = c.mass;
+    for (int i = 0; i < 3; ++i) {
+        a.c.J[i] = c.inertia[i]; a.c.K[i] = c.k_rate[i]; a.c.Dd[i] = c.drag_body[i];
+        a.c.rs[i] = c.rate_scale[i]; a.c.blo[i] = c.bound_lo[i]; a.c.bhi[i] = c.bound_hi[i];
+    }
+    a.c.pos_sq = c.pos_sq; a.c.w_pos = c.w_pos; a.c.w_obs = c.w_obs; a.c.d_safe = c.d_safe;
+    a.c.w_act = c.w_act; a.c.w_agent = c.w_agent; a.c.d_agent = c.d_agent;
+    a.c.success_radius = c.success_radius; a.c.r_quad = c.r_quad;
+    a.c.terminate = c.terminate; a.c.P = h->have_pool ? c.pool_size : 0;
+    a.N = h->N; a.M = h->M; a.NM = h->NM; a.T = h->T; a.K = h->K; a.S = h->S;
+    a.ns_max = h->ns_max; a.nb_max = h->nb_max; a.cull = c.cull;
+    for (int s = 0; s < ds::MAX_SENSORS; ++s) a.sen[s] = h->sen[s];
+    a.prims = h->d_prims; a.map_off = h->d_map_off; a.map_ns = h->d_map_ns; a.map_nb = h->d_map_nb;
+    a.env_map = h->d_env_map; a.order = h->d_order; a.targets = h->d_targets;
+    a.pool = h->have_pool ? h->d_pool : nullptr;
+    a.drag_env = h->d_drag; a.lam_env = h->d_lam;
+    a.state = h->d_state; a.pool_k = h->d_pool_k;
+    a.work = h->d_work; a.status = h->d_status;
+    a.counters = h->d_counters;
+    return a;
+}
+
+int run(sim_handle* h, bool adjoint, Args& a, cudaStream_t st, bool step_adjoint = false) {
+    a.sm = step_adjoint ? h->sm_sb : (adjoint ? h->sm_b : h->sm_f);
+    const size_t smem = step_adjoint ? h->smem_sb : (adjoint ? h->smem_b : h->smem_f);
+    CK(cudaMemsetAsync(h->d_work, 0, sizeof(int), st));
+    h->last_stream = st;
+    CK(ds::launch_sim(adjoint, h->rpt, a, adjoint ? h->grid_b : h->grid_f, 32 * h->nw, smem, st));
+    return SIM_OK;
+}
+
+void build_sensors(sim_handle* h, std::vector<float4>& cam, std::vector<float4>& lid) {
+    const sim_config& c = h->cfg;
+    int s = 0;
+    if (c.cam_w > 0) {
+        const int W = c.cam_w, H = c.cam_h;
+        const double th = std::tan(0.5 * (double)c.cam_hfov), tv = th * H / W;
+        double fmin = 1.0;
+        cam.resize((size_t)W * H);
+        for (int j = 0; j < H; ++j)
+            for (int i = 0; i < W; ++i) {
+                double u = (2.0 * (i + 0.5) / W - 1.0) * th, v = (2.0 * (j + 0.5) / H - 1.0) * tv;
+                double n = std::sqrt(1.0 + u * u + v * v);
+                cam[(size_t)j * W + i] = make_float4((float)(1.0 / n), (float)(-u / n), (float)(-v / n), (float)(1.0 / n));
+                fmin = std::min(fmin, 1.0 / n);
+            }
+        ds::Sensor& S = h->sen[s++];
+        S.R = W * H; S.range = c.cam_range; S.kind = 0;
+        S.c0 = (float)th; S.c1 = (float)tv;
+        S.c2 = (float)(1.0 / std::sqrt(1.0 + th * th)); S.c3 = (float)(1.0 / std::sqrt(1.0 + tv * tv));
+        S.maxlen = (float)(c.cam_range / fmin);
+    }
+    if (c.lid_ch > 0) {
+        const int C = c.lid_ch, Az = c.lid_az;
+        lid.resize((size_t)C * Az);
+        for (int ch = 0; ch < C; ++ch) {
+            double el = C > 1 ? c.lid_elev_lo + ch * ((double)c.lid_elev_hi - c.lid_elev_lo) / (C - 1)
+                              : 0.5 * ((double)c.lid_elev_lo + c.lid_elev_hi);
+            for (int k = 0; k < Az; ++k) {
+                double az = 2.0 * M_PI * k / Az;
+                lid[(size_t)ch * Az + k] = make_float4((float)(std::cos(el) * std::cos(az)),
+                                                       (float)(std::cos(el) * std::sin(az)), (float)std::sin(el), 1.f);
+            }
+        }
+        ds::Sensor& S = h->sen[s++];
+        S.R = C * Az; S.range = c.lid_range; S.kind = 1;
+        S.c0 = c.lid_elev_lo; S.c1 = c.lid_elev_hi;
+        S.maxlen = c.lid_range;
+    }
+    h->S = s;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* sim_version(void) { return "diffsim-b300 0.1 (sm_103a)"; }
+
+const char* sim_strerror(int code) {
+    if (code > 0 || code < -9) return "unknown error";
+    return kErr[-code];
+}
+
+int sim_state_dim(int model) { return model == SIM_MODEL_POINT_MASS ? 12 : (model == SIM_MODEL_RIGID ? 13 : -1); }
+int sim_action_dim(int model) { return model == SIM_MODEL_POINT_MASS ? 3 : (model == SIM_MODEL_RIGID ? 4 : -1); }
+
+int sim_destroy(sim_handle* h) {
+    if (!h) return SIM_OK;
+    cudaDeviceSynchronize();
+    dfree(h->d_prims); dfree(h->d_map_off); dfree(h->d_map_ns); dfree(h->d_map_nb);
+    dfree(h->d_env_map); dfree(h->d_order); dfree(h->d_targets); dfree(h->d_pool);
+    dfree(h->d_drag); dfree(h->d_lam); dfree(h->d_cam); dfree(h->d_lid);
+    dfree(h->d_state); dfree(h->d_pool_k); dfree(h->d_ckpt); dfree(h->d_ckpt_k);
+    dfree(h->d_done_tape); dfree(h->d_sdf_tape); dfree(h->d_tape_cam); dfree(h->d_tape_lid);
+    dfree(h->d_work); dfree(h->d_status); dfree(h->d_counters);
+    delete h;
+    return SIM_OK;
+}
+
+int sim_create(const sim_config* cfg, sim_handle** out) {
+    if (!cfg || !out) return SIM_ERR_NULL_PTR;
+    *out = nullptr;
+    int rc = validate(cfg);
+    if (rc) return rc;
+    sim_handle* h = new (std::nothrow) sim_handle();
+    if (!h) return SIM_ERR_OOM;
+    h->cfg = *cfg;
+    h->D = sim_state_dim(cfg->model);
+    h->A = sim_action_dim(cfg->model);
+    h->N = cfg->n_env; h->M = cfg->n_agent; h->NM = h->N * h->M; h->T = cfg->horizon;
+    h->K = cfg->ckpt_every > 0 ? std::min(cfg->ckpt_every, h->T) : h->T;
+    h->Rc = cfg->cam_w > 0 ? cfg->cam_w * cfg->cam_h : 0;
+    h->Rl = cfg->lid_ch > 0 ? cfg->lid_ch * cfg->lid_az : 0;
+#define TRY(x)                 \
+    do {                       \
+        int r_ = (x);          \
+        if (r_) {              \
+            sim_destroy(h);    \
+            return r_;         \
+        }                      \
+    } while (0)
+    TRY(cuda_err(cudaGetDevice(&h->device)));
+    TRY(cuda_err(cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device)));
+    std::vector<float4> cam, lid;
+    build_sensors(h, cam, lid);
+    int s = 0;
+    if (h->Rc) {
+        TRY(dalloc(h, &h->d_cam, cam.size()));
+        TRY(cuda_err(cudaMemcpy(h->d_cam, cam.data(), cam.size() * sizeof(float4), cudaMemcpyHostToDevice)));
+        h->sen[s++].dir = h->d_cam;
+    }
+    if (h->Rl) {
+        TRY(dalloc(h, &h->d_lid, lid.size()));
+        TRY(cuda_err(cudaMemcpy(h->d_lid, lid.data(), lid.size() * sizeof(float4), cudaMemcpyHostToDevice)));
+        h->sen[s++].dir = h->d_lid;
+    }
+    const size_t tape_bytes = (size_t)h->T * h->NM * (h->Rc + h->Rl) * 2;
+    h->tape = cfg->tape_hits == 1 || (cfg->tape_hits == -1 && tape_bytes <= (size_t(8) << 30));
+    if (h->S == 0) h->tape = false;
+    const int nseg = (h->T + h->K - 1) / h->K;
+    TRY(dalloc(h, &h->d_state, (size_t)h->NM * h->D));
+    TRY(dalloc(h, &h->d_pool_k, (size_t)h->N));
+    TRY(dalloc(h, &h->d_ckpt, (size_t)nseg * h->NM * h->D));
+    TRY(dalloc(h, &h->d_ckpt_k, (size_t)nseg * h->N));
+    TRY(dalloc(h, &h->d_done_tape, (size_t)h->T * h->NM));
+    TRY(dalloc(h, &h->d_sdf_tape, (size_t)h->T * h->NM));
+    if (h->tape) {
+        if (h->Rc) TRY(dalloc(h, &h->d_tape_cam, (size_t)h->T * h->NM * h->Rc));
+        if (h->Rl) TRY(dalloc(h, &h->d_tape_lid, (size_t)h->T * h->NM * h->Rl));
+    }
+    TRY(dalloc(h, &h->d_work, 1));
+    TRY(dalloc(h, &h->d_status, 1));
+    TRY(dalloc(h, &h->d_counters, 4));
+    TRY(cuda_err(cudaMemset(h->d_status, 0, sizeof(int))));
+    TRY(cuda_err(cudaMemset(h->d_counters, 0, 4 * sizeof(unsigned long long))));
+    TRY(cuda_err(cudaMemset(h->d_pool_k, 0, sizeof(int) * h->N)));
+    TRY(cuda_err(cudaMemset(h->d_state, 0, sizeof(float) * (size_t)h->NM * h->D)));
+#undef TRY
+    *out = h;
+    return SIM_OK;
+}
+
+int sim_workspace_bytes(const sim_handle* h, size_t* bytes) {
+    if (!h || !bytes) return SIM_ERR_NULL_PTR;
+    *bytes = h->bytes;
+    return SIM_OK;
+}
+
+int sim_set_scene(sim_handle* h, const float* spheres, const int32_t* sph_off, const float* boxes,
+                  const int32_t* box_off, int32_t n_maps, const int32_t* env_map, const float* targets) {
+    if (!h || !sph_off || !box_off || !env_map || !targets) return SIM_ERR_NULL_PTR;
+    if (n_maps < 1) return SIM_ERR_SIZE;
+    if (sph_off[0] != 0 || box_off[0] != 0) return SIM_ERR_SIZE;
+    int ns_max = 0, nb_max = 0;
+    for (int m = 0; m < n_maps; ++m) {
+        const int ns = sph_off[m + 1] - sph_off[m], nb = box_off[m + 1] - box_off[m];
+        if (ns < 0 || nb < 0 || ns + nb > 32767) return SIM_ERR_SIZE;
+        ns_max = std::max(ns_max, ns);
+        nb_max = std::max(nb_max, nb);
+    }
+    const long Ks = sph_off[n_maps], Kb = box_off[n_maps];
+    if ((Ks > 0 && !spheres) || (Kb > 0 && !boxes)) return SIM_ERR_NULL_PTR;
+    for (long k = 0; k < Ks; ++k) {
+        for (int j = 0; j < 4; ++j)
+            if (!std::isfinite(spheres[4 * k + j])) return SIM_ERR_INVALID_ARG;
+        if (spheres[4 * k + 3] < 0.f) return SIM_ERR_INVALID_ARG;
+    }
+    for (long k = 0; k < Kb; ++k)
+        for (int j = 0; j < 3; ++j) {
+            if (!std::isfinite(boxes[6 * k + j]) || !std::isfinite(boxes[6 * k + 3 + j])) return SIM_ERR_INVALID_ARG;
+            if (boxes[6 * k + 3 + j] < boxes[6 * k + j]) return SIM_ERR_INVALID_ARG;
+        }
+    for (int e = 0; e < h->N; ++e)
+        if (env_map[e] < 0 || env_map[e] >= n_maps) return SIM_ERR_SIZE;
+    for (long k = 0; k < 3L * h->NM; ++k)
+        if (!std::isfinite(targets[k])) return SIM_ERR_INVALID_ARG;
+    // map blocks: spheres (c, r), then boxes as (min, 0), (max, 0)
+    std::vector<float4> blk;
+    std::vector<int> off(n_maps), vns(n_maps), vnb(n_maps);
+    blk.reserve((size_t)Ks + 2 * Kb);
+    for (int m = 0; m < n_maps; ++m) {
+        off[m] = (int)blk.size();
+        vns[m] = sph_off[m + 1] - sph_off[m];
+        vnb[m] = box_off[m + 1] - box_off[m];
+        for (int k = sph_off[m]; k < sph_off[m + 1]; ++k)
+            blk.push_back(make_float4(spheres[4 * k], spheres[4 * k + 1], spheres[4 * k + 2], spheres[4 * k + 3]));
+        for (int k = box_off[m]; k < box_off[m + 1]; ++k) {
+            blk.push_back(make_float4(boxes[6 * k], boxes[6 * k + 1], boxes[6 * k + 2], 0.f));
+            blk.push_back(make_float4(boxes[6 * k + 3], boxes[6 * k + 4], boxes[6 * k + 5], 0.f));
+        }
+    }
+    if (blk.size() >= (size_t)INT32_MAX) return SIM_ERR_SIZE;
+    // environments in descending work order (load balance of the ticket queue)
+    std::vector<int> order(h->N);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+        return vns[env_map[x]] + vnb[env_map[x]] > vns[env_map[y]] + vnb[env_map[y]];
+    });
+    dfree(h->d_prims); dfree(h->d_map_off); dfree(h->d_map_ns); dfree(h->d_map_nb);
+    dfree(h->d_env_map); dfree(h->d_order); dfree(h->d_targets);
+    int rc;
+    if ((rc = dalloc(h, &h->d_prims, std::max<size_t>(blk.size(), 1)))) return rc;
+    if ((rc = dalloc(h, &h->d_map_off, n_maps)) || (rc = dalloc(h, &h->d_map_ns, n_maps)) ||
+        (rc = dalloc(h, &h->d_map_nb, n_maps)) || (rc = dalloc(h, &h->d_env_map, h->N)) ||
+        (rc = dalloc(h, &h->d_order, h->N)) || (rc = dalloc(h, &h->d_targets, 3 * (size_t)h->NM)))
+        return rc;
+    if (!blk.empty()) CK(cudaMemcpy(h->d_prims, blk.data(), blk.size() * sizeof(float4), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(h->d_map_off, off.data(), n_maps * sizeof(int), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(h->d_map_ns, vns.data(), n_maps * sizeof(int), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(h->d_map_nb, vnb.data(), n_maps * sizeof(int), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(h->d_env_map, env_map, h->N * sizeof(int), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(h->d_order, order.data(), h->N * sizeof(int), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(h->d_targets, targets, 3 * (size_t)h->NM * sizeof(float), cudaMemcpyHostToDevice));
+    h->ns_max = ns_max;
+    h->nb_max = nb_max;
+    h->n_maps = n_maps;
+    rc = configure_launch(h);
+    if (rc) return rc;
+    h->have_scene = true;
+    h->have_rollout = false;
+    return SIM_OK;
+}
+
+int sim_set_pool(sim_handle* h, const float* pool) {
+    if (!h || !pool) return SIM_ERR_NULL_PTR;
+    const size_t n = (size_t)h->cfg.pool_size * h->NM * h->D;
+    if (n == 0) return SIM_ERR_SIZE;
+    for (size_t k = 0; k < n; ++k)
+        if (!std::isfinite(pool[k])) return SIM_ERR_INVALID_ARG;
+    dfree(h->d_pool);
+    int rc = dalloc(h, &h->d_pool, n);
+    if (rc) return rc;
+    CK(cudaMemcpy(h->d_pool, pool, n * sizeof(float), cudaMemcpyHostToDevice));
+    h->have_pool = true;
+    return SIM_OK;
+}
+
+int sim_set_env_params(sim_handle* h, const float* drag, const float* lam) {
+    if (!h) return SIM_ERR_NULL_PTR;
+    if (h->cfg.model != SIM_MODEL_POINT_MASS && (drag || lam)) return SIM_ERR_UNSUPPORTED;
+    dfree(h->d_drag);
+    dfree(h->d_lam);
+    int rc;
+    if (drag) {
+        for (int e = 0; e < h->N; ++e)
+            if (!std::isfinite(drag[e])) return SIM_ERR_INVALID_ARG;
+        if ((rc = dalloc(h, &h->d_drag, h->N))) return rc;
+        CK(cudaMemcpy(h->d_drag, drag, h->N * sizeof(float), cudaMemcpyHostToDevice));
+    }
+    if (lam) {
+        for (int e = 0; e < h->N; ++e)
+            if (!std::isfinite(lam[e])) return SIM_ERR_INVALID_ARG;
+        if ((rc = dalloc(h, &h->d_lam, h->N))) return rc;
+        CK(cudaMemcpy(h->d_lam, lam, h->N * sizeof(float), cudaMemcpyHostToDevice));
+    }
+    return SIM_OK;
+}
+
+int sim_reset(sim_handle* h, const float* state0, sim_stream_t stream) {
+    if (!h) return SIM_ERR_NULL_PTR;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t n = (size_t)h->NM * h->D * sizeof(float);
+    if (state0) CK(cudaMemcpyAsync(h->d_state, state0, n, cudaMemcpyDeviceToDevice, st));
+    else if (h->have_pool) CK(cudaMemcpyAsync(h->d_state, h->d_pool, n, cudaMemcpyDeviceToDevice, st));
+    else return SIM_ERR_NOT_READY;
+    CK(cudaMemsetAsync(h->d_pool_k, 0, sizeof(int) * h->N, st));
+    h->have_rollout = false;
+    h->last_stream = st;
+    return SIM_OK;
+}
+
+int sim_get_state(const sim_handle* h, float* dst, sim_stream_t stream) {
+    if (!h || !dst) return SIM_ERR_NULL_PTR;
+    CK(cudaMemcpyAsync(dst, h->d_state, (size_t)h->NM * h->D * sizeof(float), cudaMemcpyDeviceToDevice,
+                       (cudaStream_t)stream));
+    return SIM_OK;
+}
+
+int sim_set_state(sim_handle* h, const float* src, sim_stream_t stream) {
+    if (!h || !src) return SIM_ERR_NULL_PTR;
+    CK(cudaMemcpyAsync(h->d_state, src, (size_t)h->NM * h->D * sizeof(float), cudaMemcpyDeviceToDevice,
+                       (cudaStream_t)stream));
+    h->have_rollout = false;
+    return SIM_OK;
+}
+
+int sim_render(sim_handle* h, float* depth, float* lidar, sim_stream_t stream) {
+    if (!h) return SIM_ERR_NULL_PTR;
+    if (!h->have_scene) return SIM_ERR_NOT_READY;
+    Args a = base_args(h);
+    a.render_only = 1;
+    a.T = 1;
+    int s = 0;
+    if (h->Rc) { a.sen[s].out = depth; a.sen[s].tape = nullptr; ++s; }
+    if (h->Rl) { a.sen[s].out = lidar; a.sen[s].tape = nullptr; ++s; }
+    return run(h, false, a, (cudaStream_t)stream);
+}
+
+int sim_step(sim_handle* h, const float* actions, float* depth, float* lidar, float* r_ctrl, int8_t* r_goal,
+             uint8_t* done, sim_stream_t stream) {
+    if (!h || !actions) return SIM_ERR_NULL_PTR;
+    if (!h->have_scene) return SIM_ERR_NOT_READY;
+    if (h->cfg.terminate && !h->have_pool) return SIM_ERR_NOT_READY;
+    Args a = base_args(h);
+    a.T = 1;
+    a.K = 1;
+    a.actions = actions;
+    a.r_ctrl = r_ctrl; a.r_goal = r_goal; a.done = done;
+    int s = 0;
+    if (h->Rc) { a.sen[s].out = depth; a.sen[s].tape = nullptr; ++s; }
+    if (h->Rl) { a.sen[s].out = lidar; a.sen[s].tape = nullptr; ++s; }
+    return run(h, false, a, (cudaStream_t)stream);
+}
+
+int sim_rollout(sim_handle* h, const float* actions, float* r_ctrl, int8_t* r_goal, uint8_t* done, float* depth,
+                float* lidar, sim_stream_t stream) {
+    if (!h || !actions) return SIM_ERR_NULL_PTR;
+    if (!h->have_scene) return SIM_ERR_NOT_READY;
+    if (h->cfg.terminate && !h->have_pool) return SIM_ERR_NOT_READY;
+    Args a = base_args(h);
+    a.actions = actions;
+    a.r_ctrl = r_ctrl; a.r_goal = r_goal; a.done = done;
+    a.done_tape = h->d_done_tape;
+    a.sdf_tape = h->d_sdf_tape;
+    a.ckpt = h->d_ckpt;
+    a.ckpt_k = h->d_ckpt_k;
+    int s = 0;
+    if (h->Rc) { a.sen[s].out = depth; a.sen[s].tape = h->d_tape_cam; ++s; }
+    if (h->Rl) { a.sen[s].out = lidar; a.sen[s].tape = h->d_tape_lid; ++s; }
+    int rc = run(h, false, a, (cudaStream_t)stream);
+    if (rc) return rc;
+    h->have_rollout = true;
+    h->rollout_actions = actions;
+    return SIM_OK;
+}
+
+int sim_backward(sim_handle* h, const float* g_r, const float* g_depth, const float* g_lidar, const float* g_sT,
+                 float* g_a, float* g_s0, sim_stream_t stream) {
+    if (!h || !g_r || !g_a) return SIM_ERR_NULL_PTR;
+    if (!h->have_rollout) return SIM_ERR_NOT_READY;
+    Args a = base_args(h);
+    a.actions = h->rollout_actions;
+    a.done_rd = h->d_done_tape;
+    a.sdf_tape = h->d_sdf_tape;
+    a.ckpt = h->d_ckpt;
+    a.ckpt_k = h->d_ckpt_k;
+    a.g_r = g_r; a.g_sT = g_sT; a.g_a = g_a; a.g_s0 = g_s0;
+    int s = 0;
+    if (h->Rc) { a.sen[s].gout = g_depth; a.sen[s].tape = h->d_tape_cam; ++s; }
+    if (h->Rl) { a.sen[s].gout = g_lidar; a.sen[s].tape = h->d_tape_lid; ++s; }
+    return run(h, true, a, (cudaStream_t)stream);
+}
+
+int sim_step_backward(sim_handle* h, const float* s_t, const float* a_t, const uint8_t* done_t,
+                      const float* g_s_next, const float* g_r, const float* g_depth, const float* g_lidar,
+                      float* g_a, float* g_s, sim_stream_t stream) {
+    if (!h || !s_t || !a_t || !done_t || !g_r || !g_a) return SIM_ERR_NULL_PTR;
+    if (!h->have_scene) return SIM_ERR_NOT_READY;
+    Args a = base_args(h);
+    a.T = 1;
+    a.K = 1;
+    a.actions = a_t;
+    a.done_rd = done_t;
+    a.sdf_tape = nullptr;
+    a.ckpt = const_cast<float*>(s_t);
+    a.ckpt_k = nullptr;
+    a.g_r = g_r; a.g_sT = g_s_next; a.g_a = g_a; a.g_s0 = g_s;
+    int s = 0;
+    if (h->Rc) { a.sen[s].gout = g_depth; a.sen[s].tape = nullptr; ++s; }
+    if (h->Rl) { a.sen[s].gout = g_lidar; a.sen[s].tape = nullptr; ++s; }
+    return run(h, true, a, (cudaStream_t)stream, true);
+}
+
+int sim_last_status(sim_handle* h, int32_t* status, int32_t* per_env) {
+    if (!h || !status) return SIM_ERR_NULL_PTR;
+    if (per_env) return SIM_ERR_INVALID_ARG;
+    CK(cudaStreamSynchronize(h->last_stream));
+    int v = 0;
+    CK(cudaMemcpy(&v, h->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+    CK(cudaMemset(h->d_status, 0, sizeof(int)));
+    *status = v;
+    if (v & SIM_STATUS_TIMEOUT) return SIM_ERR_TIMEOUT;
+    if (v & SIM_STATUS_NAN) return SIM_ERR_NAN;
+    return SIM_OK;
+}
+
+int sim_counters(sim_handle* h, uint64_t* out, int32_t reset) {
+    if (!h || !out) return SIM_ERR_NULL_PTR;
+    CK(cudaStreamSynchronize(h->last_stream));
+    unsigned long long v[4];
+    CK(cudaMemcpy(v, h->d_counters, sizeof(v), cudaMemcpyDeviceToHost));
+    for (int i = 0; i < 4; ++i) out[i] = v[i];
+    if (reset) CK(cudaMemset(h->d_counters, 0, sizeof(v)));
+    return SIM_OK;
+}
+
+int sim_launch_info(const sim_handle* h, int32_t* warps_per_cta, int32_t* rays_per_thread, int32_t* grid,
+                    int32_t* smem_bytes) {
+    if (!h) return SIM_ERR_NULL_PTR;
+    if (warps_per_cta) *warps_per_cta = h->nw;
+    if (rays_per_thread) *rays_per_thread = h->rpt;
+    if (grid) *grid = h->grid_f;
+    if (smem_bytes) *smem_bytes = (int32_t)h->smem_f;
+    return SIM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,343 @@
+// sim_device.cuh -- per-agent FP32 device math of the fused quadrotor step:
+// dynamics (Eq. 1, Eq. 3), sensor pose (Sec. III-B), signed distances,
+// rewards (Sec. III-C/D/E) and their vector-Jacobian products (Eq. 5).
+#pragma once
+#include <cuda_runtime.h>
+#include <math_constants.h>
+#include <stdint.h>
+
+namespace ds {
+
+enum { MODEL_PM = 0, MODEL_RIGID = 1 };
+
+// Physics and task constants (kernel-parameter resident).
+struct Phys {
+    int model, M, D, A;
+    float dt, g, lam, drag, act_scale, ema_alpha;
+    float mass, J[3], K[3], Dd[3], rs[3];
+    int pos_sq;
+    float w_pos, w_obs, d_safe, w_act, w_agent, d_agent, success_radius, r_quad;
+    float blo[3], bhi[3];
+    int terminate, P;
+};
+
+__device__ __forceinline__ float clip1(float x) { return fminf(fmaxf(x, -1.f), 1.f); }
+__device__ __forceinline__ float dclip1(float x) { return (x >= -1.f && x <= 1.f) ? 1.f : 0.f; }
+__device__ __forceinline__ float relu(float x) { return x > 0.f ? x : 0.f; }
+__device__ __forceinline__ float dot3(const float* a, const float* b) {
+    return fmaf(a[0], b[0], fmaf(a[1], b[1], a[2] * b[2]));
+}
+__device__ __forceinline__ void cross3(const float* a, const float* b, float* o) {
+    float x = a[1] * b[2] - a[2] * b[1];
+    float y = a[2] * b[0] - a[0] * b[2];
+    float z = a[0] * b[1] - a[1] * b[0];
+    o[0] = x; o[1] = y; o[2] = z;
+}
+
+// Row-major rotation body -> world of the Hamilton quaternion (w, x, y, z).
+__device__ __forceinline__ void quat_rot(const float* q, float* R) {
+    float w = q[0], x = q[1], y = q[2], z = q[3];
+    R[0] = 1.f - 2.f * (y * y + z * z); R[1] = 2.f * (x * y - w * z); R[2] = 2.f * (x * z + w * y);
+    R[3] = 2.f * (x * y + w * z); R[4] = 1.f - 2.f * (x * x + z * z); R[5] = 2.f * (y * z - w * x);
+    R[6] = 2.f * (x * z - w * y); R[7] = 2.f * (y * z + w * x); R[8] = 1.f - 2.f * (x * x + y * y);
+}
+
+// d<R(q), G>/dq for row-major G: partial derivatives of the polynomial R(q).
+__device__ __forceinline__ void quat_rot_vjp(const float* q, const float* G, float* gq) {
+    float w = q[0], x = q[1], y = q[2], z = q[3];
+    // d/dw: 2 [0 -z y; z 0 -x; -y x 0]
+    gq[0] += 2.f * (-z * G[1] + y * G[2] + z * G[3] - x * G[5] - y * G[6] + x * G[7]);
+    // d/dx: 2 [0 y z; y -2x -w; z w -2x]
+    gq[1] += 2.f * (y * G[1] + z * G[2] + y * G[3] - 2.f * x * G[4] - w * G[5] + z * G[6] + w * G[7] - 2.f * x * G[8]);
+    // d/dy: 2 [-2y x w; x 0 z; -w z -2y]
+    gq[2] += 2.f * (-2.f * y * G[0] + x * G[1] + w * G[2] + x * G[3] + z * G[5] - w * G[6] + z * G[7] - 2.f * y * G[8]);
+    // d/dz: 2 [-2z -w x; w -2z y; x y 0]
+    gq[3] += 2.f * (-2.f * z * G[0] - w * G[1] + x * G[2] + w * G[3] - 2.f * z * G[4] + y * G[5] + x * G[6] + y * G[7]);
+}
+
+// ------------------------------------------------------------------ dynamics
+// Eq. 3, explicit Euler; the velocity EMA feeds the point-mass heading.
+__device__ __forceinline__ void pm_step(const Phys& c, float drag, float lam, const float* s,
+                                        const float* act, float* o) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        float u = c.act_scale * clip1(act[i]);
+        float gi = (i == 2) ? -c.g : 0.f;
+        float p = s[i], v = s[3 + i], a = s[6 + i], e = s[9 + i];
+        float vn = v + c.dt * (a + gi - drag * v);
+        o[i] = p + c.dt * v;
+        o[3 + i] = vn;
+        o[6 + i] = a + c.dt * lam * (u - a);
+        o[9 + i] = (1.f - c.ema_alpha) * e + c.ema_alpha * vn;
+    }
+}
+
+// Eq. 1 with the body-rate controller, explicit Euler, quaternion renormalised.
+__device__ __forceinline__ void rb_step(const Phys& c, const float* s, const float* act, float* o) {
+    const float* q = s + 3; const float* v = s + 7; const float* w = s + 10;
+    float T = c.mass * c.g * (1.f + clip1(act[0]));
+    float Jw[3], gy[3], wd[3], R[9], vb[3], vd[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) Jw[i] = c.J[i] * w[i];
+    cross3(w, Jw, gy);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        float wc = c.rs[i] * clip1(act[1 + i]);
+        float tau = c.J[i] * c.K[i] * (wc - w[i]) + gy[i];
+        wd[i] = (tau - gy[i]) / c.J[i];
+    }
+    quat_rot(q, R);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) vb[j] = c.Dd[j] * (R[j] * v[0] + R[3 + j] * v[1] + R[6 + j] * v[2]);
+    float Tm = T / c.mass;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        float gi = (i == 2) ? -c.g : 0.f;
+        vd[i] = gi + Tm * R[3 * i + 2] - (R[3 * i] * vb[0] + R[3 * i + 1] * vb[1] + R[3 * i + 2] * vb[2]);
+    }
+    // q (x) (0, w)
+    float qd0 = -(q[1] * w[0] + q[2] * w[1] + q[3] * w[2]);
+    float qd1 = q[0] * w[0] + q[2] * w[2] - q[3] * w[1];
+    float qd2 = q[0] * w[1] + q[3] * w[0] - q[1] * w[2];
+    float qd3 = q[0] * w[2] + q[1] * w[1] - q[2] * w[0];
+    float h = 0.5f * c.dt;
+    float qt0 = q[0] + h * qd0, qt1 = q[1] + h * qd1, qt2 = q[2] + h * qd2, qt3 = q[3] + h * qd3;
+    float inv = rsqrtf(qt0 * qt0 + qt1 * qt1 + qt2 * qt2 + qt3 * qt3);
+    float n[13];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) n[i] = s[i] + c.dt * v[i];
+    n[3] = qt0 * inv; n[4] = qt1 * inv; n[5] = qt2 * inv; n[6] = qt3 * inv;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) n[7 + i] = v[i] + c.dt * vd[i];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) n[10 + i] = w[i] + c.dt * wd[i];
+#pragma unroll
+    for (int i = 0; i < 13; ++i) o[i] = n[i];
+}
+
+// Point-mass heading frame (Sec. III-B): z along thrust, x along the
+// horizontal velocity EMA made orthogonal to z, y = z x x.
+struct PmFrame {
+    float z[3], h[3], hp[3], x[3], na, nh, hz;
+    bool zfb, hfb;
+};
+
+__device__ __forceinline__ void pm_frame(const float* s, PmFrame& f) {
+    const float* a = s + 6; const float* e = s + 9;
+    f.na = sqrtf(dot3(a, a));
+    f.zfb = f.na < 1e-6f;
+    if (f.zfb) { f.z[0] = 0.f; f.z[1] = 0.f; f.z[2] = 1.f; }
+    else { float r = 1.f / f.na; f.z[0] = a[0] * r; f.z[1] = a[1] * r; f.z[2] = a[2] * r; }
+    f.h[0] = e[0]; f.h[1] = e[1]; f.h[2] = 0.f;
+    f.hfb = false;
+#pragma unroll 1
+    for (int k = 0; k < 3; ++k) {
+        f.hz = dot3(f.h, f.z);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) f.hp[i] = f.h[i] - f.hz * f.z[i];
+        f.nh = sqrtf(dot3(f.hp, f.hp));
+        if (f.nh >= 1e-6f || k == 2) break;
+        f.hfb = true;  // fall back to world +x, then +y
+        f.h[0] = (k == 0) ? 1.f : 0.f; f.h[1] = (k == 0) ? 0.f : 1.f; f.h[2] = 0.f;
+    }
+    float r = 1.f / f.nh;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) f.x[i] = f.hp[i] * r;
+}
+
+// Sensor pose: o = position, R (row-major) = body -> world.
+__device__ __forceinline__ void sensor_pose(int model, const float* s, float* o, float* R) {
+    o[0] = s[0]; o[1] = s[1]; o[2] = s[2];
+    if (model == MODEL_RIGID) { quat_rot(s + 3, R); return; }
+    PmFrame f;
+    pm_frame(s, f);
+    float y[3];
+    cross3(f.z, f.x, y);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) { R[3 * i] = f.x[i]; R[3 * i + 1] = y[i]; R[3 * i + 2] = f.z[i]; }
+}
+
+// VJP of the pose: cotangents go (origin) and gR (row-major R) into gs.
+__device__ __forceinline__ void pose_vjp(int model, const float* s, const float* go, const float* gR,
+                                         float* gs) {
+    gs[0] += go[0]; gs[1] += go[1]; gs[2] += go[2];
+    if (model == MODEL_RIGID) { quat_rot_vjp(s + 3, gR, gs + 3); return; }
+    PmFrame f;
+    pm_frame(s, f);
+    float gx[3] = {gR[0], gR[3], gR[6]}, gy[3] = {gR[1], gR[4], gR[7]}, gz[3] = {gR[2], gR[5], gR[8]};
+    float t[3];
+    cross3(f.x, gy, t);  // y = z x x
+    gz[0] += t[0]; gz[1] += t[1]; gz[2] += t[2];
+    cross3(gy, f.z, t);
+    gx[0] += t[0]; gx[1] += t[1]; gx[2] += t[2];
+    float xg = dot3(f.x, gx), ghp[3];
+    float rn = 1.f / f.nh;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) ghp[i] = (gx[i] - f.x[i] * xg) * rn;
+    float zg = dot3(f.z, ghp);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) gz[i] += -f.hz * ghp[i] - f.h[i] * zg;
+    if (!f.hfb) { gs[9] += ghp[0] - f.z[0] * zg; gs[10] += ghp[1] - f.z[1] * zg; }
+    if (!f.zfb) {
+        float zz = dot3(f.z, gz), ra = 1.f / f.na;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) gs[6 + i] += (gz[i] - f.z[i] * zz) * ra;
+    }
+}
+
+// VJP of the point-mass step.
+__device__ __forceinline__ void pm_step_vjp(const Phys& c, float drag, float lam, const float* act,
+                                            const float* go, float* gs, float* ga) {
+    float al = c.ema_alpha, dt = c.dt;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        float gp = go[i], gv = go[3 + i] + al * go[9 + i], gA = go[6 + i];
+        gs[9 + i] += (1.f - al) * go[9 + i];
+        gs[i] += gp;
+        gs[3 + i] += dt * gp + (1.f - dt * drag) * gv;
+        gs[6 + i] += dt * gv + (1.f - dt * lam) * gA;
+        ga[i] += c.act_scale * dclip1(act[i]) * (dt * lam * gA);
+    }
+}
+
+// VJP of the rigid-body step (recomputes the forward intermediates).
+__device__ __forceinline__ void rb_step_vjp(const Phys& c, const float* s, const float* act,
+                                            const float* go, float* gs, float* ga) {
+    const float* q = s + 3; const float* v = s + 7; const float* w = s + 10;
+    float dt = c.dt, m = c.mass;
+    float T = m * c.g * (1.f + clip1(act[0]));
+    float R[9], dvb[3], Jw[3];
+    quat_rot(q, R);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) dvb[j] = c.Dd[j] * (R[j] * v[0] + R[3 + j] * v[1] + R[6 + j] * v[2]);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) Jw[i] = c.J[i] * w[i];
+    float qd0 = -(q[1] * w[0] + q[2] * w[1] + q[3] * w[2]);
+    float qd1 = q[0] * w[0] + q[2] * w[2] - q[3] * w[1];
+    float qd2 = q[0] * w[1] + q[3] * w[0] - q[1] * w[2];
+    float qd3 = q[0] * w[2] + q[1] * w[1] - q[2] * w[0];
+    float h = 0.5f * dt;
+    float qt[4] = {q[0] + h * qd0, q[1] + h * qd1, q[2] + h * qd2, q[3] + h * qd3};
+    float nq = sqrtf(qt[0] * qt[0] + qt[1] * qt[1] + qt[2] * qt[2] + qt[3] * qt[3]);
+    float rq = 1.f / nq;
+    float qn[4] = {qt[0] * rq, qt[1] * rq, qt[2] * rq, qt[3] * rq};
+
+    const float* gqn = go + 3; const float* gvn = go + 7; const float* gwn = go + 10;
+    float gvd[3], gwd[3], gqd[4];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        gs[i] += go[i];
+        gs[7 + i] += dt * go[i] + gvn[i];
+        gvd[i] = dt * gvn[i];
+        gs[10 + i] += gwn[i];
+        gwd[i] = dt * gwn[i];
+    }
+    float qg = qn[0] * gqn[0] + qn[1] * gqn[1] + qn[2] * gqn[2] + qn[3] * gqn[3];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        float gqt = (gqn[k] - qn[k] * qg) * rq;
+        gs[3 + k] += gqt;
+        gqd[k] = h * gqt;
+    }
+    // qd = q (x) (0, w)
+    {
+        float vq[3] = {q[1], q[2], q[3]}, gv3[3] = {gqd[1], gqd[2], gqd[3]}, t[3];
+        gs[3] += dot3(gv3, w);
+        cross3(w, gv3, t);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) gs[4 + i] += -gqd[0] * w[i] + t[i];
+        cross3(gv3, vq, t);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) gs[10 + i] += -gqd[0] * vq[i] + q[0] * gv3[i] + t[i];
+    }
+    // vd = g + (T/m) R e3 - R dvb,  dvb = D (R^T v)
+    float gR[9], gT = 0.f, gvb[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        gT += R[3 * i + 2] * gvd[i];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) gR[3 * i + j] = -gvd[i] * dvb[j];
+        gR[3 * i + 2] += (T / m) * gvd[i];
+    }
+    gT /= m;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) gvb[j] = -c.Dd[j] * (R[j] * gvd[0] + R[3 + j] * gvd[1] + R[6 + j] * gvd[2]);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        gs[7 + i] += R[3 * i] * gvb[0] + R[3 * i + 1] * gvb[1] + R[3 * i + 2] * gvb[2];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) gR[3 * i + j] += v[i] * gvb[j];
+    }
+    quat_rot_vjp(q, gR, gs + 3);
+    // wd = (tau - gy)/J, tau = J K (wc - w) + gy, gy = w x Jw
+    float gtau[3], ggy[3], t[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        gtau[i] = gwd[i] / c.J[i];
+        ggy[i] = -gtau[i] + gtau[i];
+        gs[10 + i] += -c.J[i] * c.K[i] * gtau[i];
+        ga[1 + i] += c.rs[i] * dclip1(act[1 + i]) * (c.J[i] * c.K[i] * gtau[i]);
+    }
+    cross3(Jw, ggy, t);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) gs[10 + i] += t[i];
+    cross3(ggy, w, t);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) gs[10 + i] += c.J[i] * t[i];
+    ga[0] += m * c.g * dclip1(act[0]) * gT;
+}
+
+// ---------------------------------------------------------------- obstacles
+// Map block in memory: ns spheres float4 (cx, cy, cz, r), then nb boxes as
+// float4 (min xyz, 0) followed by float4 (max xyz, 0).
+__device__ __forceinline__ float sdf_prim(const float4* prim, int ns, int k, const float* p) {
+    if (k < ns) {
+        float4 s = prim[k];
+        float dx = p[0] - s.x, dy = p[1] - s.y, dz = p[2] - s.z;
+        return sqrtf(dx * dx + dy * dy + dz * dz) - s.w;
+    }
+    int b = k - ns;
+    float4 lo = prim[ns + 2 * b], hi = prim[ns + 2 * b + 1];
+    float qx = fabsf(p[0] - 0.5f * (lo.x + hi.x)) - 0.5f * (hi.x - lo.x);
+    float qy = fabsf(p[1] - 0.5f * (lo.y + hi.y)) - 0.5f * (hi.y - lo.y);
+    float qz = fabsf(p[2] - 0.5f * (lo.z + hi.z)) - 0.5f * (hi.z - lo.z);
+    float ox = relu(qx), oy = relu(qy), oz = relu(qz);
+    float in = fminf(fmaxf(qx, fmaxf(qy, qz)), 0.f);
+    return sqrtf(ox * ox + oy * oy + oz * oz) + in;
+}
+
+__device__ __forceinline__ void sdf_prim_grad(const float4* prim, int ns, int k, const float* p,
+                                              float* gp) {
+    if (k < ns) {
+        float4 s = prim[k];
+        float d[3] = {p[0] - s.x, p[1] - s.y, p[2] - s.z};
+        float n = sqrtf(dot3(d, d));
+        float r = n > 0.f ? 1.f / n : 0.f;
+        gp[0] = d[0] * r; gp[1] = d[1] * r; gp[2] = d[2] * r;
+        return;
+    }
+    int b = k - ns;
+    float4 lo = prim[ns + 2 * b], hi = prim[ns + 2 * b + 1];
+    float l[3] = {lo.x, lo.y, lo.z}, u[3] = {hi.x, hi.y, hi.z};
+    float q[3], sg[3], out = 0.f;
+    int am = 0;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        float ctr = 0.5f * (l[i] + u[i]);
+        sg[i] = (p[i] - ctr >= 0.f) ? 1.f : -1.f;
+        q[i] = fabsf(p[i] - ctr) - 0.5f * (u[i] - l[i]);
+        out += relu(q[i]) * relu(q[i]);
+    }
+    if (q[1] > q[am]) am = 1;
+    if (q[2] > q[am]) am = 2;
+    if (out > 0.f) {
+        float r = rsqrtf(out);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) gp[i] = relu(q[i]) * sg[i] * r;
+    } else {
+#pragma unroll
+        for (int i = 0; i < 3; ++i) gp[i] = (i == am) ? sg[i] : 0.f;
+    }
+}
+
+}  // namespace ds

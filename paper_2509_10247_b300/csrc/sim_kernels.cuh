@@ -1,0 +1,154 @@
+// sim_kernels.cuh -- kernel argument blocks, shared-memory layout and the
+// ray-casting building blocks shared by the rollout and adjoint kernels.
+#pragma once
+#include "sim_device.cuh"
+
+namespace ds {
+
+constexpr int MAX_SENSORS = 2;
+
+// One ray sensor: the camera (kind 0, z-depth) or the LiDAR (kind 1, range).
+struct Sensor {
+    int R;                 // rays per agent
+    const float4* dir;     // [R] body-frame unit direction (x, y, z) and output factor w
+    float range;           // output clamp
+    int kind;              // 0 camera frustum cull, 1 LiDAR elevation-band cull
+    float c0, c1, c2, c3;  // camera: tan_h, tan_v, 1/sqrt(1+tan_h^2), 1/sqrt(1+tan_v^2)
+                           // lidar:  elev_lo, elev_hi
+    float maxlen;          // longest ray length that is not clamped
+    float* out;            // [T][NM][R] output or nullptr
+    int16_t* tape;         // [T][NM][R] hit ids or nullptr
+    const float* gout;     // adjoint: [T][NM][R] cotangent or nullptr
+};
+
+// Byte offsets of the dynamic shared-memory regions of one CTA.
+struct Smem {
+    int prim;    // float4 [ns_max + 2 nb_max]     map block
+    int lsph;    // float4 [L][ns_max]             (oc.xyz, C) per culled sphere
+    int lr2;     // float  [L][ns_max]             r^2 per culled sphere
+    int lbox;    // float4 [L][nb_max][2]          (lo - o, hi - o) per culled box
+    int lid;     // short  [L][ns_max + nb_max]    primitive id of each list entry
+    int lmeta;   // int4   [L]                     (n_sph, n_box, inside_id, 0)
+    int st;      // float  [M][16]                 current state
+    int spre;    // float  [M][16]                 state before reset
+    int pose;    // float  [M][12]                 o, R
+    int aux;     // float  [M][8]                  sdf, collided, g_r, pose cotangent...
+    int gpose;   // float  [items][12]             adjoint: per-item pose cotangent partials
+    int gs;      // float  [M][16]                 adjoint: state cotangent
+    int seg;     // float  [K+1][M][16]            adjoint: segment states
+    int mbar;    // uint64 mbarrier
+    int total;
+};
+
+struct Args {
+    Phys c;
+    int N, M, NM, T, K, S;      // envs, agents/env, agents, steps, checkpoint interval, sensors
+    int ns_max, nb_max, cull;
+    int render_only;            // forward: only render the current state (no dynamics)
+    Sensor sen[MAX_SENSORS];
+    Smem sm;
+    // scene
+    const float4* prims; const int* map_off; const int* map_ns; const int* map_nb;
+    const int* env_map; const int* order; const float* targets; const float* pool;
+    const float* drag_env; const float* lam_env;
+    // state and io
+    float* state;               // [NM][D] current state (read at start, written at end)
+    const float* actions;       // [T][NM][A]
+    float* r_ctrl; int8_t* r_goal; uint8_t* done;   // [T][NM] or nullptr
+    uint8_t* done_tape;         // [T][NM] internal
+    int16_t* sdf_tape;          // [T][NM] internal
+    float* ckpt; int* ckpt_k;   // [nseg][NM][D], [nseg][N]
+    int* pool_k;                // [N]
+    // adjoint
+    const float* g_r; const float* g_sT; float* g_a; float* g_s0;
+    const uint8_t* done_rd;     // adjoint: [T][NM] done flags of the forward pass
+    // control
+    int* work; int* status;
+    unsigned long long* counters;  // [4]: sphere tests, box tests, rays, env-steps (nullable)
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// --------------------------------------------------------- TMA bulk staging
+__device__ __forceinline__ void mbar_init(uint64_t* bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// Copy `bytes` (multiple of 16, both addresses 16-byte aligned) from global
+// to shared memory with one cp.async.bulk completing on `bar`.
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t phase) {
+    uint32_t ok;
+    asm volatile(
+        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(phase)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for the mbarrier phase; false after ~2^22 polls (seconds).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase) {
+    for (int i = 0; i < (1 << 22); ++i) {
+        if (mbar_try(bar, phase)) return true;
+        if (i > 64) __nanosleep(256);
+    }
+    return false;
+}
+
+// ------------------------------------------------------------ warp helpers
+__device__ __forceinline__ void warp_argmin(float& v, int& id) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        float v2 = __shfl_xor_sync(0xffffffffu, v, o);
+        int i2 = __shfl_xor_sync(0xffffffffu, id, o);
+        if (v2 < v || (v2 == v && (unsigned)i2 < (unsigned)id)) { v = v2; id = i2; }
+    }
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// ---------------------------------------------------------------- culling
+// Conservative test: can any ray of the sensor reach the bounding sphere
+// (centre oc relative to the origin, radius rho) before its clamp?
+__device__ __forceinline__ bool cull_keep(const Sensor& s, const float* R, const float* oc, float rho) {
+    const float m = 1e-3f;
+    float L = sqrtf(dot3(oc, oc));
+    if (L <= rho + m) return true;
+    if (L - rho > s.maxlen + m) return false;
+    // body-frame centre c_B = R^T oc
+    float bx = R[0] * oc[0] + R[3] * oc[1] + R[6] * oc[2];
+    float by = R[1] * oc[0] + R[4] * oc[1] + R[7] * oc[2];
+    float bz = R[2] * oc[0] + R[5] * oc[1] + R[8] * oc[2];
+    float r = rho + m;
+    if (s.kind == 0) {
+        // four side planes of the pinhole frustum through the origin
+        if ((s.c0 * bx - by) * s.c2 < -r) return false;
+        if ((s.c0 * bx + by) * s.c2 < -r) return false;
+        if ((s.c1 * bx - bz) * s.c3 < -r) return false;
+        if ((s.c1 * bx + bz) * s.c3 < -r) return false;
+        return true;
+    }
+    float el = asinf(fminf(fmaxf(bz / L, -1.f), 1.f));
+    float del = asinf(fminf(r / L, 1.f));
+    return (el - del <= s.c1 + 1e-3f) && (el + del >= s.c0 - 1e-3f);
+}
+
+}  // namespace ds

@@ -1,0 +1,154 @@
+"""Helpers shared by the GPU parity tests: run the CUDA path and the FP64
+oracle on the same seeded inputs and compare what is unique.
+
+Tolerances (written here, used by every test):
+  STATE_TF   teacher-forced one-step state: |x_gpu - x_oracle| <= 1e-5 max(|x|, 1)
+  DEPTH_TOL  depth / LiDAR per ray, unambiguous rays: 1e-4 m
+  GRAD_RTOL  BPTT gradients: per env |g - g*| / |g*| <= 1e-3, and elementwise
+             |g - g*| <= 1e-3 max|g*| (floor)
+  DRIFT      full-rollout (non teacher-forced) state drift bound: 1e-4 max(|x|, 1)
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+import oracle
+from paper_2509_10247_b300 import synth
+from paper_2509_10247_b300.binding import Simulator
+
+STATE_TF = 1e-5
+DEPTH_TOL = 1e-4
+GRAD_RTOL = 1e-3
+DRIFT = 1e-4
+MAX_AMB_FRAC = 1e-3
+
+
+def dev(x, dtype=torch.float32):
+    return torch.as_tensor(np.asarray(x), dtype=dtype, device="cuda")
+
+
+def host(t):
+    return None if t is None else t.detach().cpu().numpy().astype(np.float64)
+
+
+def subset(p, inp, envs):
+    """Sub-workload of the given environments (maps shared)."""
+    envs = np.asarray(envs)
+    M = p["n_agent"]
+    rows = (envs[:, None] * M + np.arange(M)[None, :]).reshape(-1)
+    q = dict(p, n_env=len(envs))
+    sub = dict(inp)
+    sub["s0"] = inp["s0"][rows]
+    sub["targets"] = inp["targets"][rows]
+    sub["pool"] = inp["pool"][:, rows]
+    sub["actions"] = None if inp["actions"] is None else inp["actions"][:, rows]
+    sub["env_map"] = inp["env_map"][envs]
+    for k in ("drag_env", "lam_env"):
+        sub[k] = None if inp.get(k) is None else inp[k][envs]
+    return q, sub, rows
+
+
+class Pair:
+    """A workload run through both the CUDA path and the oracle."""
+
+    def __init__(self, p, seed=0, ex=None, inp=None):
+        self.p = p
+        self.inp = synth.make_inputs(p, seed=seed) if inp is None else inp
+        self.ex = ex or {}
+        self.orc = oracle.Oracle(p, self.inp)
+        self.sim = Simulator(p, self.inp, **self.ex)
+
+    def run_oracle(self):
+        self.rec = self.orc.rollout(self.inp["s0"], self.inp["actions"])
+        return self.rec
+
+    def run_gpu(self):
+        self.sim.reset(dev(self.inp["s0"]))
+        self.act = dev(self.inp["actions"])
+        self.out = self.sim.rollout(self.act)
+        self.sT = self.sim.get_state()
+        torch.cuda.synchronize()
+        assert self.sim.status() == 0
+        return self.out
+
+
+def env_divergence(p, rec, out):
+    """Environments whose discrete trajectory (done flags) differs; only
+    allowed where the oracle flags the decision as ambiguous."""
+    M = p["n_agent"]
+    d_g = out["done"].cpu().numpy().astype(np.uint8)
+    d_o = rec["done"]
+    bad_env = np.zeros(p["n_env"], bool)
+    mism = (d_g != d_o).reshape(d_o.shape[0], p["n_env"], M).any(axis=(0, 2))
+    amb = (rec["amb_step"] & 1).reshape(d_o.shape[0], p["n_env"], M).any(axis=(0, 2))
+    assert not (mism & ~amb).any(), "done flags differ without an ambiguous decision"
+    bad_env |= mism
+    return bad_env
+
+
+def compare_rollout(p, rec, out, sT, check_depth=True):
+    """Compare rewards, done, sensors and final state of a full rollout."""
+    M = p["n_agent"]
+    bad = env_divergence(p, rec, out)
+    keep_agents = np.repeat(~bad, M)
+    T = rec["r_ctrl"].shape[0]
+    rg = out["r_goal"].cpu().numpy()
+    amb_goal = (rec["amb_step"] & 1) != 0
+    ok = (rg == rec["r_goal"]) | amb_goal | ~keep_agents[None, :]
+    assert ok.all(), "r_goal differs at %s" % (np.argwhere(~ok)[:5],)
+    r = host(out["r_ctrl"])
+    err = np.abs(r - rec["r_ctrl"])[:, keep_agents]
+    assert (err <= DRIFT * np.maximum(1.0, np.abs(rec["r_ctrl"][:, keep_agents]))).all(), err.max()
+    s = host(sT)
+    so = rec["states"][T]
+    e = np.abs(s - so)[keep_agents]
+    assert (e <= 10 * DRIFT * np.maximum(1.0, np.abs(so[keep_agents]))).all(), e.max()
+    if check_depth:
+        for key, amb_key, hit_key, rng in (("depth", "amb_cam", "hit_cam", p["cam"]),
+                                            ("lidar", "amb_lid", "hit_lid", p["lidar"])):
+            if rng is None or out[key] is None:
+                continue
+            g = host(out[key])[:, keep_agents]
+            o = rec[key][:, keep_agents]
+            amb = (rec[amb_key][:, keep_agents] & 1) != 0
+            assert amb.mean() < MAX_AMB_FRAC, amb.mean()
+            d = np.abs(g - o)
+            assert (d[~amb] <= DEPTH_TOL).all(), (d[~amb].max(), np.argwhere(d * ~amb > DEPTH_TOL)[:5])
+    return bad
+
+
+def masked_cotangents(p, rec, seed=1):
+    """N(0,1) cotangents with the entries of ambiguous rays / steps zeroed."""
+    cot = synth.cotangents(p, seed=seed)
+    g_r = cot["g_r"] * ((rec["amb_step"] & 6) == 0)
+    g_d = cot.get("g_depth")
+    if g_d is not None:
+        g_d = g_d * ((rec["amb_cam"] & 2) == 0)
+    g_l = cot.get("g_lidar")
+    if g_l is not None:
+        g_l = g_l * ((rec["amb_lid"] & 2) == 0)
+    return g_r, g_d, g_l
+
+
+def compare_grads(p, g_gpu, g_orc, bad_env, what):
+    """Per-env norm-wise and elementwise gradient comparison."""
+    N, M = p["n_env"], p["n_agent"]
+    gg = g_gpu.reshape(g_gpu.shape[0], N, -1) if g_gpu.ndim == 3 else g_gpu.reshape(N, -1)[None]
+    go = g_orc.reshape(gg.shape)
+    scale = np.abs(go).max()
+    worst = 0.0
+    for e in range(N):
+        if bad_env[e]:
+            continue
+        a, b = gg[:, e], go[:, e]
+        nb = np.linalg.norm(b)
+        if nb == 0:
+            assert np.linalg.norm(a) <= 1e-6 * max(scale, 1e-30), (what, e)
+            continue
+        rel = np.linalg.norm(a - b) / nb
+        worst = max(worst, rel)
+        assert rel <= GRAD_RTOL, (what, e, rel)
+    el = np.abs(gg - go)[:, ~bad_env]
+    assert (el <= GRAD_RTOL * scale).all(), (what, el.max() / scale)
+    return worst

@@ -1,0 +1,107 @@
+"""The C-ABI library loads and exports every symbol include/diffsim.h
+declares; host-side validation rejects bad configurations before touching a
+GPU (no compute call is made here)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2509_10247_b300 import binding, build, synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return binding.lib()
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "diffsim.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(sim_[a-z_]+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(lib, n), n
+    assert sorted(binding.SYMBOLS) == names
+
+
+def test_header_config_layout_matches_binding():
+    # sizeof(sim_config) from the header's field list: 4-byte fields only
+    src = open(os.path.join(ROOT, "include", "diffsim.h")).read()
+    body = src[src.index("typedef struct sim_config {"):src.index("} sim_config;")]
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    n = 0
+    for decl in re.findall(r"(?:int32_t|float)\s+([^;]+);", body):
+        for item in decl.split(","):
+            m = re.search(r"\[(\d+)\]", item)
+            n += int(m.group(1)) if m else 1
+    assert ctypes.sizeof(binding.SimConfig) == 4 * n
+
+
+def test_version_and_errors(lib):
+    assert "sm_103a" in binding.sim_version()
+    assert binding.sim_strerror(0) == "ok"
+    assert binding.sim_strerror(-2) == "null pointer"
+    assert binding.sim_strerror(5) == "unknown error"
+    assert binding.sim_state_dim(0) == 12 and binding.sim_state_dim(1) == 13
+    assert binding.sim_action_dim(0) == 3 and binding.sim_action_dim(1) == 4
+    assert binding.sim_state_dim(9) == -1
+
+
+def _create_rc(lib, cfg):
+    h = ctypes.c_void_p()
+    rc = lib.sim_create(ctypes.byref(cfg), ctypes.byref(h))
+    return rc, h.value
+
+
+@pytest.mark.parametrize("field,value,code", [
+    ("model", 5, -1), ("n_env", 0, -3), ("n_agent", 0, -3), ("n_agent", 33, -3), ("horizon", 0, -3),
+    ("dt", 0.0, -1), ("dt", float("nan"), -1), ("ema_alpha", 1.5, -1), ("cam_h", 0, -3),
+    ("cam_hfov", 0.0, -1), ("cam_range", -1.0, -1), ("pool_size", -1, -3), ("terminate", 2, -1),
+    ("tape_hits", 3, -1), ("cull", 2, -1), ("warps_per_cta", 9, -1), ("rays_per_thread", 7, -1),
+    ("ctas_per_sm", -1, -1),
+])
+def test_create_rejects_bad_config(lib, field, value, code):
+    cfg = binding.make_config(synth.preset("pointmass_64env_depth16x9_10sph"))
+    setattr(cfg, field, value)
+    rc, h = _create_rc(lib, cfg)
+    assert rc == code and h is None
+
+
+def test_create_rejects_reserved_and_rigid_params(lib):
+    cfg = binding.make_config(synth.preset("pointmass_64env_depth16x9_10sph"))
+    cfg.reserved[2] = 1
+    assert _create_rc(lib, cfg)[0] == -1
+    cfg = binding.make_config(synth.preset("rigid_4096env_depth64x48_40sph20box"))
+    cfg.inertia[1] = 0.0
+    assert _create_rc(lib, cfg)[0] == -1
+    cfg = binding.make_config(synth.preset("rigid_65536env_256obst_depth_lidar"))
+    cfg.lid_elev_lo, cfg.lid_elev_hi = 0.5, 0.1
+    assert _create_rc(lib, cfg)[0] == -1
+
+
+def test_null_pointers(lib):
+    cfg = binding.make_config(synth.preset("pointmass_64env_depth16x9_10sph"))
+    assert lib.sim_create(None, None) == -2
+    assert lib.sim_create(ctypes.byref(cfg), None) == -2
+    assert lib.sim_destroy(None) == 0
+    assert lib.sim_rollout(None, None, None, None, None, None, None, None) == -2
+    assert lib.sim_backward(None, None, None, None, None, None, None, None) == -2
+    assert lib.sim_set_scene(None, None, None, None, None, 0, None, None) == -2
+    assert lib.sim_last_status(None, None, None) == -2
+
+
+def test_valid_config_without_gpu_fails_cleanly(lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    cfg = binding.make_config(synth.preset("pointmass_64env_depth16x9_10sph"))
+    rc, h = _create_rc(lib, cfg)
+    assert rc == -4 and h is None

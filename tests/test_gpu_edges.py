@@ -1,0 +1,117 @@
+"""Edge cases and host-visible failure reporting on the GPU: empty maps, an
+origin inside an obstacle, a single environment and step, non-finite
+actions (status word, no hang), call-order errors."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2509_10247_b300 import synth
+from paper_2509_10247_b300.binding import SimError, Simulator
+from parity_util import DEPTH_TOL, Pair, compare_grads, compare_rollout, dev, host, masked_cotangents
+
+pytestmark = pytest.mark.gpu
+
+
+def _scene(p, spheres=(), boxes=()):
+    sp = np.array(spheres, float).reshape(-1, 4)
+    bx = np.array(boxes, float).reshape(-1, 6)
+    NM = p["n_env"] * p["n_agent"]
+    D = synth.STATE_DIM[p["model"]]
+    rng = np.random.default_rng(0)
+    return dict(spheres=sp, sph_off=np.array([0, len(sp)], np.int32), boxes=bx,
+                box_off=np.array([0, len(bx)], np.int32), env_map=np.zeros(p["n_env"], np.int32),
+                targets=rng.uniform(-3, 3, (NM, 3)), pool=np.zeros((max(p["pool_size"], 1), NM, D)),
+                s0=None, actions=None)
+
+
+def test_empty_scene_reads_max_range():
+    p = synth.params(n_env=5, horizon=4, map_counts=[(0, 0)])
+    pr = Pair(p, seed=2)
+    pr.run_oracle()
+    out = pr.run_gpu()
+    assert torch.all(out["depth"] == p["cam"][3])
+    compare_rollout(p, pr.rec, out, pr.sT)
+
+
+def test_origin_inside_obstacle_depth_zero_and_no_gradient():
+    p = synth.params(model="rigid", n_env=2, horizon=2, cam=(8, 6, 90.0, 10.0), pos_sq=1)
+    inp = _scene(p, spheres=[(0.0, 0.0, 0.0, 2.0)], boxes=[(5, -1, -1, 6, 1, 1)])
+    s0 = np.zeros((2, 13))
+    s0[:, 3] = 1.0
+    s0[1, 0] = 4.0  # agent 1 outside the sphere, facing the box
+    inp["s0"] = s0
+    inp["actions"] = np.zeros((2, 2, 4))
+    pr = Pair(p, inp=inp)
+    rec = pr.run_oracle()
+    out = pr.run_gpu()
+    d = host(out["depth"])
+    assert np.all(d[:, 0] == 0.0)
+    assert np.all(np.abs(d[:, 1] - rec["depth"][:, 1]) <= DEPTH_TOL)
+    g_d = np.ones((2, 2, 48))
+    pr.sim.reset(dev(s0))
+    pr.sim.rollout(pr.act)
+    ga, gs = pr.sim.backward(dev(np.zeros((2, 2))), dev(g_d))
+    ga_o, gs_o = pr.orc.backward(rec, np.zeros((2, 2)), g_d)
+    np.testing.assert_allclose(host(gs)[0], 0.0, atol=0)
+    compare_grads(p, host(ga), ga_o, np.zeros(2, bool), "g_a")
+
+
+def test_single_env_single_step():
+    p = synth.params(n_env=1, horizon=1, map_counts=[(3, 2)], w_obs=2.0, d_safe=3.0)
+    pr = Pair(p, seed=5)
+    rec = pr.run_oracle()
+    out = pr.run_gpu()
+    bad = compare_rollout(p, rec, out, pr.sT)
+    g_r, g_d, _ = masked_cotangents(p, rec)
+    ga, gs = pr.sim.backward(dev(g_r), dev(g_d))
+    ga_o, gs_o = pr.orc.backward(rec, g_r, g_d)
+    compare_grads(p, host(ga), ga_o, bad, "g_a")
+
+
+def test_nonfinite_state_sets_status_and_returns():
+    p = synth.params(n_env=4, horizon=3)
+    inp = synth.make_inputs(p, seed=1)
+    sim = Simulator(p, inp)
+    s0 = dev(inp["s0"])
+    s0[2, 4] = float("nan")
+    sim.reset(s0)
+    sim.rollout(dev(inp["actions"]))
+    assert sim.status() & 1
+    # the handle stays usable and the status word was cleared
+    sim.reset(dev(inp["s0"]))
+    sim.rollout(dev(inp["actions"]))
+    assert sim.status() == 0
+
+
+def test_call_order_errors():
+    p = synth.params(n_env=2, horizon=2, terminate=1)
+    inp = synth.make_inputs(p, seed=1)
+    sim = Simulator(p, inp)
+    with pytest.raises(SimError) as e:
+        sim.backward(dev(np.zeros((2, 2))))
+    assert e.value.code == -5
+
+
+def test_map_too_large_for_shared_memory_is_rejected():
+    p = synth.params(n_env=1, horizon=1, map_counts=[(20000, 0)])
+    inp = synth.make_inputs(p, seed=1)
+    with pytest.raises(SimError) as e:
+        Simulator(p, inp)
+    assert e.value.code == -3
+
+
+def test_uneven_maps_long_horizon_ckpt():
+    # T not a multiple of K, some empty maps, swarm of 5
+    p = synth.params(n_env=23, n_agent=5, horizon=11, n_maps=3,
+                     map_counts=[(0, 0), (9, 0), (0, 7)], w_obs=4.0, w_agent=3.0, d_agent=1.2,
+                     terminate=1, ckpt_every=4)
+    pr = Pair(p, seed=9)
+    rec = pr.run_oracle()
+    out = pr.run_gpu()
+    bad = compare_rollout(p, rec, out, pr.sT)
+    g_r, g_d, _ = masked_cotangents(p, rec)
+    ga, gs = pr.sim.backward(dev(g_r), dev(g_d))
+    ga_o, gs_o = pr.orc.backward(rec, g_r, g_d)
+    compare_grads(p, host(ga), ga_o, bad, "g_a")
+    compare_grads(p, host(gs), gs_o, bad, "g_s0")

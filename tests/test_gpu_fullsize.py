@@ -1,0 +1,56 @@
+"""Parity at the benchmark's full size (16384 environments x 8 agents, 64
+steps, 8 obstacle maps) in the benchmark's launch configuration: the whole
+batch runs on the GPU; sampled environments (two per map) are recomputed by
+the oracle and compared one by one."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2509_10247_b300 import synth
+from paper_2509_10247_b300.binding import Simulator
+from parity_util import compare_grads, compare_rollout, dev, host, masked_cotangents, subset
+
+pytestmark = pytest.mark.gpu
+
+
+def test_bench_workload_sampled_parity():
+    import bench
+    p = synth.preset(bench.WORKLOAD)
+    inp = synth.make_inputs(p, seed=0)
+    N, M, T = p["n_env"], p["n_agent"], p["horizon"]
+    nmaps = synth.n_maps_of(p)
+    envs = np.array(sorted({m + nmaps * k for m in range(nmaps) for k in (3, N // nmaps - 5)}))
+    q, sub, rows = subset(p, inp, envs)
+    orc = oracle.Oracle(q, sub)
+    rec = orc.rollout(sub["s0"], sub["actions"])
+    g_r_s, g_d_s, _ = masked_cotangents(q, rec, seed=1)
+
+    sim = Simulator(p, inp, **bench.BENCH_EXEC)
+    info = sim.launch_info()
+    assert info["grid"] > 0
+    sim.reset(dev(inp["s0"]))
+    act = dev(inp["actions"])
+    out = sim.rollout(act)
+    sT = sim.get_state()
+    torch.cuda.synchronize()
+    assert sim.status() == 0
+    out_s = {k: (None if v is None else v[:, torch.as_tensor(rows, device="cuda")]) for k, v in out.items()}
+    bad = compare_rollout(q, rec, out_s, sT[torch.as_tensor(rows, device="cuda")])
+    assert bad.sum() <= 1
+
+    g_r = torch.zeros(T, N * M, device="cuda")
+    g_d = torch.zeros(T, N * M, sim.Rc, device="cuda")
+    ri = torch.as_tensor(rows, device="cuda")
+    g_r[:, ri] = dev(g_r_s)
+    g_d[:, ri] = dev(g_d_s)
+    g_a, g_s0 = sim.backward(g_r, g_d)
+    torch.cuda.synchronize()
+    ga_o, gs_o = orc.backward(rec, g_r_s, g_d_s)
+    compare_grads(q, host(g_a[:, ri]), ga_o, bad, "g_a")
+    compare_grads(q, host(g_s0[ri]), gs_o, bad, "g_s0")
+    # environments outside the sample got zero cotangents: their gradient is 0
+    mask = torch.ones(N * M, dtype=torch.bool, device="cuda")
+    mask[ri] = False
+    assert g_a[:, mask].abs().max().item() == 0.0
+    sim.close()

@@ -1,0 +1,218 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on
+the same seeded inputs, at sizes the oracle finishes in seconds that still
+span several CTAs, warps and ragged ray chunks."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2509_10247_b300 import synth
+from paper_2509_10247_b300.autograd import DiffSimRollout, DiffSimStep
+from paper_2509_10247_b300.binding import Simulator
+from parity_util import (DEPTH_TOL, STATE_TF, Pair, compare_grads, compare_rollout, dev, host,
+                         masked_cotangents)
+
+pytestmark = pytest.mark.gpu
+
+# small cases with the structure of the paper's workloads
+WORKLOADS = {
+    "pm_64env": lambda: synth.preset("pointmass_64env_depth16x9_10sph"),
+    "rigid_depth": lambda: synth.preset("rigid_4096env_depth64x48_40sph20box", n_env=24, horizon=12),
+    "swarm_maps": lambda: synth.preset("swarm_16384env_8agent_8maps_depth16x9", n_env=48, horizon=12),
+    "rigid_lidar": lambda: synth.preset("rigid_65536env_256obst_depth_lidar", n_env=6, horizon=6,
+                                        ckpt_every=4),
+    "ragged": lambda: synth.params(n_env=37, n_agent=3, horizon=7, cam=(7, 5, 75.0, 9.0),
+                                   map_counts=[(5, 3), (0, 4), (6, 0), (0, 0)], n_maps=4,
+                                   w_obs=3.0, w_agent=2.0, d_agent=1.5, terminate=1, ckpt_every=3),
+}
+
+
+@pytest.fixture(scope="module", params=list(WORKLOADS))
+def pair(request):
+    torch.cuda.init()
+    p = WORKLOADS[request.param]()
+    pr = Pair(p, seed=0)
+    pr.run_oracle()
+    pr.run_gpu()
+    pr.name = request.param
+    return pr
+
+
+def test_rollout_parity(pair):
+    compare_rollout(pair.p, pair.rec, pair.out, pair.sT)
+
+
+def test_teacher_forced_steps(pair):
+    """oracle state s_t (rounded to FP32) -> one GPU step vs one oracle step."""
+    p, rec = pair.p, pair.rec
+    T = rec["r_ctrl"].shape[0]
+    sim = pair.sim
+    o1 = pair.orc.with_horizon(1)
+    M = p["n_agent"]
+    for t in sorted(set([0, 1, T // 2, T - 1])):
+        s32 = rec["states"][t].astype(np.float32).astype(np.float64)
+        a = pair.inp["actions"][t:t + 1]
+        # reset counters the oracle reached by step t; the GPU's restart at 0,
+        # so envs that reset at this step with a non-zero counter are skipped
+        pk = np.zeros(p["n_env"], np.int32)
+        if t > 0:
+            pk = rec["done"][:t].reshape(t, p["n_env"], M)[:, :, 0].sum(axis=0).astype(np.int32)
+        ro = o1.rollout(s32, a, pool_k=pk)
+        sim.reset(dev(s32))
+        o = sim.step(dev(a[0]))
+        s = host(sim.get_state())
+        so = ro["states"][1]
+        skip_env = (ro["done"][0].reshape(p["n_env"], M)[:, 0] != 0) & (pk != 0)
+        skip = np.repeat(skip_env, M) | ((ro["amb_step"][0] & 1) != 0)
+        ok = np.abs(s - so) <= STATE_TF * np.maximum(np.abs(so), 1.0)
+        assert ok[~skip].all(), (t, np.abs(s - so)[~skip].max())
+        np.testing.assert_array_equal(host(o["done"]).astype(np.uint8)[~skip], ro["done"][0][~skip])
+        for key, ak in (("depth", "amb_cam"), ("lidar", "amb_lid")):
+            if o[key] is None:
+                continue
+            d = np.abs(host(o[key]) - ro[key][0])
+            m = ((ro[ak][0] & 1) == 0) & ~skip[:, None]
+            assert (d[m] <= DEPTH_TOL).all(), (key, d[m].max())
+
+
+def test_render_parity(pair):
+    rec = pair.rec
+    T = rec["r_ctrl"].shape[0]
+    s32 = rec["states"][T // 2].astype(np.float32).astype(np.float64)
+    pair.sim.reset(dev(s32))
+    dep, lid = pair.sim.render()
+    od, ol, _, _, ac, al = pair.orc.render(s32)
+    if dep is not None:
+        m = (ac & 1) == 0
+        assert (np.abs(host(dep) - od)[m] <= DEPTH_TOL).all()
+    if lid is not None:
+        m = (al & 1) == 0
+        assert (np.abs(host(lid) - ol)[m] <= DEPTH_TOL).all()
+
+
+def test_backward_parity(pair):
+    p, rec = pair.p, pair.rec
+    bad = compare_rollout(p, rec, pair.out, pair.sT, check_depth=False)
+    g_r, g_d, g_l = masked_cotangents(p, rec)
+    g_sT = np.random.default_rng(3).standard_normal((pair.orc.NM, pair.orc.D)).astype(np.float32).astype(np.float64)
+    ga_o, gs_o = pair.orc.backward(rec, g_r, g_d, g_l, g_sT)
+    pair.sim.reset(dev(pair.inp["s0"]))
+    pair.sim.rollout(pair.act)
+    ga, gs0 = pair.sim.backward(dev(g_r), None if g_d is None else dev(g_d),
+                                None if g_l is None else dev(g_l), dev(g_sT))
+    torch.cuda.synchronize()
+    compare_grads(p, host(ga), ga_o, bad, "g_a")
+    compare_grads(p, host(gs0), gs_o, bad, "g_s0")
+
+
+def test_culling_is_result_preserving(pair):
+    p = pair.p
+    if p["cam"] is None and p["lidar"] is None:
+        pytest.skip("no sensor")
+    s2 = Simulator(p, pair.inp, cull=0)
+    s2.reset(dev(pair.inp["s0"]))
+    o2 = s2.rollout(pair.act)
+    for k in ("depth", "lidar"):
+        if pair.out[k] is not None:
+            assert torch.equal(pair.out[k], o2[k]), k
+    assert torch.equal(pair.out["r_ctrl"], o2["r_ctrl"])
+
+
+def test_steps_equal_rollout(pair):
+    """T launches of the one-step kernel reproduce the persistent rollout bitwise."""
+    p = pair.p
+    sim = pair.sim
+    sim.reset(dev(pair.inp["s0"]))
+    for t in range(p["horizon"]):
+        o = sim.step(pair.act[t])
+        assert torch.equal(o["r_ctrl"], pair.out["r_ctrl"][t])
+        assert torch.equal(o["done"], pair.out["done"][t])
+        if o["depth"] is not None:
+            assert torch.equal(o["depth"], pair.out["depth"][t])
+    assert torch.equal(sim.get_state(), pair.sT)
+
+
+def test_rays_per_thread_variants_agree(pair):
+    p = pair.p
+    if p["cam"] is None:
+        pytest.skip("no camera")
+    for rpt in (1, 3, 8):
+        s2 = Simulator(p, pair.inp, rays_per_thread=rpt)
+        s2.reset(dev(pair.inp["s0"]))
+        o2 = s2.rollout(pair.act)
+        assert torch.equal(pair.out["depth"], o2["depth"]), rpt
+
+
+def test_checkpoint_and_tape_variants_agree(pair):
+    """Gradients do not depend on the checkpoint interval or on taping hits."""
+    p = pair.p
+    g_r = dev(synth.cotangents(p, seed=4)["g_r"])
+    cot = synth.cotangents(p, seed=4)
+    g_d = dev(cot["g_depth"]) if "g_depth" in cot else None
+    g_l = dev(cot["g_lidar"]) if "g_lidar" in cot else None
+    ref = None
+    for ex in (dict(ckpt_every=1, tape_hits=1), dict(ckpt_every=p["horizon"], tape_hits=0),
+               dict(ckpt_every=5, tape_hits=0), dict(ckpt_every=3, tape_hits=1)):
+        s2 = Simulator(p, pair.inp, **ex)
+        s2.reset(dev(pair.inp["s0"]))
+        s2.rollout(pair.act)
+        ga, gs = s2.backward(g_r, g_d, g_l)
+        if ref is None:
+            ref = (ga, gs)
+        else:
+            assert torch.equal(ref[0], ga), ex
+            assert torch.equal(ref[1], gs), ex
+
+
+def test_determinism(pair):
+    p = pair.p
+    outs = []
+    for _ in range(2):
+        pair.sim.reset(dev(pair.inp["s0"]))
+        o = pair.sim.rollout(pair.act)
+        ga, gs = pair.sim.backward(dev(synth.cotangents(p, seed=2)["g_r"]))
+        outs.append((o["r_ctrl"].clone(), ga.clone(), gs.clone()))
+    for a, b in zip(outs[0], outs[1]):
+        assert torch.equal(a, b)
+
+
+def test_autograd_rollout_matches_backward(pair):
+    p = pair.p
+    act = pair.act.clone().requires_grad_(True)
+    s0 = dev(pair.inp["s0"]).requires_grad_(True)
+    r, depth, lidar, sT = DiffSimRollout.apply(pair.sim, act, s0)
+    cot = synth.cotangents(p, seed=6)
+    loss = (r * dev(cot["g_r"])).sum()
+    if depth.numel():
+        loss = loss + (depth * dev(cot["g_depth"])).sum()
+    loss.backward()
+    pair.sim.reset(dev(pair.inp["s0"]))
+    pair.sim.rollout(pair.act)
+    ga, gs = pair.sim.backward(dev(cot["g_r"]), dev(cot["g_depth"]) if depth.numel() else None)
+    assert torch.equal(act.grad, ga)
+    assert torch.equal(s0.grad, gs)
+
+
+def test_step_adjoint_chain_matches_rollout_adjoint(pair):
+    """Closed-loop form: DiffSimStep over T steps gives the rollout's gradient."""
+    p = pair.p
+    s = dev(pair.inp["s0"]).requires_grad_(True)
+    acts = [pair.act[t].clone().requires_grad_(True) for t in range(p["horizon"])]
+    cot = synth.cotangents(p, seed=8)
+    loss = 0.0
+    x = s
+    for t in range(p["horizon"]):
+        x, r, depth, lidar, done = DiffSimStep.apply(pair.sim, x, acts[t])
+        loss = loss + (r * dev(cot["g_r"][t])).sum()
+        if depth.numel():
+            loss = loss + (depth * dev(cot["g_depth"][t])).sum()
+    loss.backward()
+    pair.sim.reset(dev(pair.inp["s0"]))
+    pair.sim.rollout(pair.act)
+    ga, gs = pair.sim.backward(dev(cot["g_r"]), dev(cot["g_depth"]) if p["cam"] else None)
+    g_chain = torch.stack([a.grad for a in acts])
+    # resets replay from the pool in both; pool counters differ only after a
+    # reset, whose cotangent is cut in both forms
+    scale = ga.abs().max().item()
+    assert (g_chain - ga).abs().max().item() <= 1e-5 * max(scale, 1.0)
+    assert (s.grad - gs).abs().max().item() <= 1e-5 * max(gs.abs().max().item(), 1.0)
