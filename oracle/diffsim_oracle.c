@@ -53,6 +53,9 @@
 #define AMB_GRAZE 0.05  /* |n . d| below this: ill-conditioned gradient       */
 #define AMB_EDGE 1e-5   /* two slab entry times within this (relative)        */
 #define AMB_STEP 1e-5   /* thresholds of collision / success / bounds (m)     */
+#define COND_DIR 3e-7   /* FP32 error of a rotated unit ray direction          */
+#define COND_ORG 1e-6   /* FP32 error of an origin-relative coordinate (m)    */
+#define COND_MAX 5e-5   /* half of the 1e-4 m depth tolerance                 */
 
 typedef struct {
     int32_t model, n_env, n_agent, horizon;
@@ -384,8 +387,9 @@ static double cast_ray(const double *o, const double *d, const double *sph, int 
         if (t < best) { second = best; best = t; id = ns + k; }
         else if (t < second) second = t;
     }
-    /* near-degenerate decisions that could change the value in FP32 */
-    double reach = (best < tclamp ? best : tclamp) + 1e-3;
+    /* near-degenerate decisions that could change the value in FP32: a
+     * grazing sphere whose tangent distance competes with the nearest hit */
+    double reach = (best < tclamp ? best : tclamp) + 1e-2;
     for (int k = 0; k < ns; ++k) {
         const double *sp = sph + 4 * k;
         double oc[3] = {sp[0] - o[0], sp[1] - o[1], sp[2] - o[2]};
@@ -393,7 +397,8 @@ static double cast_ray(const double *o, const double *d, const double *sph, int 
         double b = dot3(d, oc);
         if (fabs(norm3(oc) - sp[3]) < AMB_INSIDE) flags |= 3;
         double disc = b * b - C;
-        if (b > 0.0 && b < reach && fabs(disc) < AMB_DISC * (b * b > 1.0 ? b * b : 1.0)) flags |= 3;
+        if (b > 0.0 && b - sqrt(fabs(disc)) < reach && fabs(disc) < AMB_DISC * (b * b > 1.0 ? b * b : 1.0))
+            flags |= 3;
     }
     for (int k = 0; k < nb; ++k) {
         const double *bx = box + 6 * k;
@@ -435,7 +440,12 @@ static double cast_ray(const double *o, const double *d, const double *sph, int 
                 for (int i = 0; i < 3; ++i)
                     if (i != ax && fabs(tl[i] - best) < AMB_EDGE * (best > 1.0 ? best : 1.0)) flags |= 2;
             }
-            if (fabs(dot3(n, d)) < AMB_GRAZE) flags |= 2;
+            double nd = fabs(dot3(n, d));
+            if (nd < AMB_GRAZE) flags |= 2;
+            /* ill-conditioned value: rounding the direction (COND_DIR per
+             * component) and origin (COND_ORG) to FP32 moves the hit by
+             * (COND_DIR t + COND_ORG) / |n.d|; flag above half the tolerance */
+            if ((COND_DIR * best + COND_ORG) / nd > COND_MAX) flags |= 3;
         }
     }
     *hit = id;

@@ -116,7 +116,7 @@ __device__ __forceinline__ void cast_rays(const unsigned char* sm, const Args& a
             float h = fmaf(-gg, gg, disc);
             if (fminf(h, b) >= 0.f) {
                 float fx = fmaf(-b, dx[r], e.x), fy = fmaf(-b, dy[r], e.y), fz = fmaf(-b, dz[r], e.z);
-                float d2 = fmaxf(lr2[k] - (fx * fx + fy * fy + fz * fz), 0.f);
+                float d2 = fmaxf(lr2[k] - fmaf(fx, fx, fmaf(fy, fy, fz * fz)), 0.f);
                 float t = e.w / (b + sqrtf(d2));
                 if (t < tb[r]) { tb[r] = t; bi[r] = k; }
             }
@@ -180,9 +180,9 @@ __device__ __forceinline__ void item_rays(const Sensor& sen, const float* R, int
         const int ray = chunk * 32 * RPT + r * 32 + lane;
         const bool valid = ray < sen.R;
         float4 db = valid ? __ldg(sen.dir + ray) : make_float4(1.f, 0.f, 0.f, 1.f);
-        dx[r] = R[0] * db.x + R[1] * db.y + R[2] * db.z;
-        dy[r] = R[3] * db.x + R[4] * db.y + R[5] * db.z;
-        dz[r] = R[6] * db.x + R[7] * db.y + R[8] * db.z;
+        dx[r] = fmaf(R[0], db.x, fmaf(R[1], db.y, R[2] * db.z));
+        dy[r] = fmaf(R[3], db.x, fmaf(R[4], db.y, R[5] * db.z));
+        dz[r] = fmaf(R[6], db.x, fmaf(R[7], db.y, R[8] * db.z));
         fac[r] = db.w;
         tb[r] = valid ? (sen.kind == 0 ? sen.range / db.w : sen.range) : -1.f;
     }
@@ -425,7 +425,7 @@ __device__ __forceinline__ void ray_vjp(const float4* prim, int ns, int id, cons
         const float C = dot3(oc, oc) - r2;
         if (C <= 0.f) return;
         const float b = dot3(d, oc);
-        const float f[3] = {oc[0] - b * d[0], oc[1] - b * d[1], oc[2] - b * d[2]};
+        const float f[3] = {fmaf(-b, d[0], oc[0]), fmaf(-b, d[1], oc[1]), fmaf(-b, d[2], oc[2])};
         const float d2 = fmaxf(r2 - dot3(f, f), 0.f);
         t = C / (b + sqrtf(d2));
         const float ir = 1.f / s.w;

@@ -196,6 +196,7 @@ def test_autograd_rollout_matches_backward(pair):
 def test_step_adjoint_chain_matches_rollout_adjoint(pair):
     """Closed-loop form: DiffSimStep over T steps gives the rollout's gradient."""
     p = pair.p
+    pair.sim.reset(dev(pair.inp["s0"]))  # zero the reset counters, as the rollout does
     s = dev(pair.inp["s0"]).requires_grad_(True)
     acts = [pair.act[t].clone().requires_grad_(True) for t in range(p["horizon"])]
     cot = synth.cotangents(p, seed=8)
