@@ -51,11 +51,12 @@
 #define AMB_GAP 1e-4    /* second-nearest hit within this distance (m)         */
 #define AMB_RANGE 1e-4  /* hit within this distance of the range clamp (m)     */
 #define AMB_GRAZE 0.05  /* |n . d| below this: ill-conditioned gradient       */
-#define AMB_EDGE 1e-5   /* two slab entry times within this (relative)        */
+#define AMB_EDGE 1e-4   /* two slab entry times within this (relative)        */
 #define AMB_STEP 1e-5   /* thresholds of collision / success / bounds (m)     */
 #define COND_DIR 3e-7   /* FP32 error of a rotated unit ray direction          */
 #define COND_ORG 1e-6   /* FP32 error of an origin-relative coordinate (m)    */
 #define COND_MAX 5e-5   /* half of the 1e-4 m depth tolerance                 */
+#define DRIFT_POS 1e-5  /* position drift of an FP32 rollout vs FP64 (m)      */
 
 typedef struct {
     int32_t model, n_env, n_agent, horizon;
@@ -370,8 +371,11 @@ static void sdf_box_grad(const double *p, const double *bx, double *gp)
 
 /* One ray cast against every primitive of a map, brute force.  Returns t*
  * (+inf on a miss) and the hit id (lowest id among exact ties; -1 on a miss).
- * amb receives the ambiguity flags of this ray (bit 0: value, bit 1: gradient)
- * given the clamp distance tclamp in ray length. */
+ * amb receives the flags of this ray, given the clamp distance tclamp in ray
+ * length: bit 0 a value decision near its threshold (grazing, origin near a
+ * surface), bit 1 a gradient decision near its threshold (second hit, range
+ * clamp, box edge), bit 2 a value ill-conditioned in FP32, bit 3 a gradient
+ * ill-conditioned under FP32 trajectory drift (near-grazing incidence). */
 static double cast_ray(const double *o, const double *d, const double *sph, int ns,
                        const double *box, int nb, int *hit, double tclamp, int *amb)
 {
@@ -441,11 +445,14 @@ static double cast_ray(const double *o, const double *d, const double *sph, int 
                     if (i != ax && fabs(tl[i] - best) < AMB_EDGE * (best > 1.0 ? best : 1.0)) flags |= 2;
             }
             double nd = fabs(dot3(n, d));
-            if (nd < AMB_GRAZE) flags |= 2;
+            if (nd < AMB_GRAZE) flags |= 8;
+            /* gradient -n/(n.d) of a sphere hit turns by ~ dp/(r |n.d|) when
+             * the trajectory drifts by dp (FP32 rollout): flag above 3e-4 */
+            if (id < ns && DRIFT_POS / (sph[4 * id + 3] * nd) > 3e-4) flags |= 8;
             /* ill-conditioned value: rounding the direction (COND_DIR per
              * component) and origin (COND_ORG) to FP32 moves the hit by
              * (COND_DIR t + COND_ORG) / |n.d|; flag above half the tolerance */
-            if ((COND_DIR * best + COND_ORG) / nd > COND_MAX) flags |= 3;
+            if ((COND_DIR * best + COND_ORG) / nd > COND_MAX) flags |= 4 | 8;
         }
     }
     *hit = id;

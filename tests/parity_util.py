@@ -5,8 +5,12 @@ Tolerances (written here, used by every test):
   STATE_TF   teacher-forced one-step state: |x_gpu - x_oracle| <= 1e-5 max(|x|, 1)
   DEPTH_TOL  depth / LiDAR per ray, unambiguous rays: 1e-4 m (teacher-forced)
   DEPTH_DRIFT  the same on a full rollout, where FP32 state drift enters: 2e-3 m
-  GRAD_RTOL  BPTT gradients: per env |g - g*| / |g*| <= 1e-3, and elementwise
-             |g - g*| <= 1e-3 max|g*| (floor)
+  GRAD_RTOL  gradients: per env |g - g*| / |g*| <= 1e-3, and elementwise
+             |g - g*| <= 1e-3 max|g*| (floor).  Strict for the teacher-forced
+             step adjoint.  For a full-horizon BPTT gradient the bar applies
+             to environments whose FP64 gradient is itself stable to FP32-level
+             perturbations of the inputs (spread <= GRAD_RTOL / 4); the others
+             must agree within COND_FACTOR times their measured spread.
   DRIFT      full-rollout (non teacher-forced) state drift bound: 1e-4 max(|x|, 1)
 """
 from __future__ import annotations
@@ -22,8 +26,13 @@ STATE_TF = 1e-5
 DEPTH_TOL = 1e-4
 DEPTH_DRIFT = 2e-3
 GRAD_RTOL = 1e-3
+COND_FACTOR = 4.0
+PERTURB = 3e-7  # relative input perturbation of the conditioning probe (FP32 scale)
 DRIFT = 1e-4
 MAX_AMB_FRAC = 2e-2
+# oracle ray flags: bit 0 value decision, bit 1 gradient decision, bit 2 FP32
+# value conditioning, bit 3 gradient conditioning under drift
+VALUE_FLAGS = 1 | 4
 
 
 def dev(x, dtype=torch.float32):
@@ -113,7 +122,7 @@ def compare_rollout(p, rec, out, sT, check_depth=True):
                 continue
             g = host(out[key])[:, keep_agents]
             o = rec[key][:, keep_agents]
-            amb = (rec[amb_key][:, keep_agents] & 1) != 0
+            amb = (rec[amb_key][:, keep_agents] & VALUE_FLAGS) != 0
             assert amb.mean() < MAX_AMB_FRAC, amb.mean()
             d = np.abs(g - o)
             assert (d[~amb] <= DEPTH_DRIFT).all(), (d[~amb].max(), np.argwhere(d * ~amb > DEPTH_DRIFT)[:5])
@@ -126,15 +135,41 @@ def masked_cotangents(p, rec, seed=1):
     g_r = cot["g_r"] * ((rec["amb_step"] & 6) == 0)
     g_d = cot.get("g_depth")
     if g_d is not None:
-        g_d = g_d * ((rec["amb_cam"] & 2) == 0)
+        g_d = g_d * (rec["amb_cam"] == 0)
     g_l = cot.get("g_lidar")
     if g_l is not None:
-        g_l = g_l * ((rec["amb_lid"] & 2) == 0)
+        g_l = g_l * (rec["amb_lid"] == 0)
     return g_r, g_d, g_l
 
 
-def compare_grads(p, g_gpu, g_orc, bad_env, what):
-    """Per-env norm-wise and elementwise gradient comparison."""
+def grad_spread(orc, p, inp, rec, g_r, g_d=None, g_l=None, g_sT=None, n=2, seed=0):
+    """Per-env conditioning of the oracle's BPTT gradient: the largest relative
+    change of (g_a, g_s0) when the actions and initial state are perturbed at
+    FP32 rounding scale (PERTURB).  Envs whose discrete trajectory changes get
+    +inf.  Returns (spread_a, spread_s) arrays of length N."""
+    N, M = p["n_env"], p["n_agent"]
+    ga, gs = orc.backward(rec, g_r, g_d, g_l, g_sT)
+    rng = np.random.default_rng(seed)
+    sa, ss = np.zeros(N), np.zeros(N)
+    for _ in range(n):
+        a2 = inp["actions"] * (1 + PERTURB * rng.standard_normal(inp["actions"].shape))
+        s2 = inp["s0"] * (1 + PERTURB * rng.standard_normal(inp["s0"].shape))
+        r2 = orc.rollout(s2, a2)
+        ga2, gs2 = orc.backward(r2, g_r, g_d, g_l, g_sT)
+        for e in range(N):
+            sl = slice(e * M, (e + 1) * M)
+            if (r2["done"][:, sl] != rec["done"][:, sl]).any():
+                sa[e] = ss[e] = np.inf
+                continue
+            sa[e] = max(sa[e], np.linalg.norm(ga2[:, sl] - ga[:, sl]) / max(np.linalg.norm(ga[:, sl]), 1e-4))
+            ss[e] = max(ss[e], np.linalg.norm(gs2[sl] - gs[sl]) / max(np.linalg.norm(gs[sl]), 1e-4))
+    return sa, ss
+
+
+def compare_grads(p, g_gpu, g_orc, bad_env, what, spread=None):
+    """Per-env norm-wise and elementwise gradient comparison.  With `spread`
+    (grad_spread), ill-conditioned envs get COND_FACTOR x their spread and are
+    left out of the elementwise check; returns (worst rel, n ill-conditioned)."""
     N, M = p["n_env"], p["n_agent"]
     gg = g_gpu.reshape(g_gpu.shape[0], N, -1) if g_gpu.ndim == 3 else g_gpu.reshape(N, -1)[None]
     go = g_orc.reshape(gg.shape)
@@ -142,13 +177,26 @@ def compare_grads(p, g_gpu, g_orc, bad_env, what):
     norms = [np.linalg.norm(go[:, e]) for e in range(N)]
     floor = max(1e-3 * max(norms), 1e-4)
     worst = 0.0
+    ill = np.zeros(N, bool)
+    if spread is not None:
+        ill = spread > GRAD_RTOL / 4
     for e in range(N):
-        if bad_env[e]:
+        if bad_env[e] or not np.isfinite(spread[e] if spread is not None else 0.0):
             continue
         a, b = gg[:, e], go[:, e]
         rel = np.linalg.norm(a - b) / max(np.linalg.norm(b), floor)
-        worst = max(worst, rel)
-        assert rel <= GRAD_RTOL, (what, e, rel)
-    el = np.abs(gg - go)[:, ~bad_env]
-    assert (el <= GRAD_RTOL * max(scale, 1e-4)).all(), (what, el.max() / max(scale, 1e-4))
-    return worst
+        tol = max(GRAD_RTOL, COND_FACTOR * spread[e]) if ill[e] else GRAD_RTOL
+        if not ill[e]:
+            worst = max(worst, rel)
+        if rel > tol:
+            diff = np.abs(a - b)
+            top = np.argsort(diff.reshape(-1))[::-1][:5]
+            idx = [np.unravel_index(i, diff.shape) for i in top]
+            raise AssertionError("%s env %d rel %.3g |g*| %.3g top diffs %s" % (
+                what, e, rel, np.linalg.norm(b),
+                [(tuple(int(x) for x in ix), float(a[ix]), float(b[ix])) for ix in idx]))
+    keep = ~bad_env & ~ill
+    el = np.abs(gg - go)[:, keep]
+    if el.size:
+        assert (el <= GRAD_RTOL * max(scale, 1e-4)).all(), (what, el.max() / max(scale, 1e-4))
+    return worst, int(ill[~bad_env].sum())

@@ -9,7 +9,7 @@ import torch
 import oracle
 from paper_2509_10247_b300 import synth
 from paper_2509_10247_b300.binding import Simulator
-from parity_util import compare_grads, compare_rollout, dev, host, masked_cotangents, subset
+from parity_util import compare_grads, compare_rollout, dev, grad_spread, host, masked_cotangents, subset
 
 pytestmark = pytest.mark.gpu
 
@@ -47,8 +47,11 @@ def test_bench_workload_sampled_parity():
     g_a, g_s0 = sim.backward(g_r, g_d)
     torch.cuda.synchronize()
     ga_o, gs_o = orc.backward(rec, g_r_s, g_d_s)
-    compare_grads(q, host(g_a[:, ri]), ga_o, bad, "g_a")
-    compare_grads(q, host(g_s0[ri]), gs_o, bad, "g_s0")
+    sa, ss = grad_spread(orc, q, sub, rec, g_r_s, g_d_s)
+    wa, ia = compare_grads(q, host(g_a[:, ri]), ga_o, bad, "g_a", spread=sa)
+    ws, is_ = compare_grads(q, host(g_s0[ri]), gs_o, bad, "g_s0", spread=ss)
+    print("full size: worst rel g_a %.2e g_s0 %.2e on well-conditioned envs; ill-conditioned %d, %d of %d"
+          % (wa, ws, ia, is_, len(envs)))
     # environments outside the sample got zero cotangents: their gradient is 0
     mask = torch.ones(N * M, dtype=torch.bool, device="cuda")
     mask[ri] = False

@@ -19,7 +19,10 @@ def _fd_check(p, s0, seed=5, rtol=1e-6, min_depth_hits=1):
     o = oracle.Oracle(p, inp)
     act = inp["actions"]
     rec = o.rollout(s0, act)
-    assert (rec["amb_cam"] == 0).all() and (rec["amb_lid"] == 0).all() and (rec["amb_step"] == 0).all()
+    # no decision within reach of the finite-difference step (bits 0, 1);
+    # FP32 conditioning flags (bits 2, 3) do not concern an FP64 check
+    assert ((rec["amb_cam"] & 3) == 0).all() and ((rec["amb_lid"] & 3) == 0).all()
+    assert (rec["amb_step"] == 0).all()
     if p["cam"] is not None:
         assert (rec["hit_cam"] >= 0).sum() >= min_depth_hits
     cot = synth.cotangents(p, seed=seed + 1)
@@ -108,7 +111,7 @@ def test_adjoint_with_resets():
         rec = o.rollout(s0, inp["actions"])
         if rec["done"].sum() == 0 or rec["done"][-1].any():
             continue
-        if (rec["amb_cam"] != 0).any() or (rec["amb_step"] != 0).any():
+        if (rec["amb_cam"] & 3).any() or (rec["amb_step"] != 0).any():
             continue
         _fd_check(p, s0, seed=seed)
         return
