@@ -209,6 +209,40 @@ int sim_last_status(sim_handle *h, int32_t *status, int32_t *per_env);
  * last stream.  reset != 0 zeroes the counters after reading. */
 int sim_counters(sim_handle *h, uint64_t *out, int32_t reset);
 
+/* Bytes of the library's static device scratch used by sim_step_static. */
+#define SIM_STATIC_SCRATCH_BYTES (256 * 1024)
+
+/* sim_step_static: one step, like sim_step, that allocates no device memory.
+ * The paper has no counterpart; this entry point exists for callers that
+ * cannot call cudaMalloc (code that must draw all device memory from a pool
+ * or arena owned by someone else, or that has fixed its allocations up
+ * front): they pass every buffer, and the step's scratch (work ticket,
+ * status word, counters, camera / LiDAR ray tables) lives in one static
+ * device array of SIM_STATIC_SCRATCH_BYTES that every GPU which loads the
+ * library holds until the process exits.  Limit: 16 * (Rc + Rl) + 64 bytes
+ * must fit in it (at most 16380 rays per agent), else SIM_ERR_SIZE.
+ *   cfg      simulation parameters (HOST); execution fields warps_per_cta,
+ *            rays_per_thread and cull are honoured, the others ignored
+ *   prims    DEVICE, the scene in the library's layout: per map a block of
+ *            float4, map_ns[m] spheres (cx, cy, cz, r) followed by map_nb[m]
+ *            boxes as (min x, y, z, 0), (max x, y, z, 0); 16-byte aligned
+ *   map_off, map_ns, map_nb  DEVICE [n_maps]: block start (in float4),
+ *            sphere and box counts; ns_max, nb_max: their maxima (HOST ints)
+ *   env_map [N], targets [NM][3], pool [P][NM][D] (NULL: no reset)  DEVICE
+ *   state    DEVICE [NM][D], read and overwritten with the next state
+ *   actions  DEVICE [NM][A]; outputs depth, lidar, r_ctrl, r_goal, done as
+ *            in sim_step (any may be NULL); pool_k DEVICE [N] reset counters
+ *            (read and advanced; NULL: entry 0 and no counting)
+ * The first call on a device looks up the scratch address on that device;
+ * make it before any stream capture.  Every call rewrites the scratch, so
+ * calls that overlap on the GPU (other streams, other threads) race; order
+ * them on one stream.  Returns SIM_OK or a SIM_ERR_* code. */
+int sim_step_static(const sim_config *cfg, const float *prims, const int32_t *map_off,
+                    const int32_t *map_ns, const int32_t *map_nb, int32_t ns_max, int32_t nb_max,
+                    const int32_t *env_map, const float *targets, const float *pool, float *state,
+                    const float *actions, float *depth, float *lidar, float *r_ctrl,
+                    int8_t *r_goal, uint8_t *done, int32_t *pool_k, sim_stream_t stream);
+
 /* Launch shape chosen for this handle: warps per CTA, rays per thread,
  * grid size of the rollout kernel and its dynamic shared memory (bytes). */
 int sim_launch_info(const sim_handle *h, int32_t *warps_per_cta, int32_t *rays_per_thread,

@@ -33,7 +33,7 @@ SYMBOLS = ["sim_version", "sim_strerror", "sim_state_dim", "sim_action_dim", "si
            "sim_destroy", "sim_workspace_bytes", "sim_set_scene", "sim_set_pool",
            "sim_set_env_params", "sim_reset", "sim_get_state", "sim_set_state", "sim_render",
            "sim_step", "sim_rollout", "sim_backward", "sim_step_backward", "sim_last_status",
-           "sim_launch_info", "sim_counters"]
+           "sim_launch_info", "sim_counters", "sim_step_static"]
 
 
 class SimError(RuntimeError):
@@ -249,6 +249,17 @@ def sim_launch_info(h):
     w, r, g, s = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32()
     _ck(lib().sim_launch_info(h, C.byref(w), C.byref(r), C.byref(g), C.byref(s)), "sim_launch_info")
     return dict(warps_per_cta=w.value, rays_per_thread=r.value, grid=g.value, smem_bytes=s.value)
+
+
+def sim_step_static(cfg, prims, map_off, map_ns, map_nb, ns_max, nb_max, env_map, targets, pool,
+                    state, actions, depth=None, lidar=None, r_ctrl=None, r_goal=None, done=None,
+                    pool_k=None, stream=None):
+    """One step without any device allocation by the library (all buffers are
+    the caller's device tensors; see include/diffsim.h)."""
+    _ck(lib().sim_step_static(C.byref(cfg), _ptr(prims), _ptr(map_off), _ptr(map_ns), _ptr(map_nb),
+                              _i(ns_max), _i(nb_max), _ptr(env_map), _ptr(targets), _ptr(pool),
+                              _ptr(state), _ptr(actions), _ptr(depth), _ptr(lidar), _ptr(r_ctrl),
+                              _ptr(r_goal), _ptr(done), _ptr(pool_k), _stream(stream)), "sim_step_static")
 
 
 # ------------------------------------------------------------ owner class
