@@ -53,12 +53,14 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--n-env", type=int, default=None,
+                    help="override the number of environments (profiling on a smaller case)")
     return ap.parse_args()
 
 
-def workload_params(name):
+def workload_params(name, n_env=None):
     from paper_2509_10247_b300 import synth
-    return synth.preset(name)
+    return synth.preset(name) if n_env is None else synth.preset(name, n_env=n_env)
 
 
 def source_hash():
@@ -167,7 +169,7 @@ class Clocks:
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
-    p = workload_params(args.workload)
+    p = workload_params(args.workload, args.n_env)
     from paper_2509_10247_b300 import synth
     inp = synth.make_inputs(p, seed=args.seed)
     import oracle
@@ -209,7 +211,7 @@ def run_ours(args, rank, world):
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    p = workload_params(args.workload)
+    p = workload_params(args.workload, args.n_env)
     inp = synth.make_inputs(p, seed=args.seed + rank)
     sim = Simulator(p, inp, device=dev, **BENCH_EXEC)
     T, NM, Rc = p["horizon"], sim.NM, sim.Rc
@@ -283,11 +285,11 @@ def run_ours(args, rank, world):
     achieved = flop / (fwd_ms / 1e3) / 1e12
     peak = peak_fp32_tflops(props.multi_processor_count, 2032.0)
     traffic = None
-    tfile = os.path.join(ROOT, "profiles", "traffic.json")
+    tfile = os.path.join(ROOT, "profiles", "traffic.txt")
     if os.path.exists(tfile):
-        tj = json.load(open(tfile))
+        tj = dict(l.split(": ", 1) for l in open(tfile).read().splitlines() if ": " in l and not l.startswith("#"))
         if tj.get("source_hash") == source_hash() and tj.get("workload") == p["name"]:
-            traffic = tj.get("rollout_bytes_per_launch")
+            traffic = float(tj["rollout_bytes_per_launch"])
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": traffic,
                 "kernel": "k_rollout (forward rollout launch)", "kernel_ms": fwd_ms,
