@@ -219,8 +219,8 @@ int sim_counters(sim_handle *h, uint64_t *out, int32_t reset);
  * front): they pass every buffer, and the step's scratch (work ticket,
  * status word, counters, camera / LiDAR ray tables) lives in one static
  * device array of SIM_STATIC_SCRATCH_BYTES that every GPU which loads the
- * library holds until the process exits.  Limit: 16 * (Rc + Rl) + 64 bytes
- * must fit in it (at most 16380 rays per agent), else SIM_ERR_SIZE.
+ * library holds until the process exits.  Limit: 20 * (Rc + Rl) + 64 bytes
+ * must fit in it (at most 13104 rays per agent), else SIM_ERR_SIZE.
  *   cfg      simulation parameters (HOST); execution fields warps_per_cta,
  *            rays_per_thread and cull are honoured, the others ignored
  *   prims    DEVICE, the scene in the library's layout: per map a block of

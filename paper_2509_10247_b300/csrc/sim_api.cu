@@ -9,12 +9,15 @@
 #include <vector>
 
 #include "diffsim.h"
-#include "sim_kernels.cuh"
+#include "sim_raycast.cuh"
 
 namespace ds {
 bool rpt_supported(int rpt);
-cudaError_t launch_sim(bool adjoint, int rpt, const Args& a, int grid, int block, size_t smem, cudaStream_t st);
-cudaError_t occupancy_sim(bool adjoint, int rpt, int block, size_t smem, int* n);
+cudaError_t launch_physics(const Args& a, cudaStream_t st);
+cudaError_t launch_physics_bwd(const Args& a, cudaStream_t st);
+void physics_bwd_shape(int K, int M, int* warps, size_t* smem);
+cudaError_t render_call(bool vjp, bool launch, int rpt, const Args& a, int grid, int block, size_t smem,
+                        cudaStream_t st, int* occ);
 }  // namespace ds
 
 using ds::Args;
@@ -35,6 +38,7 @@ struct sim_handle {
     int ns_max = 0, nb_max = 0, n_maps = 0;
     // sensors
     float4 *d_cam = nullptr, *d_lid = nullptr;
+    float *d_cam_tmax = nullptr, *d_lid_tmax = nullptr;
     ds::Sensor sen[ds::MAX_SENSORS];
     // state and records
     float* d_state = nullptr;
@@ -44,16 +48,18 @@ struct sim_handle {
     uint8_t* d_done_tape = nullptr;
     int16_t* d_sdf_tape = nullptr;
     int16_t *d_tape_cam = nullptr, *d_tape_lid = nullptr;
+    float *d_poses = nullptr, *d_gposes = nullptr;  // [T][NM][12] rollout poses and their cotangents
+    float *d_pose1 = nullptr, *d_gpose1 = nullptr;  // [NM][12] single-step poses and cotangents
+    float* d_state2 = nullptr;                       // [NM][D] scratch state of the step adjoint
     int *d_work = nullptr, *d_status = nullptr;
     unsigned long long* d_counters = nullptr;
     size_t bytes = 0;
     bool have_rollout = false;
     const float* rollout_actions = nullptr;
     cudaStream_t last_stream = nullptr;
-    // launch shape
-    int nw = 8, rpt = 4, grid_f = 1, grid_b = 1;
-    size_t smem_f = 0, smem_b = 0, smem_sb = 0;
-    ds::Smem sm_f{}, sm_b{}, sm_sb{};
+    // launch shape of the render kernels (forward, adjoint, single-step adjoint)
+    int nw = 8, rpt = 4, grid_r = 1, grid_rv = 1, grid_rvs = 1;
+    ds::Smem sm_r{}, sm_rv{}, sm_rvs{};
 };
 
 namespace {
@@ -125,6 +131,11 @@ int validate(const sim_config* c) {
     if (c->terminate != 0 && c->terminate != 1) return SIM_ERR_INVALID_ARG;
     if (c->tape_hits < -1 || c->tape_hits > 1 || (c->cull != 0 && c->cull != 1)) return SIM_ERR_INVALID_ARG;
     if (c->warps_per_cta < 0 || c->warps_per_cta > 8) return SIM_ERR_INVALID_ARG;
+    {
+        // the physics adjoint keeps a segment of (K + 1) states per agent in shared memory
+        const long K = c->ckpt_every > 0 ? std::min(c->ckpt_every, c->horizon) : c->horizon;
+        if ((K + 1) * (long)c->n_agent * 64 > 200L * 1024) return SIM_ERR_SIZE;
+    }
     if (c->rays_per_thread != 0 && !ds::rpt_supported(c->rays_per_thread)) return SIM_ERR_INVALID_ARG;
     if (c->ctas_per_sm < 0) return SIM_ERR_INVALID_ARG;
     for (int i = 0; i < 6; ++i)
@@ -134,36 +145,24 @@ int validate(const sim_config* c) {
 
 size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 
-ds::Smem layout(const sim_handle* h, bool adjoint, bool lists) {
+// Shared memory of a render CTA: the map block, one cull list per warp, the
+// TMA barrier.
+ds::Smem layout_render(const sim_handle* h, bool lists) {
     ds::Smem s{};
     size_t o = 0;
-    const int L = h->M * h->S;
-    auto take = [&](int& field, size_t bytes) {
-        field = (int)o;
-        o = align16(o + bytes);
-    };
-    take(s.prim, (size_t)(h->ns_max + 2 * h->nb_max) * 16);
-    const int Ls = lists ? L : 0;
-    take(s.lsph, (size_t)Ls * h->ns_max * 16);
-    take(s.lbox, (size_t)Ls * h->nb_max * 32);
-    take(s.lr2, (size_t)Ls * h->ns_max * 4);
-    take(s.lid, (size_t)Ls * (h->ns_max + h->nb_max) * 2);
-    take(s.lmeta, (size_t)Ls * 16);
-    take(s.st, (size_t)h->M * 16 * 4);
-    take(s.spre, (size_t)h->M * 16 * 4);
-    take(s.pose, (size_t)h->M * 12 * 4);
-    take(s.aux, (size_t)h->M * 8 * 4);
-    long items = 0;
-    for (int k = 0; k < h->S; ++k) items += (long)h->M * ((h->sen[k].R + 32 * h->rpt - 1) / (32 * h->rpt));
-    take(s.gpose, adjoint ? (size_t)items * 12 * 4 : 0);
-    take(s.gs, adjoint ? (size_t)h->M * 16 * 4 : 0);
-    take(s.seg, adjoint ? (size_t)(h->K + 1) * h->M * 16 * 4 : 0);
-    take(s.mbar, 16);
+    s.prim = 0;
+    o = align16((size_t)(h->ns_max + 2 * h->nb_max) * 16);
+    s.wlist = (int)o;
+    s.wstride = (int)ds::wlist_bytes(h->ns_max, h->nb_max);
+    if (lists) o += (size_t)h->nw * s.wstride;
+    s.mbar = (int)o;
+    o += 16;
     s.total = (int)o;
     return s;
 }
 
-// Rays per thread: best product of lane utilisation and warp balance.
+// Rays per thread: best lane utilisation over the sensors' ray counts (ties
+// to more rays per thread, which share each list entry's load).
 int pick_rpt(const sim_handle* h) {
     if (h->cfg.rays_per_thread) return h->cfg.rays_per_thread;
     if (h->S == 0) return 1;
@@ -171,49 +170,45 @@ int pick_rpt(const sim_handle* h) {
     double best = -1.0;
     int pick = 4;
     for (int r : cands) {
-        long items = 0, rays = 0;
+        long slots = 0, rays = 0;
         for (int s = 0; s < h->S; ++s) {
-            items += (long)h->M * ((h->sen[s].R + 32 * r - 1) / (32 * r));
-            rays += (long)h->M * h->sen[s].R;
+            slots += (long)32 * r * ((h->sen[s].R + 32 * r - 1) / (32 * r));
+            rays += h->sen[s].R;
         }
-        double util = (double)rays / ((double)items * 32 * r);
-        long rounds = (items + h->nw - 1) / h->nw;
-        double bal = (double)items / (double)(rounds * h->nw);
-        double score = util * bal;
-        if (score > best + 1e-9) { best = score; pick = r; }
+        const double util = (double)rays / (double)slots;
+        if (util > best + 1e-9) { best = util; pick = r; }
     }
     return pick;
+}
+
+int grid_of(sim_handle* h, bool vjp, const ds::Smem& sm, int* grid) {
+    int occ = 0;
+    Args dummy;
+    memset(&dummy, 0, sizeof(dummy));
+    CK(ds::render_call(vjp, false, h->rpt, dummy, 0, 32 * h->nw, sm.total, nullptr, &occ));
+    if (occ < 1) return SIM_ERR_UNSUPPORTED;
+    if (h->cfg.ctas_per_sm) occ = std::min(occ, h->cfg.ctas_per_sm);
+    *grid = (int)std::min<long>((long)occ * h->num_sms, h->N);
+    return SIM_OK;
 }
 
 int configure_launch(sim_handle* h) {
     h->nw = h->cfg.warps_per_cta ? h->cfg.warps_per_cta : 8;
     h->rpt = pick_rpt(h);
-    h->sm_f = layout(h, false, h->S > 0);
-    h->sm_b = layout(h, true, h->S > 0 && !h->tape);
-    h->smem_f = h->sm_f.total;
-    h->smem_b = h->sm_b.total;
-    {
-        // the single-step adjoint re-casts rays and keeps a one-step segment
-        const int K = h->K;
-        h->K = 1;
-        h->sm_sb = layout(h, true, h->S > 0);
-        h->K = K;
-        h->smem_sb = h->sm_sb.total;
-    }
+    h->sm_r = layout_render(h, h->S > 0);
+    h->sm_rv = layout_render(h, h->S > 0 && !h->tape);
+    h->sm_rvs = layout_render(h, h->S > 0);
     int maxsm = 0;
     CK(cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
-    if ((int)h->smem_f > maxsm || (int)h->smem_b > maxsm || (int)h->smem_sb > maxsm) return SIM_ERR_SIZE;
-    const int block = 32 * h->nw;
-    int occ_f = 0, occ_b = 0;
-    CK(ds::occupancy_sim(false, h->rpt, block, h->smem_f, &occ_f));
-    CK(ds::occupancy_sim(true, h->rpt, block, h->smem_b, &occ_b));
-    if (occ_f < 1 || occ_b < 1) return SIM_ERR_UNSUPPORTED;
-    if (h->cfg.ctas_per_sm) {
-        occ_f = std::min(occ_f, h->cfg.ctas_per_sm);
-        occ_b = std::min(occ_b, h->cfg.ctas_per_sm);
-    }
-    h->grid_f = (int)std::min<long>((long)occ_f * h->num_sms, h->N);
-    h->grid_b = (int)std::min<long>((long)occ_b * h->num_sms, h->N);
+    if (h->sm_r.total > maxsm || h->sm_rv.total > maxsm) return SIM_ERR_SIZE;
+    int w;
+    size_t segb;
+    ds::physics_bwd_shape(h->K, h->M, &w, &segb);
+    if ((int)segb > maxsm) return SIM_ERR_SIZE;
+    int rc;
+    if ((rc = grid_of(h, false, h->sm_r, &h->grid_r)) || (rc = grid_of(h, true, h->sm_rv, &h->grid_rv)) ||
+        (rc = grid_of(h, true, h->sm_rvs, &h->grid_rvs)))
+        return rc;
     return SIM_OK;
 }
 
@@ -245,16 +240,32 @@ Args base_args(const sim_handle* h) {
     return a;
 }
 
-int run(sim_handle* h, bool adjoint, Args& a, cudaStream_t st, bool step_adjoint = false) {
-    a.sm = step_adjoint ? h->sm_sb : (adjoint ? h->sm_b : h->sm_f);
-    const size_t smem = step_adjoint ? h->smem_sb : (adjoint ? h->smem_b : h->smem_f);
-    CK(cudaMemsetAsync(h->d_work, 0, sizeof(int), st));
+int run_physics(sim_handle* h, const Args& a, cudaStream_t st) {
     h->last_stream = st;
-    CK(ds::launch_sim(adjoint, h->rpt, a, adjoint ? h->grid_b : h->grid_f, 32 * h->nw, smem, st));
+    CK(ds::launch_physics(a, st));
     return SIM_OK;
 }
 
-void build_sensors(sim_handle* h, std::vector<float4>& cam, std::vector<float4>& lid) {
+int run_physics_bwd(sim_handle* h, const Args& a, cudaStream_t st) {
+    h->last_stream = st;
+    CK(ds::launch_physics_bwd(a, st));
+    return SIM_OK;
+}
+
+// which: 0 render, 1 render adjoint (rollout), 2 render adjoint re-casting (step)
+int run_render(sim_handle* h, int which, Args& a, cudaStream_t st) {
+    const ds::Smem& sm = which == 0 ? h->sm_r : (which == 1 ? h->sm_rv : h->sm_rvs);
+    const int grid = which == 0 ? h->grid_r : (which == 1 ? h->grid_rv : h->grid_rvs);
+    a.sm = sm;
+    CK(cudaMemsetAsync(h->d_work, 0, sizeof(int), st));
+    h->last_stream = st;
+    int occ = 0;
+    CK(ds::render_call(which != 0, true, h->rpt, a, grid, 32 * h->nw, sm.total, st, &occ));
+    return SIM_OK;
+}
+
+void build_sensors(sim_handle* h, std::vector<float4>& cam, std::vector<float4>& lid, std::vector<float>& cam_t,
+                   std::vector<float>& lid_t) {
     const sim_config& c = h->cfg;
     int s = 0;
     if (c.cam_w > 0) {
@@ -262,11 +273,13 @@ void build_sensors(sim_handle* h, std::vector<float4>& cam, std::vector<float4>&
         const double th = std::tan(0.5 * (double)c.cam_hfov), tv = th * H / W;
         double fmin = 1.0;
         cam.resize((size_t)W * H);
+        cam_t.resize((size_t)W * H);
         for (int j = 0; j < H; ++j)
             for (int i = 0; i < W; ++i) {
                 double u = (2.0 * (i + 0.5) / W - 1.0) * th, v = (2.0 * (j + 0.5) / H - 1.0) * tv;
                 double n = std::sqrt(1.0 + u * u + v * v);
                 cam[(size_t)j * W + i] = make_float4((float)(1.0 / n), (float)(-u / n), (float)(-v / n), (float)(1.0 / n));
+                cam_t[(size_t)j * W + i] = (float)((double)c.cam_range * n);
                 fmin = std::min(fmin, 1.0 / n);
             }
         ds::Sensor& S = h->sen[s++];
@@ -278,6 +291,7 @@ void build_sensors(sim_handle* h, std::vector<float4>& cam, std::vector<float4>&
     if (c.lid_ch > 0) {
         const int C = c.lid_ch, Az = c.lid_az;
         lid.resize((size_t)C * Az);
+        lid_t.assign((size_t)C * Az, c.lid_range);
         for (int ch = 0; ch < C; ++ch) {
             double el = C > 1 ? c.lid_elev_lo + ch * ((double)c.lid_elev_hi - c.lid_elev_lo) / (C - 1)
                               : 0.5 * ((double)c.lid_elev_lo + c.lid_elev_hi);
@@ -315,8 +329,10 @@ int sim_destroy(sim_handle* h) {
     dfree(h->d_prims); dfree(h->d_map_off); dfree(h->d_map_ns); dfree(h->d_map_nb);
     dfree(h->d_env_map); dfree(h->d_order); dfree(h->d_targets); dfree(h->d_pool);
     dfree(h->d_drag); dfree(h->d_lam); dfree(h->d_cam); dfree(h->d_lid);
+    dfree(h->d_cam_tmax); dfree(h->d_lid_tmax);
     dfree(h->d_state); dfree(h->d_pool_k); dfree(h->d_ckpt); dfree(h->d_ckpt_k);
     dfree(h->d_done_tape); dfree(h->d_sdf_tape); dfree(h->d_tape_cam); dfree(h->d_tape_lid);
+    dfree(h->d_poses); dfree(h->d_gposes); dfree(h->d_pose1); dfree(h->d_gpose1); dfree(h->d_state2);
     dfree(h->d_work); dfree(h->d_status); dfree(h->d_counters);
     delete h;
     return SIM_OK;
@@ -347,17 +363,24 @@ int sim_create(const sim_config* cfg, sim_handle** out) {
     TRY(cuda_err(cudaGetDevice(&h->device)));
     TRY(cuda_err(cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device)));
     std::vector<float4> cam, lid;
-    build_sensors(h, cam, lid);
+    std::vector<float> cam_t, lid_t;
+    build_sensors(h, cam, lid, cam_t, lid_t);
     int s = 0;
     if (h->Rc) {
         TRY(dalloc(h, &h->d_cam, cam.size()));
+        TRY(dalloc(h, &h->d_cam_tmax, cam_t.size()));
         TRY(cuda_err(cudaMemcpy(h->d_cam, cam.data(), cam.size() * sizeof(float4), cudaMemcpyHostToDevice)));
-        h->sen[s++].dir = h->d_cam;
+        TRY(cuda_err(cudaMemcpy(h->d_cam_tmax, cam_t.data(), cam_t.size() * sizeof(float), cudaMemcpyHostToDevice)));
+        h->sen[s].dir = h->d_cam;
+        h->sen[s++].tmax = h->d_cam_tmax;
     }
     if (h->Rl) {
         TRY(dalloc(h, &h->d_lid, lid.size()));
+        TRY(dalloc(h, &h->d_lid_tmax, lid_t.size()));
         TRY(cuda_err(cudaMemcpy(h->d_lid, lid.data(), lid.size() * sizeof(float4), cudaMemcpyHostToDevice)));
-        h->sen[s++].dir = h->d_lid;
+        TRY(cuda_err(cudaMemcpy(h->d_lid_tmax, lid_t.data(), lid_t.size() * sizeof(float), cudaMemcpyHostToDevice)));
+        h->sen[s].dir = h->d_lid;
+        h->sen[s++].tmax = h->d_lid_tmax;
     }
     const size_t tape_bytes = (size_t)h->T * h->NM * (h->Rc + h->Rl) * 2;
     h->tape = cfg->tape_hits == 1 || (cfg->tape_hits == -1 && tape_bytes <= (size_t(8) << 30));
@@ -373,6 +396,11 @@ int sim_create(const sim_config* cfg, sim_handle** out) {
         if (h->Rc) TRY(dalloc(h, &h->d_tape_cam, (size_t)h->T * h->NM * h->Rc));
         if (h->Rl) TRY(dalloc(h, &h->d_tape_lid, (size_t)h->T * h->NM * h->Rl));
     }
+    TRY(dalloc(h, &h->d_poses, (size_t)h->T * h->NM * 12));
+    TRY(dalloc(h, &h->d_gposes, (size_t)h->T * h->NM * 12));
+    TRY(dalloc(h, &h->d_pose1, (size_t)h->NM * 12));
+    TRY(dalloc(h, &h->d_gpose1, (size_t)h->NM * 12));
+    TRY(dalloc(h, &h->d_state2, (size_t)h->NM * h->D));
     TRY(dalloc(h, &h->d_work, 1));
     TRY(dalloc(h, &h->d_status, 1));
     TRY(dalloc(h, &h->d_counters, 4));
@@ -532,13 +560,17 @@ int sim_set_state(sim_handle* h, const float* src, sim_stream_t stream) {
 int sim_render(sim_handle* h, float* depth, float* lidar, sim_stream_t stream) {
     if (!h) return SIM_ERR_NULL_PTR;
     if (!h->have_scene) return SIM_ERR_NOT_READY;
+    cudaStream_t st = (cudaStream_t)stream;
     Args a = base_args(h);
     a.render_only = 1;
     a.T = 1;
+    a.poses = h->d_pose1;
+    int rc = run_physics(h, a, st);
+    if (rc || h->S == 0) return rc;
     int s = 0;
     if (h->Rc) { a.sen[s].out = depth; a.sen[s].tape = nullptr; ++s; }
     if (h->Rl) { a.sen[s].out = lidar; a.sen[s].tape = nullptr; ++s; }
-    return run(h, false, a, (cudaStream_t)stream);
+    return run_render(h, 0, a, st);
 }
 
 int sim_step(sim_handle* h, const float* actions, float* depth, float* lidar, float* r_ctrl, int8_t* r_goal,
@@ -546,15 +578,19 @@ int sim_step(sim_handle* h, const float* actions, float* depth, float* lidar, fl
     if (!h || !actions) return SIM_ERR_NULL_PTR;
     if (!h->have_scene) return SIM_ERR_NOT_READY;
     if (h->cfg.terminate && !h->have_pool) return SIM_ERR_NOT_READY;
+    cudaStream_t st = (cudaStream_t)stream;
     Args a = base_args(h);
     a.T = 1;
     a.K = 1;
     a.actions = actions;
     a.r_ctrl = r_ctrl; a.r_goal = r_goal; a.done = done;
+    a.poses = h->d_pose1;
+    int rc = run_physics(h, a, st);
+    if (rc || h->S == 0) return rc;
     int s = 0;
     if (h->Rc) { a.sen[s].out = depth; a.sen[s].tape = nullptr; ++s; }
     if (h->Rl) { a.sen[s].out = lidar; a.sen[s].tape = nullptr; ++s; }
-    return run(h, false, a, (cudaStream_t)stream);
+    return run_render(h, 0, a, st);
 }
 
 int sim_rollout(sim_handle* h, const float* actions, float* r_ctrl, int8_t* r_goal, uint8_t* done, float* depth,
@@ -562,6 +598,7 @@ int sim_rollout(sim_handle* h, const float* actions, float* r_ctrl, int8_t* r_go
     if (!h || !actions) return SIM_ERR_NULL_PTR;
     if (!h->have_scene) return SIM_ERR_NOT_READY;
     if (h->cfg.terminate && !h->have_pool) return SIM_ERR_NOT_READY;
+    cudaStream_t st = (cudaStream_t)stream;
     Args a = base_args(h);
     a.actions = actions;
     a.r_ctrl = r_ctrl; a.r_goal = r_goal; a.done = done;
@@ -569,11 +606,16 @@ int sim_rollout(sim_handle* h, const float* actions, float* r_ctrl, int8_t* r_go
     a.sdf_tape = h->d_sdf_tape;
     a.ckpt = h->d_ckpt;
     a.ckpt_k = h->d_ckpt_k;
-    int s = 0;
-    if (h->Rc) { a.sen[s].out = depth; a.sen[s].tape = h->d_tape_cam; ++s; }
-    if (h->Rl) { a.sen[s].out = lidar; a.sen[s].tape = h->d_tape_lid; ++s; }
-    int rc = run(h, false, a, (cudaStream_t)stream);
+    a.poses = h->d_poses;
+    int rc = run_physics(h, a, st);
     if (rc) return rc;
+    if (h->S > 0) {
+        int s = 0;
+        if (h->Rc) { a.sen[s].out = depth; a.sen[s].tape = h->d_tape_cam; ++s; }
+        if (h->Rl) { a.sen[s].out = lidar; a.sen[s].tape = h->d_tape_lid; ++s; }
+        rc = run_render(h, 0, a, st);
+        if (rc) return rc;
+    }
     h->have_rollout = true;
     h->rollout_actions = actions;
     return SIM_OK;
@@ -583,17 +625,24 @@ int sim_backward(sim_handle* h, const float* g_r, const float* g_depth, const fl
                  float* g_a, float* g_s0, sim_stream_t stream) {
     if (!h || !g_r || !g_a) return SIM_ERR_NULL_PTR;
     if (!h->have_rollout) return SIM_ERR_NOT_READY;
+    cudaStream_t st = (cudaStream_t)stream;
     Args a = base_args(h);
     a.actions = h->rollout_actions;
     a.done_rd = h->d_done_tape;
     a.sdf_tape = h->d_sdf_tape;
     a.ckpt = h->d_ckpt;
     a.ckpt_k = h->d_ckpt_k;
+    a.poses = h->d_poses;
     a.g_r = g_r; a.g_sT = g_sT; a.g_a = g_a; a.g_s0 = g_s0;
     int s = 0;
     if (h->Rc) { a.sen[s].gout = g_depth; a.sen[s].tape = h->d_tape_cam; ++s; }
     if (h->Rl) { a.sen[s].gout = g_lidar; a.sen[s].tape = h->d_tape_lid; ++s; }
-    return run(h, true, a, (cudaStream_t)stream);
+    if (h->S > 0 && (g_depth || g_lidar)) {
+        a.gposes = h->d_gposes;
+        int rc = run_render(h, 1, a, st);
+        if (rc) return rc;
+    }
+    return run_physics_bwd(h, a, st);
 }
 
 int sim_step_backward(sim_handle* h, const float* s_t, const float* a_t, const uint8_t* done_t,
@@ -601,19 +650,35 @@ int sim_step_backward(sim_handle* h, const float* s_t, const float* a_t, const u
                       float* g_a, float* g_s, sim_stream_t stream) {
     if (!h || !s_t || !a_t || !done_t || !g_r || !g_a) return SIM_ERR_NULL_PTR;
     if (!h->have_scene) return SIM_ERR_NOT_READY;
+    cudaStream_t st = (cudaStream_t)stream;
     Args a = base_args(h);
     a.T = 1;
     a.K = 1;
     a.actions = a_t;
+    if (h->S > 0 && (g_depth || g_lidar)) {
+        // pose after the step, from a scratch copy of s_t (the current state is untouched)
+        CK(cudaMemcpyAsync(h->d_state2, s_t, (size_t)h->NM * h->D * sizeof(float), cudaMemcpyDeviceToDevice, st));
+        Args f = a;
+        f.state = h->d_state2;
+        f.pool_k = nullptr;
+        f.poses = h->d_pose1;
+        int rc = run_physics(h, f, st);
+        if (rc) return rc;
+        a.poses = h->d_pose1;
+        a.gposes = h->d_gpose1;
+        a.done_rd = done_t;
+        int s = 0;
+        if (h->Rc) { a.sen[s].gout = g_depth; a.sen[s].tape = nullptr; ++s; }
+        if (h->Rl) { a.sen[s].gout = g_lidar; a.sen[s].tape = nullptr; ++s; }
+        rc = run_render(h, 2, a, st);
+        if (rc) return rc;
+    }
     a.done_rd = done_t;
     a.sdf_tape = nullptr;
     a.ckpt = const_cast<float*>(s_t);
     a.ckpt_k = nullptr;
     a.g_r = g_r; a.g_sT = g_s_next; a.g_a = g_a; a.g_s0 = g_s;
-    int s = 0;
-    if (h->Rc) { a.sen[s].gout = g_depth; a.sen[s].tape = nullptr; ++s; }
-    if (h->Rl) { a.sen[s].gout = g_lidar; a.sen[s].tape = nullptr; ++s; }
-    return run(h, true, a, (cudaStream_t)stream, true);
+    return run_physics_bwd(h, a, st);
 }
 
 int sim_last_status(sim_handle* h, int32_t* status, int32_t* per_env) {
@@ -644,8 +709,8 @@ int sim_launch_info(const sim_handle* h, int32_t* warps_per_cta, int32_t* rays_p
     if (!h) return SIM_ERR_NULL_PTR;
     if (warps_per_cta) *warps_per_cta = h->nw;
     if (rays_per_thread) *rays_per_thread = h->rpt;
-    if (grid) *grid = h->grid_f;
-    if (smem_bytes) *smem_bytes = (int32_t)h->smem_f;
+    if (grid) *grid = h->grid_r;
+    if (smem_bytes) *smem_bytes = (int32_t)h->sm_r.total;
     return SIM_OK;
 }
 

@@ -11,6 +11,7 @@ constexpr int MAX_SENSORS = 2;
 struct Sensor {
     int R;                 // rays per agent
     const float4* dir;     // [R] body-frame unit direction (x, y, z) and output factor w
+    const float* tmax;     // [R] ray length at the output clamp (range / w camera, range LiDAR)
     float range;           // output clamp
     int kind;              // 0 camera frustum cull, 1 LiDAR elevation-band cull
     float c0, c1, c2, c3;  // camera: tan_h, tan_v, 1/sqrt(1+tan_h^2), 1/sqrt(1+tan_v^2)
@@ -37,6 +38,8 @@ struct Smem {
     int gs;      // float  [M][16]                 adjoint: state cotangent
     int seg;     // float  [K+1][M][16]            adjoint: segment states
     int mbar;    // uint64 mbarrier
+    int wlist;   // render kernels: first per-warp cull list
+    int wstride; // render kernels: bytes per warp list
     int total;
 };
 
@@ -62,6 +65,8 @@ struct Args {
     // adjoint
     const float* g_r; const float* g_sT; float* g_a; float* g_s0;
     const uint8_t* done_rd;     // adjoint: [T][NM] done flags of the forward pass
+    float* poses;               // [T][NM][12] sensor pose per step (origin, row-major R)
+    float* gposes;              // [T][NM][12] cotangent of the poses
     // control
     int* work; int* status;
     unsigned long long* counters;  // [4]: sphere tests, box tests, rays, env-steps (nullable)

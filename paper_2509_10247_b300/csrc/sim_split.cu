@@ -1,0 +1,516 @@
+// sim_split.cu -- rollout and adjoint as two kernels each.
+//
+// The sequential part of a step (dynamics Eq. 1 / Eq. 3, collisions,
+// rewards, termination and reset, sensor pose; Sec. III-A to III-D) is light
+// and latency-bound; the ray casting of Sec. III-B is heavy and has no
+// dependence between steps once the poses are known (actions are inputs).
+// So the physics runs first, one warp per environment with one lane per
+// agent and the state in registers for the whole horizon, writing the pose
+// trajectory [T][NM][12] (origin, rotation); then every (step, agent,
+// sensor) is rendered independently by one warp that culls the map into its
+// own shared-memory list and sweeps its rays.  The adjoint (Eq. 5) mirrors
+// it: per (step, agent) ray cotangents reduce to a pose cotangent, then the
+// physics is reverted environment by environment from checkpoints.
+#include "sim_raycast.cuh"
+
+namespace ds {
+
+// ------------------------------------------------------------------ helpers
+__device__ __forceinline__ void load_row(const float* src, int D, bool on, int model, float* s) {
+#pragma unroll
+    for (int k = 0; k < 16; ++k) s[k] = (on && k < D) ? src[k] : 0.f;
+    if (!on && model == MODEL_RIGID) s[3] = 1.f;  // a harmless unit quaternion on idle lanes
+}
+
+__device__ __forceinline__ void step_agent(const Phys& c, float drag, float lam, const float* s, const float* act,
+                                           float* sp) {
+#pragma unroll
+    for (int k = 0; k < 16; ++k) sp[k] = 0.f;
+    if (c.model == MODEL_RIGID) rb_step(c, s, act, sp);
+    else pm_step(c, drag, lam, s, act, sp);
+}
+
+// Nearest obstacle of every agent of the warp's environment: the warp splits
+// into groups of G = 32 / M' lanes (M' = M rounded up to a power of two),
+// group g scans the map for agent g at position p (lane g's p), then lane m
+// receives agent m's signed distance and arg-min (lowest id among ties).
+__device__ __forceinline__ void nearest_obstacle(const float4* prim, int ns, int nb, int M, const float* p,
+                                                 float& sd, int& id) {
+    const int lane = threadIdx.x & 31;
+    int Mp = 1;
+    while (Mp < M) Mp <<= 1;
+    const int G = 32 / Mp;
+    const int gm = lane / G, gl = lane - gm * G;
+    const float q[3] = {__shfl_sync(0xffffffffu, p[0], gm), __shfl_sync(0xffffffffu, p[1], gm),
+                        __shfl_sync(0xffffffffu, p[2], gm)};
+    float best = CUDART_INF_F;
+    int bid = -1;
+    if (gm < M)
+        for (int k = gl; k < ns + nb; k += G) {
+            const float d = sdf_prim(prim, ns, k, q);
+            if (d < best) { best = d; bid = k; }
+        }
+    for (int o = G >> 1; o > 0; o >>= 1) {
+        const float v2 = __shfl_xor_sync(0xffffffffu, best, o);
+        const int i2 = __shfl_xor_sync(0xffffffffu, bid, o);
+        if (v2 < best || (v2 == best && (unsigned)i2 < (unsigned)bid)) { best = v2; bid = i2; }
+    }
+    const int src = lane < Mp ? lane * G : 0;
+    sd = __shfl_sync(0xffffffffu, best, src);
+    id = __shfl_sync(0xffffffffu, bid, src);
+}
+
+// ----------------------------------------------------------- forward physics
+// One warp per environment.  render_only: write the pose of the current
+// state at step 0 and return.
+__global__ void __launch_bounds__(128) k_physics(const Args a) {
+    const int lane = threadIdx.x & 31;
+    const int env = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (env >= a.N) return;
+    const int M = a.M, D = a.c.D, A = a.c.A, NM = a.NM;
+    const int map = a.env_map[env];
+    const float4* prim = a.prims + a.map_off[map];
+    const int ns = a.map_ns[map], nb = a.map_nb[map];
+    const bool on = lane < M;
+    const int i = env * M + (on ? lane : 0);
+    const float drag = a.drag_env ? a.drag_env[env] : a.c.drag;
+    const float lam = a.lam_env ? a.lam_env[env] : a.c.lam;
+    float s[16];
+    load_row(a.state + (size_t)i * D, D, on, a.c.model, s);
+    if (a.render_only) {
+        if (on && a.poses) sensor_pose(a.c.model, s, a.poses + (size_t)i * 12, a.poses + (size_t)i * 12 + 3);
+        return;
+    }
+    int kpool = a.pool_k ? a.pool_k[env] : 0;
+    for (int t = 0; t < a.T; ++t) {
+        const size_t o = (size_t)t * NM + i;
+        if (a.ckpt && (t % a.K) == 0) {
+            const int c = t / a.K;
+            if (on)
+                for (int k = 0; k < D; ++k) a.ckpt[((size_t)c * NM + i) * D + k] = s[k];
+            if (lane == 0) a.ckpt_k[(size_t)c * a.N + env] = kpool;
+        }
+        float act[4], sp[16];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) act[k] = (on && k < A) ? a.actions[o * A + k] : 0.f;
+        step_agent(a.c, drag, lam, s, act, sp);
+        float sd;
+        int bid;
+        nearest_obstacle(prim, ns, nb, M, sp, sd, bid);
+        // collisions and the dense / sparse rewards (Sec. III-C, III-E)
+        bool col = sd < a.c.r_quad;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) col = col || sp[k] < a.c.blo[k] || sp[k] > a.c.bhi[k];
+        float pair = 0.f;
+        for (int n = 0; n < M; ++n) {
+            const float px = __shfl_sync(0xffffffffu, sp[0], n), py = __shfl_sync(0xffffffffu, sp[1], n),
+                        pz = __shfl_sync(0xffffffffu, sp[2], n);
+            if (n == lane) continue;
+            const float dd[3] = {sp[0] - px, sp[1] - py, sp[2] - pz};
+            const float dij = sqrtf(dot3(dd, dd));
+            col = col || dij < a.c.d_agent;
+            const float sv = relu(a.c.d_agent - dij);
+            pair += sv * sv;
+        }
+        const bool dn = a.c.terminate && __ballot_sync(0xffffffffu, on && col) != 0u;
+        if (on) {
+            const float* tg = a.targets + 3 * (size_t)i;
+            const float e[3] = {sp[0] - tg[0], sp[1] - tg[1], sp[2] - tg[2]};
+            const float ne2 = dot3(e, e), ne = sqrtf(ne2);
+            const float pos = a.c.pos_sq ? ne2 : ne;
+            const float ob = (a.c.w_obs != 0.f && sd < CUDART_INF_F) ? relu(a.c.d_safe - sd) : 0.f;
+            float aa = 0.f;
+            for (int k = 0; k < A; ++k) aa += act[k] * act[k];
+            if (a.r_ctrl) a.r_ctrl[o] = -a.c.w_pos * pos - a.c.w_obs * ob * ob - a.c.w_act * aa - a.c.w_agent * pair;
+            if (a.r_goal) a.r_goal[o] = (int8_t)(col ? -1 : (ne < a.c.success_radius ? 1 : 0));
+            if (a.sdf_tape) a.sdf_tape[o] = (int16_t)bid;
+            if (a.done) a.done[o] = dn ? 1 : 0;
+            if (a.done_tape) a.done_tape[o] = dn ? 1 : 0;
+        }
+        // termination and reset of the whole environment from the pool
+        if (dn && a.c.P > 0) load_row(a.pool + ((size_t)(kpool % a.c.P) * NM + i) * D, D, on, a.c.model, s);
+        else {
+#pragma unroll
+            for (int k = 0; k < 16; ++k) s[k] = sp[k];
+        }
+        if (dn) ++kpool;
+        if (on) {
+            bool fin = true;
+#pragma unroll
+            for (int k = 0; k < 16; ++k) fin = fin && isfinite(s[k]);
+            if (!fin) atomicOr(a.status, 1);
+            if (a.poses) sensor_pose(a.c.model, s, a.poses + o * 12, a.poses + o * 12 + 3);
+        }
+    }
+    if (on)
+        for (int k = 0; k < D; ++k) a.state[(size_t)i * D + k] = s[k];
+    if (lane == 0 && a.pool_k) a.pool_k[env] = kpool;
+}
+
+// ------------------------------------------------------------------ render
+// Persistent CTAs take environments from a ticket (descending work); the
+// environment's map is staged once into shared memory; its T x M x S items
+// (step, agent, sensor) are taken by warps from a CTA ticket.  A warp culls
+// the map into its private list and sweeps all rays of the item.
+template <int RPT>
+__global__ void __launch_bounds__(256, 4) k_render(const Args a) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    __shared__ int s_env, s_flag, s_item;
+    __shared__ unsigned long long s_cnt[4];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, NW = blockDim.x >> 5;
+    const int M = a.M, S = a.S, NM = a.NM;
+    const float4* prim = reinterpret_cast<const float4*>(sm + a.sm.prim);
+    const WList L = wlist_at(sm + a.sm.wlist + (size_t)warp * a.sm.wstride, a.ns_max, a.nb_max);
+    if (threadIdx.x < 4) s_cnt[threadIdx.x] = 0ull;
+    if (threadIdx.x == 0) mbar_init(reinterpret_cast<uint64_t*>(sm + a.sm.mbar));
+    __syncthreads();
+    uint32_t phase = 0;
+    const int per_env = a.T * M * S;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            s_env = atomicAdd(a.work, 1);
+            s_item = NW;
+        }
+        __syncthreads();
+        const int q = s_env;
+        if (q >= a.N) break;
+        const int env = a.order ? a.order[q] : q;
+        const int map = a.env_map[env];
+        const int ns = a.map_ns[map], nb = a.map_nb[map];
+        if (!stage_map(a, sm, map, ns, nb, phase, &s_flag)) return;
+        for (int it = warp; it < per_env; it = next_item(&s_item, lane)) {
+            const int t = it / (M * S), rem = it - t * M * S, m = rem / S, si = rem - m * S;
+            const Sensor& sen = a.sen[si];
+            if (!sen.out && !sen.tape) continue;
+            const size_t ti = (size_t)t * NM + env * M + m;
+            float o[3], R[9];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) o[k] = a.poses[ti * 12 + k];
+#pragma unroll
+            for (int k = 0; k < 9; ++k) R[k] = a.poses[ti * 12 + 3 + k];
+            const int4 meta = warp_build_list(prim, ns, nb, o, R, sen, a.cull, L, a.ns_max);
+            const int nch = (sen.R + 32 * RPT - 1) / (32 * RPT);
+            const size_t base = ti * sen.R;
+            for (int ch = 0; ch < nch; ++ch) {
+                float dx[RPT], dy[RPT], dz[RPT], fac[RPT], tb[RPT];
+                int bi[RPT];
+                item_rays<RPT>(sen, R, ch, lane, dx, dy, dz, fac, tb);
+#pragma unroll
+                for (int r = 0; r < RPT; ++r) bi[r] = -1;
+                if (meta.z < 0) cast_list<RPT>(L, meta, a.ns_max, dx, dy, dz, tb, bi);
+                if (a.counters && lane == 0) {
+                    const unsigned long long nr = (unsigned long long)min(32 * RPT, sen.R - ch * 32 * RPT);
+                    if (meta.z < 0) {
+                        atomicAdd(&s_cnt[0], nr * (unsigned long long)meta.x);
+                        atomicAdd(&s_cnt[1], nr * (unsigned long long)meta.y);
+                    }
+                    atomicAdd(&s_cnt[2], nr);
+                }
+#pragma unroll
+                for (int r = 0; r < RPT; ++r) {
+                    const int ray = ch * 32 * RPT + r * 32 + lane;
+                    if (ray >= sen.R) continue;
+                    float v;
+                    int id;
+                    if (meta.z >= 0) { v = 0.f; id = meta.z; }
+                    else if (bi[r] < 0) { v = sen.range; id = -1; }
+                    else { v = fminf(tb[r] * (sen.kind == 0 ? fac[r] : 1.f), sen.range); id = L.id[bi[r]]; }
+                    if (sen.out) sen.out[base + ray] = v;
+                    if (sen.tape) sen.tape[base + ray] = (int16_t)id;
+                }
+            }
+            __syncwarp();
+        }
+        if (threadIdx.x == 0) s_cnt[3] += (unsigned long long)(a.T);
+        __syncthreads();
+    }
+    __syncthreads();
+    if (a.counters && threadIdx.x < 4 && s_cnt[threadIdx.x]) atomicAdd(a.counters + threadIdx.x, s_cnt[threadIdx.x]);
+}
+
+// ---------------------------------------------------------- render adjoint
+// One warp per (step, agent) item: the cotangents of all its rays (every
+// sensor) reduce, in a fixed order, to the pose cotangent gposes[t][i] =
+// (d/d origin [3], d/d R [9]).  Zero when the step terminated (the state was
+// replaced).  Hit ids come from the rollout's tape or are re-cast.
+template <int RPT>
+__global__ void __launch_bounds__(256, 3) k_render_vjp(const Args a) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    __shared__ int s_env, s_flag, s_item;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, NW = blockDim.x >> 5;
+    const int M = a.M, S = a.S, NM = a.NM;
+    const float4* prim = reinterpret_cast<const float4*>(sm + a.sm.prim);
+    const bool recast = a.sen[0].tape == nullptr;
+    WList L;
+    if (recast) L = wlist_at(sm + a.sm.wlist + (size_t)warp * a.sm.wstride, a.ns_max, a.nb_max);
+    if (threadIdx.x == 0) mbar_init(reinterpret_cast<uint64_t*>(sm + a.sm.mbar));
+    __syncthreads();
+    uint32_t phase = 0;
+    const int per_env = a.T * M;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            s_env = atomicAdd(a.work, 1);
+            s_item = NW;
+        }
+        __syncthreads();
+        const int q = s_env;
+        if (q >= a.N) break;
+        const int env = a.order ? a.order[q] : q;
+        const int map = a.env_map[env];
+        const int ns = a.map_ns[map], nb = a.map_nb[map];
+        if (!stage_map(a, sm, map, ns, nb, phase, &s_flag)) return;
+        for (int it = warp; it < per_env; it = next_item(&s_item, lane)) {
+            const int t = it / M, m = it - t * M;
+            const size_t ti = (size_t)t * NM + env * M + m;
+            const bool dn = a.done_rd[(size_t)t * NM + env * M] != 0;
+            float go[3] = {0.f, 0.f, 0.f}, gR[9];
+#pragma unroll
+            for (int k = 0; k < 9; ++k) gR[k] = 0.f;
+            if (!dn) {
+                float o[3], R[9];
+#pragma unroll
+                for (int k = 0; k < 3; ++k) o[k] = a.poses[ti * 12 + k];
+#pragma unroll
+                for (int k = 0; k < 9; ++k) R[k] = a.poses[ti * 12 + 3 + k];
+                for (int si = 0; si < S; ++si) {
+                    const Sensor& sen = a.sen[si];
+                    if (!sen.gout) continue;
+                    int4 meta = make_int4(0, 0, -1, 0);
+                    if (recast) meta = warp_build_list(prim, ns, nb, o, R, sen, a.cull, L, a.ns_max);
+                    const int nch = (sen.R + 32 * RPT - 1) / (32 * RPT);
+                    const size_t base = ti * sen.R;
+                    for (int ch = 0; ch < nch; ++ch) {
+                        float dx[RPT], dy[RPT], dz[RPT], fac[RPT], tb[RPT];
+                        int id[RPT];
+                        item_rays<RPT>(sen, R, ch, lane, dx, dy, dz, fac, tb);
+                        if (recast) {
+                            int bi[RPT];
+#pragma unroll
+                            for (int r = 0; r < RPT; ++r) bi[r] = -1;
+                            if (meta.z < 0) cast_list<RPT>(L, meta, a.ns_max, dx, dy, dz, tb, bi);
+#pragma unroll
+                            for (int r = 0; r < RPT; ++r) id[r] = (meta.z >= 0 || bi[r] < 0) ? -1 : L.id[bi[r]];
+                        } else {
+#pragma unroll
+                            for (int r = 0; r < RPT; ++r) {
+                                const int ray = ch * 32 * RPT + r * 32 + lane;
+                                id[r] = ray < sen.R ? sen.tape[base + ray] : -1;
+                            }
+                        }
+#pragma unroll
+                        for (int r = 0; r < RPT; ++r) {
+                            const int ray = ch * 32 * RPT + r * 32 + lane;
+                            if (ray >= sen.R || id[r] < 0) continue;
+                            ray_vjp(prim, ns, id[r], o, dx[r], dy[r], dz[r], __ldg(sen.dir + ray), sen,
+                                    sen.gout[base + ray], go, gR);
+                        }
+                    }
+                    __syncwarp();
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < 3; ++k) go[k] = warp_sum(go[k]);
+#pragma unroll
+            for (int k = 0; k < 9; ++k) gR[k] = warp_sum(gR[k]);
+            if (lane == 0) {
+#pragma unroll
+                for (int k = 0; k < 3; ++k) a.gposes[ti * 12 + k] = go[k];
+#pragma unroll
+                for (int k = 0; k < 9; ++k) a.gposes[ti * 12 + 3 + k] = gR[k];
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// --------------------------------------------------------- physics adjoint
+// One warp per environment, lane per agent.  Segments are taken last to
+// first: the segment's states (after resets, replayed from the recorded done
+// flags) are recomputed from its checkpoint into the warp's shared-memory
+// slice, then steps are reverted: pose cotangent -> state after the step
+// (cut by a reset), reward -> state before reset and action, dynamics ->
+// previous state.
+__global__ void __launch_bounds__(128) k_physics_bwd(const Args a) {
+    extern __shared__ __align__(16) float segm[];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int env = blockIdx.x * (blockDim.x >> 5) + wid;
+    if (env >= a.N) return;
+    const int M = a.M, D = a.c.D, A = a.c.A, NM = a.NM;
+    float* seg = segm + (size_t)wid * (a.K + 1) * M * 16;
+    const int map = a.env_map[env];
+    const float4* prim = a.prims + a.map_off[map];
+    const int ns = a.map_ns[map], nb = a.map_nb[map];
+    const bool on = lane < M;
+    const int i = env * M + (on ? lane : 0);
+    const float drag = a.drag_env ? a.drag_env[env] : a.c.drag;
+    const float lam = a.lam_env ? a.lam_env[env] : a.c.lam;
+    float g[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) g[k] = (on && a.g_sT && k < D) ? a.g_sT[(size_t)i * D + k] : 0.f;
+    const int nseg = (a.T + a.K - 1) / a.K;
+    for (int sg = nseg - 1; sg >= 0; --sg) {
+        const int t0 = sg * a.K, t1 = min(a.T, t0 + a.K);
+        float s[16];
+        load_row(a.ckpt + ((size_t)sg * NM + i) * D, D, on, a.c.model, s);
+        int kp = a.ckpt_k ? a.ckpt_k[(size_t)sg * a.N + env] : 0;
+        if (on)
+#pragma unroll
+            for (int k = 0; k < 16; ++k) seg[(0 * M + lane) * 16 + k] = s[k];
+        for (int t = t0; t < t1; ++t) {
+            const bool dn = a.done_rd[(size_t)t * NM + env * M] != 0;
+            float act[4], sp[16];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) act[k] = (on && k < A) ? a.actions[((size_t)t * NM + i) * A + k] : 0.f;
+            if (dn && a.c.P > 0 && a.pool) load_row(a.pool + ((size_t)(kp % a.c.P) * NM + i) * D, D, on, a.c.model, sp);
+            else step_agent(a.c, drag, lam, s, act, sp);
+            if (dn) ++kp;
+#pragma unroll
+            for (int k = 0; k < 16; ++k) s[k] = sp[k];
+            if (on)
+#pragma unroll
+                for (int k = 0; k < 16; ++k) seg[((t - t0 + 1) * M + lane) * 16 + k] = s[k];
+        }
+        __syncwarp();
+        for (int t = t1 - 1; t >= t0; --t) {
+            const size_t o = (size_t)t * NM + i;
+            const bool dn = a.done_rd[(size_t)t * NM + env * M] != 0;
+            float s0[16], s1[16], act[4];
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+                s0[k] = on ? seg[((t - t0) * M + lane) * 16 + k] : 0.f;
+                s1[k] = on ? seg[((t - t0 + 1) * M + lane) * 16 + k] : 0.f;
+            }
+            if (!on && a.c.model == MODEL_RIGID) { s0[3] = 1.f; s1[3] = 1.f; }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) act[k] = (on && k < A) ? a.actions[o * A + k] : 0.f;
+            if (!dn && a.gposes && on) {
+                float gq[12];
+#pragma unroll
+                for (int k = 0; k < 12; ++k) gq[k] = a.gposes[o * 12 + k];
+                pose_vjp(a.c.model, s1, gq, gq + 3, g);
+            }
+            float gp[16], gs[16], ga[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+            for (int k = 0; k < 16; ++k) { gp[k] = dn ? 0.f : g[k]; gs[k] = 0.f; }
+            // reward R_ctrl at the state before reset
+            float sp[16];
+            step_agent(a.c, drag, lam, s0, act, sp);
+            int bid;
+            if (a.sdf_tape) bid = on ? a.sdf_tape[o] : -1;
+            else {
+                float sd;
+                nearest_obstacle(prim, ns, nb, M, sp, sd, bid);
+            }
+            const float gr = (on && a.g_r) ? a.g_r[o] : 0.f;
+            if (on) {
+                const float* tg = a.targets + 3 * (size_t)i;
+                const float e[3] = {sp[0] - tg[0], sp[1] - tg[1], sp[2] - tg[2]};
+                const float ne = sqrtf(dot3(e, e));
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    const float dpos = a.c.pos_sq ? 2.f * e[k] : (ne > 0.f ? e[k] / ne : 0.f);
+                    gp[k] += -gr * a.c.w_pos * dpos;
+                }
+                if (a.c.w_obs != 0.f && bid >= 0) {
+                    const float sd = sdf_prim(prim, ns, bid, sp);
+                    const float ob = relu(a.c.d_safe - sd);
+                    if (ob > 0.f) {
+                        float gsd[3];
+                        sdf_prim_grad(prim, ns, bid, sp, gsd);
+#pragma unroll
+                        for (int k = 0; k < 3; ++k) gp[k] += gr * 2.f * a.c.w_obs * ob * gsd[k];
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < 4; ++k) ga[k] += -2.f * a.c.w_act * gr * act[k];
+            }
+            for (int n = 0; n < M; ++n) {
+                const float px = __shfl_sync(0xffffffffu, sp[0], n), py = __shfl_sync(0xffffffffu, sp[1], n),
+                            pz = __shfl_sync(0xffffffffu, sp[2], n), grn = __shfl_sync(0xffffffffu, gr, n);
+                if (n == lane || !on) continue;
+                const float dd[3] = {sp[0] - px, sp[1] - py, sp[2] - pz};
+                const float dij = sqrtf(dot3(dd, dd));
+                const float sv = relu(a.c.d_agent - dij);
+                if (sv > 0.f && dij > 0.f) {
+                    const float gsum = (gr + grn) * 2.f * a.c.w_agent * sv / dij;
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) gp[k] += gsum * dd[k];
+                }
+            }
+            // dynamics
+            if (a.c.model == MODEL_RIGID) rb_step_vjp(a.c, s0, act, gp, gs, ga);
+            else pm_step_vjp(a.c, drag, lam, act, gp, gs, ga);
+            if (on)
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    if (k < A) a.g_a[o * A + k] = ga[k];
+#pragma unroll
+            for (int k = 0; k < 16; ++k) g[k] = gs[k];
+        }
+        __syncwarp();
+    }
+    if (on && a.g_s0)
+        for (int k = 0; k < D; ++k) a.g_s0[(size_t)i * D + k] = g[k];
+}
+
+// ------------------------------------------------------------ launchers
+constexpr int kPhysWarps = 4;
+
+cudaError_t launch_physics(const Args& a, cudaStream_t st) {
+    const int blocks = (a.N + kPhysWarps - 1) / kPhysWarps;
+    k_physics<<<blocks, 32 * kPhysWarps, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+// Warps per CTA of the physics adjoint and its dynamic shared memory.
+void physics_bwd_shape(int K, int M, int* warps, size_t* smem) {
+    const size_t per = (size_t)(K + 1) * M * 16 * sizeof(float);
+    int w = kPhysWarps;
+    while (w > 1 && (size_t)w * per > 96 * 1024) --w;
+    *warps = w;
+    *smem = (size_t)w * per;
+}
+
+cudaError_t launch_physics_bwd(const Args& a, cudaStream_t st) {
+    int w;
+    size_t smem;
+    physics_bwd_shape(a.K, a.M, &w, &smem);
+    cudaError_t e = cudaFuncSetAttribute(k_physics_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_physics_bwd<<<(a.N + w - 1) / w, 32 * w, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <int RPT>
+static cudaError_t render_rpt(bool vjp, bool launch, const Args& a, int grid, int block, size_t smem,
+                              cudaStream_t st, int* occ) {
+    cudaError_t e;
+    if (vjp) {
+        e = cudaFuncSetAttribute(k_render_vjp<RPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        if (!launch) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k_render_vjp<RPT>, block, smem);
+        k_render_vjp<RPT><<<grid, block, smem, st>>>(a);
+    } else {
+        e = cudaFuncSetAttribute(k_render<RPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        if (!launch) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k_render<RPT>, block, smem);
+        k_render<RPT><<<grid, block, smem, st>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t render_call(bool vjp, bool launch, int rpt, const Args& a, int grid, int block, size_t smem,
+                        cudaStream_t st, int* occ) {
+    switch (rpt) {
+        case 1: return render_rpt<1>(vjp, launch, a, grid, block, smem, st, occ);
+        case 2: return render_rpt<2>(vjp, launch, a, grid, block, smem, st, occ);
+        case 3: return render_rpt<3>(vjp, launch, a, grid, block, smem, st, occ);
+        case 4: return render_rpt<4>(vjp, launch, a, grid, block, smem, st, occ);
+        case 5: return render_rpt<5>(vjp, launch, a, grid, block, smem, st, occ);
+        case 6: return render_rpt<6>(vjp, launch, a, grid, block, smem, st, occ);
+        case 8: return render_rpt<8>(vjp, launch, a, grid, block, smem, st, occ);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace ds

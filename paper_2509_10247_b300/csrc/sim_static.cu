@@ -15,14 +15,15 @@
 
 namespace ds {
 bool rpt_supported(int rpt);
-cudaError_t launch_sim(bool adjoint, int rpt, const Args& a, int grid, int block, size_t smem, cudaStream_t st);
-cudaError_t occupancy_sim(bool adjoint, int rpt, int block, size_t smem, int* n);
+cudaError_t launch_fused(int rpt, const Args& a, int grid, int block, size_t smem, cudaStream_t st);
+cudaError_t occupancy_fused(int rpt, int block, size_t smem, int* n);
 }  // namespace ds
 
 namespace {
 
 // Scratch layout: [0, 64) control words (work ticket, status, 4 counters),
-// then the camera ray table and the LiDAR ray table (float4 per ray).
+// then the camera and LiDAR ray tables (float4 per ray), then their clamp
+// distances (float per ray).
 constexpr size_t kScratchBytes = SIM_STATIC_SCRATCH_BYTES;
 constexpr size_t kCtrlBytes = 64;
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
@@ -50,8 +51,8 @@ int scratch_ptr(int dev, unsigned char** out) {
 
 // Body-frame ray directions (x, y, z) and output factor w, in double then
 // rounded, with the same camera and LiDAR models as sim_create.
-__global__ void k_fill_rays(float4* cam, int W, int H, double th, float4* lid, int C, int Az, double el_lo,
-                            double el_hi) {
+__global__ void k_fill_rays(float4* cam, float* cam_t, int W, int H, double th, double range_c, float4* lid,
+                            float* lid_t, int C, int Az, double el_lo, double el_hi, float range_l) {
     const int Rc = W * H, Rl = C * Az;
     for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < Rc + Rl; r += gridDim.x * blockDim.x) {
         if (r < Rc) {
@@ -60,11 +61,13 @@ __global__ void k_fill_rays(float4* cam, int W, int H, double th, float4* lid, i
             const double u = (2.0 * (i + 0.5) / W - 1.0) * th, v = (2.0 * (j + 0.5) / H - 1.0) * tv;
             const double n = sqrt(1.0 + u * u + v * v);
             cam[r] = make_float4((float)(1.0 / n), (float)(-u / n), (float)(-v / n), (float)(1.0 / n));
+            cam_t[r] = (float)(range_c * n);
         } else {
             const int q = r - Rc, ch = q / Az, k = q - ch * Az;
             const double el = C > 1 ? el_lo + ch * (el_hi - el_lo) / (C - 1) : 0.5 * (el_lo + el_hi);
             const double az = 2.0 * M_PI * k / Az;
             lid[q] = make_float4((float)(cos(el) * cos(az)), (float)(cos(el) * sin(az)), (float)sin(el), 1.f);
+            lid_t[q] = range_l;
         }
     }
 }
@@ -106,7 +109,7 @@ extern "C" int sim_step_static(const sim_config* cfg, const float* prims, const 
     const int Rc = cfg->cam_w > 0 ? cfg->cam_w * cfg->cam_h : 0;
     const int Rl = cfg->lid_ch > 0 ? cfg->lid_ch * cfg->lid_az : 0;
     // the ray tables must fit the static scratch next to the control words
-    if (kCtrlBytes + 16 * ((size_t)Rc + Rl) > kScratchBytes) return SIM_ERR_SIZE;
+    if (kCtrlBytes + 20 * ((size_t)Rc + Rl) > kScratchBytes) return SIM_ERR_SIZE;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return SIM_ERR_CUDA;
@@ -135,13 +138,15 @@ extern "C" int sim_step_static(const sim_config* cfg, const float* prims, const 
     // sensors: tables in scratch, same models and culling constants as sim_create
     float4* cam = reinterpret_cast<float4*>(base + kCtrlBytes);
     float4* lid = cam + Rc;
+    float* cam_t = reinterpret_cast<float*>(lid + Rl);
+    float* lid_t = cam_t + Rc;
     int S = 0;
     if (Rc) {
         const double th = std::tan(0.5 * (double)c.cam_hfov), tv = th * c.cam_h / c.cam_w;
         const double u = (1.0 - 1.0 / c.cam_w) * th, v = (1.0 - 1.0 / c.cam_h) * tv;
         const double fmin = 1.0 / std::sqrt(1.0 + u * u + v * v);
         ds::Sensor& s = a.sen[S++];
-        s.R = Rc; s.dir = cam; s.range = c.cam_range; s.kind = 0;
+        s.R = Rc; s.dir = cam; s.tmax = cam_t; s.range = c.cam_range; s.kind = 0;
         s.c0 = (float)th; s.c1 = (float)tv;
         s.c2 = (float)(1.0 / std::sqrt(1.0 + th * th)); s.c3 = (float)(1.0 / std::sqrt(1.0 + tv * tv));
         s.maxlen = (float)(c.cam_range / fmin);
@@ -149,7 +154,7 @@ extern "C" int sim_step_static(const sim_config* cfg, const float* prims, const 
     }
     if (Rl) {
         ds::Sensor& s = a.sen[S++];
-        s.R = Rl; s.dir = lid; s.range = c.lid_range; s.kind = 1;
+        s.R = Rl; s.dir = lid; s.tmax = lid_t; s.range = c.lid_range; s.kind = 1;
         s.c0 = c.lid_elev_lo; s.c1 = c.lid_elev_hi; s.maxlen = c.lid_range;
         s.out = lidar;
     }
@@ -186,7 +191,7 @@ extern "C" int sim_step_static(const sim_config* cfg, const float* prims, const 
     const int nw = c.warps_per_cta ? c.warps_per_cta : 8;
     const int rpt = c.rays_per_thread ? c.rays_per_thread : 4;
     int occ = 0;
-    if (ds::occupancy_sim(false, rpt, 32 * nw, a.sm.total, &occ) != cudaSuccess || occ < 1) {
+    if (ds::occupancy_fused(rpt, 32 * nw, a.sm.total, &occ) != cudaSuccess || occ < 1) {
         cudaGetLastError();
         return SIM_ERR_UNSUPPORTED;
     }
@@ -195,11 +200,13 @@ extern "C" int sim_step_static(const sim_config* cfg, const float* prims, const 
     // the previous call's contents)
     if (cudaMemsetAsync(base, 0, kCtrlBytes, st) != cudaSuccess) return SIM_ERR_CUDA;
     if (Rc + Rl) {
-        k_fill_rays<<<(Rc + Rl + 255) / 256, 256, 0, st>>>(cam, c.cam_w, c.cam_h, std::tan(0.5 * (double)c.cam_hfov),
-                                                           lid, c.lid_ch, c.lid_az, c.lid_elev_lo, c.lid_elev_hi);
+        k_fill_rays<<<(Rc + Rl + 255) / 256, 256, 0, st>>>(cam, cam_t, c.cam_w, c.cam_h,
+                                                           std::tan(0.5 * (double)c.cam_hfov), (double)c.cam_range,
+                                                           lid, lid_t, c.lid_ch, c.lid_az, c.lid_elev_lo,
+                                                           c.lid_elev_hi, c.lid_range);
         if (cudaGetLastError() != cudaSuccess) return SIM_ERR_CUDA;
     }
-    e = ds::launch_sim(false, rpt, a, grid, 32 * nw, a.sm.total, st);
+    e = ds::launch_fused(rpt, a, grid, 32 * nw, a.sm.total, st);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return SIM_ERR_CUDA;
