@@ -134,7 +134,7 @@ def make_config(p, **ex):
     c.terminate, c.pool_size = int(p["terminate"]), p["pool_size"]
     c.ckpt_every = ex.get("ckpt_every", p.get("ckpt_every", 16))
     c.tape_hits = ex.get("tape_hits", -1)
-    c.cull = ex.get("cull", 1)
+    c.cull = ex.get("cull", -1)
     c.warps_per_cta = ex.get("warps_per_cta", 0)
     c.rays_per_thread = ex.get("rays_per_thread", 0)
     c.ctas_per_sm = ex.get("ctas_per_sm", 0)

@@ -39,6 +39,15 @@ struct sim_handle {
     // sensors
     float4 *d_cam = nullptr, *d_lid = nullptr;
     float *d_cam_tmax = nullptr, *d_lid_tmax = nullptr;
+    std::vector<float4> h_dirs[ds::MAX_SENSORS];     // host copies of the body-frame ray tables
+    std::vector<float> h_tmax[ds::MAX_SENSORS];
+    int img_w[ds::MAX_SENSORS] = {0, 0}, img_h[ds::MAX_SENSORS] = {0, 0};  // ray grid (camera W x H, LiDAR Az x C)
+    float4* d_cone[ds::MAX_SENSORS] = {nullptr, nullptr};
+    float* d_cone_sin[ds::MAX_SENSORS] = {nullptr, nullptr};
+    float4* d_dirp[ds::MAX_SENSORS] = {nullptr, nullptr};  // tile-ordered ray tables of the render kernels
+    float* d_tmaxp[ds::MAX_SENSORS] = {nullptr, nullptr};
+    int* d_pix[ds::MAX_SENSORS] = {nullptr, nullptr};
+    int cull_mode = 1;
     ds::Sensor sen[ds::MAX_SENSORS];
     // state and records
     float* d_state = nullptr;
@@ -129,7 +138,7 @@ int validate(const sim_config* c) {
     }
     if (c->pool_size < 0 || c->ckpt_every < 0) return SIM_ERR_SIZE;
     if (c->terminate != 0 && c->terminate != 1) return SIM_ERR_INVALID_ARG;
-    if (c->tape_hits < -1 || c->tape_hits > 1 || (c->cull != 0 && c->cull != 1)) return SIM_ERR_INVALID_ARG;
+    if (c->tape_hits < -1 || c->tape_hits > 1 || c->cull < -1 || c->cull > 2) return SIM_ERR_INVALID_ARG;
     if (c->warps_per_cta < 0 || c->warps_per_cta > 8) return SIM_ERR_INVALID_ARG;
     {
         // the physics adjoint keeps a segment of (K + 1) states per agent in shared memory
@@ -192,9 +201,78 @@ int grid_of(sim_handle* h, bool vjp, const ds::Smem& sm, int* grid) {
     return SIM_OK;
 }
 
+// Ray order of the render kernels: the sensor's ray grid is cut into tiles
+// of 32 * rpt rays (tw x th, tw >= th), taken tile by tile, so that each
+// chunk of a warp pass covers a compact patch of directions.  Each chunk's
+// cone (body frame): axis = normalised mean direction, half-angle = largest
+// angle to the axis + 2 mrad.  Tables are uploaded in that order with the
+// output index of every slot.  Returns the mean cone half-angle (rad).
+int build_tables(sim_handle* h, int s, double* mean_angle) {
+    const int cs = 32 * h->rpt, W = h->img_w[s], H = h->img_h[s];
+    int tw = 1;
+    while (tw * tw < cs) tw <<= 1;
+    int th = std::max(1, cs / tw);
+    std::vector<int> order;
+    order.reserve((size_t)W * H);
+    for (int ty = 0; ty < H; ty += th)
+        for (int tx = 0; tx < W; tx += tw)
+            for (int y = ty; y < std::min(H, ty + th); ++y)
+                for (int x = tx; x < std::min(W, tx + tw); ++x) order.push_back(y * W + x);
+    const std::vector<float4>& d0 = h->h_dirs[s];
+    const int R = (int)order.size(), n = (R + cs - 1) / cs;
+    std::vector<float4> dirp(R), cone(n);
+    std::vector<float> tp(R), sn(n);
+    for (int j = 0; j < R; ++j) { dirp[j] = d0[order[j]]; tp[j] = h->h_tmax[s][order[j]]; }
+    double sum = 0.0;
+    for (int c = 0; c < n; ++c) {
+        const int r0 = c * cs, r1 = std::min(R, r0 + cs);
+        double ax = 0, ay = 0, az = 0;
+        for (int r = r0; r < r1; ++r) { ax += dirp[r].x; ay += dirp[r].y; az += dirp[r].z; }
+        const double nn = std::sqrt(ax * ax + ay * ay + az * az);
+        double cmin = -1.0;
+        if (nn > 1e-9) {
+            ax /= nn; ay /= nn; az /= nn;
+            cmin = 1.0;
+            for (int r = r0; r < r1; ++r)
+                cmin = std::min(cmin, (double)dirp[r].x * ax + (double)dirp[r].y * ay + (double)dirp[r].z * az);
+        } else {
+            ax = 1; ay = 0; az = 0;
+        }
+        const double th_c = std::min(std::acos(std::max(-1.0, std::min(1.0, cmin))) + 2e-3, M_PI);
+        sum += th_c;
+        cone[c] = make_float4((float)ax, (float)ay, (float)az, (float)std::cos(th_c));
+        sn[c] = (float)std::sin(th_c);
+    }
+    *mean_angle = sum / n;
+    dfree(h->d_cone[s]); dfree(h->d_cone_sin[s]); dfree(h->d_dirp[s]); dfree(h->d_tmaxp[s]); dfree(h->d_pix[s]);
+    int rc;
+    if ((rc = dalloc(h, &h->d_cone[s], n)) || (rc = dalloc(h, &h->d_cone_sin[s], n)) || (rc = dalloc(h, &h->d_dirp[s], R)) ||
+        (rc = dalloc(h, &h->d_tmaxp[s], R)) || (rc = dalloc(h, &h->d_pix[s], R)))
+        return rc;
+    CK(cudaMemcpy(h->d_cone[s], cone.data(), n * sizeof(float4), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(h->d_cone_sin[s], sn.data(), n * sizeof(float), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(h->d_dirp[s], dirp.data(), R * sizeof(float4), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(h->d_tmaxp[s], tp.data(), R * sizeof(float), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(h->d_pix[s], order.data(), R * sizeof(int), cudaMemcpyHostToDevice));
+    bool identity = true;
+    for (int j = 0; j < R && identity; ++j) identity = order[j] == j;
+    if (identity) dfree(h->d_pix[s]);  // natural order: no index table
+    return SIM_OK;
+}
+
 int configure_launch(sim_handle* h) {
     h->nw = h->cfg.warps_per_cta ? h->cfg.warps_per_cta : 8;
     h->rpt = pick_rpt(h);
+    // culling: 0 off, 1 sensor frustum, 2 frustum + chunk cones; auto enables
+    // the cones when they are narrow (mean half-angle below 0.35 rad)
+    double widest = 0.0;
+    for (int s = 0; s < h->S; ++s) {
+        double ang = 0.0;
+        int rc = build_tables(h, s, &ang);
+        if (rc) return rc;
+        widest = std::max(widest, ang);
+    }
+    h->cull_mode = h->cfg.cull >= 0 ? h->cfg.cull : (widest < 0.35 ? 2 : 1);
     h->sm_r = layout_render(h, h->S > 0);
     h->sm_rv = layout_render(h, h->S > 0 && !h->tape);
     h->sm_rvs = layout_render(h, h->S > 0);
@@ -228,8 +306,17 @@ Args base_args(const sim_handle* h) {
     a.c.success_radius = c.success_radius; a.c.r_quad = c.r_quad;
     a.c.terminate = c.terminate; a.c.P = h->have_pool ? c.pool_size : 0;
     a.N = h->N; a.M = h->M; a.NM = h->NM; a.T = h->T; a.K = h->K; a.S = h->S;
-    a.ns_max = h->ns_max; a.nb_max = h->nb_max; a.cull = c.cull;
-    for (int s = 0; s < ds::MAX_SENSORS; ++s) a.sen[s] = h->sen[s];
+    a.ns_max = h->ns_max; a.nb_max = h->nb_max; a.cull = h->cull_mode;
+    for (int s = 0; s < ds::MAX_SENSORS; ++s) {
+        a.sen[s] = h->sen[s];
+        if (s < h->S) {  // the render kernels read the tile-ordered tables
+            a.sen[s].dir = h->d_dirp[s];
+            a.sen[s].tmax = h->d_tmaxp[s];
+            a.sen[s].pix = h->d_pix[s];
+            a.sen[s].cone = h->d_cone[s];
+            a.sen[s].cone_sin = h->d_cone_sin[s];
+        }
+    }
     a.prims = h->d_prims; a.map_off = h->d_map_off; a.map_ns = h->d_map_ns; a.map_nb = h->d_map_nb;
     a.env_map = h->d_env_map; a.order = h->d_order; a.targets = h->d_targets;
     a.pool = h->have_pool ? h->d_pool : nullptr;
@@ -330,6 +417,9 @@ int sim_destroy(sim_handle* h) {
     dfree(h->d_env_map); dfree(h->d_order); dfree(h->d_targets); dfree(h->d_pool);
     dfree(h->d_drag); dfree(h->d_lam); dfree(h->d_cam); dfree(h->d_lid);
     dfree(h->d_cam_tmax); dfree(h->d_lid_tmax);
+    for (int s = 0; s < ds::MAX_SENSORS; ++s) {
+        dfree(h->d_cone[s]); dfree(h->d_cone_sin[s]); dfree(h->d_dirp[s]); dfree(h->d_tmaxp[s]); dfree(h->d_pix[s]);
+    }
     dfree(h->d_state); dfree(h->d_pool_k); dfree(h->d_ckpt); dfree(h->d_ckpt_k);
     dfree(h->d_done_tape); dfree(h->d_sdf_tape); dfree(h->d_tape_cam); dfree(h->d_tape_lid);
     dfree(h->d_poses); dfree(h->d_gposes); dfree(h->d_pose1); dfree(h->d_gpose1); dfree(h->d_state2);
@@ -372,6 +462,10 @@ int sim_create(const sim_config* cfg, sim_handle** out) {
         TRY(cuda_err(cudaMemcpy(h->d_cam, cam.data(), cam.size() * sizeof(float4), cudaMemcpyHostToDevice)));
         TRY(cuda_err(cudaMemcpy(h->d_cam_tmax, cam_t.data(), cam_t.size() * sizeof(float), cudaMemcpyHostToDevice)));
         h->sen[s].dir = h->d_cam;
+        h->h_dirs[s] = cam;
+        h->h_tmax[s] = cam_t;
+        h->img_w[s] = cfg->cam_w;
+        h->img_h[s] = cfg->cam_h;
         h->sen[s++].tmax = h->d_cam_tmax;
     }
     if (h->Rl) {
@@ -380,6 +474,10 @@ int sim_create(const sim_config* cfg, sim_handle** out) {
         TRY(cuda_err(cudaMemcpy(h->d_lid, lid.data(), lid.size() * sizeof(float4), cudaMemcpyHostToDevice)));
         TRY(cuda_err(cudaMemcpy(h->d_lid_tmax, lid_t.data(), lid_t.size() * sizeof(float), cudaMemcpyHostToDevice)));
         h->sen[s].dir = h->d_lid;
+        h->h_dirs[s] = lid;
+        h->h_tmax[s] = lid_t;
+        h->img_w[s] = cfg->lid_az;
+        h->img_h[s] = cfg->lid_ch;
         h->sen[s++].tmax = h->d_lid_tmax;
     }
     const size_t tape_bytes = (size_t)h->T * h->NM * (h->Rc + h->Rl) * 2;

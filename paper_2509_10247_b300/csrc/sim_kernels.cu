@@ -23,7 +23,7 @@ namespace ds {
 __device__ inline WList fused_list(const Args& a, unsigned char* sm, int Lx) {
     WList L;
     L.sph = reinterpret_cast<float4*>(sm + a.sm.lsph) + (size_t)Lx * a.ns_max;
-    L.r2 = reinterpret_cast<float*>(sm + a.sm.lr2) + (size_t)Lx * a.ns_max;
+    L.sx = reinterpret_cast<float2*>(sm + a.sm.lr2) + (size_t)Lx * a.ns_max;
     L.box = reinterpret_cast<float4*>(sm + a.sm.lbox) + (size_t)Lx * a.nb_max * 2;
     L.id = reinterpret_cast<short*>(sm + a.sm.lid) + (size_t)Lx * (a.ns_max + a.nb_max);
     L.meta = reinterpret_cast<int4*>(sm + a.sm.lmeta) + Lx;

@@ -12,6 +12,9 @@ struct Sensor {
     int R;                 // rays per agent
     const float4* dir;     // [R] body-frame unit direction (x, y, z) and output factor w
     const float* tmax;     // [R] ray length at the output clamp (range / w camera, range LiDAR)
+    const int* pix;        // [R] output ray index of each table slot (tile order), nullptr: identity
+    const float4* cone;    // [chunks] cone of each chunk of 32 x rays-per-thread slots: axis, cos
+    const float* cone_sin; // [chunks] sin of the cone's half-angle
     float range;           // output clamp
     int kind;              // 0 camera frustum cull, 1 LiDAR elevation-band cull
     float c0, c1, c2, c3;  // camera: tan_h, tan_v, 1/sqrt(1+tan_h^2), 1/sqrt(1+tan_v^2)
@@ -25,9 +28,9 @@ struct Sensor {
 // Byte offsets of the dynamic shared-memory regions of one CTA.
 struct Smem {
     int prim;    // float4 [ns_max + 2 nb_max]     map block
-    int lsph;    // float4 [L][ns_max]             (oc.xyz, C) per culled sphere
-    int lr2;     // float  [L][ns_max]             r^2 per culled sphere
-    int lbox;    // float4 [L][nb_max][2]          (lo - o, hi - o) per culled box
+    int lsph;    // float4 [L][ns_max]             (oc.xyz, -sqrt(C)) per culled sphere
+    int lr2;     // float2 [L][ns_max]             (C, r) per culled sphere
+    int lbox;    // float4 [L][nb_max][2]          (centre - o, half extents) per culled box
     int lid;     // short  [L][ns_max + nb_max]    primitive id of each list entry
     int lmeta;   // int4   [L]                     (n_sph, n_box, inside_id, 0)
     int st;      // float  [M][16]                 current state

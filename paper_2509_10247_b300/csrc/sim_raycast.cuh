@@ -10,22 +10,30 @@
 namespace ds {
 
 // One culled list of an (agent, sensor) pair, origin-relative:
-//   sph [ns_max] float4 (oc.xyz, C = |oc|^2 - r^2), r2 [ns_max] float (r^2),
-//   box [nb_max][2] float4 (lo - o, hi - o), id [ns_max + nb_max] short
-//   (map primitive id of each slot; boxes from slot ns_max), meta int4
-//   (kept spheres, kept boxes, lowest id of a primitive containing the
-//   origin or -1, 0).
+//   sph [ns_max] float4 (oc.xyz, -sqrt(C)) with C = |oc|^2 - r^2 (sqrt(C) is
+//       the tangent length: a ray reaches the sphere iff d.oc >= sqrt(C),
+//       and then hits it no farther than sqrt(C)),
+//   sx  [ns_max] float2 (C, r),
+//   box [nb_max][2] float4 (centre - o, tangent length of the bounding
+//       sphere or -1e30 when the origin is inside it), (half extents, radius
+//       of the bounding sphere),
+//   id  [ns_max + nb_max] short (map primitive id of each slot; boxes from
+//       slot ns_max),
+//   sub [ns_max + nb_max] short (slots kept for the current ray chunk),
+//   meta int4 (kept spheres, kept boxes, lowest id of a primitive containing
+//       the origin or -1, 0).
 struct WList {
     float4* sph;
-    float* r2;
+    float2* sx;
     float4* box;
     short* id;
+    short* sub;
     int4* meta;
 };
 
 // Bytes of one list laid out contiguously (16-byte aligned parts).
 __host__ __device__ inline size_t wlist_bytes(int ns_max, int nb_max) {
-    size_t b = (size_t)16 * (ns_max + 2 * nb_max) + 4 * (size_t)ns_max + 2 * (size_t)(ns_max + nb_max);
+    size_t b = (size_t)16 * (ns_max + 2 * nb_max) + 8 * (size_t)ns_max + 4 * (size_t)(ns_max + nb_max);
     return ((b + 15) & ~size_t(15)) + 16;
 }
 
@@ -33,11 +41,39 @@ __device__ inline WList wlist_at(unsigned char* p, int ns_max, int nb_max) {
     WList L;
     L.sph = reinterpret_cast<float4*>(p);
     L.box = L.sph + ns_max;
-    L.r2 = reinterpret_cast<float*>(L.box + 2 * nb_max);
-    L.id = reinterpret_cast<short*>(L.r2 + ns_max);
-    size_t b = (size_t)16 * (ns_max + 2 * nb_max) + 4 * (size_t)ns_max + 2 * (size_t)(ns_max + nb_max);
+    L.sx = reinterpret_cast<float2*>(L.box + 2 * nb_max);
+    L.id = reinterpret_cast<short*>(L.sx + ns_max);
+    L.sub = L.id + ns_max + nb_max;
+    size_t b = (size_t)16 * (ns_max + 2 * nb_max) + 8 * (size_t)ns_max + 4 * (size_t)(ns_max + nb_max);
     L.meta = reinterpret_cast<int4*>(p + ((b + 15) & ~size_t(15)));
     return L;
+}
+
+__device__ __forceinline__ float min3f(float x, float y, float z) {
+    float r;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(x), "f"(y), "f"(z));
+    return r;
+}
+
+__device__ __forceinline__ float max3f(float x, float y, float z) {
+    float r;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(x), "f"(y), "f"(z));
+    return r;
+}
+
+// Box relative to an origin, in the centre / half-extent form the slab test uses.
+__device__ __forceinline__ void box_rel(const float4& bl, const float4& bh, const float* o, float* c, float* h) {
+    c[0] = 0.5f * (bl.x + bh.x) - o[0];
+    c[1] = 0.5f * (bl.y + bh.y) - o[1];
+    c[2] = 0.5f * (bl.z + bh.z) - o[2];
+    h[0] = 0.5f * (bh.x - bl.x);
+    h[1] = 0.5f * (bh.y - bl.y);
+    h[2] = 0.5f * (bh.z - bl.z);
+}
+
+// Correctly rounded reciprocal of a direction component kept away from 0.
+__device__ __forceinline__ float safe_rcp(float d) {
+    return __frcp_rn(fabsf(d) < 1e-20f ? copysignf(1e-20f, d) : d);
 }
 
 // Cull the map (ns spheres then nb boxes at prim) for the sensor at origin o
@@ -51,21 +87,22 @@ __device__ inline int4 warp_build_list(const float4* prim, int ns, int nb, const
         const int k = base + lane;
         bool keep = false;
         float4 e = make_float4(0.f, 0.f, 0.f, 0.f);
-        float r2 = 0.f;
+        float2 x = make_float2(0.f, 0.f);
         if (k < ns) {
             float4 sp = prim[k];
             float oc[3] = {sp.x - o[0], sp.y - o[1], sp.z - o[2]};
-            r2 = sp.w * sp.w;
-            float C = dot3(oc, oc) - r2;
+            const float r2 = sp.w * sp.w;
+            const float C = dot3(oc, oc) - r2;
             if (C <= 0.f) inside = min(inside, k);
             keep = !cull || cull_keep(sen, R, oc, sp.w);
-            e = make_float4(oc[0], oc[1], oc[2], C);
+            e = make_float4(oc[0], oc[1], oc[2], -sqrtf(fmaxf(C, 0.f)));
+            x = make_float2(C, sp.w);
         }
         unsigned bal = __ballot_sync(0xffffffffu, keep);
         if (keep) {
             int pos = cnt + __popc(bal & ((1u << lane) - 1u));
             L.sph[pos] = e;
-            L.r2[pos] = r2;
+            L.sx[pos] = x;
             L.id[pos] = (short)k;
         }
         cnt += __popc(bal);
@@ -75,22 +112,24 @@ __device__ inline int4 warp_build_list(const float4* prim, int ns, int nb, const
     for (int base = 0; base < nb; base += 32) {
         const int k = base + lane;
         bool keep = false;
-        float4 lo = make_float4(0.f, 0.f, 0.f, 0.f), hi = lo;
+        float4 cc = make_float4(0.f, 0.f, 0.f, 0.f), hh = cc;
         if (k < nb) {
-            float4 bl = prim[ns + 2 * k], bh = prim[ns + 2 * k + 1];
-            lo = make_float4(bl.x - o[0], bl.y - o[1], bl.z - o[2], 0.f);
-            hi = make_float4(bh.x - o[0], bh.y - o[1], bh.z - o[2], 0.f);
-            if (lo.x <= 0.f && hi.x >= 0.f && lo.y <= 0.f && hi.y >= 0.f && lo.z <= 0.f && hi.z >= 0.f)
+            const float4 bl = prim[ns + 2 * k], bh = prim[ns + 2 * k + 1];
+            if (bl.x <= o[0] && bh.x >= o[0] && bl.y <= o[1] && bh.y >= o[1] && bl.z <= o[2] && bh.z >= o[2])
                 inside = min(inside, ns + k);
-            float c[3] = {0.5f * (lo.x + hi.x), 0.5f * (lo.y + hi.y), 0.5f * (lo.z + hi.z)};
-            float h[3] = {0.5f * (hi.x - lo.x), 0.5f * (hi.y - lo.y), 0.5f * (hi.z - lo.z)};
-            keep = !cull || cull_keep(sen, R, c, sqrtf(dot3(h, h)));
+            float c[3], h[3];
+            box_rel(bl, bh, o, c, h);
+            const float rho = sqrtf(dot3(h, h));
+            keep = !cull || cull_keep(sen, R, c, rho);
+            const float cb = dot3(c, c) - rho * rho;
+            cc = make_float4(c[0], c[1], c[2], cb > 0.f ? sqrtf(cb) : -1e30f);
+            hh = make_float4(h[0], h[1], h[2], rho);
         }
         unsigned bal = __ballot_sync(0xffffffffu, keep);
         if (keep) {
             int pos = cnt + __popc(bal & ((1u << lane) - 1u));
-            L.box[2 * pos] = lo;
-            L.box[2 * pos + 1] = hi;
+            L.box[2 * pos] = cc;
+            L.box[2 * pos + 1] = hh;
             L.id[ns_max + pos] = (short)(ns + k);
         }
         cnt += __popc(bal);
@@ -105,9 +144,10 @@ __device__ inline int4 warp_build_list(const float4* prim, int ns, int nb, const
 
 // Sweep RPT rays per lane over a list.  tb holds each ray's best distance
 // (start: its clamp distance), bi the list slot of the best hit (spheres
-// 0.., boxes ns_max..).  Spheres: the ray misses or cannot beat tb unless
-// disc >= min(tb - b, 0)^2 and b >= 0, then the root is refined with the
-// perpendicular-offset form.  Boxes: slabs with correctly rounded reciprocals.
+// 0.., boxes ns_max..).  Sphere: one dot product decides whether the ray
+// reaches the sphere (d.oc - sqrt(C) >= 0); only then is the near root found
+// (perpendicular-offset form) and compared with tb.  Box: slab times in
+// centre / half-extent form, t = c/d -+ h/|d|, entry = max, exit = min.
 template <int RPT>
 __device__ __forceinline__ void cast_list(const WList& L, const int4& meta, int ns_max, const float* dx,
                                           const float* dy, const float* dz, float* tb, int* bi) {
@@ -115,40 +155,136 @@ __device__ __forceinline__ void cast_list(const WList& L, const int4& meta, int 
         const float4 e = L.sph[k];
 #pragma unroll
         for (int r = 0; r < RPT; ++r) {
-            float b = fmaf(dx[r], e.x, fmaf(dy[r], e.y, dz[r] * e.z));
-            float disc = fmaf(b, b, -e.w);
-            float gg = fminf(tb[r] - b, 0.f);
-            float h = fmaf(-gg, gg, disc);
-            if (fminf(h, b) >= 0.f) {
-                float fx = fmaf(-b, dx[r], e.x), fy = fmaf(-b, dy[r], e.y), fz = fmaf(-b, dz[r], e.z);
-                float d2 = fmaxf(L.r2[k] - fmaf(fx, fx, fmaf(fy, fy, fz * fz)), 0.f);
-                float t = e.w / (b + sqrtf(d2));
+            const float v = fmaf(dx[r], e.x, fmaf(dy[r], e.y, fmaf(dz[r], e.z, e.w)));
+            if (v >= 0.f) {
+                const float2 x = L.sx[k];
+                const float b = v - e.w;
+                const float fx = fmaf(-b, dx[r], e.x), fy = fmaf(-b, dy[r], e.y), fz = fmaf(-b, dz[r], e.z);
+                const float d2 = fmaxf(x.y * x.y - fmaf(fx, fx, fmaf(fy, fy, fz * fz)), 0.f);
+                const float t = b - sqrtf(d2);
                 if (t < tb[r]) { tb[r] = t; bi[r] = k; }
             }
         }
     }
     if (meta.y > 0) {
-        float ix[RPT], iy[RPT], iz[RPT];
+        float ix[RPT], iy[RPT], iz[RPT], ax[RPT], ay[RPT], az[RPT];
 #pragma unroll
         for (int r = 0; r < RPT; ++r) {
-            ix[r] = __frcp_rn(fabsf(dx[r]) < 1e-20f ? copysignf(1e-20f, dx[r]) : dx[r]);
-            iy[r] = __frcp_rn(fabsf(dy[r]) < 1e-20f ? copysignf(1e-20f, dy[r]) : dy[r]);
-            iz[r] = __frcp_rn(fabsf(dz[r]) < 1e-20f ? copysignf(1e-20f, dz[r]) : dz[r]);
+            ix[r] = safe_rcp(dx[r]); iy[r] = safe_rcp(dy[r]); iz[r] = safe_rcp(dz[r]);
+            ax[r] = fabsf(ix[r]); ay[r] = fabsf(iy[r]); az[r] = fabsf(iz[r]);
         }
         for (int k = 0; k < meta.y; ++k) {
-            const float4 lo = L.box[2 * k], hi = L.box[2 * k + 1];
+            const float4 c = L.box[2 * k], h = L.box[2 * k + 1];
 #pragma unroll
             for (int r = 0; r < RPT; ++r) {
-                float t1 = lo.x * ix[r], t2 = hi.x * ix[r];
-                float t3 = lo.y * iy[r], t4 = hi.y * iy[r];
-                float t5 = lo.z * iz[r], t6 = hi.z * iz[r];
-                float tn = fmaxf(fmaxf(fminf(t1, t2), fminf(t3, t4)), fminf(t5, t6));
-                float tf = fminf(fminf(fmaxf(t1, t2), fmaxf(t3, t4)), fmaxf(t5, t6));
+                const float mx = c.x * ix[r], my = c.y * iy[r], mz = c.z * iz[r];
+                const float tn = max3f(fmaf(-h.x, ax[r], mx), fmaf(-h.y, ay[r], my), fmaf(-h.z, az[r], mz));
+                const float tf = min3f(fmaf(h.x, ax[r], mx), fmaf(h.y, ay[r], my), fmaf(h.z, az[r], mz));
                 if (tn <= tf && tn > 0.f && tn < tb[r]) { tb[r] = tn; bi[r] = ns_max + k; }
             }
         }
     }
 }
+
+// Second-level cull for one chunk of rays whose body directions lie in the
+// cone (axis cone.xyz, cos = cone.w, sin = sn); aw = R axis in the world.  A
+// sphere (or a box's bounding sphere) at oc with tangent length sC and radius
+// rho meets the cone iff oc.aw >= cos * sC - sin * rho.  Writes the kept slots
+// in index order to L.sub (spheres from 0, boxes from ns_max); one full warp.
+__device__ inline int2 warp_sub_cull(const WList& L, const int4& meta, int ns_max, const float* aw, float cs,
+                                     float sn) {
+    const int lane = threadIdx.x & 31;
+    int ns = 0, nb = 0;
+    for (int base = 0; base < meta.x; base += 32) {
+        const int k = base + lane;
+        bool keep = false;
+        if (k < meta.x) {
+            const float4 e = L.sph[k];
+            const float2 x = L.sx[k];
+            keep = fmaf(e.x, aw[0], fmaf(e.y, aw[1], fmaf(e.z, aw[2], fmaf(cs, e.w, sn * x.y)))) >= 0.f;
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, keep);
+        if (keep) L.sub[ns + __popc(bal & ((1u << lane) - 1u))] = (short)k;
+        ns += __popc(bal);
+    }
+    for (int base = 0; base < meta.y; base += 32) {
+        const int k = base + lane;
+        bool keep = false;
+        if (k < meta.y) {
+            const float4 c = L.box[2 * k], h = L.box[2 * k + 1];
+            keep = c.w < 0.f || fmaf(c.x, aw[0], fmaf(c.y, aw[1], fmaf(c.z, aw[2], fmaf(-cs, c.w, sn * h.w)))) >= 0.f;
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, keep);
+        if (keep) L.sub[ns_max + nb + __popc(bal & ((1u << lane) - 1u))] = (short)k;
+        nb += __popc(bal);
+    }
+    __syncwarp();
+    return make_int2(ns, nb);
+}
+
+// Sweep RPT rays per lane over the chunk's sub-list (same tests and order as
+// cast_list, on the kept slots only).
+template <int RPT>
+__device__ __forceinline__ void cast_sub(const WList& L, const int2& n, int ns_max, const float* dx,
+                                         const float* dy, const float* dz, float* tb, int* bi) {
+    for (int j = 0; j < n.x; ++j) {
+        const int k = L.sub[j];
+        const float4 e = L.sph[k];
+#pragma unroll
+        for (int r = 0; r < RPT; ++r) {
+            const float v = fmaf(dx[r], e.x, fmaf(dy[r], e.y, fmaf(dz[r], e.z, e.w)));
+            if (v >= 0.f) {
+                const float2 x = L.sx[k];
+                const float b = v - e.w;
+                const float fx = fmaf(-b, dx[r], e.x), fy = fmaf(-b, dy[r], e.y), fz = fmaf(-b, dz[r], e.z);
+                const float d2 = fmaxf(x.y * x.y - fmaf(fx, fx, fmaf(fy, fy, fz * fz)), 0.f);
+                const float t = b - sqrtf(d2);
+                if (t < tb[r]) { tb[r] = t; bi[r] = k; }
+            }
+        }
+    }
+    if (n.y > 0) {
+        float ix[RPT], iy[RPT], iz[RPT], ax[RPT], ay[RPT], az[RPT];
+#pragma unroll
+        for (int r = 0; r < RPT; ++r) {
+            ix[r] = safe_rcp(dx[r]); iy[r] = safe_rcp(dy[r]); iz[r] = safe_rcp(dz[r]);
+            ax[r] = fabsf(ix[r]); ay[r] = fabsf(iy[r]); az[r] = fabsf(iz[r]);
+        }
+        for (int j = 0; j < n.y; ++j) {
+            const int k = L.sub[ns_max + j];
+            const float4 c = L.box[2 * k], h = L.box[2 * k + 1];
+#pragma unroll
+            for (int r = 0; r < RPT; ++r) {
+                const float mx = c.x * ix[r], my = c.y * iy[r], mz = c.z * iz[r];
+                const float tn = max3f(fmaf(-h.x, ax[r], mx), fmaf(-h.y, ay[r], my), fmaf(-h.z, az[r], mz));
+                const float tf = min3f(fmaf(h.x, ax[r], mx), fmaf(h.y, ay[r], my), fmaf(h.z, az[r], mz));
+                if (tn <= tf && tn > 0.f && tn < tb[r]) { tb[r] = tn; bi[r] = ns_max + k; }
+            }
+        }
+    }
+}
+
+// Slots of a chunk: the sub-cull of the chunk's cone (two-level culling,
+// cull > 1) or the whole list.  Returns the sub-list counts.
+__device__ __forceinline__ int2 chunk_slots(const WList& L, const int4& meta, int ns_max, const Sensor& sen,
+                                            int cull, int ch, const float* R) {
+    const int lane = threadIdx.x & 31;
+    if (cull > 1 && sen.cone) {
+        const float4 cn = __ldg(sen.cone + ch);
+        const float sn = __ldg(sen.cone_sin + ch);
+        const float aw[3] = {fmaf(R[0], cn.x, fmaf(R[1], cn.y, R[2] * cn.z)),
+                             fmaf(R[3], cn.x, fmaf(R[4], cn.y, R[5] * cn.z)),
+                             fmaf(R[6], cn.x, fmaf(R[7], cn.y, R[8] * cn.z))};
+        return warp_sub_cull(L, meta, ns_max, aw, cn.w, sn);
+    }
+    for (int k = lane; k < meta.x; k += 32) L.sub[k] = (short)k;
+    for (int k = lane; k < meta.y; k += 32) L.sub[ns_max + k] = (short)k;
+    __syncwarp();
+    return make_int2(meta.x, meta.y);
+}
+
+// Output index of table slot j (rays are stored in tile order when pix is set).
+__device__ __forceinline__ int out_index(const Sensor& sen, int j) { return sen.pix ? __ldg(sen.pix + j) : j; }
 
 // Next work item of the warp from a shared ticket (dynamic balance).
 __device__ __forceinline__ int next_item(int* ticket, int lane) {
@@ -162,7 +298,7 @@ __device__ __forceinline__ void item_rays(const Sensor& sen, const float* R, int
                                           float* dx, float* dy, float* dz, float* fac, float* tb) {
 #pragma unroll
     for (int r = 0; r < RPT; ++r) {
-        const int ray = chunk * 32 * RPT + r * 32 + lane;
+        const int ray = chunk * 32 * RPT + r * 32 + lane;  // table slot
         const bool valid = ray < sen.R;
         float4 db = valid ? __ldg(sen.dir + ray) : make_float4(1.f, 0.f, 0.f, 1.f);
         dx[r] = fmaf(R[0], db.x, fmaf(R[1], db.y, R[2] * db.z));
@@ -220,15 +356,12 @@ __device__ __forceinline__ void ray_vjp(const float4* prim, int ns, int id, cons
         for (int k = 0; k < 3; ++k) n[k] = (t * d[k] - oc[k]) * ir;
     } else {
         const int b = id - ns;
-        const float4 lo = prim[ns + 2 * b], hi = prim[ns + 2 * b + 1];
-        const float l[3] = {lo.x - o[0], lo.y - o[1], lo.z - o[2]};
-        const float u[3] = {hi.x - o[0], hi.y - o[1], hi.z - o[2]};
-        float tl[3];
+        float c[3], h[3], tl[3];
+        box_rel(prim[ns + 2 * b], prim[ns + 2 * b + 1], o, c, h);
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            const float dk = fabsf(d[k]) < 1e-20f ? copysignf(1e-20f, d[k]) : d[k];
-            const float iv = __frcp_rn(dk);
-            tl[k] = fminf(l[k] * iv, u[k] * iv);
+            const float iv = safe_rcp(d[k]);
+            tl[k] = fmaf(-h[k], fabsf(iv), c[k] * iv);
         }
         int ax = 0;
         if (tl[1] > tl[ax]) ax = 1;

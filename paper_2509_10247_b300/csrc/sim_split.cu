@@ -197,19 +197,28 @@ __global__ void __launch_bounds__(256, 4) k_render(const Args a) {
                 item_rays<RPT>(sen, R, ch, lane, dx, dy, dz, fac, tb);
 #pragma unroll
                 for (int r = 0; r < RPT; ++r) bi[r] = -1;
-                if (meta.z < 0) cast_list<RPT>(L, meta, a.ns_max, dx, dy, dz, tb, bi);
+                int2 nsub = make_int2(meta.x, meta.y);
+                if (meta.z < 0) {
+                    if (a.cull > 1 && sen.cone) {
+                        nsub = chunk_slots(L, meta, a.ns_max, sen, a.cull, ch, R);
+                        cast_sub<RPT>(L, nsub, a.ns_max, dx, dy, dz, tb, bi);
+                    } else {
+                        cast_list<RPT>(L, meta, a.ns_max, dx, dy, dz, tb, bi);
+                    }
+                }
                 if (a.counters && lane == 0) {
                     const unsigned long long nr = (unsigned long long)min(32 * RPT, sen.R - ch * 32 * RPT);
                     if (meta.z < 0) {
-                        atomicAdd(&s_cnt[0], nr * (unsigned long long)meta.x);
-                        atomicAdd(&s_cnt[1], nr * (unsigned long long)meta.y);
+                        atomicAdd(&s_cnt[0], nr * (unsigned long long)nsub.x);
+                        atomicAdd(&s_cnt[1], nr * (unsigned long long)nsub.y);
                     }
                     atomicAdd(&s_cnt[2], nr);
                 }
 #pragma unroll
                 for (int r = 0; r < RPT; ++r) {
-                    const int ray = ch * 32 * RPT + r * 32 + lane;
-                    if (ray >= sen.R) continue;
+                    const int j = ch * 32 * RPT + r * 32 + lane;
+                    if (j >= sen.R) continue;
+                    const int ray = out_index(sen, j);
                     float v;
                     int id;
                     if (meta.z >= 0) { v = 0.f; id = meta.z; }
@@ -287,22 +296,29 @@ __global__ void __launch_bounds__(256, 3) k_render_vjp(const Args a) {
                             int bi[RPT];
 #pragma unroll
                             for (int r = 0; r < RPT; ++r) bi[r] = -1;
-                            if (meta.z < 0) cast_list<RPT>(L, meta, a.ns_max, dx, dy, dz, tb, bi);
+                            if (meta.z < 0) {
+                                if (a.cull > 1 && sen.cone) {
+                                    const int2 nsub = chunk_slots(L, meta, a.ns_max, sen, a.cull, ch, R);
+                                    cast_sub<RPT>(L, nsub, a.ns_max, dx, dy, dz, tb, bi);
+                                } else {
+                                    cast_list<RPT>(L, meta, a.ns_max, dx, dy, dz, tb, bi);
+                                }
+                            }
 #pragma unroll
                             for (int r = 0; r < RPT; ++r) id[r] = (meta.z >= 0 || bi[r] < 0) ? -1 : L.id[bi[r]];
                         } else {
 #pragma unroll
                             for (int r = 0; r < RPT; ++r) {
-                                const int ray = ch * 32 * RPT + r * 32 + lane;
-                                id[r] = ray < sen.R ? sen.tape[base + ray] : -1;
+                                const int j = ch * 32 * RPT + r * 32 + lane;
+                                id[r] = j < sen.R ? sen.tape[base + out_index(sen, j)] : -1;
                             }
                         }
 #pragma unroll
                         for (int r = 0; r < RPT; ++r) {
-                            const int ray = ch * 32 * RPT + r * 32 + lane;
-                            if (ray >= sen.R || id[r] < 0) continue;
-                            ray_vjp(prim, ns, id[r], o, dx[r], dy[r], dz[r], __ldg(sen.dir + ray), sen,
-                                    sen.gout[base + ray], go, gR);
+                            const int j = ch * 32 * RPT + r * 32 + lane;
+                            if (j >= sen.R || id[r] < 0) continue;
+                            ray_vjp(prim, ns, id[r], o, dx[r], dy[r], dz[r], __ldg(sen.dir + j), sen,
+                                    sen.gout[base + out_index(sen, j)], go, gR);
                         }
                     }
                     __syncwarp();

@@ -85,7 +85,7 @@ bool bad_cfg(const sim_config* c) {
         for (int i = 0; i < 3; ++i)
             if (!(c->inertia[i] > 0.f)) return true;
     if (c->model == SIM_MODEL_RIGID && !(c->mass > 0.f)) return true;
-    if (c->pool_size < 0 || c->cull < 0 || c->cull > 1) return true;
+    if (c->pool_size < 0 || c->cull < -1 || c->cull > 2) return true;
     if (c->warps_per_cta < 0 || c->warps_per_cta > 8) return true;
     if (c->rays_per_thread != 0 && !ds::rpt_supported(c->rays_per_thread)) return true;
     return false;
@@ -174,7 +174,7 @@ extern "C" int sim_step_static(const sim_config* cfg, const float* prims, const 
     take(a.sm.prim, (size_t)(ns_max + 2 * nb_max) * 16);
     take(a.sm.lsph, (size_t)L * ns_max * 16);
     take(a.sm.lbox, (size_t)L * nb_max * 32);
-    take(a.sm.lr2, (size_t)L * ns_max * 4);
+    take(a.sm.lr2, (size_t)L * ns_max * 8);
     take(a.sm.lid, (size_t)L * (ns_max + nb_max) * 2);
     take(a.sm.lmeta, (size_t)L * 16);
     take(a.sm.st, (size_t)M * 64);

@@ -65,7 +65,7 @@ def _create_rc(lib, cfg):
     ("model", 5, -1), ("n_env", 0, -3), ("n_agent", 0, -3), ("n_agent", 33, -3), ("horizon", 0, -3),
     ("dt", 0.0, -1), ("dt", float("nan"), -1), ("ema_alpha", 1.5, -1), ("cam_h", 0, -3),
     ("cam_hfov", 0.0, -1), ("cam_range", -1.0, -1), ("pool_size", -1, -3), ("terminate", 2, -1),
-    ("tape_hits", 3, -1), ("cull", 2, -1), ("warps_per_cta", 9, -1), ("rays_per_thread", 7, -1),
+    ("tape_hits", 3, -1), ("cull", 3, -1), ("warps_per_cta", 9, -1), ("rays_per_thread", 7, -1),
     ("ctas_per_sm", -1, -1),
 ])
 def test_create_rejects_bad_config(lib, field, value, code):

@@ -155,13 +155,19 @@ def test_culling_is_result_preserving(pair):
     p = pair.p
     if p["cam"] is None and p["lidar"] is None:
         pytest.skip("no sensor")
-    s2 = Simulator(p, pair.inp, cull=0)
-    s2.reset(dev(pair.inp["s0"]))
-    o2 = s2.rollout(pair.act)
+    outs = {}
+    for mode in (0, 1, 2):
+        s2 = Simulator(p, pair.inp, cull=mode)
+        s2.reset(dev(pair.inp["s0"]))
+        outs[mode] = s2.rollout(pair.act)
+    for mode in (1, 2):
+        for k in ("depth", "lidar"):
+            if pair.out[k] is not None:
+                assert torch.equal(outs[0][k], outs[mode][k]), (mode, k)
+        assert torch.equal(outs[0]["r_ctrl"], outs[mode]["r_ctrl"])
     for k in ("depth", "lidar"):
         if pair.out[k] is not None:
-            assert torch.equal(pair.out[k], o2[k]), k
-    assert torch.equal(pair.out["r_ctrl"], o2["r_ctrl"])
+            assert torch.equal(pair.out[k], outs[0][k]), k
 
 
 def test_steps_equal_rollout(pair):
