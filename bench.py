@@ -45,13 +45,14 @@ FLOP_BOX_TEST = 16
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=25)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--n-env", type=int, default=None,
                     help="override the number of environments (profiling on a smaller case)")
@@ -243,12 +244,16 @@ def run_ours(args, rank, world):
         step()
     torch.cuda.synchronize()
     sim.counters(reset=True)
-    # one counted pass for the algorithmic work of a rollout launch
+    # one counted pass for the algorithmic work of a render launch
     step()
     cnt = sim.counters(reset=True)
     if sim.status() != 0:
         raise RuntimeError("device status flagged during warm-up")
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    # the library brackets each of its kernel launches with CUDA events on the
+    # launching stream: per-kernel device time inside the timed region
+    sim.profile(True)
+    sim.kernel_times(reset=True)
     clocks = Clocks(local) if rank == 0 else None
     if world > 1:
         torch.distributed.barrier()
@@ -263,6 +268,8 @@ def run_ours(args, rank, world):
     if world > 1:
         torch.distributed.barrier()
     ck = clocks.stop() if clocks else None
+    kt = sim.kernel_times(reset=True)
+    sim.profile(False)
     ms = t_start.elapsed_time(t_end)
     if world > 1:
         tt = torch.tensor([ms], device=dev)
@@ -276,26 +283,50 @@ def run_ours(args, rank, world):
     value = env_steps / (ms / 1e3)
     rays_per_step = NM * (Rc + sim.Rl) * T  # per rollout launch
     grays = rays_per_step * args.steps * world / (ms / 1e3) / 1e9
+    launches = sum(n for _, n in kt.values())
+
+    # the same pass captured once into a CUDA graph (reset + rollout + adjoint)
+    graph = None
+    if not args.no_graph:
+        gr = sim.graph(act, s0=s0, out=out, g_r=g_r, g_depth=g_d, g_a=g_a, g_s0=g_s0)
+        for _ in range(args.warmup):
+            gr.launch()
+        torch.cuda.synchronize()
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        for _ in range(args.steps):
+            gr.launch()
+        g1.record(stream)
+        torch.cuda.synchronize()
+        gms = g0.elapsed_time(g1) / args.steps
+        graph = {"ms_per_step": gms, "value": p["n_env"] * T / (gms / 1e3), "kernels": gr.kernels}
+        gr.close()
+        if sim.status() != 0:
+            raise RuntimeError("device status flagged during the graph replay")
 
     if rank != 0:
         return 0
-    # roofline of the dominant kernel (the forward rollout: FP32 ray casting)
+    # roofline of the dominant kernel: k_render (FP32 ray casting), per launch
     props = torch.cuda.get_device_properties(dev)
     flop = FLOP_SPHERE_TEST * cnt["sphere_tests"] + FLOP_BOX_TEST * cnt["box_tests"]
-    achieved = flop / (fwd_ms / 1e3) / 1e12
+    render_ms = kt["render"][0] / max(kt["render"][1], 1)
+    achieved = flop / (render_ms / 1e3) / 1e12
     peak = peak_fp32_tflops(props.multi_processor_count, 2032.0)
     traffic = None
     tfile = os.path.join(ROOT, "profiles", "traffic.txt")
     if os.path.exists(tfile):
         tj = dict(l.split(": ", 1) for l in open(tfile).read().splitlines() if ": " in l and not l.startswith("#"))
-        if tj.get("source_hash") == source_hash() and tj.get("workload") == p["name"]:
-            traffic = float(tj["rollout_bytes_per_launch"])
+        if tj.get("source_hash") == source_hash() and tj.get("workload") == p["name"] \
+                and "render_bytes_per_launch" in tj:
+            traffic = float(tj["render_bytes_per_launch"])
+    per_kernel = {k: {"ms_per_launch": v[0] / max(v[1], 1), "launches": v[1]} for k, v in kt.items()}
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": traffic,
-                "kernel": "k_rollout (forward rollout launch)", "kernel_ms": fwd_ms,
-                "adjoint_ms": bwd_ms, "peak_basis": "FP32 FMA issue, %d SMs x 128 lanes x 2 x 2032 MHz (derived)"
+                "kernel": "k_render (ray casting of all T steps)", "kernel_ms": render_ms,
+                "peak_basis": "FP32 FMA issue, %d SMs x 128 lanes x 2 x 2032 MHz (derived, not measured)"
                 % props.multi_processor_count,
-                "tests_per_launch": cnt["sphere_tests"] + cnt["box_tests"]}
+                "tests_per_launch": cnt["sphere_tests"] + cnt["box_tests"],
+                "flop_per_launch": flop, "kernels": per_kernel}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -304,7 +335,8 @@ def run_ours(args, rank, world):
                                                                             4e-9 * T * NM * Rc),
                                     "exec": BENCH_EXEC}),
             "grays_per_s": grays, "agent_steps_per_s": value * p["n_agent"],
-            "roofline": roofline, "gpu_launches": 2 * args.steps * 1, "clocks": ck}
+            "fwd_ms": fwd_ms, "bwd_ms": bwd_ms,
+            "roofline": roofline, "gpu_launches": launches, "clocks": ck, "graph": graph}
     # end to end: host actions and initial state in, rewards and action gradients out
     if not args.no_e2e:
         line["e2e"] = run_e2e(args, sim, inp, dev, g_r, g_d, out, g_a, g_s0, p)

@@ -8,8 +8,10 @@
  * spheres and axis-aligned boxes (Sec. III-B), evaluates collisions, the
  * differentiable reward R_ctrl and the sparse reward R_goal (Sec. III-C,
  * III-D, III-E), terminates and resets environments, and renders the new
- * observation.  A rollout of T steps runs in one persistent launch; its
- * adjoint (backpropagation through time, Eq. 5) is hand-written.
+ * observation.  A rollout of T steps is two launches (the sequential physics
+ * of all T steps, then every step's ray casting); its adjoint
+ * (backpropagation through time, Eq. 5) is hand-written, also two launches.
+ * A reset + rollout + adjoint can be captured once into a CUDA graph.
  *
  * Conventions
  *  - Every function returns SIM_OK (0) or a negative SIM_ERR_* code; no C++
@@ -248,6 +250,65 @@ int sim_step_static(const sim_config *cfg, const float *prims, const int32_t *ma
  * grid size of the rollout kernel and its dynamic shared memory (bytes). */
 int sim_launch_info(const sim_handle *h, int32_t *warps_per_cta, int32_t *rays_per_thread,
                     int32_t *grid, int32_t *smem_bytes);
+
+/* Kernel kinds counted and timed by the library. */
+enum {
+    SIM_KERNEL_PHYSICS = 0,     /* sequential dynamics, collisions, rewards, resets, poses */
+    SIM_KERNEL_RENDER = 1,      /* ray casting of camera / LiDAR for every step */
+    SIM_KERNEL_RENDER_VJP = 2,  /* ray adjoint: depth / range cotangent -> pose cotangent */
+    SIM_KERNEL_PHYSICS_BWD = 3, /* physics adjoint over checkpointed segments */
+    SIM_KERNEL_KINDS = 4
+};
+
+/* sim_profile: on != 0 makes every later kernel launch of h (outside a graph
+ * capture) record a CUDA event pair around itself on its own stream, so each
+ * kernel's device duration is measured where it runs.  At most 65536 pairs
+ * are kept between resets of sim_kernel_times. */
+int sim_profile(sim_handle *h, int32_t on);
+
+/* sim_kernel_times: ms (HOST double[SIM_KERNEL_KINDS], nullable) receives the
+ * summed device milliseconds of the profiled launches per kind (waits for
+ * them); launches (HOST int64[SIM_KERNEL_KINDS], nullable) the number of
+ * kernels h launched per kind, profiled or not, graph launches included.
+ * reset != 0 clears both afterwards.  SIM_ERR_SIZE if event pairs ran out
+ * (the times then cover only the first 65536 launches). */
+int sim_kernel_times(sim_handle *h, double *ms, int64_t *launches, int32_t reset);
+
+/* Buffers of a captured reset + rollout (+ adjoint); all DEVICE pointers with
+ * the layouts of sim_reset, sim_rollout and sim_backward.  g_r == NULL
+ * captures no adjoint. */
+typedef struct sim_graph_io {
+    const float *state0; /* [NM][D]; NULL: pool entry 0 */
+    const float *actions;
+    float *r_ctrl;
+    int8_t *r_goal;
+    uint8_t *done;
+    float *depth, *lidar;
+    const float *g_r, *g_depth, *g_lidar, *g_sT;
+    float *g_a, *g_s0;
+} sim_graph_io;
+
+typedef struct sim_graph sim_graph;
+
+/* sim_graph_create: captures sim_reset + sim_rollout (+ sim_backward) of h
+ * with the buffers of io (HOST struct) into one CUDA graph (a memcpy, memsets
+ * and 2 or 4 kernels), launched by sim_graph_launch without any host work
+ * per kernel.  Nothing runs during creation.  The pointers in io are baked
+ * in: they stay valid while the graph is used.  A later sim_set_scene,
+ * sim_set_pool or sim_set_env_params on h makes the graph refuse to launch
+ * (SIM_ERR_NOT_READY); sim_destroy(h) does too (the sim_graph object itself
+ * stays owned by the caller).  Errors: those of the captured calls. */
+int sim_graph_create(sim_handle *h, const sim_graph_io *io, sim_graph **out);
+
+/* sim_graph_launch: one reset + rollout (+ adjoint) on stream.  Afterwards h
+ * holds that rollout, as if the captured calls had been made. */
+int sim_graph_launch(sim_graph *g, sim_stream_t stream);
+
+/* sim_graph_kernels: number of kernel nodes in the graph (HOST out). */
+int sim_graph_kernels(const sim_graph *g, int32_t *kernels);
+
+/* sim_graph_destroy: waits for h's last stream and frees the graph; NULL-safe. */
+int sim_graph_destroy(sim_graph *g);
 
 #ifdef __cplusplus
 }

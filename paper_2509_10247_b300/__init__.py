@@ -3,11 +3,12 @@
 include/diffsim.h, with a ctypes binding and torch.autograd wrappers.
 
 Submodules load lazily: ``synth`` (seeded inputs, numpy only), ``binding``
-(the C-ABI calls), ``autograd`` (DiffSimRollout, DiffSimStep), ``build``.
+(the C-ABI calls), ``autograd`` (DiffSimRollout, DiffSimStep), ``build``,
+``autotune`` (launch-shape search with a bitwise parity gate and a JSON cache).
 """
 import importlib
 
-__all__ = ["synth", "binding", "autograd", "build"]
+__all__ = ["synth", "binding", "autograd", "build", "autotune"]
 
 
 def __getattr__(name):

@@ -33,7 +33,10 @@ SYMBOLS = ["sim_version", "sim_strerror", "sim_state_dim", "sim_action_dim", "si
            "sim_destroy", "sim_workspace_bytes", "sim_set_scene", "sim_set_pool",
            "sim_set_env_params", "sim_reset", "sim_get_state", "sim_set_state", "sim_render",
            "sim_step", "sim_rollout", "sim_backward", "sim_step_backward", "sim_last_status",
-           "sim_launch_info", "sim_counters", "sim_step_static"]
+           "sim_launch_info", "sim_counters", "sim_step_static", "sim_profile", "sim_kernel_times",
+           "sim_graph_create", "sim_graph_launch", "sim_graph_kernels", "sim_graph_destroy"]
+
+KERNEL_KINDS = ("physics", "render", "render_vjp", "physics_bwd")
 
 
 class SimError(RuntimeError):
@@ -58,6 +61,12 @@ class SimConfig(C.Structure):
         ("ckpt_every", _i), ("tape_hits", _i), ("cull", _i), ("warps_per_cta", _i),
         ("rays_per_thread", _i), ("ctas_per_sm", _i), ("reserved", _i * 6),
     ]
+
+
+class SimGraphIO(C.Structure):
+    _fields_ = [("state0", _vp), ("actions", _vp), ("r_ctrl", _vp), ("r_goal", _vp), ("done", _vp),
+                ("depth", _vp), ("lidar", _vp), ("g_r", _vp), ("g_depth", _vp), ("g_lidar", _vp),
+                ("g_sT", _vp), ("g_a", _vp), ("g_s0", _vp)]
 
 
 _lib = None
@@ -262,6 +271,67 @@ def sim_step_static(cfg, prims, map_off, map_ns, map_nb, ns_max, nb_max, env_map
                               _ptr(r_goal), _ptr(done), _ptr(pool_k), _stream(stream)), "sim_step_static")
 
 
+def sim_profile(h, on=True):
+    _ck(lib().sim_profile(h, _i(1 if on else 0)), "sim_profile")
+
+
+def sim_kernel_times(h, reset=True):
+    """Per kernel kind: summed device milliseconds of the profiled launches
+    and the number of launches since the last reset."""
+    ms = (C.c_double * len(KERNEL_KINDS))()
+    n = (C.c_int64 * len(KERNEL_KINDS))()
+    _ck(lib().sim_kernel_times(h, ms, n, _i(1 if reset else 0)), "sim_kernel_times")
+    return {k: (ms[i], n[i]) for i, k in enumerate(KERNEL_KINDS)}
+
+
+def sim_graph_create(h, io):
+    g = _vp()
+    _ck(lib().sim_graph_create(h, C.byref(io), C.byref(g)), "sim_graph_create")
+    return g
+
+
+def sim_graph_launch(g, stream=None):
+    _ck(lib().sim_graph_launch(g, _stream(stream)), "sim_graph_launch")
+
+
+def sim_graph_kernels(g):
+    n = C.c_int32()
+    _ck(lib().sim_graph_kernels(g, C.byref(n)), "sim_graph_kernels")
+    return n.value
+
+
+def sim_graph_destroy(g):
+    _ck(lib().sim_graph_destroy(g), "sim_graph_destroy")
+
+
+class SimGraph:
+    """Owner of one captured reset + rollout (+ adjoint).  Keeps the tensors
+    whose pointers the graph holds alive."""
+
+    def __init__(self, h, tensors):
+        self.tensors = tensors
+        io = SimGraphIO(**{k: (None if v is None else v.data_ptr()) for k, v in tensors.items()})
+        for k, v in tensors.items():
+            if v is not None:
+                assert v.is_cuda and v.is_contiguous(), k
+        self.g = sim_graph_create(h, io)
+        self.kernels = sim_graph_kernels(self.g)
+
+    def launch(self, stream=None):
+        sim_graph_launch(self.g, stream)
+
+    def close(self):
+        if getattr(self, "g", None):
+            sim_graph_destroy(self.g)
+            self.g = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 # ------------------------------------------------------------ owner class
 class Simulator:
     """One handle bound to a workload: parameters `p` (synth.preset/params) and
@@ -363,3 +433,30 @@ class Simulator:
 
     def workspace_bytes(self):
         return sim_workspace_bytes(self.h)
+
+    def profile(self, on=True):
+        sim_profile(self.h, on)
+
+    def kernel_times(self, reset=True):
+        return sim_kernel_times(self.h, reset)
+
+    def graph(self, actions, s0=None, out=None, g_r=None, g_depth=None, g_lidar=None, g_sT=None,
+              g_a=None, g_s0=None):
+        """Capture reset(s0) + rollout(actions) (+ backward when g_r is given)
+        into one CUDA graph writing `out` (dict as returned by rollout) and
+        g_a / g_s0.  Returns a SimGraph; launching it runs the whole pass."""
+        T, NM = self.T, self.NM
+        o = out if out is not None else dict(
+            r_ctrl=self._empty(T, NM), r_goal=self._empty(T, NM, dtype=torch.int8),
+            done=self._empty(T, NM, dtype=torch.uint8),
+            depth=self._empty(T, NM, self.Rc) if self.Rc else None,
+            lidar=self._empty(T, NM, self.Rl) if self.Rl else None)
+        if g_r is not None:
+            g_a = self._empty(T, NM, self.A) if g_a is None else g_a
+            g_s0 = self._empty(NM, self.D) if g_s0 is None else g_s0
+        tensors = dict(state0=s0, actions=actions, r_ctrl=o["r_ctrl"], r_goal=o["r_goal"], done=o["done"],
+                       depth=o["depth"], lidar=o["lidar"], g_r=g_r, g_depth=g_depth, g_lidar=g_lidar,
+                       g_sT=g_sT, g_a=g_a, g_s0=g_s0)
+        g = SimGraph(self.h, tensors)
+        g.out = o
+        return g

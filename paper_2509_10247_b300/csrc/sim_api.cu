@@ -22,6 +22,8 @@ cudaError_t render_call(bool vjp, bool launch, int rpt, const Args& a, int grid,
 
 using ds::Args;
 
+struct sim_graph;
+
 struct sim_handle {
     sim_config cfg;
     int D = 0, A = 0, N = 0, M = 0, NM = 0, T = 0, K = 0, S = 0, Rc = 0, Rl = 0;
@@ -69,6 +71,31 @@ struct sim_handle {
     // launch shape of the render kernels (forward, adjoint, single-step adjoint)
     int nw = 8, rpt = 4, grid_r = 1, grid_rv = 1, grid_rvs = 1;
     ds::Smem sm_r{}, sm_rv{}, sm_rvs{};
+    // kernel launches per kind; while profiling, one CUDA event pair per launch
+    bool profiling = false, capturing = false, ev_overflow = false;
+    long long launches[SIM_KERNEL_KINDS] = {};
+    long long cap_launches[SIM_KERNEL_KINDS] = {};
+    struct Ev {
+        cudaEvent_t a = nullptr, b = nullptr;
+        int kind = 0;
+    };
+    std::vector<Ev> evs;
+    size_t ev_used = 0;
+    // advanced by every call that reallocates scene, pool or per-env buffers:
+    // a graph captured before such a call refuses to launch
+    unsigned generation = 0;
+    std::vector<sim_graph*> graphs;
+};
+
+// A captured reset + rollout (+ adjoint) of one handle.
+struct sim_graph {
+    sim_handle* h = nullptr;  // NULL once the handle is destroyed
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    unsigned generation = 0;
+    const float* actions = nullptr;
+    long long launches[SIM_KERNEL_KINDS] = {};
+    int kernels = 0;
 };
 
 namespace {
@@ -190,10 +217,12 @@ int pick_rpt(const sim_handle* h) {
     return pick;
 }
 
-int grid_of(sim_handle* h, bool vjp, const ds::Smem& sm, int* grid) {
+int grid_of(sim_handle* h, bool vjp, bool tape, const ds::Smem& sm, int* grid) {
     int occ = 0;
     Args dummy;
     memset(&dummy, 0, sizeof(dummy));
+    static int16_t tape_marker;  // selects the taped-adjoint kernel; never dereferenced here
+    dummy.sen[0].tape = tape ? &tape_marker : nullptr;
     CK(ds::render_call(vjp, false, h->rpt, dummy, 0, 32 * h->nw, sm.total, nullptr, &occ));
     if (occ < 1) return SIM_ERR_UNSUPPORTED;
     if (h->cfg.ctas_per_sm) occ = std::min(occ, h->cfg.ctas_per_sm);
@@ -201,23 +230,30 @@ int grid_of(sim_handle* h, bool vjp, const ds::Smem& sm, int* grid) {
     return SIM_OK;
 }
 
-// Ray order of the render kernels: the sensor's ray grid is cut into tiles
-// of 32 * rpt rays (tw x th, tw >= th), taken tile by tile, so that each
-// chunk of a warp pass covers a compact patch of directions.  Each chunk's
-// cone (body frame): axis = normalised mean direction, half-angle = largest
-// angle to the axis + 2 mrad.  Tables are uploaded in that order with the
-// output index of every slot.  Returns the mean cone half-angle (rad).
+// Interleaves the bits of x (even positions) and y (odd positions).
+uint64_t morton2(uint32_t x, uint32_t y) {
+    uint64_t m = 0;
+    for (int b = 0; b < 16; ++b) m |= (uint64_t)((x >> b) & 1u) << (2 * b) | (uint64_t)((y >> b) & 1u) << (2 * b + 1);
+    return m;
+}
+
+// Ray order of the render kernels: a function of the ray grid alone (never
+// of rays per thread, culling mode or CTA shape), so every launch shape sums
+// the adjoint's ray cotangents in one order and agrees bit for bit.  Grids of
+// at most 256 rays keep row-major order (a warp pass covers most of such a
+// grid anyway); larger grids take Z (Morton) order, so that each chunk of a
+// warp pass covers a compact patch of directions.  Each chunk's cone (body
+// frame): axis = normalised mean direction, half-angle = largest angle to
+// the axis + 2 mrad.  Tables are uploaded in that order with the output index
+// of every slot.  Returns the mean cone half-angle (rad).
 int build_tables(sim_handle* h, int s, double* mean_angle) {
     const int cs = 32 * h->rpt, W = h->img_w[s], H = h->img_h[s];
-    int tw = 1;
-    while (tw * tw < cs) tw <<= 1;
-    int th = std::max(1, cs / tw);
-    std::vector<int> order;
-    order.reserve((size_t)W * H);
-    for (int ty = 0; ty < H; ty += th)
-        for (int tx = 0; tx < W; tx += tw)
-            for (int y = ty; y < std::min(H, ty + th); ++y)
-                for (int x = tx; x < std::min(W, tx + tw); ++x) order.push_back(y * W + x);
+    std::vector<int> order((size_t)W * H);
+    std::iota(order.begin(), order.end(), 0);
+    if ((size_t)W * H > 256)
+        std::stable_sort(order.begin(), order.end(), [W](int a, int b) {
+            return morton2(a % W, a / W) < morton2(b % W, b / W);
+        });
     const std::vector<float4>& d0 = h->h_dirs[s];
     const int R = (int)order.size(), n = (R + cs - 1) / cs;
     std::vector<float4> dirp(R), cone(n);
@@ -284,8 +320,9 @@ int configure_launch(sim_handle* h) {
     ds::physics_bwd_shape(h->K, h->M, &w, &segb);
     if ((int)segb > maxsm) return SIM_ERR_SIZE;
     int rc;
-    if ((rc = grid_of(h, false, h->sm_r, &h->grid_r)) || (rc = grid_of(h, true, h->sm_rv, &h->grid_rv)) ||
-        (rc = grid_of(h, true, h->sm_rvs, &h->grid_rvs)))
+    if ((rc = grid_of(h, false, false, h->sm_r, &h->grid_r)) ||
+        (rc = grid_of(h, true, h->tape, h->sm_rv, &h->grid_rv)) ||
+        (rc = grid_of(h, true, false, h->sm_rvs, &h->grid_rvs)))
         return rc;
     return SIM_OK;
 }
@@ -327,16 +364,51 @@ Args base_args(const sim_handle* h) {
     return a;
 }
 
-int run_physics(sim_handle* h, const Args& a, cudaStream_t st) {
+constexpr size_t kMaxEvents = size_t(1) << 16;
+
+// Enqueues one kernel through launch() on st and counts it under `kind`.
+// While profiling (and not capturing a graph) the launch is bracketed by a
+// CUDA event pair recorded on st, read back by sim_kernel_times.
+template <class F>
+int launch_kernel(sim_handle* h, int kind, cudaStream_t st, F&& launch) {
     h->last_stream = st;
-    CK(ds::launch_physics(a, st));
+    size_t slot = SIZE_MAX;
+    if (h->profiling && !h->capturing) {
+        if (h->ev_used == kMaxEvents) {
+            h->ev_overflow = true;
+        } else {
+            if (h->ev_used == h->evs.size()) {
+                sim_handle::Ev e;
+                CK(cudaEventCreate(&e.a));
+                cudaError_t err = cudaEventCreate(&e.b);
+                if (err != cudaSuccess) {
+                    cudaEventDestroy(e.a);
+                    cudaGetLastError();
+                    return cuda_err(err);
+                }
+                h->evs.push_back(e);
+            }
+            slot = h->ev_used;
+            h->evs[slot].kind = kind;
+            CK(cudaEventRecord(h->evs[slot].a, st));
+        }
+    }
+    CK(launch());
+    if (slot != SIZE_MAX) {
+        CK(cudaEventRecord(h->evs[slot].b, st));
+        h->ev_used = slot + 1;
+    }
+    if (h->capturing) ++h->cap_launches[kind];
+    else ++h->launches[kind];
     return SIM_OK;
 }
 
+int run_physics(sim_handle* h, const Args& a, cudaStream_t st) {
+    return launch_kernel(h, SIM_KERNEL_PHYSICS, st, [&] { return ds::launch_physics(a, st); });
+}
+
 int run_physics_bwd(sim_handle* h, const Args& a, cudaStream_t st) {
-    h->last_stream = st;
-    CK(ds::launch_physics_bwd(a, st));
-    return SIM_OK;
+    return launch_kernel(h, SIM_KERNEL_PHYSICS_BWD, st, [&] { return ds::launch_physics_bwd(a, st); });
 }
 
 // which: 0 render, 1 render adjoint (rollout), 2 render adjoint re-casting (step)
@@ -345,10 +417,10 @@ int run_render(sim_handle* h, int which, Args& a, cudaStream_t st) {
     const int grid = which == 0 ? h->grid_r : (which == 1 ? h->grid_rv : h->grid_rvs);
     a.sm = sm;
     CK(cudaMemsetAsync(h->d_work, 0, sizeof(int), st));
-    h->last_stream = st;
     int occ = 0;
-    CK(ds::render_call(which != 0, true, h->rpt, a, grid, 32 * h->nw, sm.total, st, &occ));
-    return SIM_OK;
+    return launch_kernel(h, which == 0 ? SIM_KERNEL_RENDER : SIM_KERNEL_RENDER_VJP, st, [&] {
+        return ds::render_call(which != 0, true, h->rpt, a, grid, 32 * h->nw, sm.total, st, &occ);
+    });
 }
 
 void build_sensors(sim_handle* h, std::vector<float4>& cam, std::vector<float4>& lid, std::vector<float>& cam_t,
@@ -413,6 +485,17 @@ int sim_action_dim(int model) { return model == SIM_MODEL_POINT_MASS ? 3 : (mode
 int sim_destroy(sim_handle* h) {
     if (!h) return SIM_OK;
     cudaDeviceSynchronize();
+    for (sim_graph* g : h->graphs) {  // the graph objects stay valid but refuse to launch
+        if (g->exec) cudaGraphExecDestroy(g->exec);
+        if (g->graph) cudaGraphDestroy(g->graph);
+        g->exec = nullptr;
+        g->graph = nullptr;
+        g->h = nullptr;
+    }
+    for (auto& e : h->evs) {
+        cudaEventDestroy(e.a);
+        cudaEventDestroy(e.b);
+    }
     dfree(h->d_prims); dfree(h->d_map_off); dfree(h->d_map_ns); dfree(h->d_map_nb);
     dfree(h->d_env_map); dfree(h->d_order); dfree(h->d_targets); dfree(h->d_pool);
     dfree(h->d_drag); dfree(h->d_lam); dfree(h->d_cam); dfree(h->d_lid);
@@ -567,6 +650,7 @@ int sim_set_scene(sim_handle* h, const float* spheres, const int32_t* sph_off, c
     std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
         return vns[env_map[x]] + vnb[env_map[x]] > vns[env_map[y]] + vnb[env_map[y]];
     });
+    ++h->generation;
     dfree(h->d_prims); dfree(h->d_map_off); dfree(h->d_map_ns); dfree(h->d_map_nb);
     dfree(h->d_env_map); dfree(h->d_order); dfree(h->d_targets);
     int rc;
@@ -598,6 +682,7 @@ int sim_set_pool(sim_handle* h, const float* pool) {
     if (n == 0) return SIM_ERR_SIZE;
     for (size_t k = 0; k < n; ++k)
         if (!std::isfinite(pool[k])) return SIM_ERR_INVALID_ARG;
+    ++h->generation;
     dfree(h->d_pool);
     int rc = dalloc(h, &h->d_pool, n);
     if (rc) return rc;
@@ -609,6 +694,7 @@ int sim_set_pool(sim_handle* h, const float* pool) {
 int sim_set_env_params(sim_handle* h, const float* drag, const float* lam) {
     if (!h) return SIM_ERR_NULL_PTR;
     if (h->cfg.model != SIM_MODEL_POINT_MASS && (drag || lam)) return SIM_ERR_UNSUPPORTED;
+    ++h->generation;
     dfree(h->d_drag);
     dfree(h->d_lam);
     int rc;
@@ -809,6 +895,129 @@ int sim_launch_info(const sim_handle* h, int32_t* warps_per_cta, int32_t* rays_p
     if (rays_per_thread) *rays_per_thread = h->rpt;
     if (grid) *grid = h->grid_r;
     if (smem_bytes) *smem_bytes = (int32_t)h->sm_r.total;
+    return SIM_OK;
+}
+
+
+int sim_profile(sim_handle* h, int32_t on) {
+    if (!h) return SIM_ERR_NULL_PTR;
+    h->profiling = on != 0;
+    return SIM_OK;
+}
+
+int sim_kernel_times(sim_handle* h, double* ms, int64_t* launches, int32_t reset) {
+    if (!h) return SIM_ERR_NULL_PTR;
+    if (ms) {
+        for (int k = 0; k < SIM_KERNEL_KINDS; ++k) ms[k] = 0.0;
+        for (size_t i = 0; i < h->ev_used; ++i) {
+            const sim_handle::Ev& e = h->evs[i];
+            CK(cudaEventSynchronize(e.b));
+            float t = 0.f;
+            CK(cudaEventElapsedTime(&t, e.a, e.b));
+            ms[e.kind] += t;
+        }
+    }
+    if (launches)
+        for (int k = 0; k < SIM_KERNEL_KINDS; ++k) launches[k] = h->launches[k];
+    const bool overflow = h->ev_overflow;
+    if (reset) {
+        h->ev_used = 0;
+        h->ev_overflow = false;
+        for (int k = 0; k < SIM_KERNEL_KINDS; ++k) h->launches[k] = 0;
+    }
+    return overflow ? SIM_ERR_SIZE : SIM_OK;
+}
+
+int sim_graph_create(sim_handle* h, const sim_graph_io* io, sim_graph** out) {
+    if (!h || !io || !out) return SIM_ERR_NULL_PTR;
+    *out = nullptr;
+    if (!io->actions || (io->g_r && !io->g_a)) return SIM_ERR_NULL_PTR;
+    if (!h->have_scene || (!io->state0 && !h->have_pool)) return SIM_ERR_NOT_READY;
+    if (h->cfg.terminate && !h->have_pool) return SIM_ERR_NOT_READY;
+    sim_graph* g = new (std::nothrow) sim_graph();
+    if (!g) return SIM_ERR_OOM;
+    cudaStream_t cs = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        delete g;
+        return cuda_err(e);
+    }
+    const bool had_rollout = h->have_rollout;
+    const float* had_actions = h->rollout_actions;
+    cudaStream_t had_stream = h->last_stream;
+    h->capturing = true;
+    for (int k = 0; k < SIM_KERNEL_KINDS; ++k) h->cap_launches[k] = 0;
+    int rc = cuda_err(cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed));
+    if (!rc) {
+        rc = sim_reset(h, io->state0, cs);
+        if (!rc) rc = sim_rollout(h, io->actions, io->r_ctrl, io->r_goal, io->done, io->depth, io->lidar, cs);
+        if (!rc && io->g_r) rc = sim_backward(h, io->g_r, io->g_depth, io->g_lidar, io->g_sT, io->g_a, io->g_s0, cs);
+        e = cudaStreamEndCapture(cs, &g->graph);  // ends the capture whatever happened inside
+        if (!rc && e != cudaSuccess) rc = cuda_err(e);
+    }
+    h->capturing = false;
+    h->have_rollout = had_rollout;
+    h->rollout_actions = had_actions;
+    h->last_stream = had_stream;
+    if (!rc) rc = cuda_err(cudaGraphInstantiate(&g->exec, g->graph, 0));
+    if (!rc) {
+        size_t n = 0;
+        rc = cuda_err(cudaGraphGetNodes(g->graph, nullptr, &n));
+        std::vector<cudaGraphNode_t> nodes(n);
+        if (!rc && n) rc = cuda_err(cudaGraphGetNodes(g->graph, nodes.data(), &n));
+        for (size_t i = 0; !rc && i < n; ++i) {
+            cudaGraphNodeType t;
+            rc = cuda_err(cudaGraphNodeGetType(nodes[i], &t));
+            if (!rc && t == cudaGraphNodeTypeKernel) ++g->kernels;
+        }
+    }
+    cudaStreamDestroy(cs);
+    if (rc) {
+        cudaGetLastError();
+        if (g->exec) cudaGraphExecDestroy(g->exec);
+        if (g->graph) cudaGraphDestroy(g->graph);
+        delete g;
+        return rc;
+    }
+    g->h = h;
+    g->generation = h->generation;
+    g->actions = io->actions;
+    for (int k = 0; k < SIM_KERNEL_KINDS; ++k) g->launches[k] = h->cap_launches[k];
+    h->graphs.push_back(g);
+    *out = g;
+    return SIM_OK;
+}
+
+int sim_graph_launch(sim_graph* g, sim_stream_t stream) {
+    if (!g) return SIM_ERR_NULL_PTR;
+    sim_handle* h = g->h;
+    if (!h || g->generation != h->generation) return SIM_ERR_NOT_READY;
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(cudaGraphLaunch(g->exec, st));
+    h->last_stream = st;
+    h->have_rollout = true;
+    h->rollout_actions = g->actions;
+    for (int k = 0; k < SIM_KERNEL_KINDS; ++k) h->launches[k] += g->launches[k];
+    return SIM_OK;
+}
+
+int sim_graph_kernels(const sim_graph* g, int32_t* kernels) {
+    if (!g || !kernels) return SIM_ERR_NULL_PTR;
+    *kernels = g->kernels;
+    return SIM_OK;
+}
+
+int sim_graph_destroy(sim_graph* g) {
+    if (!g) return SIM_OK;
+    if (g->h) {
+        cudaStreamSynchronize(g->h->last_stream);
+        auto& v = g->h->graphs;
+        v.erase(std::remove(v.begin(), v.end(), g), v.end());
+        if (g->exec) cudaGraphExecDestroy(g->exec);
+        if (g->graph) cudaGraphDestroy(g->graph);
+    }
+    delete g;
     return SIM_OK;
 }
 

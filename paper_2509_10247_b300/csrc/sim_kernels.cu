@@ -224,9 +224,9 @@ __global__ void __launch_bounds__(256, 3) k_rollout(const Args a) {
                 const float* R = pose + I.m * 12 + 3;
                 const int4 meta = *(reinterpret_cast<const int4*>(sm + a.sm.lmeta) + I.Lx);
                 const short* lid = reinterpret_cast<const short*>(sm + a.sm.lid) + (size_t)I.Lx * (a.ns_max + a.nb_max);
-                float dx[RPT], dy[RPT], dz[RPT], fac[RPT], tb[RPT];
+                float dx[RPT], dy[RPT], dz[RPT], tb[RPT];
                 int bi[RPT];
-                item_rays<RPT>(sen, R, I.chunk, lane, dx, dy, dz, fac, tb);
+                item_rays<RPT>(sen, R, I.chunk, lane, dx, dy, dz, tb);
 #pragma unroll
                 for (int r = 0; r < RPT; ++r) bi[r] = -1;
                 if (meta.z < 0) cast_list<RPT>(fused_list(a, sm, I.Lx), meta, a.ns_max, dx, dy, dz, tb, bi);
@@ -247,7 +247,10 @@ __global__ void __launch_bounds__(256, 3) k_rollout(const Args a) {
                     int id;
                     if (meta.z >= 0) { v = 0.f; id = meta.z; }
                     else if (bi[r] < 0) { v = sen.range; id = -1; }
-                    else { v = fminf(tb[r] * (sen.kind == 0 ? fac[r] : 1.f), sen.range); id = lid[bi[r]]; }
+                    else {
+                        v = fminf(sen.kind == 0 ? tb[r] * __ldg(&sen.dir[ray].w) : tb[r], sen.range);
+                        id = lid[bi[r]];
+                    }
                     if (sen.out) sen.out[base + ray] = v;
                     if (sen.tape) sen.tape[base + ray] = (int16_t)id;
                 }

@@ -142,6 +142,18 @@ __device__ inline int4 warp_build_list(const float4* prim, int ns, int nb, const
     return meta;
 }
 
+// Slab test of one box (centre - origin c, half extents h) against one ray
+// given by its reciprocal direction: t = c/d -+ h/|d| per axis, entry = max,
+// exit = min; a hit in front of the origin nearer than tb replaces the best.
+// |1/d| enters as an operand modifier, so no absolute values are kept.
+__device__ __forceinline__ void box_test(const float4& c, const float4& h, float ix, float iy, float iz, int slot,
+                                         float& tb, int& bi) {
+    const float mx = c.x * ix, my = c.y * iy, mz = c.z * iz;
+    const float tn = max3f(fmaf(-h.x, fabsf(ix), mx), fmaf(-h.y, fabsf(iy), my), fmaf(-h.z, fabsf(iz), mz));
+    const float tf = min3f(fmaf(h.x, fabsf(ix), mx), fmaf(h.y, fabsf(iy), my), fmaf(h.z, fabsf(iz), mz));
+    if (tn <= tf && tn > 0.f && tn < tb) { tb = tn; bi = slot; }
+}
+
 // Sweep RPT rays per lane over a list.  tb holds each ray's best distance
 // (start: its clamp distance), bi the list slot of the best hit (spheres
 // 0.., boxes ns_max..).  Sphere: one dot product decides whether the ray
@@ -167,21 +179,15 @@ __device__ __forceinline__ void cast_list(const WList& L, const int4& meta, int 
         }
     }
     if (meta.y > 0) {
-        float ix[RPT], iy[RPT], iz[RPT], ax[RPT], ay[RPT], az[RPT];
+        float ix[RPT], iy[RPT], iz[RPT];
 #pragma unroll
         for (int r = 0; r < RPT; ++r) {
             ix[r] = safe_rcp(dx[r]); iy[r] = safe_rcp(dy[r]); iz[r] = safe_rcp(dz[r]);
-            ax[r] = fabsf(ix[r]); ay[r] = fabsf(iy[r]); az[r] = fabsf(iz[r]);
         }
         for (int k = 0; k < meta.y; ++k) {
             const float4 c = L.box[2 * k], h = L.box[2 * k + 1];
 #pragma unroll
-            for (int r = 0; r < RPT; ++r) {
-                const float mx = c.x * ix[r], my = c.y * iy[r], mz = c.z * iz[r];
-                const float tn = max3f(fmaf(-h.x, ax[r], mx), fmaf(-h.y, ay[r], my), fmaf(-h.z, az[r], mz));
-                const float tf = min3f(fmaf(h.x, ax[r], mx), fmaf(h.y, ay[r], my), fmaf(h.z, az[r], mz));
-                if (tn <= tf && tn > 0.f && tn < tb[r]) { tb[r] = tn; bi[r] = ns_max + k; }
-            }
+            for (int r = 0; r < RPT; ++r) box_test(c, h, ix[r], iy[r], iz[r], ns_max + k, tb[r], bi[r]);
         }
     }
 }
@@ -244,22 +250,16 @@ __device__ __forceinline__ void cast_sub(const WList& L, const int2& n, int ns_m
         }
     }
     if (n.y > 0) {
-        float ix[RPT], iy[RPT], iz[RPT], ax[RPT], ay[RPT], az[RPT];
+        float ix[RPT], iy[RPT], iz[RPT];
 #pragma unroll
         for (int r = 0; r < RPT; ++r) {
             ix[r] = safe_rcp(dx[r]); iy[r] = safe_rcp(dy[r]); iz[r] = safe_rcp(dz[r]);
-            ax[r] = fabsf(ix[r]); ay[r] = fabsf(iy[r]); az[r] = fabsf(iz[r]);
         }
         for (int j = 0; j < n.y; ++j) {
             const int k = L.sub[ns_max + j];
             const float4 c = L.box[2 * k], h = L.box[2 * k + 1];
 #pragma unroll
-            for (int r = 0; r < RPT; ++r) {
-                const float mx = c.x * ix[r], my = c.y * iy[r], mz = c.z * iz[r];
-                const float tn = max3f(fmaf(-h.x, ax[r], mx), fmaf(-h.y, ay[r], my), fmaf(-h.z, az[r], mz));
-                const float tf = min3f(fmaf(h.x, ax[r], mx), fmaf(h.y, ay[r], my), fmaf(h.z, az[r], mz));
-                if (tn <= tf && tn > 0.f && tn < tb[r]) { tb[r] = tn; bi[r] = ns_max + k; }
-            }
+            for (int r = 0; r < RPT; ++r) box_test(c, h, ix[r], iy[r], iz[r], ns_max + k, tb[r], bi[r]);
         }
     }
 }
@@ -293,9 +293,11 @@ __device__ __forceinline__ int next_item(int* ticket, int lane) {
     return __shfl_sync(0xffffffffu, v, 0);
 }
 
+// World directions and start distances (clamp distances) of the lane's RPT
+// rays of chunk `chunk`; a slot past the table gets tb = -1 (never hit).
 template <int RPT>
 __device__ __forceinline__ void item_rays(const Sensor& sen, const float* R, int chunk, int lane,
-                                          float* dx, float* dy, float* dz, float* fac, float* tb) {
+                                          float* dx, float* dy, float* dz, float* tb) {
 #pragma unroll
     for (int r = 0; r < RPT; ++r) {
         const int ray = chunk * 32 * RPT + r * 32 + lane;  // table slot
@@ -304,9 +306,51 @@ __device__ __forceinline__ void item_rays(const Sensor& sen, const float* R, int
         dx[r] = fmaf(R[0], db.x, fmaf(R[1], db.y, R[2] * db.z));
         dy[r] = fmaf(R[3], db.x, fmaf(R[4], db.y, R[5] * db.z));
         dz[r] = fmaf(R[6], db.x, fmaf(R[7], db.y, R[8] * db.z));
-        fac[r] = db.w;
         tb[r] = valid ? __ldg(sen.tmax + ray) : -1.f;
     }
+}
+
+// World direction of table slot j.
+__device__ __forceinline__ float4 ray_dir(const Sensor& sen, const float* R, int j, float* d) {
+    const float4 db = __ldg(sen.dir + j);
+    d[0] = fmaf(R[0], db.x, fmaf(R[1], db.y, R[2] * db.z));
+    d[1] = fmaf(R[3], db.x, fmaf(R[4], db.y, R[5] * db.z));
+    d[2] = fmaf(R[6], db.x, fmaf(R[7], db.y, R[8] * db.z));
+    return db;
+}
+
+// Sum of 12 per-lane values over the warp in a fixed tree order
+// (reduce-scatter: 16 shuffles instead of 60).  Returns, on every lane, the
+// total of value (lane >> 1) & 15 (meaningful below 12; lanes 2i and 2i+1
+// hold the same total).
+__device__ __forceinline__ float warp_sum12(const float* v) {
+    const int lane = threadIdx.x & 31;
+    float a[8];
+    const bool h16 = lane & 16;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const float lo = v[k], hi = k + 8 < 12 ? v[k + 8] : 0.f;
+        const float send = h16 ? lo : hi;
+        a[k] = (h16 ? hi : lo) + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+    const bool h8 = lane & 8;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const float send = h8 ? a[k] : a[k + 4];
+        a[k] = (h8 ? a[k + 4] : a[k]) + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+    const bool h4 = lane & 4;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const float send = h4 ? a[k] : a[k + 2];
+        a[k] = (h4 ? a[k + 2] : a[k]) + __shfl_xor_sync(0xffffffffu, send, 4);
+    }
+    const bool h2 = lane & 2;
+    {
+        const float send = h2 ? a[0] : a[1];
+        a[0] = (h2 ? a[1] : a[0]) + __shfl_xor_sync(0xffffffffu, send, 2);
+    }
+    return a[0] + __shfl_xor_sync(0xffffffffu, a[0], 1);
 }
 
 // ------------------------------------------------------ map staging (TMA)
@@ -363,13 +407,16 @@ __device__ __forceinline__ void ray_vjp(const float4* prim, int ns, int id, cons
             const float iv = safe_rcp(d[k]);
             tl[k] = fmaf(-h[k], fabsf(iv), c[k] * iv);
         }
-        int ax = 0;
-        if (tl[1] > tl[ax]) ax = 1;
-        if (tl[2] > tl[ax]) ax = 2;
-        t = tl[ax];
+        // entry axis: the largest entry time, lowest axis on ties (selects,
+        // no runtime-indexed arrays)
+        const bool x1 = tl[1] > tl[0];
+        const float t01 = x1 ? tl[1] : tl[0];
+        const bool x2 = tl[2] > t01;
+        t = x2 ? tl[2] : t01;
         if (!(t > 0.f)) return;
-        n[0] = n[1] = n[2] = 0.f;
-        n[ax] = d[ax] > 0.f ? -1.f : 1.f;
+        const int ax = x2 ? 2 : (x1 ? 1 : 0);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) n[k] = k == ax ? (d[k] > 0.f ? -1.f : 1.f) : 0.f;
     }
     const float fac = sen.kind == 0 ? db.w : 1.f;
     if (t * fac >= sen.range) return;

@@ -87,7 +87,9 @@ __global__ void __launch_bounds__(128) k_physics(const Args a) {
         if (a.ckpt && (t % a.K) == 0) {
             const int c = t / a.K;
             if (on)
-                for (int k = 0; k < D; ++k) a.ckpt[((size_t)c * NM + i) * D + k] = s[k];
+#pragma unroll
+                for (int k = 0; k < 16; ++k)
+                    if (k < D) a.ckpt[((size_t)c * NM + i) * D + k] = s[k];
             if (lane == 0) a.ckpt_k[(size_t)c * a.N + env] = kpool;
         }
         float act[4], sp[16];
@@ -120,7 +122,9 @@ __global__ void __launch_bounds__(128) k_physics(const Args a) {
             const float pos = a.c.pos_sq ? ne2 : ne;
             const float ob = (a.c.w_obs != 0.f && sd < CUDART_INF_F) ? relu(a.c.d_safe - sd) : 0.f;
             float aa = 0.f;
-            for (int k = 0; k < A; ++k) aa += act[k] * act[k];
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                if (k < A) aa += act[k] * act[k];
             if (a.r_ctrl) a.r_ctrl[o] = -a.c.w_pos * pos - a.c.w_obs * ob * ob - a.c.w_act * aa - a.c.w_agent * pair;
             if (a.r_goal) a.r_goal[o] = (int8_t)(col ? -1 : (ne < a.c.success_radius ? 1 : 0));
             if (a.sdf_tape) a.sdf_tape[o] = (int16_t)bid;
@@ -143,7 +147,9 @@ __global__ void __launch_bounds__(128) k_physics(const Args a) {
         }
     }
     if (on)
-        for (int k = 0; k < D; ++k) a.state[(size_t)i * D + k] = s[k];
+#pragma unroll
+        for (int k = 0; k < 16; ++k)
+            if (k < D) a.state[(size_t)i * D + k] = s[k];
     if (lane == 0 && a.pool_k) a.pool_k[env] = kpool;
 }
 
@@ -192,9 +198,9 @@ __global__ void __launch_bounds__(256, 4) k_render(const Args a) {
             const int nch = (sen.R + 32 * RPT - 1) / (32 * RPT);
             const size_t base = ti * sen.R;
             for (int ch = 0; ch < nch; ++ch) {
-                float dx[RPT], dy[RPT], dz[RPT], fac[RPT], tb[RPT];
+                float dx[RPT], dy[RPT], dz[RPT], tb[RPT];
                 int bi[RPT];
-                item_rays<RPT>(sen, R, ch, lane, dx, dy, dz, fac, tb);
+                item_rays<RPT>(sen, R, ch, lane, dx, dy, dz, tb);
 #pragma unroll
                 for (int r = 0; r < RPT; ++r) bi[r] = -1;
                 int2 nsub = make_int2(meta.x, meta.y);
@@ -223,7 +229,10 @@ __global__ void __launch_bounds__(256, 4) k_render(const Args a) {
                     int id;
                     if (meta.z >= 0) { v = 0.f; id = meta.z; }
                     else if (bi[r] < 0) { v = sen.range; id = -1; }
-                    else { v = fminf(tb[r] * (sen.kind == 0 ? fac[r] : 1.f), sen.range); id = L.id[bi[r]]; }
+                    else {
+                        v = fminf(sen.kind == 0 ? tb[r] * __ldg(&sen.dir[j].w) : tb[r], sen.range);
+                        id = L.id[bi[r]];
+                    }
                     if (sen.out) sen.out[base + ray] = v;
                     if (sen.tape) sen.tape[base + ray] = (int16_t)id;
                 }
@@ -242,14 +251,14 @@ __global__ void __launch_bounds__(256, 4) k_render(const Args a) {
 // sensor) reduce, in a fixed order, to the pose cotangent gposes[t][i] =
 // (d/d origin [3], d/d R [9]).  Zero when the step terminated (the state was
 // replaced).  Hit ids come from the rollout's tape or are re-cast.
-template <int RPT>
-__global__ void __launch_bounds__(256, 3) k_render_vjp(const Args a) {
+template <int RPT, bool TAPE>
+__global__ void __launch_bounds__(256, TAPE ? 4 : 3) k_render_vjp(const Args a) {
     extern __shared__ __align__(16) unsigned char sm[];
     __shared__ int s_env, s_flag, s_item;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, NW = blockDim.x >> 5;
     const int M = a.M, S = a.S, NM = a.NM;
     const float4* prim = reinterpret_cast<const float4*>(sm + a.sm.prim);
-    const bool recast = a.sen[0].tape == nullptr;
+    constexpr bool recast = !TAPE;
     WList L;
     if (recast) L = wlist_at(sm + a.sm.wlist + (size_t)warp * a.sm.wstride, a.ns_max, a.nb_max);
     if (threadIdx.x == 0) mbar_init(reinterpret_cast<uint64_t*>(sm + a.sm.mbar));
@@ -284,56 +293,53 @@ __global__ void __launch_bounds__(256, 3) k_render_vjp(const Args a) {
                 for (int si = 0; si < S; ++si) {
                     const Sensor& sen = a.sen[si];
                     if (!sen.gout) continue;
-                    int4 meta = make_int4(0, 0, -1, 0);
-                    if (recast) meta = warp_build_list(prim, ns, nb, o, R, sen, a.cull, L, a.ns_max);
-                    const int nch = (sen.R + 32 * RPT - 1) / (32 * RPT);
                     const size_t base = ti * sen.R;
+                    if (TAPE) {
+                        // taped hit ids: rays in slot order j = lane, lane + 32, ...
+                        for (int j = lane; j < sen.R; j += 32) {
+                            const int ray = out_index(sen, j);
+                            const int id = sen.tape[base + ray];
+                            if (id < 0) continue;
+                            float d[3];
+                            const float4 db = ray_dir(sen, R, j, d);
+                            ray_vjp(prim, ns, id, o, d[0], d[1], d[2], db, sen, sen.gout[base + ray], go, gR);
+                        }
+                        continue;
+                    }
+                    const int4 meta = warp_build_list(prim, ns, nb, o, R, sen, a.cull, L, a.ns_max);
+                    const int nch = (sen.R + 32 * RPT - 1) / (32 * RPT);
                     for (int ch = 0; ch < nch; ++ch) {
-                        float dx[RPT], dy[RPT], dz[RPT], fac[RPT], tb[RPT];
-                        int id[RPT];
-                        item_rays<RPT>(sen, R, ch, lane, dx, dy, dz, fac, tb);
-                        if (recast) {
-                            int bi[RPT];
+                        float dx[RPT], dy[RPT], dz[RPT], tb[RPT];
+                        int bi[RPT];
+                        item_rays<RPT>(sen, R, ch, lane, dx, dy, dz, tb);
 #pragma unroll
-                            for (int r = 0; r < RPT; ++r) bi[r] = -1;
-                            if (meta.z < 0) {
-                                if (a.cull > 1 && sen.cone) {
-                                    const int2 nsub = chunk_slots(L, meta, a.ns_max, sen, a.cull, ch, R);
-                                    cast_sub<RPT>(L, nsub, a.ns_max, dx, dy, dz, tb, bi);
-                                } else {
-                                    cast_list<RPT>(L, meta, a.ns_max, dx, dy, dz, tb, bi);
-                                }
-                            }
-#pragma unroll
-                            for (int r = 0; r < RPT; ++r) id[r] = (meta.z >= 0 || bi[r] < 0) ? -1 : L.id[bi[r]];
-                        } else {
-#pragma unroll
-                            for (int r = 0; r < RPT; ++r) {
-                                const int j = ch * 32 * RPT + r * 32 + lane;
-                                id[r] = j < sen.R ? sen.tape[base + out_index(sen, j)] : -1;
+                        for (int r = 0; r < RPT; ++r) bi[r] = -1;
+                        if (meta.z < 0) {
+                            if (a.cull > 1 && sen.cone) {
+                                const int2 nsub = chunk_slots(L, meta, a.ns_max, sen, a.cull, ch, R);
+                                cast_sub<RPT>(L, nsub, a.ns_max, dx, dy, dz, tb, bi);
+                            } else {
+                                cast_list<RPT>(L, meta, a.ns_max, dx, dy, dz, tb, bi);
                             }
                         }
 #pragma unroll
                         for (int r = 0; r < RPT; ++r) {
                             const int j = ch * 32 * RPT + r * 32 + lane;
-                            if (j >= sen.R || id[r] < 0) continue;
-                            ray_vjp(prim, ns, id[r], o, dx[r], dy[r], dz[r], __ldg(sen.dir + j), sen,
+                            if (j >= sen.R || meta.z >= 0 || bi[r] < 0) continue;
+                            ray_vjp(prim, ns, L.id[bi[r]], o, dx[r], dy[r], dz[r], __ldg(sen.dir + j), sen,
                                     sen.gout[base + out_index(sen, j)], go, gR);
                         }
                     }
                     __syncwarp();
                 }
             }
+            float v12[12];
 #pragma unroll
-            for (int k = 0; k < 3; ++k) go[k] = warp_sum(go[k]);
+            for (int k = 0; k < 3; ++k) v12[k] = go[k];
 #pragma unroll
-            for (int k = 0; k < 9; ++k) gR[k] = warp_sum(gR[k]);
-            if (lane == 0) {
-#pragma unroll
-                for (int k = 0; k < 3; ++k) a.gposes[ti * 12 + k] = go[k];
-#pragma unroll
-                for (int k = 0; k < 9; ++k) a.gposes[ti * 12 + 3 + k] = gR[k];
-            }
+            for (int k = 0; k < 9; ++k) v12[3 + k] = gR[k];
+            const float tot = warp_sum12(v12);
+            if (!(lane & 1) && (lane >> 1) < 12) a.gposes[ti * 12 + (lane >> 1)] = tot;
         }
         __syncthreads();
     }
@@ -466,7 +472,9 @@ __global__ void __launch_bounds__(128) k_physics_bwd(const Args a) {
         __syncwarp();
     }
     if (on && a.g_s0)
-        for (int k = 0; k < D; ++k) a.g_s0[(size_t)i * D + k] = g[k];
+#pragma unroll
+        for (int k = 0; k < 16; ++k)
+            if (k < D) a.g_s0[(size_t)i * D + k] = g[k];
 }
 
 // ------------------------------------------------------------ launchers
@@ -501,11 +509,16 @@ template <int RPT>
 static cudaError_t render_rpt(bool vjp, bool launch, const Args& a, int grid, int block, size_t smem,
                               cudaStream_t st, int* occ) {
     cudaError_t e;
-    if (vjp) {
-        e = cudaFuncSetAttribute(k_render_vjp<RPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (vjp && a.sen[0].tape) {  // taped hit ids: one kernel for every RPT
+        e = cudaFuncSetAttribute(k_render_vjp<1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        if (!launch) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k_render_vjp<RPT>, block, smem);
-        k_render_vjp<RPT><<<grid, block, smem, st>>>(a);
+        if (!launch) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k_render_vjp<1, true>, block, smem);
+        k_render_vjp<1, true><<<grid, block, smem, st>>>(a);
+    } else if (vjp) {
+        e = cudaFuncSetAttribute(k_render_vjp<RPT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        if (!launch) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k_render_vjp<RPT, false>, block, smem);
+        k_render_vjp<RPT, false><<<grid, block, smem, st>>>(a);
     } else {
         e = cudaFuncSetAttribute(k_render<RPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;

@@ -105,3 +105,20 @@ def test_valid_config_without_gpu_fails_cleanly(lib):
     cfg = binding.make_config(synth.preset("pointmass_64env_depth16x9_10sph"))
     rc, h = _create_rc(lib, cfg)
     assert rc == -4 and h is None
+
+
+def test_graph_and_profiling_null_pointers(lib):
+    assert lib.sim_profile(None, 1) == -2
+    assert lib.sim_kernel_times(None, None, None, 0) == -2
+    assert lib.sim_graph_create(None, None, None) == -2
+    assert lib.sim_graph_launch(None, None) == -2
+    assert lib.sim_graph_kernels(None, None) == -2
+    assert lib.sim_graph_destroy(None) == 0
+
+
+def test_graph_io_layout_matches_header():
+    src = open(os.path.join(ROOT, "include", "diffsim.h")).read()
+    body = src[src.index("typedef struct sim_graph_io {"):src.index("} sim_graph_io;")]
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    n = sum(len(d.split(",")) for d in re.findall(r"\*\s*([^;]+);", body))
+    assert ctypes.sizeof(binding.SimGraphIO) == 8 * n

@@ -184,15 +184,28 @@ def test_steps_equal_rollout(pair):
     assert torch.equal(sim.get_state(), pair.sT)
 
 
-def test_rays_per_thread_variants_agree(pair):
+def test_launch_shape_variants_agree(pair):
+    """Rays per thread, warps per CTA and culling mode change only the work
+    split: outputs and adjoint gradients agree bit for bit."""
     p = pair.p
     if p["cam"] is None:
         pytest.skip("no camera")
-    for rpt in (1, 3, 8):
-        s2 = Simulator(p, pair.inp, rays_per_thread=rpt)
+    cot = synth.cotangents(p, seed=9)
+    g_r = dev(cot["g_r"])
+    g_d = dev(cot["g_depth"])
+    g_l = dev(cot["g_lidar"]) if "g_lidar" in cot else None
+    ref = None
+    for ex in (dict(), dict(rays_per_thread=1), dict(rays_per_thread=3, warps_per_cta=4),
+               dict(rays_per_thread=8, cull=2), dict(rays_per_thread=2, cull=1, tape_hits=0)):
+        s2 = Simulator(p, pair.inp, **ex)
         s2.reset(dev(pair.inp["s0"]))
         o2 = s2.rollout(pair.act)
-        assert torch.equal(pair.out["depth"], o2["depth"]), rpt
+        ga, gs = s2.backward(g_r, g_d, g_l)
+        assert torch.equal(pair.out["depth"], o2["depth"]), ex
+        if ref is None:
+            ref = (ga, gs)
+        else:
+            assert torch.equal(ref[0], ga) and torch.equal(ref[1], gs), ex
 
 
 def test_checkpoint_and_tape_variants_agree(pair):
