@@ -153,7 +153,8 @@ def in_range(x, lo, hi, margin=0.1):
     margin (hi - lo): where the surrogate was trained."""
     x = np.asarray(x, np.float64)
     span = np.asarray(hi, np.float64) - np.asarray(lo, np.float64)
-    return np.all((x >= lo - margin * span) & (x <= hi + margin * span), axis=1)
+    m = margin * span if margin > 0 else np.zeros_like(span)  # no 0 * inf for unbounded features
+    return np.all((x >= lo - m) & (x <= hi + m), axis=1)
 
 
 # --------------------------------------------------------------- rollout

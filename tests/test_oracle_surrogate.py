@@ -197,3 +197,12 @@ def test_rollout_falls_back_outside_the_trained_range():
     for t in range(4):
         s = plain(s, acts[t].astype(np.float32).astype(np.float64)).astype(np.float32).astype(np.float64)
         np.testing.assert_array_equal(states[t + 1], s)
+
+
+def test_in_range_unbounded_features_and_zero_margin():
+    lo = np.array([-np.inf, 0.0] + [0.0] * 15)
+    hi = np.array([np.inf, 1.0] + [1.0] * 15)
+    x = np.full((2, 17), 0.5)
+    x[1, 1] = 1.0 + 1e-9
+    np.testing.assert_array_equal(S.in_range(x, lo, hi, margin=0.0), [True, False])
+    np.testing.assert_array_equal(S.in_range(x, lo, hi, margin=0.1), [True, True])
