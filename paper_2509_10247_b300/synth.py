@@ -86,7 +86,18 @@ PRESETS = {
         init_lo=(-18.0, -18.0, 1.0), init_hi=(18.0, 18.0, 9.0),
         bound_lo=(-INF, -INF, 0.0), bound_hi=(INF, INF, 10.0),
         pos_sq=0, w_obs=10.0, terminate=1),
+    # rigid-body dynamics alone (no sensor, no obstacle, no termination): the
+    # transition source and the rollout workload of the learned surrogate,
+    # 65536 envs x 32 steps
+    "surrogate_rigid_65536env_32step": dict(
+        model="rigid", n_env=65536, horizon=32, dt=0.005, cam=None, map_counts=[(0, 0)],
+        n_maps=1, pos_sq=0, terminate=0),
 }
+
+# Surrogate MLP sizes (inputs: state 13 + action 4; two hidden layers of 256;
+# outputs: the 13 residuals), parameter order W1, b1, W2, b2, W3, b3.
+SURR_SHAPES = (("W1", (256, 17)), ("b1", (256,)), ("W2", (256, 256)), ("b2", (256,)),
+               ("W3", (13, 256)), ("b3", (13,)))
 
 
 def preset(name, **overrides):
@@ -207,3 +218,43 @@ def cotangents(p, seed=1, depth=True, lidar=True):
         R = p["lidar"][0] * p["lidar"][1]
         out["g_lidar"] = _f32(rng.standard_normal((T, NM, R)))
     return out
+
+
+def surrogate_init(seed=0, scale=1.0):
+    """Initial surrogate parameters: weights U(-1, 1) * scale / sqrt(fan_in),
+    biases U(-0.1, 0.1) * scale; returns (flat float32 vector, dict of float64
+    views with float32 values)."""
+    rng = np.random.default_rng(seed)
+    parts, views = [], {}
+    for name, shape in SURR_SHAPES:
+        if name.startswith("W"):
+            a = rng.uniform(-1.0, 1.0, size=shape) * scale / math.sqrt(shape[1])
+        else:
+            a = rng.uniform(-0.1, 0.1, size=shape) * scale
+        a = _f32(a)
+        views[name] = a
+        parts.append(a.reshape(-1))
+    return np.concatenate(parts).astype(np.float32), views
+
+
+def surrogate_split(flat):
+    """Dict of float64 arrays from a flat parameter vector."""
+    out, o = {}, 0
+    flat = np.asarray(flat, dtype=np.float64)
+    for name, shape in SURR_SHAPES:
+        n = int(np.prod(shape))
+        out[name] = flat[o:o + n].reshape(shape)
+        o += n
+    return out
+
+
+def surrogate_actions(n_env, steps, seed=0):
+    """Random rigid-body actions U(-1, 1)^4 per env and step, float32 [steps, n_env, 4]."""
+    rng = np.random.default_rng(seed)
+    return rng.uniform(-1.0, 1.0, size=(steps, n_env, 4)).astype(np.float32)
+
+
+def minibatch_order(n, seed, epoch):
+    """Seeded permutation of the n transition rows for one epoch (int32)."""
+    rng = np.random.default_rng([seed, epoch])
+    return rng.permutation(n).astype(np.int32)

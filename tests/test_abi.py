@@ -5,6 +5,7 @@ import ctypes
 import os
 import re
 
+import numpy as np
 import pytest
 
 from paper_2509_10247_b300 import binding, build, synth
@@ -18,10 +19,10 @@ def lib():
     return binding.lib()
 
 
-def declared_functions():
-    src = open(os.path.join(ROOT, "include", "diffsim.h")).read()
+def declared_functions(header="diffsim.h", prefix="sim_"):
+    src = open(os.path.join(ROOT, "include", header)).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(sim_[a-z_]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(%s[a-z_]+)\s*\(" % prefix, src)))
 
 
 def test_every_declared_symbol_is_exported(lib):
@@ -122,3 +123,34 @@ def test_graph_io_layout_matches_header():
     body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
     n = sum(len(d.split(",")) for d in re.findall(r"\*\s*([^;]+);", body))
     assert ctypes.sizeof(binding.SimGraphIO) == 8 * n
+
+
+def test_surrogate_symbols_exported(lib):
+    from paper_2509_10247_b300 import surrogate
+    names = declared_functions("surrogate.h", "surr_")
+    assert sorted(surrogate.SYMBOLS) == names
+    for n in names:
+        assert hasattr(lib, n), n
+    src = open(os.path.join(ROOT, "include", "surrogate.h")).read()
+    assert "#define SURR_NPARAM %d" % surrogate.NPARAM in src
+    assert "#define SURR_NSTATS %d" % surrogate.NSTATS in src
+    assert sum(n for _, n in surrogate.STATS_LAYOUT) == surrogate.NSTATS
+    from paper_2509_10247_b300 import synth
+    assert sum(int(np.prod(s)) for _, s in synth.SURR_SHAPES) == surrogate.NPARAM
+
+
+def test_surrogate_rejects_bad_config(lib):
+    from paper_2509_10247_b300 import surrogate, synth
+    phys = binding.make_config(synth.preset("surrogate_rigid_65536env_32step"))
+    for kw in (dict(batch=100), dict(batch=0), dict(lr=0.0), dict(beta1=1.0), dict(margin=-1.0)):
+        cfg = surrogate.SurrConfig(batch=kw.get("batch", 256), splits=0, lr=kw.get("lr", 1e-3),
+                                   beta1=kw.get("beta1", 0.9), beta2=0.999, eps=1e-8, margin=kw.get("margin", 0.1))
+        h = ctypes.c_void_p()
+        assert lib.surr_create(ctypes.byref(cfg), ctypes.byref(phys), ctypes.byref(h)) in (-1, -3)
+    cfg = surrogate.SurrConfig(batch=256, splits=0, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, margin=0.1)
+    pm = binding.make_config(synth.preset("pointmass_64env_depth16x9_10sph"))
+    h = ctypes.c_void_p()
+    assert lib.surr_create(ctypes.byref(cfg), ctypes.byref(pm), ctypes.byref(h)) == -9
+    assert lib.surr_create(None, None, None) == -2
+    assert lib.surr_destroy(None) == 0
+    assert lib.surr_rollout(None, None, None, 0, 0, None, None, None, None) == -2

@@ -1,0 +1,215 @@
+"""Surrogate MLP on the tensor cores (through the C ABI) against the FP64
+oracle with bf16 rounding: forward pass, statistics, gradients, one Adam
+step, rollouts with the trained-range fallback; and the trained surrogate's
+rollout error against the FP64 rigid-body simulator.
+
+Tolerance of a network output (derivation): both sides round the same
+operands to bf16 and sum exact products, the GPU in fp32 (relative error of
+a 256-term sum below 256 * 2^-24 of the absolute sum S = sum |w h| + |b|), the
+oracle in fp64.  Where an fp32 pre-activation lies within that error of a
+bf16 rounding boundary, the two sides round one activation to neighbouring
+bf16 values, changing an output by at most 2^-8 |w h| <= 2^-8 S per flipped
+activation.  So: every output within 2^-5 S (a few flips), the median within
+1e-5 S, and at most 5% of the outputs beyond 1e-4 S."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle import surrogate as S
+from paper_2509_10247_b300 import synth
+from paper_2509_10247_b300.surrogate import Surrogate, collect_transitions, stats_vector, train
+
+pytestmark = pytest.mark.gpu
+
+P_RIGID = synth.preset("surrogate_rigid_65536env_32step")
+
+
+def dev(a, dtype=torch.float32):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=dtype, device="cuda")
+
+
+def host(t):
+    return t.detach().cpu().numpy().astype(np.float64)
+
+
+def random_states(rng, n):
+    s = np.zeros((n, 13))
+    s[:, 0:3] = rng.uniform(-5, 5, (n, 3))
+    q = rng.standard_normal((n, 4))
+    s[:, 3:7] = q / np.linalg.norm(q, axis=1, keepdims=True)
+    s[:, 7:10] = rng.standard_normal((n, 3))
+    s[:, 10:13] = rng.standard_normal((n, 3)) * 2.0
+    return s.astype(np.float32)
+
+
+def data_stats(rng, n=4000):
+    X = np.concatenate([random_states(rng, n), rng.uniform(-1, 1, (n, 4)).astype(np.float32)], axis=1)
+    D = (rng.standard_normal((n, 13)) * np.linspace(0.001, 0.05, 13)).astype(np.float32)
+    st = S.column_stats(X, D)
+    return {k: np.asarray(v, np.float32) for k, v in st.items()}
+
+
+def check_outputs(y, f, P, what):
+    W3b = S.bf16_round(P["W3"])
+    scale = np.abs(f["h2"]) @ np.abs(W3b).T + np.abs(P["b3"])
+    rel = np.abs(y - f["y"]) / scale
+    assert rel.max() <= 2.0 ** -5, (what, rel.max())
+    assert np.median(rel) <= 1e-5, (what, np.median(rel))
+    assert (rel > 1e-4).mean() <= 0.05, (what, (rel > 1e-4).mean())
+
+
+def make_surrogate(seed=3, scale=1.0, batch=256, **kw):
+    flat, P = synth.surrogate_init(seed, scale)
+    sur = Surrogate(P_RIGID, batch=batch, **kw)
+    sur.set_params(flat)
+    return sur, flat, P
+
+
+@pytest.mark.parametrize("n", [1, 128, 333])
+def test_forward_matches_oracle(n):
+    rng = np.random.default_rng(n)
+    st = data_stats(rng)
+    sur, flat, P = make_surrogate(scale=2.0)
+    sur.set_stats(st)
+    X = np.concatenate([random_states(rng, n), rng.uniform(-1.3, 1.3, (n, 4)).astype(np.float32)], axis=1)
+    Y = host(sur.forward(dev(X)))
+    assert sur.status() == 0
+    np.testing.assert_array_equal(sur.get_params(), flat)
+    xh = S.normalise_inputs(X[:, :13], X[:, 13:], st["mu_x"], st["rs_x"])
+    f = S.forward(P, xh)
+    check_outputs(Y, f, P, "forward n=%d" % n)
+
+
+def test_fit_stats_matches_oracle():
+    rng = np.random.default_rng(5)
+    n = 100003
+    X = np.concatenate([random_states(rng, n), rng.uniform(-1.5, 1.5, (n, 4)).astype(np.float32)], axis=1)
+    S1 = (X[:, :13] + rng.standard_normal((n, 13)) * 0.01).astype(np.float32)
+    sur, _, _ = make_surrogate()
+    sur.fit_stats(dev(X), dev(S1))
+    g = sur.get_stats()
+    Xc = X.copy()
+    Xc[:, 13:] = np.clip(Xc[:, 13:], -1, 1)
+    o = S.column_stats(Xc, (S1 - X[:, :13]).astype(np.float32))
+    for k in ("mu_x", "rs_x", "lo_x", "hi_x", "mu_d", "sd_d", "rs_d"):
+        np.testing.assert_allclose(g[k], o[k], rtol=2e-6, atol=1e-9, err_msg=k)
+
+
+def _batch(rng, n=2000, B=256):
+    X = np.concatenate([random_states(rng, n), rng.uniform(-1.2, 1.2, (n, 4)).astype(np.float32)], axis=1)
+    S1 = (X[:, :13] + rng.standard_normal((n, 13)) * np.linspace(0.001, 0.05, 13)).astype(np.float32)
+    idx = rng.permutation(n)[:B].astype(np.int32)
+    return X, S1, idx
+
+
+def test_gradients_match_oracle():
+    rng = np.random.default_rng(7)
+    st = data_stats(rng)
+    sur, flat, P = make_surrogate(seed=8, scale=2.0, batch=256)
+    sur.set_stats(st)
+    X, S1, idx = _batch(rng)
+    loss = torch.zeros(1, device="cuda")
+    grads = torch.zeros(73741, device="cuda")
+    sur.train_step(dev(X), dev(S1), dev(idx, torch.int32), apply=False, loss=loss, grads=grads)
+    assert sur.status() == 0
+    np.testing.assert_array_equal(sur.get_params(), flat)  # apply = 0 leaves the parameters alone
+    xh = S.normalise_inputs(X[idx, :13], X[idx, 13:], st["mu_x"], st["rs_x"])
+    t = S.targets(X[idx, :13], S1[idx], st["mu_d"], st["rs_d"])
+    L, go, _ = S.loss_grads(P, xh, t)
+    assert abs(loss.item() - L) <= 1e-4 * L
+    g = synth.surrogate_split(host(grads))
+    for k in go:
+        e = np.linalg.norm(g[k] - go[k]) / np.linalg.norm(go[k])
+        assert e <= 1e-2, (k, e)
+        assert np.median(np.abs(g[k] - go[k])) <= 1e-4 * np.abs(go[k]).max(), k
+
+
+def test_adam_step_matches_oracle():
+    rng = np.random.default_rng(9)
+    st = data_stats(rng)
+    sur, flat, P = make_surrogate(seed=10, scale=2.0, batch=256)
+    sur.set_stats(st)
+    X, S1, idx = _batch(rng)
+    sur.train_step(dev(X), dev(S1), dev(idx, torch.int32), apply=True)
+    P1 = sur.get_params().astype(np.float64)
+    xh = S.normalise_inputs(X[idx, :13], X[idx, 13:], st["mu_x"], st["rs_x"])
+    t = S.targets(X[idx, :13], S1[idx], st["mu_d"], st["rs_d"])
+    _, go, _ = S.loss_grads(P, xh, t)
+    g = np.concatenate([go[k].reshape(-1) for k, _ in synth.SURR_SHAPES])
+    w1, _, _ = S.adam_step(flat.astype(np.float64), g, 0.0, 0.0, 1)
+    # the first Adam step moves a weight by ~ lr sign(g): compare where the
+    # gradient is well resolved (the update's sign is then unambiguous)
+    strong = np.abs(g) > 1e-2 * np.abs(g).max()
+    assert strong.mean() > 0.2
+    np.testing.assert_allclose(P1[strong], w1[strong], rtol=0, atol=2e-6)
+    assert np.abs(P1 - w1).max() <= 2.1e-3  # at most one full step apart anywhere
+
+
+def _plain(s, a):
+    return np.stack([oracle.rb_step(P_RIGID, s[i], a[i]) for i in range(s.shape[0])])
+
+
+def test_rollout_matches_oracle_with_fallback():
+    rng = np.random.default_rng(11)
+    st = data_stats(rng)
+    st["lo_x"][:] = -np.inf
+    st["hi_x"][:] = np.inf
+    st["lo_x"][0], st["hi_x"][0] = -4.0, 4.0  # x position trained in [-4, 4]: margin 0.8
+    N, T = 300, 6
+    s0 = random_states(rng, N)
+    side = rng.integers(0, 3, N)
+    s0[:, 0] = np.where(side == 0, rng.uniform(-5.0, -4.95, N),
+                        np.where(side == 1, rng.uniform(-4.6, 4.6, N), rng.uniform(4.95, 5.0, N)))
+    s0[:, 7:10] *= 0.2
+    acts = rng.uniform(-1, 1, (T, N, 4)).astype(np.float32)
+    sur, flat, P = make_surrogate(seed=12, scale=0.5)
+    sur.set_stats(st)
+    o = sur.rollout(dev(s0), dev(acts))
+    assert sur.status() == 0
+    states = host(o["states"])
+    fb = host(o["fallback"]).astype(bool)
+    so, fbo = S.rollout(P, st, s0, acts, _plain)
+    np.testing.assert_array_equal(fb, fbo)
+    assert fb[0].sum() > 50 and (~fb[0]).sum() > 50
+    out = fbo.all(axis=0)
+    # fallback environments: the plain rigid step, fp32 against fp64
+    np.testing.assert_allclose(states[:, out], so[:, out], rtol=1e-5, atol=1e-5)
+    # surrogate environments: per-step flips bounded as for the forward pass
+    e = np.abs(states[:, ~out] - so[:, ~out])
+    sd = np.asarray(st["sd_d"], np.float64)
+    assert np.median(e) <= 1e-6
+    assert (e.max(axis=(0, 1)) <= T * 2.0 ** -5 * sd * 50 + 1e-6).all(), e.max(axis=(0, 1))
+    np.testing.assert_allclose(host(o["sT"]), states[T])
+
+
+def test_training_fits_the_rigid_step():
+    """The trained surrogate's 32-step rollout error against the FP64 rigid
+    simulator (position RMSE, attitude angle), against the zero-residual
+    baseline s' = s + mu_d."""
+    torch.manual_seed(0)
+    X, S1 = collect_transitions(P_RIGID, n_env=8192, steps=96, seed=21)
+    sur, _, _ = make_surrogate(seed=22, batch=4096)
+    sur.fit_stats(X, S1)
+    losses = train(sur, X, S1, epochs=4, seed=23)
+    assert sur.status() == 0
+    assert losses[-1] < 0.1 * losses[0], losses
+    n, T = 2048, 32
+    q = dict(P_RIGID, n_env=n, horizon=T)
+    inp = synth.make_inputs(q, seed=24)
+    o = sur.rollout(dev(inp["s0"]), dev(inp["actions"]))
+    ref = oracle.Oracle(q, inp).rollout(inp["s0"], inp["actions"])["states"]
+    s = host(o["states"])[T]
+    r = ref[T]
+    rmse = np.sqrt(np.mean(np.sum((s[:, :3] - r[:, :3]) ** 2, axis=1)))
+    dq = np.abs(np.sum(s[:, 3:7] * r[:, 3:7], axis=1))
+    ang = 2 * np.arccos(np.clip(dq, 0, 1))
+    st = sur.get_stats()
+    base = inp["s0"].copy()
+    for _ in range(T):
+        base = base + st["mu_d"]
+    rmse0 = np.sqrt(np.mean(np.sum((base[:, :3] - r[:, :3]) ** 2, axis=1)))
+    print("surrogate t=32: position RMSE %.3e m (zero-residual %.3e), attitude error mean %.3e rad, "
+          "fallback %.3f, losses %s" % (rmse, rmse0, ang.mean(), host(o["fallback"]).mean(), losses))
+    assert rmse < 0.2 * rmse0
+    assert ang.mean() < 0.05
