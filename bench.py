@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-graph", action="store_true")
+    ap.add_argument("--surr-epochs", type=int, default=3)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--n-env", type=int, default=None,
                     help="override the number of environments (profiling on a smaller case)")
@@ -349,6 +350,112 @@ def run_ours(args, rank, world):
     return 0
 
 
+SURROGATE_WORKLOAD = "surrogate_rigid_65536env_32step"
+SURR_TRANSITIONS = (65536, 153)  # envs x steps: 10.03M transitions of the rigid step
+SURR_FLOP_PER_SAMPLE = 2 * (17 * 256 + 256 * 256 + 256 * 13)  # forward multiply-adds x 2
+
+
+def run_surrogate(args, rank, world):
+    """Learned surrogate of the rigid step: 10M simulator transitions, GPU
+    training with the library's tensor-core kernels, then the 65536 x 32
+    rollout timed against the plain GPU rigid step; the state error is taken
+    against that plain step (itself held to the FP64 oracle by the tests)."""
+    import torch
+    from paper_2509_10247_b300 import build as B, synth
+    from paper_2509_10247_b300.binding import Simulator
+    from paper_2509_10247_b300.surrogate import Surrogate, collect_transitions, train
+    B.build()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    p = workload_params(SURROGATE_WORKLOAD, args.n_env)
+    N, T = p["n_env"], p["horizon"]
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    # 1. transitions from the simulator's own rigid step
+    e0, e1 = ev(), ev()
+    e0.record()
+    X, S1 = collect_transitions(p, n_env=SURR_TRANSITIONS[0], steps=SURR_TRANSITIONS[1], seed=args.seed + 100,
+                                device=dev)
+    e1.record()
+    torch.cuda.synchronize()
+    collect_ms = e0.elapsed_time(e1)
+    # 2. training
+    sur = Surrogate(p, batch=8192, device=dev)
+    flat, _ = synth.surrogate_init(args.seed + 101)
+    sur.set_params(flat)
+    sur.fit_stats(X, S1)
+    e0, e1 = ev(), ev()
+    e0.record()
+    losses = train(sur, X, S1, epochs=args.surr_epochs, seed=args.seed + 102)
+    e1.record()
+    torch.cuda.synchronize()
+    train_ms = e0.elapsed_time(e1)
+    steps = args.surr_epochs * (X.shape[0] // 8192)
+    if sur.status() != 0:
+        raise RuntimeError("surrogate status flagged during training")
+    # 3. rollout: surrogate vs plain rigid step, same states and actions
+    inp = synth.make_inputs(p, seed=args.seed + 103)
+    s0 = torch.as_tensor(inp["s0"], dtype=torch.float32, device=dev)
+    act = torch.as_tensor(inp["actions"], dtype=torch.float32, device=dev)
+    sim = Simulator(p, inp, device=dev)
+    sim.profile(True)
+
+    def plain():
+        sim.reset(s0)
+        return sim.rollout(act, depth=False, lidar=False)
+
+    def surr():
+        return sur.rollout(s0, act, states=False, fallback=True)
+
+    for _ in range(args.warmup):
+        plain(); surr()
+    torch.cuda.synchronize()
+    sim.kernel_times(reset=True)
+    clocks = Clocks(local)
+    times = {}
+    for name, fn in (("surrogate", surr), ("plain", plain)):
+        a0, a1 = ev(), ev()
+        a0.record()
+        for _ in range(args.steps):
+            o = fn()
+        a1.record()
+        torch.cuda.synchronize()
+        times[name] = a0.elapsed_time(a1) / args.steps
+    ck = clocks.stop()
+    so = surr()
+    plain()
+    ref = sim.get_state()
+    torch.cuda.synchronize()
+    d = (so["sT"] - ref).double()
+    rmse = float(torch.sqrt(torch.mean(torch.sum(d[:, :3] ** 2, dim=1))))
+    dq = torch.abs(torch.sum(so["sT"][:, 3:7].double() * ref[:, 3:7].double(), dim=1)).clamp(max=1.0)
+    ang = float(torch.mean(2 * torch.acos(dq)))
+    fb = float(so["fallback"].float().mean())
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) \
+        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else {"bf16_tflops": 1800.0}
+    flop = SURR_FLOP_PER_SAMPLE * N * T
+    achieved = flop / (times["surrogate"] / 1e3) / 1e12
+    line = {"metric": "surrogate rollout env-steps/s at 65536 envs x 32 steps", "workload": SURROGATE_WORKLOAD,
+            "value": N * T / (times["surrogate"] / 1e3), "unit": "env-steps/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": times["surrogate"],
+            "higher_is_better": True, "dtype": "bf16 (fp32 accumulate)", "data": "synthetic",
+            "plain_step": {"ms": times["plain"], "value": N * T / (times["plain"] / 1e3)},
+            "speedup_vs_plain_step": times["plain"] / times["surrogate"],
+            "state_error_vs_plain_step_t32": {"position_rmse_m": rmse, "attitude_mean_rad": ang,
+                                              "fallback_fraction": fb},
+            "training": {"transitions": int(X.shape[0]), "epochs": args.surr_epochs, "batch": 8192,
+                         "steps": steps, "ms": train_ms, "samples_per_s": steps * 8192 / (train_ms / 1e3),
+                         "tflops": 3 * SURR_FLOP_PER_SAMPLE * steps * 8192 / (train_ms / 1e3) / 1e12,
+                         "loss_per_epoch": losses, "collect_ms": collect_ms},
+            "roofline": {"bound": "tensor", "achieved": achieved, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
+                         "frac": achieved / peaks["bf16_tflops"], "traffic": None,
+                         "kernel": "k_surr_fwd (fused persistent rollout)",
+                         "peak_basis": "measured cuBLAS bf16 burst (MEASURED_PEAKS.json)"},
+            "clocks": ck}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_e2e(args, sim, inp, dev, g_r, g_d, out, g_a, g_s0, p):
     import torch
     T, NM = p["horizon"], sim.NM
@@ -401,6 +508,8 @@ def main():
     try:
         if args.impl == "reference":
             return run_reference(args, rank, world)
+        if args.workload == SURROGATE_WORKLOAD:
+            return run_surrogate(args, rank, world)
         return run_ours(args, rank, world)
     finally:
         if world > 1:

@@ -26,9 +26,11 @@ constexpr int WG_STAGES = 4;
 constexpr uint32_t WG_STAGE = 16384 + 32768;
 constexpr uint32_t SMEM_WG_LAUNCH = WG_STAGES * WG_STAGE + 1024 + 128;
 
-__device__ __forceinline__ float silu_t(float z) { return z / (1.f + __expf(-z)); }
+// SiLU and its derivative with the fast exponential and division (a few
+// ulp of fp32; activations and cotangents are rounded to bf16 right after).
+__device__ __forceinline__ float silu_t(float z) { return __fdividef(z, 1.f + __expf(-z)); }
 __device__ __forceinline__ float dsilu_t(float z) {
-    const float sg = 1.f / (1.f + __expf(-z));
+    const float sg = __fdividef(1.f, 1.f + __expf(-z));
     return sg * (1.f + z * (1.f - sg));
 }
 

@@ -213,3 +213,44 @@ def test_training_fits_the_rigid_step():
           "fallback %.3f, losses %s" % (rmse, rmse0, ang.mean(), host(o["fallback"]).mean(), losses))
     assert rmse < 0.2 * rmse0
     assert ang.mean() < 0.05
+
+
+def test_full_size_surrogate_workload():
+    """The learned-surrogate workload at full size: 10M transitions of the
+    simulator's rigid step, three epochs of GPU training, the 65536 x 32
+    rollout; sampled environments are recomputed by the FP64 rigid-body
+    oracle (position RMSE and attitude error at t = 32 reported and bounded),
+    and the sample's surrogate rollout is held to the bf16 oracle MLP rolled
+    out from the same initial states with the trained parameters."""
+    import bench
+    p = synth.preset(bench.SURROGATE_WORKLOAD)
+    X, S1 = collect_transitions(p, n_env=bench.SURR_TRANSITIONS[0], steps=bench.SURR_TRANSITIONS[1], seed=31)
+    assert X.shape[0] >= 10_000_000
+    sur, _, _ = make_surrogate(seed=32, batch=8192)
+    sur.fit_stats(X, S1)
+    losses = train(sur, X, S1, epochs=3, seed=33)
+    del X, S1
+    assert losses[-1] < 0.02 * losses[0], losses
+    inp = synth.make_inputs(p, seed=34)
+    N, T = p["n_env"], p["horizon"]
+    o = sur.rollout(dev(inp["s0"]), dev(inp["actions"]))
+    assert sur.status() == 0
+    rows = np.linspace(0, N - 1, 512).astype(int)
+    q = dict(p, n_env=len(rows))
+    sub = dict(inp, s0=inp["s0"][rows], actions=inp["actions"][:, rows], targets=inp["targets"][rows],
+               pool=inp["pool"][:, rows], env_map=np.zeros(len(rows), np.int32))
+    ref = oracle.Oracle(q, sub).rollout(sub["s0"], sub["actions"])["states"]
+    s = host(o["states"])[:, rows]
+    rmse = np.sqrt(np.mean(np.sum((s[T, :, :3] - ref[T, :, :3]) ** 2, axis=1)))
+    ang = 2 * np.arccos(np.clip(np.abs(np.sum(s[T, :, 3:7] * ref[T, :, 3:7], axis=1)), 0, 1))
+    st = sur.get_stats()
+    P = synth.surrogate_split(sur.get_params())
+    so, fbo = S.rollout(P, st, sub["s0"], sub["actions"], _plain)
+    fb = host(o["fallback"])[:, rows].astype(bool)
+    print("full-size surrogate t=32: position RMSE %.3e m, attitude mean %.3e rad vs the FP64 simulator; "
+          "fallback %.4f; max |GPU - oracle MLP| position %.3e m; losses %s"
+          % (rmse, ang.mean(), fb.mean(), np.abs(s[:, :, :3] - so[:, :, :3]).max(), losses))
+    assert rmse < 5e-3 and ang.mean() < 5e-3
+    same = (fb == fbo).all(axis=0)
+    assert same.mean() > 0.99
+    assert np.median(np.abs(s[:, same, :3] - so[:, same, :3])) <= 1e-5
