@@ -65,10 +65,15 @@ def workload_params(name, n_env=None):
     return synth.preset(name) if n_env is None else synth.preset(name, n_env=n_env)
 
 
+# sources that define the render kernel and its launch (the DRAM traffic
+# recorded in profiles/traffic.txt is valid while they are unchanged)
+RENDER_SOURCES = ("sim_split.cu", "sim_raycast.cuh", "sim_kernels.cuh", "sim_device.cuh", "sim_api.cu")
+
+
 def source_hash():
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2509_10247_b300", "csrc")
-    for f in sorted(os.listdir(csrc)):
+    for f in RENDER_SOURCES:
         h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
