@@ -258,3 +258,30 @@ def minibatch_order(n, seed, epoch):
     """Seeded permutation of the n transition rows for one epoch (int32)."""
     rng = np.random.default_rng([seed, epoch])
     return rng.permutation(n).astype(np.int32)
+
+
+# Closed-loop policy (two layers, 256 hidden units, 4 actions); the input
+# width is 16 state features + camera rays + LiDAR rays of the workload.
+POLICY_HIDDEN = 256
+
+
+def policy_width(p):
+    Rc = p["cam"][0] * p["cam"][1] if p["cam"] is not None else 0
+    Rl = p["lidar"][0] * p["lidar"][1] if p["lidar"] is not None else 0
+    return 16 + Rc + Rl
+
+
+def policy_init(p, seed=0, scale=1.0):
+    """Initial policy parameters, flat float32 in the order W1 [256, F],
+    b1 [256], W2 [4, 256], b2 [4]: weights U(-1, 1) * scale / sqrt(fan_in),
+    biases U(-0.1, 0.1) * scale."""
+    rng = np.random.default_rng(seed)
+    F = policy_width(p)
+    parts = []
+    for shape in ((POLICY_HIDDEN, F), (POLICY_HIDDEN,), (4, POLICY_HIDDEN), (4,)):
+        if len(shape) == 2:
+            a = rng.uniform(-1.0, 1.0, size=shape) * scale / math.sqrt(shape[1])
+        else:
+            a = rng.uniform(-0.1, 0.1, size=shape) * scale
+        parts.append(_f32(a).reshape(-1))
+    return np.concatenate(parts).astype(np.float32)
