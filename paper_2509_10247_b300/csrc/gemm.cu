@@ -1,0 +1,142 @@
+// gemm.cu -- streamed-K tcgen05 GEMM with the closed-loop policy's epilogues
+// (see gemm.cuh).
+#include <cuda_bf16.h>
+
+#include "gemm.cuh"
+#include "umma.cuh"
+
+namespace gm {
+using namespace um;
+
+constexpr int STAGES = 4;
+constexpr uint32_t A_TILE = 16384, B_TILE = 32768, STAGE = A_TILE + B_TILE;
+constexpr uint32_t SMEM_LAUNCH = STAGES * STAGE + 1024 + 128;
+
+__global__ void __launch_bounds__(128, 1) k_gemm(const GemmArgs a) {
+    extern __shared__ __align__(1024) uint8_t smraw[];
+    const uint32_t raw = smem_u32(smraw);
+    uint8_t* sm = smraw + (((raw + 1023u) & ~1023u) - raw);
+    uint64_t* full = reinterpret_cast<uint64_t*>(sm + STAGES * STAGE);
+    uint64_t* empty = full + STAGES;
+    uint64_t* done = empty + STAGES;
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 1);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int mt = blockIdx.x, nt = blockIdx.y, sp = blockIdx.z;
+    const int n0 = nt * 256;
+    const uint32_t Nt = (uint32_t)min(256, a.N - n0);
+    const int kb0 = (int)((long long)sp * a.nkb / a.splits), kb1 = (int)((long long)(sp + 1) * a.nkb / a.splits);
+    const uint32_t bbytes = Nt * 128u;
+    if (tid == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(done, 1);
+        fence_barrier_init();
+    }
+    __syncthreads();
+    if (warp == 0) tmem_alloc(tslot, 256);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot;
+    const uint32_t sbase = smem_u32(sm);
+    bool ok = true;  // producer / MMA issuer (thread 0)
+    if (tid == 0) {
+        const int n = kb1 - kb0;
+        auto issue = [&](int i) {
+            const int s = i % STAGES;
+            const size_t kb = (size_t)(kb0 + i);
+            mbar_expect_tx(&full[s], A_TILE + bbytes);
+            bulk_g2s(sm + s * STAGE, a.A + kb * (size_t)a.RA * 128 + (size_t)mt * 128 * 128, A_TILE, &full[s]);
+            bulk_g2s(sm + s * STAGE + A_TILE, a.B + kb * (size_t)a.RB * 128 + (size_t)n0 * 128, bbytes, &full[s]);
+        };
+        for (int i = 0; i < n && i < STAGES; ++i) issue(i);
+        const uint32_t idesc = idesc_bf16(128, Nt);
+        for (int i = 0; i < n && ok; ++i) {
+            const int s = i % STAGES;
+            const uint32_t par = (uint32_t)(i / STAGES) & 1u;
+            if (!(ok = mbar_wait(&full[s], par))) break;
+            tc_fence_after();
+            const uint32_t sa = sbase + s * STAGE, sb = sa + A_TILE;
+#pragma unroll
+            for (uint32_t kk = 0; kk < 4; ++kk)
+                mma_bf16(tmem, desc_sw128(sa + 32 * kk), desc_sw128(sb + 32 * kk), idesc, (i > 0 || kk > 0));
+            mma_commit(&empty[s]);
+            if (i + STAGES < n) {
+                if (!(ok = mbar_wait(&empty[s], par))) break;
+                issue(i + STAGES);
+            }
+        }
+        if (n > 0) mma_commit(done);
+        else mbar_expect_tx(done, 0);
+    }
+    const bool all_ok = __syncthreads_and(mbar_wait(done, 0) && ok) != 0;
+    tc_fence_after();
+    const bool empty_k = kb1 <= kb0;  // no K-block: the accumulator holds nothing
+    if (all_ok) {
+        const uint32_t tq = tmem + ((32u * (uint32_t)warp) << 16);
+        const int row = mt * 128 + 32 * warp + lane;
+        const bool valid = row < a.M;
+        for (uint32_t c0 = 0; c0 < Nt; c0 += 16) {
+            float v[16];
+            tmem_ld16(tq + c0, v);
+            if (empty_k)
+#pragma unroll
+                for (int i = 0; i < 16; ++i) v[i] = 0.f;
+            if (!valid) continue;
+            const int col = n0 + (int)c0;
+            if (a.epi == EPI_STORE) {
+                float* out = a.C + ((size_t)sp * a.M + row) * a.ldc + col;
+#pragma unroll
+                for (int i = 0; i < 16; i += 4)
+                    *reinterpret_cast<float4*>(out + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+            } else if (a.epi == EPI_POLICY) {
+                float* zo = a.z_out + (size_t)row * 256 + col;
+                uint32_t hp[8];
+#pragma unroll
+                for (int i = 0; i < 16; ++i) v[i] += __ldg(a.bias + col + i);
+#pragma unroll
+                for (int i = 0; i < 16; i += 4)
+                    *reinterpret_cast<float4*>(zo + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const float s0 = __fdividef(v[2 * i], 1.f + __expf(-v[2 * i]));
+                    const float s1 = __fdividef(v[2 * i + 1], 1.f + __expf(-v[2 * i + 1]));
+                    hp[i] = pack_bf16(s0, s1);
+                }
+                uint4* ho = reinterpret_cast<uint4*>(a.h_out + (size_t)row * 256 + col);
+                ho[0] = make_uint4(hp[0], hp[1], hp[2], hp[3]);
+                ho[1] = make_uint4(hp[4], hp[5], hp[6], hp[7]);
+            } else {
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    const int n = col + i;
+                    if (n < 16) a.g_f[(size_t)row * 16 + n] = v[i];
+                    else if (n < 16 + a.Rc) a.g_cam[(size_t)row * a.Rc + (n - 16)] = v[i] * a.cam_scale;
+                    else if (n < 16 + a.Rc + a.Rl) a.g_lid[(size_t)row * a.Rl + (n - 16 - a.Rc)] = v[i] * a.lid_scale;
+                }
+            }
+        }
+    } else if (tid == 0) {
+        atomicOr(a.status, 2);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_dealloc(tmem, 256);
+    }
+}
+
+cudaError_t launch_gemm(const GemmArgs& a, cudaStream_t st) {
+    if (a.M <= 0 || a.N <= 0) return cudaSuccess;
+    if (a.N % 16 || a.RA % 128 || a.RB < a.N || a.splits < 1) return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(k_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_LAUNCH);
+    if (e != cudaSuccess) return e;
+    const dim3 grid((a.M + 127) / 128, (a.N + 255) / 256, a.splits);
+    k_gemm<<<grid, 128, SMEM_LAUNCH, st>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace gm

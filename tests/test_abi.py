@@ -154,3 +154,18 @@ def test_surrogate_rejects_bad_config(lib):
     assert lib.surr_create(None, None, None) == -2
     assert lib.surr_destroy(None) == 0
     assert lib.surr_rollout(None, None, None, 0, 0, None, None, None, None) == -2
+
+
+def test_policy_symbols_exported(lib):
+    from paper_2509_10247_b300 import policy
+    names = declared_functions("policy.h", "pol_")
+    assert sorted(policy.SYMBOLS) == names
+    for n in names:
+        assert hasattr(lib, n), n
+    L = policy._lib()
+    h = ctypes.c_void_p()
+    assert L.pol_create(0, 0, 1.0, 0, 1.0, ctypes.byref(h)) == -3
+    assert L.pol_create(4, 10, 0.0, 0, 1.0, ctypes.byref(h)) == -1
+    assert L.pol_create(4, 10, 1.0, 0, 1.0, None) == -2
+    assert L.pol_destroy(None) == 0
+    assert L.pol_backward(None, None, None, None, None, None) == -2
