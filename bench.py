@@ -54,6 +54,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--surr-epochs", type=int, default=3)
+    ap.add_argument("--horizon", type=int, default=None, help="override the horizon (closed-loop workload)")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--n-env", type=int, default=None,
                     help="override the number of environments (profiling on a smaller case)")
@@ -461,6 +462,80 @@ def run_surrogate(args, rank, world):
     return 0
 
 
+CLOSED_LOOP_WORKLOAD = "rigid_65536env_256obst_depth_lidar"
+
+
+def run_closed_loop(args, rank, world):
+    """Closed-loop policy gradient at full scale: 65536 rigid agents, 256
+    obstacles each, depth 64x48 + LiDAR 16x360, 128 steps; a two-layer policy
+    (8848 -> 256 -> 4) acts on the rendered observations, and the gradient of
+    the rollout's reward w.r.t. the policy parameters is taken by
+    backpropagation through time (per step: re-render, policy forward, the
+    simulator's step adjoint, the policy backward)."""
+    import torch
+    from paper_2509_10247_b300 import build as B, synth
+    from paper_2509_10247_b300.policy import ClosedLoop
+    B.build()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    p = workload_params(CLOSED_LOOP_WORKLOAD, args.n_env)
+    if args.horizon:
+        p["horizon"] = args.horizon
+    N, T = p["n_env"], p["horizon"]
+    inp = synth.make_inputs(p, seed=args.seed, actions=False)
+    cl = ClosedLoop(p, inp, device=dev)
+    cl.pol.set_params(synth.policy_init(p, seed=args.seed + 1))
+    s0 = torch.as_tensor(inp["s0"], dtype=torch.float32, device=dev)
+    g_r = torch.full((T, N), -1.0 / (N * T), device=dev)
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    for _ in range(args.warmup):
+        cl.gradient(s0, g_r, T=2)
+    torch.cuda.synchronize()
+    # the policy's layer-1 GEMM (M = agents, N = 256, K = 8848): one act on rendered observations
+    depth, lidar = cl.sim.render()
+    a = torch.empty(N, 4, device=dev)
+    cl.pol.act(s0, cl.targets, depth, lidar, out=a)
+    e0, e1 = ev(), ev()
+    reps = 20
+    e0.record()
+    for _ in range(reps):
+        cl.pol.act(s0, cl.targets, depth, lidar, out=a)
+    e1.record()
+    torch.cuda.synchronize()
+    act_ms = e0.elapsed_time(e1) / reps
+    F = synth.policy_width(p)
+    gemm_flop = 2.0 * N * F * 256
+    clocks = Clocks(local)
+    e0, e1 = ev(), ev()
+    e0.record()
+    for _ in range(args.steps):
+        L, g, rec = cl.gradient(s0, g_r)
+    e1.record()
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    if cl.sim.status() != 0 or cl.pol.status() != 0:
+        raise RuntimeError("device status flagged in the closed loop")
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) \
+        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else {"bf16_tflops": 1800.0}
+    line = {"metric": "closed-loop policy-gradient env-steps/s (fwd + BPTT, depth 64x48 + LiDAR 16x360)",
+            "workload": CLOSED_LOOP_WORKLOAD, "value": N * T / (ms / 1e3), "unit": "env-steps/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "dtype": "f32 simulator, bf16 policy (fp32 accumulate)", "data": "synthetic",
+            "config": {"n_env": N, "horizon": T, "policy": "%d -> 256 -> 4" % F, "obstacles": 256},
+            "loss": L, "grad_norm": float(np.linalg.norm(g)),
+            "policy_act_ms": act_ms,
+            "roofline": {"bound": "tensor", "achieved": gemm_flop / (act_ms / 1e3) / 1e12,
+                         "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
+                         "frac": gemm_flop / (act_ms / 1e3) / 1e12 / peaks["bf16_tflops"], "traffic": None,
+                         "kernel": "policy act (observation packing + layer-1 k_gemm + head), layer-1 FLOP",
+                         "peak_basis": "measured cuBLAS bf16 burst (MEASURED_PEAKS.json)"},
+            "clocks": ck}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_e2e(args, sim, inp, dev, g_r, g_d, out, g_a, g_s0, p):
     import torch
     T, NM = p["horizon"], sim.NM
@@ -515,6 +590,8 @@ def main():
             return run_reference(args, rank, world)
         if args.workload == SURROGATE_WORKLOAD:
             return run_surrogate(args, rank, world)
+        if args.workload == CLOSED_LOOP_WORKLOAD:
+            return run_closed_loop(args, rank, world)
         return run_ours(args, rank, world)
     finally:
         if world > 1:

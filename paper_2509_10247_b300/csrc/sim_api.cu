@@ -70,6 +70,9 @@ struct sim_handle {
     cudaStream_t last_stream = nullptr;
     // launch shape of the render kernels (forward, adjoint, single-step adjoint)
     int nw = 8, rpt = 4, grid_r = 1, grid_rv = 1, grid_rvs = 1;
+    // ray parts per render item of a rollout and of a single step: enough
+    // items per environment for 8 warps (a function of T and M only)
+    int parts_roll = 1, parts_one = 1;
     ds::Smem sm_r{}, sm_rv{}, sm_rvs{};
     // kernel launches per kind; while profiling, one CUDA event pair per launch
     bool profiling = false, capturing = false, ev_overflow = false;
@@ -361,6 +364,7 @@ Args base_args(const sim_handle* h) {
     a.state = h->d_state; a.pool_k = h->d_pool_k;
     a.work = h->d_work; a.status = h->d_status;
     a.counters = h->d_counters;
+    a.parts = h->parts_roll;
     return a;
 }
 
@@ -563,6 +567,8 @@ int sim_create(const sim_config* cfg, sim_handle** out) {
         h->img_h[s] = cfg->lid_ch;
         h->sen[s++].tmax = h->d_lid_tmax;
     }
+    h->parts_roll = std::min(8, std::max(1, (8 + h->T * h->M - 1) / (h->T * h->M)));
+    h->parts_one = std::min(8, std::max(1, (8 + h->M - 1) / h->M));
     const size_t tape_bytes = (size_t)h->T * h->NM * (h->Rc + h->Rl) * 2;
     h->tape = cfg->tape_hits == 1 || (cfg->tape_hits == -1 && tape_bytes <= (size_t(8) << 30));
     if (h->S == 0) h->tape = false;
@@ -578,9 +584,9 @@ int sim_create(const sim_config* cfg, sim_handle** out) {
         if (h->Rl) TRY(dalloc(h, &h->d_tape_lid, (size_t)h->T * h->NM * h->Rl));
     }
     TRY(dalloc(h, &h->d_poses, (size_t)h->T * h->NM * 12));
-    TRY(dalloc(h, &h->d_gposes, (size_t)h->T * h->NM * 12));
+    TRY(dalloc(h, &h->d_gposes, (size_t)h->T * h->NM * h->parts_roll * 12));
     TRY(dalloc(h, &h->d_pose1, (size_t)h->NM * 12));
-    TRY(dalloc(h, &h->d_gpose1, (size_t)h->NM * 12));
+    TRY(dalloc(h, &h->d_gpose1, (size_t)h->NM * h->parts_one * 12));
     TRY(dalloc(h, &h->d_state2, (size_t)h->NM * h->D));
     TRY(dalloc(h, &h->d_work, 1));
     TRY(dalloc(h, &h->d_status, 1));
@@ -748,6 +754,7 @@ int sim_render(sim_handle* h, float* depth, float* lidar, sim_stream_t stream) {
     Args a = base_args(h);
     a.render_only = 1;
     a.T = 1;
+    a.parts = h->parts_one;
     a.poses = h->d_pose1;
     int rc = run_physics(h, a, st);
     if (rc || h->S == 0) return rc;
@@ -765,6 +772,7 @@ int sim_step(sim_handle* h, const float* actions, float* depth, float* lidar, fl
     cudaStream_t st = (cudaStream_t)stream;
     Args a = base_args(h);
     a.T = 1;
+    a.parts = h->parts_one;
     a.K = 1;
     a.actions = actions;
     a.r_ctrl = r_ctrl; a.r_goal = r_goal; a.done = done;
@@ -837,6 +845,7 @@ int sim_step_backward(sim_handle* h, const float* s_t, const float* a_t, const u
     cudaStream_t st = (cudaStream_t)stream;
     Args a = base_args(h);
     a.T = 1;
+    a.parts = h->parts_one;
     a.K = 1;
     a.actions = a_t;
     if (h->S > 0 && (g_depth || g_lidar)) {

@@ -69,7 +69,8 @@ struct Args {
     const float* g_r; const float* g_sT; float* g_a; float* g_s0;
     const uint8_t* done_rd;     // adjoint: [T][NM] done flags of the forward pass
     float* poses;               // [T][NM][12] sensor pose per step (origin, row-major R)
-    float* gposes;              // [T][NM][12] cotangent of the poses
+    float* gposes;              // [T][NM][parts][12] cotangent of the poses, per ray part
+    int parts;                  // ray parts per (step, agent) item of the render kernels
     // control
     int* work; int* status;
     unsigned long long* counters;  // [4]: sphere tests, box tests, rays, env-steps (nullable)

@@ -171,7 +171,14 @@ __global__ void __launch_bounds__(256, 4) k_render(const Args a) {
     if (threadIdx.x == 0) mbar_init(reinterpret_cast<uint64_t*>(sm + a.sm.mbar));
     __syncthreads();
     uint32_t phase = 0;
-    const int per_env = a.T * M * S;
+    // items: (step, agent, sensor, part); a sensor's chunks are split into
+    // up to `parts` consecutive ranges so that short horizons still give
+    // every warp of the CTA work
+    const int nch0 = (a.sen[0].R + 32 * RPT - 1) / (32 * RPT);
+    const int nch1 = S > 1 ? (a.sen[1].R + 32 * RPT - 1) / (32 * RPT) : 0;
+    const int P0 = S > 0 ? min(a.parts, max(nch0, 1)) : 0, P1 = S > 1 ? min(a.parts, max(nch1, 1)) : 0;
+    const int per_tm = P0 + P1;
+    const int per_env = a.T * M * per_tm;
     for (;;) {
         if (threadIdx.x == 0) {
             s_env = atomicAdd(a.work, 1);
@@ -185,7 +192,10 @@ __global__ void __launch_bounds__(256, 4) k_render(const Args a) {
         const int ns = a.map_ns[map], nb = a.map_nb[map];
         if (!stage_map(a, sm, map, ns, nb, phase, &s_flag)) return;
         for (int it = warp; it < per_env; it = next_item(&s_item, lane)) {
-            const int t = it / (M * S), rem = it - t * M * S, m = rem / S, si = rem - m * S;
+            const int tm = it / per_tm, r = it - tm * per_tm;
+            const int t = tm / M, m = tm - t * M;
+            const int si = r < P0 ? 0 : 1, part = si ? r - P0 : r, np = si ? P1 : P0, nchs = si ? nch1 : nch0;
+            const int c0 = part * nchs / np, c1 = (part + 1) * nchs / np;
             const Sensor& sen = a.sen[si];
             if (!sen.out && !sen.tape) continue;
             const size_t ti = (size_t)t * NM + env * M + m;
@@ -195,9 +205,8 @@ __global__ void __launch_bounds__(256, 4) k_render(const Args a) {
 #pragma unroll
             for (int k = 0; k < 9; ++k) R[k] = a.poses[ti * 12 + 3 + k];
             const int4 meta = warp_build_list(prim, ns, nb, o, R, sen, a.cull, L, a.ns_max);
-            const int nch = (sen.R + 32 * RPT - 1) / (32 * RPT);
             const size_t base = ti * sen.R;
-            for (int ch = 0; ch < nch; ++ch) {
+            for (int ch = c0; ch < c1; ++ch) {
                 float dx[RPT], dy[RPT], dz[RPT], tb[RPT];
                 int bi[RPT];
                 item_rays<RPT>(sen, R, ch, lane, dx, dy, dz, tb);
@@ -264,7 +273,12 @@ __global__ void __launch_bounds__(256, TAPE ? 4 : 3) k_render_vjp(const Args a) 
     if (threadIdx.x == 0) mbar_init(reinterpret_cast<uint64_t*>(sm + a.sm.mbar));
     __syncthreads();
     uint32_t phase = 0;
-    const int per_env = a.T * M;
+    // items: (step, agent, part); part p takes the slots [32 w0, 32 w1) of
+    // every sensor, w0 = p W / P, w1 = (p + 1) W / P with W = ceil(R / 32)
+    // (the same slots for every rays-per-thread setting, so taped and
+    // re-cast gradients agree bit for bit)
+    const int P = a.parts;
+    const int per_env = a.T * M * P;
     for (;;) {
         if (threadIdx.x == 0) {
             s_env = atomicAdd(a.work, 1);
@@ -278,7 +292,8 @@ __global__ void __launch_bounds__(256, TAPE ? 4 : 3) k_render_vjp(const Args a) 
         const int ns = a.map_ns[map], nb = a.map_nb[map];
         if (!stage_map(a, sm, map, ns, nb, phase, &s_flag)) return;
         for (int it = warp; it < per_env; it = next_item(&s_item, lane)) {
-            const int t = it / M, m = it - t * M;
+            const int tm = it / P, part = it - tm * P;
+            const int t = tm / M, m = tm - t * M;
             const size_t ti = (size_t)t * NM + env * M + m;
             const bool dn = a.done_rd[(size_t)t * NM + env * M] != 0;
             float go[3] = {0.f, 0.f, 0.f}, gR[9];
@@ -294,9 +309,11 @@ __global__ void __launch_bounds__(256, TAPE ? 4 : 3) k_render_vjp(const Args a) 
                     const Sensor& sen = a.sen[si];
                     if (!sen.gout) continue;
                     const size_t base = ti * sen.R;
+                    const int W32 = (sen.R + 31) / 32;
+                    const int j0 = 32 * (part * W32 / P), j1 = min(sen.R, 32 * ((part + 1) * W32 / P));
                     if (TAPE) {
-                        // taped hit ids: rays in slot order j = lane, lane + 32, ...
-                        for (int j = lane; j < sen.R; j += 32) {
+                        // taped hit ids: rays in slot order j = j0 + lane, + 32, ...
+                        for (int j = j0 + lane; j < j1; j += 32) {
                             const int ray = out_index(sen, j);
                             const int id = sen.tape[base + ray];
                             if (id < 0) continue;
@@ -306,9 +323,10 @@ __global__ void __launch_bounds__(256, TAPE ? 4 : 3) k_render_vjp(const Args a) 
                         }
                         continue;
                     }
+                    if (j0 >= j1) continue;
                     const int4 meta = warp_build_list(prim, ns, nb, o, R, sen, a.cull, L, a.ns_max);
-                    const int nch = (sen.R + 32 * RPT - 1) / (32 * RPT);
-                    for (int ch = 0; ch < nch; ++ch) {
+                    const int chb = j0 / (32 * RPT), che = (j1 + 32 * RPT - 1) / (32 * RPT);
+                    for (int ch = chb; ch < che; ++ch) {
                         float dx[RPT], dy[RPT], dz[RPT], tb[RPT];
                         int bi[RPT];
                         item_rays<RPT>(sen, R, ch, lane, dx, dy, dz, tb);
@@ -325,7 +343,7 @@ __global__ void __launch_bounds__(256, TAPE ? 4 : 3) k_render_vjp(const Args a) 
 #pragma unroll
                         for (int r = 0; r < RPT; ++r) {
                             const int j = ch * 32 * RPT + r * 32 + lane;
-                            if (j >= sen.R || meta.z >= 0 || bi[r] < 0) continue;
+                            if (j < j0 || j >= j1 || meta.z >= 0 || bi[r] < 0) continue;
                             ray_vjp(prim, ns, L.id[bi[r]], o, dx[r], dy[r], dz[r], __ldg(sen.dir + j), sen,
                                     sen.gout[base + out_index(sen, j)], go, gR);
                         }
@@ -339,7 +357,7 @@ __global__ void __launch_bounds__(256, TAPE ? 4 : 3) k_render_vjp(const Args a) 
 #pragma unroll
             for (int k = 0; k < 9; ++k) v12[3 + k] = gR[k];
             const float tot = warp_sum12(v12);
-            if (!(lane & 1) && (lane >> 1) < 12) a.gposes[ti * 12 + (lane >> 1)] = tot;
+            if (!(lane & 1) && (lane >> 1) < 12) a.gposes[(ti * P + part) * 12 + (lane >> 1)] = tot;
         }
         __syncthreads();
     }
@@ -408,7 +426,10 @@ __global__ void __launch_bounds__(128) k_physics_bwd(const Args a) {
             if (!dn && a.gposes && on) {
                 float gq[12];
 #pragma unroll
-                for (int k = 0; k < 12; ++k) gq[k] = a.gposes[o * 12 + k];
+                for (int k = 0; k < 12; ++k) gq[k] = 0.f;
+                for (int pp = 0; pp < a.parts; ++pp)  // ray parts in order
+#pragma unroll
+                    for (int k = 0; k < 12; ++k) gq[k] += a.gposes[(o * a.parts + pp) * 12 + k];
                 pose_vjp(a.c.model, s1, gq, gq + 3, g);
             }
             float gp[16], gs[16], ga[4] = {0.f, 0.f, 0.f, 0.f};

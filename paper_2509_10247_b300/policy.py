@@ -137,7 +137,7 @@ class ClosedLoop:
             r[t], done[t] = o["r_ctrl"], o["done"]
             depth, lidar = o["depth"], o["lidar"]
             states[t + 1] = sim.get_state()
-        loss = float((g_r * r).sum())
+        loss = float((g_r[:T] * r).sum())
         g_s = torch.zeros(N, 13, device=dev)
         g_dep = torch.zeros(N, Rc, device=dev) if Rc else None
         g_lid = torch.zeros(N, Rl, device=dev) if Rl else None
