@@ -72,6 +72,13 @@ def build(force=False):
     return _LIB
 
 
+# dynamics models: continuous point mass (Eq. 3), rigid body (Eq. 1), discrete
+# point mass (Eq. 4), simplified quadrotor (Eq. 2)
+MODELS = {"pm": 0, "rigid": 1, "pm_disc": 2, "simple": 3}
+STATE_DIM = {"pm": 12, "rigid": 13, "pm_disc": 12, "simple": 15}
+ACTION_DIM = {"pm": 3, "rigid": 4, "pm_disc": 3, "simple": 4}
+
+
 _lib = None
 
 
@@ -108,7 +115,7 @@ def _c64(a):
 def make_config(p):
     """oc_config from a workload parameter dict (angles given in degrees)."""
     c = OcConfig()
-    c.model = 1 if p["model"] == "rigid" else 0
+    c.model = MODELS[p["model"]]
     c.n_env, c.n_agent, c.horizon = p["n_env"], p["n_agent"], p["horizon"]
     c.dt, c.gravity = p["dt"], p["gravity"]
     c.lam, c.drag, c.act_scale, c.ema_alpha = p["lam"], p["drag"], p["act_scale"], p["ema_alpha"]
@@ -141,8 +148,8 @@ class Oracle:
     def __init__(self, p, inp):
         self.p = p
         self.cfg = make_config(p)
-        self.D = 13 if p["model"] == "rigid" else 12
-        self.A = 4 if p["model"] == "rigid" else 3
+        self.D = STATE_DIM[p["model"]]
+        self.A = ACTION_DIM[p["model"]]
         self.N, self.M, self.T = p["n_env"], p["n_agent"], p["horizon"]
         self.NM = self.N * self.M
         self.Rc = p["cam"][0] * p["cam"][1] if p["cam"] is not None else 0
@@ -269,6 +276,22 @@ def pm_step(p, s, a, drag=None, lam=None):
     o = np.zeros(12)
     lib().oc_pm_step(C.byref(cfg), _d(p["drag"] if drag is None else drag),
                      _d(p["lam"] if lam is None else lam), _p(_v(s)), _p(_v(a)), _p(o))
+    return o
+
+
+def pmd_step(p, s, a):
+    """One discrete point-mass step (Eq. 4)."""
+    cfg = make_config(p)
+    o = np.zeros(12)
+    lib().oc_pmd_step(C.byref(cfg), _p(_v(s)), _p(_v(a)), _p(o))
+    return o
+
+
+def simple_step(p, s, a):
+    """One simplified-quadrotor step (Eq. 2); state (p, v, R row-major)."""
+    cfg = make_config(p)
+    o = np.zeros(15)
+    lib().oc_simple_step(C.byref(cfg), _p(_v(s)), _p(_v(a)), _p(o))
     return o
 
 

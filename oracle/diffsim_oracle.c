@@ -41,6 +41,8 @@
 
 #define OC_PM 0
 #define OC_RIGID 1
+#define OC_PMD 2    /* discrete point mass, Eq. 4 */
+#define OC_SIMPLE 3 /* simplified quadrotor, Eq. 2 */
 #define OC_INF HUGE_VAL
 
 /* Ambiguity margins used to flag rays and steps where an FP32 evaluation may
@@ -92,8 +94,8 @@ typedef struct {
 } oc_scene;
 
 /* ------------------------------------------------------------------ utils */
-int oc_state_dim(int model) { return model == OC_RIGID ? 13 : 12; }
-int oc_action_dim(int model) { return model == OC_RIGID ? 4 : 3; }
+int oc_state_dim(int model) { return model == OC_RIGID ? 13 : (model == OC_SIMPLE ? 15 : 12); }
+int oc_action_dim(int model) { return (model == OC_RIGID || model == OC_SIMPLE) ? 4 : 3; }
 
 static double clamp1(double x) { return x < -1.0 ? -1.0 : (x > 1.0 ? 1.0 : x); }
 static double dclamp1(double x) { return (x >= -1.0 && x <= 1.0) ? 1.0 : 0.0; }
@@ -204,6 +206,77 @@ void oc_rb_step(const oc_config *c, const double *s, const double *act, double *
     memcpy(o, n, sizeof(n));
 }
 
+/* Discrete point mass, Eq. 4: p_{t+1} = p_t + v_t dt + 1/2 w_t dt^2,
+ * v_{t+1} = v_t + 1/2 (w_t + w_{t+1}) dt, with w the total acceleration.  The
+ * state's acceleration slot carries the thrust acceleration u_t of the
+ * command in force (w_t = u_t + g); the step's action is the next command,
+ * u_{t+1} = act_scale * clip(action), so the half-step average of Eq. 4 needs
+ * no look-ahead.  The velocity EMA (attitude, Sec. III-B) follows v_{t+1}. */
+void oc_pmd_step(const oc_config *c, const double *s, const double *act, double *o)
+{
+    const double g[3] = {0.0, 0.0, -c->gravity};
+    const double dt = c->dt;
+    double n[12];
+    for (int i = 0; i < 3; ++i) {
+        double p = s[i], v = s[3 + i], u = s[6 + i], e = s[9 + i];
+        double u1 = c->act_scale * clamp1(act[i]);
+        n[i] = p + v * dt + 0.5 * (u + g[i]) * dt * dt;
+        n[3 + i] = v + 0.5 * ((u + g[i]) + (u1 + g[i])) * dt;
+        n[6 + i] = u1;
+        n[9 + i] = (1.0 - c->ema_alpha) * e + c->ema_alpha * n[3 + i];
+    }
+    memcpy(o, n, sizeof(n));
+}
+
+/* Simplified quadrotor, Eq. 2: p' = v, v' = R c e3 + g, R' = R [omega]_x, with
+ * the collective thrust acceleration c = g (1 + clip(a0)) (hover at a0 = 0)
+ * and body rates omega = rate_scale * clip(a1..3) taken directly as inputs.
+ * State (p, v, R) with R row-major, body -> world.  One explicit-Euler step,
+ * then the rotation is re-orthonormalised by Gram-Schmidt on its columns
+ * (x normalised, y made orthogonal to x and normalised, z = x cross y). */
+static void simple_pre(const oc_config *c, const double *s, const double *act, double *Rt, double *w,
+                       double *cth)
+{
+    const double *R = s + 6;
+    *cth = c->gravity * (1.0 + clamp1(act[0]));
+    for (int i = 0; i < 3; ++i) w[i] = c->rate_scale[i] * clamp1(act[1 + i]);
+    /* Rt = R + dt R [w]_x;  column j of R [w]_x is R (w x e_j) */
+    const double W[9] = {0.0, -w[2], w[1], w[2], 0.0, -w[0], -w[1], w[0], 0.0};
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double acc = 0.0;
+            for (int k = 0; k < 3; ++k) acc += R[3 * i + k] * W[3 * k + j];
+            Rt[3 * i + j] = R[3 * i + j] + c->dt * acc;
+        }
+}
+
+static void gram_schmidt(const double *Rt, double *Ro)
+{
+    double u0[3] = {Rt[0], Rt[3], Rt[6]}, u1[3] = {Rt[1], Rt[4], Rt[7]};
+    double n0 = norm3(u0), x[3], wv[3], y[3], z[3];
+    for (int i = 0; i < 3; ++i) x[i] = u0[i] / n0;
+    double sx = dot3(x, u1);
+    for (int i = 0; i < 3; ++i) wv[i] = u1[i] - sx * x[i];
+    double n1 = norm3(wv);
+    for (int i = 0; i < 3; ++i) y[i] = wv[i] / n1;
+    cross3(x, y, z);
+    for (int i = 0; i < 3; ++i) { Ro[3 * i] = x[i]; Ro[3 * i + 1] = y[i]; Ro[3 * i + 2] = z[i]; }
+}
+
+void oc_simple_step(const oc_config *c, const double *s, const double *act, double *o)
+{
+    const double *p = s, *v = s + 3, *R = s + 6;
+    double Rt[9], w[3], cth, n[15];
+    simple_pre(c, s, act, Rt, w, &cth);
+    const double g[3] = {0.0, 0.0, -c->gravity};
+    for (int i = 0; i < 3; ++i) {
+        n[i] = p[i] + c->dt * v[i];
+        n[3 + i] = v[i] + c->dt * (R[3 * i + 2] * cth + g[i]);
+    }
+    gram_schmidt(Rt, n + 6);
+    memcpy(o, n, sizeof(n));
+}
+
 /* ------------------------------------------------------ attitude (Sec. III-B) */
 
 /* Sensor pose of one agent: origin = position, R = body->world rotation.
@@ -219,6 +292,10 @@ int oc_pose(const oc_config *c, const double *s, double *o, double *R)
     o[0] = s[0]; o[1] = s[1]; o[2] = s[2];
     if (c->model == OC_RIGID) {
         oc_quat_to_rot(s + 3, R);
+        return 0;
+    }
+    if (c->model == OC_SIMPLE) {
+        memcpy(R, s + 6, 9 * sizeof(double));
         return 0;
     }
     int flags = 0;
@@ -539,6 +616,8 @@ static void map_of(const ctx_t *x, int env, const double **sph, int *ns, const d
 static void dyn_step(const ctx_t *x, int env, const double *s, const double *a, double *o)
 {
     if (x->c->model == OC_RIGID) { oc_rb_step(x->c, s, a, o); return; }
+    if (x->c->model == OC_PMD) { oc_pmd_step(x->c, s, a, o); return; }
+    if (x->c->model == OC_SIMPLE) { oc_simple_step(x->c, s, a, o); return; }
     double drag = x->sc->drag_env ? x->sc->drag_env[env] : x->c->drag;
     double lam = x->sc->lam_env ? x->sc->lam_env[env] : x->c->lam;
     oc_pm_step(x->c, drag, lam, s, a, o);
@@ -680,7 +759,8 @@ static void env_step(const ctx_t *x, int env, int t, const double *s_t, const do
     for (int m = 0; m < M; ++m) {
         int i = i0 + m;
         double o[3], R[9];
-        if (c->model == OC_PM && (oc_pose(c, s_next + (size_t)i * D, o, R) & 4)) amb_step[i] |= 4;
+        if ((c->model == OC_PM || c->model == OC_PMD) && (oc_pose(c, s_next + (size_t)i * D, o, R) & 4))
+            amb_step[i] |= 4;
         render_agent(x, env, s_next + (size_t)i * D,
                      depth ? depth + (size_t)i * x->Rc : NULL, lidar ? lidar + (size_t)i * x->Rl : NULL,
                      hc + (size_t)i * x->Rc, hl + (size_t)i * x->Rl,
@@ -745,6 +825,93 @@ static void pm_step_vjp(const oc_config *c, double drag, double lam, const doubl
         ga[i] += c->act_scale * dclamp1(act[i]) * gu;
     }
     (void)s;
+}
+
+/* VJP of the discrete point-mass step (Eq. 4). */
+static void pmd_step_vjp(const oc_config *c, const double *act, const double *go, double *gs, double *ga)
+{
+    double al = c->ema_alpha, dt = c->dt;
+    for (int i = 0; i < 3; ++i) {
+        double gp = go[i], gv = go[3 + i], gu1 = go[6 + i], ge = go[9 + i];
+        gv += al * ge;
+        gs[9 + i] += (1.0 - al) * ge;
+        gs[i] += gp;                                 /* p' = p + v dt + 1/2 (u + g) dt^2 */
+        gs[3 + i] += dt * gp + gv;                   /* v' = v + 1/2 (u + u1 + 2 g) dt */
+        gs[6 + i] += 0.5 * dt * dt * gp + 0.5 * dt * gv;
+        gu1 += 0.5 * dt * gv;
+        ga[i] += c->act_scale * dclamp1(act[i]) * gu1;
+    }
+}
+
+/* VJP of Gram-Schmidt (columns of Rt -> Ro) given the cotangent gRo. */
+static void gram_schmidt_vjp(const double *Rt, const double *gRo, double *gRt)
+{
+    double u0[3] = {Rt[0], Rt[3], Rt[6]}, u1[3] = {Rt[1], Rt[4], Rt[7]};
+    double n0 = norm3(u0), x[3], wv[3], y[3];
+    for (int i = 0; i < 3; ++i) x[i] = u0[i] / n0;
+    double sx = dot3(x, u1);
+    for (int i = 0; i < 3; ++i) wv[i] = u1[i] - sx * x[i];
+    double n1 = norm3(wv);
+    for (int i = 0; i < 3; ++i) y[i] = wv[i] / n1;
+    double gx[3] = {gRo[0], gRo[3], gRo[6]}, gy[3] = {gRo[1], gRo[4], gRo[7]}, gz[3] = {gRo[2], gRo[5], gRo[8]};
+    double t[3];
+    cross3(y, gz, t);                   /* z = x cross y */
+    for (int i = 0; i < 3; ++i) gx[i] += t[i];
+    cross3(gz, x, t);
+    for (int i = 0; i < 3; ++i) gy[i] += t[i];
+    double yg = dot3(y, gy), gw[3];     /* y = w / |w| */
+    for (int i = 0; i < 3; ++i) gw[i] = (gy[i] - y[i] * yg) / n1;
+    double xg = dot3(x, gw), gu1[3];    /* w = u1 - (x.u1) x */
+    for (int i = 0; i < 3; ++i) {
+        gu1[i] = gw[i] - x[i] * xg;
+        gx[i] -= xg * u1[i] + sx * gw[i];
+    }
+    double xx = dot3(x, gx), gu0[3];    /* x = u0 / |u0| */
+    for (int i = 0; i < 3; ++i) gu0[i] = (gx[i] - x[i] * xx) / n0;
+    for (int i = 0; i < 3; ++i) {
+        gRt[3 * i] = gu0[i];
+        gRt[3 * i + 1] = gu1[i];
+        gRt[3 * i + 2] = 0.0;
+    }
+}
+
+/* VJP of the simplified quadrotor step (Eq. 2, explicit Euler, Gram-Schmidt). */
+static void simple_step_vjp(const oc_config *c, const double *s, const double *act, const double *go, double *gs,
+                            double *ga)
+{
+    const double *R = s + 6;
+    double Rt[9], w[3], cth, gRt[9];
+    simple_pre(c, s, act, Rt, w, &cth);
+    const double dt = c->dt;
+    for (int i = 0; i < 3; ++i) {
+        gs[i] += go[i];                      /* p' = p + dt v */
+        gs[3 + i] += dt * go[i] + go[3 + i]; /* v' = v + dt (R e3 c + g) */
+    }
+    double gc = 0.0;
+    for (int i = 0; i < 3; ++i) {
+        gs[6 + 3 * i + 2] += dt * cth * go[3 + i];
+        gc += dt * R[3 * i + 2] * go[3 + i];
+    }
+    gram_schmidt_vjp(Rt, go + 6, gRt);
+    /* Rt = R (I + dt [w]_x): gR += gRt (I + dt [w]_x)^T = gRt (I - dt [w]_x) */
+    const double W[9] = {0.0, -w[2], w[1], w[2], 0.0, -w[0], -w[1], w[0], 0.0};
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double acc = 0.0;
+            for (int k = 0; k < 3; ++k) acc += gRt[3 * i + k] * W[3 * j + k];
+            gs[6 + 3 * i + j] += gRt[3 * i + j] + dt * acc;
+        }
+    /* w: M = R^T gRt; dL/dw1 = dt (M21 - M12), dw2 = dt (M02 - M20), dw3 = dt (M10 - M01) */
+    double Mt[9];
+    for (int a2 = 0; a2 < 3; ++a2)
+        for (int b = 0; b < 3; ++b) {
+            double acc = 0.0;
+            for (int k = 0; k < 3; ++k) acc += R[3 * k + a2] * gRt[3 * k + b];
+            Mt[3 * a2 + b] = acc;
+        }
+    double gw[3] = {dt * (Mt[7] - Mt[5]), dt * (Mt[2] - Mt[6]), dt * (Mt[3] - Mt[1])};
+    ga[0] += c->gravity * dclamp1(act[0]) * gc;
+    for (int i = 0; i < 3; ++i) ga[1 + i] += c->rate_scale[i] * dclamp1(act[1 + i]) * gw[i];
 }
 
 /* VJP of the rigid-body step (Eq. 1 with the rate controller, explicit Euler,
@@ -828,6 +995,10 @@ static void pose_vjp(const oc_config *c, const double *s, const double *go, cons
 {
     for (int i = 0; i < 3; ++i) gs[i] += go[i];
     if (c->model == OC_RIGID) { quat_to_rot_vjp(s + 3, gR, gs + 3); return; }
+    if (c->model == OC_SIMPLE) {
+        for (int k = 0; k < 9; ++k) gs[6 + k] += gR[k];
+        return;
+    }
     const double *a = s + 6, *e = s + 9;
     double z[3], hp[3], x[3], h[3];
     double na = norm3(a);
@@ -1025,6 +1196,10 @@ int oc_backward(const oc_config *c, const oc_scene *sc, const double *act, const
                 const double *a = act + (sT + i) * A;
                 if (c->model == OC_RIGID)
                     rb_step_vjp(c, s, a, gpre + (size_t)m * D, g, g_a + (sT + i) * A);
+                else if (c->model == OC_PMD)
+                    pmd_step_vjp(c, a, gpre + (size_t)m * D, g, g_a + (sT + i) * A);
+                else if (c->model == OC_SIMPLE)
+                    simple_step_vjp(c, s, a, gpre + (size_t)m * D, g, g_a + (sT + i) * A);
                 else {
                     double drag = sc->drag_env ? sc->drag_env[env] : c->drag;
                     double lam = sc->lam_env ? sc->lam_env[env] : c->lam;

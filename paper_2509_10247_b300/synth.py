@@ -17,10 +17,12 @@ All floating-point values are rounded to float32 once, so the FP32 device path
 and the FP64 oracle start from bit-identical numbers.
 
 State layout (one agent, float components in this order):
-  point mass  (D=12): p[3], v[3], a[3], ema_v[3]
-  rigid body  (D=13): p[3], q[4] (w, x, y, z), v[3], omega[3]
+  point mass (Eq. 3, Eq. 4) (D=12): p[3], v[3], a[3], ema_v[3]
+  rigid body (Eq. 1)        (D=13): p[3], q[4] (w, x, y, z), v[3], omega[3]
+  simplified (Eq. 2)        (D=15): p[3], v[3], R[9] (row-major, body -> world)
 Action layout: point mass A=3 (acceleration command in [-1, 1]^3),
-rigid body A=4 (collective thrust, then three body rates, each in [-1, 1]).
+rigid body and simplified A=4 (collective thrust, then three body rates,
+each in [-1, 1]).
 """
 from __future__ import annotations
 
@@ -31,8 +33,8 @@ import numpy as np
 
 INF = float("inf")
 
-STATE_DIM = {"pm": 12, "rigid": 13}
-ACTION_DIM = {"pm": 3, "rigid": 4}
+STATE_DIM = {"pm": 12, "rigid": 13, "pm_disc": 12, "simple": 15}
+ACTION_DIM = {"pm": 3, "rigid": 4, "pm_disc": 3, "simple": 4}
 
 # Parameters shared by every workload.  Values the paper leaves open are the
 # readings listed in the design notes (thrust along +z_B, lag lambda = 1/tau, ...).
@@ -201,6 +203,8 @@ def _rest_state(model, pos):
     s[:, 0:3] = pos
     if model == "rigid":
         s[:, 3] = 1.0  # unit quaternion (w, x, y, z) = identity
+    if model == "simple":
+        s[:, 6] = s[:, 10] = s[:, 14] = 1.0  # rotation matrix = identity
     return s
 
 
