@@ -22,11 +22,15 @@
  *    pointers are read synchronously and may be freed on return.
  *  - Floating point is FP32 everywhere on the device.  Layouts are row-major
  *    with the last index fastest:
- *      state    [NM][D]   NM = N*M; D = 12 point mass (p[3], v[3], a[3],
- *                          ema_v[3]); D = 13 rigid (p[3], q[4] = (w,x,y,z),
- *                          v[3], omega[3])
- *      actions  [T][NM][A]  A = 3 point mass, 4 rigid (thrust, 3 body rates),
- *                          each in [-1, 1] (clipped)
+ *      state    [NM][D]   NM = N*M; D = 12 point mass, continuous and discrete
+ *                          (p[3], v[3], a[3], ema_v[3]; for the discrete
+ *                          model a is the thrust acceleration in force);
+ *                          D = 13 rigid (p[3], q[4] = (w,x,y,z), v[3],
+ *                          omega[3]); D = 15 simplified (p[3], v[3], R[9]
+ *                          row-major body -> world)
+ *      actions  [T][NM][A]  A = 3 point mass (acceleration command), 4 rigid
+ *                          and simplified (thrust, 3 body rates), each in
+ *                          [-1, 1] (clipped)
  *      r_ctrl   [T][NM] float, r_goal [T][NM] int8, done [T][NM] uint8
  *      depth    [T][NM][Rc], Rc = cam_w * cam_h, ray = row * cam_w + col
  *      lidar    [T][NM][Rl], Rl = lid_ch * lid_az, ray = ch * lid_az + k
@@ -60,7 +64,9 @@ enum {
     SIM_ERR_UNSUPPORTED = -9  /* no kernel for this configuration */
 };
 
-enum { SIM_MODEL_POINT_MASS = 0, SIM_MODEL_RIGID = 1 };
+/* Dynamics models (Sec. III-A): continuous point mass (Eq. 3), full rigid
+ * body (Eq. 1), discrete point mass (Eq. 4), simplified quadrotor (Eq. 2). */
+enum { SIM_MODEL_POINT_MASS = 0, SIM_MODEL_RIGID = 1, SIM_MODEL_POINT_MASS_DISCRETE = 2, SIM_MODEL_SIMPLE = 3 };
 
 /* Status bits accumulated on the device (sim_last_status). */
 enum { SIM_STATUS_NAN = 1, SIM_STATUS_TIMEOUT = 2 };

@@ -23,7 +23,9 @@ _i, _f = C.c_int32, C.c_float
 _vp = C.c_void_p
 
 SIM_OK = 0
-SIM_MODEL_POINT_MASS, SIM_MODEL_RIGID = 0, 1
+SIM_MODEL_POINT_MASS, SIM_MODEL_RIGID, SIM_MODEL_POINT_MASS_DISCRETE, SIM_MODEL_SIMPLE = 0, 1, 2, 3
+MODELS = {"pm": SIM_MODEL_POINT_MASS, "rigid": SIM_MODEL_RIGID, "pm_disc": SIM_MODEL_POINT_MASS_DISCRETE,
+          "simple": SIM_MODEL_SIMPLE}
 ERRORS = {0: "SIM_OK", -1: "SIM_ERR_INVALID_ARG", -2: "SIM_ERR_NULL_PTR", -3: "SIM_ERR_SIZE",
           -4: "SIM_ERR_CUDA", -5: "SIM_ERR_NOT_READY", -6: "SIM_ERR_NAN", -7: "SIM_ERR_TIMEOUT",
           -8: "SIM_ERR_OOM", -9: "SIM_ERR_UNSUPPORTED"}
@@ -120,7 +122,7 @@ def make_config(p, **ex):
     fields (ckpt_every, tape_hits, cull, warps_per_cta, rays_per_thread,
     ctas_per_sm)."""
     c = SimConfig()
-    c.model = SIM_MODEL_RIGID if p["model"] == "rigid" else SIM_MODEL_POINT_MASS
+    c.model = MODELS[p["model"]]
     c.n_env, c.n_agent, c.horizon = p["n_env"], p["n_agent"], p["horizon"]
     c.dt, c.gravity = p["dt"], p["gravity"]
     c.lam, c.drag, c.act_scale, c.ema_alpha = p["lam"], p["drag"], p["act_scale"], p["ema_alpha"]

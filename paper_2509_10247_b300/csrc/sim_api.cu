@@ -140,14 +140,17 @@ void dfree(T*& p) {
 bool finite_pos(float x) { return std::isfinite(x) && x > 0.f; }
 
 int validate(const sim_config* c) {
-    if (c->model != SIM_MODEL_POINT_MASS && c->model != SIM_MODEL_RIGID) return SIM_ERR_INVALID_ARG;
+    if (c->model < SIM_MODEL_POINT_MASS || c->model > SIM_MODEL_SIMPLE) return SIM_ERR_INVALID_ARG;
     if (c->n_env < 1 || c->n_agent < 1 || c->horizon < 1) return SIM_ERR_SIZE;
     if (c->n_agent > 32) return SIM_ERR_SIZE;
     if ((long long)c->n_env * c->n_agent > (1LL << 30)) return SIM_ERR_SIZE;
     if (!finite_pos(c->dt) || !std::isfinite(c->gravity)) return SIM_ERR_INVALID_ARG;
-    if (c->model == SIM_MODEL_POINT_MASS) {
+    if (c->model == SIM_MODEL_POINT_MASS || c->model == SIM_MODEL_POINT_MASS_DISCRETE) {
         if (!std::isfinite(c->lam) || !std::isfinite(c->drag) || !std::isfinite(c->act_scale)) return SIM_ERR_INVALID_ARG;
         if (!(c->ema_alpha >= 0.f && c->ema_alpha <= 1.f)) return SIM_ERR_INVALID_ARG;
+    } else if (c->model == SIM_MODEL_SIMPLE) {
+        for (int i = 0; i < 3; ++i)
+            if (!std::isfinite(c->rate_scale[i])) return SIM_ERR_INVALID_ARG;
     } else {
         if (!finite_pos(c->mass)) return SIM_ERR_INVALID_ARG;
         for (int i = 0; i < 3; ++i)
@@ -483,8 +486,21 @@ const char* sim_strerror(int code) {
     return kErr[-code];
 }
 
-int sim_state_dim(int model) { return model == SIM_MODEL_POINT_MASS ? 12 : (model == SIM_MODEL_RIGID ? 13 : -1); }
-int sim_action_dim(int model) { return model == SIM_MODEL_POINT_MASS ? 3 : (model == SIM_MODEL_RIGID ? 4 : -1); }
+int sim_state_dim(int model) {
+    switch (model) {
+        case SIM_MODEL_POINT_MASS: case SIM_MODEL_POINT_MASS_DISCRETE: return 12;
+        case SIM_MODEL_RIGID: return 13;
+        case SIM_MODEL_SIMPLE: return 15;
+        default: return -1;
+    }
+}
+int sim_action_dim(int model) {
+    switch (model) {
+        case SIM_MODEL_POINT_MASS: case SIM_MODEL_POINT_MASS_DISCRETE: return 3;
+        case SIM_MODEL_RIGID: case SIM_MODEL_SIMPLE: return 4;
+        default: return -1;
+    }
+}
 
 int sim_destroy(sim_handle* h) {
     if (!h) return SIM_OK;

@@ -1,5 +1,5 @@
 // sim_device.cuh -- per-agent FP32 device math of the fused quadrotor step:
-// dynamics (Eq. 1, Eq. 3), sensor pose (Sec. III-B), signed distances,
+// dynamics (Eq. 1, Eq. 2, Eq. 3, Eq. 4), sensor pose (Sec. III-B), signed distances,
 // rewards (Sec. III-C/D/E) and their vector-Jacobian products (Eq. 5).
 #pragma once
 #include <cuda_runtime.h>
@@ -8,7 +8,7 @@
 
 namespace ds {
 
-enum { MODEL_PM = 0, MODEL_RIGID = 1 };
+enum { MODEL_PM = 0, MODEL_RIGID = 1, MODEL_PMD = 2, MODEL_SIMPLE = 3 };
 
 // Physics and task constants (kernel-parameter resident).
 struct Phys {
@@ -70,6 +70,156 @@ __device__ __forceinline__ void pm_step(const Phys& c, float drag, float lam, co
         o[6 + i] = a + c.dt * lam * (u - a);
         o[9 + i] = (1.f - c.ema_alpha) * e + c.ema_alpha * vn;
     }
+}
+
+// Eq. 4, discrete point mass: p' = p + v dt + (u + g) dt^2 / 2,
+// v' = v + ((u + g) + (u' + g)) dt / 2, where the state's acceleration slot
+// holds the command in force u and the action gives the next one u'.
+__device__ __forceinline__ void pmd_step(const Phys& c, const float* s, const float* act, float* o) {
+    const float dt = c.dt;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const float gi = (i == 2) ? -c.g : 0.f;
+        const float p = s[i], v = s[3 + i], u = s[6 + i], e = s[9 + i];
+        const float u1 = c.act_scale * clip1(act[i]);
+        const float vn = v + 0.5f * ((u + gi) + (u1 + gi)) * dt;
+        o[i] = p + v * dt + 0.5f * (u + gi) * dt * dt;
+        o[3 + i] = vn;
+        o[6 + i] = u1;
+        o[9 + i] = (1.f - c.ema_alpha) * e + c.ema_alpha * vn;
+    }
+}
+
+__device__ __forceinline__ void pmd_step_vjp(const Phys& c, const float* act, const float* go, float* gs,
+                                             float* ga) {
+    const float al = c.ema_alpha, dt = c.dt;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const float gp = go[i], gv = go[3 + i] + al * go[9 + i];
+        gs[9 + i] += (1.f - al) * go[9 + i];
+        gs[i] += gp;
+        gs[3 + i] += dt * gp + gv;
+        gs[6 + i] += 0.5f * dt * dt * gp + 0.5f * dt * gv;
+        ga[i] += c.act_scale * dclip1(act[i]) * (go[6 + i] + 0.5f * dt * gv);
+    }
+}
+
+// Eq. 2, simplified quadrotor: state (p, v, R row-major), thrust
+// acceleration c = g (1 + clip(a0)) along z_B, body rates omega = rate_scale
+// clip(a1..3) as inputs; explicit Euler R~ = R (I + dt [omega]_x), then
+// Gram-Schmidt on the columns (x, y orthogonalised, z = x cross y).
+__device__ __forceinline__ void simple_pre(const Phys& c, const float* s, const float* act, float* Rt, float* w,
+                                           float& cth) {
+    const float* R = s + 6;
+    cth = c.g * (1.f + clip1(act[0]));
+#pragma unroll
+    for (int i = 0; i < 3; ++i) w[i] = c.rs[i] * clip1(act[1 + i]);
+    const float W[9] = {0.f, -w[2], w[1], w[2], 0.f, -w[0], -w[1], w[0], 0.f};
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const float acc = R[3 * i] * W[j] + R[3 * i + 1] * W[3 + j] + R[3 * i + 2] * W[6 + j];
+            Rt[3 * i + j] = R[3 * i + j] + c.dt * acc;
+        }
+}
+
+struct GsFrame {
+    float x[3], y[3], u1[3], n0, n1, sx;
+};
+
+__device__ __forceinline__ void gram_schmidt(const float* Rt, GsFrame& f) {
+    const float u0[3] = {Rt[0], Rt[3], Rt[6]};
+    f.u1[0] = Rt[1]; f.u1[1] = Rt[4]; f.u1[2] = Rt[7];
+    f.n0 = sqrtf(dot3(u0, u0));
+#pragma unroll
+    for (int i = 0; i < 3; ++i) f.x[i] = u0[i] / f.n0;
+    f.sx = dot3(f.x, f.u1);
+    float wv[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) wv[i] = f.u1[i] - f.sx * f.x[i];
+    f.n1 = sqrtf(dot3(wv, wv));
+#pragma unroll
+    for (int i = 0; i < 3; ++i) f.y[i] = wv[i] / f.n1;
+}
+
+__device__ __forceinline__ void simple_step(const Phys& c, const float* s, const float* act, float* o) {
+    float Rt[9], w[3], cth;
+    simple_pre(c, s, act, Rt, w, cth);
+    const float* R = s + 6;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const float gi = (i == 2) ? -c.g : 0.f;
+        o[i] = s[i] + c.dt * s[3 + i];
+        o[3 + i] = s[3 + i] + c.dt * (R[3 * i + 2] * cth + gi);
+    }
+    GsFrame f;
+    gram_schmidt(Rt, f);
+    float z[3];
+    cross3(f.x, f.y, z);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) { o[6 + 3 * i] = f.x[i]; o[7 + 3 * i] = f.y[i]; o[8 + 3 * i] = z[i]; }
+}
+
+__device__ __forceinline__ void simple_step_vjp(const Phys& c, const float* s, const float* act, const float* go,
+                                                float* gs, float* ga) {
+    float Rt[9], w[3], cth;
+    simple_pre(c, s, act, Rt, w, cth);
+    const float* R = s + 6;
+    const float dt = c.dt;
+    float gc = 0.f;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        gs[i] += go[i];
+        gs[3 + i] += dt * go[i] + go[3 + i];
+        gs[6 + 3 * i + 2] += dt * cth * go[3 + i];
+        gc += dt * R[3 * i + 2] * go[3 + i];
+    }
+    GsFrame f;
+    gram_schmidt(Rt, f);
+    const float* gRo = go + 6;
+    float gx[3] = {gRo[0], gRo[3], gRo[6]}, gy[3] = {gRo[1], gRo[4], gRo[7]}, gz[3] = {gRo[2], gRo[5], gRo[8]};
+    float t[3];
+    cross3(f.y, gz, t);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) gx[i] += t[i];
+    cross3(gz, f.x, t);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) gy[i] += t[i];
+    const float yg = dot3(f.y, gy);
+    float gw[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) gw[i] = (gy[i] - f.y[i] * yg) / f.n1;
+    const float xg = dot3(f.x, gw);
+    float gRt[9];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        gRt[3 * i + 1] = gw[i] - f.x[i] * xg;
+        gx[i] -= xg * f.u1[i] + f.sx * gw[i];
+    }
+    const float xx = dot3(f.x, gx);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        gRt[3 * i] = (gx[i] - f.x[i] * xx) / f.n0;
+        gRt[3 * i + 2] = 0.f;
+    }
+    const float W[9] = {0.f, -w[2], w[1], w[2], 0.f, -w[0], -w[1], w[0], 0.f};
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const float acc = gRt[3 * i] * W[3 * j] + gRt[3 * i + 1] * W[3 * j + 1] + gRt[3 * i + 2] * W[3 * j + 2];
+            gs[6 + 3 * i + j] += gRt[3 * i + j] + dt * acc;
+        }
+    float Mt[9];  // R^T gRt
+#pragma unroll
+    for (int a2 = 0; a2 < 3; ++a2)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) Mt[3 * a2 + b] = R[a2] * gRt[b] + R[3 + a2] * gRt[3 + b] + R[6 + a2] * gRt[6 + b];
+    const float gwr[3] = {dt * (Mt[7] - Mt[5]), dt * (Mt[2] - Mt[6]), dt * (Mt[3] - Mt[1])};
+    ga[0] += c.g * dclip1(act[0]) * gc;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) ga[1 + i] += c.rs[i] * dclip1(act[1 + i]) * gwr[i];
 }
 
 // Eq. 1 with the body-rate controller, explicit Euler, quaternion renormalised.
@@ -149,6 +299,11 @@ __device__ __forceinline__ void pm_frame(const float* s, PmFrame& f) {
 __device__ __forceinline__ void sensor_pose(int model, const float* s, float* o, float* R) {
     o[0] = s[0]; o[1] = s[1]; o[2] = s[2];
     if (model == MODEL_RIGID) { quat_rot(s + 3, R); return; }
+    if (model == MODEL_SIMPLE) {
+#pragma unroll
+        for (int k = 0; k < 9; ++k) R[k] = s[6 + k];
+        return;
+    }
     PmFrame f;
     pm_frame(s, f);
     float y[3];
@@ -162,6 +317,11 @@ __device__ __forceinline__ void pose_vjp(int model, const float* s, const float*
                                          float* gs) {
     gs[0] += go[0]; gs[1] += go[1]; gs[2] += go[2];
     if (model == MODEL_RIGID) { quat_rot_vjp(s + 3, gR, gs + 3); return; }
+    if (model == MODEL_SIMPLE) {
+#pragma unroll
+        for (int k = 0; k < 9; ++k) gs[6 + k] += gR[k];
+        return;
+    }
     PmFrame f;
     pm_frame(s, f);
     float gx[3] = {gR[0], gR[3], gR[6]}, gy[3] = {gR[1], gR[4], gR[7]}, gz[3] = {gR[2], gR[5], gR[8]};

@@ -122,6 +122,8 @@ __global__ void __launch_bounds__(256, 3) k_rollout(const Args a) {
 #pragma unroll
                     for (int k = 0; k < 16; ++k) sp[k] = 0.f;
                     if (a.c.model == MODEL_RIGID) rb_step(a.c, s, act, sp);
+                    else if (a.c.model == MODEL_PMD) pmd_step(a.c, s, act, sp);
+                    else if (a.c.model == MODEL_SIMPLE) simple_step(a.c, s, act, sp);
                     else pm_step(a.c, drag, lam, s, act, sp);
                     float best = CUDART_INF_F;
                     int bid = -1;

@@ -195,8 +195,11 @@ __device__ __forceinline__ void cast_list(const WList& L, const int4& meta, int 
 // Second-level cull for one chunk of rays whose body directions lie in the
 // cone (axis cone.xyz, cos = cone.w, sin = sn); aw = R axis in the world.  A
 // sphere (or a box's bounding sphere) at oc with tangent length sC and radius
-// rho meets the cone iff oc.aw >= cos * sC - sin * rho.  Writes the kept slots
-// in index order to L.sub (spheres from 0, boxes from ns_max); one full warp.
+// rho meets the cone iff oc.aw >= cos * sC - sin * rho (the angle to the axis
+// at most the half-angle plus the sphere's angular radius).  That form holds
+// while the two angles add up to at most pi, so a chunk whose half-angle
+// exceeds pi/2 (cos < 0) keeps every entry.  Writes the kept slots in index
+// order to L.sub (spheres from 0, boxes from ns_max); one full warp.
 __device__ inline int2 warp_sub_cull(const WList& L, const int4& meta, int ns_max, const float* aw, float cs,
                                      float sn) {
     const int lane = threadIdx.x & 31;
@@ -207,7 +210,7 @@ __device__ inline int2 warp_sub_cull(const WList& L, const int4& meta, int ns_ma
         if (k < meta.x) {
             const float4 e = L.sph[k];
             const float2 x = L.sx[k];
-            keep = fmaf(e.x, aw[0], fmaf(e.y, aw[1], fmaf(e.z, aw[2], fmaf(cs, e.w, sn * x.y)))) >= 0.f;
+            keep = cs < 0.f || fmaf(e.x, aw[0], fmaf(e.y, aw[1], fmaf(e.z, aw[2], fmaf(cs, e.w, sn * x.y)))) >= 0.f;
         }
         const unsigned bal = __ballot_sync(0xffffffffu, keep);
         if (keep) L.sub[ns + __popc(bal & ((1u << lane) - 1u))] = (short)k;
@@ -218,7 +221,8 @@ __device__ inline int2 warp_sub_cull(const WList& L, const int4& meta, int ns_ma
         bool keep = false;
         if (k < meta.y) {
             const float4 c = L.box[2 * k], h = L.box[2 * k + 1];
-            keep = c.w < 0.f || fmaf(c.x, aw[0], fmaf(c.y, aw[1], fmaf(c.z, aw[2], fmaf(-cs, c.w, sn * h.w)))) >= 0.f;
+            keep = cs < 0.f || c.w < 0.f ||
+                   fmaf(c.x, aw[0], fmaf(c.y, aw[1], fmaf(c.z, aw[2], fmaf(-cs, c.w, sn * h.w)))) >= 0.f;
         }
         const unsigned bal = __ballot_sync(0xffffffffu, keep);
         if (keep) L.sub[ns_max + nb + __popc(bal & ((1u << lane) - 1u))] = (short)k;

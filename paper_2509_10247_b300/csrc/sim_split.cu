@@ -20,6 +20,7 @@ __device__ __forceinline__ void load_row(const float* src, int D, bool on, int m
 #pragma unroll
     for (int k = 0; k < 16; ++k) s[k] = (on && k < D) ? src[k] : 0.f;
     if (!on && model == MODEL_RIGID) s[3] = 1.f;  // a harmless unit quaternion on idle lanes
+    if (!on && model == MODEL_SIMPLE) s[6] = s[10] = s[14] = 1.f;  // and rotation
 }
 
 __device__ __forceinline__ void step_agent(const Phys& c, float drag, float lam, const float* s, const float* act,
@@ -27,6 +28,8 @@ __device__ __forceinline__ void step_agent(const Phys& c, float drag, float lam,
 #pragma unroll
     for (int k = 0; k < 16; ++k) sp[k] = 0.f;
     if (c.model == MODEL_RIGID) rb_step(c, s, act, sp);
+    else if (c.model == MODEL_PMD) pmd_step(c, s, act, sp);
+    else if (c.model == MODEL_SIMPLE) simple_step(c, s, act, sp);
     else pm_step(c, drag, lam, s, act, sp);
 }
 
@@ -421,6 +424,7 @@ __global__ void __launch_bounds__(128) k_physics_bwd(const Args a) {
                 s1[k] = on ? seg[((t - t0 + 1) * M + lane) * 16 + k] : 0.f;
             }
             if (!on && a.c.model == MODEL_RIGID) { s0[3] = 1.f; s1[3] = 1.f; }
+            if (!on && a.c.model == MODEL_SIMPLE) { s0[6] = s0[10] = s0[14] = 1.f; s1[6] = s1[10] = s1[14] = 1.f; }
 #pragma unroll
             for (int k = 0; k < 4; ++k) act[k] = (on && k < A) ? a.actions[o * A + k] : 0.f;
             if (!dn && a.gposes && on) {
@@ -482,6 +486,8 @@ __global__ void __launch_bounds__(128) k_physics_bwd(const Args a) {
             }
             // dynamics
             if (a.c.model == MODEL_RIGID) rb_step_vjp(a.c, s0, act, gp, gs, ga);
+            else if (a.c.model == MODEL_PMD) pmd_step_vjp(a.c, act, gp, gs, ga);
+            else if (a.c.model == MODEL_SIMPLE) simple_step_vjp(a.c, s0, act, gp, gs, ga);
             else pm_step_vjp(a.c, drag, lam, act, gp, gs, ga);
             if (on)
 #pragma unroll

@@ -73,7 +73,7 @@ __global__ void k_fill_rays(float4* cam, float* cam_t, int W, int H, double th, 
 }
 
 bool bad_cfg(const sim_config* c) {
-    if (c->model != SIM_MODEL_POINT_MASS && c->model != SIM_MODEL_RIGID) return true;
+    if (c->model < SIM_MODEL_POINT_MASS || c->model > SIM_MODEL_SIMPLE) return true;
     if (c->n_env < 1 || c->n_agent < 1 || c->n_agent > 32) return true;
     if (!(c->dt > 0.f) || !std::isfinite(c->dt)) return true;
     if (c->cam_w < 0 || c->cam_h < 0 || c->lid_ch < 0 || c->lid_az < 0) return true;
@@ -121,8 +121,8 @@ extern "C" int sim_step_static(const sim_config* cfg, const float* prims, const 
     ds::Args a;
     memset(&a, 0, sizeof(a));
     const sim_config& c = *cfg;
-    a.c.model = c.model; a.c.M = c.n_agent; a.c.D = c.model == SIM_MODEL_RIGID ? 13 : 12;
-    a.c.A = c.model == SIM_MODEL_RIGID ? 4 : 3;
+    a.c.model = c.model; a.c.M = c.n_agent; a.c.D = sim_state_dim(c.model);
+    a.c.A = sim_action_dim(c.model);
     a.c.dt = c.dt; a.c.g = c.gravity; a.c.lam = c.lam; a.c.drag = c.drag;
     a.c.act_scale = c.act_scale; a.c.ema_alpha = c.ema_alpha; a.c.mass = c.mass;
     for (int i = 0; i < 3; ++i) {

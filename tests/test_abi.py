@@ -53,6 +53,8 @@ def test_version_and_errors(lib):
     assert binding.sim_strerror(5) == "unknown error"
     assert binding.sim_state_dim(0) == 12 and binding.sim_state_dim(1) == 13
     assert binding.sim_action_dim(0) == 3 and binding.sim_action_dim(1) == 4
+    assert binding.sim_state_dim(2) == 12 and binding.sim_action_dim(2) == 3
+    assert binding.sim_state_dim(3) == 15 and binding.sim_action_dim(3) == 4
     assert binding.sim_state_dim(9) == -1
 
 

@@ -21,6 +21,13 @@ WORKLOADS = {
     "swarm_maps": lambda: synth.preset("swarm_16384env_8agent_8maps_depth16x9", n_env=48, horizon=12),
     "rigid_lidar": lambda: synth.preset("rigid_65536env_256obst_depth_lidar", n_env=6, horizon=6,
                                         ckpt_every=4),
+    "pm_discrete": lambda: synth.params(model="pm_disc", n_env=40, horizon=10, cam=(16, 9, 90.0, 10.0),
+                                        map_counts=[(30, 15)], n_maps=5, obst_lo=(-6, -6, -6), obst_hi=(6, 6, 6),
+                                        w_obs=5.0, terminate=1, ckpt_every=4),
+    "simple_quad": lambda: synth.params(model="simple", n_env=40, horizon=10, cam=(12, 8, 90.0, 10.0),
+                                        lidar=(4, 32, -15.0, 15.0, 10.0), map_counts=[(30, 15)], n_maps=5,
+                                        obst_lo=(-6, -6, -6), obst_hi=(6, 6, 6), w_obs=5.0, pos_sq=0,
+                                        terminate=1, ckpt_every=4),
     "ragged": lambda: synth.params(n_env=37, n_agent=3, horizon=7, cam=(7, 5, 75.0, 9.0),
                                    map_counts=[(5, 3), (0, 4), (6, 0), (0, 0)], n_maps=4,
                                    w_obs=3.0, w_agent=2.0, d_agent=1.5, terminate=1, ckpt_every=3),
@@ -202,6 +209,8 @@ def test_launch_shape_variants_agree(pair):
         o2 = s2.rollout(pair.act)
         ga, gs = s2.backward(g_r, g_d, g_l)
         assert torch.equal(pair.out["depth"], o2["depth"]), ex
+        if pair.out["lidar"] is not None:
+            assert torch.equal(pair.out["lidar"], o2["lidar"]), ex
         if ref is None:
             ref = (ga, gs)
         else:
