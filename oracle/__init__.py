@@ -55,6 +55,7 @@ class OcConfig(C.Structure):
 class OcScene(C.Structure):
     _fields_ = [
         ("spheres", _pd), ("sph_off", _pi), ("boxes", _pd), ("box_off", _pi),
+        ("cylinders", _pd), ("cyl_off", _pi), ("gates", _pd), ("gate_off", _pi),
         ("env_map", _pi), ("n_maps", _i), ("targets", _pd), ("pool", _pd),
         ("drag_env", _pd), ("lam_env", _pd),
     ]
@@ -95,6 +96,14 @@ def lib():
         L.oc_sdf_sphere.argtypes = [_pd, _pd]
         L.oc_sdf_box.restype = _d
         L.oc_sdf_box.argtypes = [_pd, _pd]
+        L.oc_ray_cylinder.restype = _d
+        L.oc_ray_cylinder.argtypes = [_pd, _pd, _pd, _pi]
+        L.oc_ray_gate.restype = _d
+        L.oc_ray_gate.argtypes = [_pd, _pd, _pd, _pi]
+        L.oc_sdf_cylinder.restype = _d
+        L.oc_sdf_cylinder.argtypes = [_pd, _pd]
+        L.oc_sdf_gate.restype = _d
+        L.oc_sdf_gate.argtypes = [_pd, _pd, _pi]
         L.oc_pose.restype = C.c_int
         L.oc_loss.restype = _d
         L.oc_max_threads.restype = C.c_int
@@ -159,13 +168,18 @@ class Oracle:
             sph_off=np.ascontiguousarray(inp["sph_off"], dtype=np.int32),
             boxes=_c64(inp["boxes"].reshape(-1, 6)),
             box_off=np.ascontiguousarray(inp["box_off"], dtype=np.int32),
+            cylinders=_c64(inp["cylinders"].reshape(-1, 5)) if inp.get("cylinders") is not None else None,
+            cyl_off=np.ascontiguousarray(inp["cyl_off"], dtype=np.int32) if inp.get("cylinders") is not None else None,
+            gates=_c64(inp["gates"].reshape(-1, 7)) if inp.get("gates") is not None else None,
+            gate_off=np.ascontiguousarray(inp["gate_off"], dtype=np.int32) if inp.get("gates") is not None else None,
             env_map=np.ascontiguousarray(inp["env_map"], dtype=np.int32),
             targets=_c64(inp["targets"]), pool=_c64(inp["pool"]),
             drag_env=_c64(inp.get("drag_env")), lam_env=_c64(inp.get("lam_env")),
         )
         k = self._keep
         self.scene = OcScene(_p(k["spheres"]), _p(k["sph_off"], _pi), _p(k["boxes"]),
-                             _p(k["box_off"], _pi), _p(k["env_map"], _pi),
+                             _p(k["box_off"], _pi), _p(k["cylinders"]), _p(k["cyl_off"], _pi),
+                             _p(k["gates"]), _p(k["gate_off"], _pi), _p(k["env_map"], _pi),
                              len(k["sph_off"]) - 1, _p(k["targets"]), _p(k["pool"]),
                              _p(k["drag_env"]), _p(k["lam_env"]))
 
@@ -255,6 +269,28 @@ def ray_box(o, d, box):
     ax = np.zeros(1, np.int32)
     t = lib().oc_ray_box(_p(_v(o)), _p(_v(d)), _p(_v(box)), _p(ax, _pi))
     return t, int(ax[0])
+
+
+def ray_cylinder(o, d, cyl):
+    """(t, face): face 0 side, 1 cap; cyl = (cx, cy, r, zmin, zmax)."""
+    f = np.zeros(1, np.int32)
+    t = lib().oc_ray_cylinder(_p(_v(o)), _p(_v(d)), _p(_v(cyl)), _p(f, _pi))
+    return t, int(f[0])
+
+
+def ray_gate(o, d, gate):
+    """(t, axis): gate = (cx, cy, cz, yaw, w, b, hd); axis 0..2 outer face, 3..4 inner wall."""
+    ax = np.zeros(1, np.int32)
+    t = lib().oc_ray_gate(_p(_v(o)), _p(_v(d)), _p(_v(gate)), _p(ax, _pi))
+    return t, int(ax[0])
+
+
+def sdf_cylinder(p, cyl):
+    return lib().oc_sdf_cylinder(_p(_v(p)), _p(_v(cyl)))
+
+
+def sdf_gate(p, gate):
+    return lib().oc_sdf_gate(_p(_v(p)), _p(_v(gate)), None)
 
 
 def sdf_sphere(p, sphere):

@@ -13,9 +13,11 @@
  *     side taken at time t (the paper gives only the continuous equations);
  *   - point-mass attitude from the thrust direction and the horizontal
  *     projection of an exponential moving average of velocity (Sec. III-B);
- *   - depth camera and LiDAR by ray casting against analytic spheres and
- *     axis-aligned boxes (Sec. III-B), brute force over every primitive, no
- *     field-of-view culling (culling only skips primitives no ray can hit);
+ *   - depth camera and LiDAR by ray casting against analytic spheres,
+ *     axis-aligned boxes, vertical capped cylinders and racing-gate frames
+ *     (Sec. III-B: one ray-casting function per primitive shape), brute force
+ *     over every primitive, no field-of-view culling (culling only skips
+ *     primitives no ray can hit);
  *   - collisions, the dense differentiable reward R_ctrl and the sparse
  *     reward R_goal (Sec. III-C, III-D, III-E), termination and reset;
  *   - the reverse-mode adjoint of the whole rollout, i.e. the chain rule of
@@ -28,8 +30,12 @@
  *   state  [NM][D], D = 12 (point mass: p, v, a, ema_v) or 13 (rigid: p,
  *          q=(w,x,y,z), v, omega); actions [T][NM][A], A = 3 or 4;
  *   spheres [K][4] = (cx, cy, cz, r); boxes [K][6] = (min xyz, max xyz);
- *   per-map CSR offsets; env_map [N]; targets [NM][3]; pool [P][NM][D].
- *   Primitive ids within a map: spheres 0..Ks-1, then boxes Ks..Ks+Kb-1.
+ *   cylinders [K][5] = (cx, cy, r, zmin, zmax), axis along world z;
+ *   gates [K][7] = (cx, cy, cz, yaw, w, b, hd): a square frame whose opening
+ *   has half-width w, border width b and half-depth hd along its normal
+ *   (cos yaw, sin yaw, 0); per-map CSR offsets; env_map [N]; targets [NM][3];
+ *   pool [P][NM][D].  Primitive ids within a map: spheres 0..ns-1, boxes
+ *   ns..ns+nb-1, cylinders from ns+nb, gates from ns+nb+nc.
  */
 #include <math.h>
 #include <stdint.h>
@@ -85,6 +91,10 @@ typedef struct {
     const int32_t *sph_off;
     const double *boxes;
     const int32_t *box_off;
+    const double *cylinders; /* NULL: none */
+    const int32_t *cyl_off;
+    const double *gates;     /* NULL: none */
+    const int32_t *gate_off;
     const int32_t *env_map;
     int32_t n_maps;
     const double *targets;
@@ -446,44 +456,278 @@ static void sdf_box_grad(const double *p, const double *bx, double *gp)
     }
 }
 
-/* One ray cast against every primitive of a map, brute force.  Returns t*
- * (+inf on a miss) and the hit id (lowest id among exact ties; -1 on a miss).
- * amb receives the flags of this ray, given the clamp distance tclamp in ray
- * length: bit 0 a value decision near its threshold (grazing, origin near a
- * surface), bit 1 a gradient decision near its threshold (second hit, range
- * clamp, box edge), bit 2 a value ill-conditioned in FP32, bit 3 a gradient
- * ill-conditioned under FP32 trajectory drift (near-grazing incidence). */
-static double cast_ray(const double *o, const double *d, const double *sph, int ns,
-                       const double *box, int nb, int *hit, double tclamp, int *amb)
+/* Ray vs vertical capped cylinder cy = (cx, cy, r, zmin, zmax): the solid is
+ * the intersection of the infinite cylinder (x - cx)^2 + (y - cy)^2 <= r^2
+ * (a quadratic in the ray parameter) and the slab zmin <= z <= zmax.  Entry =
+ * the later of the two entries, exit = the earlier exit; hit iff entry <=
+ * exit and exit >= 0; 0 when the origin is inside.  A ray parallel to the
+ * axis keeps the quadratic interval only from inside the infinite cylinder,
+ * a horizontal ray the slab only from between its planes.  *face receives 0
+ * for an entry through the side, 1 through a cap. */
+double oc_ray_cylinder(const double *o, const double *d, const double *cy, int *face)
 {
-    double best = OC_INF, second = OC_INF;
-    int id = -1, flags = 0;
-    for (int k = 0; k < ns; ++k) {
-        double t = oc_ray_sphere(o, d, sph + 4 * k);
-        if (t < best) { second = best; best = t; id = k; }
-        else if (t < second) second = t;
+    double ex = o[0] - cy[0], ey = o[1] - cy[1];
+    double a = d[0] * d[0] + d[1] * d[1];
+    double b = d[0] * ex + d[1] * ey;
+    double cc = ex * ex + ey * ey - cy[2] * cy[2];
+    double s0, s1, z0, z1;
+    if (a == 0.0) {
+        if (cc > 0.0) return OC_INF;
+        s0 = -OC_INF; s1 = OC_INF;
+    } else {
+        double disc = b * b - a * cc;
+        if (disc < 0.0) return OC_INF;
+        double sq = sqrt(disc);
+        s0 = (-b - sq) / a; s1 = (-b + sq) / a;
     }
-    for (int k = 0; k < nb; ++k) {
-        double t = oc_ray_box(o, d, box + 6 * k, NULL);
-        if (t < best) { second = best; best = t; id = ns + k; }
-        else if (t < second) second = t;
+    if (d[2] == 0.0) {
+        if (o[2] < cy[3] || o[2] > cy[4]) return OC_INF;
+        z0 = -OC_INF; z1 = OC_INF;
+    } else {
+        double t1 = (cy[3] - o[2]) / d[2], t2 = (cy[4] - o[2]) / d[2];
+        z0 = t1 < t2 ? t1 : t2; z1 = t1 < t2 ? t2 : t1;
     }
-    /* near-degenerate decisions that could change the value in FP32: a
-     * grazing sphere whose tangent distance competes with the nearest hit */
-    double reach = (best < tclamp ? best : tclamp) + 1e-2;
-    for (int k = 0; k < ns; ++k) {
-        const double *sp = sph + 4 * k;
+    double tn = s0 > z0 ? s0 : z0, tf = s1 < z1 ? s1 : z1;
+    if (face) *face = s0 >= z0 ? 0 : 1;
+    if (tn > tf || tf < 0.0) return OC_INF;
+    return tn > 0.0 ? tn : 0.0;
+}
+
+/* Signed distance to the capped cylinder: radial excess q_r = rho - r and
+ * axial excess q_z = |z - zc| - hz combine like a 2D box. */
+double oc_sdf_cylinder(const double *p, const double *cy)
+{
+    double rho = hypot(p[0] - cy[0], p[1] - cy[1]);
+    double zc = 0.5 * (cy[3] + cy[4]), hz = 0.5 * (cy[4] - cy[3]);
+    double qr = rho - cy[2], qz = fabs(p[2] - zc) - hz;
+    double in = qr > qz ? qr : qz;
+    return sqrt(relu(qr) * relu(qr) + relu(qz) * relu(qz)) + (in < 0.0 ? in : 0.0);
+}
+
+static void sdf_cylinder_grad(const double *p, const double *cy, double *gp)
+{
+    double ex = p[0] - cy[0], ey = p[1] - cy[1];
+    double rho = hypot(ex, ey);
+    double zc = 0.5 * (cy[3] + cy[4]), hz = 0.5 * (cy[4] - cy[3]);
+    double qr = rho - cy[2], qz = fabs(p[2] - zc) - hz;
+    double ur[2] = {rho > 0.0 ? ex / rho : 0.0, rho > 0.0 ? ey / rho : 0.0};
+    double sz = p[2] - zc >= 0.0 ? 1.0 : -1.0;
+    double out = sqrt(relu(qr) * relu(qr) + relu(qz) * relu(qz));
+    if (out > 0.0) {
+        gp[0] = relu(qr) * ur[0] / out;
+        gp[1] = relu(qr) * ur[1] / out;
+        gp[2] = relu(qz) * sz / out;
+    } else if (qr >= qz) {
+        gp[0] = ur[0]; gp[1] = ur[1]; gp[2] = 0.0;
+    } else {
+        gp[0] = 0.0; gp[1] = 0.0; gp[2] = sz;
+    }
+}
+
+/* Racing gate g = (cx, cy, cz, yaw, w, b, hd).  Its frame: normal
+ * n = (cos yaw, sin yaw, 0), lateral l = (-sin yaw, cos yaw, 0), up z.  Local
+ * coordinates of a point x: u = (n.(x - c), l.(x - c), z - cz).  The solid is
+ * the box |u_n| <= hd, |u_l| <= w + b, |u_z| <= w + b without the open
+ * square |u_l| < w, |u_z| < w (all u_n): a frame of four bars. */
+static void gate_axes(const double *g, double *n, double *l)
+{
+    double cs = cos(g[3]), sn = sin(g[3]);
+    n[0] = cs; n[1] = sn; n[2] = 0.0;
+    l[0] = -sn; l[1] = cs; l[2] = 0.0;
+}
+
+static void gate_local(const double *g, const double *x, int is_dir, double *u)
+{
+    double n[3], l[3], r[3];
+    gate_axes(g, n, l);
+    for (int i = 0; i < 3; ++i) r[i] = x[i] - (is_dir ? 0.0 : g[i]);
+    u[0] = dot3(n, r); u[1] = dot3(l, r); u[2] = r[2];
+}
+
+static void gate_world(const double *g, const double *u, double *x)
+{
+    double n[3], l[3];
+    gate_axes(g, n, l);
+    for (int i = 0; i < 3; ++i) x[i] = u[0] * n[i] + u[1] * l[i] + (i == 2 ? u[2] : 0.0);
+}
+
+/* Ray vs gate frame.  The ray meets the outer box over [t_n, t_f] (slabs in
+ * local coordinates) and the open square prism over (i_n, i_f) (slabs in u_l
+ * and u_z only).  The first solid point at or after max(t_n, 0) is that point
+ * itself unless it lies strictly inside the prism; then it is where the ray
+ * leaves the prism, i_f, if that is still inside the outer box.  0 when the
+ * origin is in the solid.  *axis: 0..2 = outer face entered (u_n, u_l, u_z),
+ * 3 / 4 = inner wall met (u_l / u_z), -1 at t = 0. */
+double oc_ray_gate(const double *o, const double *d, const double *g, int *axis)
+{
+    double uo[3], ud[3];
+    gate_local(g, o, 0, uo);
+    gate_local(g, d, 1, ud);
+    double W = g[4] + g[5], half[3] = {g[6], W, W};
+    double tn = -OC_INF, tf = OC_INF, in = -OC_INF, inf_ = OC_INF;
+    int ax = -1, bx = -1, open = 1;
+    for (int i = 0; i < 3; ++i) {
+        if (ud[i] == 0.0) {
+            if (fabs(uo[i]) > half[i]) return OC_INF;
+            continue;
+        }
+        double t1 = (-half[i] - uo[i]) / ud[i], t2 = (half[i] - uo[i]) / ud[i];
+        double lo = t1 < t2 ? t1 : t2, hi = t1 < t2 ? t2 : t1;
+        if (lo > tn) { tn = lo; ax = i; }
+        if (hi < tf) tf = hi;
+    }
+    if (tn > tf || tf < 0.0) return OC_INF;
+    for (int i = 1; i < 3; ++i) {
+        if (ud[i] == 0.0) {
+            if (fabs(uo[i]) >= g[4]) open = 0;
+            continue;
+        }
+        double t1 = (-g[4] - uo[i]) / ud[i], t2 = (g[4] - uo[i]) / ud[i];
+        double lo = t1 < t2 ? t1 : t2, hi = t1 < t2 ? t2 : t1;
+        if (lo > in) in = lo;
+        if (hi < inf_) { inf_ = hi; bx = i; }
+    }
+    if (in >= inf_) open = 0;
+    double ta = tn > 0.0 ? tn : 0.0;
+    if (!open || ta <= in || ta >= inf_) {
+        if (axis) *axis = tn > 0.0 ? ax : -1;
+        return ta;
+    }
+    if (inf_ <= tf) {
+        if (axis) *axis = 2 + bx;
+        return inf_;
+    }
+    return OC_INF;
+}
+
+/* The gate's four bars as boxes in local coordinates (min u, max u):
+ * top and bottom span the full outer width, left and right the opening's
+ * height, so the bars tile the frame without overlap. */
+static void gate_bar(const double *g, int k, double *bx)
+{
+    double w = g[4], b = g[5], hd = g[6], W = w + b, m = w + 0.5 * b;
+    double cl = 0.0, cz = 0.0, hl, hz;
+    if (k < 2) { cz = k == 0 ? m : -m; hl = W; hz = 0.5 * b; }
+    else { cl = k == 2 ? -m : m; hl = 0.5 * b; hz = w; }
+    bx[0] = -hd; bx[1] = cl - hl; bx[2] = cz - hz;
+    bx[3] = hd; bx[4] = cl + hl; bx[5] = cz + hz;
+}
+
+/* Signed distance to the gate: the minimum over its four bars (exact outside
+ * the frame, negative inside it).  *bar receives the arg-min bar. */
+double oc_sdf_gate(const double *p, const double *g, int *bar)
+{
+    double u[3], best = OC_INF;
+    int bi = 0;
+    gate_local(g, p, 0, u);
+    for (int k = 0; k < 4; ++k) {
+        double bx[6];
+        gate_bar(g, k, bx);
+        double s = oc_sdf_box(u, bx);
+        if (s < best) { best = s; bi = k; }
+    }
+    if (bar) *bar = bi;
+    return best;
+}
+
+static void sdf_gate_grad(const double *p, const double *g, double *gp)
+{
+    double u[3], bx[6], gu[3];
+    int k;
+    oc_sdf_gate(p, g, &k);
+    gate_local(g, p, 0, u);
+    gate_bar(g, k, bx);
+    sdf_box_grad(u, bx, gu);
+    gate_world(g, gu, gp);
+}
+
+/* ------------------------------------------------------------ maps */
+
+/* The primitives of one map, by kind. */
+typedef struct {
+    const double *sph, *box, *cyl, *gate;
+    int ns, nb, nc, ng;
+} map_t;
+
+static int map_count(const map_t *m) { return m->ns + m->nb + m->nc + m->ng; }
+
+/* Ray parameter of the first hit of primitive id (aux: box entry axis,
+ * cylinder face or gate axis). */
+static double prim_ray(const map_t *m, int id, const double *o, const double *d, int *aux)
+{
+    *aux = -1;
+    if (id < m->ns) return oc_ray_sphere(o, d, m->sph + 4 * id);
+    id -= m->ns;
+    if (id < m->nb) return oc_ray_box(o, d, m->box + 6 * id, aux);
+    id -= m->nb;
+    if (id < m->nc) return oc_ray_cylinder(o, d, m->cyl + 5 * id, aux);
+    return oc_ray_gate(o, d, m->gate + 7 * (id - m->nc), aux);
+}
+
+/* Outward unit normal of primitive id at the hit o + t d (t > 0); false when
+ * the hit has no face (aux -1). */
+static int prim_normal(const map_t *m, int id, const double *o, const double *d, double t, int aux, double *n)
+{
+    for (int i = 0; i < 3; ++i) n[i] = 0.0;
+    if (id < m->ns) {
+        const double *sp = m->sph + 4 * id;
+        for (int i = 0; i < 3; ++i) n[i] = (o[i] + t * d[i] - sp[i]) / sp[3];
+        return 1;
+    }
+    id -= m->ns;
+    if (aux < 0) return 0;
+    if (id < m->nb) {
+        n[aux] = d[aux] > 0.0 ? -1.0 : 1.0;
+        return 1;
+    }
+    id -= m->nb;
+    if (id < m->nc) {
+        const double *cy = m->cyl + 5 * id;
+        if (aux == 1) { n[2] = d[2] > 0.0 ? -1.0 : 1.0; return 1; }
+        n[0] = (o[0] + t * d[0] - cy[0]) / cy[2];
+        n[1] = (o[1] + t * d[1] - cy[1]) / cy[2];
+        return 1;
+    }
+    const double *g = m->gate + 7 * (id - m->nc);
+    double ud[3], un[3] = {0.0, 0.0, 0.0};
+    gate_local(g, d, 1, ud);
+    int k = aux < 3 ? aux : aux - 2;
+    un[k] = ud[k] > 0.0 ? -1.0 : 1.0;
+    gate_world(g, un, n);
+    return 1;
+}
+
+static double prim_sdf(const map_t *m, int id, const double *p)
+{
+    if (id < m->ns) return oc_sdf_sphere(p, m->sph + 4 * id);
+    id -= m->ns;
+    if (id < m->nb) return oc_sdf_box(p, m->box + 6 * id);
+    id -= m->nb;
+    if (id < m->nc) return oc_sdf_cylinder(p, m->cyl + 5 * id);
+    return oc_sdf_gate(p, m->gate + 7 * (id - m->nc), NULL);
+}
+
+/* Slab-type decisions of primitive id that are near their thresholds for
+ * the ray: entry and exit close (grazing), or two candidate entry times
+ * close (the entry face, or for a gate whether the entry is inside the
+ * opening, may change in FP32).  Returns amb bits: 1|2 value, 2 gradient. */
+static int prim_amb(const map_t *m, int id, const double *o, const double *d, double reach)
+{
+    int flags = 0;
+    if (fabs(prim_sdf(m, id, o)) < AMB_INSIDE) flags |= 3;
+    if (id < m->ns) {
+        const double *sp = m->sph + 4 * id;
         double oc[3] = {sp[0] - o[0], sp[1] - o[1], sp[2] - o[2]};
         double C = dot3(oc, oc) - sp[3] * sp[3];
         double b = dot3(d, oc);
-        if (fabs(norm3(oc) - sp[3]) < AMB_INSIDE) flags |= 3;
         double disc = b * b - C;
         if (b > 0.0 && b - sqrt(fabs(disc)) < reach && fabs(disc) < AMB_DISC * (b * b > 1.0 ? b * b : 1.0))
             flags |= 3;
+        return flags;
     }
-    for (int k = 0; k < nb; ++k) {
-        const double *bx = box + 6 * k;
-        if (fabs(oc_sdf_box(o, bx)) < AMB_INSIDE) flags |= 3;
+    int k = id - m->ns;
+    if (k < m->nb) {
+        const double *bx = m->box + 6 * k;
         double tn = -OC_INF, tf = OC_INF;
         int ok = 1;
         for (int i = 0; i < 3; ++i) {
@@ -494,24 +738,82 @@ static double cast_ray(const double *o, const double *d, const double *sph, int 
             if (hi < tf) tf = hi;
         }
         if (ok && tn > 0.0 && tn < reach && fabs(tf - tn) < AMB_SLAB) flags |= 3;
+        return flags;
     }
+    k -= m->nb;
+    /* cylinders and gates: collect the interval end points and compare */
+    double e[10];
+    int ne = 0;
+    if (k < m->nc) {
+        const double *cy = m->cyl + 5 * k;
+        double ex = o[0] - cy[0], ey = o[1] - cy[1];
+        double a = d[0] * d[0] + d[1] * d[1], b = d[0] * ex + d[1] * ey;
+        double cc = ex * ex + ey * ey - cy[2] * cy[2];
+        if (a > 0.0) {
+            double disc = b * b - a * cc;
+            double sq = sqrt(fabs(disc));
+            /* grazing the side: the two roots (nearly) coincide */
+            if ((-b - sq) / a < reach && -b + sq > 0.0 && fabs(disc) < AMB_DISC * (b * b > a ? b * b : a))
+                flags |= 3;
+            if (disc >= 0.0) { e[ne++] = (-b - sq) / a; e[ne++] = (-b + sq) / a; }
+        }
+        if (d[2] != 0.0) { e[ne++] = (cy[3] - o[2]) / d[2]; e[ne++] = (cy[4] - o[2]) / d[2]; }
+    } else {
+        const double *g = m->gate + 7 * (k - m->nc);
+        double uo[3], ud[3];
+        gate_local(g, o, 0, uo);
+        gate_local(g, d, 1, ud);
+        double W = g[4] + g[5], half[3] = {g[6], W, W};
+        for (int i = 0; i < 3; ++i)
+            if (ud[i] != 0.0) {
+                e[ne++] = (-half[i] - uo[i]) / ud[i];
+                e[ne++] = (half[i] - uo[i]) / ud[i];
+            }
+        for (int i = 1; i < 3; ++i)
+            if (ud[i] != 0.0) {
+                e[ne++] = (-g[4] - uo[i]) / ud[i];
+                e[ne++] = (g[4] - uo[i]) / ud[i];
+            }
+    }
+    for (int i = 0; i < ne; ++i)
+        for (int j = i + 1; j < ne; ++j) {
+            double lo = e[i] < e[j] ? e[i] : e[j];
+            if (lo > 0.0 && lo < reach && fabs(e[i] - e[j]) < AMB_EDGE * (lo > 1.0 ? lo : 1.0)) flags |= 3;
+        }
+    return flags;
+}
+
+/* One ray cast against every primitive of a map, brute force.  Returns t*
+ * (+inf on a miss) and the hit id (lowest id among exact ties; -1 on a miss).
+ * amb receives the flags of this ray, given the clamp distance tclamp in ray
+ * length: bit 0 a value decision near its threshold (grazing, origin near a
+ * surface), bit 1 a gradient decision near its threshold (second hit, range
+ * clamp, box edge), bit 2 a value ill-conditioned in FP32, bit 3 a gradient
+ * ill-conditioned under FP32 trajectory drift (near-grazing incidence). */
+static double cast_ray(const double *o, const double *d, const map_t *m, int *hit, double tclamp, int *amb)
+{
+    double best = OC_INF, second = OC_INF;
+    int id = -1, flags = 0, aux = -1;
+    const int np = map_count(m);
+    for (int k = 0; k < np; ++k) {
+        int ak;
+        double t = prim_ray(m, k, o, d, &ak);
+        if (t < best) { second = best; best = t; id = k; aux = ak; }
+        else if (t < second) second = t;
+    }
+    /* near-degenerate decisions that could change the value in FP32 */
+    double reach = (best < tclamp ? best : tclamp) + 1e-2;
+    for (int k = 0; k < np; ++k) flags |= prim_amb(m, k, o, d, reach);
     /* gradient-only ambiguities: second hit close, range clamp, grazing,
-     * entry through an edge */
+     * entry through a box edge */
     if (best < OC_INF) {
         if (second - best < AMB_GAP) flags |= 2;
         if (fabs(best - tclamp) < AMB_RANGE) flags |= 2;
-        if (best > 0.0 && best < tclamp) {
-            double n[3];
-            if (id < ns) {
-                const double *sp = sph + 4 * id;
-                for (int i = 0; i < 3; ++i) n[i] = (o[i] + best * d[i] - sp[i]) / sp[3];
-            } else {
-                const double *bx = box + 6 * (id - ns);
-                int ax = -1;
-                oc_ray_box(o, d, bx, &ax);
-                for (int i = 0; i < 3; ++i) n[i] = 0.0;
-                if (ax >= 0) n[ax] = d[ax] > 0 ? -1.0 : 1.0;
+        double n[3];
+        if (best > 0.0 && best < tclamp && prim_normal(m, id, o, d, best, aux, n)) {
+            if (id >= m->ns && id < m->ns + m->nb) {
                 /* two slab entry times within AMB_EDGE: the ray enters at an edge */
+                const double *bx = m->box + 6 * (id - m->ns);
                 double tl[3];
                 for (int i = 0; i < 3; ++i) {
                     if (d[i] == 0.0) { tl[i] = -OC_INF; continue; }
@@ -519,13 +821,16 @@ static double cast_ray(const double *o, const double *d, const double *sph, int 
                     tl[i] = t1 < t2 ? t1 : t2;
                 }
                 for (int i = 0; i < 3; ++i)
-                    if (i != ax && fabs(tl[i] - best) < AMB_EDGE * (best > 1.0 ? best : 1.0)) flags |= 2;
+                    if (i != aux && fabs(tl[i] - best) < AMB_EDGE * (best > 1.0 ? best : 1.0)) flags |= 2;
             }
             double nd = fabs(dot3(n, d));
             if (nd < AMB_GRAZE) flags |= 8;
-            /* gradient -n/(n.d) of a sphere hit turns by ~ dp/(r |n.d|) when
+            /* gradient -n/(n.d) of a curved hit turns by ~ dp/(r |n.d|) when
              * the trajectory drifts by dp (FP32 rollout): flag above 3e-4 */
-            if (id < ns && DRIFT_POS / (sph[4 * id + 3] * nd) > 3e-4) flags |= 8;
+            if (id < m->ns && DRIFT_POS / (m->sph[4 * id + 3] * nd) > 3e-4) flags |= 8;
+            if (id >= m->ns + m->nb && id < m->ns + m->nb + m->nc && aux == 0 &&
+                DRIFT_POS / (m->cyl[5 * (id - m->ns - m->nb) + 2] * nd) > 3e-4)
+                flags |= 8;
             /* ill-conditioned value: rounding the direction (COND_DIR per
              * component) and origin (COND_ORG) to FP32 moves the hit by
              * (COND_DIR t + COND_ORG) / |n.d|; flag above half the tolerance */
@@ -542,19 +847,14 @@ static double cast_ray(const double *o, const double *d, const double *sph, int 
 /* Minimum signed distance from p to the map's primitives and the arg-min id
  * (lowest id among exact ties; -1 and +inf for an empty map).  gap receives
  * the distance between the two smallest values. */
-static double sdf_min(const double *p, const double *sph, int ns, const double *box, int nb,
-                      int *id, double *gap)
+static double sdf_min(const double *p, const map_t *m, int *id, double *gap)
 {
     double best = OC_INF, second = OC_INF;
     int bi = -1;
-    for (int k = 0; k < ns; ++k) {
-        double s = oc_sdf_sphere(p, sph + 4 * k);
+    const int np = map_count(m);
+    for (int k = 0; k < np; ++k) {
+        double s = prim_sdf(m, k, p);
         if (s < best) { second = best; best = s; bi = k; }
-        else if (s < second) second = s;
-    }
-    for (int k = 0; k < nb; ++k) {
-        double s = oc_sdf_box(p, box + 6 * k);
-        if (s < best) { second = best; best = s; bi = ns + k; }
         else if (s < second) second = s;
     }
     *id = bi;
@@ -562,17 +862,20 @@ static double sdf_min(const double *p, const double *sph, int ns, const double *
     return best;
 }
 
-static void sdf_grad(const double *p, const double *sph, int ns, const double *box, int id,
-                     double *gp)
+static void sdf_grad(const double *p, const map_t *m, int id, double *gp)
 {
-    if (id < ns) {
-        const double *sp = sph + 4 * id;
+    if (id < m->ns) {
+        const double *sp = m->sph + 4 * id;
         double d[3] = {p[0] - sp[0], p[1] - sp[1], p[2] - sp[2]};
         double n = norm3(d);
         for (int i = 0; i < 3; ++i) gp[i] = n > 0.0 ? d[i] / n : 0.0;
-    } else {
-        sdf_box_grad(p, box + 6 * (id - ns), gp);
+        return;
     }
+    id -= m->ns;
+    if (id < m->nb) { sdf_box_grad(p, m->box + 6 * id, gp); return; }
+    id -= m->nb;
+    if (id < m->nc) { sdf_cylinder_grad(p, m->cyl + 5 * id, gp); return; }
+    sdf_gate_grad(p, m->gate + 7 * (id - m->nc), gp);
 }
 
 /* ------------------------------------------------------------ rollout state */
@@ -604,13 +907,18 @@ static void ctx_free(ctx_t *x)
     free(x->cam_dir); free(x->cam_fac); free(x->lid_dir);
 }
 
-static void map_of(const ctx_t *x, int env, const double **sph, int *ns, const double **box, int *nb)
+static void map_of(const ctx_t *x, int env, map_t *mp)
 {
-    int m = x->sc->env_map[env];
-    *sph = x->sc->spheres + 4 * x->sc->sph_off[m];
-    *ns = x->sc->sph_off[m + 1] - x->sc->sph_off[m];
-    *box = x->sc->boxes + 6 * x->sc->box_off[m];
-    *nb = x->sc->box_off[m + 1] - x->sc->box_off[m];
+    const oc_scene *sc = x->sc;
+    int m = sc->env_map[env];
+    mp->sph = sc->spheres + 4 * sc->sph_off[m];
+    mp->ns = sc->sph_off[m + 1] - sc->sph_off[m];
+    mp->box = sc->boxes + 6 * sc->box_off[m];
+    mp->nb = sc->box_off[m + 1] - sc->box_off[m];
+    mp->cyl = sc->cylinders ? sc->cylinders + 5 * sc->cyl_off[m] : NULL;
+    mp->nc = sc->cylinders ? sc->cyl_off[m + 1] - sc->cyl_off[m] : 0;
+    mp->gate = sc->gates ? sc->gates + 7 * sc->gate_off[m] : NULL;
+    mp->ng = sc->gates ? sc->gate_off[m + 1] - sc->gate_off[m] : 0;
 }
 
 static void dyn_step(const ctx_t *x, int env, const double *s, const double *a, double *o)
@@ -628,9 +936,8 @@ static void dyn_step(const ctx_t *x, int env, const double *s, const double *a, 
 static void render_agent(const ctx_t *x, int env, const double *s, double *depth, double *lidar,
                          int32_t *hc, int32_t *hl, uint8_t *ac, uint8_t *al)
 {
-    const double *sph, *box;
-    int ns, nb;
-    map_of(x, env, &sph, &ns, &box, &nb);
+    map_t mp;
+    map_of(x, env, &mp);
     double o[3], R[9];
     int pf = oc_pose(x->c, s, o, R);
     for (int r = 0; r < x->Rc; ++r) {
@@ -639,7 +946,7 @@ static void render_agent(const ctx_t *x, int env, const double *s, double *depth
         for (int i = 0; i < 3; ++i) d[i] = R[3 * i] * db[0] + R[3 * i + 1] * db[1] + R[3 * i + 2] * db[2];
         int id, amb;
         double tcl = x->c->cam_range / x->cam_fac[r];
-        double t = cast_ray(o, d, sph, ns, box, nb, &id, tcl, &amb);
+        double t = cast_ray(o, d, &mp, &id, tcl, &amb);
         double z = t * x->cam_fac[r];
         if (depth) depth[r] = z < x->c->cam_range ? z : x->c->cam_range;
         hc[r] = id;
@@ -650,7 +957,7 @@ static void render_agent(const ctx_t *x, int env, const double *s, double *depth
         double d[3];
         for (int i = 0; i < 3; ++i) d[i] = R[3 * i] * db[0] + R[3 * i + 1] * db[1] + R[3 * i + 2] * db[2];
         int id, amb;
-        double t = cast_ray(o, d, sph, ns, box, nb, &id, x->c->lid_range, &amb);
+        double t = cast_ray(o, d, &mp, &id, x->c->lid_range, &amb);
         if (lidar) lidar[r] = t < x->c->lid_range ? t : x->c->lid_range;
         hl[r] = id;
         al[r] = (uint8_t)(amb | ((pf & 4) ? 3 : 0));
@@ -691,9 +998,8 @@ static void env_step(const ctx_t *x, int env, int t, const double *s_t, const do
 {
     const oc_config *c = x->c;
     int M = c->n_agent, D = x->D, A = x->A;
-    const double *sph, *box;
-    int ns, nb;
-    map_of(x, env, &sph, &ns, &box, &nb);
+    map_t mp;
+    map_of(x, env, &mp);
     int i0 = env * M;
     int any = 0;
     int *coll = calloc((size_t)M, sizeof(int));
@@ -706,7 +1012,7 @@ static void env_step(const ctx_t *x, int env, int t, const double *s_t, const do
         const double *p = spre + (size_t)i * D;
         const double *a = act_t + (size_t)i * A;
         double gap;
-        double sd = sdf_min(p, sph, ns, box, nb, &id, &gap);
+        double sd = sdf_min(p, &mp, &id, &gap);
         sdf_id[i] = id;
         int col = sd < c->r_quad;
         if (fabs(sd - c->r_quad) < AMB_STEP) flags |= 1;
@@ -1053,23 +1359,15 @@ static void pose_vjp(const oc_config *c, const double *s, const double *go, cons
  * factor or 1), clampv the output clamp.  Zero on a miss, a clamped output,
  * or an origin inside a primitive (t* = 0).  The hit-point normal n gives
  * dt/do = -n / (n.d) and dt/dd = -t n / (n.d). */
-static void ray_vjp(const double *o, const double *d, const double *sph, int ns, const double *box,
-                    int id, double g, double fac, double clampv, double *go, double *gd)
+static void ray_vjp(const double *o, const double *d, const map_t *m, int id, double g, double fac,
+                    double clampv, double *go, double *gd)
 {
     if (id < 0 || g == 0.0) return;
-    double t, n[3];
-    if (id < ns) {
-        const double *sp = sph + 4 * id;
-        t = oc_ray_sphere(o, d, sp);
-        if (!(t > 0.0) || t * fac >= clampv) return;
-        for (int i = 0; i < 3; ++i) n[i] = (o[i] + t * d[i] - sp[i]) / sp[3];
-    } else {
-        int ax = -1;
-        t = oc_ray_box(o, d, box + 6 * (id - ns), &ax);
-        if (!(t > 0.0) || t * fac >= clampv || ax < 0) return;
-        for (int i = 0; i < 3; ++i) n[i] = 0.0;
-        n[ax] = d[ax] > 0.0 ? -1.0 : 1.0;
-    }
+    int aux;
+    double n[3];
+    double t = prim_ray(m, id, o, d, &aux);
+    if (!(t > 0.0) || t * fac >= clampv) return;
+    if (!prim_normal(m, id, o, d, t, aux, n)) return;
     double nd = dot3(n, d);
     double gt = g * fac;
     for (int i = 0; i < 3; ++i) {
@@ -1082,16 +1380,15 @@ static void ray_vjp(const double *o, const double *d, const double *sph, int ns,
 static void render_vjp(const ctx_t *x, int env, const double *s, const int32_t *hc,
                        const int32_t *hl, const double *gdep, const double *glid, double *gs)
 {
-    const double *sph, *box;
-    int ns, nb;
-    map_of(x, env, &sph, &ns, &box, &nb);
+    map_t mp;
+    map_of(x, env, &mp);
     double o[3], R[9], go[3] = {0, 0, 0}, gR[9] = {0};
     oc_pose(x->c, s, o, R);
     for (int r = 0; gdep && r < x->Rc; ++r) {
         const double *db = x->cam_dir + 3 * r;
         double d[3], gd[3] = {0, 0, 0};
         for (int i = 0; i < 3; ++i) d[i] = R[3 * i] * db[0] + R[3 * i + 1] * db[1] + R[3 * i + 2] * db[2];
-        ray_vjp(o, d, sph, ns, box, hc[r], gdep[r], x->cam_fac[r], x->c->cam_range, go, gd);
+        ray_vjp(o, d, &mp, hc[r], gdep[r], x->cam_fac[r], x->c->cam_range, go, gd);
         for (int i = 0; i < 3; ++i)
             for (int j = 0; j < 3; ++j) gR[3 * i + j] += gd[i] * db[j];
     }
@@ -1099,11 +1396,10 @@ static void render_vjp(const ctx_t *x, int env, const double *s, const int32_t *
         const double *db = x->lid_dir + 3 * r;
         double d[3], gd[3] = {0, 0, 0};
         for (int i = 0; i < 3; ++i) d[i] = R[3 * i] * db[0] + R[3 * i + 1] * db[1] + R[3 * i + 2] * db[2];
-        ray_vjp(o, d, sph, ns, box, hl[r], glid[r], 1.0, x->c->lid_range, go, gd);
+        ray_vjp(o, d, &mp, hl[r], glid[r], 1.0, x->c->lid_range, go, gd);
         for (int i = 0; i < 3; ++i)
             for (int j = 0; j < 3; ++j) gR[3 * i + j] += gd[i] * db[j];
     }
-    (void)nb;
     pose_vjp(x->c, s, go, gR, gs);
 }
 
@@ -1127,9 +1423,8 @@ int oc_backward(const oc_config *c, const oc_scene *sc, const double *act, const
 #pragma omp parallel for schedule(dynamic, 1) num_threads(nt)
 #endif
     for (int env = 0; env < N; ++env) {
-        const double *sph, *box;
-        int ns, nb;
-        map_of(&x, env, &sph, &ns, &box, &nb);
+        map_t mp;
+        map_of(&x, env, &mp);
         int i0 = env * M;
         double *gs = calloc((size_t)M * D, sizeof(double));
         double *gpre = calloc((size_t)M * D, sizeof(double));
@@ -1165,11 +1460,11 @@ int oc_backward(const oc_config *c, const oc_scene *sc, const double *act, const
                 }
                 if (c->w_obs != 0.0) {
                     double gap;
-                    double sd = sdf_min(p, sph, ns, box, nb, &id, &gap);
+                    double sd = sdf_min(p, &mp, &id, &gap);
                     double ob = sd < OC_INF ? relu(c->d_safe - sd) : 0.0;
                     if (ob > 0.0) {
                         double gsd[3];
-                        sdf_grad(p, sph, ns, box, id, gsd);
+                        sdf_grad(p, &mp, id, gsd);
                         for (int k = 0; k < 3; ++k) gp[k] += gr * 2.0 * c->w_obs * ob * gsd[k];
                     }
                 }

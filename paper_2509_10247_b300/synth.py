@@ -13,6 +13,9 @@ Every array is drawn from ``numpy.random.default_rng(seed)`` in one fixed order:
   4. per map: sphere centres, sphere radii, box centres, box half-extents
   5. reset-pool positions         [P, N*M, 3]
   6. per-env drag and latency factors (only when ranges are given)
+  7. per map with cylinders or gates: cylinder centres (xy), radii, centre
+     heights and half-heights, then gate positions, yaw jitters and
+     half-widths (only for maps whose counts name them)
 All floating-point values are rounded to float32 once, so the FP32 device path
 and the FP64 oracle start from bit-identical numbers.
 
@@ -53,11 +56,17 @@ _BASE = dict(
     d_agent=0.4, success_radius=0.5, r_quad=0.2,
     bound_lo=(-INF, -INF, -INF), bound_hi=(INF, INF, INF),
     terminate=0, pool_size=4, ckpt_every=16,
-    # scene recipe: map_counts is a list of (n_spheres, n_boxes) per map;
-    # n_maps None means one map per environment with map_counts[0]
+    # scene recipe: map_counts is a list of (n_spheres, n_boxes) or
+    # (n_spheres, n_boxes, n_cylinders, n_gates) per map; n_maps None means
+    # one map per environment with map_counts[0]
     n_maps=None, map_counts=[(10, 0)],
     obst_lo=(-8.0, -8.0, -8.0), obst_hi=(8.0, 8.0, 8.0),
     sph_radius=(0.3, 1.0), box_half=(0.2, 1.5),
+    cyl_radius=(0.2, 0.8), cyl_half_height=(0.5, 3.0),
+    # racing course: gates on a circle of race_radius around the middle of
+    # the obstacle box, each jittered by race_jitter, facing along the loop
+    # (counter-clockwise); opening half-width, border width, half-depth
+    race_radius=6.0, race_jitter=1.0, gate_half=(0.6, 1.0), gate_border=0.15, gate_depth=0.1,
     init_lo=(-5.0, -5.0, -5.0), init_hi=(5.0, 5.0, 5.0), formation_radius=1.0,
     drag_range=None, lam_range=None,
 )
@@ -124,8 +133,14 @@ def n_maps_of(p):
 
 
 def counts_of_map(p, m):
-    mc = p["map_counts"]
-    return mc[m % len(mc)]
+    """(spheres, boxes) of map m; see counts4_of_map for all four kinds."""
+    return tuple(counts4_of_map(p, m)[:2])
+
+
+def counts4_of_map(p, m):
+    """(spheres, boxes, cylinders, gates) of map m."""
+    mc = p["map_counts"][m % len(p["map_counts"])]
+    return tuple(mc) + (0,) * (4 - len(mc))
 
 
 def _f32(x):
@@ -137,7 +152,9 @@ def make_inputs(p, seed=0, actions=True):
     and int32 index arrays.  Keys: s0 [NM,D], targets [NM,3], actions [T,NM,A],
     spheres [Ks,4] (cx,cy,cz,r), sph_off [n_maps+1], boxes [Kb,6]
     (min xyz, max xyz), box_off [n_maps+1], env_map [N], pool [P,NM,D],
-    drag_env [N] or None, lam_env [N] or None."""
+    drag_env [N] or None, lam_env [N] or None; when a map has cylinders or
+    gates also cylinders [Kc,5] (cx,cy,r,zmin,zmax), cyl_off, gates [Kg,7]
+    (cx,cy,cz,yaw,w,b,hd), gate_off."""
     rng = np.random.default_rng(seed)
     N, M, T = p["n_env"], p["n_agent"], p["horizon"]
     NM = N * M
@@ -161,7 +178,7 @@ def make_inputs(p, seed=0, actions=True):
     olo, ohi = np.array(p["obst_lo"]), np.array(p["obst_hi"])
     sph, box, so, bo = [], [], [0], [0]
     for m in range(nm):
-        ns, nb = counts_of_map(p, m)
+        ns, nb = counts4_of_map(p, m)[:2]
         c = rng.uniform(olo, ohi, size=(ns, 3))
         r = rng.uniform(p["sph_radius"][0], p["sph_radius"][1], size=(ns, 1))
         bc = rng.uniform(olo, ohi, size=(nb, 3))
@@ -183,6 +200,29 @@ def make_inputs(p, seed=0, actions=True):
     if p.get("lam_range") is not None:
         lam_env = rng.uniform(*p["lam_range"], size=N)
 
+    # 7. cylinders and racing gates
+    cyl, gat, co, go = [], [], [0], [0]
+    for m in range(nm):
+        _, _, nc, ng = counts4_of_map(p, m)
+        if nc:
+            cxy = rng.uniform(olo[:2], ohi[:2], size=(nc, 2))
+            cr = rng.uniform(p["cyl_radius"][0], p["cyl_radius"][1], size=(nc, 1))
+            cz = rng.uniform(olo[2], ohi[2], size=(nc, 1))
+            hz = rng.uniform(p["cyl_half_height"][0], p["cyl_half_height"][1], size=(nc, 1))
+            cyl.append(np.concatenate([cxy, cr, cz - hz, cz + hz], axis=1))
+        if ng:
+            mid = 0.5 * (olo + ohi)
+            ang = 2.0 * math.pi * np.arange(ng) / ng
+            ring = np.stack([np.cos(ang), np.sin(ang), np.zeros(ng)], axis=1) * p["race_radius"]
+            gc = mid + ring + rng.uniform(-1.0, 1.0, size=(ng, 3)) * p["race_jitter"]
+            yaw = ang + 0.5 * math.pi + rng.uniform(-0.3, 0.3, size=ng)
+            gw = rng.uniform(p["gate_half"][0], p["gate_half"][1], size=ng)
+            gat.append(np.stack([gc[:, 0], gc[:, 1], gc[:, 2], yaw, gw,
+                                 np.full(ng, p["gate_border"]), np.full(ng, p["gate_depth"])], axis=1))
+        co.append(co[-1] + nc)
+        go.append(go[-1] + ng)
+    any4 = co[-1] > 0 or go[-1] > 0
+
     s0 = _rest_state(p["model"], pos0)
     pool = np.stack([_rest_state(p["model"], pool_pos[k]) for k in range(P)], axis=0)
     out = dict(
@@ -193,6 +233,11 @@ def make_inputs(p, seed=0, actions=True):
         drag_env=None if drag_env is None else _f32(drag_env),
         lam_env=None if lam_env is None else _f32(lam_env),
     )
+    if any4:
+        out.update(cylinders=_f32(np.concatenate(cyl, axis=0) if cyl else np.zeros((0, 5))),
+                   cyl_off=np.array(co, dtype=np.int32),
+                   gates=_f32(np.concatenate(gat, axis=0) if gat else np.zeros((0, 7))),
+                   gate_off=np.array(go, dtype=np.int32))
     return out
 
 

@@ -116,3 +116,31 @@ def test_adjoint_with_resets():
         _fd_check(p, s0, seed=seed)
         return
     pytest.fail("no screened instance with a reset")
+
+
+def test_adjoint_cylinders_and_gates():
+    # depth and LiDAR hits on cylinder sides / caps and gate bars, and the
+    # obstacle reward through their signed distances
+    p = synth.params(model="rigid", n_env=2, horizon=5, dt=0.005, cam=(8, 6, 90.0, 12.0),
+                     lidar=(3, 24, -20.0, 20.0, 12.0), map_counts=[(1, 1, 4, 4)],
+                     obst_lo=(-6, -6, -2), obst_hi=(6, 6, 2), init_lo=(-1, -1, -1),
+                     init_hi=(1, 1, 1), race_radius=4.0, gate_half=(0.8, 1.2), gate_border=0.4,
+                     pos_sq=0, w_obs=5.0, d_safe=6.0)
+    for seed in range(30, 90):
+        inp = synth.make_inputs(p, seed=seed)
+        o = oracle.Oracle(p, inp)
+        s0 = inp["s0"].copy()
+        q = np.array([0.97, 0.05, -0.1, 0.2])
+        s0[:, 3:7] = q / np.linalg.norm(q)
+        s0[:, 7:10] = [0.5, -0.3, 0.2]
+        rec = o.rollout(s0, inp["actions"])
+        if (rec["amb_cam"] & 3).any() or (rec["amb_lid"] & 3).any() or (rec["amb_step"] != 0).any():
+            continue
+        hits = np.concatenate([rec["hit_cam"].ravel(), rec["hit_lid"].ravel()])
+        if (hits >= 2).sum() < 10 or ((hits >= 2) & (hits < 6)).sum() < 3 or (hits >= 6).sum() < 3:
+            continue
+        if not ((rec["sdf_id"] >= 2).any()):
+            continue
+        _fd_check(p, s0, seed=seed, min_depth_hits=5)
+        return
+    pytest.fail("no screened instance hitting cylinders and gates")
