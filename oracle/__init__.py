@@ -49,7 +49,13 @@ class OcConfig(C.Structure):
         ("w_agent", _d), ("d_agent", _d), ("success_radius", _d), ("r_quad", _d),
         ("bound_lo", _d * 3), ("bound_hi", _d * 3),
         ("terminate", _i), ("pool_size", _i),
+        ("task", _i), ("imu_noise", _d * 2), ("imu_walk", _d * 2),
     ]
+
+
+class OcExtra(C.Structure):
+    _fields_ = [("gate_k", _pi), ("gate_tape", _pi), ("imu", _pd), ("imu_noise", _pd),
+                ("imu_bias", _pd)]
 
 
 class OcScene(C.Structure):
@@ -76,6 +82,8 @@ def build(force=False):
 # dynamics models: continuous point mass (Eq. 3), rigid body (Eq. 1), discrete
 # point mass (Eq. 4), simplified quadrotor (Eq. 2)
 MODELS = {"pm": 0, "rigid": 1, "pm_disc": 2, "simple": 3}
+# flight tasks (Sec. III-C): reaching / avoidance (targets), racing (gates)
+TASKS = {"reach": 0, "racing": 1}
 STATE_DIM = {"pm": 12, "rigid": 13, "pm_disc": 12, "simple": 15}
 ACTION_DIM = {"pm": 3, "rigid": 4, "pm_disc": 3, "simple": 4}
 
@@ -148,6 +156,10 @@ def make_config(p):
     c.w_agent, c.d_agent = p["w_agent"], p["d_agent"]
     c.success_radius, c.r_quad = p["success_radius"], p["r_quad"]
     c.terminate, c.pool_size = int(p["terminate"]), p["pool_size"]
+    c.task = TASKS[p.get("task", "reach")]
+    for k in range(2):
+        c.imu_noise[k] = p.get("imu_noise", (0.0, 0.0))[k]
+        c.imu_walk[k] = p.get("imu_walk", (0.0, 0.0))[k]
     return c
 
 
@@ -177,6 +189,8 @@ class Oracle:
             drag_env=_c64(inp.get("drag_env")), lam_env=_c64(inp.get("lam_env")),
         )
         k = self._keep
+        if p.get("task", "reach") == "racing":
+            assert k["gates"] is not None and (np.diff(k["gate_off"]) > 0).all(), "racing needs gates"
         self.scene = OcScene(_p(k["spheres"]), _p(k["sph_off"], _pi), _p(k["boxes"]),
                              _p(k["box_off"], _pi), _p(k["cylinders"]), _p(k["cyl_off"], _pi),
                              _p(k["gates"]), _p(k["gate_off"], _pi), _p(k["env_map"], _pi),
@@ -190,15 +204,24 @@ class Oracle:
         o.T = T
         return o
 
-    def rollout(self, s0, actions, pool_k=None, n_threads=0):
+    def rollout(self, s0, actions, pool_k=None, n_threads=0, gate_k=None, imu_noise=None,
+                imu_bias=None):
         """Run T steps from s0 [NM, D] with actions [T, NM, A].  Returns a dict:
         states [T+1,NM,D], spre [T,NM,D], r_ctrl, r_goal, done [T,NM],
         depth/hit_cam/amb_cam [T,NM,Rc], lidar/hit_lid/amb_lid [T,NM,Rl],
-        amb_step, sdf_id [T,NM], pool_k [N] (advanced)."""
+        amb_step, sdf_id [T,NM], pool_k [N] (advanced), imu [T,NM,6],
+        gate_tape [T,NM] and gate_k [NM] (racing, advanced from gate_k, default
+        0), imu_bias [NM,6] (advanced when imu_noise [T,NM,12] is given)."""
         T, NM, D = self.T, self.NM, self.D
         s0 = _c64(s0).reshape(NM, D)
         act = _c64(actions).reshape(T, NM, self.A)
         pk = np.zeros(self.N, np.int32) if pool_k is None else np.array(pool_k, np.int32)
+        gk = np.zeros(NM, np.int32) if gate_k is None else np.array(gate_k, np.int32)
+        gt = np.zeros((T, NM), np.int32)
+        imu = np.zeros((T, NM, 6))
+        nz = None if imu_noise is None else _c64(imu_noise).reshape(T, NM, 12)
+        bias = np.zeros((NM, 6)) if imu_bias is None else np.array(imu_bias, np.float64).reshape(NM, 6)
+        ex = OcExtra(_p(gk, _pi), _p(gt, _pi), _p(imu), _p(nz), _p(bias))
         out = dict(
             states=np.zeros((T + 1, NM, D)), spre=np.zeros((T, NM, D)),
             r_ctrl=np.zeros((T, NM)), r_goal=np.zeros((T, NM), np.int8),
@@ -214,12 +237,13 @@ class Oracle:
                          _p(o["done"], _pu8), _p(o["depth"]), _p(o["lidar"]),
                          _p(o["hit_cam"], _pi), _p(o["hit_lid"], _pi), _p(o["amb_cam"], _pu8),
                          _p(o["amb_lid"], _pu8), _p(o["amb_step"], _pu8), _p(o["sdf_id"], _pi),
-                         C.c_int(n_threads))
+                         C.byref(ex), C.c_int(n_threads))
         out["pool_k"] = pk
         out["actions"] = act
+        out.update(gate_k=gk, gate_tape=gt, imu=imu, imu_bias=bias)
         return out
 
-    def backward(self, rec, g_r, g_depth=None, g_lidar=None, g_sT=None, n_threads=0):
+    def backward(self, rec, g_r, g_depth=None, g_lidar=None, g_sT=None, n_threads=0, g_imu=None):
         """Adjoint of a recorded rollout.  Returns (g_a [T,NM,A], g_s0 [NM,D])."""
         T, NM, D, A = self.T, self.NM, self.D, self.A
         g_a = np.zeros((T, NM, A))
@@ -228,20 +252,27 @@ class Oracle:
         gd = None if (g_depth is None or self.Rc == 0) else _c64(g_depth).reshape(T, NM, self.Rc)
         gl = None if (g_lidar is None or self.Rl == 0) else _c64(g_lidar).reshape(T, NM, self.Rl)
         gs = None if g_sT is None else _c64(g_sT).reshape(NM, D)
+        gi = None if g_imu is None else _c64(g_imu).reshape(T, NM, 6)
         lib().oc_backward(C.byref(self.cfg), C.byref(self.scene), _p(rec["actions"]),
                           _p(rec["states"]), _p(rec["spre"]), _p(rec["done"], _pu8),
                           _p(rec["hit_cam"], _pi), _p(rec["hit_lid"], _pi), _p(gr), _p(gd),
-                          _p(gl), _p(gs), _p(g_a), _p(g_s0), C.c_int(n_threads))
+                          _p(gl), _p(gs), _p(gi), _p(rec["gate_tape"], _pi), _p(g_a), _p(g_s0),
+                          C.c_int(n_threads))
         return g_a, g_s0
 
-    def loss(self, s0, actions, g_r, g_depth=None, g_lidar=None, g_sT=None):
-        """L = <g_r, r_ctrl> + <g_depth, depth> + <g_lidar, lidar> + <g_sT, s_T>."""
+    def loss(self, s0, actions, g_r, g_depth=None, g_lidar=None, g_sT=None, g_imu=None,
+             gate_k=None, imu_noise=None, imu_bias=None):
+        """L = <g_r, r_ctrl> + <g_depth, depth> + <g_lidar, lidar> + <g_sT, s_T>
+        + <g_imu, imu>."""
         T, NM = self.T, self.NM
         gd = None if (g_depth is None or self.Rc == 0) else _c64(g_depth).reshape(T, NM, self.Rc)
         gl = None if (g_lidar is None or self.Rl == 0) else _c64(g_lidar).reshape(T, NM, self.Rl)
         gs = None if g_sT is None else _c64(g_sT).reshape(NM, self.D)
+        gi = None if g_imu is None else _c64(g_imu).reshape(T, NM, 6)
+        gk = None if gate_k is None else np.ascontiguousarray(gate_k, dtype=np.int32)
         return lib().oc_loss(C.byref(self.cfg), C.byref(self.scene), _p(_c64(s0)),
-                             _p(_c64(actions)), _p(_c64(g_r)), _p(gd), _p(gl), _p(gs))
+                             _p(_c64(actions)), _p(_c64(g_r)), _p(gd), _p(gl), _p(gs), _p(gi),
+                             _p(gk, _pi), _p(_c64(imu_noise)), _p(_c64(imu_bias)))
 
     def render(self, s):
         """Sensor outputs of states s [NM, D]: (depth, lidar, hit_cam, hit_lid, amb_cam, amb_lid)."""

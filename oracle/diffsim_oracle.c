@@ -84,6 +84,13 @@ typedef struct {
     double w_pos, w_obs, d_safe, w_act, w_agent, d_agent, success_radius, r_quad;
     double bound_lo[3], bound_hi[3];
     int32_t terminate, pool_size;
+    /* task 0: reach targets / avoid obstacles; 1: racing through the map's
+     * gates in order (Sec. III-C), progress reward as in the design notes */
+    int32_t task;
+    /* IMU noise (Sec. III-B): white-noise standard deviation of the specific
+     * force (m/s^2) and angular rate (rad/s) samples, and the standard
+     * deviations per sqrt(s) of their bias random walks */
+    double imu_noise[2], imu_walk[2];
 } oc_config;
 
 typedef struct {
@@ -102,6 +109,15 @@ typedef struct {
     const double *drag_env; /* [N] or NULL */
     const double *lam_env;  /* [N] or NULL */
 } oc_scene;
+
+/* Per-rollout task and IMU state, any pointer NULL when unused. */
+typedef struct {
+    int32_t *gate_k;         /* [NM] racing: each agent's next gate, read and advanced */
+    int32_t *gate_tape;      /* [T][NM] out: the gate each agent targets during step t */
+    double *imu;             /* [T][NM][6] out: specific force, angular rate (body frame) */
+    const double *imu_noise; /* [T][NM][12] standard normal samples: 6 white, 6 bias steps */
+    double *imu_bias;        /* [NM][6] bias, read and advanced (with imu_noise) */
+} oc_extra;
 
 /* ------------------------------------------------------------------ utils */
 int oc_state_dim(int model) { return model == OC_RIGID ? 13 : (model == OC_SIMPLE ? 15 : 12); }
@@ -982,6 +998,85 @@ int oc_render(const oc_config *c, const oc_scene *sc, const double *s, double *d
     return 0;
 }
 
+/* ------------------------------------------------------------------ IMU */
+
+/* IMU readout of one agent after a step (Sec. III-B), noise-free: the
+ * specific force f = R^T (v' - g) of the model's translational dynamics and
+ * the body angular rate, both in the body frame of the new state s1 (before
+ * any reset), with the step's action a held over the step.
+ *   rigid (Eq. 1):      f = (T/m) e3 - D R^T v,   omega = the state's omega
+ *   point mass (Eq. 3): f = R^T (a - d v)          (a: the lagged thrust)
+ *   discrete (Eq. 4):   f = R^T u                  (u: the command in force)
+ *   simplified (Eq. 2): f = c e3,                  omega = the commanded rates
+ * The point-mass attitude has no rate state, so its angular rate is that of
+ * the attitude change over the step, vee(A - A^T) / (2 dt), A = R0^T R1, with
+ * R0 the attitude of s0, the state the step started from. */
+static void imu_eval(const oc_config *c, double drag, const double *s0, const double *a,
+                     const double *s1, double *out)
+{
+    double o[3], R1[9];
+    oc_pose(c, s1, o, R1);
+    if (c->model == OC_RIGID) {
+        const double *v = s1 + 7, *w = s1 + 10;
+        double T = c->mass * c->gravity * (1.0 + clamp1(a[0]));
+        for (int j = 0; j < 3; ++j) {
+            double vb = R1[j] * v[0] + R1[3 + j] * v[1] + R1[6 + j] * v[2];
+            out[j] = (j == 2 ? T / c->mass : 0.0) - c->drag_body[j] * vb;
+            out[3 + j] = w[j];
+        }
+        return;
+    }
+    if (c->model == OC_SIMPLE) {
+        for (int j = 0; j < 3; ++j) {
+            out[j] = j == 2 ? c->gravity * (1.0 + clamp1(a[0])) : 0.0;
+            out[3 + j] = c->rate_scale[j] * clamp1(a[1 + j]);
+        }
+        return;
+    }
+    double acc[3], R0[9], A[9];
+    for (int i = 0; i < 3; ++i)
+        acc[i] = c->model == OC_PMD ? s1[6 + i] : s1[6 + i] - drag * s1[3 + i];
+    for (int j = 0; j < 3; ++j) out[j] = R1[j] * acc[0] + R1[3 + j] * acc[1] + R1[6 + j] * acc[2];
+    oc_pose(c, s0, o, R0);
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j)
+            A[3 * i + j] = R0[i] * R1[j] + R0[3 + i] * R1[3 + j] + R0[6 + i] * R1[6 + j];
+    out[3] = (A[7] - A[5]) / (2.0 * c->dt);
+    out[4] = (A[2] - A[6]) / (2.0 * c->dt);
+    out[5] = (A[3] - A[1]) / (2.0 * c->dt);
+}
+
+/* IMU after a reset: the new state read as held at rest (f = -R^T g, the
+ * rigid body's rate state, else no rate); carries no cotangent. */
+static void imu_reset(const oc_config *c, const double *s, double *out)
+{
+    double o[3], R[9];
+    oc_pose(c, s, o, R);
+    for (int j = 0; j < 3; ++j) {
+        out[j] = R[6 + j] * c->gravity;
+        out[3 + j] = c->model == OC_RIGID ? s[10 + j] : 0.0;
+    }
+}
+
+/* ---------------------------------------------------------------- racing */
+
+/* Local normal coordinate u_n of point x and, at the crossing of the gate's
+ * centre plane on the segment x0 -> x1, whether it lies inside the opening.
+ * A gate is passed when u_n goes from negative to non-negative along the
+ * step (travel along the normal) and the crossing point is in the opening. */
+static int gate_passed(const double *g, const double *x0, const double *x1, int *amb)
+{
+    double u0[3], u1[3];
+    gate_local(g, x0, 0, u0);
+    gate_local(g, x1, 0, u1);
+    if (fabs(u0[0]) < AMB_STEP || fabs(u1[0]) < AMB_STEP) *amb |= 1;
+    if (!(u0[0] < 0.0 && u1[0] >= 0.0)) return 0;
+    double f = -u0[0] / (u1[0] - u0[0]);
+    double ul = u0[1] + f * (u1[1] - u0[1]), uz = u0[2] + f * (u1[2] - u0[2]);
+    if (fabs(fabs(ul) - g[4]) < AMB_STEP || fabs(fabs(uz) - g[4]) < AMB_STEP) *amb |= 1;
+    return fabs(ul) < g[4] && fabs(uz) < g[4];
+}
+
 /* One environment step for all agents of env (Sec. III-C, III-D):
  * dynamics -> collision and rewards on the new state -> termination ->
  * reset of the whole environment from the pool -> sensor rendering of the
@@ -989,12 +1084,17 @@ int oc_render(const oc_config *c, const oc_scene *sc, const double *s, double *d
  * outside [bound_lo, bound_hi], or another agent of the env closer than
  * d_agent.  R_ctrl = -w_pos |e|^(1 or 2) - w_obs relu(d_safe - sdf)^2
  *                    - w_act |action|^2 - w_agent sum_j relu(d_agent - d_ij)^2,
- * R_goal = -1 on collision, +1 within success_radius of the target, else 0. */
+ * R_goal = -1 on collision, +1 within success_radius of the target, else 0.
+ * Racing (task 1): each agent targets gate k of the map's ordered gates;
+ * the position term becomes the progress w_pos (|p_t - g_k| - |p_{t+1} - g_k|)
+ * towards that gate's centre, R_goal = +1 when the step passes the gate
+ * (then k advances, cyclically), -1 on collision; a reset restarts at gate 0.
+ * The IMU (when ex->imu is set) reads the new state after a possible reset. */
 static void env_step(const ctx_t *x, int env, int t, const double *s_t, const double *act_t,
                      int32_t *pool_k, double *s_next, double *spre, double *r_ctrl,
                      int8_t *r_goal, uint8_t *done, double *depth, double *lidar,
                      int32_t *hc, int32_t *hl, uint8_t *ac, uint8_t *al, uint8_t *amb_step,
-                     int32_t *sdf_id)
+                     int32_t *sdf_id, const oc_extra *ex)
 {
     const oc_config *c = x->c;
     int M = c->n_agent, D = x->D, A = x->A;
@@ -1030,20 +1130,36 @@ static void env_step(const ctx_t *x, int env, int t, const double *s_t, const do
             if (fabs(dij - c->d_agent) < AMB_STEP) flags |= 1;
             pair += relu(c->d_agent - dij) * relu(c->d_agent - dij);
         }
-        const double *tg = x->sc->targets + 3 * (size_t)i;
-        double e[3] = {p[0] - tg[0], p[1] - tg[1], p[2] - tg[2]};
-        double ne = norm3(e);
-        double pos = c->pos_sq ? ne * ne : ne;
         double ob = (c->w_obs != 0.0 && sd < OC_INF) ? relu(c->d_safe - sd) : 0.0;
         double aa = 0.0;
         for (int k = 0; k < A; ++k) aa += a[k] * a[k];
-        r_ctrl[i] = -c->w_pos * pos - c->w_obs * ob * ob - c->w_act * aa - c->w_agent * pair;
-        r_goal[i] = (int8_t)(col ? -1 : (ne < c->success_radius ? 1 : 0));
-        if (fabs(ne - c->success_radius) < AMB_STEP) flags |= 1;
+        double ne = 1.0;
+        if (c->task == 1) {
+            const int gk = ex->gate_k[i];
+            const double *g = mp.gate + 7 * gk;
+            const double *p0 = s_t + (size_t)i * D;
+            double e0[3] = {p0[0] - g[0], p0[1] - g[1], p0[2] - g[2]};
+            double e1[3] = {p[0] - g[0], p[1] - g[1], p[2] - g[2]};
+            ne = norm3(e1);
+            if (ex->gate_tape) ex->gate_tape[(size_t)t * x->NM + i] = gk;
+            int passed = gate_passed(g, p0, p, &flags);
+            r_ctrl[i] = c->w_pos * (norm3(e0) - ne) - c->w_obs * ob * ob - c->w_act * aa - c->w_agent * pair;
+            r_goal[i] = (int8_t)(col ? -1 : (passed ? 1 : 0));
+            if (passed) ex->gate_k[i] = (gk + 1) % mp.ng;
+            if (norm3(e0) < 1e-6) flags |= 2;
+        } else {
+            const double *tg = x->sc->targets + 3 * (size_t)i;
+            double e[3] = {p[0] - tg[0], p[1] - tg[1], p[2] - tg[2]};
+            ne = norm3(e);
+            double pos = c->pos_sq ? ne * ne : ne;
+            r_ctrl[i] = -c->w_pos * pos - c->w_obs * ob * ob - c->w_act * aa - c->w_agent * pair;
+            r_goal[i] = (int8_t)(col ? -1 : (ne < c->success_radius ? 1 : 0));
+            if (fabs(ne - c->success_radius) < AMB_STEP) flags |= 1;
+        }
         /* gradient kinks: arg-min tie of an active obstacle term, norm at 0,
          * action clip boundary, box SDF on its medial axis */
         if (ob > 0.0 && gap < AMB_STEP) flags |= 2;
-        if (!c->pos_sq && ne < 1e-6) flags |= 2;
+        if ((!c->pos_sq || c->task == 1) && ne < 1e-6) flags |= 2;
         for (int k = 0; k < A; ++k)
             if (fabs(fabs(a[k]) - 1.0) < 1e-9) flags |= 2;
         amb_step[i] = (uint8_t)flags;
@@ -1062,6 +1178,27 @@ static void env_step(const ctx_t *x, int env, int t, const double *s_t, const do
         }
     }
     if (dn) pool_k[env] += 1;
+    if (dn && c->task == 1)
+        for (int m = 0; m < M; ++m) ex->gate_k[i0 + m] = 0;
+    if (ex && ex->imu) {
+        double drag = x->sc->drag_env ? x->sc->drag_env[env] : c->drag;
+        for (int m = 0; m < M; ++m) {
+            int i = i0 + m;
+            size_t o6 = ((size_t)t * x->NM + i) * 6;
+            double *out = ex->imu + o6;
+            if (dn) imu_reset(c, s_next + (size_t)i * D, out);
+            else imu_eval(c, drag, s_t + (size_t)i * D, act_t + (size_t)i * A, spre + (size_t)i * D, out);
+            if (ex->imu_noise) {
+                const double *z = ex->imu_noise + 2 * o6;
+                double *b = ex->imu_bias + (size_t)i * 6;
+                if (dn) memset(b, 0, 6 * sizeof(double));
+                for (int k = 0; k < 6; ++k) {
+                    out[k] += b[k] + c->imu_noise[k / 3] * z[k];
+                    b[k] += c->imu_walk[k / 3] * sqrt(c->dt) * z[6 + k];
+                }
+            }
+        }
+    }
     for (int m = 0; m < M; ++m) {
         int i = i0 + m;
         double o[3], R[9];
@@ -1079,13 +1216,14 @@ static void env_step(const ctx_t *x, int env, int t, const double *s_t, const do
 /* Rollout over the horizon.  states [T+1][NM][D] receives s_0..s_T (after
  * resets), spre [T][NM][D] the states before reset.  pool_k [N] is the reset
  * counter of each env, read and advanced.  depth/lidar and their hit ids and
- * flags are [T][NM][R]; output t is the observation of s_{t+1}.  n_threads
- * parallelises over environments only. */
+ * flags are [T][NM][R]; output t is the observation of s_{t+1}.  ex holds the
+ * racing and IMU state (NULL: neither; racing requires ex->gate_k).
+ * n_threads parallelises over environments only. */
 int oc_rollout(const oc_config *c, const oc_scene *sc, const double *s0, int32_t *pool_k,
                const double *act, double *states, double *spre, double *r_ctrl, int8_t *r_goal,
                uint8_t *done, double *depth, double *lidar, int32_t *hit_cam, int32_t *hit_lid,
                uint8_t *amb_cam, uint8_t *amb_lid, uint8_t *amb_step, int32_t *sdf_id,
-               int n_threads)
+               const oc_extra *ex, int n_threads)
 {
     ctx_t x;
     ctx_init(&x, c, sc);
@@ -1102,7 +1240,7 @@ int oc_rollout(const oc_config *c, const oc_scene *sc, const double *s0, int32_t
                      states + (sT + NM) * D, spre + sT * D, r_ctrl + sT, r_goal + sT, done + sT,
                      depth ? depth + sT * x.Rc : NULL, lidar ? lidar + sT * x.Rl : NULL,
                      hit_cam + sT * x.Rc, hit_lid + sT * x.Rl, amb_cam + sT * x.Rc,
-                     amb_lid + sT * x.Rl, amb_step + sT, sdf_id + sT);
+                     amb_lid + sT * x.Rl, amb_step + sT, sdf_id + sT, ex);
         }
     }
     (void)M;
@@ -1354,6 +1492,60 @@ static void pose_vjp(const oc_config *c, const double *s, const double *go, cons
     }
 }
 
+/* VJP of imu_eval: the cotangent g [6] of the readout into gs0 (the state
+ * the step started from), gs1 (the new state before reset) and ga (the raw
+ * action). */
+static void imu_vjp(const oc_config *c, double drag, const double *s0, const double *a, const double *s1,
+                    const double *g, double *gs0, double *gs1, double *ga)
+{
+    double o[3], R1[9], gR1[9] = {0}, zero[3] = {0.0, 0.0, 0.0};
+    oc_pose(c, s1, o, R1);
+    if (c->model == OC_RIGID) {
+        /* f_j = g (1 + clip(a0)) [j = z] - D_j sum_i R_ij v_i */
+        const double *v = s1 + 7;
+        for (int j = 0; j < 3; ++j)
+            for (int i = 0; i < 3; ++i) {
+                gR1[3 * i + j] += -c->drag_body[j] * v[i] * g[j];
+                gs1[7 + i] += -c->drag_body[j] * R1[3 * i + j] * g[j];
+            }
+        ga[0] += c->gravity * dclamp1(a[0]) * g[2];
+        for (int j = 0; j < 3; ++j) gs1[10 + j] += g[3 + j];
+        pose_vjp(c, s1, zero, gR1, gs1);
+        return;
+    }
+    if (c->model == OC_SIMPLE) {
+        ga[0] += c->gravity * dclamp1(a[0]) * g[2];
+        for (int j = 0; j < 3; ++j) ga[1 + j] += c->rate_scale[j] * dclamp1(a[1 + j]) * g[3 + j];
+        return;
+    }
+    /* f_j = sum_i R1_ij acc_i, acc = a_state - d v (continuous) or u (discrete) */
+    double acc[3], gacc[3] = {0.0, 0.0, 0.0}, R0[9], gR0[9] = {0}, gA[9] = {0};
+    for (int i = 0; i < 3; ++i) acc[i] = c->model == OC_PMD ? s1[6 + i] : s1[6 + i] - drag * s1[3 + i];
+    for (int j = 0; j < 3; ++j)
+        for (int i = 0; i < 3; ++i) {
+            gR1[3 * i + j] += acc[i] * g[j];
+            gacc[i] += R1[3 * i + j] * g[j];
+        }
+    for (int i = 0; i < 3; ++i) {
+        gs1[6 + i] += gacc[i];
+        if (c->model != OC_PMD) gs1[3 + i] += -drag * gacc[i];
+    }
+    /* omega = vee(A - A^T) / (2 dt), A_ij = sum_k R0_ki R1_kj */
+    oc_pose(c, s0, o, R0);
+    double h = 1.0 / (2.0 * c->dt);
+    gA[7] += h * g[3]; gA[5] -= h * g[3];
+    gA[2] += h * g[4]; gA[6] -= h * g[4];
+    gA[3] += h * g[5]; gA[1] -= h * g[5];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j)
+            for (int k = 0; k < 3; ++k) {
+                gR0[3 * k + i] += gA[3 * i + j] * R1[3 * k + j];
+                gR1[3 * k + j] += gA[3 * i + j] * R0[3 * k + i];
+            }
+    pose_vjp(c, s1, zero, gR1, gs1);
+    pose_vjp(c, s0, zero, gR0, gs0);
+}
+
 /* VJP of one ray's output w.r.t. origin o and world direction d.  g is the
  * cotangent of the output, fac the factor from t* to the output (z-depth
  * factor or 1), clampv the output clamp.  Zero on a miss, a clamped output,
@@ -1406,13 +1598,15 @@ static void render_vjp(const ctx_t *x, int env, const double *s, const int32_t *
 /* Adjoint of the rollout (Eq. 5 applied step by step, reverse order).  Inputs
  * are the actions and the records of oc_rollout; cotangents g_r [T][NM] of
  * R_ctrl, g_depth / g_lidar [T][NM][R] (NULL = zero), g_sT [NM][D] of the
- * final state (NULL = zero).  Outputs g_a [T][NM][A] and g_s0 [NM][D].
+ * final state (NULL = zero), g_imu [T][NM][6] of the IMU readout (NULL =
+ * zero); gate_tape [T][NM] the racing record (task 1).  Outputs g_a
+ * [T][NM][A] and g_s0 [NM][D].
  * A reset replaces the state, so no cotangent crosses it. */
 int oc_backward(const oc_config *c, const oc_scene *sc, const double *act, const double *states,
                 const double *spre, const uint8_t *done, const int32_t *hit_cam,
                 const int32_t *hit_lid, const double *g_r, const double *g_depth,
-                const double *g_lidar, const double *g_sT, double *g_a, double *g_s0,
-                int n_threads)
+                const double *g_lidar, const double *g_sT, const double *g_imu,
+                const int32_t *gate_tape, double *g_a, double *g_s0, int n_threads)
 {
     ctx_t x;
     ctx_init(&x, c, sc);
@@ -1428,6 +1622,8 @@ int oc_backward(const oc_config *c, const oc_scene *sc, const double *act, const
         int i0 = env * M;
         double *gs = calloc((size_t)M * D, sizeof(double));
         double *gpre = calloc((size_t)M * D, sizeof(double));
+        double *gs0x = calloc((size_t)M * D, sizeof(double)); /* direct terms on s_t */
+        double drag = sc->drag_env ? sc->drag_env[env] : c->drag;
         if (g_sT) memcpy(gs, g_sT + (size_t)i0 * D, sizeof(double) * M * D);
         for (int t = T - 1; t >= 0; --t) {
             size_t sT = (size_t)t * NM;
@@ -1451,13 +1647,29 @@ int oc_backward(const oc_config *c, const oc_scene *sc, const double *act, const
                 const double *a = act + (sT + i) * A;
                 double *gp = gpre + (size_t)m * D;
                 double *gaa = g_a + (sT + i) * A;
-                const double *tg = sc->targets + 3 * (size_t)i;
-                double e[3] = {p[0] - tg[0], p[1] - tg[1], p[2] - tg[2]};
-                double ne = norm3(e);
-                for (int k = 0; k < 3; ++k) {
-                    double dpos = c->pos_sq ? 2.0 * e[k] : (ne > 0.0 ? e[k] / ne : 0.0);
-                    gp[k] += -gr * c->w_pos * dpos;
+                if (c->task == 1) {
+                    /* progress w_pos (|p_t - g| - |p_{t+1} - g|) */
+                    const double *g = mp.gate + 7 * gate_tape[sT + i];
+                    const double *p0 = states + (sT + i) * D;
+                    double e0[3] = {p0[0] - g[0], p0[1] - g[1], p0[2] - g[2]};
+                    double e1[3] = {p[0] - g[0], p[1] - g[1], p[2] - g[2]};
+                    double n0 = norm3(e0), n1 = norm3(e1);
+                    for (int k = 0; k < 3; ++k) {
+                        if (n0 > 0.0) gs0x[(size_t)m * D + k] += gr * c->w_pos * e0[k] / n0;
+                        if (n1 > 0.0) gp[k] += -gr * c->w_pos * e1[k] / n1;
+                    }
+                } else {
+                    const double *tg = sc->targets + 3 * (size_t)i;
+                    double e[3] = {p[0] - tg[0], p[1] - tg[1], p[2] - tg[2]};
+                    double ne = norm3(e);
+                    for (int k = 0; k < 3; ++k) {
+                        double dpos = c->pos_sq ? 2.0 * e[k] : (ne > 0.0 ? e[k] / ne : 0.0);
+                        gp[k] += -gr * c->w_pos * dpos;
+                    }
                 }
+                if (g_imu && !dn)
+                    imu_vjp(c, drag, states + (sT + i) * D, a, p, g_imu + (sT + i) * 6,
+                            gs0x + (size_t)m * D, gp, gaa);
                 if (c->w_obs != 0.0) {
                     double gap;
                     double sd = sdf_min(p, &mp, &id, &gap);
@@ -1496,15 +1708,19 @@ int oc_backward(const oc_config *c, const oc_scene *sc, const double *act, const
                 else if (c->model == OC_SIMPLE)
                     simple_step_vjp(c, s, a, gpre + (size_t)m * D, g, g_a + (sT + i) * A);
                 else {
-                    double drag = sc->drag_env ? sc->drag_env[env] : c->drag;
                     double lam = sc->lam_env ? sc->lam_env[env] : c->lam;
                     pm_step_vjp(c, drag, lam, s, a, gpre + (size_t)m * D, g, g_a + (sT + i) * A);
+                }
+                for (int k = 0; k < D; ++k) {
+                    g[k] += gs0x[(size_t)m * D + k];
+                    gs0x[(size_t)m * D + k] = 0.0;
                 }
             }
         }
         memcpy(g_s0 + (size_t)i0 * D, gs, sizeof(double) * M * D);
         free(gs);
         free(gpre);
+        free(gs0x);
     }
     ctx_free(&x);
     return 0;
@@ -1516,7 +1732,8 @@ int oc_backward(const oc_config *c, const oc_scene *sc, const double *act, const
  * Used by the finite-difference checks. */
 double oc_loss(const oc_config *c, const oc_scene *sc, const double *s0, const double *act,
                const double *g_r, const double *g_depth, const double *g_lidar,
-               const double *g_sT)
+               const double *g_sT, const double *g_imu, const int32_t *gate_k0,
+               const double *imu_noise, const double *imu_bias0)
 {
     ctx_t x;
     ctx_init(&x, c, sc);
@@ -1533,14 +1750,22 @@ double oc_loss(const oc_config *c, const oc_scene *sc, const double *s0, const d
     int32_t *hc = malloc(sizeof(int32_t) * (nc ? nc : 1)), *hl = malloc(sizeof(int32_t) * (nl ? nl : 1));
     uint8_t *ac = malloc(nc ? nc : 1), *al = malloc(nl ? nl : 1);
     int32_t *pk = calloc((size_t)N, sizeof(int32_t));
-    oc_rollout(c, sc, s0, pk, act, states, spre, r, rg, dn, dep, lid, hc, hl, ac, al, as, sid, 1);
+    int32_t *gk = calloc((size_t)NM, sizeof(int32_t));
+    double *imu = malloc(sizeof(double) * (size_t)T * NM * 6);
+    double *bias = calloc((size_t)NM * 6, sizeof(double));
+    if (gate_k0) memcpy(gk, gate_k0, sizeof(int32_t) * NM);
+    if (imu_bias0) memcpy(bias, imu_bias0, sizeof(double) * NM * 6);
+    oc_extra ex = {gk, NULL, imu, imu_noise, bias};
+    oc_rollout(c, sc, s0, pk, act, states, spre, r, rg, dn, dep, lid, hc, hl, ac, al, as, sid, &ex, 1);
     double L = 0.0;
+    if (g_imu) for (size_t k = 0; k < (size_t)T * NM * 6; ++k) L += g_imu[k] * imu[k];
     for (size_t k = 0; k < (size_t)T * NM; ++k) L += g_r[k] * r[k];
     if (g_depth) for (size_t k = 0; k < nc; ++k) L += g_depth[k] * dep[k];
     if (g_lidar) for (size_t k = 0; k < nl; ++k) L += g_lidar[k] * lid[k];
     if (g_sT) for (size_t k = 0; k < (size_t)NM * D; ++k) L += g_sT[k] * states[(size_t)T * NM * D + k];
     free(states); free(spre); free(r); free(rg); free(dn); free(as); free(sid);
     free(dep); free(lid); free(hc); free(hl); free(ac); free(al); free(pk);
+    free(gk); free(imu); free(bias);
     ctx_free(&x);
     return L;
 }

@@ -56,6 +56,12 @@ _BASE = dict(
     d_agent=0.4, success_radius=0.5, r_quad=0.2,
     bound_lo=(-INF, -INF, -INF), bound_hi=(INF, INF, INF),
     terminate=0, pool_size=4, ckpt_every=16,
+    # flight task (Sec. III-C): "reach" (targets; position control and
+    # obstacle avoidance) or "racing" (the map's gates in order)
+    task="reach",
+    # IMU noise (Sec. III-B): white-noise std of specific force / angular
+    # rate samples and the std per sqrt(s) of their bias random walks
+    imu_noise=(0.0, 0.0), imu_walk=(0.0, 0.0),
     # scene recipe: map_counts is a list of (n_spheres, n_boxes) or
     # (n_spheres, n_boxes, n_cylinders, n_gates) per map; n_maps None means
     # one map per environment with map_counts[0]
