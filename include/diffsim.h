@@ -3,10 +3,11 @@
  * environment step (DiffAero, arXiv 2509.10247), sm_103a CUDA.
  *
  * One handle simulates N environments of M agents each.  Per step it
- * integrates the point-mass (Eq. 3) or rigid-body (Eq. 1) dynamics,
- * ray-casts the depth camera and / or LiDAR against the environment's
- * spheres and axis-aligned boxes (Sec. III-B), evaluates collisions, the
- * differentiable reward R_ctrl and the sparse reward R_goal (Sec. III-C,
+ * integrates one of the four dynamics models (Eq. 1-4), ray-casts the depth
+ * camera and / or LiDAR against the environment's spheres, axis-aligned
+ * boxes, vertical cylinders and racing-gate frames (Sec. III-B), reads the
+ * IMU, evaluates collisions, the differentiable reward R_ctrl and the sparse
+ * reward R_goal of the reaching / avoidance or racing task (Sec. III-C,
  * III-D, III-E), terminates and resets environments, and renders the new
  * observation.  A rollout of T steps is two launches (the sequential physics
  * of all T steps, then every step's ray casting); its adjoint
@@ -114,8 +115,20 @@ typedef struct sim_config {
     int32_t warps_per_cta;   /* 0: auto (8); else warps per CTA, 1..8 */
     int32_t rays_per_thread; /* 0: auto; else one of 1, 2, 3, 4, 5, 6, 8 */
     int32_t ctas_per_sm;     /* 0: occupancy limit; else cap of resident CTAs per SM */
-    int32_t reserved[6];     /* must be 0 */
+    /* flight task (Sec. III-C): SIM_TASK_REACH (targets; position control and
+       obstacle avoidance) or SIM_TASK_RACING (the map's gates in order; needs
+       at least one gate in every map) */
+    int32_t task;
+    /* IMU noise (Sec. III-B), used when noise samples are given: white-noise
+       standard deviation of the specific force (m/s^2) and angular rate
+       (rad/s), and the standard deviation per sqrt(s) of their bias random
+       walks; all >= 0 */
+    float imu_noise[2], imu_walk[2];
+    int32_t reserved[1];     /* must be 0 */
 } sim_config;
+
+/* Flight tasks. */
+enum { SIM_TASK_REACH = 0, SIM_TASK_RACING = 1 };
 
 /* Library version string. */
 const char *sim_version(void);
@@ -154,6 +167,41 @@ int sim_set_scene(sim_handle *h, const float *spheres, const int32_t *sph_off,
                   const float *boxes, const int32_t *box_off, int32_t n_maps,
                   const int32_t *env_map, const float *targets);
 
+/* Scene with all four primitive kinds (HOST pointers, copied in).  Each kind
+ * has a CSR offset array [n_maps + 1]; a kind's array may be NULL with its
+ * offsets NULL (none of that kind).  Within a map, ids run over spheres,
+ * boxes, cylinders, gates in that order (at most 32767 in total), ties of
+ * the ray cast go to the lowest id.
+ *   cylinders [Kc][5] = (cx, cy, r, zmin, zmax): vertical (axis along world
+ *     z), capped; r >= 0, zmin <= zmax
+ *   gates [Kg][7] = (cx, cy, cz, yaw, w, b, hd): a square frame around an
+ *     open square of half-width w, border width b, half-depth hd along its
+ *     normal (cos yaw, sin yaw, 0); w, b, hd > 0.  In the racing task the
+ *     map's gates are the course, passed in id order along their normals.
+ * Errors as sim_set_scene; SIZE also when the racing task meets a map
+ * without gates. */
+typedef struct sim_scene {
+    int32_t n_maps;
+    const float *spheres;
+    const int32_t *sph_off;
+    const float *boxes;
+    const int32_t *box_off;
+    const float *cylinders;
+    const int32_t *cyl_off;
+    const float *gates;
+    const int32_t *gate_off;
+    const int32_t *env_map; /* [N] */
+    const float *targets;   /* [NM][3] (ignored by the racing task) */
+} sim_scene;
+
+int sim_set_scene_ex(sim_handle *h, const sim_scene *scene);
+
+/* Racing: each agent's index of the next gate [NM] (DEVICE int32), read or
+ * set.  sim_reset sets every index to 0; a reset of an environment sets its
+ * agents' indices to 0; passing the targeted gate advances it cyclically. */
+int sim_get_gate_index(const sim_handle *h, int32_t *gate_k, sim_stream_t stream);
+int sim_set_gate_index(sim_handle *h, const int32_t *gate_k, sim_stream_t stream);
+
 /* Reset pool [P][NM][D], HOST pointer, P = cfg.pool_size: on termination
  * environment e takes entry (k_e mod P) for all its agents, k_e counting
  * its resets.  Required when terminate = 1. */
@@ -188,6 +236,46 @@ int sim_step(sim_handle *h, const float *actions, float *depth, float *lidar,
 int sim_rollout(sim_handle *h, const float *actions, float *r_ctrl, int8_t *r_goal,
                 uint8_t *done, float *depth, float *lidar, sim_stream_t stream);
 
+/* Inputs and outputs of one rollout (sim_rollout_ex) or one step
+ * (sim_step_ex, T = 1), DEVICE pointers, any output NULL to skip:
+ *   actions [T][NM][A]; r_ctrl, r_goal, done [T][NM]; depth [T][NM][Rc],
+ *   lidar [T][NM][Rl] as in sim_rollout;
+ *   imu [T][NM][6]: the IMU readout of the state after each step (Sec.
+ *     III-B) in the body frame: specific force f = R^T (v' - g) of the
+ *     model's translational dynamics (rigid: (T/m) e3 - D R^T v; point mass:
+ *     R^T (a - d v); discrete: R^T u; simplified: c e3), then the angular
+ *     rate (rigid: the state's omega; simplified: the commanded rates; point
+ *     mass: the attitude change over the step, vee(A - A^T) / (2 dt),
+ *     A = R_t^T R_{t+1}); after a reset the new state read at rest
+ *     (-R^T g, the rigid rate state, else 0);
+ *   imu_noise [T][NM][12] (nullable): standard normal samples, 6 white-noise
+ *     terms added with the cfg.imu_noise deviations and 6 steps of the bias
+ *     random walk (cfg.imu_walk * sqrt(dt)); the bias starts at 0 at
+ *     sim_reset and at every reset of an environment. */
+typedef struct sim_rollout_io {
+    const float *actions;
+    float *r_ctrl;
+    int8_t *r_goal;
+    uint8_t *done;
+    float *depth, *lidar;
+    float *imu;
+    const float *imu_noise;
+} sim_rollout_io;
+
+int sim_rollout_ex(sim_handle *h, const sim_rollout_io *io, sim_stream_t stream);
+int sim_step_ex(sim_handle *h, const sim_rollout_io *io, sim_stream_t stream);
+
+/* Cotangents and gradients of the adjoint, DEVICE pointers (inputs NULL =
+ * zero): g_r [T][NM], g_depth [T][NM][Rc], g_lidar [T][NM][Rl], g_sT
+ * [NM][D], g_imu [T][NM][6] (the IMU readout; the noise is additive and
+ * passes no cotangent); outputs g_a [T][NM][A], g_s0 [NM][D] (nullable). */
+typedef struct sim_grad_io {
+    const float *g_r, *g_depth, *g_lidar, *g_sT, *g_imu;
+    float *g_a, *g_s0;
+} sim_grad_io;
+
+int sim_backward_ex(sim_handle *h, const sim_grad_io *io, sim_stream_t stream);
+
 /* Adjoint of the last sim_rollout (Eq. 5): given cotangents g_r [T][NM] of
  * r_ctrl, g_depth [T][NM][Rc], g_lidar [T][NM][Rl] and g_sT [NM][D] of the
  * final state (DEVICE; g_depth, g_lidar, g_sT may be NULL = zero), writes
@@ -198,7 +286,8 @@ int sim_rollout(sim_handle *h, const float *actions, float *r_ctrl, int8_t *r_go
 int sim_backward(sim_handle *h, const float *g_r, const float *g_depth, const float *g_lidar,
                  const float *g_sT, float *g_a, float *g_s0, sim_stream_t stream);
 
-/* Vector-Jacobian product of one step (closed-loop use): state s_t [NM][D],
+/* Vector-Jacobian product of one step (closed-loop use; the reaching task
+ * only, SIM_ERR_UNSUPPORTED for racing): state s_t [NM][D],
  * actions a_t [NM][A], done_t [NM] (the step's done output), cotangents
  * g_s_next [NM][D] (may be NULL), g_r [NM], g_depth [NM][Rc], g_lidar
  * [NM][Rl] (may be NULL); outputs g_a [NM][A], g_s [NM][D] (may be NULL).
@@ -221,7 +310,8 @@ int sim_counters(sim_handle *h, uint64_t *out, int32_t reset);
 /* Bytes of the library's static device scratch used by sim_step_static. */
 #define SIM_STATIC_SCRATCH_BYTES (256 * 1024)
 
-/* sim_step_static: one step, like sim_step, that allocates no device memory.
+/* sim_step_static: one step, like sim_step, that allocates no device memory
+ * (reaching task, spheres and boxes, no IMU: cfg.task must be SIM_TASK_REACH).
  * The paper has no counterpart; this entry point exists for callers that
  * cannot call cudaMalloc (code that must draw all device memory from a pool
  * or arena owned by someone else, or that has fixed its allocations up

@@ -36,7 +36,12 @@ SYMBOLS = ["sim_version", "sim_strerror", "sim_state_dim", "sim_action_dim", "si
            "sim_set_env_params", "sim_reset", "sim_get_state", "sim_set_state", "sim_render",
            "sim_step", "sim_rollout", "sim_backward", "sim_step_backward", "sim_last_status",
            "sim_launch_info", "sim_counters", "sim_step_static", "sim_profile", "sim_kernel_times",
-           "sim_graph_create", "sim_graph_launch", "sim_graph_kernels", "sim_graph_destroy"]
+           "sim_graph_create", "sim_graph_launch", "sim_graph_kernels", "sim_graph_destroy",
+           "sim_set_scene_ex", "sim_get_gate_index", "sim_set_gate_index", "sim_rollout_ex",
+           "sim_step_ex", "sim_backward_ex"]
+
+# flight tasks (Sec. III-C)
+TASKS = {"reach": 0, "racing": 1}
 
 KERNEL_KINDS = ("physics", "render", "render_vjp", "physics_bwd")
 
@@ -61,8 +66,25 @@ class SimConfig(C.Structure):
         ("bound_lo", _f * 3), ("bound_hi", _f * 3),
         ("terminate", _i), ("pool_size", _i),
         ("ckpt_every", _i), ("tape_hits", _i), ("cull", _i), ("warps_per_cta", _i),
-        ("rays_per_thread", _i), ("ctas_per_sm", _i), ("reserved", _i * 6),
+        ("rays_per_thread", _i), ("ctas_per_sm", _i),
+        ("task", _i), ("imu_noise", _f * 2), ("imu_walk", _f * 2), ("reserved", _i * 1),
     ]
+
+
+class SimScene(C.Structure):
+    _fields_ = [("n_maps", _i), ("spheres", _vp), ("sph_off", _vp), ("boxes", _vp), ("box_off", _vp),
+                ("cylinders", _vp), ("cyl_off", _vp), ("gates", _vp), ("gate_off", _vp),
+                ("env_map", _vp), ("targets", _vp)]
+
+
+class SimRolloutIO(C.Structure):
+    _fields_ = [("actions", _vp), ("r_ctrl", _vp), ("r_goal", _vp), ("done", _vp), ("depth", _vp),
+                ("lidar", _vp), ("imu", _vp), ("imu_noise", _vp)]
+
+
+class SimGradIO(C.Structure):
+    _fields_ = [("g_r", _vp), ("g_depth", _vp), ("g_lidar", _vp), ("g_sT", _vp), ("g_imu", _vp),
+                ("g_a", _vp), ("g_s0", _vp)]
 
 
 class SimGraphIO(C.Structure):
@@ -149,6 +171,10 @@ def make_config(p, **ex):
     c.warps_per_cta = ex.get("warps_per_cta", 0)
     c.rays_per_thread = ex.get("rays_per_thread", 0)
     c.ctas_per_sm = ex.get("ctas_per_sm", 0)
+    c.task = TASKS[p.get("task", "reach")]
+    for k in range(2):
+        c.imu_noise[k] = p.get("imu_noise", (0.0, 0.0))[k]
+        c.imu_walk[k] = p.get("imu_walk", (0.0, 0.0))[k]
     return c
 
 
@@ -192,6 +218,51 @@ def sim_set_scene(h, spheres, sph_off, boxes, box_off, env_map, targets):
     em, tg = _host(env_map, np.int32), _host(targets, np.float32)
     _ck(lib().sim_set_scene(h, _np_ptr(sp), _np_ptr(so), _np_ptr(bx), _np_ptr(bo),
                             _i(len(so) - 1), _np_ptr(em), _np_ptr(tg)), "sim_set_scene")
+
+
+def sim_set_scene_ex(h, spheres, sph_off, boxes, box_off, env_map, targets, cylinders=None, cyl_off=None,
+                     gates=None, gate_off=None):
+    keep = dict(sp=_host(spheres, np.float32).reshape(-1, 4), so=_host(sph_off, np.int32),
+                bx=_host(boxes, np.float32).reshape(-1, 6), bo=_host(box_off, np.int32),
+                em=_host(env_map, np.int32), tg=_host(targets, np.float32))
+    if cylinders is not None:
+        keep.update(cy=_host(cylinders, np.float32).reshape(-1, 5), co=_host(cyl_off, np.int32))
+    if gates is not None:
+        keep.update(gt=_host(gates, np.float32).reshape(-1, 7), go=_host(gate_off, np.int32))
+    g = lambda k: _np_ptr(keep.get(k))
+    sc = SimScene(len(keep["so"]) - 1, g("sp"), g("so"), g("bx"), g("bo"), g("cy"), g("co"), g("gt"),
+                  g("go"), g("em"), g("tg"))
+    _ck(lib().sim_set_scene_ex(h, C.byref(sc)), "sim_set_scene_ex")
+
+
+def sim_get_gate_index(h, gate_k, stream=None):
+    _ck(lib().sim_get_gate_index(h, _ptr(gate_k), _stream(stream)), "sim_get_gate_index")
+
+
+def sim_set_gate_index(h, gate_k, stream=None):
+    _ck(lib().sim_set_gate_index(h, _ptr(gate_k), _stream(stream)), "sim_set_gate_index")
+
+
+def _rollout_io(actions, r_ctrl, r_goal, done, depth, lidar, imu, imu_noise):
+    return SimRolloutIO(*[None if t is None else _ptr(t).value
+                          for t in (actions, r_ctrl, r_goal, done, depth, lidar, imu, imu_noise)])
+
+
+def sim_rollout_ex(h, actions, r_ctrl=None, r_goal=None, done=None, depth=None, lidar=None, imu=None,
+                   imu_noise=None, stream=None):
+    io = _rollout_io(actions, r_ctrl, r_goal, done, depth, lidar, imu, imu_noise)
+    _ck(lib().sim_rollout_ex(h, C.byref(io), _stream(stream)), "sim_rollout_ex")
+
+
+def sim_step_ex(h, actions, r_ctrl=None, r_goal=None, done=None, depth=None, lidar=None, imu=None,
+                imu_noise=None, stream=None):
+    io = _rollout_io(actions, r_ctrl, r_goal, done, depth, lidar, imu, imu_noise)
+    _ck(lib().sim_step_ex(h, C.byref(io), _stream(stream)), "sim_step_ex")
+
+
+def sim_backward_ex(h, g_r, g_a, g_depth=None, g_lidar=None, g_sT=None, g_imu=None, g_s0=None, stream=None):
+    io = SimGradIO(*[None if t is None else _ptr(t).value for t in (g_r, g_depth, g_lidar, g_sT, g_imu, g_a, g_s0)])
+    _ck(lib().sim_backward_ex(h, C.byref(io), _stream(stream)), "sim_backward_ex")
 
 
 def sim_set_pool(h, pool):
@@ -350,8 +421,13 @@ class Simulator:
         self.cfg = make_config(p, **ex)
         with torch.cuda.device(self.device):
             self.h = sim_create(self.cfg)
-            sim_set_scene(self.h, inp["spheres"], inp["sph_off"], inp["boxes"], inp["box_off"],
-                          inp["env_map"], inp["targets"])
+            if inp.get("cylinders") is not None or inp.get("gates") is not None:
+                sim_set_scene_ex(self.h, inp["spheres"], inp["sph_off"], inp["boxes"], inp["box_off"],
+                                 inp["env_map"], inp["targets"], inp.get("cylinders"), inp.get("cyl_off"),
+                                 inp.get("gates"), inp.get("gate_off"))
+            else:
+                sim_set_scene(self.h, inp["spheres"], inp["sph_off"], inp["boxes"], inp["box_off"],
+                              inp["env_map"], inp["targets"])
             if p["pool_size"] > 0:
                 sim_set_pool(self.h, inp["pool"])
             if inp.get("drag_env") is not None or inp.get("lam_env") is not None:
@@ -396,7 +472,7 @@ class Simulator:
         sim_step(self.h, actions.contiguous(), o["depth"], o["lidar"], o["r_ctrl"], o["r_goal"], o["done"])
         return o
 
-    def rollout(self, actions, depth=True, lidar=True, out=None):
+    def rollout(self, actions, depth=True, lidar=True, out=None, imu=False, imu_noise=None):
         T, NM = self.T, self.NM
         o = out if out is not None else dict(
             r_ctrl=self._empty(T, NM), r_goal=self._empty(T, NM, dtype=torch.int8),
@@ -404,13 +480,30 @@ class Simulator:
             depth=self._empty(T, NM, self.Rc) if (self.Rc and depth) else None,
             lidar=self._empty(T, NM, self.Rl) if (self.Rl and lidar) else None)
         self._actions = actions.contiguous()
-        sim_rollout(self.h, self._actions, o["r_ctrl"], o["r_goal"], o["done"], o["depth"], o["lidar"])
+        if imu or imu_noise is not None:
+            o["imu"] = self._empty(T, NM, 6)
+            sim_rollout_ex(self.h, self._actions, o["r_ctrl"], o["r_goal"], o["done"], o["depth"], o["lidar"],
+                           o["imu"], None if imu_noise is None else imu_noise.contiguous())
+        else:
+            sim_rollout(self.h, self._actions, o["r_ctrl"], o["r_goal"], o["done"], o["depth"], o["lidar"])
         return o
 
-    def backward(self, g_r, g_depth=None, g_lidar=None, g_sT=None, g_a=None, g_s0=None):
+    def gate_index(self):
+        out = self._empty(self.NM, dtype=torch.int32)
+        sim_get_gate_index(self.h, out)
+        return out
+
+    def set_gate_index(self, k):
+        sim_set_gate_index(self.h, k.to(device=self.device, dtype=torch.int32).contiguous())
+
+    def backward(self, g_r, g_depth=None, g_lidar=None, g_sT=None, g_a=None, g_s0=None, g_imu=None):
         T, NM = self.T, self.NM
         g_a = self._empty(T, NM, self.A) if g_a is None else g_a
         g_s0 = self._empty(NM, self.D) if g_s0 is None else g_s0
+        if g_imu is not None:
+            c = lambda t: None if t is None else t.contiguous()
+            sim_backward_ex(self.h, g_r.contiguous(), g_a, c(g_depth), c(g_lidar), c(g_sT), g_imu.contiguous(), g_s0)
+            return g_a, g_s0
         sim_backward(self.h, g_r.contiguous(), None if g_depth is None else g_depth.contiguous(),
                      None if g_lidar is None else g_lidar.contiguous(),
                      None if g_sT is None else g_sT.contiguous(), g_a, g_s0)

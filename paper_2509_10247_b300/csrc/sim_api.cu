@@ -33,11 +33,13 @@ struct sim_handle {
     bool have_scene = false, have_pool = false;
     float4* d_prims = nullptr;
     int *d_map_off = nullptr, *d_map_ns = nullptr, *d_map_nb = nullptr;
+    int *d_map_nc = nullptr, *d_map_ng = nullptr;
     int *d_env_map = nullptr, *d_order = nullptr;
     float* d_targets = nullptr;
     float* d_pool = nullptr;
     float *d_drag = nullptr, *d_lam = nullptr;
-    int ns_max = 0, nb_max = 0, n_maps = 0;
+    int ns_max = 0, nb_max = 0, nc_max = 0, ng_max = 0, n_maps = 0;
+    std::vector<int> h_map_ng, h_env_map;  // host copies (gate index checks)
     // sensors
     float4 *d_cam = nullptr, *d_lid = nullptr;
     float *d_cam_tmax = nullptr, *d_lid_tmax = nullptr;
@@ -59,6 +61,9 @@ struct sim_handle {
     uint8_t* d_done_tape = nullptr;
     int16_t* d_sdf_tape = nullptr;
     int16_t *d_tape_cam = nullptr, *d_tape_lid = nullptr;
+    int* d_gate_k = nullptr;          // [NM] racing: next gate of each agent
+    int16_t* d_gate_tape = nullptr;   // [T][NM] racing: gate targeted during each step
+    float* d_imu_bias = nullptr;      // [NM][6] IMU bias state
     float *d_poses = nullptr, *d_gposes = nullptr;  // [T][NM][12] rollout poses and their cotangents
     float *d_pose1 = nullptr, *d_gpose1 = nullptr;  // [NM][12] single-step poses and cotangents
     float* d_state2 = nullptr;                       // [NM][D] scratch state of the step adjoint
@@ -180,8 +185,12 @@ int validate(const sim_config* c) {
     }
     if (c->rays_per_thread != 0 && !ds::rpt_supported(c->rays_per_thread)) return SIM_ERR_INVALID_ARG;
     if (c->ctas_per_sm < 0) return SIM_ERR_INVALID_ARG;
-    for (int i = 0; i < 6; ++i)
-        if (c->reserved[i] != 0) return SIM_ERR_INVALID_ARG;
+    if (c->task != SIM_TASK_REACH && c->task != SIM_TASK_RACING) return SIM_ERR_INVALID_ARG;
+    for (int i = 0; i < 2; ++i)
+        if (!(c->imu_noise[i] >= 0.f) || !(c->imu_walk[i] >= 0.f) || !std::isfinite(c->imu_noise[i]) ||
+            !std::isfinite(c->imu_walk[i]))
+            return SIM_ERR_INVALID_ARG;
+    if (c->reserved[0] != 0) return SIM_ERR_INVALID_ARG;
     return SIM_OK;
 }
 
@@ -193,9 +202,10 @@ ds::Smem layout_render(const sim_handle* h, bool lists) {
     ds::Smem s{};
     size_t o = 0;
     s.prim = 0;
-    o = align16((size_t)(h->ns_max + 2 * h->nb_max) * 16);
+    const ds::LCap cap{h->ns_max, h->nb_max, h->nc_max, h->ng_max};
+    o = align16((size_t)(h->ns_max + 2 * (h->nb_max + h->nc_max + h->ng_max)) * 16);
     s.wlist = (int)o;
-    s.wstride = (int)ds::wlist_bytes(h->ns_max, h->nb_max);
+    s.wstride = (int)ds::wlist_bytes(cap);
     if (lists) o += (size_t)h->nw * s.wstride;
     s.mbar = (int)o;
     o += 16;
@@ -229,6 +239,8 @@ int grid_of(sim_handle* h, bool vjp, bool tape, const ds::Smem& sm, int* grid) {
     memset(&dummy, 0, sizeof(dummy));
     static int16_t tape_marker;  // selects the taped-adjoint kernel; never dereferenced here
     dummy.sen[0].tape = tape ? &tape_marker : nullptr;
+    dummy.nc_max = h->nc_max;  // selects the kernels with cylinders and gates
+    dummy.ng_max = h->ng_max;
     CK(ds::render_call(vjp, false, h->rpt, dummy, 0, 32 * h->nw, sm.total, nullptr, &occ));
     if (occ < 1) return SIM_ERR_UNSUPPORTED;
     if (h->cfg.ctas_per_sm) occ = std::min(occ, h->cfg.ctas_per_sm);
@@ -348,8 +360,11 @@ Args base_args(const sim_handle* h) {
     a.c.w_act = c.w_act; a.c.w_agent = c.w_agent; a.c.d_agent = c.d_agent;
     a.c.success_radius = c.success_radius; a.c.r_quad = c.r_quad;
     a.c.terminate = c.terminate; a.c.P = h->have_pool ? c.pool_size : 0;
+    a.c.task = c.task;
+    for (int i = 0; i < 2; ++i) { a.c.imu_noise[i] = c.imu_noise[i]; a.c.imu_walk[i] = c.imu_walk[i]; }
     a.N = h->N; a.M = h->M; a.NM = h->NM; a.T = h->T; a.K = h->K; a.S = h->S;
     a.ns_max = h->ns_max; a.nb_max = h->nb_max; a.cull = h->cull_mode;
+    a.nc_max = h->nc_max; a.ng_max = h->ng_max;
     for (int s = 0; s < ds::MAX_SENSORS; ++s) {
         a.sen[s] = h->sen[s];
         if (s < h->S) {  // the render kernels read the tile-ordered tables
@@ -361,6 +376,8 @@ Args base_args(const sim_handle* h) {
         }
     }
     a.prims = h->d_prims; a.map_off = h->d_map_off; a.map_ns = h->d_map_ns; a.map_nb = h->d_map_nb;
+    a.map_nc = h->d_map_nc; a.map_ng = h->d_map_ng;
+    a.gate_k = h->d_gate_k; a.imu_bias = h->d_imu_bias;
     a.env_map = h->d_env_map; a.order = h->d_order; a.targets = h->d_targets;
     a.pool = h->have_pool ? h->d_pool : nullptr;
     a.drag_env = h->d_drag; a.lam_env = h->d_lam;
@@ -517,6 +534,8 @@ int sim_destroy(sim_handle* h) {
         cudaEventDestroy(e.b);
     }
     dfree(h->d_prims); dfree(h->d_map_off); dfree(h->d_map_ns); dfree(h->d_map_nb);
+    dfree(h->d_map_nc); dfree(h->d_map_ng);
+    dfree(h->d_gate_k); dfree(h->d_gate_tape); dfree(h->d_imu_bias);
     dfree(h->d_env_map); dfree(h->d_order); dfree(h->d_targets); dfree(h->d_pool);
     dfree(h->d_drag); dfree(h->d_lam); dfree(h->d_cam); dfree(h->d_lid);
     dfree(h->d_cam_tmax); dfree(h->d_lid_tmax);
@@ -595,6 +614,11 @@ int sim_create(const sim_config* cfg, sim_handle** out) {
     TRY(dalloc(h, &h->d_ckpt_k, (size_t)nseg * h->N));
     TRY(dalloc(h, &h->d_done_tape, (size_t)h->T * h->NM));
     TRY(dalloc(h, &h->d_sdf_tape, (size_t)h->T * h->NM));
+    TRY(dalloc(h, &h->d_gate_k, (size_t)h->NM));
+    TRY(dalloc(h, &h->d_imu_bias, (size_t)h->NM * 6));
+    if (cfg->task == SIM_TASK_RACING) TRY(dalloc(h, &h->d_gate_tape, (size_t)h->T * h->NM));
+    TRY(cuda_err(cudaMemset(h->d_gate_k, 0, sizeof(int) * h->NM)));
+    TRY(cuda_err(cudaMemset(h->d_imu_bias, 0, sizeof(float) * 6 * h->NM)));
     if (h->tape) {
         if (h->Rc) TRY(dalloc(h, &h->d_tape_cam, (size_t)h->T * h->NM * h->Rc));
         if (h->Rl) TRY(dalloc(h, &h->d_tape_lid, (size_t)h->T * h->NM * h->Rl));
@@ -624,56 +648,115 @@ int sim_workspace_bytes(const sim_handle* h, size_t* bytes) {
 
 int sim_set_scene(sim_handle* h, const float* spheres, const int32_t* sph_off, const float* boxes,
                   const int32_t* box_off, int32_t n_maps, const int32_t* env_map, const float* targets) {
-    if (!h || !sph_off || !box_off || !env_map || !targets) return SIM_ERR_NULL_PTR;
-    if (n_maps < 1) return SIM_ERR_SIZE;
-    if (sph_off[0] != 0 || box_off[0] != 0) return SIM_ERR_SIZE;
-    int ns_max = 0, nb_max = 0;
+    sim_scene sc{};
+    sc.n_maps = n_maps;
+    sc.spheres = spheres; sc.sph_off = sph_off;
+    sc.boxes = boxes; sc.box_off = box_off;
+    sc.env_map = env_map; sc.targets = targets;
+    return sim_set_scene_ex(h, &sc);
+}
+
+namespace {
+// Counts of one kind per map from its CSR offsets (all zero when absent);
+// false when the offsets are inconsistent.
+bool kind_counts(const int32_t* off, int n_maps, std::vector<int>& cnt) {
+    cnt.assign(n_maps, 0);
+    if (!off) return true;
+    if (off[0] != 0) return false;
     for (int m = 0; m < n_maps; ++m) {
-        const int ns = sph_off[m + 1] - sph_off[m], nb = box_off[m + 1] - box_off[m];
-        if (ns < 0 || nb < 0 || ns + nb > 32767) return SIM_ERR_SIZE;
-        ns_max = std::max(ns_max, ns);
-        nb_max = std::max(nb_max, nb);
+        cnt[m] = off[m + 1] - off[m];
+        if (cnt[m] < 0) return false;
     }
-    const long Ks = sph_off[n_maps], Kb = box_off[n_maps];
-    if ((Ks > 0 && !spheres) || (Kb > 0 && !boxes)) return SIM_ERR_NULL_PTR;
-    for (long k = 0; k < Ks; ++k) {
-        for (int j = 0; j < 4; ++j)
-            if (!std::isfinite(spheres[4 * k + j])) return SIM_ERR_INVALID_ARG;
-        if (spheres[4 * k + 3] < 0.f) return SIM_ERR_INVALID_ARG;
+    return true;
+}
+
+bool all_finite(const float* x, long n) {
+    for (long k = 0; k < n; ++k)
+        if (!std::isfinite(x[k])) return false;
+    return true;
+}
+}  // namespace
+
+int sim_set_scene_ex(sim_handle* h, const sim_scene* sc) {
+    if (!h || !sc) return SIM_ERR_NULL_PTR;
+    const int n_maps = sc->n_maps;
+    if (!sc->sph_off || !sc->box_off || !sc->env_map || !sc->targets) return SIM_ERR_NULL_PTR;
+    if ((sc->cylinders != nullptr) != (sc->cyl_off != nullptr) || (sc->gates != nullptr) != (sc->gate_off != nullptr))
+        return SIM_ERR_NULL_PTR;
+    if (n_maps < 1) return SIM_ERR_SIZE;
+    std::vector<int> vns, vnb, vnc, vng;
+    if (!kind_counts(sc->sph_off, n_maps, vns) || !kind_counts(sc->box_off, n_maps, vnb) ||
+        !kind_counts(sc->cyl_off, n_maps, vnc) || !kind_counts(sc->gate_off, n_maps, vng))
+        return SIM_ERR_SIZE;
+    int ns_max = 0, nb_max = 0, nc_max = 0, ng_max = 0;
+    for (int m = 0; m < n_maps; ++m) {
+        if ((long)vns[m] + vnb[m] + vnc[m] + vng[m] > 32767) return SIM_ERR_SIZE;
+        if (vnc[m] > 0xffff || vng[m] > 0x7fff) return SIM_ERR_SIZE;
+        if (h->cfg.task == SIM_TASK_RACING && vng[m] < 1) return SIM_ERR_SIZE;
+        ns_max = std::max(ns_max, vns[m]);
+        nb_max = std::max(nb_max, vnb[m]);
+        nc_max = std::max(nc_max, vnc[m]);
+        ng_max = std::max(ng_max, vng[m]);
     }
+    const long Ks = sc->sph_off[n_maps], Kb = sc->box_off[n_maps];
+    const long Kc = sc->cyl_off ? sc->cyl_off[n_maps] : 0, Kg = sc->gate_off ? sc->gate_off[n_maps] : 0;
+    if ((Ks > 0 && !sc->spheres) || (Kb > 0 && !sc->boxes)) return SIM_ERR_NULL_PTR;
+    if (!all_finite(sc->spheres, 4 * Ks) || !all_finite(sc->boxes, 6 * Kb) || !all_finite(sc->cylinders, 5 * Kc) ||
+        !all_finite(sc->gates, 7 * Kg))
+        return SIM_ERR_INVALID_ARG;
+    for (long k = 0; k < Ks; ++k)
+        if (sc->spheres[4 * k + 3] < 0.f) return SIM_ERR_INVALID_ARG;
     for (long k = 0; k < Kb; ++k)
-        for (int j = 0; j < 3; ++j) {
-            if (!std::isfinite(boxes[6 * k + j]) || !std::isfinite(boxes[6 * k + 3 + j])) return SIM_ERR_INVALID_ARG;
-            if (boxes[6 * k + 3 + j] < boxes[6 * k + j]) return SIM_ERR_INVALID_ARG;
-        }
+        for (int j = 0; j < 3; ++j)
+            if (sc->boxes[6 * k + 3 + j] < sc->boxes[6 * k + j]) return SIM_ERR_INVALID_ARG;
+    for (long k = 0; k < Kc; ++k)
+        if (sc->cylinders[5 * k + 2] < 0.f || sc->cylinders[5 * k + 4] < sc->cylinders[5 * k + 3])
+            return SIM_ERR_INVALID_ARG;
+    for (long k = 0; k < Kg; ++k)
+        if (!(sc->gates[7 * k + 4] > 0.f && sc->gates[7 * k + 5] > 0.f && sc->gates[7 * k + 6] > 0.f))
+            return SIM_ERR_INVALID_ARG;
     for (int e = 0; e < h->N; ++e)
-        if (env_map[e] < 0 || env_map[e] >= n_maps) return SIM_ERR_SIZE;
-    for (long k = 0; k < 3L * h->NM; ++k)
-        if (!std::isfinite(targets[k])) return SIM_ERR_INVALID_ARG;
-    // map blocks: spheres (c, r), then boxes as (min, 0), (max, 0)
+        if (sc->env_map[e] < 0 || sc->env_map[e] >= n_maps) return SIM_ERR_SIZE;
+    if (!all_finite(sc->targets, 3L * h->NM)) return SIM_ERR_INVALID_ARG;
+    // map blocks: spheres (c, r); boxes (min, 0), (max, 0); cylinders
+    // (cx, cy, r, 0), (zmin, zmax, 0, 0); gates (c, w), (cos yaw, sin yaw, b, hd)
     std::vector<float4> blk;
-    std::vector<int> off(n_maps), vns(n_maps), vnb(n_maps);
-    blk.reserve((size_t)Ks + 2 * Kb);
+    std::vector<int> off(n_maps);
+    blk.reserve((size_t)Ks + 2 * (Kb + Kc + Kg));
     for (int m = 0; m < n_maps; ++m) {
         off[m] = (int)blk.size();
-        vns[m] = sph_off[m + 1] - sph_off[m];
-        vnb[m] = box_off[m + 1] - box_off[m];
-        for (int k = sph_off[m]; k < sph_off[m + 1]; ++k)
-            blk.push_back(make_float4(spheres[4 * k], spheres[4 * k + 1], spheres[4 * k + 2], spheres[4 * k + 3]));
-        for (int k = box_off[m]; k < box_off[m + 1]; ++k) {
-            blk.push_back(make_float4(boxes[6 * k], boxes[6 * k + 1], boxes[6 * k + 2], 0.f));
-            blk.push_back(make_float4(boxes[6 * k + 3], boxes[6 * k + 4], boxes[6 * k + 5], 0.f));
+        for (int k = sc->sph_off[m]; k < sc->sph_off[m + 1]; ++k) {
+            const float* q = sc->spheres + 4 * k;
+            blk.push_back(make_float4(q[0], q[1], q[2], q[3]));
+        }
+        for (int k = sc->box_off[m]; k < sc->box_off[m + 1]; ++k) {
+            const float* q = sc->boxes + 6 * k;
+            blk.push_back(make_float4(q[0], q[1], q[2], 0.f));
+            blk.push_back(make_float4(q[3], q[4], q[5], 0.f));
+        }
+        for (int k = sc->cyl_off ? sc->cyl_off[m] : 0; sc->cyl_off && k < sc->cyl_off[m + 1]; ++k) {
+            const float* q = sc->cylinders + 5 * k;
+            blk.push_back(make_float4(q[0], q[1], q[2], 0.f));
+            blk.push_back(make_float4(q[3], q[4], 0.f, 0.f));
+        }
+        for (int k = sc->gate_off ? sc->gate_off[m] : 0; sc->gate_off && k < sc->gate_off[m + 1]; ++k) {
+            const float* q = sc->gates + 7 * k;
+            blk.push_back(make_float4(q[0], q[1], q[2], q[4]));
+            blk.push_back(make_float4((float)std::cos((double)q[3]), (float)std::sin((double)q[3]), q[5], q[6]));
         }
     }
     if (blk.size() >= (size_t)INT32_MAX) return SIM_ERR_SIZE;
     // environments in descending work order (load balance of the ticket queue)
     std::vector<int> order(h->N);
     std::iota(order.begin(), order.end(), 0);
-    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
-        return vns[env_map[x]] + vnb[env_map[x]] > vns[env_map[y]] + vnb[env_map[y]];
-    });
+    auto work = [&](int e) {
+        const int m = sc->env_map[e];
+        return vns[m] + vnb[m] + 2 * (vnc[m] + vng[m]);
+    };
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return work(x) > work(y); });
     ++h->generation;
     dfree(h->d_prims); dfree(h->d_map_off); dfree(h->d_map_ns); dfree(h->d_map_nb);
+    dfree(h->d_map_nc); dfree(h->d_map_ng);
     dfree(h->d_env_map); dfree(h->d_order); dfree(h->d_targets);
     int rc;
     if ((rc = dalloc(h, &h->d_prims, std::max<size_t>(blk.size(), 1)))) return rc;
@@ -681,18 +764,30 @@ int sim_set_scene(sim_handle* h, const float* spheres, const int32_t* sph_off, c
         (rc = dalloc(h, &h->d_map_nb, n_maps)) || (rc = dalloc(h, &h->d_env_map, h->N)) ||
         (rc = dalloc(h, &h->d_order, h->N)) || (rc = dalloc(h, &h->d_targets, 3 * (size_t)h->NM)))
         return rc;
+    const bool extra = nc_max > 0 || ng_max > 0;
+    if (extra && ((rc = dalloc(h, &h->d_map_nc, n_maps)) || (rc = dalloc(h, &h->d_map_ng, n_maps)))) return rc;
     if (!blk.empty()) CK(cudaMemcpy(h->d_prims, blk.data(), blk.size() * sizeof(float4), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(h->d_map_off, off.data(), n_maps * sizeof(int), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(h->d_map_ns, vns.data(), n_maps * sizeof(int), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(h->d_map_nb, vnb.data(), n_maps * sizeof(int), cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(h->d_env_map, env_map, h->N * sizeof(int), cudaMemcpyHostToDevice));
+    if (extra) {
+        CK(cudaMemcpy(h->d_map_nc, vnc.data(), n_maps * sizeof(int), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(h->d_map_ng, vng.data(), n_maps * sizeof(int), cudaMemcpyHostToDevice));
+    }
+    CK(cudaMemcpy(h->d_env_map, sc->env_map, h->N * sizeof(int), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(h->d_order, order.data(), h->N * sizeof(int), cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(h->d_targets, targets, 3 * (size_t)h->NM * sizeof(float), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(h->d_targets, sc->targets, 3 * (size_t)h->NM * sizeof(float), cudaMemcpyHostToDevice));
     h->ns_max = ns_max;
     h->nb_max = nb_max;
+    h->nc_max = nc_max;
+    h->ng_max = ng_max;
     h->n_maps = n_maps;
+    h->h_map_ng = vng;
+    h->h_env_map.assign(sc->env_map, sc->env_map + h->N);
     rc = configure_launch(h);
     if (rc) return rc;
+    // gate indices start at the first gate
+    CK(cudaMemset(h->d_gate_k, 0, sizeof(int) * h->NM));
     h->have_scene = true;
     h->have_rollout = false;
     return SIM_OK;
@@ -743,8 +838,31 @@ int sim_reset(sim_handle* h, const float* state0, sim_stream_t stream) {
     else if (h->have_pool) CK(cudaMemcpyAsync(h->d_state, h->d_pool, n, cudaMemcpyDeviceToDevice, st));
     else return SIM_ERR_NOT_READY;
     CK(cudaMemsetAsync(h->d_pool_k, 0, sizeof(int) * h->N, st));
+    CK(cudaMemsetAsync(h->d_gate_k, 0, sizeof(int) * h->NM, st));
+    CK(cudaMemsetAsync(h->d_imu_bias, 0, sizeof(float) * 6 * h->NM, st));
     h->have_rollout = false;
     h->last_stream = st;
+    return SIM_OK;
+}
+
+int sim_get_gate_index(const sim_handle* h, int32_t* gate_k, sim_stream_t stream) {
+    if (!h || !gate_k) return SIM_ERR_NULL_PTR;
+    CK(cudaMemcpyAsync(gate_k, h->d_gate_k, sizeof(int) * h->NM, cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+    return SIM_OK;
+}
+
+int sim_set_gate_index(sim_handle* h, const int32_t* gate_k, sim_stream_t stream) {
+    if (!h || !gate_k) return SIM_ERR_NULL_PTR;
+    if (h->cfg.task != SIM_TASK_RACING) return SIM_ERR_UNSUPPORTED;
+    if (!h->have_scene) return SIM_ERR_NOT_READY;
+    // indices must name a gate of the agent's map: checked on the host
+    std::vector<int> k(h->NM);
+    CK(cudaMemcpyAsync(k.data(), gate_k, sizeof(int) * h->NM, cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+    CK(cudaStreamSynchronize((cudaStream_t)stream));
+    for (int i = 0; i < h->NM; ++i)
+        if (k[i] < 0 || k[i] >= h->h_map_ng[h->h_env_map[i / h->M]]) return SIM_ERR_INVALID_ARG;
+    CK(cudaMemcpyAsync(h->d_gate_k, gate_k, sizeof(int) * h->NM, cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+    h->have_rollout = false;
     return SIM_OK;
 }
 
@@ -780,9 +898,8 @@ int sim_render(sim_handle* h, float* depth, float* lidar, sim_stream_t stream) {
     return run_render(h, 0, a, st);
 }
 
-int sim_step(sim_handle* h, const float* actions, float* depth, float* lidar, float* r_ctrl, int8_t* r_goal,
-             uint8_t* done, sim_stream_t stream) {
-    if (!h || !actions) return SIM_ERR_NULL_PTR;
+int sim_step_ex(sim_handle* h, const sim_rollout_io* io, sim_stream_t stream) {
+    if (!h || !io || !io->actions) return SIM_ERR_NULL_PTR;
     if (!h->have_scene) return SIM_ERR_NOT_READY;
     if (h->cfg.terminate && !h->have_pool) return SIM_ERR_NOT_READY;
     cudaStream_t st = (cudaStream_t)stream;
@@ -790,28 +907,39 @@ int sim_step(sim_handle* h, const float* actions, float* depth, float* lidar, fl
     a.T = 1;
     a.parts = h->parts_one;
     a.K = 1;
-    a.actions = actions;
-    a.r_ctrl = r_ctrl; a.r_goal = r_goal; a.done = done;
+    a.actions = io->actions;
+    a.r_ctrl = io->r_ctrl; a.r_goal = io->r_goal; a.done = io->done;
+    a.imu = io->imu; a.imu_noise = io->imu_noise;
     a.poses = h->d_pose1;
     int rc = run_physics(h, a, st);
     if (rc || h->S == 0) return rc;
     int s = 0;
-    if (h->Rc) { a.sen[s].out = depth; a.sen[s].tape = nullptr; ++s; }
-    if (h->Rl) { a.sen[s].out = lidar; a.sen[s].tape = nullptr; ++s; }
+    if (h->Rc) { a.sen[s].out = io->depth; a.sen[s].tape = nullptr; ++s; }
+    if (h->Rl) { a.sen[s].out = io->lidar; a.sen[s].tape = nullptr; ++s; }
     return run_render(h, 0, a, st);
 }
 
-int sim_rollout(sim_handle* h, const float* actions, float* r_ctrl, int8_t* r_goal, uint8_t* done, float* depth,
-                float* lidar, sim_stream_t stream) {
-    if (!h || !actions) return SIM_ERR_NULL_PTR;
+int sim_step(sim_handle* h, const float* actions, float* depth, float* lidar, float* r_ctrl, int8_t* r_goal,
+             uint8_t* done, sim_stream_t stream) {
+    sim_rollout_io io{};
+    io.actions = actions;
+    io.r_ctrl = r_ctrl; io.r_goal = r_goal; io.done = done;
+    io.depth = depth; io.lidar = lidar;
+    return sim_step_ex(h, &io, stream);
+}
+
+int sim_rollout_ex(sim_handle* h, const sim_rollout_io* io, sim_stream_t stream) {
+    if (!h || !io || !io->actions) return SIM_ERR_NULL_PTR;
     if (!h->have_scene) return SIM_ERR_NOT_READY;
     if (h->cfg.terminate && !h->have_pool) return SIM_ERR_NOT_READY;
     cudaStream_t st = (cudaStream_t)stream;
     Args a = base_args(h);
-    a.actions = actions;
-    a.r_ctrl = r_ctrl; a.r_goal = r_goal; a.done = done;
+    a.actions = io->actions;
+    a.r_ctrl = io->r_ctrl; a.r_goal = io->r_goal; a.done = io->done;
+    a.imu = io->imu; a.imu_noise = io->imu_noise;
     a.done_tape = h->d_done_tape;
     a.sdf_tape = h->d_sdf_tape;
+    a.gate_tape = h->d_gate_tape;
     a.ckpt = h->d_ckpt;
     a.ckpt_k = h->d_ckpt_k;
     a.poses = h->d_poses;
@@ -819,33 +947,43 @@ int sim_rollout(sim_handle* h, const float* actions, float* r_ctrl, int8_t* r_go
     if (rc) return rc;
     if (h->S > 0) {
         int s = 0;
-        if (h->Rc) { a.sen[s].out = depth; a.sen[s].tape = h->d_tape_cam; ++s; }
-        if (h->Rl) { a.sen[s].out = lidar; a.sen[s].tape = h->d_tape_lid; ++s; }
+        if (h->Rc) { a.sen[s].out = io->depth; a.sen[s].tape = h->d_tape_cam; ++s; }
+        if (h->Rl) { a.sen[s].out = io->lidar; a.sen[s].tape = h->d_tape_lid; ++s; }
         rc = run_render(h, 0, a, st);
         if (rc) return rc;
     }
     h->have_rollout = true;
-    h->rollout_actions = actions;
+    h->rollout_actions = io->actions;
     return SIM_OK;
 }
 
-int sim_backward(sim_handle* h, const float* g_r, const float* g_depth, const float* g_lidar, const float* g_sT,
-                 float* g_a, float* g_s0, sim_stream_t stream) {
-    if (!h || !g_r || !g_a) return SIM_ERR_NULL_PTR;
+int sim_rollout(sim_handle* h, const float* actions, float* r_ctrl, int8_t* r_goal, uint8_t* done, float* depth,
+                float* lidar, sim_stream_t stream) {
+    sim_rollout_io io{};
+    io.actions = actions;
+    io.r_ctrl = r_ctrl; io.r_goal = r_goal; io.done = done;
+    io.depth = depth; io.lidar = lidar;
+    return sim_rollout_ex(h, &io, stream);
+}
+
+int sim_backward_ex(sim_handle* h, const sim_grad_io* io, sim_stream_t stream) {
+    if (!h || !io || !io->g_r || !io->g_a) return SIM_ERR_NULL_PTR;
     if (!h->have_rollout) return SIM_ERR_NOT_READY;
     cudaStream_t st = (cudaStream_t)stream;
     Args a = base_args(h);
     a.actions = h->rollout_actions;
     a.done_rd = h->d_done_tape;
     a.sdf_tape = h->d_sdf_tape;
+    a.gate_tape = h->d_gate_tape;
     a.ckpt = h->d_ckpt;
     a.ckpt_k = h->d_ckpt_k;
     a.poses = h->d_poses;
-    a.g_r = g_r; a.g_sT = g_sT; a.g_a = g_a; a.g_s0 = g_s0;
+    a.g_r = io->g_r; a.g_sT = io->g_sT; a.g_a = io->g_a; a.g_s0 = io->g_s0;
+    a.g_imu = io->g_imu;
     int s = 0;
-    if (h->Rc) { a.sen[s].gout = g_depth; a.sen[s].tape = h->d_tape_cam; ++s; }
-    if (h->Rl) { a.sen[s].gout = g_lidar; a.sen[s].tape = h->d_tape_lid; ++s; }
-    if (h->S > 0 && (g_depth || g_lidar)) {
+    if (h->Rc) { a.sen[s].gout = io->g_depth; a.sen[s].tape = h->d_tape_cam; ++s; }
+    if (h->Rl) { a.sen[s].gout = io->g_lidar; a.sen[s].tape = h->d_tape_lid; ++s; }
+    if (h->S > 0 && (io->g_depth || io->g_lidar)) {
         a.gposes = h->d_gposes;
         int rc = run_render(h, 1, a, st);
         if (rc) return rc;
@@ -853,11 +991,20 @@ int sim_backward(sim_handle* h, const float* g_r, const float* g_depth, const fl
     return run_physics_bwd(h, a, st);
 }
 
+int sim_backward(sim_handle* h, const float* g_r, const float* g_depth, const float* g_lidar, const float* g_sT,
+                 float* g_a, float* g_s0, sim_stream_t stream) {
+    sim_grad_io io{};
+    io.g_r = g_r; io.g_depth = g_depth; io.g_lidar = g_lidar; io.g_sT = g_sT;
+    io.g_a = g_a; io.g_s0 = g_s0;
+    return sim_backward_ex(h, &io, stream);
+}
+
 int sim_step_backward(sim_handle* h, const float* s_t, const float* a_t, const uint8_t* done_t,
                       const float* g_s_next, const float* g_r, const float* g_depth, const float* g_lidar,
                       float* g_a, float* g_s, sim_stream_t stream) {
     if (!h || !s_t || !a_t || !done_t || !g_r || !g_a) return SIM_ERR_NULL_PTR;
     if (!h->have_scene) return SIM_ERR_NOT_READY;
+    if (h->cfg.task != SIM_TASK_REACH) return SIM_ERR_UNSUPPORTED;
     cudaStream_t st = (cudaStream_t)stream;
     Args a = base_args(h);
     a.T = 1;

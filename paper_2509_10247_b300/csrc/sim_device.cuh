@@ -19,6 +19,8 @@ struct Phys {
     float w_pos, w_obs, d_safe, w_act, w_agent, d_agent, success_radius, r_quad;
     float blo[3], bhi[3];
     int terminate, P;
+    int task;                  // 0 reach / avoid, 1 racing through the map's gates
+    float imu_noise[2], imu_walk[2];  // IMU white-noise and bias-walk std (force, rate)
 };
 
 __device__ __forceinline__ float clip1(float x) { return fminf(fmaxf(x, -1.f), 1.f); }
@@ -448,44 +450,105 @@ __device__ __forceinline__ void rb_step_vjp(const Phys& c, const float* s, const
 }
 
 // ---------------------------------------------------------------- obstacles
-// Map block in memory: ns spheres float4 (cx, cy, cz, r), then nb boxes as
-// float4 (min xyz, 0) followed by float4 (max xyz, 0).
-__device__ __forceinline__ float sdf_prim(const float4* prim, int ns, int k, const float* p) {
-    if (k < ns) {
-        float4 s = prim[k];
+// Map block in memory (float4): ns spheres (cx, cy, cz, r); nb boxes as
+// (min xyz, 0), (max xyz, 0); nc vertical capped cylinders as (cx, cy, r, 0),
+// (zmin, zmax, 0, 0); ng racing gates as (cx, cy, cz, w), (cos yaw, sin yaw,
+// b, hd).  Primitive ids: spheres 0.., boxes ns.., cylinders ns + nb..,
+// gates ns + nb + nc...
+struct MapView {
+    const float4* prim;
+    int ns, nb, nc, ng;
+    __device__ __forceinline__ int count() const { return ns + nb + nc + ng; }
+    __device__ __forceinline__ const float4* box(int k) const { return prim + ns + 2 * k; }
+    __device__ __forceinline__ const float4* cyl(int k) const { return prim + ns + 2 * nb + 2 * k; }
+    __device__ __forceinline__ const float4* gate(int k) const { return prim + ns + 2 * (nb + nc) + 2 * k; }
+};
+
+// Local gate coordinates (normal, lateral, up) of a point relative to the centre.
+__device__ __forceinline__ void gate_local(const float4& g0, const float4& g1, const float* p, float* u) {
+    const float rx = p[0] - g0.x, ry = p[1] - g0.y;
+    u[0] = fmaf(g1.x, rx, g1.y * ry);
+    u[1] = fmaf(g1.x, ry, -g1.y * rx);
+    u[2] = p[2] - g0.z;
+}
+
+// Signed distance of a box given by centre ctr and half extents h (local frame).
+__device__ __forceinline__ float sdf_box_ch(const float* q0, const float* ctr, const float* h) {
+    float q[3], out = 0.f;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        q[i] = fabsf(q0[i] - ctr[i]) - h[i];
+        out = fmaf(relu(q[i]), relu(q[i]), out);
+    }
+    return sqrtf(out) + fminf(fmaxf(q[0], fmaxf(q[1], q[2])), 0.f);
+}
+
+// Bar k of a gate (0 top, 1 bottom, 2 left, 3 right) in local coordinates:
+// centre and half extents; top and bottom span the outer width, the sides
+// the opening's height.
+__device__ __forceinline__ void gate_bar(const float4& g0, const float4& g1, int k, float* ctr, float* h) {
+    const float w = g0.w, b = g1.z, m = w + 0.5f * b;
+    ctr[0] = 0.f;
+    h[0] = g1.w;
+    ctr[1] = k < 2 ? 0.f : (k == 2 ? -m : m);
+    ctr[2] = k < 2 ? (k == 0 ? m : -m) : 0.f;
+    h[1] = k < 2 ? w + b : 0.5f * b;
+    h[2] = k < 2 ? 0.5f * b : w;
+}
+
+__device__ __forceinline__ float sdf_gate(const float4& g0, const float4& g1, const float* p, int* bar) {
+    float u[3];
+    gate_local(g0, g1, p, u);
+    float best = CUDART_INF_F;
+    int bi = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        float ctr[3], h[3];
+        gate_bar(g0, g1, k, ctr, h);
+        const float d = sdf_box_ch(u, ctr, h);
+        if (d < best) { best = d; bi = k; }
+    }
+    *bar = bi;
+    return best;
+}
+
+__device__ __forceinline__ float sdf_prim(const MapView& m, int k, const float* p) {
+    if (k < m.ns) {
+        float4 s = m.prim[k];
         float dx = p[0] - s.x, dy = p[1] - s.y, dz = p[2] - s.z;
         return sqrtf(dx * dx + dy * dy + dz * dz) - s.w;
     }
-    int b = k - ns;
-    float4 lo = prim[ns + 2 * b], hi = prim[ns + 2 * b + 1];
-    float qx = fabsf(p[0] - 0.5f * (lo.x + hi.x)) - 0.5f * (hi.x - lo.x);
-    float qy = fabsf(p[1] - 0.5f * (lo.y + hi.y)) - 0.5f * (hi.y - lo.y);
-    float qz = fabsf(p[2] - 0.5f * (lo.z + hi.z)) - 0.5f * (hi.z - lo.z);
-    float ox = relu(qx), oy = relu(qy), oz = relu(qz);
-    float in = fminf(fmaxf(qx, fmaxf(qy, qz)), 0.f);
-    return sqrtf(ox * ox + oy * oy + oz * oz) + in;
+    k -= m.ns;
+    if (k < m.nb) {
+        float4 lo = m.box(k)[0], hi = m.box(k)[1];
+        float qx = fabsf(p[0] - 0.5f * (lo.x + hi.x)) - 0.5f * (hi.x - lo.x);
+        float qy = fabsf(p[1] - 0.5f * (lo.y + hi.y)) - 0.5f * (hi.y - lo.y);
+        float qz = fabsf(p[2] - 0.5f * (lo.z + hi.z)) - 0.5f * (hi.z - lo.z);
+        float ox = relu(qx), oy = relu(qy), oz = relu(qz);
+        float in = fminf(fmaxf(qx, fmaxf(qy, qz)), 0.f);
+        return sqrtf(ox * ox + oy * oy + oz * oz) + in;
+    }
+    k -= m.nb;
+    if (k < m.nc) {
+        const float4 c0 = m.cyl(k)[0], c1 = m.cyl(k)[1];
+        const float ex = p[0] - c0.x, ey = p[1] - c0.y;
+        const float qr = sqrtf(fmaf(ex, ex, ey * ey)) - c0.z;
+        const float qz = fabsf(p[2] - 0.5f * (c1.x + c1.y)) - 0.5f * (c1.y - c1.x);
+        return sqrtf(fmaf(relu(qr), relu(qr), relu(qz) * relu(qz))) + fminf(fmaxf(qr, qz), 0.f);
+    }
+    k -= m.nc;
+    int bar;
+    return sdf_gate(m.gate(k)[0], m.gate(k)[1], p, &bar);
 }
 
-__device__ __forceinline__ void sdf_prim_grad(const float4* prim, int ns, int k, const float* p,
-                                              float* gp) {
-    if (k < ns) {
-        float4 s = prim[k];
-        float d[3] = {p[0] - s.x, p[1] - s.y, p[2] - s.z};
-        float n = sqrtf(dot3(d, d));
-        float r = n > 0.f ? 1.f / n : 0.f;
-        gp[0] = d[0] * r; gp[1] = d[1] * r; gp[2] = d[2] * r;
-        return;
-    }
-    int b = k - ns;
-    float4 lo = prim[ns + 2 * b], hi = prim[ns + 2 * b + 1];
-    float l[3] = {lo.x, lo.y, lo.z}, u[3] = {hi.x, hi.y, hi.z};
+// Gradient of a box's signed distance (centre / half-extent form).
+__device__ __forceinline__ void sdf_box_grad_ch(const float* p, const float* ctr, const float* h, float* gp) {
     float q[3], sg[3], out = 0.f;
     int am = 0;
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-        float ctr = 0.5f * (l[i] + u[i]);
-        sg[i] = (p[i] - ctr >= 0.f) ? 1.f : -1.f;
-        q[i] = fabsf(p[i] - ctr) - 0.5f * (u[i] - l[i]);
+        sg[i] = (p[i] - ctr[i] >= 0.f) ? 1.f : -1.f;
+        q[i] = fabsf(p[i] - ctr[i]) - h[i];
         out += relu(q[i]) * relu(q[i]);
     }
     if (q[1] > q[am]) am = 1;
@@ -498,6 +561,187 @@ __device__ __forceinline__ void sdf_prim_grad(const float4* prim, int ns, int k,
 #pragma unroll
         for (int i = 0; i < 3; ++i) gp[i] = (i == am) ? sg[i] : 0.f;
     }
+}
+
+__device__ __forceinline__ void sdf_prim_grad(const MapView& m, int k, const float* p, float* gp) {
+    if (k < m.ns) {
+        float4 s = m.prim[k];
+        float d[3] = {p[0] - s.x, p[1] - s.y, p[2] - s.z};
+        float n = sqrtf(dot3(d, d));
+        float r = n > 0.f ? 1.f / n : 0.f;
+        gp[0] = d[0] * r; gp[1] = d[1] * r; gp[2] = d[2] * r;
+        return;
+    }
+    k -= m.ns;
+    if (k < m.nb) {
+        float4 lo = m.box(k)[0], hi = m.box(k)[1];
+        const float ctr[3] = {0.5f * (lo.x + hi.x), 0.5f * (lo.y + hi.y), 0.5f * (lo.z + hi.z)};
+        const float h[3] = {0.5f * (hi.x - lo.x), 0.5f * (hi.y - lo.y), 0.5f * (hi.z - lo.z)};
+        sdf_box_grad_ch(p, ctr, h, gp);
+        return;
+    }
+    k -= m.nb;
+    if (k < m.nc) {
+        const float4 c0 = m.cyl(k)[0], c1 = m.cyl(k)[1];
+        const float ex = p[0] - c0.x, ey = p[1] - c0.y, zc = 0.5f * (c1.x + c1.y);
+        const float rho = sqrtf(fmaf(ex, ex, ey * ey));
+        const float qr = rho - c0.z, qz = fabsf(p[2] - zc) - 0.5f * (c1.y - c1.x);
+        const float ir = rho > 0.f ? 1.f / rho : 0.f;
+        const float sz = p[2] - zc >= 0.f ? 1.f : -1.f;
+        const float out = sqrtf(fmaf(relu(qr), relu(qr), relu(qz) * relu(qz)));
+        if (out > 0.f) {
+            const float io = 1.f / out;
+            gp[0] = relu(qr) * ex * ir * io; gp[1] = relu(qr) * ey * ir * io; gp[2] = relu(qz) * sz * io;
+        } else if (qr >= qz) {
+            gp[0] = ex * ir; gp[1] = ey * ir; gp[2] = 0.f;
+        } else {
+            gp[0] = 0.f; gp[1] = 0.f; gp[2] = sz;
+        }
+        return;
+    }
+    k -= m.nc;
+    const float4 g0 = m.gate(k)[0], g1 = m.gate(k)[1];
+    int bar;
+    sdf_gate(g0, g1, p, &bar);
+    float u[3], ctr[3], h[3], gu[3];
+    gate_local(g0, g1, p, u);
+    gate_bar(g0, g1, bar, ctr, h);
+    sdf_box_grad_ch(u, ctr, h, gu);
+    gp[0] = fmaf(g1.x, gu[0], -g1.y * gu[1]);
+    gp[1] = fmaf(g1.y, gu[0], g1.x * gu[1]);
+    gp[2] = gu[2];
+}
+
+// Racing: true when the segment x0 -> x1 crosses the gate's centre plane
+// from its back (u_n < 0) to its front (u_n >= 0) inside the opening.
+__device__ __forceinline__ bool gate_passed(const float4& g0, const float4& g1, const float* x0, const float* x1) {
+    float u0[3], u1[3];
+    gate_local(g0, g1, x0, u0);
+    gate_local(g0, g1, x1, u1);
+    if (!(u0[0] < 0.f && u1[0] >= 0.f)) return false;
+    const float f = -u0[0] / (u1[0] - u0[0]);
+    const float ul = fmaf(f, u1[1] - u0[1], u0[1]), uz = fmaf(f, u1[2] - u0[2], u0[2]);
+    return fabsf(ul) < g0.w && fabsf(uz) < g0.w;
+}
+
+// ------------------------------------------------------------------- IMU
+// Readout of one agent after a step (Sec. III-B), noise-free: specific
+// force f = R^T (v' - g) of the model's translational dynamics and the body
+// angular rate, in the body frame of the new state s1, the step's action
+// held: rigid f = (T/m) e3 - D R^T v, omega from the state; point mass
+// f = R^T (a - d v); discrete f = R^T u; simplified f = c e3 and the
+// commanded rates; the point-mass rate is the attitude change over the step,
+// vee(A - A^T) / (2 dt) with A = R0^T R1.
+__device__ __forceinline__ void imu_eval(const Phys& c, float drag, const float* s0, const float* act,
+                                         const float* s1, float* out) {
+    float o[3], R1[9];
+    sensor_pose(c.model, s1, o, R1);
+    if (c.model == MODEL_RIGID) {
+        const float T = c.g * (1.f + clip1(act[0]));
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const float vb = fmaf(R1[j], s1[7], fmaf(R1[3 + j], s1[8], R1[6 + j] * s1[9]));
+            out[j] = (j == 2 ? T : 0.f) - c.Dd[j] * vb;
+            out[3 + j] = s1[10 + j];
+        }
+        return;
+    }
+    if (c.model == MODEL_SIMPLE) {
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            out[j] = j == 2 ? c.g * (1.f + clip1(act[0])) : 0.f;
+            out[3 + j] = c.rs[j] * clip1(act[1 + j]);
+        }
+        return;
+    }
+    float acc[3], R0[9];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) acc[i] = c.model == MODEL_PMD ? s1[6 + i] : fmaf(-drag, s1[3 + i], s1[6 + i]);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) out[j] = fmaf(R1[j], acc[0], fmaf(R1[3 + j], acc[1], R1[6 + j] * acc[2]));
+    sensor_pose(c.model, s0, o, R0);
+    // A_ij = sum_k R0_ki R1_kj, only the off-diagonal pairs are needed
+    auto A = [&](int i, int j) { return fmaf(R0[i], R1[j], fmaf(R0[3 + i], R1[3 + j], R0[6 + i] * R1[6 + j])); };
+    const float h = 0.5f / c.dt;
+    out[3] = (A(2, 1) - A(1, 2)) * h;
+    out[4] = (A(0, 2) - A(2, 0)) * h;
+    out[5] = (A(1, 0) - A(0, 1)) * h;
+}
+
+// After a reset: the new state read as held at rest (f = -R^T g; the rigid
+// body's rate state, else no rate).
+__device__ __forceinline__ void imu_reset(const Phys& c, const float* s, float* out) {
+    float o[3], R[9];
+    sensor_pose(c.model, s, o, R);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        out[j] = R[6 + j] * c.g;
+        out[3 + j] = c.model == MODEL_RIGID ? s[10 + j] : 0.f;
+    }
+}
+
+// VJP of imu_eval: g [6] into gs0 (state the step started from), gs1 (new
+// state before reset) and ga (raw action).
+__device__ __forceinline__ void imu_vjp(const Phys& c, float drag, const float* s0, const float* act,
+                                        const float* s1, const float* g, float* gs0, float* gs1, float* ga) {
+    float o[3], R1[9], gR1[9];
+    const float zero[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int k = 0; k < 9; ++k) gR1[k] = 0.f;
+    sensor_pose(c.model, s1, o, R1);
+    if (c.model == MODEL_RIGID) {
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                gR1[3 * i + j] += -c.Dd[j] * s1[7 + i] * g[j];
+                gs1[7 + i] += -c.Dd[j] * R1[3 * i + j] * g[j];
+            }
+        ga[0] += c.g * dclip1(act[0]) * g[2];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) gs1[10 + j] += g[3 + j];
+        pose_vjp(c.model, s1, zero, gR1, gs1);
+        return;
+    }
+    if (c.model == MODEL_SIMPLE) {
+        ga[0] += c.g * dclip1(act[0]) * g[2];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) ga[1 + j] += c.rs[j] * dclip1(act[1 + j]) * g[3 + j];
+        return;
+    }
+    float acc[3], gacc[3] = {0.f, 0.f, 0.f}, R0[9], gR0[9], gA[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) { gR0[k] = 0.f; gA[k] = 0.f; }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) acc[i] = c.model == MODEL_PMD ? s1[6 + i] : fmaf(-drag, s1[3 + i], s1[6 + i]);
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            gR1[3 * i + j] += acc[i] * g[j];
+            gacc[i] += R1[3 * i + j] * g[j];
+        }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        gs1[6 + i] += gacc[i];
+        if (c.model != MODEL_PMD) gs1[3 + i] += -drag * gacc[i];
+    }
+    sensor_pose(c.model, s0, o, R0);
+    const float h = 0.5f / c.dt;
+    gA[7] += h * g[3]; gA[5] -= h * g[3];
+    gA[2] += h * g[4]; gA[6] -= h * g[4];
+    gA[3] += h * g[5]; gA[1] -= h * g[5];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                gR0[3 * k + i] += gA[3 * i + j] * R1[3 * k + j];
+                gR1[3 * k + j] += gA[3 * i + j] * R0[3 * k + i];
+            }
+    pose_vjp(c.model, s1, zero, gR1, gs1);
+    pose_vjp(c.model, s0, zero, gR0, gs0);
 }
 
 }  // namespace ds

@@ -25,20 +25,22 @@ __device__ inline WList fused_list(const Args& a, unsigned char* sm, int Lx) {
     L.sph = reinterpret_cast<float4*>(sm + a.sm.lsph) + (size_t)Lx * a.ns_max;
     L.sx = reinterpret_cast<float2*>(sm + a.sm.lr2) + (size_t)Lx * a.ns_max;
     L.box = reinterpret_cast<float4*>(sm + a.sm.lbox) + (size_t)Lx * a.nb_max * 2;
+    L.cyl = nullptr;  // spheres and boxes only
+    L.gat = nullptr;
     L.id = reinterpret_cast<short*>(sm + a.sm.lid) + (size_t)Lx * (a.ns_max + a.nb_max);
+    L.sub = nullptr;
     L.meta = reinterpret_cast<int4*>(sm + a.sm.lmeta) + Lx;
     return L;
 }
 
 // Cull the map for every (agent, sensor) list of the CTA (one warp per list).
-__device__ void build_lists(const Args& a, unsigned char* sm, int ns, int nb) {
+__device__ void build_lists(const Args& a, unsigned char* sm, const MapView& mv) {
     const int warp = threadIdx.x >> 5, NW = blockDim.x >> 5;
     const int L = a.M * a.S;
-    const float4* prim = reinterpret_cast<const float4*>(sm + a.sm.prim);
     const float* pose = reinterpret_cast<const float*>(sm + a.sm.pose);
     for (int Lx = warp; Lx < L; Lx += NW) {
         const float* o = pose + (Lx / a.S) * 12;
-        warp_build_list(prim, ns, nb, o, o + 3, a.sen[Lx % a.S], a.cull, fused_list(a, sm, Lx), a.ns_max);
+        warp_build_list<false>(mv, o, o + 3, a.sen[Lx % a.S], a.cull, fused_list(a, sm, Lx), cap_of(a));
     }
 }
 
@@ -91,12 +93,12 @@ __global__ void __launch_bounds__(256, 3) k_rollout(const Args a) {
         if (q >= a.N) break;
         const int env = a.order ? a.order[q] : q;
         const int map = a.env_map[env];
-        const int ns = a.map_ns[map], nb = a.map_nb[map];
+        const MapView mv = map_view(a, map, prim);
         for (int i = threadIdx.x; i < M * 16; i += blockDim.x) {
             const int m = i >> 4, k = i & 15;
             st[i] = k < D ? a.state[(size_t)(env * M + m) * D + k] : 0.f;
         }
-        if (!stage_map(a, sm, map, ns, nb, phase, &s_flag)) return;
+        if (!stage_map(a, sm, map, mv, phase, &s_flag)) return;
         const float drag = a.drag_env ? a.drag_env[env] : a.c.drag;
         const float lam = a.lam_env ? a.lam_env[env] : a.c.lam;
         int kpool = a.pool_k ? a.pool_k[env] : 0;
@@ -127,8 +129,8 @@ __global__ void __launch_bounds__(256, 3) k_rollout(const Args a) {
                     else pm_step(a.c, drag, lam, s, act, sp);
                     float best = CUDART_INF_F;
                     int bid = -1;
-                    for (int k = lane; k < ns + nb; k += 32) {
-                        float d = sdf_prim(prim, ns, k, sp);
+                    for (int k = lane; k < mv.count(); k += 32) {
+                        float d = sdf_prim(mv, k, sp);
                         if (d < best) { best = d; bid = k; }
                     }
                     warp_argmin(best, bid);
@@ -215,7 +217,7 @@ __global__ void __launch_bounds__(256, 3) k_rollout(const Args a) {
             }
             if (a.S == 0) continue;
             // B: cull
-            build_lists(a, sm, ns, nb);
+            build_lists(a, sm, mv);
             __syncthreads();
             // C: rays
             const int nit = n_items<RPT>(a);
@@ -231,7 +233,7 @@ __global__ void __launch_bounds__(256, 3) k_rollout(const Args a) {
                 item_rays<RPT>(sen, R, I.chunk, lane, dx, dy, dz, tb);
 #pragma unroll
                 for (int r = 0; r < RPT; ++r) bi[r] = -1;
-                if (meta.z < 0) cast_list<RPT>(fused_list(a, sm, I.Lx), meta, a.ns_max, dx, dy, dz, tb, bi);
+                if (meta.z < 0) cast_list<RPT, false>(fused_list(a, sm, I.Lx), meta, cap_of(a), dx, dy, dz, tb, bi);
                 if (a.counters && lane == 0) {
                     const unsigned long long nr = (unsigned long long)min(32 * RPT, sen.R - I.chunk * 32 * RPT);
                     if (meta.z < 0) {

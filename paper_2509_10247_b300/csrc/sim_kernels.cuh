@@ -7,6 +7,11 @@ namespace ds {
 
 constexpr int MAX_SENSORS = 2;
 
+// Capacities of a cull list (the largest per-map counts of each kind).
+struct LCap {
+    int ns, nb, nc, ng;
+};
+
 // One ray sensor: the camera (kind 0, z-depth) or the LiDAR (kind 1, range).
 struct Sensor {
     int R;                 // rays per agent
@@ -27,7 +32,7 @@ struct Sensor {
 
 // Byte offsets of the dynamic shared-memory regions of one CTA.
 struct Smem {
-    int prim;    // float4 [ns_max + 2 nb_max]     map block
+    int prim;    // float4 [ns_max + 2 (nb_max + nc_max + ng_max)]  map block
     int lsph;    // float4 [L][ns_max]             (oc.xyz, -sqrt(C)) per culled sphere
     int lr2;     // float2 [L][ns_max]             (C, r) per culled sphere
     int lbox;    // float4 [L][nb_max][2]          (centre - o, half extents) per culled box
@@ -50,11 +55,13 @@ struct Args {
     Phys c;
     int N, M, NM, T, K, S;      // envs, agents/env, agents, steps, checkpoint interval, sensors
     int ns_max, nb_max, cull;
+    int nc_max, ng_max;         // largest cylinder and gate counts of a map
     int render_only;            // forward: only render the current state (no dynamics)
     Sensor sen[MAX_SENSORS];
     Smem sm;
     // scene
     const float4* prims; const int* map_off; const int* map_ns; const int* map_nb;
+    const int* map_nc; const int* map_ng;   // cylinder and gate counts [n_maps] (nullable: none)
     const int* env_map; const int* order; const float* targets; const float* pool;
     const float* drag_env; const float* lam_env;
     // state and io
@@ -71,10 +78,19 @@ struct Args {
     float* poses;               // [T][NM][12] sensor pose per step (origin, row-major R)
     float* gposes;              // [T][NM][parts][12] cotangent of the poses, per ray part
     int parts;                  // ray parts per (step, agent) item of the render kernels
+    // racing (task 1) and IMU
+    int* gate_k;                // [NM] each agent's next gate, read and advanced
+    int16_t* gate_tape;         // [T][NM] gate targeted during step t (internal)
+    float* imu;                 // [T][NM][6] readout or nullptr
+    const float* imu_noise;     // [T][NM][12] standard normal samples or nullptr
+    float* imu_bias;            // [NM][6] bias state (advanced with imu_noise)
+    const float* g_imu;         // adjoint: [T][NM][6] cotangent of the readout or nullptr
     // control
     int* work; int* status;
-    unsigned long long* counters;  // [4]: sphere tests, box tests, rays, env-steps (nullable)
+    unsigned long long* counters;  // [4]: sphere tests, box / cylinder / gate tests, rays, env-steps (nullable)
 };
+
+__device__ __forceinline__ LCap cap_of(const Args& a) { return LCap{a.ns_max, a.nb_max, a.nc_max, a.ng_max}; }
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));

@@ -10,42 +10,53 @@
 namespace ds {
 
 // One culled list of an (agent, sensor) pair, origin-relative:
-//   sph [ns_max] float4 (oc.xyz, -sqrt(C)) with C = |oc|^2 - r^2 (sqrt(C) is
-//       the tangent length: a ray reaches the sphere iff d.oc >= sqrt(C),
-//       and then hits it no farther than sqrt(C)),
-//   sx  [ns_max] float2 (C, r),
-//   box [nb_max][2] float4 (centre - o, tangent length of the bounding
-//       sphere or -1e30 when the origin is inside it), (half extents, radius
-//       of the bounding sphere),
-//   id  [ns_max + nb_max] short (map primitive id of each slot; boxes from
-//       slot ns_max),
-//   sub [ns_max + nb_max] short (slots kept for the current ray chunk),
+//   sph [ns] float4 (oc.xyz, -sqrt(C)) with C = |oc|^2 - r^2 (sqrt(C) is the
+//       tangent length: a ray reaches the sphere iff d.oc >= sqrt(C), and
+//       then hits it no farther than sqrt(C)),
+//   box [nb][2] float4 (centre - o, tangent length of the bounding sphere or
+//       -1e30 when the origin is inside it), (half extents, radius of the
+//       bounding sphere),
+//   cyl [nc][2] float4 (axis centre - o, bounding tangent), (r^2, half
+//       height, 0, bounding radius),
+//   gat [ng][3] float4 (centre - o, bounding tangent), (cos yaw, sin yaw,
+//       half depth, bounding radius), (w, w + b, origin in local normal and
+//       lateral coordinates),
+//   sx  [ns] float2 (C, r),
+//   id  [ns + nb + nc + ng] short (map primitive id of each slot; slots of
+//       boxes from ns, cylinders from ns + nb, gates from ns + nb + nc, with
+//       the capacities as the bases),
+//   sub [same] short (slots kept for the current ray chunk),
 //   meta int4 (kept spheres, kept boxes, lowest id of a primitive containing
-//       the origin or -1, 0).
+//       the origin or -1, kept cylinders | kept gates << 16).
 struct WList {
     float4* sph;
     float2* sx;
     float4* box;
+    float4* cyl;
+    float4* gat;
     short* id;
     short* sub;
     int4* meta;
 };
 
-// Bytes of one list laid out contiguously (16-byte aligned parts).
-__host__ __device__ inline size_t wlist_bytes(int ns_max, int nb_max) {
-    size_t b = (size_t)16 * (ns_max + 2 * nb_max) + 8 * (size_t)ns_max + 4 * (size_t)(ns_max + nb_max);
-    return ((b + 15) & ~size_t(15)) + 16;
+__host__ __device__ inline size_t wlist_raw(const LCap& c) {
+    return (size_t)16 * (c.ns + 2 * c.nb + 2 * c.nc + 3 * c.ng) + 8 * (size_t)c.ns +
+           4 * (size_t)(c.ns + c.nb + c.nc + c.ng);
 }
 
-__device__ inline WList wlist_at(unsigned char* p, int ns_max, int nb_max) {
+// Bytes of one list laid out contiguously (16-byte aligned parts).
+__host__ __device__ inline size_t wlist_bytes(const LCap& c) { return ((wlist_raw(c) + 15) & ~size_t(15)) + 16; }
+
+__device__ inline WList wlist_at(unsigned char* p, const LCap& c) {
     WList L;
     L.sph = reinterpret_cast<float4*>(p);
-    L.box = L.sph + ns_max;
-    L.sx = reinterpret_cast<float2*>(L.box + 2 * nb_max);
-    L.id = reinterpret_cast<short*>(L.sx + ns_max);
-    L.sub = L.id + ns_max + nb_max;
-    size_t b = (size_t)16 * (ns_max + 2 * nb_max) + 8 * (size_t)ns_max + 4 * (size_t)(ns_max + nb_max);
-    L.meta = reinterpret_cast<int4*>(p + ((b + 15) & ~size_t(15)));
+    L.box = L.sph + c.ns;
+    L.cyl = L.box + 2 * c.nb;
+    L.gat = L.cyl + 2 * c.nc;
+    L.sx = reinterpret_cast<float2*>(L.gat + 3 * c.ng);
+    L.id = reinterpret_cast<short*>(L.sx + c.ns);
+    L.sub = L.id + c.ns + c.nb + c.nc + c.ng;
+    L.meta = reinterpret_cast<int4*>(p + ((wlist_raw(c) + 15) & ~size_t(15)));
     return L;
 }
 
@@ -76,12 +87,16 @@ __device__ __forceinline__ float safe_rcp(float d) {
     return __frcp_rn(fabsf(d) < 1e-20f ? copysignf(1e-20f, d) : d);
 }
 
-// Cull the map (ns spheres then nb boxes at prim) for the sensor at origin o
-// with rotation R into L, keeping index order (ties resolve to the lowest
-// id).  Executed by one full warp; returns the list's meta.
-__device__ inline int4 warp_build_list(const float4* prim, int ns, int nb, const float* o, const float* R,
-                                       const Sensor& sen, int cull, const WList& L, int ns_max) {
+// Cull the map for the sensor at origin o with rotation R into L, keeping
+// index order within each kind (ties resolve to the lowest id).  Executed
+// by one full warp; returns the list's meta.  EXTRA: the map kinds include
+// cylinders and gates (else only spheres and boxes are read).
+template <bool EXTRA>
+__device__ inline int4 warp_build_list(const MapView& mv, const float* o, const float* R, const Sensor& sen,
+                                       int cull, const WList& L, const LCap& cap) {
     const int lane = threadIdx.x & 31;
+    const float4* prim = mv.prim;
+    const int ns = mv.ns, nb = mv.nb;
     int inside = INT_MAX, cnt = 0;
     for (int base = 0; base < ns; base += 32) {
         const int k = base + lane;
@@ -130,13 +145,68 @@ __device__ inline int4 warp_build_list(const float4* prim, int ns, int nb, const
             int pos = cnt + __popc(bal & ((1u << lane) - 1u));
             L.box[2 * pos] = cc;
             L.box[2 * pos + 1] = hh;
-            L.id[ns_max + pos] = (short)(ns + k);
+            L.id[cap.ns + pos] = (short)(ns + k);
         }
         cnt += __popc(bal);
     }
+    const int nbk = cnt;
+    int nck = 0, ngk = 0;
+    for (int base = 0; EXTRA && base < mv.nc; base += 32) {
+        const int k = base + lane;
+        bool keep = false;
+        float4 c0 = make_float4(0.f, 0.f, 0.f, 0.f), c1 = c0;
+        if (k < mv.nc) {
+            const float4 a0 = mv.cyl(k)[0], a1 = mv.cyl(k)[1];
+            const float hz = 0.5f * (a1.y - a1.x);
+            const float c[3] = {a0.x - o[0], a0.y - o[1], 0.5f * (a1.x + a1.y) - o[2]};
+            const float r2 = a0.z * a0.z;
+            if (fmaf(c[0], c[0], c[1] * c[1]) <= r2 && a1.x <= o[2] && a1.y >= o[2]) inside = min(inside, ns + nb + k);
+            const float rho = sqrtf(fmaf(hz, hz, r2));
+            keep = !cull || cull_keep(sen, R, c, rho);
+            const float cb = dot3(c, c) - rho * rho;
+            c0 = make_float4(c[0], c[1], c[2], cb > 0.f ? sqrtf(cb) : -1e30f);
+            c1 = make_float4(r2, hz, 0.f, rho);
+        }
+        unsigned bal = __ballot_sync(0xffffffffu, keep);
+        if (keep) {
+            int pos = nck + __popc(bal & ((1u << lane) - 1u));
+            L.cyl[2 * pos] = c0;
+            L.cyl[2 * pos + 1] = c1;
+            L.id[cap.ns + cap.nb + pos] = (short)(ns + nb + k);
+        }
+        nck += __popc(bal);
+    }
+    for (int base = 0; EXTRA && base < mv.ng; base += 32) {
+        const int k = base + lane;
+        bool keep = false;
+        float4 g0 = make_float4(0.f, 0.f, 0.f, 0.f), g1 = g0, g2 = g0;
+        if (k < mv.ng) {
+            const float4 a0 = mv.gate(k)[0], a1 = mv.gate(k)[1];
+            const float W = a0.w + a1.z;
+            const float c[3] = {a0.x - o[0], a0.y - o[1], a0.z - o[2]};
+            const float un = -fmaf(a1.x, c[0], a1.y * c[1]), ul = -fmaf(a1.x, c[1], -a1.y * c[0]), uz = -c[2];
+            if (fabsf(un) <= a1.w && fabsf(ul) <= W && fabsf(uz) <= W && !(fabsf(ul) < a0.w && fabsf(uz) < a0.w))
+                inside = min(inside, ns + nb + mv.nc + k);
+            const float rho = sqrtf(fmaf(a1.w, a1.w, 2.f * W * W));
+            keep = !cull || cull_keep(sen, R, c, rho);
+            const float cb = dot3(c, c) - rho * rho;
+            g0 = make_float4(c[0], c[1], c[2], cb > 0.f ? sqrtf(cb) : -1e30f);
+            g1 = make_float4(a1.x, a1.y, a1.w, rho);
+            g2 = make_float4(a0.w, W, un, ul);
+        }
+        unsigned bal = __ballot_sync(0xffffffffu, keep);
+        if (keep) {
+            int pos = ngk + __popc(bal & ((1u << lane) - 1u));
+            L.gat[3 * pos] = g0;
+            L.gat[3 * pos + 1] = g1;
+            L.gat[3 * pos + 2] = g2;
+            L.id[cap.ns + cap.nb + cap.nc + pos] = (short)(ns + nb + mv.nc + k);
+        }
+        ngk += __popc(bal);
+    }
 #pragma unroll
     for (int o2 = 16; o2 > 0; o2 >>= 1) inside = min(inside, __shfl_xor_sync(0xffffffffu, inside, o2));
-    const int4 meta = make_int4(nsk, cnt, inside == INT_MAX ? -1 : inside, 0);
+    const int4 meta = make_int4(nsk, nbk, inside == INT_MAX ? -1 : inside, nck | (ngk << 16));
     if (lane == 0) *L.meta = meta;
     __syncwarp();
     return meta;
@@ -154,14 +224,111 @@ __device__ __forceinline__ void box_test(const float4& c, const float4& h, float
     if (tn <= tf && tn > 0.f && tn < tb) { tb = tn; bi = slot; }
 }
 
+// Vertical capped cylinder (list entry c0 = axis centre - o and bounding
+// tangent, c1 = (r^2, half height, 0, bounding radius)) against one ray
+// with horizontal squared length a = dx^2 + dy^2 (ia = 1/a; vt: the ray is
+// parallel to the axis), iz = 1/dz.  Side interval: around the closest
+// approach tm = (c.d)/a in the horizontal plane, half-width
+// sqrt((r^2 - |c - tm d|^2)/a) (offset form, accurate near tangency); cap
+// slab as for boxes; entry = max, exit = min.
+__device__ __forceinline__ void cyl_test(const float4& c0, const float4& c1, float dx, float dy, float ia,
+                                         bool vt, float iz, int slot, float& tb, int& bi) {
+    const float tm = fmaf(dx, c0.x, dy * c0.y) * ia;
+    const float fx = fmaf(-tm, dx, c0.x), fy = fmaf(-tm, dy, c0.y);
+    const float h2 = (c1.x - fmaf(fx, fx, fy * fy)) * ia;
+    const float h = sqrtf(fmaxf(h2, 0.f));
+    float t0 = h2 >= 0.f ? tm - h : CUDART_INF_F, t1 = tm + h;
+    if (vt) {
+        const bool in = fmaf(c0.x, c0.x, c0.y * c0.y) <= c1.x;
+        t0 = in ? -CUDART_INF_F : CUDART_INF_F;
+        t1 = in ? CUDART_INF_F : -CUDART_INF_F;
+    }
+    const float mz = c0.z * iz;
+    const float tn = fmaxf(t0, fmaf(-c1.y, fabsf(iz), mz)), tf = fminf(t1, fmaf(c1.y, fabsf(iz), mz));
+    if (tn <= tf && tn > 0.f && tn < tb) { tb = tn; bi = slot; }
+}
+
+// Racing gate (list entry g0 = centre - o and bounding tangent, g1 = (cos,
+// sin, half depth, bounding radius), g2 = (w, w + b, origin's local normal
+// and lateral coordinates)) against one ray, iz = 1/dz.  Outer box slabs in
+// local coordinates give [tn, tf]; the open square prism (lateral and up
+// slabs of half-width w) gives (pn, pf).  The first solid point is
+// max(tn, 0) unless that lies strictly inside the prism, then the prism's
+// exit pf if it is still inside the outer box.
+__device__ __forceinline__ float gate_t(const float4& g0, const float4& g1, const float4& g2, float dx, float dy,
+                                        float iz, int* axis) {
+    const float un = fmaf(g1.x, dx, g1.y * dy), ul = fmaf(g1.x, dy, -g1.y * dx);
+    const float in_ = safe_rcp(un), il = safe_rcp(ul);
+    const float mn = -g2.z * in_, ml = -g2.w * il, mz = g0.z * iz;
+    const float an = fabsf(in_), al = fabsf(il), az = fabsf(iz);
+    const float en = fmaf(-g1.z, an, mn), el = fmaf(-g2.y, al, ml), ez = fmaf(-g2.y, az, mz);
+    const float tn = max3f(en, el, ez);
+    const float tf = min3f(fmaf(g1.z, an, mn), fmaf(g2.y, al, ml), fmaf(g2.y, az, mz));
+    const float pn = fmaxf(fmaf(-g2.x, al, ml), fmaf(-g2.x, az, mz));
+    const float xl = fmaf(g2.x, al, ml), xz = fmaf(g2.x, az, mz);
+    const float pf = fminf(xl, xz);
+    const float ta = fmaxf(tn, 0.f);
+    const bool in_open = pn < pf && ta > pn && ta < pf;
+    const bool hit = tn <= tf && tf >= 0.f && (!in_open || pf <= tf);
+    if (axis) {
+        // outer entry axis: largest entry time, lowest axis on ties; inner
+        // wall: the earlier prism exit, lateral on ties
+        const int oa = ez > fmaxf(en, el) ? 2 : (el > en ? 1 : 0);
+        *axis = in_open ? (xz < xl ? 4 : 3) : oa;
+    }
+    return hit ? (in_open ? pf : ta) : CUDART_INF_F;
+}
+
+__device__ __forceinline__ void gate_test(const float4& g0, const float4& g1, const float4& g2, float dx, float dy,
+                                          float iz, int slot, float& tb, int& bi) {
+    const float t = gate_t(g0, g1, g2, dx, dy, iz, nullptr);
+    if (t > 0.f && t < tb) { tb = t; bi = slot; }
+}
+
+// Sweep of the cylinder and gate sections of a list (ids from the sub-list
+// when sub is set).
+template <int RPT>
+__device__ __forceinline__ void cast_rest(const WList& L, const LCap& cap, int nck, int ngk, bool sub,
+                                          const float* dx, const float* dy, const float* dz, float* tb, int* bi) {
+    if (nck <= 0 && ngk <= 0) return;
+    float iz[RPT];
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) iz[r] = safe_rcp(dz[r]);
+    if (nck > 0) {
+        float ia[RPT];
+        bool vt[RPT];
+#pragma unroll
+        for (int r = 0; r < RPT; ++r) {
+            const float a = fmaf(dx[r], dx[r], dy[r] * dy[r]);
+            vt[r] = a < 1e-12f;
+            ia[r] = vt[r] ? 0.f : __frcp_rn(a);
+        }
+        const int base = cap.ns + cap.nb;
+        for (int j = 0; j < nck; ++j) {
+            const int k = sub ? L.sub[base + j] : j;
+            const float4 c0 = L.cyl[2 * k], c1 = L.cyl[2 * k + 1];
+#pragma unroll
+            for (int r = 0; r < RPT; ++r) cyl_test(c0, c1, dx[r], dy[r], ia[r], vt[r], iz[r], base + k, tb[r], bi[r]);
+        }
+    }
+    const int base = cap.ns + cap.nb + cap.nc;
+    for (int j = 0; j < ngk; ++j) {
+        const int k = sub ? L.sub[base + j] : j;
+        const float4 g0 = L.gat[3 * k], g1 = L.gat[3 * k + 1], g2 = L.gat[3 * k + 2];
+#pragma unroll
+        for (int r = 0; r < RPT; ++r) gate_test(g0, g1, g2, dx[r], dy[r], iz[r], base + k, tb[r], bi[r]);
+    }
+}
+
 // Sweep RPT rays per lane over a list.  tb holds each ray's best distance
 // (start: its clamp distance), bi the list slot of the best hit (spheres
-// 0.., boxes ns_max..).  Sphere: one dot product decides whether the ray
-// reaches the sphere (d.oc - sqrt(C) >= 0); only then is the near root found
-// (perpendicular-offset form) and compared with tb.  Box: slab times in
-// centre / half-extent form, t = c/d -+ h/|d|, entry = max, exit = min.
-template <int RPT>
-__device__ __forceinline__ void cast_list(const WList& L, const int4& meta, int ns_max, const float* dx,
+// 0.., boxes cap.ns.., cylinders and gates after).  Sphere: one dot product
+// decides whether the ray reaches the sphere (d.oc - sqrt(C) >= 0); only
+// then is the near root found (perpendicular-offset form) and compared with
+// tb.  Box: slab times in centre / half-extent form, t = c/d -+ h/|d|,
+// entry = max, exit = min.
+template <int RPT, bool EXTRA>
+__device__ __forceinline__ void cast_list(const WList& L, const int4& meta, const LCap& cap, const float* dx,
                                           const float* dy, const float* dz, float* tb, int* bi) {
     for (int k = 0; k < meta.x; ++k) {
         const float4 e = L.sph[k];
@@ -187,23 +354,31 @@ __device__ __forceinline__ void cast_list(const WList& L, const int4& meta, int 
         for (int k = 0; k < meta.y; ++k) {
             const float4 c = L.box[2 * k], h = L.box[2 * k + 1];
 #pragma unroll
-            for (int r = 0; r < RPT; ++r) box_test(c, h, ix[r], iy[r], iz[r], ns_max + k, tb[r], bi[r]);
+            for (int r = 0; r < RPT; ++r) box_test(c, h, ix[r], iy[r], iz[r], cap.ns + k, tb[r], bi[r]);
         }
     }
+    if (EXTRA && meta.w) cast_rest<RPT>(L, cap, meta.w & 0xffff, meta.w >> 16, false, dx, dy, dz, tb, bi);
 }
 
 // Second-level cull for one chunk of rays whose body directions lie in the
 // cone (axis cone.xyz, cos = cone.w, sin = sn); aw = R axis in the world.  A
-// sphere (or a box's bounding sphere) at oc with tangent length sC and radius
-// rho meets the cone iff oc.aw >= cos * sC - sin * rho (the angle to the axis
-// at most the half-angle plus the sphere's angular radius).  That form holds
-// while the two angles add up to at most pi, so a chunk whose half-angle
-// exceeds pi/2 (cos < 0) keeps every entry.  Writes the kept slots in index
-// order to L.sub (spheres from 0, boxes from ns_max); one full warp.
-__device__ inline int2 warp_sub_cull(const WList& L, const int4& meta, int ns_max, const float* aw, float cs,
+// sphere (or the bounding sphere of a box, cylinder or gate) at oc with
+// tangent length sC and radius rho meets the cone iff oc.aw >= cos * sC -
+// sin * rho (the angle to the axis at most the half-angle plus the sphere's
+// angular radius).  That form holds while the two angles add up to at most
+// pi, so a chunk whose half-angle exceeds pi/2 (cos < 0) keeps every entry.
+// Writes the kept slots in index order to L.sub (per kind from its slot
+// base); one full warp.  Returns the kept counts of the four kinds.
+__device__ __forceinline__ bool cone_keep_bound(const float4& c, float rho, const float* aw, float cs, float sn) {
+    return cs < 0.f || c.w < 0.f ||
+           fmaf(c.x, aw[0], fmaf(c.y, aw[1], fmaf(c.z, aw[2], fmaf(-cs, c.w, sn * rho)))) >= 0.f;
+}
+
+template <bool EXTRA>
+__device__ inline int4 warp_sub_cull(const WList& L, const int4& meta, const LCap& cap, const float* aw, float cs,
                                      float sn) {
     const int lane = threadIdx.x & 31;
-    int ns = 0, nb = 0;
+    int ns = 0, nb = 0, nc = 0, ng = 0;
     for (int base = 0; base < meta.x; base += 32) {
         const int k = base + lane;
         bool keep = false;
@@ -219,23 +394,34 @@ __device__ inline int2 warp_sub_cull(const WList& L, const int4& meta, int ns_ma
     for (int base = 0; base < meta.y; base += 32) {
         const int k = base + lane;
         bool keep = false;
-        if (k < meta.y) {
-            const float4 c = L.box[2 * k], h = L.box[2 * k + 1];
-            keep = cs < 0.f || c.w < 0.f ||
-                   fmaf(c.x, aw[0], fmaf(c.y, aw[1], fmaf(c.z, aw[2], fmaf(-cs, c.w, sn * h.w)))) >= 0.f;
-        }
+        if (k < meta.y) keep = cone_keep_bound(L.box[2 * k], L.box[2 * k + 1].w, aw, cs, sn);
         const unsigned bal = __ballot_sync(0xffffffffu, keep);
-        if (keep) L.sub[ns_max + nb + __popc(bal & ((1u << lane) - 1u))] = (short)k;
+        if (keep) L.sub[cap.ns + nb + __popc(bal & ((1u << lane) - 1u))] = (short)k;
         nb += __popc(bal);
     }
+    const int nck = EXTRA ? meta.w & 0xffff : 0, ngk = EXTRA ? meta.w >> 16 : 0;
+    for (int base = 0; base < nck; base += 32) {
+        const int k = base + lane;
+        const bool keep = k < nck && cone_keep_bound(L.cyl[2 * k], L.cyl[2 * k + 1].w, aw, cs, sn);
+        const unsigned bal = __ballot_sync(0xffffffffu, keep);
+        if (keep) L.sub[cap.ns + cap.nb + nc + __popc(bal & ((1u << lane) - 1u))] = (short)k;
+        nc += __popc(bal);
+    }
+    for (int base = 0; base < ngk; base += 32) {
+        const int k = base + lane;
+        const bool keep = k < ngk && cone_keep_bound(L.gat[3 * k], L.gat[3 * k + 1].w, aw, cs, sn);
+        const unsigned bal = __ballot_sync(0xffffffffu, keep);
+        if (keep) L.sub[cap.ns + cap.nb + cap.nc + ng + __popc(bal & ((1u << lane) - 1u))] = (short)k;
+        ng += __popc(bal);
+    }
     __syncwarp();
-    return make_int2(ns, nb);
+    return make_int4(ns, nb, nc, ng);
 }
 
 // Sweep RPT rays per lane over the chunk's sub-list (same tests and order as
 // cast_list, on the kept slots only).
-template <int RPT>
-__device__ __forceinline__ void cast_sub(const WList& L, const int2& n, int ns_max, const float* dx,
+template <int RPT, bool EXTRA>
+__device__ __forceinline__ void cast_sub(const WList& L, const int4& n, const LCap& cap, const float* dx,
                                          const float* dy, const float* dz, float* tb, int* bi) {
     for (int j = 0; j < n.x; ++j) {
         const int k = L.sub[j];
@@ -260,17 +446,19 @@ __device__ __forceinline__ void cast_sub(const WList& L, const int2& n, int ns_m
             ix[r] = safe_rcp(dx[r]); iy[r] = safe_rcp(dy[r]); iz[r] = safe_rcp(dz[r]);
         }
         for (int j = 0; j < n.y; ++j) {
-            const int k = L.sub[ns_max + j];
+            const int k = L.sub[cap.ns + j];
             const float4 c = L.box[2 * k], h = L.box[2 * k + 1];
 #pragma unroll
-            for (int r = 0; r < RPT; ++r) box_test(c, h, ix[r], iy[r], iz[r], ns_max + k, tb[r], bi[r]);
+            for (int r = 0; r < RPT; ++r) box_test(c, h, ix[r], iy[r], iz[r], cap.ns + k, tb[r], bi[r]);
         }
     }
+    if (EXTRA) cast_rest<RPT>(L, cap, n.z, n.w, true, dx, dy, dz, tb, bi);
 }
 
 // Slots of a chunk: the sub-cull of the chunk's cone (two-level culling,
 // cull > 1) or the whole list.  Returns the sub-list counts.
-__device__ __forceinline__ int2 chunk_slots(const WList& L, const int4& meta, int ns_max, const Sensor& sen,
+template <bool EXTRA>
+__device__ __forceinline__ int4 chunk_slots(const WList& L, const int4& meta, const LCap& cap, const Sensor& sen,
                                             int cull, int ch, const float* R) {
     const int lane = threadIdx.x & 31;
     if (cull > 1 && sen.cone) {
@@ -279,12 +467,15 @@ __device__ __forceinline__ int2 chunk_slots(const WList& L, const int4& meta, in
         const float aw[3] = {fmaf(R[0], cn.x, fmaf(R[1], cn.y, R[2] * cn.z)),
                              fmaf(R[3], cn.x, fmaf(R[4], cn.y, R[5] * cn.z)),
                              fmaf(R[6], cn.x, fmaf(R[7], cn.y, R[8] * cn.z))};
-        return warp_sub_cull(L, meta, ns_max, aw, cn.w, sn);
+        return warp_sub_cull<EXTRA>(L, meta, cap, aw, cn.w, sn);
     }
+    const int nck = EXTRA ? meta.w & 0xffff : 0, ngk = EXTRA ? meta.w >> 16 : 0;
     for (int k = lane; k < meta.x; k += 32) L.sub[k] = (short)k;
-    for (int k = lane; k < meta.y; k += 32) L.sub[ns_max + k] = (short)k;
+    for (int k = lane; k < meta.y; k += 32) L.sub[cap.ns + k] = (short)k;
+    for (int k = lane; k < nck; k += 32) L.sub[cap.ns + cap.nb + k] = (short)k;
+    for (int k = lane; k < ngk; k += 32) L.sub[cap.ns + cap.nb + cap.nc + k] = (short)k;
     __syncwarp();
-    return make_int2(meta.x, meta.y);
+    return make_int4(meta.x, meta.y, nck, ngk);
 }
 
 // Output index of table slot j (rays are stored in tile order when pix is set).
@@ -359,11 +550,12 @@ __device__ __forceinline__ float warp_sum12(const float* v) {
 
 // ------------------------------------------------------ map staging (TMA)
 // Stage the map block into shared memory with one cp.async.bulk (thread 0
-// issues and waits, bounded).  Returns false (and flags SIM_STATUS_TIMEOUT) if the bulk copy never landed.
-__device__ inline bool stage_map(const Args& a, unsigned char* sm, int map, int ns, int nb, uint32_t& phase,
-                          int* s_flag) {
+// issues and waits, bounded).  Returns false (and flags SIM_STATUS_TIMEOUT)
+// if the bulk copy never landed.
+__device__ inline bool stage_map(const Args& a, unsigned char* sm, int map, const MapView& mv, uint32_t& phase,
+                                 int* s_flag) {
     uint64_t* bar = reinterpret_cast<uint64_t*>(sm + a.sm.mbar);
-    const uint32_t bytes = (uint32_t)(ns + 2 * nb) * 16u;
+    const uint32_t bytes = (uint32_t)(mv.ns + 2 * (mv.nb + mv.nc + mv.ng)) * 16u;
     if (bytes == 0) return true;
     if (threadIdx.x == 0) {
         bulk_load(sm + a.sm.prim, a.prims + a.map_off[map], bytes, bar);
@@ -379,14 +571,28 @@ __device__ inline bool stage_map(const Args& a, unsigned char* sm, int map, int 
     return *s_flag != 0;
 }
 
+// Counts of the environment's map, with the block at prim (global or staged).
+__device__ __forceinline__ MapView map_view(const Args& a, int map, const float4* prim) {
+    MapView m;
+    m.prim = prim;
+    m.ns = a.map_ns[map];
+    m.nb = a.map_nb[map];
+    m.nc = a.map_nc ? a.map_nc[map] : 0;
+    m.ng = a.map_ng ? a.map_ng[map] : 0;
+    return m;
+}
+
 // ------------------------------------------------------------ ray adjoint
 // Cotangent of one ray's output w.r.t. the origin (go) and the world
 // direction, folded into the rotation cotangent gR += g_d (x) d_B.  Zero for a
-// miss, a clamped output or an origin inside the primitive.
-__device__ __forceinline__ void ray_vjp(const float4* prim, int ns, int id, const float* o, float dx, float dy,
-                                        float dz, const float4& db, const Sensor& sen, float g, float* go,
-                                        float* gR) {
+// miss, a clamped output or an origin inside the primitive.  With the hit
+// point's outward normal n: dt/do = -n / (n.d), dt/dd = -t n / (n.d).
+template <bool EXTRA>
+__device__ __forceinline__ void ray_vjp(const MapView& mv, int id, const float* o, float dx, float dy, float dz,
+                                        const float4& db, const Sensor& sen, float g, float* go, float* gR) {
     if (id < 0 || g == 0.f) return;
+    const float4* prim = mv.prim;
+    const int ns = mv.ns;
     const float d[3] = {dx, dy, dz};
     float t, n[3];
     if (id < ns) {
@@ -402,7 +608,7 @@ __device__ __forceinline__ void ray_vjp(const float4* prim, int ns, int id, cons
         const float ir = 1.f / s.w;
 #pragma unroll
         for (int k = 0; k < 3; ++k) n[k] = (t * d[k] - oc[k]) * ir;
-    } else {
+    } else if (id < ns + mv.nb) {
         const int b = id - ns;
         float c[3], h[3], tl[3];
         box_rel(prim[ns + 2 * b], prim[ns + 2 * b + 1], o, c, h);
@@ -421,6 +627,51 @@ __device__ __forceinline__ void ray_vjp(const float4* prim, int ns, int id, cons
         const int ax = x2 ? 2 : (x1 ? 1 : 0);
 #pragma unroll
         for (int k = 0; k < 3; ++k) n[k] = k == ax ? (d[k] > 0.f ? -1.f : 1.f) : 0.f;
+    } else if (!EXTRA) {
+        return;
+    } else if (id < ns + mv.nb + mv.nc) {
+        const float4 a0 = mv.cyl(id - ns - mv.nb)[0], a1 = mv.cyl(id - ns - mv.nb)[1];
+        const float hz = 0.5f * (a1.y - a1.x);
+        const float4 c0 = make_float4(a0.x - o[0], a0.y - o[1], 0.5f * (a1.x + a1.y) - o[2], 0.f);
+        const float4 c1 = make_float4(a0.z * a0.z, hz, 0.f, 0.f);
+        const float a = fmaf(dx, dx, dy * dy);
+        const bool vt = a < 1e-12f;
+        const float ia = vt ? 0.f : __frcp_rn(a), iz = safe_rcp(dz);
+        float tb = CUDART_INF_F;
+        int bi = -1;
+        cyl_test(c0, c1, dx, dy, ia, vt, iz, 0, tb, bi);
+        if (bi < 0) return;
+        t = tb;
+        // side or cap: the side entry is the later one
+        const float tm = fmaf(dx, c0.x, dy * c0.y) * ia;
+        const float fx = fmaf(-tm, dx, c0.x), fy = fmaf(-tm, dy, c0.y);
+        const float t0 = vt ? -CUDART_INF_F : tm - sqrtf(fmaxf((c1.x - fmaf(fx, fx, fy * fy)) * ia, 0.f));
+        const float tz0 = fmaf(-hz, fabsf(iz), c0.z * iz);
+        if (t0 >= tz0) {
+            const float ir = 1.f / a0.z;
+            n[0] = fmaf(t, dx, -c0.x) * ir; n[1] = fmaf(t, dy, -c0.y) * ir; n[2] = 0.f;
+        } else {
+            n[0] = 0.f; n[1] = 0.f; n[2] = dz > 0.f ? -1.f : 1.f;
+        }
+    } else {
+        const float4 a0 = mv.gate(id - ns - mv.nb - mv.nc)[0], a1 = mv.gate(id - ns - mv.nb - mv.nc)[1];
+        const float c[3] = {a0.x - o[0], a0.y - o[1], a0.z - o[2]};
+        const float4 g0 = make_float4(c[0], c[1], c[2], 0.f);
+        const float4 g1 = make_float4(a1.x, a1.y, a1.w, 0.f);
+        const float4 g2 = make_float4(a0.w, a0.w + a1.z, -fmaf(a1.x, c[0], a1.y * c[1]),
+                                      -fmaf(a1.x, c[1], -a1.y * c[0]));
+        int ax;
+        t = gate_t(g0, g1, g2, dx, dy, safe_rcp(dz), &ax);
+        if (!(t > 0.f) || t == CUDART_INF_F) return;
+        // local axis k (0 normal, 1 lateral, 2 up; walls 3 lateral, 4 up):
+        // outward normal -sign(d_k) e_k, rotated to the world
+        const int k = ax < 3 ? ax : ax - 2;
+        const float un = fmaf(a1.x, dx, a1.y * dy), ul = fmaf(a1.x, dy, -a1.y * dx);
+        const float dk = k == 0 ? un : (k == 1 ? ul : dz);
+        const float sg = dk > 0.f ? -1.f : 1.f;
+        n[0] = k == 0 ? sg * a1.x : (k == 1 ? -sg * a1.y : 0.f);
+        n[1] = k == 0 ? sg * a1.y : (k == 1 ? sg * a1.x : 0.f);
+        n[2] = k == 2 ? sg : 0.f;
     }
     const float fac = sen.kind == 0 ? db.w : 1.f;
     if (t * fac >= sen.range) return;

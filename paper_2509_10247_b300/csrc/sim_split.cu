@@ -37,8 +37,7 @@ __device__ __forceinline__ void step_agent(const Phys& c, float drag, float lam,
 // into groups of G = 32 / M' lanes (M' = M rounded up to a power of two),
 // group g scans the map for agent g at position p (lane g's p), then lane m
 // receives agent m's signed distance and arg-min (lowest id among ties).
-__device__ __forceinline__ void nearest_obstacle(const float4* prim, int ns, int nb, int M, const float* p,
-                                                 float& sd, int& id) {
+__device__ __forceinline__ void nearest_obstacle(const MapView& mv, int M, const float* p, float& sd, int& id) {
     const int lane = threadIdx.x & 31;
     int Mp = 1;
     while (Mp < M) Mp <<= 1;
@@ -48,9 +47,10 @@ __device__ __forceinline__ void nearest_obstacle(const float4* prim, int ns, int
                         __shfl_sync(0xffffffffu, p[2], gm)};
     float best = CUDART_INF_F;
     int bid = -1;
+    const int np = mv.count();
     if (gm < M)
-        for (int k = gl; k < ns + nb; k += G) {
-            const float d = sdf_prim(prim, ns, k, q);
+        for (int k = gl; k < np; k += G) {
+            const float d = sdf_prim(mv, k, q);
             if (d < best) { best = d; bid = k; }
         }
     for (int o = G >> 1; o > 0; o >>= 1) {
@@ -72,8 +72,7 @@ __global__ void __launch_bounds__(128) k_physics(const Args a) {
     if (env >= a.N) return;
     const int M = a.M, D = a.c.D, A = a.c.A, NM = a.NM;
     const int map = a.env_map[env];
-    const float4* prim = a.prims + a.map_off[map];
-    const int ns = a.map_ns[map], nb = a.map_nb[map];
+    const MapView mv = map_view(a, map, a.prims + a.map_off[map]);
     const bool on = lane < M;
     const int i = env * M + (on ? lane : 0);
     const float drag = a.drag_env ? a.drag_env[env] : a.c.drag;
@@ -85,6 +84,11 @@ __global__ void __launch_bounds__(128) k_physics(const Args a) {
         return;
     }
     int kpool = a.pool_k ? a.pool_k[env] : 0;
+    const bool racing = a.c.task == 1;
+    int gk = (racing && on) ? a.gate_k[i] : 0;
+    float bias[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) bias[k] = (a.imu && a.imu_noise && on) ? a.imu_bias[(size_t)i * 6 + k] : 0.f;
     for (int t = 0; t < a.T; ++t) {
         const size_t o = (size_t)t * NM + i;
         if (a.ckpt && (t % a.K) == 0) {
@@ -101,7 +105,7 @@ __global__ void __launch_bounds__(128) k_physics(const Args a) {
         step_agent(a.c, drag, lam, s, act, sp);
         float sd;
         int bid;
-        nearest_obstacle(prim, ns, nb, M, sp, sd, bid);
+        nearest_obstacle(mv, M, sp, sd, bid);
         // collisions and the dense / sparse rewards (Sec. III-C, III-E)
         bool col = sd < a.c.r_quad;
 #pragma unroll
@@ -119,28 +123,61 @@ __global__ void __launch_bounds__(128) k_physics(const Args a) {
         }
         const bool dn = a.c.terminate && __ballot_sync(0xffffffffu, on && col) != 0u;
         if (on) {
-            const float* tg = a.targets + 3 * (size_t)i;
-            const float e[3] = {sp[0] - tg[0], sp[1] - tg[1], sp[2] - tg[2]};
-            const float ne2 = dot3(e, e), ne = sqrtf(ne2);
-            const float pos = a.c.pos_sq ? ne2 : ne;
             const float ob = (a.c.w_obs != 0.f && sd < CUDART_INF_F) ? relu(a.c.d_safe - sd) : 0.f;
             float aa = 0.f;
 #pragma unroll
             for (int k = 0; k < 4; ++k)
                 if (k < A) aa += act[k] * act[k];
-            if (a.r_ctrl) a.r_ctrl[o] = -a.c.w_pos * pos - a.c.w_obs * ob * ob - a.c.w_act * aa - a.c.w_agent * pair;
-            if (a.r_goal) a.r_goal[o] = (int8_t)(col ? -1 : (ne < a.c.success_radius ? 1 : 0));
+            const float rest = -a.c.w_obs * ob * ob - a.c.w_act * aa - a.c.w_agent * pair;
+            if (racing) {
+                // progress towards the targeted gate; +1 for passing it
+                const float4 g0 = mv.gate(gk)[0], g1 = mv.gate(gk)[1];
+                const float e0[3] = {s[0] - g0.x, s[1] - g0.y, s[2] - g0.z};
+                const float e1[3] = {sp[0] - g0.x, sp[1] - g0.y, sp[2] - g0.z};
+                const bool passed = gate_passed(g0, g1, s, sp);
+                if (a.r_ctrl) a.r_ctrl[o] = a.c.w_pos * (sqrtf(dot3(e0, e0)) - sqrtf(dot3(e1, e1))) + rest;
+                if (a.r_goal) a.r_goal[o] = (int8_t)(col ? -1 : (passed ? 1 : 0));
+                if (a.gate_tape) a.gate_tape[o] = (int16_t)gk;
+                if (passed) gk = gk + 1 < mv.ng ? gk + 1 : 0;
+            } else {
+                const float* tg = a.targets + 3 * (size_t)i;
+                const float e[3] = {sp[0] - tg[0], sp[1] - tg[1], sp[2] - tg[2]};
+                const float ne2 = dot3(e, e), ne = sqrtf(ne2);
+                const float pos = a.c.pos_sq ? ne2 : ne;
+                if (a.r_ctrl) a.r_ctrl[o] = -a.c.w_pos * pos + rest;
+                if (a.r_goal) a.r_goal[o] = (int8_t)(col ? -1 : (ne < a.c.success_radius ? 1 : 0));
+            }
             if (a.sdf_tape) a.sdf_tape[o] = (int16_t)bid;
             if (a.done) a.done[o] = dn ? 1 : 0;
             if (a.done_tape) a.done_tape[o] = dn ? 1 : 0;
         }
+        float imu6[6];
+        if (a.imu && on && !dn) imu_eval(a.c, drag, s, act, sp, imu6);
         // termination and reset of the whole environment from the pool
         if (dn && a.c.P > 0) load_row(a.pool + ((size_t)(kpool % a.c.P) * NM + i) * D, D, on, a.c.model, s);
         else {
 #pragma unroll
             for (int k = 0; k < 16; ++k) s[k] = sp[k];
         }
-        if (dn) ++kpool;
+        if (dn) {
+            ++kpool;
+            gk = 0;
+        }
+        if (a.imu && on) {
+            if (dn) imu_reset(a.c, s, imu6);
+            if (a.imu_noise) {
+                const float* z = a.imu_noise + o * 12;
+                const float sdt = sqrtf(a.c.dt);
+#pragma unroll
+                for (int k = 0; k < 6; ++k) {
+                    if (dn) bias[k] = 0.f;
+                    imu6[k] += fmaf(a.c.imu_noise[k / 3], z[k], bias[k]);
+                    bias[k] = fmaf(a.c.imu_walk[k / 3] * sdt, z[6 + k], bias[k]);
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < 6; ++k) a.imu[o * 6 + k] = imu6[k];
+        }
         if (on) {
             bool fin = true;
 #pragma unroll
@@ -154,6 +191,10 @@ __global__ void __launch_bounds__(128) k_physics(const Args a) {
         for (int k = 0; k < 16; ++k)
             if (k < D) a.state[(size_t)i * D + k] = s[k];
     if (lane == 0 && a.pool_k) a.pool_k[env] = kpool;
+    if (racing && on) a.gate_k[i] = gk;
+    if (a.imu && a.imu_noise && on)
+#pragma unroll
+        for (int k = 0; k < 6; ++k) a.imu_bias[(size_t)i * 6 + k] = bias[k];
 }
 
 // ------------------------------------------------------------------ render
@@ -161,7 +202,7 @@ __global__ void __launch_bounds__(128) k_physics(const Args a) {
 // environment's map is staged once into shared memory; its T x M x S items
 // (step, agent, sensor) are taken by warps from a CTA ticket.  A warp culls
 // the map into its private list and sweeps all rays of the item.
-template <int RPT>
+template <int RPT, bool EXTRA>
 __global__ void __launch_bounds__(256, 4) k_render(const Args a) {
     extern __shared__ __align__(16) unsigned char sm[];
     __shared__ int s_env, s_flag, s_item;
@@ -169,7 +210,8 @@ __global__ void __launch_bounds__(256, 4) k_render(const Args a) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, NW = blockDim.x >> 5;
     const int M = a.M, S = a.S, NM = a.NM;
     const float4* prim = reinterpret_cast<const float4*>(sm + a.sm.prim);
-    const WList L = wlist_at(sm + a.sm.wlist + (size_t)warp * a.sm.wstride, a.ns_max, a.nb_max);
+    const LCap cap = cap_of(a);
+    const WList L = wlist_at(sm + a.sm.wlist + (size_t)warp * a.sm.wstride, cap);
     if (threadIdx.x < 4) s_cnt[threadIdx.x] = 0ull;
     if (threadIdx.x == 0) mbar_init(reinterpret_cast<uint64_t*>(sm + a.sm.mbar));
     __syncthreads();
@@ -192,8 +234,8 @@ __global__ void __launch_bounds__(256, 4) k_render(const Args a) {
         if (q >= a.N) break;
         const int env = a.order ? a.order[q] : q;
         const int map = a.env_map[env];
-        const int ns = a.map_ns[map], nb = a.map_nb[map];
-        if (!stage_map(a, sm, map, ns, nb, phase, &s_flag)) return;
+        const MapView mv = map_view(a, map, prim);
+        if (!stage_map(a, sm, map, mv, phase, &s_flag)) return;
         for (int it = warp; it < per_env; it = next_item(&s_item, lane)) {
             const int tm = it / per_tm, r = it - tm * per_tm;
             const int t = tm / M, m = tm - t * M;
@@ -207,7 +249,7 @@ __global__ void __launch_bounds__(256, 4) k_render(const Args a) {
             for (int k = 0; k < 3; ++k) o[k] = a.poses[ti * 12 + k];
 #pragma unroll
             for (int k = 0; k < 9; ++k) R[k] = a.poses[ti * 12 + 3 + k];
-            const int4 meta = warp_build_list(prim, ns, nb, o, R, sen, a.cull, L, a.ns_max);
+            const int4 meta = warp_build_list<EXTRA>(mv, o, R, sen, a.cull, L, cap);
             const size_t base = ti * sen.R;
             for (int ch = c0; ch < c1; ++ch) {
                 float dx[RPT], dy[RPT], dz[RPT], tb[RPT];
@@ -215,20 +257,20 @@ __global__ void __launch_bounds__(256, 4) k_render(const Args a) {
                 item_rays<RPT>(sen, R, ch, lane, dx, dy, dz, tb);
 #pragma unroll
                 for (int r = 0; r < RPT; ++r) bi[r] = -1;
-                int2 nsub = make_int2(meta.x, meta.y);
+                int4 nsub = make_int4(meta.x, meta.y, meta.w & 0xffff, meta.w >> 16);
                 if (meta.z < 0) {
                     if (a.cull > 1 && sen.cone) {
-                        nsub = chunk_slots(L, meta, a.ns_max, sen, a.cull, ch, R);
-                        cast_sub<RPT>(L, nsub, a.ns_max, dx, dy, dz, tb, bi);
+                        nsub = chunk_slots<EXTRA>(L, meta, cap, sen, a.cull, ch, R);
+                        cast_sub<RPT, EXTRA>(L, nsub, cap, dx, dy, dz, tb, bi);
                     } else {
-                        cast_list<RPT>(L, meta, a.ns_max, dx, dy, dz, tb, bi);
+                        cast_list<RPT, EXTRA>(L, meta, cap, dx, dy, dz, tb, bi);
                     }
                 }
                 if (a.counters && lane == 0) {
                     const unsigned long long nr = (unsigned long long)min(32 * RPT, sen.R - ch * 32 * RPT);
                     if (meta.z < 0) {
                         atomicAdd(&s_cnt[0], nr * (unsigned long long)nsub.x);
-                        atomicAdd(&s_cnt[1], nr * (unsigned long long)nsub.y);
+                        atomicAdd(&s_cnt[1], nr * (unsigned long long)(nsub.y + nsub.z + nsub.w));
                     }
                     atomicAdd(&s_cnt[2], nr);
                 }
@@ -263,7 +305,7 @@ __global__ void __launch_bounds__(256, 4) k_render(const Args a) {
 // sensor) reduce, in a fixed order, to the pose cotangent gposes[t][i] =
 // (d/d origin [3], d/d R [9]).  Zero when the step terminated (the state was
 // replaced).  Hit ids come from the rollout's tape or are re-cast.
-template <int RPT, bool TAPE>
+template <int RPT, bool TAPE, bool EXTRA>
 __global__ void __launch_bounds__(256, TAPE ? 4 : 3) k_render_vjp(const Args a) {
     extern __shared__ __align__(16) unsigned char sm[];
     __shared__ int s_env, s_flag, s_item;
@@ -271,8 +313,9 @@ __global__ void __launch_bounds__(256, TAPE ? 4 : 3) k_render_vjp(const Args a) 
     const int M = a.M, S = a.S, NM = a.NM;
     const float4* prim = reinterpret_cast<const float4*>(sm + a.sm.prim);
     constexpr bool recast = !TAPE;
+    const LCap cap = cap_of(a);
     WList L;
-    if (recast) L = wlist_at(sm + a.sm.wlist + (size_t)warp * a.sm.wstride, a.ns_max, a.nb_max);
+    if (recast) L = wlist_at(sm + a.sm.wlist + (size_t)warp * a.sm.wstride, cap);
     if (threadIdx.x == 0) mbar_init(reinterpret_cast<uint64_t*>(sm + a.sm.mbar));
     __syncthreads();
     uint32_t phase = 0;
@@ -292,8 +335,8 @@ __global__ void __launch_bounds__(256, TAPE ? 4 : 3) k_render_vjp(const Args a) 
         if (q >= a.N) break;
         const int env = a.order ? a.order[q] : q;
         const int map = a.env_map[env];
-        const int ns = a.map_ns[map], nb = a.map_nb[map];
-        if (!stage_map(a, sm, map, ns, nb, phase, &s_flag)) return;
+        const MapView mv = map_view(a, map, prim);
+        if (!stage_map(a, sm, map, mv, phase, &s_flag)) return;
         for (int it = warp; it < per_env; it = next_item(&s_item, lane)) {
             const int tm = it / P, part = it - tm * P;
             const int t = tm / M, m = tm - t * M;
@@ -322,12 +365,12 @@ __global__ void __launch_bounds__(256, TAPE ? 4 : 3) k_render_vjp(const Args a) 
                             if (id < 0) continue;
                             float d[3];
                             const float4 db = ray_dir(sen, R, j, d);
-                            ray_vjp(prim, ns, id, o, d[0], d[1], d[2], db, sen, sen.gout[base + ray], go, gR);
+                            ray_vjp<EXTRA>(mv, id, o, d[0], d[1], d[2], db, sen, sen.gout[base + ray], go, gR);
                         }
                         continue;
                     }
                     if (j0 >= j1) continue;
-                    const int4 meta = warp_build_list(prim, ns, nb, o, R, sen, a.cull, L, a.ns_max);
+                    const int4 meta = warp_build_list<EXTRA>(mv, o, R, sen, a.cull, L, cap);
                     const int chb = j0 / (32 * RPT), che = (j1 + 32 * RPT - 1) / (32 * RPT);
                     for (int ch = chb; ch < che; ++ch) {
                         float dx[RPT], dy[RPT], dz[RPT], tb[RPT];
@@ -337,17 +380,17 @@ __global__ void __launch_bounds__(256, TAPE ? 4 : 3) k_render_vjp(const Args a) 
                         for (int r = 0; r < RPT; ++r) bi[r] = -1;
                         if (meta.z < 0) {
                             if (a.cull > 1 && sen.cone) {
-                                const int2 nsub = chunk_slots(L, meta, a.ns_max, sen, a.cull, ch, R);
-                                cast_sub<RPT>(L, nsub, a.ns_max, dx, dy, dz, tb, bi);
+                                const int4 nsub = chunk_slots<EXTRA>(L, meta, cap, sen, a.cull, ch, R);
+                                cast_sub<RPT, EXTRA>(L, nsub, cap, dx, dy, dz, tb, bi);
                             } else {
-                                cast_list<RPT>(L, meta, a.ns_max, dx, dy, dz, tb, bi);
+                                cast_list<RPT, EXTRA>(L, meta, cap, dx, dy, dz, tb, bi);
                             }
                         }
 #pragma unroll
                         for (int r = 0; r < RPT; ++r) {
                             const int j = ch * 32 * RPT + r * 32 + lane;
                             if (j < j0 || j >= j1 || meta.z >= 0 || bi[r] < 0) continue;
-                            ray_vjp(prim, ns, L.id[bi[r]], o, dx[r], dy[r], dz[r], __ldg(sen.dir + j), sen,
+                            ray_vjp<EXTRA>(mv, L.id[bi[r]], o, dx[r], dy[r], dz[r], __ldg(sen.dir + j), sen,
                                     sen.gout[base + out_index(sen, j)], go, gR);
                         }
                     }
@@ -381,8 +424,7 @@ __global__ void __launch_bounds__(128) k_physics_bwd(const Args a) {
     const int M = a.M, D = a.c.D, A = a.c.A, NM = a.NM;
     float* seg = segm + (size_t)wid * (a.K + 1) * M * 16;
     const int map = a.env_map[env];
-    const float4* prim = a.prims + a.map_off[map];
-    const int ns = a.map_ns[map], nb = a.map_nb[map];
+    const MapView mv = map_view(a, map, a.prims + a.map_off[map]);
     const bool on = lane < M;
     const int i = env * M + (on ? lane : 0);
     const float drag = a.drag_env ? a.drag_env[env] : a.c.drag;
@@ -436,9 +478,9 @@ __global__ void __launch_bounds__(128) k_physics_bwd(const Args a) {
                     for (int k = 0; k < 12; ++k) gq[k] += a.gposes[(o * a.parts + pp) * 12 + k];
                 pose_vjp(a.c.model, s1, gq, gq + 3, g);
             }
-            float gp[16], gs[16], ga[4] = {0.f, 0.f, 0.f, 0.f};
+            float gp[16], gs[16], gsx[16], ga[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-            for (int k = 0; k < 16; ++k) { gp[k] = dn ? 0.f : g[k]; gs[k] = 0.f; }
+            for (int k = 0; k < 16; ++k) { gp[k] = dn ? 0.f : g[k]; gs[k] = 0.f; gsx[k] = 0.f; }
             // reward R_ctrl at the state before reset
             float sp[16];
             step_agent(a.c, drag, lam, s0, act, sp);
@@ -446,24 +488,39 @@ __global__ void __launch_bounds__(128) k_physics_bwd(const Args a) {
             if (a.sdf_tape) bid = on ? a.sdf_tape[o] : -1;
             else {
                 float sd;
-                nearest_obstacle(prim, ns, nb, M, sp, sd, bid);
+                nearest_obstacle(mv, M, sp, sd, bid);
             }
             const float gr = (on && a.g_r) ? a.g_r[o] : 0.f;
             if (on) {
-                const float* tg = a.targets + 3 * (size_t)i;
-                const float e[3] = {sp[0] - tg[0], sp[1] - tg[1], sp[2] - tg[2]};
-                const float ne = sqrtf(dot3(e, e));
+                if (a.c.task == 1) {
+                    // progress w_pos (|p_t - g| - |p_{t+1} - g|) towards the taped gate
+                    const float4 g0 = mv.gate(a.gate_tape[o])[0];
+                    const float e0[3] = {s0[0] - g0.x, s0[1] - g0.y, s0[2] - g0.z};
+                    const float e1[3] = {sp[0] - g0.x, sp[1] - g0.y, sp[2] - g0.z};
+                    const float n0 = sqrtf(dot3(e0, e0)), n1 = sqrtf(dot3(e1, e1));
+                    const float i0 = n0 > 0.f ? 1.f / n0 : 0.f, i1 = n1 > 0.f ? 1.f / n1 : 0.f;
 #pragma unroll
-                for (int k = 0; k < 3; ++k) {
-                    const float dpos = a.c.pos_sq ? 2.f * e[k] : (ne > 0.f ? e[k] / ne : 0.f);
-                    gp[k] += -gr * a.c.w_pos * dpos;
+                    for (int k = 0; k < 3; ++k) {
+                        gsx[k] += gr * a.c.w_pos * e0[k] * i0;
+                        gp[k] += -gr * a.c.w_pos * e1[k] * i1;
+                    }
+                } else {
+                    const float* tg = a.targets + 3 * (size_t)i;
+                    const float e[3] = {sp[0] - tg[0], sp[1] - tg[1], sp[2] - tg[2]};
+                    const float ne = sqrtf(dot3(e, e));
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) {
+                        const float dpos = a.c.pos_sq ? 2.f * e[k] : (ne > 0.f ? e[k] / ne : 0.f);
+                        gp[k] += -gr * a.c.w_pos * dpos;
+                    }
                 }
+                if (a.g_imu && !dn) imu_vjp(a.c, drag, s0, act, sp, a.g_imu + o * 6, gsx, gp, ga);
                 if (a.c.w_obs != 0.f && bid >= 0) {
-                    const float sd = sdf_prim(prim, ns, bid, sp);
+                    const float sd = sdf_prim(mv, bid, sp);
                     const float ob = relu(a.c.d_safe - sd);
                     if (ob > 0.f) {
                         float gsd[3];
-                        sdf_prim_grad(prim, ns, bid, sp, gsd);
+                        sdf_prim_grad(mv, bid, sp, gsd);
 #pragma unroll
                         for (int k = 0; k < 3; ++k) gp[k] += gr * 2.f * a.c.w_obs * ob * gsd[k];
                     }
@@ -494,7 +551,7 @@ __global__ void __launch_bounds__(128) k_physics_bwd(const Args a) {
                 for (int k = 0; k < 4; ++k)
                     if (k < A) a.g_a[o * A + k] = ga[k];
 #pragma unroll
-            for (int k = 0; k < 16; ++k) g[k] = gs[k];
+            for (int k = 0; k < 16; ++k) g[k] = gs[k] + gsx[k];
         }
         __syncwarp();
     }
@@ -532,41 +589,46 @@ cudaError_t launch_physics_bwd(const Args& a, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-template <int RPT>
+template <class K>
+static cudaError_t render_launch(K kernel, bool launch, const Args& a, int grid, int block, size_t smem,
+                                 cudaStream_t st, int* occ) {
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    if (!launch) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, kernel, block, smem);
+    kernel<<<grid, block, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+// EXTRA kernels read cylinders and gates; maps of spheres and boxes only use
+// the kernels compiled without that code.
+template <int RPT, bool EXTRA>
 static cudaError_t render_rpt(bool vjp, bool launch, const Args& a, int grid, int block, size_t smem,
                               cudaStream_t st, int* occ) {
-    cudaError_t e;
-    if (vjp && a.sen[0].tape) {  // taped hit ids: one kernel for every RPT
-        e = cudaFuncSetAttribute(k_render_vjp<1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        if (!launch) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k_render_vjp<1, true>, block, smem);
-        k_render_vjp<1, true><<<grid, block, smem, st>>>(a);
-    } else if (vjp) {
-        e = cudaFuncSetAttribute(k_render_vjp<RPT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        if (!launch) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k_render_vjp<RPT, false>, block, smem);
-        k_render_vjp<RPT, false><<<grid, block, smem, st>>>(a);
-    } else {
-        e = cudaFuncSetAttribute(k_render<RPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        if (!launch) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k_render<RPT>, block, smem);
-        k_render<RPT><<<grid, block, smem, st>>>(a);
+    if (vjp && a.sen[0].tape)  // taped hit ids: one kernel for every RPT
+        return render_launch(k_render_vjp<1, true, EXTRA>, launch, a, grid, block, smem, st, occ);
+    if (vjp) return render_launch(k_render_vjp<RPT, false, EXTRA>, launch, a, grid, block, smem, st, occ);
+    return render_launch(k_render<RPT, EXTRA>, launch, a, grid, block, smem, st, occ);
+}
+
+template <bool EXTRA>
+static cudaError_t render_sel(bool vjp, bool launch, int rpt, const Args& a, int grid, int block, size_t smem,
+                              cudaStream_t st, int* occ) {
+    switch (rpt) {
+        case 1: return render_rpt<1, EXTRA>(vjp, launch, a, grid, block, smem, st, occ);
+        case 2: return render_rpt<2, EXTRA>(vjp, launch, a, grid, block, smem, st, occ);
+        case 3: return render_rpt<3, EXTRA>(vjp, launch, a, grid, block, smem, st, occ);
+        case 4: return render_rpt<4, EXTRA>(vjp, launch, a, grid, block, smem, st, occ);
+        case 5: return render_rpt<5, EXTRA>(vjp, launch, a, grid, block, smem, st, occ);
+        case 6: return render_rpt<6, EXTRA>(vjp, launch, a, grid, block, smem, st, occ);
+        case 8: return render_rpt<8, EXTRA>(vjp, launch, a, grid, block, smem, st, occ);
+        default: return cudaErrorInvalidValue;
     }
-    return cudaGetLastError();
 }
 
 cudaError_t render_call(bool vjp, bool launch, int rpt, const Args& a, int grid, int block, size_t smem,
                         cudaStream_t st, int* occ) {
-    switch (rpt) {
-        case 1: return render_rpt<1>(vjp, launch, a, grid, block, smem, st, occ);
-        case 2: return render_rpt<2>(vjp, launch, a, grid, block, smem, st, occ);
-        case 3: return render_rpt<3>(vjp, launch, a, grid, block, smem, st, occ);
-        case 4: return render_rpt<4>(vjp, launch, a, grid, block, smem, st, occ);
-        case 5: return render_rpt<5>(vjp, launch, a, grid, block, smem, st, occ);
-        case 6: return render_rpt<6>(vjp, launch, a, grid, block, smem, st, occ);
-        case 8: return render_rpt<8>(vjp, launch, a, grid, block, smem, st, occ);
-        default: return cudaErrorInvalidValue;
-    }
+    if (a.nc_max > 0 || a.ng_max > 0) return render_sel<true>(vjp, launch, rpt, a, grid, block, smem, st, occ);
+    return render_sel<false>(vjp, launch, rpt, a, grid, block, smem, st, occ);
 }
 
 }  // namespace ds

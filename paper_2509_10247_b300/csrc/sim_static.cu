@@ -88,6 +88,7 @@ bool bad_cfg(const sim_config* c) {
     if (c->pool_size < 0 || c->cull < -1 || c->cull > 2) return true;
     if (c->warps_per_cta < 0 || c->warps_per_cta > 8) return true;
     if (c->rays_per_thread != 0 && !ds::rpt_supported(c->rays_per_thread)) return true;
+    if (c->task != SIM_TASK_REACH) return true;  // the reaching task only
     return false;
 }
 

@@ -80,7 +80,13 @@ def test_create_rejects_bad_config(lib, field, value, code):
 
 def test_create_rejects_reserved_and_rigid_params(lib):
     cfg = binding.make_config(synth.preset("pointmass_64env_depth16x9_10sph"))
-    cfg.reserved[2] = 1
+    cfg.reserved[0] = 1
+    assert _create_rc(lib, cfg)[0] == -1
+    cfg = binding.make_config(synth.preset("pointmass_64env_depth16x9_10sph"))
+    cfg.task = 2
+    assert _create_rc(lib, cfg)[0] == -1
+    cfg = binding.make_config(synth.preset("pointmass_64env_depth16x9_10sph"))
+    cfg.imu_walk[1] = -0.1
     assert _create_rc(lib, cfg)[0] == -1
     cfg = binding.make_config(synth.preset("rigid_4096env_depth64x48_40sph20box"))
     cfg.inertia[1] = 0.0
@@ -98,6 +104,12 @@ def test_null_pointers(lib):
     assert lib.sim_rollout(None, None, None, None, None, None, None, None) == -2
     assert lib.sim_backward(None, None, None, None, None, None, None, None) == -2
     assert lib.sim_set_scene(None, None, None, None, None, 0, None, None) == -2
+    assert lib.sim_set_scene_ex(None, None) == -2
+    assert lib.sim_rollout_ex(None, None, None) == -2
+    assert lib.sim_step_ex(None, None, None) == -2
+    assert lib.sim_backward_ex(None, None, None) == -2
+    assert lib.sim_get_gate_index(None, None, None) == -2
+    assert lib.sim_set_gate_index(None, None, None) == -2
     assert lib.sim_last_status(None, None, None) == -2
 
 

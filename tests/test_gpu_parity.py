@@ -28,6 +28,11 @@ WORKLOADS = {
                                         lidar=(4, 32, -15.0, 15.0, 10.0), map_counts=[(30, 15)], n_maps=5,
                                         obst_lo=(-6, -6, -6), obst_hi=(6, 6, 6), w_obs=5.0, pos_sq=0,
                                         terminate=1, ckpt_every=4),
+    "cyl_gate": lambda: synth.params(model="rigid", n_env=40, horizon=10, dt=0.01, cam=(16, 9, 90.0, 12.0),
+                                     lidar=(4, 48, -15.0, 15.0, 12.0),
+                                     map_counts=[(10, 5, 8, 4), (0, 0, 6, 6), (5, 0, 0, 3)], n_maps=3,
+                                     obst_lo=(-6, -6, -3), obst_hi=(6, 6, 3), race_radius=4.0, w_obs=5.0,
+                                     pos_sq=0, terminate=1, ckpt_every=4),
     "ragged": lambda: synth.params(n_env=37, n_agent=3, horizon=7, cam=(7, 5, 75.0, 9.0),
                                    map_counts=[(5, 3), (0, 4), (6, 0), (0, 0)], n_maps=4,
                                    w_obs=3.0, w_agent=2.0, d_agent=1.5, terminate=1, ckpt_every=3),
