@@ -155,9 +155,9 @@ __device__ __forceinline__ float warp_sum(float v) {
 // (centre oc relative to the origin, radius rho) before its clamp?
 __device__ __forceinline__ bool cull_keep(const Sensor& s, const float* R, const float* oc, float rho) {
     const float m = 1e-3f;
-    float L = sqrtf(dot3(oc, oc));
-    if (L <= rho + m) return true;
-    if (L - rho > s.maxlen + m) return false;
+    const float L2 = dot3(oc, oc), rin = rho + m, rout = s.maxlen + m + rho;
+    if (L2 <= rin * rin) return true;        // |oc| <= rho + m
+    if (L2 > rout * rout) return false;      // |oc| - rho > maxlen + m
     // body-frame centre c_B = R^T oc
     float bx = R[0] * oc[0] + R[3] * oc[1] + R[6] * oc[2];
     float by = R[1] * oc[0] + R[4] * oc[1] + R[7] * oc[2];
@@ -171,6 +171,7 @@ __device__ __forceinline__ bool cull_keep(const Sensor& s, const float* R, const
         if ((s.c1 * bx + bz) * s.c3 < -r) return false;
         return true;
     }
+    const float L = sqrtf(L2);
     float el = asinf(fminf(fmaxf(bz / L, -1.f), 1.f));
     float del = asinf(fminf(r / L, 1.f));
     return (el - del <= s.c1 + 1e-3f) && (el + del >= s.c0 - 1e-3f);

@@ -21,7 +21,7 @@ namespace ds {
 //   gat [ng][3] float4 (centre - o, bounding tangent), (cos yaw, sin yaw,
 //       half depth, bounding radius), (w, w + b, origin in local normal and
 //       lateral coordinates),
-//   sx  [ns] float2 (C, r),
+//   sx  [ns] float2 (r^2, r),
 //   id  [ns + nb + nc + ng] short (map primitive id of each slot; slots of
 //       boxes from ns, cylinders from ns + nb, gates from ns + nb + nc, with
 //       the capacities as the bases),
@@ -58,6 +58,15 @@ __device__ inline WList wlist_at(unsigned char* p, const LCap& c) {
     L.sub = L.id + c.ns + c.nb + c.nc + c.ng;
     L.meta = reinterpret_cast<int4*>(p + ((wlist_raw(c) + 15) & ~size_t(15)));
     return L;
+}
+
+// Square root by the hardware approximation (relative error about 2^-22,
+// exact at 0): the near-root of a ray-sphere hit needs no correct rounding
+// (its error, ~1e-7 r, is far inside the depth tolerance).
+__device__ __forceinline__ float sqrt_approx(float x) {
+    float r;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
 }
 
 __device__ __forceinline__ float min3f(float x, float y, float z) {
@@ -111,7 +120,7 @@ __device__ inline int4 warp_build_list(const MapView& mv, const float* o, const 
             if (C <= 0.f) inside = min(inside, k);
             keep = !cull || cull_keep(sen, R, oc, sp.w);
             e = make_float4(oc[0], oc[1], oc[2], -sqrtf(fmaxf(C, 0.f)));
-            x = make_float2(C, sp.w);
+            x = make_float2(r2, sp.w);
         }
         unsigned bal = __ballot_sync(0xffffffffu, keep);
         if (keep) {
@@ -136,8 +145,13 @@ __device__ inline int4 warp_build_list(const MapView& mv, const float* o, const 
             box_rel(bl, bh, o, c, h);
             const float rho = sqrtf(dot3(h, h));
             keep = !cull || cull_keep(sen, R, c, rho);
-            const float cb = dot3(c, c) - rho * rho;
-            cc = make_float4(c[0], c[1], c[2], cb > 0.f ? sqrtf(cb) : -1e30f);
+            // the bounding tangent serves only the chunk cones (cull > 1)
+            float tw = -1e30f;
+            if (cull > 1) {
+                const float cb = dot3(c, c) - rho * rho;
+                if (cb > 0.f) tw = sqrtf(cb);
+            }
+            cc = make_float4(c[0], c[1], c[2], tw);
             hh = make_float4(h[0], h[1], h[2], rho);
         }
         unsigned bal = __ballot_sync(0xffffffffu, keep);
@@ -216,12 +230,15 @@ __device__ inline int4 warp_build_list(const MapView& mv, const float* o, const 
 // given by its reciprocal direction: t = c/d -+ h/|d| per axis, entry = max,
 // exit = min; a hit in front of the origin nearer than tb replaces the best.
 // |1/d| enters as an operand modifier, so no absolute values are kept.
+// 0 <= tn < tb is one unsigned comparison of the bit patterns (a negative tn
+// has the sign bit set); tn = +0 means the origin is on the box, a case the
+// list's inside test has already taken.
 __device__ __forceinline__ void box_test(const float4& c, const float4& h, float ix, float iy, float iz, int slot,
                                          float& tb, int& bi) {
     const float mx = c.x * ix, my = c.y * iy, mz = c.z * iz;
     const float tn = max3f(fmaf(-h.x, fabsf(ix), mx), fmaf(-h.y, fabsf(iy), my), fmaf(-h.z, fabsf(iz), mz));
     const float tf = min3f(fmaf(h.x, fabsf(ix), mx), fmaf(h.y, fabsf(iy), my), fmaf(h.z, fabsf(iz), mz));
-    if (tn <= tf && tn > 0.f && tn < tb) { tb = tn; bi = slot; }
+    if (tn <= tf && __float_as_uint(tn) < __float_as_uint(tb)) { tb = tn; bi = slot; }
 }
 
 // Vertical capped cylinder (list entry c0 = axis centre - o and bounding
@@ -336,11 +353,11 @@ __device__ __forceinline__ void cast_list(const WList& L, const int4& meta, cons
         for (int r = 0; r < RPT; ++r) {
             const float v = fmaf(dx[r], e.x, fmaf(dy[r], e.y, fmaf(dz[r], e.z, e.w)));
             if (v >= 0.f) {
-                const float2 x = L.sx[k];
+                const float r2 = L.sx[k].x;
                 const float b = v - e.w;
                 const float fx = fmaf(-b, dx[r], e.x), fy = fmaf(-b, dy[r], e.y), fz = fmaf(-b, dz[r], e.z);
-                const float d2 = fmaxf(x.y * x.y - fmaf(fx, fx, fmaf(fy, fy, fz * fz)), 0.f);
-                const float t = b - sqrtf(d2);
+                const float d2 = fmaxf(r2 - fmaf(fx, fx, fmaf(fy, fy, fz * fz)), 0.f);
+                const float t = b - sqrt_approx(d2);
                 if (t < tb[r]) { tb[r] = t; bi[r] = k; }
             }
         }
@@ -430,11 +447,11 @@ __device__ __forceinline__ void cast_sub(const WList& L, const int4& n, const LC
         for (int r = 0; r < RPT; ++r) {
             const float v = fmaf(dx[r], e.x, fmaf(dy[r], e.y, fmaf(dz[r], e.z, e.w)));
             if (v >= 0.f) {
-                const float2 x = L.sx[k];
+                const float r2 = L.sx[k].x;
                 const float b = v - e.w;
                 const float fx = fmaf(-b, dx[r], e.x), fy = fmaf(-b, dy[r], e.y), fz = fmaf(-b, dz[r], e.z);
-                const float d2 = fmaxf(x.y * x.y - fmaf(fx, fx, fmaf(fy, fy, fz * fz)), 0.f);
-                const float t = b - sqrtf(d2);
+                const float d2 = fmaxf(r2 - fmaf(fx, fx, fmaf(fy, fy, fz * fz)), 0.f);
+                const float t = b - sqrt_approx(d2);
                 if (t < tb[r]) { tb[r] = t; bi[r] = k; }
             }
         }

@@ -66,6 +66,8 @@ __device__ __forceinline__ void nearest_obstacle(const MapView& mv, int M, const
 // ----------------------------------------------------------- forward physics
 // One warp per environment.  render_only: write the pose of the current
 // state at step 0 and return.
+// EXT: the racing task or the IMU readout is on (else their code is compiled out).
+template <bool EXT>
 __global__ void __launch_bounds__(128) k_physics(const Args a) {
     const int lane = threadIdx.x & 31;
     const int env = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -84,11 +86,12 @@ __global__ void __launch_bounds__(128) k_physics(const Args a) {
         return;
     }
     int kpool = a.pool_k ? a.pool_k[env] : 0;
-    const bool racing = a.c.task == 1;
+    const bool racing = EXT && a.c.task == 1;
+    const bool imu = EXT && a.imu;
     int gk = (racing && on) ? a.gate_k[i] : 0;
     float bias[6];
 #pragma unroll
-    for (int k = 0; k < 6; ++k) bias[k] = (a.imu && a.imu_noise && on) ? a.imu_bias[(size_t)i * 6 + k] : 0.f;
+    for (int k = 0; k < 6; ++k) bias[k] = (imu && a.imu_noise && on) ? a.imu_bias[(size_t)i * 6 + k] : 0.f;
     for (int t = 0; t < a.T; ++t) {
         const size_t o = (size_t)t * NM + i;
         if (a.ckpt && (t % a.K) == 0) {
@@ -152,7 +155,7 @@ __global__ void __launch_bounds__(128) k_physics(const Args a) {
             if (a.done_tape) a.done_tape[o] = dn ? 1 : 0;
         }
         float imu6[6];
-        if (a.imu && on && !dn) imu_eval(a.c, drag, s, act, sp, imu6);
+        if (imu && on && !dn) imu_eval(a.c, drag, s, act, sp, imu6);
         // termination and reset of the whole environment from the pool
         if (dn && a.c.P > 0) load_row(a.pool + ((size_t)(kpool % a.c.P) * NM + i) * D, D, on, a.c.model, s);
         else {
@@ -163,7 +166,7 @@ __global__ void __launch_bounds__(128) k_physics(const Args a) {
             ++kpool;
             gk = 0;
         }
-        if (a.imu && on) {
+        if (imu && on) {
             if (dn) imu_reset(a.c, s, imu6);
             if (a.imu_noise) {
                 const float* z = a.imu_noise + o * 12;
@@ -192,7 +195,7 @@ __global__ void __launch_bounds__(128) k_physics(const Args a) {
             if (k < D) a.state[(size_t)i * D + k] = s[k];
     if (lane == 0 && a.pool_k) a.pool_k[env] = kpool;
     if (racing && on) a.gate_k[i] = gk;
-    if (a.imu && a.imu_noise && on)
+    if (imu && a.imu_noise && on)
 #pragma unroll
         for (int k = 0; k < 6; ++k) a.imu_bias[(size_t)i * 6 + k] = bias[k];
 }
@@ -416,6 +419,7 @@ __global__ void __launch_bounds__(256, TAPE ? 4 : 3) k_render_vjp(const Args a) 
 // slice, then steps are reverted: pose cotangent -> state after the step
 // (cut by a reset), reward -> state before reset and action, dynamics ->
 // previous state.
+template <bool EXT>
 __global__ void __launch_bounds__(128) k_physics_bwd(const Args a) {
     extern __shared__ __align__(16) float segm[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -492,7 +496,7 @@ __global__ void __launch_bounds__(128) k_physics_bwd(const Args a) {
             }
             const float gr = (on && a.g_r) ? a.g_r[o] : 0.f;
             if (on) {
-                if (a.c.task == 1) {
+                if (EXT && a.c.task == 1) {
                     // progress w_pos (|p_t - g| - |p_{t+1} - g|) towards the taped gate
                     const float4 g0 = mv.gate(a.gate_tape[o])[0];
                     const float e0[3] = {s0[0] - g0.x, s0[1] - g0.y, s0[2] - g0.z};
@@ -514,7 +518,7 @@ __global__ void __launch_bounds__(128) k_physics_bwd(const Args a) {
                         gp[k] += -gr * a.c.w_pos * dpos;
                     }
                 }
-                if (a.g_imu && !dn) imu_vjp(a.c, drag, s0, act, sp, a.g_imu + o * 6, gsx, gp, ga);
+                if (EXT && a.g_imu && !dn) imu_vjp(a.c, drag, s0, act, sp, a.g_imu + o * 6, gsx, gp, ga);
                 if (a.c.w_obs != 0.f && bid >= 0) {
                     const float sd = sdf_prim(mv, bid, sp);
                     const float ob = relu(a.c.d_safe - sd);
@@ -566,7 +570,8 @@ constexpr int kPhysWarps = 4;
 
 cudaError_t launch_physics(const Args& a, cudaStream_t st) {
     const int blocks = (a.N + kPhysWarps - 1) / kPhysWarps;
-    k_physics<<<blocks, 32 * kPhysWarps, 0, st>>>(a);
+    if (a.c.task == 1 || a.imu) k_physics<true><<<blocks, 32 * kPhysWarps, 0, st>>>(a);
+    else k_physics<false><<<blocks, 32 * kPhysWarps, 0, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -583,9 +588,12 @@ cudaError_t launch_physics_bwd(const Args& a, cudaStream_t st) {
     int w;
     size_t smem;
     physics_bwd_shape(a.K, a.M, &w, &smem);
-    cudaError_t e = cudaFuncSetAttribute(k_physics_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const bool ext = a.c.task == 1 || a.g_imu;
+    cudaError_t e = cudaFuncSetAttribute(ext ? k_physics_bwd<true> : k_physics_bwd<false>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_physics_bwd<<<(a.N + w - 1) / w, 32 * w, smem, st>>>(a);
+    if (ext) k_physics_bwd<true><<<(a.N + w - 1) / w, 32 * w, smem, st>>>(a);
+    else k_physics_bwd<false><<<(a.N + w - 1) / w, 32 * w, smem, st>>>(a);
     return cudaGetLastError();
 }
 
