@@ -60,6 +60,27 @@ __device__ inline WList wlist_at(unsigned char* p, const LCap& c) {
     return L;
 }
 
+// Packed pairs of the lane's rays: sm_100-class FP32 pair instructions
+// (FFMA2 / FMUL2, each element rounded as its scalar counterpart, so results
+// are bit-identical to scalar code) halve the issue slots of the tests.
+template <int RPT>
+struct RayPairs {
+    static constexpr int NP = (RPT + 1) / 2;
+    float2 x[NP], y[NP], z[NP];
+    __device__ __forceinline__ RayPairs(const float* dx, const float* dy, const float* dz) {
+#pragma unroll
+        for (int p = 0; p < NP; ++p) {
+            const int r = 2 * p;
+            x[p] = make_float2(dx[r], r + 1 < RPT ? dx[r + 1] : 0.f);
+            y[p] = make_float2(dy[r], r + 1 < RPT ? dy[r + 1] : 0.f);
+            z[p] = make_float2(dz[r], r + 1 < RPT ? dz[r + 1] : 0.f);
+        }
+    }
+};
+
+__device__ __forceinline__ float2 f2(float v) { return make_float2(v, v); }
+__device__ __forceinline__ float lo_hi(const float2& v, int q) { return q ? v.y : v.x; }
+
 // Square root by the hardware approximation (relative error about 2^-22,
 // exact at 0): the near-root of a ray-sphere hit needs no correct rounding
 // (its error, ~1e-7 r, is far inside the depth tolerance).
@@ -302,6 +323,54 @@ __device__ __forceinline__ void gate_test(const float4& g0, const float4& g1, co
     if (t > 0.f && t < tb) { tb = t; bi = slot; }
 }
 
+// One sphere list entry against the lane's rays: the reach test
+// d.oc - sqrt(C) >= 0 on ray pairs, then the near root (perpendicular-offset
+// form) for the rays that reach it.
+template <int RPT>
+__device__ __forceinline__ void sphere_entry(const WList& L, int k, const RayPairs<RPT>& P, float* tb, int* bi) {
+    const float4 e = L.sph[k];
+#pragma unroll
+    for (int p = 0; p < RayPairs<RPT>::NP; ++p) {
+        const float2 v2 = __ffma2_rn(P.x[p], f2(e.x), __ffma2_rn(P.y[p], f2(e.y), __ffma2_rn(P.z[p], f2(e.z), f2(e.w))));
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int r = 2 * p + q;
+            if (r >= RPT) continue;
+            const float v = lo_hi(v2, q);
+            if (v >= 0.f) {
+                const float dxr = lo_hi(P.x[p], q), dyr = lo_hi(P.y[p], q), dzr = lo_hi(P.z[p], q);
+                const float r2 = L.sx[k].x;
+                const float b = v - e.w;
+                const float fx = fmaf(-b, dxr, e.x), fy = fmaf(-b, dyr, e.y), fz = fmaf(-b, dzr, e.z);
+                const float d2 = fmaxf(r2 - fmaf(fx, fx, fmaf(fy, fy, fz * fz)), 0.f);
+                const float t = b - sqrt_approx(d2);
+                if (t < tb[r]) { tb[r] = t; bi[r] = k; }
+            }
+        }
+    }
+}
+
+// Reciprocal directions of the lane's rays (from the packed pairs).
+template <int RPT>
+struct BoxRays {
+    float ix[RPT], iy[RPT], iz[RPT];
+    __device__ __forceinline__ explicit BoxRays(const RayPairs<RPT>& P) {
+#pragma unroll
+        for (int r = 0; r < RPT; ++r) {
+            ix[r] = safe_rcp(lo_hi(P.x[r / 2], r & 1));
+            iy[r] = safe_rcp(lo_hi(P.y[r / 2], r & 1));
+            iz[r] = safe_rcp(lo_hi(P.z[r / 2], r & 1));
+        }
+    }
+};
+
+template <int RPT>
+__device__ __forceinline__ void box_entry(const float4& c, const float4& h, const BoxRays<RPT>& B, int slot,
+                                          float* tb, int* bi) {
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) box_test(c, h, B.ix[r], B.iy[r], B.iz[r], slot, tb[r], bi[r]);
+}
+
 // Sweep of the cylinder and gate sections of a list (ids from the sub-list
 // when sub is set).
 template <int RPT>
@@ -347,32 +416,11 @@ __device__ __forceinline__ void cast_rest(const WList& L, const LCap& cap, int n
 template <int RPT, bool EXTRA>
 __device__ __forceinline__ void cast_list(const WList& L, const int4& meta, const LCap& cap, const float* dx,
                                           const float* dy, const float* dz, float* tb, int* bi) {
-    for (int k = 0; k < meta.x; ++k) {
-        const float4 e = L.sph[k];
-#pragma unroll
-        for (int r = 0; r < RPT; ++r) {
-            const float v = fmaf(dx[r], e.x, fmaf(dy[r], e.y, fmaf(dz[r], e.z, e.w)));
-            if (v >= 0.f) {
-                const float r2 = L.sx[k].x;
-                const float b = v - e.w;
-                const float fx = fmaf(-b, dx[r], e.x), fy = fmaf(-b, dy[r], e.y), fz = fmaf(-b, dz[r], e.z);
-                const float d2 = fmaxf(r2 - fmaf(fx, fx, fmaf(fy, fy, fz * fz)), 0.f);
-                const float t = b - sqrt_approx(d2);
-                if (t < tb[r]) { tb[r] = t; bi[r] = k; }
-            }
-        }
-    }
+    const RayPairs<RPT> P(dx, dy, dz);
+    for (int k = 0; k < meta.x; ++k) sphere_entry<RPT>(L, k, P, tb, bi);
     if (meta.y > 0) {
-        float ix[RPT], iy[RPT], iz[RPT];
-#pragma unroll
-        for (int r = 0; r < RPT; ++r) {
-            ix[r] = safe_rcp(dx[r]); iy[r] = safe_rcp(dy[r]); iz[r] = safe_rcp(dz[r]);
-        }
-        for (int k = 0; k < meta.y; ++k) {
-            const float4 c = L.box[2 * k], h = L.box[2 * k + 1];
-#pragma unroll
-            for (int r = 0; r < RPT; ++r) box_test(c, h, ix[r], iy[r], iz[r], cap.ns + k, tb[r], bi[r]);
-        }
+        const BoxRays<RPT> B(P);
+        for (int k = 0; k < meta.y; ++k) box_entry<RPT>(L.box[2 * k], L.box[2 * k + 1], B, cap.ns + k, tb, bi);
     }
     if (EXTRA && meta.w) cast_rest<RPT>(L, cap, meta.w & 0xffff, meta.w >> 16, false, dx, dy, dz, tb, bi);
 }
@@ -440,33 +488,13 @@ __device__ inline int4 warp_sub_cull(const WList& L, const int4& meta, const LCa
 template <int RPT, bool EXTRA>
 __device__ __forceinline__ void cast_sub(const WList& L, const int4& n, const LCap& cap, const float* dx,
                                          const float* dy, const float* dz, float* tb, int* bi) {
-    for (int j = 0; j < n.x; ++j) {
-        const int k = L.sub[j];
-        const float4 e = L.sph[k];
-#pragma unroll
-        for (int r = 0; r < RPT; ++r) {
-            const float v = fmaf(dx[r], e.x, fmaf(dy[r], e.y, fmaf(dz[r], e.z, e.w)));
-            if (v >= 0.f) {
-                const float r2 = L.sx[k].x;
-                const float b = v - e.w;
-                const float fx = fmaf(-b, dx[r], e.x), fy = fmaf(-b, dy[r], e.y), fz = fmaf(-b, dz[r], e.z);
-                const float d2 = fmaxf(r2 - fmaf(fx, fx, fmaf(fy, fy, fz * fz)), 0.f);
-                const float t = b - sqrt_approx(d2);
-                if (t < tb[r]) { tb[r] = t; bi[r] = k; }
-            }
-        }
-    }
+    const RayPairs<RPT> P(dx, dy, dz);
+    for (int j = 0; j < n.x; ++j) sphere_entry<RPT>(L, L.sub[j], P, tb, bi);
     if (n.y > 0) {
-        float ix[RPT], iy[RPT], iz[RPT];
-#pragma unroll
-        for (int r = 0; r < RPT; ++r) {
-            ix[r] = safe_rcp(dx[r]); iy[r] = safe_rcp(dy[r]); iz[r] = safe_rcp(dz[r]);
-        }
+        const BoxRays<RPT> B(P);
         for (int j = 0; j < n.y; ++j) {
             const int k = L.sub[cap.ns + j];
-            const float4 c = L.box[2 * k], h = L.box[2 * k + 1];
-#pragma unroll
-            for (int r = 0; r < RPT; ++r) box_test(c, h, ix[r], iy[r], iz[r], cap.ns + k, tb[r], bi[r]);
+            box_entry<RPT>(L.box[2 * k], L.box[2 * k + 1], B, cap.ns + k, tb, bi);
         }
     }
     if (EXTRA) cast_rest<RPT>(L, cap, n.z, n.w, true, dx, dy, dz, tb, bi);
@@ -604,6 +632,8 @@ __device__ __forceinline__ MapView map_view(const Args& a, int map, const float4
 // direction, folded into the rotation cotangent gR += g_d (x) d_B.  Zero for a
 // miss, a clamped output or an origin inside the primitive.  With the hit
 // point's outward normal n: dt/do = -n / (n.d), dt/dd = -t n / (n.d).
+// Quotients by the hardware approximation (a few ulp: the gradient's bar is
+// 1e-3 relative).
 template <bool EXTRA>
 __device__ __forceinline__ void ray_vjp(const MapView& mv, int id, const float* o, float dx, float dy, float dz,
                                         const float4& db, const Sensor& sen, float g, float* go, float* gR) {
@@ -621,8 +651,8 @@ __device__ __forceinline__ void ray_vjp(const MapView& mv, int id, const float* 
         const float b = dot3(d, oc);
         const float f[3] = {fmaf(-b, d[0], oc[0]), fmaf(-b, d[1], oc[1]), fmaf(-b, d[2], oc[2])};
         const float d2 = fmaxf(r2 - dot3(f, f), 0.f);
-        t = C / (b + sqrtf(d2));
-        const float ir = 1.f / s.w;
+        t = __fdividef(C, b + sqrt_approx(d2));
+        const float ir = __fdividef(1.f, s.w);
 #pragma unroll
         for (int k = 0; k < 3; ++k) n[k] = (t * d[k] - oc[k]) * ir;
     } else if (id < ns + mv.nb) {
@@ -665,7 +695,7 @@ __device__ __forceinline__ void ray_vjp(const MapView& mv, int id, const float* 
         const float t0 = vt ? -CUDART_INF_F : tm - sqrtf(fmaxf((c1.x - fmaf(fx, fx, fy * fy)) * ia, 0.f));
         const float tz0 = fmaf(-hz, fabsf(iz), c0.z * iz);
         if (t0 >= tz0) {
-            const float ir = 1.f / a0.z;
+            const float ir = __fdividef(1.f, a0.z);
             n[0] = fmaf(t, dx, -c0.x) * ir; n[1] = fmaf(t, dy, -c0.y) * ir; n[2] = 0.f;
         } else {
             n[0] = 0.f; n[1] = 0.f; n[2] = dz > 0.f ? -1.f : 1.f;
@@ -693,7 +723,7 @@ __device__ __forceinline__ void ray_vjp(const MapView& mv, int id, const float* 
     const float fac = sen.kind == 0 ? db.w : 1.f;
     if (t * fac >= sen.range) return;
     const float nd = dot3(n, d);
-    const float gt = g * fac / nd;
+    const float gt = __fdividef(g * fac, nd);
     const float db3[3] = {db.x, db.y, db.z};
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
