@@ -264,11 +264,13 @@ uint64_t morton2(uint32_t x, uint32_t y) {
 // frame): axis = normalised mean direction, half-angle = largest angle to
 // the axis + 2 mrad.  Tables are uploaded in that order with the output index
 // of every slot.  Returns the mean cone half-angle (rad).
+constexpr size_t kMortonMin = 0;  // grids above this many rays take Z order
+
 int build_tables(sim_handle* h, int s, double* mean_angle) {
     const int cs = 32 * h->rpt, W = h->img_w[s], H = h->img_h[s];
     std::vector<int> order((size_t)W * H);
     std::iota(order.begin(), order.end(), 0);
-    if ((size_t)W * H > 256)
+    if ((size_t)W * H > kMortonMin)
         std::stable_sort(order.begin(), order.end(), [W](int a, int b) {
             return morton2(a % W, a / W) < morton2(b % W, b / W);
         });

@@ -40,7 +40,7 @@ __device__ void build_lists(const Args& a, unsigned char* sm, const MapView& mv)
     const float* pose = reinterpret_cast<const float*>(sm + a.sm.pose);
     for (int Lx = warp; Lx < L; Lx += NW) {
         const float* o = pose + (Lx / a.S) * 12;
-        warp_build_list<false>(mv, o, o + 3, a.sen[Lx % a.S], a.cull, fused_list(a, sm, Lx), cap_of(a));
+        warp_build_list<false, false>(mv, o, o + 3, a.sen[Lx % a.S], a.cull, fused_list(a, sm, Lx), cap_of(a));
     }
 }
 

@@ -159,17 +159,16 @@ __device__ __forceinline__ bool cull_keep(const Sensor& s, const float* R, const
     if (L2 <= rin * rin) return true;        // |oc| <= rho + m
     if (L2 > rout * rout) return false;      // |oc| - rho > maxlen + m
     // body-frame centre c_B = R^T oc
-    float bx = R[0] * oc[0] + R[3] * oc[1] + R[6] * oc[2];
-    float by = R[1] * oc[0] + R[4] * oc[1] + R[7] * oc[2];
-    float bz = R[2] * oc[0] + R[5] * oc[1] + R[8] * oc[2];
-    float r = rho + m;
+    const float bx = fmaf(R[0], oc[0], fmaf(R[3], oc[1], R[6] * oc[2]));
+    const float by = fmaf(R[1], oc[0], fmaf(R[4], oc[1], R[7] * oc[2]));
+    const float bz = fmaf(R[2], oc[0], fmaf(R[5], oc[1], R[8] * oc[2]));
+    const float r = rin;
     if (s.kind == 0) {
-        // four side planes of the pinhole frustum through the origin
-        if ((s.c0 * bx - by) * s.c2 < -r) return false;
-        if ((s.c0 * bx + by) * s.c2 < -r) return false;
-        if ((s.c1 * bx - bz) * s.c3 < -r) return false;
-        if ((s.c1 * bx + bz) * s.c3 < -r) return false;
-        return true;
+        // four side planes of the pinhole frustum through the origin: signed
+        // distance (tan * x -+ y) / sqrt(1 + tan^2) = (c0 c2) x -+ c2 y
+        const float hx = s.c0 * s.c2 * bx, vx = s.c1 * s.c3 * bx;
+        return fmaf(-s.c2, by, hx) >= -r && fmaf(s.c2, by, hx) >= -r && fmaf(-s.c3, bz, vx) >= -r &&
+               fmaf(s.c3, bz, vx) >= -r;
     }
     const float L = sqrtf(L2);
     float el = asinf(fminf(fmaxf(bz / L, -1.f), 1.f));

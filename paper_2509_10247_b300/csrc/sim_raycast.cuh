@@ -121,36 +121,53 @@ __device__ __forceinline__ float safe_rcp(float d) {
 // index order within each kind (ties resolve to the lowest id).  Executed
 // by one full warp; returns the list's meta.  EXTRA: the map kinds include
 // cylinders and gates (else only spheres and boxes are read).
-template <bool EXTRA>
+template <bool EXTRA, bool PREP>
 __device__ inline int4 warp_build_list(const MapView& mv, const float* o, const float* R, const Sensor& sen,
                                        int cull, const WList& L, const LCap& cap) {
     const int lane = threadIdx.x & 31;
     const float4* prim = mv.prim;
     const int ns = mv.ns, nb = mv.nb;
     int inside = INT_MAX, cnt = 0;
-    for (int base = 0; base < ns; base += 32) {
-        const int k = base + lane;
-        bool keep = false;
-        float4 e = make_float4(0.f, 0.f, 0.f, 0.f);
-        float2 x = make_float2(0.f, 0.f);
+    const unsigned below = (1u << lane) - 1u;
+    // spheres two batches of 32 at a time (two independent dependency chains
+    // per lane), kept entries appended in index order
+    auto sphere_cand = [&](int k, bool& keep, float4& e, float2& x) {
+        keep = false;
+        e = make_float4(0.f, 0.f, 0.f, 0.f);
+        x = make_float2(0.f, 0.f);
         if (k < ns) {
-            float4 sp = prim[k];
-            float oc[3] = {sp.x - o[0], sp.y - o[1], sp.z - o[2]};
+            const float4 sp = prim[k];
+            const float oc[3] = {sp.x - o[0], sp.y - o[1], sp.z - o[2]};
             const float r2 = sp.w * sp.w;
             const float C = dot3(oc, oc) - r2;
             if (C <= 0.f) inside = min(inside, k);
             keep = !cull || cull_keep(sen, R, oc, sp.w);
-            e = make_float4(oc[0], oc[1], oc[2], -sqrtf(fmaxf(C, 0.f)));
+            e = make_float4(oc[0], oc[1], oc[2], -sqrt_approx(fmaxf(C, 0.f)));
             x = make_float2(r2, sp.w);
         }
-        unsigned bal = __ballot_sync(0xffffffffu, keep);
-        if (keep) {
-            int pos = cnt + __popc(bal & ((1u << lane) - 1u));
-            L.sph[pos] = e;
-            L.sx[pos] = x;
-            L.id[pos] = (short)k;
+    };
+    for (int base = 0; base < ns; base += 64) {
+        const int k0 = base + lane, k1 = base + 32 + lane;
+        bool keep0, keep1;
+        float4 e0, e1;
+        float2 x0, x1;
+        sphere_cand(k0, keep0, e0, x0);
+        sphere_cand(k1, keep1, e1, x1);
+        const unsigned b0 = __ballot_sync(0xffffffffu, keep0), b1 = __ballot_sync(0xffffffffu, keep1);
+        const int n0 = __popc(b0);
+        if (keep0) {
+            const int pos = cnt + __popc(b0 & below);
+            L.sph[pos] = e0;
+            L.sx[pos] = x0;
+            L.id[pos] = (short)k0;
         }
-        cnt += __popc(bal);
+        if (keep1) {
+            const int pos = cnt + n0 + __popc(b1 & below);
+            L.sph[pos] = e1;
+            L.sx[pos] = x1;
+            L.id[pos] = (short)k1;
+        }
+        cnt += n0 + __popc(b1);
     }
     const int nsk = cnt;
     cnt = 0;
@@ -160,11 +177,18 @@ __device__ inline int4 warp_build_list(const MapView& mv, const float* o, const 
         float4 cc = make_float4(0.f, 0.f, 0.f, 0.f), hh = cc;
         if (k < nb) {
             const float4 bl = prim[ns + 2 * k], bh = prim[ns + 2 * k + 1];
-            if (bl.x <= o[0] && bh.x >= o[0] && bl.y <= o[1] && bh.y >= o[1] && bl.z <= o[2] && bh.z >= o[2])
-                inside = min(inside, ns + k);
-            float c[3], h[3];
-            box_rel(bl, bh, o, c, h);
-            const float rho = sqrtf(dot3(h, h));
+            float c[3], h[3], rho;
+            if (PREP) {  // staged as (centre, radius), (half extents, 0)
+                c[0] = bl.x - o[0]; c[1] = bl.y - o[1]; c[2] = bl.z - o[2];
+                h[0] = bh.x; h[1] = bh.y; h[2] = bh.z;
+                rho = bl.w;
+                if (fabsf(c[0]) <= h[0] && fabsf(c[1]) <= h[1] && fabsf(c[2]) <= h[2]) inside = min(inside, ns + k);
+            } else {
+                if (bl.x <= o[0] && bh.x >= o[0] && bl.y <= o[1] && bh.y >= o[1] && bl.z <= o[2] && bh.z >= o[2])
+                    inside = min(inside, ns + k);
+                box_rel(bl, bh, o, c, h);
+                rho = sqrtf(dot3(h, h));
+            }
             keep = !cull || cull_keep(sen, R, c, rho);
             // the bounding tangent serves only the chunk cones (cull > 1)
             float tw = -1e30f;
@@ -616,6 +640,22 @@ __device__ inline bool stage_map(const Args& a, unsigned char* sm, int map, cons
     return *s_flag != 0;
 }
 
+// Rewrite the staged boxes of a map block from (min, 0), (max, 0) to
+// (centre, bounding radius), (half extents, 0), the form every list build
+// and ray adjoint of the CTA reads; one pass per environment instead of one
+// per (step, agent, sensor) item.  All threads; ends with a block barrier.
+__device__ inline void prep_boxes(unsigned char* sm, const Args& a, int ns, int nb) {
+    float4* prim = reinterpret_cast<float4*>(sm + a.sm.prim);
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+        const float4 lo = prim[ns + 2 * b], hi = prim[ns + 2 * b + 1];
+        const float h[3] = {0.5f * (hi.x - lo.x), 0.5f * (hi.y - lo.y), 0.5f * (hi.z - lo.z)};
+        prim[ns + 2 * b] = make_float4(0.5f * (lo.x + hi.x), 0.5f * (lo.y + hi.y), 0.5f * (lo.z + hi.z),
+                                       sqrtf(dot3(h, h)));
+        prim[ns + 2 * b + 1] = make_float4(h[0], h[1], h[2], 0.f);
+    }
+    __syncthreads();
+}
+
 // Counts of the environment's map, with the block at prim (global or staged).
 __device__ __forceinline__ MapView map_view(const Args& a, int map, const float4* prim) {
     MapView m;
@@ -657,8 +697,9 @@ __device__ __forceinline__ void ray_vjp(const MapView& mv, int id, const float* 
         for (int k = 0; k < 3; ++k) n[k] = (t * d[k] - oc[k]) * ir;
     } else if (id < ns + mv.nb) {
         const int b = id - ns;
-        float c[3], h[3], tl[3];
-        box_rel(prim[ns + 2 * b], prim[ns + 2 * b + 1], o, c, h);
+        const float4 bc = prim[ns + 2 * b], bh = prim[ns + 2 * b + 1];  // staged (centre, radius), (half, 0)
+        const float c[3] = {bc.x - o[0], bc.y - o[1], bc.z - o[2]}, h[3] = {bh.x, bh.y, bh.z};
+        float tl[3];
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
             const float iv = safe_rcp(d[k]);

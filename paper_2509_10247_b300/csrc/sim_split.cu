@@ -239,6 +239,7 @@ __global__ void __launch_bounds__(256, 4) k_render(const Args a) {
         const int map = a.env_map[env];
         const MapView mv = map_view(a, map, prim);
         if (!stage_map(a, sm, map, mv, phase, &s_flag)) return;
+        prep_boxes(sm, a, mv.ns, mv.nb);
         for (int it = warp; it < per_env; it = next_item(&s_item, lane)) {
             const int tm = it / per_tm, r = it - tm * per_tm;
             const int t = tm / M, m = tm - t * M;
@@ -252,7 +253,7 @@ __global__ void __launch_bounds__(256, 4) k_render(const Args a) {
             for (int k = 0; k < 3; ++k) o[k] = a.poses[ti * 12 + k];
 #pragma unroll
             for (int k = 0; k < 9; ++k) R[k] = a.poses[ti * 12 + 3 + k];
-            const int4 meta = warp_build_list<EXTRA>(mv, o, R, sen, a.cull, L, cap);
+            const int4 meta = warp_build_list<EXTRA, true>(mv, o, R, sen, a.cull, L, cap);
             const size_t base = ti * sen.R;
             for (int ch = c0; ch < c1; ++ch) {
                 float dx[RPT], dy[RPT], dz[RPT], tb[RPT];
@@ -340,6 +341,7 @@ __global__ void __launch_bounds__(256, TAPE ? 4 : 3) k_render_vjp(const Args a) 
         const int map = a.env_map[env];
         const MapView mv = map_view(a, map, prim);
         if (!stage_map(a, sm, map, mv, phase, &s_flag)) return;
+        prep_boxes(sm, a, mv.ns, mv.nb);
         for (int it = warp; it < per_env; it = next_item(&s_item, lane)) {
             const int tm = it / P, part = it - tm * P;
             const int t = tm / M, m = tm - t * M;
@@ -373,7 +375,7 @@ __global__ void __launch_bounds__(256, TAPE ? 4 : 3) k_render_vjp(const Args a) 
                         continue;
                     }
                     if (j0 >= j1) continue;
-                    const int4 meta = warp_build_list<EXTRA>(mv, o, R, sen, a.cull, L, cap);
+                    const int4 meta = warp_build_list<EXTRA, true>(mv, o, R, sen, a.cull, L, cap);
                     const int chb = j0 / (32 * RPT), che = (j1 + 32 * RPT - 1) / (32 * RPT);
                     for (int ch = chb; ch < che; ++ch) {
                         float dx[RPT], dy[RPT], dz[RPT], tb[RPT];
