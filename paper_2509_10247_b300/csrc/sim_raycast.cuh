@@ -129,86 +129,82 @@ __device__ inline int4 warp_build_list(const MapView& mv, const float* o, const 
     const int ns = mv.ns, nb = mv.nb;
     int inside = INT_MAX, cnt = 0;
     const unsigned below = (1u << lane) - 1u;
-    // spheres two batches of 32 at a time (two independent dependency chains
-    // per lane), kept entries appended in index order
-    auto sphere_cand = [&](int k, bool& keep, float4& e, float2& x) {
-        keep = false;
-        e = make_float4(0.f, 0.f, 0.f, 0.f);
-        x = make_float2(0.f, 0.f);
+    // Two passes per kind.  Pass 1 tests every primitive's bounding sphere
+    // against the field of view and appends the kept ids in index order;
+    // pass 2 builds the origin-relative entries of the kept ones only.  A
+    // primitive containing the origin is always kept (its bounding sphere
+    // contains the origin), so the inside test runs in pass 2.
+    for (int base = 0; base < ns; base += 32) {
+        const int k = base + lane;
+        bool keep = false;
         if (k < ns) {
             const float4 sp = prim[k];
             const float oc[3] = {sp.x - o[0], sp.y - o[1], sp.z - o[2]};
-            const float r2 = sp.w * sp.w;
-            const float C = dot3(oc, oc) - r2;
-            if (C <= 0.f) inside = min(inside, k);
             keep = !cull || cull_keep(sen, R, oc, sp.w);
-            e = make_float4(oc[0], oc[1], oc[2], -sqrt_approx(fmaxf(C, 0.f)));
-            x = make_float2(r2, sp.w);
         }
-    };
-    for (int base = 0; base < ns; base += 64) {
-        const int k0 = base + lane, k1 = base + 32 + lane;
-        bool keep0, keep1;
-        float4 e0, e1;
-        float2 x0, x1;
-        sphere_cand(k0, keep0, e0, x0);
-        sphere_cand(k1, keep1, e1, x1);
-        const unsigned b0 = __ballot_sync(0xffffffffu, keep0), b1 = __ballot_sync(0xffffffffu, keep1);
-        const int n0 = __popc(b0);
-        if (keep0) {
-            const int pos = cnt + __popc(b0 & below);
-            L.sph[pos] = e0;
-            L.sx[pos] = x0;
-            L.id[pos] = (short)k0;
-        }
-        if (keep1) {
-            const int pos = cnt + n0 + __popc(b1 & below);
-            L.sph[pos] = e1;
-            L.sx[pos] = x1;
-            L.id[pos] = (short)k1;
-        }
-        cnt += n0 + __popc(b1);
+        const unsigned bal = __ballot_sync(0xffffffffu, keep);
+        if (keep) L.id[cnt + __popc(bal & below)] = (short)k;
+        cnt += __popc(bal);
     }
     const int nsk = cnt;
+    __syncwarp();
+    for (int j = lane; j < nsk; j += 32) {
+        const int k = L.id[j];
+        const float4 sp = prim[k];
+        const float oc[3] = {sp.x - o[0], sp.y - o[1], sp.z - o[2]};
+        const float r2 = sp.w * sp.w;
+        const float C = dot3(oc, oc) - r2;
+        if (C <= 0.f) inside = min(inside, k);
+        L.sph[j] = make_float4(oc[0], oc[1], oc[2], -sqrt_approx(fmaxf(C, 0.f)));
+        L.sx[j] = make_float2(r2, sp.w);
+    }
     cnt = 0;
     for (int base = 0; base < nb; base += 32) {
         const int k = base + lane;
         bool keep = false;
-        float4 cc = make_float4(0.f, 0.f, 0.f, 0.f), hh = cc;
         if (k < nb) {
-            const float4 bl = prim[ns + 2 * k], bh = prim[ns + 2 * k + 1];
-            float c[3], h[3], rho;
+            const float4 bl = prim[ns + 2 * k];
+            float c[3], rho;
             if (PREP) {  // staged as (centre, radius), (half extents, 0)
                 c[0] = bl.x - o[0]; c[1] = bl.y - o[1]; c[2] = bl.z - o[2];
-                h[0] = bh.x; h[1] = bh.y; h[2] = bh.z;
                 rho = bl.w;
-                if (fabsf(c[0]) <= h[0] && fabsf(c[1]) <= h[1] && fabsf(c[2]) <= h[2]) inside = min(inside, ns + k);
             } else {
-                if (bl.x <= o[0] && bh.x >= o[0] && bl.y <= o[1] && bh.y >= o[1] && bl.z <= o[2] && bh.z >= o[2])
-                    inside = min(inside, ns + k);
-                box_rel(bl, bh, o, c, h);
+                float h[3];
+                box_rel(bl, prim[ns + 2 * k + 1], o, c, h);
                 rho = sqrtf(dot3(h, h));
             }
             keep = !cull || cull_keep(sen, R, c, rho);
-            // the bounding tangent serves only the chunk cones (cull > 1)
-            float tw = -1e30f;
-            if (cull > 1) {
-                const float cb = dot3(c, c) - rho * rho;
-                if (cb > 0.f) tw = sqrtf(cb);
-            }
-            cc = make_float4(c[0], c[1], c[2], tw);
-            hh = make_float4(h[0], h[1], h[2], rho);
         }
-        unsigned bal = __ballot_sync(0xffffffffu, keep);
-        if (keep) {
-            int pos = cnt + __popc(bal & ((1u << lane) - 1u));
-            L.box[2 * pos] = cc;
-            L.box[2 * pos + 1] = hh;
-            L.id[cap.ns + pos] = (short)(ns + k);
-        }
+        const unsigned bal = __ballot_sync(0xffffffffu, keep);
+        if (keep) L.id[cap.ns + cnt + __popc(bal & below)] = (short)(ns + k);
         cnt += __popc(bal);
     }
     const int nbk = cnt;
+    __syncwarp();
+    for (int j = lane; j < nbk; j += 32) {
+        const int k = L.id[cap.ns + j] - ns;
+        const float4 bl = prim[ns + 2 * k], bh = prim[ns + 2 * k + 1];
+        float c[3], h[3], rho;
+        if (PREP) {
+            c[0] = bl.x - o[0]; c[1] = bl.y - o[1]; c[2] = bl.z - o[2];
+            h[0] = bh.x; h[1] = bh.y; h[2] = bh.z;
+            rho = bl.w;
+            if (fabsf(c[0]) <= h[0] && fabsf(c[1]) <= h[1] && fabsf(c[2]) <= h[2]) inside = min(inside, ns + k);
+        } else {
+            if (bl.x <= o[0] && bh.x >= o[0] && bl.y <= o[1] && bh.y >= o[1] && bl.z <= o[2] && bh.z >= o[2])
+                inside = min(inside, ns + k);
+            box_rel(bl, bh, o, c, h);
+            rho = sqrtf(dot3(h, h));
+        }
+        // the bounding tangent serves only the chunk cones (cull > 1)
+        float tw = -1e30f;
+        if (cull > 1) {
+            const float cb = dot3(c, c) - rho * rho;
+            if (cb > 0.f) tw = sqrtf(cb);
+        }
+        L.box[2 * j] = make_float4(c[0], c[1], c[2], tw);
+        L.box[2 * j + 1] = make_float4(h[0], h[1], h[2], rho);
+    }
     int nck = 0, ngk = 0;
     for (int base = 0; EXTRA && base < mv.nc; base += 32) {
         const int k = base + lane;
