@@ -152,28 +152,47 @@ __device__ __forceinline__ float warp_sum(float v) {
 
 // ---------------------------------------------------------------- culling
 // Conservative test: can any ray of the sensor reach the bounding sphere
-// (centre oc relative to the origin, radius rho) before its clamp?
-__device__ __forceinline__ bool cull_keep(const Sensor& s, const float* R, const float* oc, float rho) {
-    const float m = 1e-3f;
-    const float L2 = dot3(oc, oc), rin = rho + m, rout = s.maxlen + m + rho;
-    if (L2 <= rin * rin) return true;        // |oc| <= rho + m
-    if (L2 > rout * rout) return false;      // |oc| - rho > maxlen + m
+// (centre oc relative to the origin, radius rho) before its clamp?  The
+// sensor's constants are gathered once per list (CullK), and the camera test
+// is evaluated without early exits (one predicate chain, no divergence).
+struct CullK {
+    float c2, c0c2, c3, c1c3;  // camera: frustum plane factors
+    float reach;               // longest unclamped ray + margin
+    float lo, hi;              // LiDAR elevation band (with margin)
+    int kind;
+};
+
+__device__ __forceinline__ CullK cull_consts(const Sensor& s) {
+    CullK k;
+    k.c2 = s.c2; k.c0c2 = s.c0 * s.c2; k.c3 = s.c3; k.c1c3 = s.c1 * s.c3;
+    k.reach = s.maxlen + 1e-3f;
+    k.lo = s.c0 - 1e-3f; k.hi = s.c1 + 1e-3f;
+    k.kind = s.kind;
+    return k;
+}
+
+__device__ __forceinline__ bool cull_keep(const CullK& s, const float* R, const float* oc, float rho) {
+    const float L2 = dot3(oc, oc), r = rho + 1e-3f, rout = s.reach + rho;
+    const bool near = L2 <= r * r;        // |oc| <= rho + m: the origin may be inside
+    const bool far = L2 > rout * rout;    // |oc| - rho > maxlen + m: beyond every ray
     // body-frame centre c_B = R^T oc
     const float bx = fmaf(R[0], oc[0], fmaf(R[3], oc[1], R[6] * oc[2]));
     const float by = fmaf(R[1], oc[0], fmaf(R[4], oc[1], R[7] * oc[2]));
     const float bz = fmaf(R[2], oc[0], fmaf(R[5], oc[1], R[8] * oc[2]));
-    const float r = rin;
     if (s.kind == 0) {
         // four side planes of the pinhole frustum through the origin: signed
         // distance (tan * x -+ y) / sqrt(1 + tan^2) = (c0 c2) x -+ c2 y
-        const float hx = s.c0 * s.c2 * bx, vx = s.c1 * s.c3 * bx;
-        return fmaf(-s.c2, by, hx) >= -r && fmaf(s.c2, by, hx) >= -r && fmaf(-s.c3, bz, vx) >= -r &&
-               fmaf(s.c3, bz, vx) >= -r;
+        const float hx = s.c0c2 * bx, vx = s.c1c3 * bx;
+        const bool in = (fmaf(-s.c2, by, hx) >= -r) & (fmaf(s.c2, by, hx) >= -r) & (fmaf(-s.c3, bz, vx) >= -r) &
+                        (fmaf(s.c3, bz, vx) >= -r);
+        return near | (!far & in);
     }
+    if (near) return true;
+    if (far) return false;
     const float L = sqrtf(L2);
-    float el = asinf(fminf(fmaxf(bz / L, -1.f), 1.f));
-    float del = asinf(fminf(r / L, 1.f));
-    return (el - del <= s.c1 + 1e-3f) && (el + del >= s.c0 - 1e-3f);
+    const float el = asinf(fminf(fmaxf(bz / L, -1.f), 1.f));
+    const float del = asinf(fminf(r / L, 1.f));
+    return (el - del <= s.hi) && (el + del >= s.lo);
 }
 
 }  // namespace ds

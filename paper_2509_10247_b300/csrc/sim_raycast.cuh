@@ -127,6 +127,7 @@ __device__ inline int4 warp_build_list(const MapView& mv, const float* o, const 
     const int lane = threadIdx.x & 31;
     const float4* prim = mv.prim;
     const int ns = mv.ns, nb = mv.nb;
+    const CullK ck = cull_consts(sen);
     int inside = INT_MAX, cnt = 0;
     const unsigned below = (1u << lane) - 1u;
     // Two passes per kind.  Pass 1 tests every primitive's bounding sphere
@@ -140,7 +141,7 @@ __device__ inline int4 warp_build_list(const MapView& mv, const float* o, const 
         if (k < ns) {
             const float4 sp = prim[k];
             const float oc[3] = {sp.x - o[0], sp.y - o[1], sp.z - o[2]};
-            keep = !cull || cull_keep(sen, R, oc, sp.w);
+            keep = !cull || cull_keep(ck, R, oc, sp.w);
         }
         const unsigned bal = __ballot_sync(0xffffffffu, keep);
         if (keep) L.id[cnt + __popc(bal & below)] = (short)k;
@@ -173,7 +174,7 @@ __device__ inline int4 warp_build_list(const MapView& mv, const float* o, const 
                 box_rel(bl, prim[ns + 2 * k + 1], o, c, h);
                 rho = sqrtf(dot3(h, h));
             }
-            keep = !cull || cull_keep(sen, R, c, rho);
+            keep = !cull || cull_keep(ck, R, c, rho);
         }
         const unsigned bal = __ballot_sync(0xffffffffu, keep);
         if (keep) L.id[cap.ns + cnt + __popc(bal & below)] = (short)(ns + k);
@@ -217,7 +218,7 @@ __device__ inline int4 warp_build_list(const MapView& mv, const float* o, const 
             const float r2 = a0.z * a0.z;
             if (fmaf(c[0], c[0], c[1] * c[1]) <= r2 && a1.x <= o[2] && a1.y >= o[2]) inside = min(inside, ns + nb + k);
             const float rho = sqrtf(fmaf(hz, hz, r2));
-            keep = !cull || cull_keep(sen, R, c, rho);
+            keep = !cull || cull_keep(ck, R, c, rho);
             const float cb = dot3(c, c) - rho * rho;
             c0 = make_float4(c[0], c[1], c[2], cb > 0.f ? sqrtf(cb) : -1e30f);
             c1 = make_float4(r2, hz, 0.f, rho);
@@ -243,7 +244,7 @@ __device__ inline int4 warp_build_list(const MapView& mv, const float* o, const 
             if (fabsf(un) <= a1.w && fabsf(ul) <= W && fabsf(uz) <= W && !(fabsf(ul) < a0.w && fabsf(uz) < a0.w))
                 inside = min(inside, ns + nb + mv.nc + k);
             const float rho = sqrtf(fmaf(a1.w, a1.w, 2.f * W * W));
-            keep = !cull || cull_keep(sen, R, c, rho);
+            keep = !cull || cull_keep(ck, R, c, rho);
             const float cb = dot3(c, c) - rho * rho;
             g0 = make_float4(c[0], c[1], c[2], cb > 0.f ? sqrtf(cb) : -1e30f);
             g1 = make_float4(a1.x, a1.y, a1.w, rho);
