@@ -8,10 +8,14 @@
 namespace gm {
 using namespace um;
 
-constexpr int STAGES = 4;
 constexpr uint32_t A_TILE = 16384, B_TILE = 32768, STAGE = A_TILE + B_TILE;
-constexpr uint32_t SMEM_LAUNCH = STAGES * STAGE + 1024 + 128;
+__host__ __device__ constexpr uint32_t smem_launch(int stages) { return stages * STAGE + 1024 + 128; }
 
+// STAGES: depth of the K ring.  A long K (the policy's layer 1) keeps four
+// stages in flight; a short K (the observation cotangent, K = 256) needs two,
+// which lets two CTAs share an SM so one CTA's epilogue overlaps another's
+// loads and MMAs.
+template <int STAGES>
 __global__ void __launch_bounds__(128, 1) k_gemm(const GemmArgs a) {
     extern __shared__ __align__(1024) uint8_t smraw[];
     const uint32_t raw = smem_u32(smraw);
@@ -74,7 +78,41 @@ __global__ void __launch_bounds__(128, 1) k_gemm(const GemmArgs a) {
     const bool all_ok = __syncthreads_and(mbar_wait(done, 0) && ok) != 0;
     tc_fence_after();
     const bool empty_k = kb1 <= kb0;  // no K-block: the accumulator holds nothing
-    if (all_ok) {
+    if (all_ok && a.epi == EPI_OBS_GRAD) {
+        // Observation cotangent: 64 accumulator columns at a time go through
+        // shared memory (the drained stage ring) so that the warp stores whole
+        // row segments (32 lanes on consecutive columns of one row) instead of
+        // one column per row.  Each warp stages and stores its own 32 rows.
+        fence_async_smem();
+        float* stg = reinterpret_cast<float*>(sm) + warp * 32 * 65;
+        const uint32_t tq = tmem + ((32u * (uint32_t)warp) << 16);
+        const int Rc = a.Rc, Rl = a.Rl;
+        for (uint32_t c0 = 0; c0 < Nt; c0 += 64) {
+            const uint32_t nc = min(64u, Nt - c0);
+            for (uint32_t cc = 0; cc < nc; cc += 16) {
+                float v[16];
+                tmem_ld16(tq + c0 + cc, v);
+#pragma unroll
+                for (int i = 0; i < 16; ++i) stg[lane * 65 + cc + i] = empty_k ? 0.f : v[i];
+            }
+            __syncwarp();
+            for (int rr = 0; rr < 32; ++rr) {
+                const int row = mt * 128 + 32 * warp + rr;
+                if (row >= a.M) break;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int cp = lane + 32 * h;
+                    if (cp >= (int)nc) continue;
+                    const int n = n0 + (int)c0 + cp;
+                    const float x = stg[rr * 65 + cp];
+                    if (n < 16) a.g_f[(size_t)row * 16 + n] = x;
+                    else if (n < 16 + Rc) a.g_cam[(size_t)row * Rc + (n - 16)] = x * a.cam_scale;
+                    else if (n < 16 + Rc + Rl) a.g_lid[(size_t)row * Rl + (n - 16 - Rc)] = x * a.lid_scale;
+                }
+            }
+            __syncwarp();
+        }
+    } else if (all_ok) {
         const uint32_t tq = tmem + ((32u * (uint32_t)warp) << 16);
         const int row = mt * 128 + 32 * warp + lane;
         const bool valid = row < a.M;
@@ -132,10 +170,15 @@ __global__ void __launch_bounds__(128, 1) k_gemm(const GemmArgs a) {
 cudaError_t launch_gemm(const GemmArgs& a, cudaStream_t st) {
     if (a.M <= 0 || a.N <= 0) return cudaSuccess;
     if (a.N % 16 || a.RA % 128 || a.RB < a.N || a.splits < 1) return cudaErrorInvalidValue;
-    cudaError_t e = cudaFuncSetAttribute(k_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_LAUNCH);
+    const int per_split = (a.nkb + a.splits - 1) / a.splits;
+    const bool shallow = per_split <= 8;
+    const uint32_t smem = smem_launch(shallow ? 2 : 4);
+    cudaError_t e = shallow ? cudaFuncSetAttribute(k_gemm<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+                            : cudaFuncSetAttribute(k_gemm<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const dim3 grid((a.M + 127) / 128, (a.N + 255) / 256, a.splits);
-    k_gemm<<<grid, 128, SMEM_LAUNCH, st>>>(a);
+    if (shallow) k_gemm<2><<<grid, 128, smem, st>>>(a);
+    else k_gemm<4><<<grid, 128, smem, st>>>(a);
     return cudaGetLastError();
 }
 

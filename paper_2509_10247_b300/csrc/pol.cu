@@ -40,23 +40,60 @@ __device__ __forceinline__ float feature(int m, int f, int N, int Rc, int Rl, co
     return 0.f;
 }
 
-// Thread (row m < Np, chunk c < Fp / 8): 8 features into X (rows = agents,
-// K = features) as one 16-byte chunk and into X^T (rows = features, K =
-// agents) as 8 elements.
-__global__ void k_obs_pack(int N, int Np, int Fp, int Rc, int Rl, const float* s, const float* tg,
-                           const float* dep, const float* lid, float cs, float ls, uint8_t* X, uint8_t* XT) {
-    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const int nch = Fp / 8;
-    if (idx >= (long long)Np * nch) return;
-    const int m = (int)(idx % Np), c = (int)(idx / Np);
-    uint16_t b[8];
+// Block: a tile of 64 agents x 64 features (one K-block).  Loads are
+// coalesced along each agent's observation row (16-feature spans, 16-byte
+// vector loads inside the depth and LiDAR blocks); the tile goes to X (rows =
+// agents, K = features) directly and, through shared memory, to X^T (rows =
+// features, K = agents) as whole 16-byte chunks of 8 agents.
+__global__ void __launch_bounds__(256) k_obs_pack(int N, int Np, int Fp, int Rc, int Rl, const float* s,
+                                                  const float* tg, const float* dep, const float* lid, float cs,
+                                                  float ls, uint8_t* X, uint8_t* XT) {
+    __shared__ uint16_t tile[64][72];
+    const int m0 = blockIdx.x * 64, f0 = blockIdx.y * 64;
+    const int t = threadIdx.x, r = t >> 2, c16 = (t & 3) * 16;
+    const int m = m0 + r, f = f0 + c16;
+    float v[16];
+    const float* src = nullptr;
+    float sc = 1.f;
+    // vector loads need 16-byte alignment of the row start and of the base
+    const bool dv = (Rc & 3) == 0 && ((uintptr_t)dep & 15) == 0;
+    const bool lv = (Rl & 3) == 0 && ((uintptr_t)lid & 15) == 0;
+    if (dv && m < N && f >= 16 && f + 16 <= 16 + Rc) {
+        src = dep + (size_t)m * Rc + (f - 16);
+        sc = cs;
+    } else if (lv && (Rc & 3) == 0 && m < N && f >= 16 + Rc && f + 16 <= 16 + Rc + Rl) {
+        src = lid + (size_t)m * Rl + (f - 16 - Rc);
+        sc = ls;
+    }
+    if (src) {
 #pragma unroll
-    for (int i = 0; i < 8; ++i) b[i] = tobf(feature(m, 8 * c + i, N, Rc, Rl, s, tg, dep, lid, cs, ls));
-    *reinterpret_cast<uint4*>(X + img_off(m, 8 * c, Np)) =
-        make_uint4(b[0] | (uint32_t)b[1] << 16, b[2] | (uint32_t)b[3] << 16, b[4] | (uint32_t)b[5] << 16,
-                   b[6] | (uint32_t)b[7] << 16);
+        for (int i = 0; i < 16; i += 4) {
+            const float4 x = __ldg(reinterpret_cast<const float4*>(src + i));
+            v[i] = __fmul_rn(x.x, sc); v[i + 1] = __fmul_rn(x.y, sc);
+            v[i + 2] = __fmul_rn(x.z, sc); v[i + 3] = __fmul_rn(x.w, sc);
+        }
+    } else {
 #pragma unroll
-    for (int i = 0; i < 8; ++i) *reinterpret_cast<uint16_t*>(XT + img_off(8 * c + i, m, Fp)) = b[i];
+        for (int i = 0; i < 16; ++i) v[i] = feature(m, f + i, N, Rc, Rl, s, tg, dep, lid, cs, ls);
+    }
+    uint16_t b[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) b[i] = tobf(v[i]);
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+        *reinterpret_cast<uint4*>(X + img_off(m, f + 8 * h, Np)) =
+            make_uint4(b[8 * h] | (uint32_t)b[8 * h + 1] << 16, b[8 * h + 2] | (uint32_t)b[8 * h + 3] << 16,
+                       b[8 * h + 4] | (uint32_t)b[8 * h + 5] << 16, b[8 * h + 6] | (uint32_t)b[8 * h + 7] << 16);
+#pragma unroll
+    for (int i = 0; i < 16; ++i) tile[r][c16 + i] = b[i];
+    __syncthreads();
+    for (int q = t; q < 512; q += 256) {
+        const int fr = q >> 3, a8 = (q & 7) * 8;
+        uint32_t w[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) w[j] = tile[a8 + 2 * j][fr] | (uint32_t)tile[a8 + 2 * j + 1][fr] << 16;
+        *reinterpret_cast<uint4*>(XT + img_off(f0 + fr, m0 + a8, Fp)) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
 }
 
 // Master parameters -> W1 image (rows = hidden units, K = features), its
@@ -366,9 +403,8 @@ int pol_act(pol_handle* h, const float* state, const float* targets, const float
     if ((h->Rc && !depth) || (h->Rl && !lidar)) return SIM_ERR_NULL_PTR;
     cudaStream_t st = (cudaStream_t)stream;
     h->last = st;
-    const long long nthr = (long long)h->Np * (h->Fp / 8);
-    pl::k_obs_pack<<<(unsigned)((nthr + 255) / 256), 256, 0, st>>>(h->N, h->Np, h->Fp, h->Rc, h->Rl, state, targets,
-                                                                  depth, lidar, h->cs, h->ls, h->d_X, h->d_XT);
+    pl::k_obs_pack<<<dim3((unsigned)(h->Np / 64), (unsigned)(h->Fp / 64)), 256, 0, st>>>(
+        h->N, h->Np, h->Fp, h->Rc, h->Rl, state, targets, depth, lidar, h->cs, h->ls, h->d_X, h->d_XT);
     PCK(cudaGetLastError());
     gm::GemmArgs g;
     memset(&g, 0, sizeof(g));
