@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--surr-epochs", type=int, default=3)
     ap.add_argument("--horizon", type=int, default=None, help="override the horizon (closed-loop workload)")
+    ap.add_argument("--policy-only", action="store_true",
+                    help="closed-loop workload: time the policy's act and backward on rendered observations only")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--n-env", type=int, default=None,
                     help="override the number of environments (profiling on a smaller case)")
@@ -506,6 +508,21 @@ def run_closed_loop(args, rank, world):
     act_ms = e0.elapsed_time(e1) / reps
     F = synth.policy_width(p)
     gemm_flop = 2.0 * N * F * 256
+    if args.policy_only:
+        g_a = torch.randn(N, 4, device=dev)
+        g_s = torch.zeros(N, 13, device=dev)
+        g_d, g_l = torch.empty_like(depth), torch.empty_like(lidar)
+        cl.pol.backward(g_a, g_s, g_d, g_l)
+        e0, e1 = ev(), ev()
+        e0.record()
+        for _ in range(reps):
+            cl.pol.backward(g_a, g_s, g_d, g_l)
+        e1.record()
+        torch.cuda.synchronize()
+        print(json.dumps({"metric": "policy act / backward ms at %d agents x %d features" % (N, F),
+                          "workload": CLOSED_LOOP_WORKLOAD, "act_ms": act_ms,
+                          "backward_ms": e0.elapsed_time(e1) / reps, "reps": reps}))
+        return
     clocks = Clocks(local)
     e0, e1 = ev(), ev()
     e0.record()

@@ -8,15 +8,21 @@
 namespace gm {
 using namespace um;
 
-constexpr uint32_t A_TILE = 16384, B_TILE = 32768, STAGE = A_TILE + B_TILE;
-__host__ __device__ constexpr uint32_t smem_launch(int stages) { return stages * STAGE + 1024 + 128; }
+constexpr uint32_t A_TILE = 16384;
+__host__ __device__ constexpr uint32_t stage_bytes(int bn) { return A_TILE + (uint32_t)bn * 128u; }
+__host__ __device__ constexpr uint32_t smem_launch(int stages, int bn) {
+    return stages * stage_bytes(bn) + 1024 + 128;
+}
 
-// STAGES: depth of the K ring.  A long K (the policy's layer 1) keeps four
-// stages in flight; a short K (the observation cotangent, K = 256) needs two,
-// which lets two CTAs share an SM so one CTA's epilogue overlaps another's
-// loads and MMAs.
-template <int STAGES>
+// STAGES: depth of the K ring; BN: columns of the n-tile (and of the tensor
+// memory the CTA holds).  A long K (the policy's layer 1, the weight
+// gradient) keeps four stages of 256-column tiles in flight; a short K (the
+// observation cotangent, K = 256) takes two stages of 128 columns, so three
+// CTAs share an SM (3 x 128 tensor-memory columns) and their epilogues
+// overlap one another's loads and MMAs.
+template <int STAGES, int BN>
 __global__ void __launch_bounds__(128, 1) k_gemm(const GemmArgs a) {
+    constexpr uint32_t STAGE = stage_bytes(BN);
     extern __shared__ __align__(1024) uint8_t smraw[];
     const uint32_t raw = smem_u32(smraw);
     uint8_t* sm = smraw + (((raw + 1023u) & ~1023u) - raw);
@@ -26,8 +32,8 @@ __global__ void __launch_bounds__(128, 1) k_gemm(const GemmArgs a) {
     uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 1);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int mt = blockIdx.x, nt = blockIdx.y, sp = blockIdx.z;
-    const int n0 = nt * 256;
-    const uint32_t Nt = (uint32_t)min(256, a.N - n0);
+    const int n0 = nt * BN;
+    const uint32_t Nt = (uint32_t)min(BN, a.N - n0);
     const int kb0 = (int)((long long)sp * a.nkb / a.splits), kb1 = (int)((long long)(sp + 1) * a.nkb / a.splits);
     const uint32_t bbytes = Nt * 128u;
     if (tid == 0) {
@@ -39,7 +45,7 @@ __global__ void __launch_bounds__(128, 1) k_gemm(const GemmArgs a) {
         fence_barrier_init();
     }
     __syncthreads();
-    if (warp == 0) tmem_alloc(tslot, 256);
+    if (warp == 0) tmem_alloc(tslot, BN);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -87,6 +93,8 @@ __global__ void __launch_bounds__(128, 1) k_gemm(const GemmArgs a) {
         float* stg = reinterpret_cast<float*>(sm) + warp * 32 * 65;
         const uint32_t tq = tmem + ((32u * (uint32_t)warp) << 16);
         const int Rc = a.Rc, Rl = a.Rl;
+        const bool vec4 = (Rc & 3) == 0 && (Rl & 3) == 0 && ((uintptr_t)a.g_f & 15) == 0 &&
+                          ((uintptr_t)a.g_cam & 15) == 0 && ((uintptr_t)a.g_lid & 15) == 0;
         for (uint32_t c0 = 0; c0 < Nt; c0 += 64) {
             const uint32_t nc = min(64u, Nt - c0);
             for (uint32_t cc = 0; cc < nc; cc += 16) {
@@ -96,18 +104,43 @@ __global__ void __launch_bounds__(128, 1) k_gemm(const GemmArgs a) {
                 for (int i = 0; i < 16; ++i) stg[lane * 65 + cc + i] = empty_k ? 0.f : v[i];
             }
             __syncwarp();
-            for (int rr = 0; rr < 32; ++rr) {
-                const int row = mt * 128 + 32 * warp + rr;
-                if (row >= a.M) break;
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int cp = lane + 32 * h;
-                    if (cp >= (int)nc) continue;
+            if (vec4) {
+                // two rows per pass, 16 lanes x 4 consecutive columns each:
+                // 16-byte stores (every region starts at a multiple of 4)
+                for (int it = 0; it < 16; ++it) {
+                    const int rr = 2 * it + (lane >> 4), cp = (lane & 15) * 4;
+                    const int row = mt * 128 + 32 * warp + rr;
+                    if (row >= a.M || cp >= (int)nc) continue;
                     const int n = n0 + (int)c0 + cp;
-                    const float x = stg[rr * 65 + cp];
-                    if (n < 16) a.g_f[(size_t)row * 16 + n] = x;
-                    else if (n < 16 + Rc) a.g_cam[(size_t)row * Rc + (n - 16)] = x * a.cam_scale;
-                    else if (n < 16 + Rc + Rl) a.g_lid[(size_t)row * Rl + (n - 16 - Rc)] = x * a.lid_scale;
+                    float4 x = make_float4(stg[rr * 65 + cp], stg[rr * 65 + cp + 1], stg[rr * 65 + cp + 2],
+                                           stg[rr * 65 + cp + 3]);
+                    float* dst;
+                    if (n < 16) dst = a.g_f + (size_t)row * 16 + n;
+                    else if (n < 16 + Rc) {
+                        dst = a.g_cam + (size_t)row * Rc + (n - 16);
+                        x = make_float4(x.x * a.cam_scale, x.y * a.cam_scale, x.z * a.cam_scale, x.w * a.cam_scale);
+                    } else if (n < 16 + Rc + Rl) {
+                        dst = a.g_lid + (size_t)row * Rl + (n - 16 - Rc);
+                        x = make_float4(x.x * a.lid_scale, x.y * a.lid_scale, x.z * a.lid_scale, x.w * a.lid_scale);
+                    } else {
+                        continue;
+                    }
+                    *reinterpret_cast<float4*>(dst) = x;
+                }
+            } else {
+                for (int rr = 0; rr < 32; ++rr) {
+                    const int row = mt * 128 + 32 * warp + rr;
+                    if (row >= a.M) break;
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int cp = lane + 32 * h;
+                        if (cp >= (int)nc) continue;
+                        const int n = n0 + (int)c0 + cp;
+                        const float x = stg[rr * 65 + cp];
+                        if (n < 16) a.g_f[(size_t)row * 16 + n] = x;
+                        else if (n < 16 + Rc) a.g_cam[(size_t)row * Rc + (n - 16)] = x * a.cam_scale;
+                        else if (n < 16 + Rc + Rl) a.g_lid[(size_t)row * Rl + (n - 16 - Rc)] = x * a.lid_scale;
+                    }
                 }
             }
             __syncwarp();
@@ -163,23 +196,26 @@ __global__ void __launch_bounds__(128, 1) k_gemm(const GemmArgs a) {
     __syncthreads();
     if (warp == 0) {
         tc_fence_after();
-        tmem_dealloc(tmem, 256);
+        tmem_dealloc(tmem, BN);
     }
+}
+
+template <int STAGES, int BN>
+static cudaError_t launch_shape(const GemmArgs& a, cudaStream_t st) {
+    const uint32_t smem = smem_launch(STAGES, BN);
+    cudaError_t e = cudaFuncSetAttribute(k_gemm<STAGES, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const dim3 grid((a.M + 127) / 128, (a.N + BN - 1) / BN, a.splits);
+    k_gemm<STAGES, BN><<<grid, 128, smem, st>>>(a);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_gemm(const GemmArgs& a, cudaStream_t st) {
     if (a.M <= 0 || a.N <= 0) return cudaSuccess;
     if (a.N % 16 || a.RA % 128 || a.RB < a.N || a.splits < 1) return cudaErrorInvalidValue;
     const int per_split = (a.nkb + a.splits - 1) / a.splits;
-    const bool shallow = per_split <= 8;
-    const uint32_t smem = smem_launch(shallow ? 2 : 4);
-    cudaError_t e = shallow ? cudaFuncSetAttribute(k_gemm<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
-                            : cudaFuncSetAttribute(k_gemm<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    const dim3 grid((a.M + 127) / 128, (a.N + 255) / 256, a.splits);
-    if (shallow) k_gemm<2><<<grid, 128, smem, st>>>(a);
-    else k_gemm<4><<<grid, 128, smem, st>>>(a);
-    return cudaGetLastError();
+    if (per_split <= 8) return launch_shape<2, 128>(a, st);
+    return launch_shape<4, 256>(a, st);
 }
 
 }  // namespace gm
