@@ -210,6 +210,23 @@ def run_reference(args, rank, world):
 
 
 # ------------------------------------------------------------- our arm
+def max_over_ranks(ms, world, device=None):
+    """The job's time: the slowest rank's (all ranks receive it)."""
+    if world == 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(n_env_per_rank, horizon, steps, world, ms):
+    """Whole-job env-steps/s: every rank simulates its own n_env environments
+    (weak scaling), so the job does world times the work in the max time."""
+    return n_env_per_rank * horizon * steps * world / (ms / 1e3)
+
+
 def run_ours(args, rank, world):
     import torch
     from paper_2509_10247_b300 import build as B, synth
@@ -279,17 +296,12 @@ def run_ours(args, rank, world):
     ck = clocks.stop() if clocks else None
     kt = sim.kernel_times(reset=True)
     sim.profile(False)
-    ms = t_start.elapsed_time(t_end)
-    if world > 1:
-        tt = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        ms = tt.item()
+    ms = max_over_ranks(t_start.elapsed_time(t_end), world, dev)
     fwd_ms = statistics.mean(e[0].elapsed_time(e[1]) for e in evs)
     bwd_ms = statistics.mean(e[1].elapsed_time(e[2]) for e in evs)
     if sim.status() != 0:
         raise RuntimeError("device status flagged during the timed region")
-    env_steps = p["n_env"] * T * args.steps * world
-    value = env_steps / (ms / 1e3)
+    value = job_throughput(p["n_env"], T, args.steps, world, ms)
     rays_per_step = NM * (Rc + sim.Rl) * T  # per rollout launch
     grays = rays_per_step * args.steps * world / (ms / 1e3) / 1e9
     launches = sum(n for _, n in kt.values())
