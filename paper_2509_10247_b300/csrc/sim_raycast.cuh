@@ -547,6 +547,16 @@ __device__ __forceinline__ int4 chunk_slots(const WList& L, const int4& meta, co
 // Output index of table slot j (rays are stored in tile order when pix is set).
 __device__ __forceinline__ int out_index(const Sensor& sen, int j) { return sen.pix ? __ldg(sen.pix + j) : j; }
 
+// Quotient n / d of small non-negative integers (n < 2^21, 0 < d < 2^10)
+// through single precision: (n + 0.5) / d is at least 0.5 / d away from an
+// integer and the approximate float quotient (2 ulp) errs by less than
+// n 2^-22 / d, so its truncation is exact; larger n fall back to integer
+// division.
+__device__ __forceinline__ int div_small(int n, int d) {
+    if (n >= (1 << 21) || d >= (1 << 10)) return n / d;
+    return (int)__fdividef((float)n + 0.5f, (float)d);
+}
+
 // Next work item of the warp from a shared ticket (dynamic balance).
 __device__ __forceinline__ int next_item(int* ticket, int lane) {
     int v = 0;

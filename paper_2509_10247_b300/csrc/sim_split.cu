@@ -241,10 +241,10 @@ __global__ void __launch_bounds__(256, 4) k_render(const Args a) {
         if (!stage_map(a, sm, map, mv, phase, &s_flag)) return;
         prep_boxes(sm, a, mv.ns, mv.nb);
         for (int it = warp; it < per_env; it = next_item(&s_item, lane)) {
-            const int tm = it / per_tm, r = it - tm * per_tm;
-            const int t = tm / M, m = tm - t * M;
+            const int tm = div_small(it, per_tm), r = it - tm * per_tm;
+            const int t = div_small(tm, M), m = tm - t * M;
             const int si = r < P0 ? 0 : 1, part = si ? r - P0 : r, np = si ? P1 : P0, nchs = si ? nch1 : nch0;
-            const int c0 = part * nchs / np, c1 = (part + 1) * nchs / np;
+            const int c0 = div_small(part * nchs, np), c1 = div_small((part + 1) * nchs, np);
             const Sensor& sen = a.sen[si];
             if (!sen.out && !sen.tape) continue;
             const size_t ti = (size_t)t * NM + env * M + m;
@@ -343,8 +343,8 @@ __global__ void __launch_bounds__(256, TAPE ? 4 : 3) k_render_vjp(const Args a) 
         if (!stage_map(a, sm, map, mv, phase, &s_flag)) return;
         prep_boxes(sm, a, mv.ns, mv.nb);
         for (int it = warp; it < per_env; it = next_item(&s_item, lane)) {
-            const int tm = it / P, part = it - tm * P;
-            const int t = tm / M, m = tm - t * M;
+            const int tm = div_small(it, P), part = it - tm * P;
+            const int t = div_small(tm, M), m = tm - t * M;
             const size_t ti = (size_t)t * NM + env * M + m;
             const bool dn = a.done_rd[(size_t)t * NM + env * M] != 0;
             float go[3] = {0.f, 0.f, 0.f}, gR[9];
@@ -366,11 +366,13 @@ __global__ void __launch_bounds__(256, TAPE ? 4 : 3) k_render_vjp(const Args a) 
                         // taped hit ids: rays in slot order j = j0 + lane, + 32, ...
                         for (int j = j0 + lane; j < j1; j += 32) {
                             const int ray = out_index(sen, j);
+                            // the id and the cotangent load together (one memory round trip)
                             const int id = sen.tape[base + ray];
+                            const float gv = sen.gout[base + ray];
                             if (id < 0) continue;
                             float d[3];
                             const float4 db = ray_dir(sen, R, j, d);
-                            ray_vjp<EXTRA>(mv, id, o, d[0], d[1], d[2], db, sen, sen.gout[base + ray], go, gR);
+                            ray_vjp<EXTRA>(mv, id, o, d[0], d[1], d[2], db, sen, gv, go, gR);
                         }
                         continue;
                     }
