@@ -364,11 +364,25 @@ __global__ void __launch_bounds__(256, TAPE ? 4 : 3) k_render_vjp(const Args a) 
                     const int j0 = 32 * (part * W32 / P), j1 = min(sen.R, 32 * ((part + 1) * W32 / P));
                     if (TAPE) {
                         // taped hit ids: rays in slot order j = j0 + lane, + 32, ...
-                        for (int j = j0 + lane; j < j1; j += 32) {
-                            const int ray = out_index(sen, j);
-                            // the id and the cotangent load together (one memory round trip)
-                            const int id = sen.tape[base + ray];
-                            const float gv = sen.gout[base + ray];
+                        // the next ray's hit id and cotangent are in flight while
+                        // the current one is processed
+                        int jn = j0 + lane;
+                        int idn = -1;
+                        float gn = 0.f;
+                        if (jn < j1) {
+                            const int ray = out_index(sen, jn);
+                            idn = sen.tape[base + ray];
+                            gn = sen.gout[base + ray];
+                        }
+                        while (jn < j1) {
+                            const int j = jn, id = idn;
+                            const float gv = gn;
+                            jn += 32;
+                            if (jn < j1) {
+                                const int ray = out_index(sen, jn);
+                                idn = sen.tape[base + ray];
+                                gn = sen.gout[base + ray];
+                            }
                             if (id < 0) continue;
                             float d[3];
                             const float4 db = ray_dir(sen, R, j, d);
