@@ -23,6 +23,15 @@ struct Phys {
     float imu_noise[2], imu_walk[2];  // IMU white-noise and bias-walk std (force, rate)
 };
 
+// Square root by the hardware approximation (relative error about 2^-22,
+// exact at 0): distances and ray-sphere near roots need no correct rounding
+// (an error of ~1e-7 of the value is far inside every tolerance).
+__device__ __forceinline__ float sqrt_approx(float x) {
+    float r;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 __device__ __forceinline__ float clip1(float x) { return fminf(fmaxf(x, -1.f), 1.f); }
 __device__ __forceinline__ float dclip1(float x) { return (x >= -1.f && x <= 1.f) ? 1.f : 0.f; }
 __device__ __forceinline__ float relu(float x) { return x > 0.f ? x : 0.f; }
@@ -480,7 +489,7 @@ __device__ __forceinline__ float sdf_box_ch(const float* q0, const float* ctr, c
         q[i] = fabsf(q0[i] - ctr[i]) - h[i];
         out = fmaf(relu(q[i]), relu(q[i]), out);
     }
-    return sqrtf(out) + fminf(fmaxf(q[0], fmaxf(q[1], q[2])), 0.f);
+    return sqrt_approx(out) + fminf(fmaxf(q[0], fmaxf(q[1], q[2])), 0.f);
 }
 
 // Bar k of a gate (0 top, 1 bottom, 2 left, 3 right) in local coordinates:
@@ -515,8 +524,8 @@ __device__ __forceinline__ float sdf_gate(const float4& g0, const float4& g1, co
 __device__ __forceinline__ float sdf_prim(const MapView& m, int k, const float* p) {
     if (k < m.ns) {
         float4 s = m.prim[k];
-        float dx = p[0] - s.x, dy = p[1] - s.y, dz = p[2] - s.z;
-        return sqrtf(dx * dx + dy * dy + dz * dz) - s.w;
+        const float dx = p[0] - s.x, dy = p[1] - s.y, dz = p[2] - s.z;
+        return sqrt_approx(fmaf(dx, dx, fmaf(dy, dy, dz * dz))) - s.w;
     }
     k -= m.ns;
     if (k < m.nb) {
@@ -526,15 +535,15 @@ __device__ __forceinline__ float sdf_prim(const MapView& m, int k, const float* 
         float qz = fabsf(p[2] - 0.5f * (lo.z + hi.z)) - 0.5f * (hi.z - lo.z);
         float ox = relu(qx), oy = relu(qy), oz = relu(qz);
         float in = fminf(fmaxf(qx, fmaxf(qy, qz)), 0.f);
-        return sqrtf(ox * ox + oy * oy + oz * oz) + in;
+        return sqrt_approx(fmaf(ox, ox, fmaf(oy, oy, oz * oz))) + in;
     }
     k -= m.nb;
     if (k < m.nc) {
         const float4 c0 = m.cyl(k)[0], c1 = m.cyl(k)[1];
         const float ex = p[0] - c0.x, ey = p[1] - c0.y;
-        const float qr = sqrtf(fmaf(ex, ex, ey * ey)) - c0.z;
+        const float qr = sqrt_approx(fmaf(ex, ex, ey * ey)) - c0.z;
         const float qz = fabsf(p[2] - 0.5f * (c1.x + c1.y)) - 0.5f * (c1.y - c1.x);
-        return sqrtf(fmaf(relu(qr), relu(qr), relu(qz) * relu(qz))) + fminf(fmaxf(qr, qz), 0.f);
+        return sqrt_approx(fmaf(relu(qr), relu(qr), relu(qz) * relu(qz))) + fminf(fmaxf(qr, qz), 0.f);
     }
     k -= m.nc;
     int bar;

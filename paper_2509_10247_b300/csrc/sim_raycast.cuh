@@ -81,15 +81,6 @@ struct RayPairs {
 __device__ __forceinline__ float2 f2(float v) { return make_float2(v, v); }
 __device__ __forceinline__ float lo_hi(const float2& v, int q) { return q ? v.y : v.x; }
 
-// Square root by the hardware approximation (relative error about 2^-22,
-// exact at 0): the near-root of a ray-sphere hit needs no correct rounding
-// (its error, ~1e-7 r, is far inside the depth tolerance).
-__device__ __forceinline__ float sqrt_approx(float x) {
-    float r;
-    asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
-    return r;
-}
-
 __device__ __forceinline__ float min3f(float x, float y, float z) {
     float r;
     asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(x), "f"(y), "f"(z));
