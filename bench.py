@@ -566,41 +566,77 @@ def run_closed_loop(args, rank, world):
 
 
 def run_e2e(args, sim, inp, dev, g_r, g_d, out, g_a, g_s0, p):
+    """End to end through the public API: every step copies its actions and
+    initial state in from pinned host memory and its rewards and action
+    gradients out.  Copies run on a second stream, double-buffered, so step
+    k + 1's inputs arrive and step k - 1's results leave while step k
+    computes (events order each buffer's reuse)."""
     import torch
     T, NM = p["horizon"], sim.NM
     act_h = torch.as_tensor(inp["actions"], dtype=torch.float32).pin_memory()
     s0_h = torch.as_tensor(inp["s0"], dtype=torch.float32).pin_memory()
-    r_h = torch.empty(T, NM, dtype=torch.float32).pin_memory()
-    ga_h = torch.empty(T, NM, sim.A, dtype=torch.float32).pin_memory()
-    act_d = torch.empty_like(act_h, device=dev)
-    s0_d = torch.empty_like(s0_h, device=dev)
-    stream = torch.cuda.current_stream(dev)
+    r_h = [torch.empty(T, NM, dtype=torch.float32).pin_memory() for _ in range(2)]
+    ga_h = [torch.empty(T, NM, sim.A, dtype=torch.float32).pin_memory() for _ in range(2)]
+    act_d = [torch.empty_like(act_h, device=dev) for _ in range(2)]
+    s0_d = [torch.empty_like(s0_h, device=dev) for _ in range(2)]
+    outs = [out, {k: (None if v is None else torch.empty_like(v)) for k, v in out.items()}]
+    gas = [g_a, torch.empty_like(g_a)]
+    comp = torch.cuda.current_stream(dev)
+    copy = torch.cuda.Stream(device=dev)
+    ev = lambda: torch.cuda.Event()
+    h2d_done = [ev(), ev()]    # inputs of buffer b are on the device
+    comp_done = [ev(), ev()]   # step using buffer b finished (inputs free, outputs ready)
+    d2h_done = [ev(), ev()]    # outputs of buffer b are on the host
 
-    def step():
-        act_d.copy_(act_h, non_blocking=True)
-        s0_d.copy_(s0_h, non_blocking=True)
-        sim.reset(s0_d)
-        sim.rollout(act_d, out=out)
-        sim.backward(g_r, g_d, None, None, g_a, g_s0)
-        r_h.copy_(out["r_ctrl"], non_blocking=True)
-        ga_h.copy_(g_a, non_blocking=True)
+    def h2d(b):
+        with torch.cuda.stream(copy):
+            copy.wait_event(comp_done[b])      # the previous step on b has read its inputs
+            act_d[b].copy_(act_h, non_blocking=True)
+            s0_d[b].copy_(s0_h, non_blocking=True)
+            h2d_done[b].record(copy)
 
-    for _ in range(args.warmup):
-        step()
+    def compute(b):
+        comp.wait_event(h2d_done[b])
+        comp.wait_event(d2h_done[b])           # its output buffers have been read out
+        sim.reset(s0_d[b])
+        sim.rollout(act_d[b], out=outs[b])
+        sim.backward(g_r, g_d, None, None, gas[b], g_s0)
+        comp_done[b].record(comp)
+
+    def d2h(b):
+        with torch.cuda.stream(copy):
+            copy.wait_event(comp_done[b])
+            r_h[b].copy_(outs[b]["r_ctrl"], non_blocking=True)
+            ga_h[b].copy_(gas[b], non_blocking=True)
+            d2h_done[b].record(copy)
+
+    def run(n):
+        for b in range(2):
+            comp_done[b].record(comp)
+            d2h_done[b].record(comp)
+        h2d(0)
+        for k in range(n):
+            b = k % 2
+            if k + 1 < n:
+                h2d(1 - b)
+            compute(b)
+            d2h(b)
+        comp.wait_event(d2h_done[(n - 1) % 2])
+
+    run(args.warmup)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        step()
-    e1.record(stream)
+    e0.record(comp)
+    run(args.steps)
+    e1.record(comp)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
-    h2d = act_h.numel() * 4 + s0_h.numel() * 4
-    d2h = r_h.numel() * 4 + ga_h.numel() * 4
+    h2d_b = act_h.numel() * 4 + s0_h.numel() * 4
+    d2h_b = r_h[0].numel() * 4 + ga_h[0].numel() * 4
     return {"value": p["n_env"] * T * args.steps / (ms / 1e3), "unit": UNIT,
-            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-            "what": "pinned host actions + initial state in; rewards + action gradients out; "
-                    "reward/depth cotangents device-resident"}
+            "h2d_bytes_per_step": h2d_b, "d2h_bytes_per_step": d2h_b,
+            "what": "pinned host actions + initial state in; rewards + action gradients out, on a copy "
+                    "stream double-buffered against the compute; reward/depth cotangents device-resident"}
 
 
 def main():
