@@ -28,11 +28,12 @@ def cache_path():
 
 def workload_key(p, inp):
     """Stable key of what the kernels compute: all parameters of `p` except
-    its name, the per-map obstacle counts and the env -> map assignment."""
+    its name, the per-map obstacle counts (every primitive kind) and the
+    env -> map assignment."""
     q = {k: v for k, v in p.items() if k not in ("name",) + EXEC_FIELDS}
-    so = [int(x) for x in inp["sph_off"]]
-    bo = [int(x) for x in inp["box_off"]]
-    counts = [(so[m + 1] - so[m], bo[m + 1] - bo[m]) for m in range(len(so) - 1)]
+    offs = [[int(x) for x in inp[k]] for k in ("sph_off", "box_off", "cyl_off", "gate_off")
+            if inp.get(k) is not None]
+    counts = [tuple(o[m + 1] - o[m] for o in offs) for m in range(len(offs[0]) - 1)]
     h = hashlib.sha256()
     h.update(json.dumps(q, sort_keys=True, default=str).encode())
     h.update(json.dumps(counts).encode())
