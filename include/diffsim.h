@@ -223,6 +223,18 @@ int sim_set_state(sim_handle *h, const float *src, sim_stream_t stream);
  * [NM][Rc] and lidar [NM][Rl], DEVICE, either NULL to skip. */
 int sim_render(sim_handle *h, float *depth, float *lidar, sim_stream_t stream);
 
+/* sim_render that also records, per ray, the primitive its depth comes from
+ * (Sec. III-B ray casting; the ray term of the Eq. 5 adjoint needs only that
+ * primitive): hits_cam [NM][Rc] and hits_lidar [NM][Rl], int16 DEVICE,
+ * caller-owned; -1 = no hit within range, -2 = the sensor's origin lies
+ * inside a primitive (depth 0, no gradient).  Either may be NULL (that
+ * sensor's hits are not written).  Feeds sim_step_backward_taped of the step
+ * that produced this state, which then gathers the hits instead of casting
+ * every ray again (closed loop: the backward pass re-renders state t for
+ * the policy anyway; its hits serve the adjoint of step t-1). */
+int sim_render_taped(sim_handle *h, float *depth, float *lidar, int16_t *hits_cam,
+                     int16_t *hits_lidar, sim_stream_t stream);
+
 /* One step of the current state with actions [NM][A] (DEVICE).  Outputs
  * (DEVICE, any may be NULL): depth [NM][Rc], lidar [NM][Rl], r_ctrl [NM],
  * r_goal [NM], done [NM].  Advances the current state. */
@@ -295,6 +307,20 @@ int sim_backward(sim_handle *h, const float *g_r, const float *g_depth, const fl
 int sim_step_backward(sim_handle *h, const float *s_t, const float *a_t, const uint8_t *done_t,
                       const float *g_s_next, const float *g_r, const float *g_depth,
                       const float *g_lidar, float *g_a, float *g_s, sim_stream_t stream);
+
+/* sim_step_backward whose ray adjoint gathers hit ids instead of re-casting:
+ * hits_cam [NM][Rc], hits_lidar [NM][Rl] (int16, DEVICE) written by
+ * sim_render_taped of the state this step produces (s_t stepped with a_t).
+ * Each sensor with a non-NULL cotangent needs its hits (SIM_ERR_NULL_PTR
+ * otherwise); both hits NULL = sim_step_backward.  Ids from another state
+ * give a wrong gradient but stay memory-safe (ids outside the environment's
+ * map are ignored).  The result equals sim_step_backward's bit for bit when
+ * the hits match the step. */
+int sim_step_backward_taped(sim_handle *h, const float *s_t, const float *a_t,
+                            const uint8_t *done_t, const float *g_s_next, const float *g_r,
+                            const float *g_depth, const float *g_lidar, const int16_t *hits_cam,
+                            const int16_t *hits_lidar, float *g_a, float *g_s,
+                            sim_stream_t stream);
 
 /* Device status word accumulated by the kernels since the last call
  * (SIM_STATUS_* bits; synchronises the handle's last stream and clears it).

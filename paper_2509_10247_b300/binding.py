@@ -38,7 +38,7 @@ SYMBOLS = ["sim_version", "sim_strerror", "sim_state_dim", "sim_action_dim", "si
            "sim_launch_info", "sim_counters", "sim_step_static", "sim_profile", "sim_kernel_times",
            "sim_graph_create", "sim_graph_launch", "sim_graph_kernels", "sim_graph_destroy",
            "sim_set_scene_ex", "sim_get_gate_index", "sim_set_gate_index", "sim_rollout_ex",
-           "sim_step_ex", "sim_backward_ex"]
+           "sim_step_ex", "sim_backward_ex", "sim_render_taped", "sim_step_backward_taped"]
 
 # flight tasks (Sec. III-C)
 TASKS = {"reach": 0, "racing": 1}
@@ -292,6 +292,11 @@ def sim_render(h, depth=None, lidar=None, stream=None):
     _ck(lib().sim_render(h, _ptr(depth), _ptr(lidar), _stream(stream)), "sim_render")
 
 
+def sim_render_taped(h, depth, lidar, hits_cam, hits_lidar, stream=None):
+    _ck(lib().sim_render_taped(h, _ptr(depth), _ptr(lidar), _ptr(hits_cam), _ptr(hits_lidar), _stream(stream)),
+        "sim_render_taped")
+
+
 def sim_step(h, actions, depth=None, lidar=None, r_ctrl=None, r_goal=None, done=None, stream=None):
     _ck(lib().sim_step(h, _ptr(actions), _ptr(depth), _ptr(lidar), _ptr(r_ctrl), _ptr(r_goal),
                        _ptr(done), _stream(stream)), "sim_step")
@@ -311,6 +316,13 @@ def sim_step_backward(h, s_t, a_t, done_t, g_s_next, g_r, g_depth, g_lidar, g_a,
     _ck(lib().sim_step_backward(h, _ptr(s_t), _ptr(a_t), _ptr(done_t), _ptr(g_s_next), _ptr(g_r),
                                 _ptr(g_depth), _ptr(g_lidar), _ptr(g_a), _ptr(g_s),
                                 _stream(stream)), "sim_step_backward")
+
+
+def sim_step_backward_taped(h, s_t, a_t, done_t, g_s_next, g_r, g_depth, g_lidar, hits_cam, hits_lidar, g_a,
+                            g_s=None, stream=None):
+    _ck(lib().sim_step_backward_taped(h, _ptr(s_t), _ptr(a_t), _ptr(done_t), _ptr(g_s_next), _ptr(g_r),
+                                      _ptr(g_depth), _ptr(g_lidar), _ptr(hits_cam), _ptr(hits_lidar), _ptr(g_a),
+                                      _ptr(g_s), _stream(stream)), "sim_step_backward_taped")
 
 
 def sim_last_status(h):
@@ -458,11 +470,22 @@ class Simulator:
     def set_state(self, s):
         sim_set_state(self.h, s.contiguous())
 
-    def render(self):
+    def render(self, hits=None):
+        """Depth and LiDAR of the current state.  hits: None, or a pair of
+        int16 tensors ([NM][Rc], [NM][Rl]; None where a sensor is absent),
+        e.g. from hit_buffers(), that receive each ray's hit primitive id
+        for step_backward(hits=...) of the step that produced this state."""
         depth = self._empty(self.NM, self.Rc) if self.Rc else None
         lidar = self._empty(self.NM, self.Rl) if self.Rl else None
-        sim_render(self.h, depth, lidar)
+        if hits is None:
+            sim_render(self.h, depth, lidar)
+        else:
+            sim_render_taped(self.h, depth, lidar, hits[0], hits[1])
         return depth, lidar
+
+    def hit_buffers(self):
+        return (self._empty(self.NM, self.Rc, dtype=torch.int16) if self.Rc else None,
+                self._empty(self.NM, self.Rl, dtype=torch.int16) if self.Rl else None)
 
     def step(self, actions):
         o = dict(r_ctrl=self._empty(self.NM), r_goal=self._empty(self.NM, dtype=torch.int8),
@@ -509,12 +532,19 @@ class Simulator:
                      None if g_sT is None else g_sT.contiguous(), g_a, g_s0)
         return g_a, g_s0
 
-    def step_backward(self, s_t, a_t, done_t, g_s_next, g_r, g_depth=None, g_lidar=None):
+    def step_backward(self, s_t, a_t, done_t, g_s_next, g_r, g_depth=None, g_lidar=None, hits=None):
+        """VJP of one step.  hits: the pair render(hits=...) wrote for the
+        state this step produces; the ray adjoint then gathers them instead
+        of casting the rays again (same result, bit for bit)."""
         g_a = self._empty(self.NM, self.A)
         g_s = self._empty(self.NM, self.D)
         c = lambda x: None if x is None else x.contiguous()
-        sim_step_backward(self.h, c(s_t), c(a_t), c(done_t), c(g_s_next), c(g_r), c(g_depth),
-                          c(g_lidar), g_a, g_s)
+        if hits is None:
+            sim_step_backward(self.h, c(s_t), c(a_t), c(done_t), c(g_s_next), c(g_r), c(g_depth),
+                              c(g_lidar), g_a, g_s)
+        else:
+            sim_step_backward_taped(self.h, c(s_t), c(a_t), c(done_t), c(g_s_next), c(g_r), c(g_depth),
+                                    c(g_lidar), hits[0], hits[1], g_a, g_s)
         return g_a, g_s
 
     def status(self):

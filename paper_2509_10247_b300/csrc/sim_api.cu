@@ -74,11 +74,11 @@ struct sim_handle {
     const float* rollout_actions = nullptr;
     cudaStream_t last_stream = nullptr;
     // launch shape of the render kernels (forward, adjoint, single-step adjoint)
-    int nw = 8, rpt = 4, grid_r = 1, grid_rv = 1, grid_rvs = 1;
+    int nw = 8, rpt = 4, grid_r = 1, grid_rv = 1, grid_rvs = 1, grid_rvt = 1;
     // ray parts per render item of a rollout and of a single step: enough
     // items per environment for 8 warps (a function of T and M only)
     int parts_roll = 1, parts_one = 1;
-    ds::Smem sm_r{}, sm_rv{}, sm_rvs{};
+    ds::Smem sm_r{}, sm_rv{}, sm_rvs{}, sm_rvt{};
     // kernel launches per kind; while profiling, one CUDA event pair per launch
     bool profiling = false, capturing = false, ev_overflow = false;
     long long launches[SIM_KERNEL_KINDS] = {};
@@ -332,6 +332,7 @@ int configure_launch(sim_handle* h) {
     h->sm_r = layout_render(h, h->S > 0);
     h->sm_rv = layout_render(h, h->S > 0 && !h->tape);
     h->sm_rvs = layout_render(h, h->S > 0);
+    h->sm_rvt = layout_render(h, false);
     int maxsm = 0;
     CK(cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
     if (h->sm_r.total > maxsm || h->sm_rv.total > maxsm) return SIM_ERR_SIZE;
@@ -342,7 +343,8 @@ int configure_launch(sim_handle* h) {
     int rc;
     if ((rc = grid_of(h, false, false, h->sm_r, &h->grid_r)) ||
         (rc = grid_of(h, true, h->tape, h->sm_rv, &h->grid_rv)) ||
-        (rc = grid_of(h, true, false, h->sm_rvs, &h->grid_rvs)))
+        (rc = grid_of(h, true, false, h->sm_rvs, &h->grid_rvs)) ||
+        (rc = grid_of(h, true, true, h->sm_rvt, &h->grid_rvt)))
         return rc;
     return SIM_OK;
 }
@@ -437,10 +439,11 @@ int run_physics_bwd(sim_handle* h, const Args& a, cudaStream_t st) {
     return launch_kernel(h, SIM_KERNEL_PHYSICS_BWD, st, [&] { return ds::launch_physics_bwd(a, st); });
 }
 
-// which: 0 render, 1 render adjoint (rollout), 2 render adjoint re-casting (step)
+// which: 0 render, 1 render adjoint (rollout), 2 render adjoint re-casting
+// (step), 3 render adjoint gathering caller-supplied hit ids (step)
 int run_render(sim_handle* h, int which, Args& a, cudaStream_t st) {
-    const ds::Smem& sm = which == 0 ? h->sm_r : (which == 1 ? h->sm_rv : h->sm_rvs);
-    const int grid = which == 0 ? h->grid_r : (which == 1 ? h->grid_rv : h->grid_rvs);
+    const ds::Smem& sm = which == 0 ? h->sm_r : (which == 1 ? h->sm_rv : (which == 2 ? h->sm_rvs : h->sm_rvt));
+    const int grid = which == 0 ? h->grid_r : (which == 1 ? h->grid_rv : (which == 2 ? h->grid_rvs : h->grid_rvt));
     a.sm = sm;
     CK(cudaMemsetAsync(h->d_work, 0, sizeof(int), st));
     int occ = 0;
@@ -883,7 +886,8 @@ int sim_set_state(sim_handle* h, const float* src, sim_stream_t stream) {
     return SIM_OK;
 }
 
-int sim_render(sim_handle* h, float* depth, float* lidar, sim_stream_t stream) {
+int sim_render_taped(sim_handle* h, float* depth, float* lidar, int16_t* hits_cam, int16_t* hits_lidar,
+                     sim_stream_t stream) {
     if (!h) return SIM_ERR_NULL_PTR;
     if (!h->have_scene) return SIM_ERR_NOT_READY;
     cudaStream_t st = (cudaStream_t)stream;
@@ -895,9 +899,13 @@ int sim_render(sim_handle* h, float* depth, float* lidar, sim_stream_t stream) {
     int rc = run_physics(h, a, st);
     if (rc || h->S == 0) return rc;
     int s = 0;
-    if (h->Rc) { a.sen[s].out = depth; a.sen[s].tape = nullptr; ++s; }
-    if (h->Rl) { a.sen[s].out = lidar; a.sen[s].tape = nullptr; ++s; }
+    if (h->Rc) { a.sen[s].out = depth; a.sen[s].tape = hits_cam; ++s; }
+    if (h->Rl) { a.sen[s].out = lidar; a.sen[s].tape = hits_lidar; ++s; }
     return run_render(h, 0, a, st);
+}
+
+int sim_render(sim_handle* h, float* depth, float* lidar, sim_stream_t stream) {
+    return sim_render_taped(h, depth, lidar, nullptr, nullptr, stream);
 }
 
 int sim_step_ex(sim_handle* h, const sim_rollout_io* io, sim_stream_t stream) {
@@ -1001,12 +1009,15 @@ int sim_backward(sim_handle* h, const float* g_r, const float* g_depth, const fl
     return sim_backward_ex(h, &io, stream);
 }
 
-int sim_step_backward(sim_handle* h, const float* s_t, const float* a_t, const uint8_t* done_t,
-                      const float* g_s_next, const float* g_r, const float* g_depth, const float* g_lidar,
-                      float* g_a, float* g_s, sim_stream_t stream) {
+int sim_step_backward_taped(sim_handle* h, const float* s_t, const float* a_t, const uint8_t* done_t,
+                            const float* g_s_next, const float* g_r, const float* g_depth, const float* g_lidar,
+                            const int16_t* hits_cam, const int16_t* hits_lidar, float* g_a, float* g_s,
+                            sim_stream_t stream) {
     if (!h || !s_t || !a_t || !done_t || !g_r || !g_a) return SIM_ERR_NULL_PTR;
     if (!h->have_scene) return SIM_ERR_NOT_READY;
     if (h->cfg.task != SIM_TASK_REACH) return SIM_ERR_UNSUPPORTED;
+    const bool taped = hits_cam || hits_lidar;
+    if (taped && ((h->Rc && g_depth && !hits_cam) || (h->Rl && g_lidar && !hits_lidar))) return SIM_ERR_NULL_PTR;
     cudaStream_t st = (cudaStream_t)stream;
     Args a = base_args(h);
     a.T = 1;
@@ -1026,9 +1037,9 @@ int sim_step_backward(sim_handle* h, const float* s_t, const float* a_t, const u
         a.gposes = h->d_gpose1;
         a.done_rd = done_t;
         int s = 0;
-        if (h->Rc) { a.sen[s].gout = g_depth; a.sen[s].tape = nullptr; ++s; }
-        if (h->Rl) { a.sen[s].gout = g_lidar; a.sen[s].tape = nullptr; ++s; }
-        rc = run_render(h, 2, a, st);
+        if (h->Rc) { a.sen[s].gout = g_depth; a.sen[s].tape = const_cast<int16_t*>(hits_cam); ++s; }
+        if (h->Rl) { a.sen[s].gout = g_lidar; a.sen[s].tape = const_cast<int16_t*>(hits_lidar); ++s; }
+        rc = run_render(h, taped ? 3 : 2, a, st);
         if (rc) return rc;
     }
     a.done_rd = done_t;
@@ -1037,6 +1048,13 @@ int sim_step_backward(sim_handle* h, const float* s_t, const float* a_t, const u
     a.ckpt_k = nullptr;
     a.g_r = g_r; a.g_sT = g_s_next; a.g_a = g_a; a.g_s0 = g_s;
     return run_physics_bwd(h, a, st);
+}
+
+int sim_step_backward(sim_handle* h, const float* s_t, const float* a_t, const uint8_t* done_t,
+                      const float* g_s_next, const float* g_r, const float* g_depth, const float* g_lidar,
+                      float* g_a, float* g_s, sim_stream_t stream) {
+    return sim_step_backward_taped(h, s_t, a_t, done_t, g_s_next, g_r, g_depth, g_lidar, nullptr, nullptr, g_a,
+                                   g_s, stream);
 }
 
 int sim_last_status(sim_handle* h, int32_t* status, int32_t* per_env) {

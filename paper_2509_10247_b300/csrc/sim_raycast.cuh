@@ -675,7 +675,7 @@ __device__ __forceinline__ MapView map_view(const Args& a, int map, const float4
 template <bool EXTRA>
 __device__ __forceinline__ void ray_vjp(const MapView& mv, int id, const float* o, float dx, float dy, float dz,
                                         const float4& db, const Sensor& sen, float g, float* go, float* gR) {
-    if (id < 0 || g == 0.f) return;
+    if (id < 0 || id >= mv.count() || g == 0.f) return;  // miss (or an id foreign to the map)
     const float4* prim = mv.prim;
     const int ns = mv.ns;
     const float d[3] = {dx, dy, dz};

@@ -285,7 +285,7 @@ __global__ void __launch_bounds__(256, 4) k_render(const Args a) {
                     const int ray = out_index(sen, j);
                     float v;
                     int id;
-                    if (meta.z >= 0) { v = 0.f; id = meta.z; }
+                    if (meta.z >= 0) { v = 0.f; id = -2; }  // origin inside a primitive: no ray cotangent
                     else if (bi[r] < 0) { v = sen.range; id = -1; }
                     else {
                         v = fminf(sen.kind == 0 ? tb[r] * __ldg(&sen.dir[j].w) : tb[r], sen.range);
@@ -358,7 +358,7 @@ __global__ void __launch_bounds__(256, TAPE ? 4 : 3) k_render_vjp(const Args a) 
                 for (int k = 0; k < 9; ++k) R[k] = a.poses[ti * 12 + 3 + k];
                 for (int si = 0; si < S; ++si) {
                     const Sensor& sen = a.sen[si];
-                    if (!sen.gout) continue;
+                    if (!sen.gout || (TAPE && !sen.tape)) continue;
                     const size_t base = ti * sen.R;
                     const int W32 = (sen.R + 31) / 32;
                     const int j0 = 32 * (part * W32 / P), j1 = min(sen.R, 32 * ((part + 1) * W32 / P));
@@ -630,7 +630,7 @@ static cudaError_t render_launch(K kernel, bool launch, const Args& a, int grid,
 template <int RPT, bool EXTRA>
 static cudaError_t render_rpt(bool vjp, bool launch, const Args& a, int grid, int block, size_t smem,
                               cudaStream_t st, int* occ) {
-    if (vjp && a.sen[0].tape)  // taped hit ids: one kernel for every RPT
+    if (vjp && (a.sen[0].tape || (a.S > 1 && a.sen[1].tape)))  // taped hit ids: one kernel for every RPT
         return render_launch(k_render_vjp<1, true, EXTRA>, launch, a, grid, block, smem, st, occ);
     if (vjp) return render_launch(k_render_vjp<RPT, false, EXTRA>, launch, a, grid, block, smem, st, occ);
     return render_launch(k_render<RPT, EXTRA>, launch, a, grid, block, smem, st, occ);

@@ -109,7 +109,11 @@ class ClosedLoop:
     gives the action cotangent, the policy's backward pass the parameter
     gradient and the observation cotangent, whose depth / LiDAR part feeds
     the previous step's adjoint and whose state part joins the state
-    cotangent.  Rigid-body agents, one per environment."""
+    cotangent.  The re-render of state t records each ray's hit primitive,
+    which the adjoint of step t - 1 (the step producing state t) gathers
+    instead of casting the rays a third time; the last step's observation
+    feeds no action, so its adjoint has no ray term.  Rigid-body agents, one
+    per environment."""
 
     def __init__(self, p, inp, device="cuda", **ex):
         assert p["model"] == "rigid" and p["n_agent"] == 1
@@ -139,14 +143,15 @@ class ClosedLoop:
             states[t + 1] = sim.get_state()
         loss = float((g_r[:T] * r).sum())
         g_s = torch.zeros(N, 13, device=dev)
-        g_dep = torch.zeros(N, Rc, device=dev) if Rc else None
-        g_lid = torch.zeros(N, Rl, device=dev) if Rl else None
+        g_dep = g_lid = hits = None
+        hit_buf = sim.hit_buffers() if Rc or Rl else None
         scratch = torch.empty(N, 4, device=dev)
         pol.grads(reset=True)
         for t in range(T - 1, -1, -1):
-            g_a, g_st = sim.step_backward(states[t], actions[t], done[t], g_s, g_r[t], g_dep, g_lid)
+            g_a, g_st = sim.step_backward(states[t], actions[t], done[t], g_s, g_r[t], g_dep, g_lid, hits=hits)
             sim.set_state(states[t])
-            depth, lidar = sim.render()
+            depth, lidar = sim.render(hits=hit_buf)
+            hits = hit_buf
             pol.act(states[t], self.targets, depth, lidar, out=scratch)
             g_dep = torch.empty(N, Rc, device=dev) if Rc else None
             g_lid = torch.empty(N, Rl, device=dev) if Rl else None

@@ -111,6 +111,9 @@ def test_null_pointers(lib):
     assert lib.sim_get_gate_index(None, None, None) == -2
     assert lib.sim_set_gate_index(None, None, None) == -2
     assert lib.sim_last_status(None, None, None) == -2
+    assert lib.sim_render_taped(None, None, None, None, None, None) == -2
+    assert lib.sim_step_backward_taped(None, None, None, None, None, None, None, None, None, None, None, None,
+                                       None) == -2
 
 
 def test_valid_config_without_gpu_fails_cleanly(lib):

@@ -163,6 +163,49 @@ def test_teacher_forced_adjoint(pair):
         assert ia <= max(1, p["n_env"] // 10) and is_ <= max(1, p["n_env"] // 10)
 
 
+
+def test_step_backward_with_recorded_hits_matches_recast(pair):
+    """sim_render_taped of the state a step produces records each ray's hit;
+    the step adjoint gathering those hits equals the re-casting one bit for
+    bit (both sensors, and a cotangent on one sensor only)."""
+    p = pair.p
+    if p["cam"] is None and p["lidar"] is None:
+        pytest.skip("no sensor")
+    if p.get("task", "reach") != "reach":
+        pytest.skip("step adjoint: reaching task only")
+    sim = Simulator(p, pair.inp)
+    sim.reset(dev(pair.inp["s0"]))
+    o = sim.step(pair.act[0])
+    o = sim.step(pair.act[1])  # a state away from the initial one
+    s_t = sim.get_state().clone()
+    o = sim.step(pair.act[2])
+    hits = sim.hit_buffers()
+    depth, lidar = sim.render(hits=hits)
+    if depth is not None:
+        assert torch.equal(depth, o["depth"])
+        assert int(hits[0].min()) >= -2 and int(hits[0].max()) < 32767
+    if lidar is not None:
+        assert torch.equal(lidar, o["lidar"])
+    g = torch.Generator(device="cuda").manual_seed(5)
+    rn = lambda *s: torch.randn(*s, device="cuda", generator=g)
+    g_sn, g_r = rn(sim.NM, sim.D), rn(sim.NM)
+    g_d = rn(sim.NM, sim.Rc) if sim.Rc else None
+    g_l = rn(sim.NM, sim.Rl) if sim.Rl else None
+    a2 = pair.act[2]
+    cases = [(g_d, g_l, hits)]
+    if sim.Rc and sim.Rl:
+        cases.append((None, g_l, (None, hits[1])))
+        cases.append((g_d, None, (hits[0], None)))
+    for gd, gl, hh in cases:
+        ga0, gs0 = sim.step_backward(s_t, a2, o["done"], g_sn, g_r, gd, gl)
+        ga1, gs1 = sim.step_backward(s_t, a2, o["done"], g_sn, g_r, gd, gl, hits=hh)
+        torch.cuda.synchronize()
+        assert torch.equal(ga0, ga1) and torch.equal(gs0, gs1)
+    assert sim.status() == 0
+    if sim.Rc and sim.Rl:
+        with pytest.raises(RuntimeError):  # a cotangent without its sensor's hits
+            sim.step_backward(s_t, a2, o["done"], g_sn, g_r, g_d, g_l, hits=(None, hits[1]))
+
 def test_culling_is_result_preserving(pair):
     p = pair.p
     if p["cam"] is None and p["lidar"] is None:
