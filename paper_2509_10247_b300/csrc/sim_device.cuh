@@ -521,22 +521,26 @@ __device__ __forceinline__ float sdf_gate(const float4& g0, const float4& g1, co
     return best;
 }
 
+// Signed distance of p to a sphere (c, r).
+__device__ __forceinline__ float sdf_sphere(const float4& s, const float* p) {
+    const float dx = p[0] - s.x, dy = p[1] - s.y, dz = p[2] - s.z;
+    return sqrt_approx(fmaf(dx, dx, fmaf(dy, dy, dz * dz))) - s.w;
+}
+
+// Signed distance of p to an axis-aligned box given by its corners.
+__device__ __forceinline__ float sdf_box_lohi(const float4& lo, const float4& hi, const float* p) {
+    const float qx = fabsf(p[0] - 0.5f * (lo.x + hi.x)) - 0.5f * (hi.x - lo.x);
+    const float qy = fabsf(p[1] - 0.5f * (lo.y + hi.y)) - 0.5f * (hi.y - lo.y);
+    const float qz = fabsf(p[2] - 0.5f * (lo.z + hi.z)) - 0.5f * (hi.z - lo.z);
+    const float ox = relu(qx), oy = relu(qy), oz = relu(qz);
+    const float in = fminf(fmaxf(qx, fmaxf(qy, qz)), 0.f);
+    return sqrt_approx(fmaf(ox, ox, fmaf(oy, oy, oz * oz))) + in;
+}
+
 __device__ __forceinline__ float sdf_prim(const MapView& m, int k, const float* p) {
-    if (k < m.ns) {
-        float4 s = m.prim[k];
-        const float dx = p[0] - s.x, dy = p[1] - s.y, dz = p[2] - s.z;
-        return sqrt_approx(fmaf(dx, dx, fmaf(dy, dy, dz * dz))) - s.w;
-    }
+    if (k < m.ns) return sdf_sphere(m.prim[k], p);
     k -= m.ns;
-    if (k < m.nb) {
-        float4 lo = m.box(k)[0], hi = m.box(k)[1];
-        float qx = fabsf(p[0] - 0.5f * (lo.x + hi.x)) - 0.5f * (hi.x - lo.x);
-        float qy = fabsf(p[1] - 0.5f * (lo.y + hi.y)) - 0.5f * (hi.y - lo.y);
-        float qz = fabsf(p[2] - 0.5f * (lo.z + hi.z)) - 0.5f * (hi.z - lo.z);
-        float ox = relu(qx), oy = relu(qy), oz = relu(qz);
-        float in = fminf(fmaxf(qx, fmaxf(qy, qz)), 0.f);
-        return sqrt_approx(fmaf(ox, ox, fmaf(oy, oy, oz * oz))) + in;
-    }
+    if (k < m.nb) return sdf_box_lohi(m.box(k)[0], m.box(k)[1], p);
     k -= m.nb;
     if (k < m.nc) {
         const float4 c0 = m.cyl(k)[0], c1 = m.cyl(k)[1];

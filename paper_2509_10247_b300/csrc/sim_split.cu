@@ -47,12 +47,36 @@ __device__ __forceinline__ void nearest_obstacle(const MapView& mv, int M, const
                         __shfl_sync(0xffffffffu, p[2], gm)};
     float best = CUDART_INF_F;
     int bid = -1;
-    const int np = mv.count();
-    if (gm < M)
-        for (int k = gl; k < np; k += G) {
-            const float d = sdf_prim(mv, k, q);
-            if (d < best) { best = d; bid = k; }
+    if (gm < M) {
+        // one loop per kind, two primitives in flight; a lane visits its ids
+        // in increasing order and keeps the first of equal distances
+        const int ns = mv.ns, nb = mv.nb, np = mv.count();
+        int k = gl;
+        for (; k + G < ns; k += 2 * G) {
+            const float d0 = sdf_sphere(mv.prim[k], q), d1 = sdf_sphere(mv.prim[k + G], q);
+            if (d0 < best) { best = d0; bid = k; }
+            if (d1 < best) { best = d1; bid = k + G; }
         }
+        if (k < ns) {
+            const float d0 = sdf_sphere(mv.prim[k], q);
+            if (d0 < best) { best = d0; bid = k; }
+        }
+        int j = gl;
+        for (; j + G < nb; j += 2 * G) {
+            const float d0 = sdf_box_lohi(mv.box(j)[0], mv.box(j)[1], q);
+            const float d1 = sdf_box_lohi(mv.box(j + G)[0], mv.box(j + G)[1], q);
+            if (d0 < best) { best = d0; bid = ns + j; }
+            if (d1 < best) { best = d1; bid = ns + j + G; }
+        }
+        if (j < nb) {
+            const float d0 = sdf_box_lohi(mv.box(j)[0], mv.box(j)[1], q);
+            if (d0 < best) { best = d0; bid = ns + j; }
+        }
+        for (int c = ns + nb + gl; c < np; c += G) {  // cylinders and gates
+            const float d = sdf_prim(mv, c, q);
+            if (d < best) { best = d; bid = c; }
+        }
+    }
     for (int o = G >> 1; o > 0; o >>= 1) {
         const float v2 = __shfl_xor_sync(0xffffffffu, best, o);
         const int i2 = __shfl_xor_sync(0xffffffffu, bid, o);
