@@ -52,12 +52,15 @@ __device__ __forceinline__ void nearest_obstacle(const MapView& mv, int M, const
         // in increasing order and keeps the first of equal distances
         const int ns = mv.ns, nb = mv.nb, np = mv.count();
         int k = gl;
-        for (; k + G < ns; k += 2 * G) {
+        for (; k + 3 * G < ns; k += 4 * G) {
             const float d0 = sdf_sphere(mv.prim[k], q), d1 = sdf_sphere(mv.prim[k + G], q);
+            const float d2 = sdf_sphere(mv.prim[k + 2 * G], q), d3 = sdf_sphere(mv.prim[k + 3 * G], q);
             if (d0 < best) { best = d0; bid = k; }
             if (d1 < best) { best = d1; bid = k + G; }
+            if (d2 < best) { best = d2; bid = k + 2 * G; }
+            if (d3 < best) { best = d3; bid = k + 3 * G; }
         }
-        if (k < ns) {
+        for (; k < ns; k += G) {
             const float d0 = sdf_sphere(mv.prim[k], q);
             if (d0 < best) { best = d0; bid = k; }
         }
