@@ -111,9 +111,12 @@ typedef struct sim_config {
     int32_t tape_hits;    /* 1: rollout stores ray hit ids, backward gathers them;
                              0: backward re-casts the rays; -1: auto (tape if <= 8 GiB) */
     int32_t cull;         /* field-of-view culling (result-preserving): 0 off, 1 per sensor
-                             frustum, 2 frustum and per ray-chunk cones, -1 auto */
+                             frustum, 2 frustum and per ray-chunk cones, -1 auto (cones
+                             when a 128-ray chunk's cone is on average under half the
+                             sensor's own, ray-weighted: large images, LiDAR scans) */
     int32_t warps_per_cta;   /* 0: auto (8); else warps per CTA, 1..8 */
-    int32_t rays_per_thread; /* 0: auto; else one of 1, 2, 3, 4, 5, 6, 8 */
+    int32_t rays_per_thread; /* 0: auto (4 with cones, else the best lane fill); else one
+                                of 1, 2, 3, 4, 5, 6, 8 */
     int32_t ctas_per_sm;     /* 0: occupancy limit; else cap of resident CTAs per SM */
     /* flight task (Sec. III-C): SIM_TASK_REACH (targets; position control and
        obstacle avoidance) or SIM_TASK_RACING (the map's gates in order; needs

@@ -257,10 +257,9 @@ uint64_t morton2(uint32_t x, uint32_t y) {
 
 // Ray order of the render kernels: a function of the ray grid alone (never
 // of rays per thread, culling mode or CTA shape), so every launch shape sums
-// the adjoint's ray cotangents in one order and agrees bit for bit.  Grids of
-// at most 256 rays keep row-major order (a warp pass covers most of such a
-// grid anyway); larger grids take Z (Morton) order, so that each chunk of a
-// warp pass covers a compact patch of directions.  Each chunk's cone (body
+// the adjoint's ray cotangents in one order and agrees bit for bit.  Grids
+// above kMortonMin rays (all of them) take Z (Morton) order, so that each
+// chunk of a warp pass covers a compact patch of directions.  Each chunk's cone (body
 // frame): axis = normalised mean direction, half-angle = largest angle to
 // the axis + 2 mrad.  Tables are uploaded in that order with the output index
 // of every slot.  Returns the mean cone half-angle (rad).
@@ -316,19 +315,49 @@ int build_tables(sim_handle* h, int s, double* mean_angle) {
     return SIM_OK;
 }
 
+// Half-angle of the cone around all rays of sensor s (pi when their mean
+// direction vanishes, as for a full-circle LiDAR).
+double sensor_half_angle(const sim_handle* h, int s) {
+    const std::vector<float4>& d = h->h_dirs[s];
+    double ax = 0, ay = 0, az = 0;
+    for (const float4& v : d) { ax += v.x; ay += v.y; az += v.z; }
+    const double nn = std::sqrt(ax * ax + ay * ay + az * az);
+    if (nn <= 1e-9 * (double)d.size()) return M_PI;
+    double cmin = 1.0;
+    for (const float4& v : d) cmin = std::min(cmin, (v.x * ax + v.y * ay + v.z * az) / nn);
+    return std::min(std::acos(std::max(-1.0, std::min(1.0, cmin))) + 2e-3, M_PI);
+}
+
+// Rays per thread and culling mode.  Culling: 0 off, 1 sensor frustum, 2
+// frustum + chunk cones.  Chunks of a power-of-two ray count cover whole
+// Z-order blocks of the ray grid, so the cones take 4 rays per thread (128
+// per chunk) unless the caller fixes it; auto enables them when such a
+// chunk's cone is on average under half the sensor's own (ray-weighted over
+// the sensors: large camera images and LiDAR scans), else the frustum alone
+// with the rays per thread that fill the lanes best.
 int configure_launch(sim_handle* h) {
     h->nw = h->cfg.warps_per_cta ? h->cfg.warps_per_cta : 8;
-    h->rpt = pick_rpt(h);
-    // culling: 0 off, 1 sensor frustum, 2 frustum + chunk cones; auto enables
-    // the cones when they are narrow (mean half-angle below 0.35 rad)
-    double widest = 0.0;
+    const int cone_rpt = h->cfg.rays_per_thread ? h->cfg.rays_per_thread : 4;
+    int cull = h->cfg.cull;
+    if (cull < 0) {
+        h->rpt = cone_rpt;
+        double num = 0.0, den = 0.0;
+        for (int s = 0; s < h->S; ++s) {
+            double ang = 0.0;
+            int rc = build_tables(h, s, &ang);
+            if (rc) return rc;
+            num += h->sen[s].R * ang / sensor_half_angle(h, s);
+            den += h->sen[s].R;
+        }
+        cull = den > 0.0 && num < 0.5 * den ? 2 : 1;
+    }
+    h->rpt = cull == 2 ? cone_rpt : pick_rpt(h);
     for (int s = 0; s < h->S; ++s) {
         double ang = 0.0;
         int rc = build_tables(h, s, &ang);
         if (rc) return rc;
-        widest = std::max(widest, ang);
     }
-    h->cull_mode = h->cfg.cull >= 0 ? h->cfg.cull : (widest < 0.35 ? 2 : 1);
+    h->cull_mode = cull;
     h->sm_r = layout_render(h, h->S > 0);
     h->sm_rv = layout_render(h, h->S > 0 && !h->tape);
     h->sm_rvs = layout_render(h, h->S > 0);
