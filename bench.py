@@ -552,7 +552,9 @@ def run_closed_loop(args, rank, world):
             "workload": CLOSED_LOOP_WORKLOAD, "value": N * T / (ms / 1e3), "unit": "env-steps/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "dtype": "f32 simulator, bf16 policy (fp32 accumulate)", "data": "synthetic",
-            "config": {"n_env": N, "horizon": T, "policy": "%d -> 256 -> 4" % F, "obstacles": 256},
+            "config": {"n_env": N, "horizon": T, "policy": "%d -> 256 -> 4" % F, "obstacles": 256,
+                       "backward_observations": "rebuilt from the forward's stored hit ids (%.0f GB)"
+                       % (cl.hits_bytes(T) / 1e9) if cl.stored_hits else "re-rendered"},
             "loss": L, "grad_norm": float(np.linalg.norm(g)),
             "policy_act_ms": act_ms,
             "roofline": {"bound": "tensor", "achieved": gemm_flop / (act_ms / 1e3) / 1e12,

@@ -238,6 +238,18 @@ int sim_render(sim_handle *h, float *depth, float *lidar, sim_stream_t stream);
 int sim_render_taped(sim_handle *h, float *depth, float *lidar, int16_t *hits_cam,
                      int16_t *hits_lidar, sim_stream_t stream);
 
+/* Depth [NM][Rc] and lidar [NM][Rl] (DEVICE, either NULL to skip) of the
+ * current state from hit ids recorded for that state (sim_render_taped or
+ * sim_step_ex): each ray evaluates only its recorded primitive with the
+ * cast's own arithmetic, so the images equal sim_render's bit for bit at a
+ * fraction of the cost (no culling, no search).  Hits of another state
+ * give wrong images but stay memory-safe (ids outside the environment's map
+ * read as misses).  A sensor with an output needs its hits (else
+ * SIM_ERR_NULL_PTR).  Lets a closed loop keep every step's hits (2 bytes
+ * per ray) instead of casting each observation again in its backward pass. */
+int sim_render_hits(sim_handle *h, const int16_t *hits_cam, const int16_t *hits_lidar, float *depth,
+                    float *lidar, sim_stream_t stream);
+
 /* One step of the current state with actions [NM][A] (DEVICE).  Outputs
  * (DEVICE, any may be NULL): depth [NM][Rc], lidar [NM][Rl], r_ctrl [NM],
  * r_goal [NM], done [NM].  Advances the current state. */
@@ -275,6 +287,10 @@ typedef struct sim_rollout_io {
     float *depth, *lidar;
     float *imu;
     const float *imu_noise;
+    /* sim_step_ex only (sim_rollout_ex: must be NULL, SIM_ERR_INVALID_ARG):
+     * per-ray hit ids of the rendered state as sim_render_taped writes them,
+     * [NM][Rc] / [NM][Rl] int16, nullable */
+    int16_t *hits_cam, *hits_lidar;
 } sim_rollout_io;
 
 int sim_rollout_ex(sim_handle *h, const sim_rollout_io *io, sim_stream_t stream);

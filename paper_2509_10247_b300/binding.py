@@ -38,7 +38,7 @@ SYMBOLS = ["sim_version", "sim_strerror", "sim_state_dim", "sim_action_dim", "si
            "sim_launch_info", "sim_counters", "sim_step_static", "sim_profile", "sim_kernel_times",
            "sim_graph_create", "sim_graph_launch", "sim_graph_kernels", "sim_graph_destroy",
            "sim_set_scene_ex", "sim_get_gate_index", "sim_set_gate_index", "sim_rollout_ex",
-           "sim_step_ex", "sim_backward_ex", "sim_render_taped", "sim_step_backward_taped"]
+           "sim_step_ex", "sim_backward_ex", "sim_render_taped", "sim_step_backward_taped", "sim_render_hits"]
 
 # flight tasks (Sec. III-C)
 TASKS = {"reach": 0, "racing": 1}
@@ -79,7 +79,7 @@ class SimScene(C.Structure):
 
 class SimRolloutIO(C.Structure):
     _fields_ = [("actions", _vp), ("r_ctrl", _vp), ("r_goal", _vp), ("done", _vp), ("depth", _vp),
-                ("lidar", _vp), ("imu", _vp), ("imu_noise", _vp)]
+                ("lidar", _vp), ("imu", _vp), ("imu_noise", _vp), ("hits_cam", _vp), ("hits_lidar", _vp)]
 
 
 class SimGradIO(C.Structure):
@@ -243,9 +243,10 @@ def sim_set_gate_index(h, gate_k, stream=None):
     _ck(lib().sim_set_gate_index(h, _ptr(gate_k), _stream(stream)), "sim_set_gate_index")
 
 
-def _rollout_io(actions, r_ctrl, r_goal, done, depth, lidar, imu, imu_noise):
+def _rollout_io(actions, r_ctrl, r_goal, done, depth, lidar, imu, imu_noise, hits_cam=None, hits_lidar=None):
     return SimRolloutIO(*[None if t is None else _ptr(t).value
-                          for t in (actions, r_ctrl, r_goal, done, depth, lidar, imu, imu_noise)])
+                          for t in (actions, r_ctrl, r_goal, done, depth, lidar, imu, imu_noise, hits_cam,
+                                    hits_lidar)])
 
 
 def sim_rollout_ex(h, actions, r_ctrl=None, r_goal=None, done=None, depth=None, lidar=None, imu=None,
@@ -255,8 +256,8 @@ def sim_rollout_ex(h, actions, r_ctrl=None, r_goal=None, done=None, depth=None, 
 
 
 def sim_step_ex(h, actions, r_ctrl=None, r_goal=None, done=None, depth=None, lidar=None, imu=None,
-                imu_noise=None, stream=None):
-    io = _rollout_io(actions, r_ctrl, r_goal, done, depth, lidar, imu, imu_noise)
+                imu_noise=None, hits_cam=None, hits_lidar=None, stream=None):
+    io = _rollout_io(actions, r_ctrl, r_goal, done, depth, lidar, imu, imu_noise, hits_cam, hits_lidar)
     _ck(lib().sim_step_ex(h, C.byref(io), _stream(stream)), "sim_step_ex")
 
 
@@ -290,6 +291,11 @@ def sim_set_state(h, src, stream=None):
 
 def sim_render(h, depth=None, lidar=None, stream=None):
     _ck(lib().sim_render(h, _ptr(depth), _ptr(lidar), _stream(stream)), "sim_render")
+
+
+def sim_render_hits(h, hits_cam, hits_lidar, depth, lidar, stream=None):
+    _ck(lib().sim_render_hits(h, _ptr(hits_cam), _ptr(hits_lidar), _ptr(depth), _ptr(lidar), _stream(stream)),
+        "sim_render_hits")
 
 
 def sim_render_taped(h, depth, lidar, hits_cam, hits_lidar, stream=None):
@@ -487,13 +493,28 @@ class Simulator:
         return (self._empty(self.NM, self.Rc, dtype=torch.int16) if self.Rc else None,
                 self._empty(self.NM, self.Rl, dtype=torch.int16) if self.Rl else None)
 
-    def step(self, actions):
+    def step(self, actions, hits=None):
+        """One step; hits: None or a pair from hit_buffers() that receives
+        the rendered state's per-ray hit ids (as render(hits=...))."""
         o = dict(r_ctrl=self._empty(self.NM), r_goal=self._empty(self.NM, dtype=torch.int8),
                  done=self._empty(self.NM, dtype=torch.uint8),
                  depth=self._empty(self.NM, self.Rc) if self.Rc else None,
                  lidar=self._empty(self.NM, self.Rl) if self.Rl else None)
-        sim_step(self.h, actions.contiguous(), o["depth"], o["lidar"], o["r_ctrl"], o["r_goal"], o["done"])
+        if hits is None:
+            sim_step(self.h, actions.contiguous(), o["depth"], o["lidar"], o["r_ctrl"], o["r_goal"], o["done"])
+        else:
+            sim_step_ex(self.h, actions.contiguous(), o["r_ctrl"], o["r_goal"], o["done"], o["depth"], o["lidar"],
+                        hits_cam=hits[0], hits_lidar=hits[1])
         return o
+
+    def render_from_hits(self, hits):
+        """Depth and LiDAR of the current state from the hit ids recorded for
+        it (render(hits=...) or step(hits=...)): equal to render() bit for
+        bit, without casting."""
+        depth = self._empty(self.NM, self.Rc) if self.Rc else None
+        lidar = self._empty(self.NM, self.Rl) if self.Rl else None
+        sim_render_hits(self.h, hits[0], hits[1], depth, lidar)
+        return depth, lidar
 
     def rollout(self, actions, depth=True, lidar=True, out=None, imu=False, imu_noise=None):
         T, NM = self.T, self.NM

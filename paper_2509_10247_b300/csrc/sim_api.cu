@@ -18,6 +18,7 @@ cudaError_t launch_physics_bwd(const Args& a, cudaStream_t st);
 void physics_bwd_shape(int K, int M, int* warps, size_t* smem);
 cudaError_t render_call(bool vjp, bool launch, int rpt, const Args& a, int grid, int block, size_t smem,
                         cudaStream_t st, int* occ);
+cudaError_t launch_render_hits(const Args& a, int grid, cudaStream_t st);
 }  // namespace ds
 
 using ds::Args;
@@ -937,6 +938,25 @@ int sim_render(sim_handle* h, float* depth, float* lidar, sim_stream_t stream) {
     return sim_render_taped(h, depth, lidar, nullptr, nullptr, stream);
 }
 
+int sim_render_hits(sim_handle* h, const int16_t* hits_cam, const int16_t* hits_lidar, float* depth, float* lidar,
+                    sim_stream_t stream) {
+    if (!h) return SIM_ERR_NULL_PTR;
+    if (!h->have_scene) return SIM_ERR_NOT_READY;
+    if ((h->Rc && depth && !hits_cam) || (h->Rl && lidar && !hits_lidar)) return SIM_ERR_NULL_PTR;
+    cudaStream_t st = (cudaStream_t)stream;
+    Args a = base_args(h);
+    a.render_only = 1;
+    a.T = 1;
+    a.poses = h->d_pose1;
+    int rc = run_physics(h, a, st);
+    if (rc || h->S == 0) return rc;
+    int s = 0;
+    if (h->Rc) { a.sen[s].out = depth; a.sen[s].tape = const_cast<int16_t*>(hits_cam); ++s; }
+    if (h->Rl) { a.sen[s].out = lidar; a.sen[s].tape = const_cast<int16_t*>(hits_lidar); ++s; }
+    const int grid = std::max(1, std::min(h->NM, h->num_sms * 8));
+    return launch_kernel(h, SIM_KERNEL_RENDER, st, [&] { return ds::launch_render_hits(a, grid, st); });
+}
+
 int sim_step_ex(sim_handle* h, const sim_rollout_io* io, sim_stream_t stream) {
     if (!h || !io || !io->actions) return SIM_ERR_NULL_PTR;
     if (!h->have_scene) return SIM_ERR_NOT_READY;
@@ -953,8 +973,8 @@ int sim_step_ex(sim_handle* h, const sim_rollout_io* io, sim_stream_t stream) {
     int rc = run_physics(h, a, st);
     if (rc || h->S == 0) return rc;
     int s = 0;
-    if (h->Rc) { a.sen[s].out = io->depth; a.sen[s].tape = nullptr; ++s; }
-    if (h->Rl) { a.sen[s].out = io->lidar; a.sen[s].tape = nullptr; ++s; }
+    if (h->Rc) { a.sen[s].out = io->depth; a.sen[s].tape = io->hits_cam; ++s; }
+    if (h->Rl) { a.sen[s].out = io->lidar; a.sen[s].tape = io->hits_lidar; ++s; }
     return run_render(h, 0, a, st);
 }
 
@@ -969,6 +989,7 @@ int sim_step(sim_handle* h, const float* actions, float* depth, float* lidar, fl
 
 int sim_rollout_ex(sim_handle* h, const sim_rollout_io* io, sim_stream_t stream) {
     if (!h || !io || !io->actions) return SIM_ERR_NULL_PTR;
+    if (io->hits_cam || io->hits_lidar) return SIM_ERR_INVALID_ARG;  // the rollout tapes its hits itself
     if (!h->have_scene) return SIM_ERR_NOT_READY;
     if (h->cfg.terminate && !h->have_pool) return SIM_ERR_NOT_READY;
     cudaStream_t st = (cudaStream_t)stream;

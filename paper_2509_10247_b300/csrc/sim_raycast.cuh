@@ -108,6 +108,58 @@ __device__ __forceinline__ float safe_rcp(float d) {
     return __frcp_rn(fabsf(d) < 1e-20f ? copysignf(1e-20f, d) : d);
 }
 
+// Origin-relative list entries of the four kinds (o: sensor origin).  The
+// list builder and hit_distance both build them here, so a recorded hit
+// reproduces the cast's distance bit for bit.
+// Sphere (c, r): (oc, -sqrt(C)) and (r^2, r), C = |oc|^2 - r^2 (<= 0: inside).
+__device__ __forceinline__ bool sphere_list_entry(const float4& sp, const float* o, float4& e, float2& x) {
+    const float oc[3] = {sp.x - o[0], sp.y - o[1], sp.z - o[2]};
+    const float r2 = sp.w * sp.w;
+    const float C = dot3(oc, oc) - r2;
+    e = make_float4(oc[0], oc[1], oc[2], -sqrt_approx(fmaxf(C, 0.f)));
+    x = make_float2(r2, sp.w);
+    return C <= 0.f;
+}
+
+// Box corners -> (centre, bounding radius), (half extents, 0).
+__device__ __forceinline__ void prep_box(const float4& lo, const float4& hi, float4& cb, float4& hb) {
+    const float h[3] = {0.5f * (hi.x - lo.x), 0.5f * (hi.y - lo.y), 0.5f * (hi.z - lo.z)};
+    cb = make_float4(0.5f * (lo.x + hi.x), 0.5f * (lo.y + hi.y), 0.5f * (lo.z + hi.z), sqrtf(dot3(h, h)));
+    hb = make_float4(h[0], h[1], h[2], 0.f);
+}
+
+// Cylinder (axis x, y, radius; z range): (centre - o, bounding tangent) and
+// (r^2, half height, 0, bounding radius).  Returns whether o is inside.
+__device__ __forceinline__ bool cyl_list_entry(const float4& a0, const float4& a1, const float* o, float4& c0,
+                                               float4& c1) {
+    const float hz = 0.5f * (a1.y - a1.x);
+    const float c[3] = {a0.x - o[0], a0.y - o[1], 0.5f * (a1.x + a1.y) - o[2]};
+    const float r2 = a0.z * a0.z;
+    const bool in = fmaf(c[0], c[0], c[1] * c[1]) <= r2 && a1.x <= o[2] && a1.y >= o[2];
+    const float rho = sqrtf(fmaf(hz, hz, r2));
+    const float cb = dot3(c, c) - rho * rho;
+    c0 = make_float4(c[0], c[1], c[2], cb > 0.f ? sqrtf(cb) : -1e30f);
+    c1 = make_float4(r2, hz, 0.f, rho);
+    return in;
+}
+
+// Gate frame: (centre - o, bounding tangent), (cos, sin, half depth,
+// bounding radius), (opening half size, outer half size, -n.c, -l.c).
+// Returns whether o is inside one of its bars.
+__device__ __forceinline__ bool gate_list_entry(const float4& a0, const float4& a1, const float* o, float4& g0,
+                                                float4& g1, float4& g2) {
+    const float W = a0.w + a1.z;
+    const float c[3] = {a0.x - o[0], a0.y - o[1], a0.z - o[2]};
+    const float un = -fmaf(a1.x, c[0], a1.y * c[1]), ul = -fmaf(a1.x, c[1], -a1.y * c[0]), uz = -c[2];
+    const bool in = fabsf(un) <= a1.w && fabsf(ul) <= W && fabsf(uz) <= W && !(fabsf(ul) < a0.w && fabsf(uz) < a0.w);
+    const float rho = sqrtf(fmaf(a1.w, a1.w, 2.f * W * W));
+    const float cb = dot3(c, c) - rho * rho;
+    g0 = make_float4(c[0], c[1], c[2], cb > 0.f ? sqrtf(cb) : -1e30f);
+    g1 = make_float4(a1.x, a1.y, a1.w, rho);
+    g2 = make_float4(a0.w, W, un, ul);
+    return in;
+}
+
 // Cull the map for the sensor at origin o with rotation R into L, keeping
 // index order within each kind (ties resolve to the lowest id).  Executed
 // by one full warp; returns the list's meta.  EXTRA: the map kinds include
@@ -142,13 +194,11 @@ __device__ inline int4 warp_build_list(const MapView& mv, const float* o, const 
     __syncwarp();
     for (int j = lane; j < nsk; j += 32) {
         const int k = L.id[j];
-        const float4 sp = prim[k];
-        const float oc[3] = {sp.x - o[0], sp.y - o[1], sp.z - o[2]};
-        const float r2 = sp.w * sp.w;
-        const float C = dot3(oc, oc) - r2;
-        if (C <= 0.f) inside = min(inside, k);
-        L.sph[j] = make_float4(oc[0], oc[1], oc[2], -sqrt_approx(fmaxf(C, 0.f)));
-        L.sx[j] = make_float2(r2, sp.w);
+        float4 e;
+        float2 x;
+        if (sphere_list_entry(prim[k], o, e, x)) inside = min(inside, k);
+        L.sph[j] = e;
+        L.sx[j] = x;
     }
     cnt = 0;
     for (int base = 0; base < nb; base += 32) {
@@ -203,16 +253,9 @@ __device__ inline int4 warp_build_list(const MapView& mv, const float* o, const 
         bool keep = false;
         float4 c0 = make_float4(0.f, 0.f, 0.f, 0.f), c1 = c0;
         if (k < mv.nc) {
-            const float4 a0 = mv.cyl(k)[0], a1 = mv.cyl(k)[1];
-            const float hz = 0.5f * (a1.y - a1.x);
-            const float c[3] = {a0.x - o[0], a0.y - o[1], 0.5f * (a1.x + a1.y) - o[2]};
-            const float r2 = a0.z * a0.z;
-            if (fmaf(c[0], c[0], c[1] * c[1]) <= r2 && a1.x <= o[2] && a1.y >= o[2]) inside = min(inside, ns + nb + k);
-            const float rho = sqrtf(fmaf(hz, hz, r2));
-            keep = !cull || cull_keep(ck, R, c, rho);
-            const float cb = dot3(c, c) - rho * rho;
-            c0 = make_float4(c[0], c[1], c[2], cb > 0.f ? sqrtf(cb) : -1e30f);
-            c1 = make_float4(r2, hz, 0.f, rho);
+            if (cyl_list_entry(mv.cyl(k)[0], mv.cyl(k)[1], o, c0, c1)) inside = min(inside, ns + nb + k);
+            const float c[3] = {c0.x, c0.y, c0.z};
+            keep = !cull || cull_keep(ck, R, c, c1.w);
         }
         unsigned bal = __ballot_sync(0xffffffffu, keep);
         if (keep) {
@@ -228,18 +271,9 @@ __device__ inline int4 warp_build_list(const MapView& mv, const float* o, const 
         bool keep = false;
         float4 g0 = make_float4(0.f, 0.f, 0.f, 0.f), g1 = g0, g2 = g0;
         if (k < mv.ng) {
-            const float4 a0 = mv.gate(k)[0], a1 = mv.gate(k)[1];
-            const float W = a0.w + a1.z;
-            const float c[3] = {a0.x - o[0], a0.y - o[1], a0.z - o[2]};
-            const float un = -fmaf(a1.x, c[0], a1.y * c[1]), ul = -fmaf(a1.x, c[1], -a1.y * c[0]), uz = -c[2];
-            if (fabsf(un) <= a1.w && fabsf(ul) <= W && fabsf(uz) <= W && !(fabsf(ul) < a0.w && fabsf(uz) < a0.w))
-                inside = min(inside, ns + nb + mv.nc + k);
-            const float rho = sqrtf(fmaf(a1.w, a1.w, 2.f * W * W));
-            keep = !cull || cull_keep(ck, R, c, rho);
-            const float cb = dot3(c, c) - rho * rho;
-            g0 = make_float4(c[0], c[1], c[2], cb > 0.f ? sqrtf(cb) : -1e30f);
-            g1 = make_float4(a1.x, a1.y, a1.w, rho);
-            g2 = make_float4(a0.w, W, un, ul);
+            if (gate_list_entry(mv.gate(k)[0], mv.gate(k)[1], o, g0, g1, g2)) inside = min(inside, ns + nb + mv.nc + k);
+            const float c[3] = {g0.x, g0.y, g0.z};
+            keep = !cull || cull_keep(ck, R, c, g1.w);
         }
         unsigned bal = __ballot_sync(0xffffffffu, keep);
         if (keep) {
@@ -335,6 +369,16 @@ __device__ __forceinline__ void gate_test(const float4& g0, const float4& g1, co
     if (t > 0.f && t < tb) { tb = t; bi = slot; }
 }
 
+// Near root of a sphere entry e (oc, -sqrt(C)), r2 = r^2, for a ray d that
+// reaches it (v = d.oc - sqrt(C) >= 0): perpendicular-offset form
+// b - sqrt(r^2 - |oc - b d|^2), b = d.oc.
+__device__ __forceinline__ float sphere_near_root(const float4& e, float r2, float v, float dx, float dy, float dz) {
+    const float b = v - e.w;
+    const float fx = fmaf(-b, dx, e.x), fy = fmaf(-b, dy, e.y), fz = fmaf(-b, dz, e.z);
+    const float d2 = fmaxf(r2 - fmaf(fx, fx, fmaf(fy, fy, fz * fz)), 0.f);
+    return b - sqrt_approx(d2);
+}
+
 // One sphere list entry against the lane's rays: the reach test
 // d.oc - sqrt(C) >= 0 on ray pairs, then the near root (perpendicular-offset
 // form) for the rays that reach it.
@@ -350,12 +394,7 @@ __device__ __forceinline__ void sphere_entry(const WList& L, int k, const RayPai
             if (r >= RPT) continue;
             const float v = lo_hi(v2, q);
             if (v >= 0.f) {
-                const float dxr = lo_hi(P.x[p], q), dyr = lo_hi(P.y[p], q), dzr = lo_hi(P.z[p], q);
-                const float r2 = L.sx[k].x;
-                const float b = v - e.w;
-                const float fx = fmaf(-b, dxr, e.x), fy = fmaf(-b, dyr, e.y), fz = fmaf(-b, dzr, e.z);
-                const float d2 = fmaxf(r2 - fmaf(fx, fx, fmaf(fy, fy, fz * fz)), 0.f);
-                const float t = b - sqrt_approx(d2);
+                const float t = sphere_near_root(e, L.sx[k].x, v, lo_hi(P.x[p], q), lo_hi(P.y[p], q), lo_hi(P.z[p], q));
                 if (t < tb[r]) { tb[r] = t; bi[r] = k; }
             }
         }
@@ -416,6 +455,48 @@ __device__ __forceinline__ void cast_rest(const WList& L, const LCap& cap, int n
 #pragma unroll
         for (int r = 0; r < RPT; ++r) gate_test(g0, g1, g2, dx[r], dy[r], iz[r], base + k, tb[r], bi[r]);
     }
+}
+
+// Distance along the ray (origin o, world direction d) to primitive id of
+// the map mv (the global map block: boxes as corners), with the entry and
+// the test the cast applies to that primitive, so that for a hit the cast
+// recorded it equals the cast's distance bit for bit.  +inf if the test
+// reports no hit.
+template <bool EXTRA>
+__device__ __forceinline__ float hit_distance(const MapView& mv, int id, const float* o, float dx, float dy,
+                                              float dz) {
+    float tb = CUDART_INF_F;
+    int bi = -1;
+    if (id < mv.ns) {
+        float4 e;
+        float2 x;
+        sphere_list_entry(mv.prim[id], o, e, x);
+        const float v = fmaf(dx, e.x, fmaf(dy, e.y, fmaf(dz, e.z, e.w)));  // the cast's packed product, per lane
+        return v >= 0.f ? sphere_near_root(e, x.x, v, dx, dy, dz) : CUDART_INF_F;
+    }
+    if (id < mv.ns + mv.nb) {
+        float4 cb, hb;
+        prep_box(mv.box(id - mv.ns)[0], mv.box(id - mv.ns)[1], cb, hb);
+        const float4 c = make_float4(cb.x - o[0], cb.y - o[1], cb.z - o[2], 0.f);
+        box_test(c, hb, safe_rcp(dx), safe_rcp(dy), safe_rcp(dz), 0, tb, bi);
+        return tb;
+    }
+    if (!EXTRA) return CUDART_INF_F;
+    const float iz = safe_rcp(dz);
+    if (id < mv.ns + mv.nb + mv.nc) {
+        float4 c0, c1;
+        const int k = id - mv.ns - mv.nb;
+        cyl_list_entry(mv.cyl(k)[0], mv.cyl(k)[1], o, c0, c1);
+        const float a = fmaf(dx, dx, dy * dy);
+        const bool vt = a < 1e-12f;
+        cyl_test(c0, c1, dx, dy, vt ? 0.f : __frcp_rn(a), vt, iz, 0, tb, bi);
+        return tb;
+    }
+    float4 g0, g1, g2;
+    const int k = id - mv.ns - mv.nb - mv.nc;
+    gate_list_entry(mv.gate(k)[0], mv.gate(k)[1], o, g0, g1, g2);
+    gate_test(g0, g1, g2, dx, dy, iz, 0, tb, bi);
+    return tb;
 }
 
 // Sweep RPT rays per lane over a list.  tb holds each ray's best distance
@@ -645,11 +726,10 @@ __device__ inline bool stage_map(const Args& a, unsigned char* sm, int map, cons
 __device__ inline void prep_boxes(unsigned char* sm, const Args& a, int ns, int nb) {
     float4* prim = reinterpret_cast<float4*>(sm + a.sm.prim);
     for (int b = threadIdx.x; b < nb; b += blockDim.x) {
-        const float4 lo = prim[ns + 2 * b], hi = prim[ns + 2 * b + 1];
-        const float h[3] = {0.5f * (hi.x - lo.x), 0.5f * (hi.y - lo.y), 0.5f * (hi.z - lo.z)};
-        prim[ns + 2 * b] = make_float4(0.5f * (lo.x + hi.x), 0.5f * (lo.y + hi.y), 0.5f * (lo.z + hi.z),
-                                       sqrtf(dot3(h, h)));
-        prim[ns + 2 * b + 1] = make_float4(h[0], h[1], h[2], 0.f);
+        float4 cb, hb;
+        prep_box(prim[ns + 2 * b], prim[ns + 2 * b + 1], cb, hb);
+        prim[ns + 2 * b] = cb;
+        prim[ns + 2 * b + 1] = hb;
     }
     __syncthreads();
 }

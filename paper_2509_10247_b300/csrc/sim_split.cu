@@ -331,6 +331,51 @@ __global__ void __launch_bounds__(256, 4) k_render(const Args a) {
     if (a.counters && threadIdx.x < 4 && s_cnt[threadIdx.x]) atomicAdd(a.counters + threadIdx.x, s_cnt[threadIdx.x]);
 }
 
+// ------------------------------------------------------ render from hits
+// Depth / range of the current poses from recorded hit ids (sen.tape read,
+// sen.out written): a CTA per agent (grid-stride), a thread per ray slot,
+// each evaluating only its recorded primitive with the cast's own entry and
+// test (hit_distance), so the image equals a full render of the same state
+// bit for bit.  Ids: -1 miss (range), -2 origin inside a primitive (0); ids
+// outside the map are treated as misses.
+template <bool EXTRA>
+__global__ void __launch_bounds__(256) k_render_hits(const Args a) {
+    const int R0 = a.sen[0].R, Rt = R0 + (a.S > 1 ? a.sen[1].R : 0);
+    for (int i = blockIdx.x; i < a.NM; i += gridDim.x) {
+        float o[3], R[9];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) o[k] = a.poses[(size_t)i * 12 + k];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) R[k] = a.poses[(size_t)i * 12 + 3 + k];
+        const int map = a.env_map[i / a.M];
+        const MapView mv = map_view(a, map, a.prims + a.map_off[map]);
+        const int np = mv.count();
+        for (int jj = threadIdx.x; jj < Rt; jj += blockDim.x) {
+            const int si = jj < R0 ? 0 : 1, j = si ? jj - R0 : jj;
+            const Sensor& sen = a.sen[si];
+            if (!sen.out || !sen.tape) continue;
+            const size_t at = (size_t)i * sen.R + out_index(sen, j);
+            const int id = sen.tape[at];
+            float v = sen.range;
+            if (id == -2) {
+                v = 0.f;
+            } else if (id >= 0 && id < np) {
+                float d[3];
+                const float4 db = ray_dir(sen, R, j, d);
+                const float t = hit_distance<EXTRA>(mv, id, o, d[0], d[1], d[2]);
+                v = fminf(sen.kind == 0 ? t * db.w : t, sen.range);
+            }
+            sen.out[at] = v;
+        }
+    }
+}
+
+cudaError_t launch_render_hits(const Args& a, int grid, cudaStream_t st) {
+    if (a.nc_max > 0 || a.ng_max > 0) k_render_hits<true><<<grid, 256, 0, st>>>(a);
+    else k_render_hits<false><<<grid, 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
 // ---------------------------------------------------------- render adjoint
 // One warp per (step, agent) item: the cotangents of all its rays (every
 // sensor) reduce, in a fixed order, to the pose cotangent gposes[t][i] =

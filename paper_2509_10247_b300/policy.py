@@ -109,11 +109,14 @@ class ClosedLoop:
     gives the action cotangent, the policy's backward pass the parameter
     gradient and the observation cotangent, whose depth / LiDAR part feeds
     the previous step's adjoint and whose state part joins the state
-    cotangent.  The re-render of state t records each ray's hit primitive,
-    which the adjoint of step t - 1 (the step producing state t) gathers
-    instead of casting the rays a third time; the last step's observation
-    feeds no action, so its adjoint has no ray term.  Rigid-body agents, one
-    per environment."""
+    cotangent.  The last step's observation feeds no action, so its adjoint
+    has no ray term.  Rays are cast once per step: the forward pass records
+    every ray's hit primitive (2 bytes per ray and step, kept when it fits in
+    free device memory; store_hits forces either way), the backward pass
+    rebuilds each observation from its hits (sim_render_hits, bit for bit)
+    and the adjoint of step t - 1 gathers the hits of state t.  Without the
+    stored hits the backward pass re-renders state t, recording its hits
+    for that adjoint.  Rigid-body agents, one per environment."""
 
     def __init__(self, p, inp, device="cuda", **ex):
         assert p["model"] == "rigid" and p["n_agent"] == 1
@@ -123,35 +126,52 @@ class ClosedLoop:
         self.pol = Policy.for_workload(p, device=self.device)
         self.targets = torch.as_tensor(inp["targets"], dtype=torch.float32, device=self.device)
 
-    def gradient(self, s0, g_r, T=None):
+    def hits_bytes(self, T=None):
+        T = self.p["horizon"] if T is None else T
+        return 2 * T * self.p["n_env"] * (self.sim.Rc + self.sim.Rl)
+
+    def gradient(self, s0, g_r, T=None, store_hits=None):
         sim, pol, dev = self.sim, self.pol, self.device
         T = self.p["horizon"] if T is None else T
         N = self.p["n_env"]
         Rc, Rl = sim.Rc, sim.Rl
+        if not (Rc or Rl):
+            store_hits = False
+        elif store_hits is None:
+            store_hits = self.hits_bytes(T) + (24 << 30) < torch.cuda.mem_get_info(dev)[0]
+        self.stored_hits = store_hits
+        if store_hits:
+            tape = (torch.empty(T, N, Rc, dtype=torch.int16, device=dev) if Rc else None,
+                    torch.empty(T, N, Rl, dtype=torch.int16, device=dev) if Rl else None)
+            hits_of = lambda t: tuple(None if x is None else x[t] for x in tape)
         states = torch.empty(T + 1, N, 13, device=dev)
         actions = torch.empty(T, N, 4, device=dev)
         done = torch.empty(T, N, dtype=torch.uint8, device=dev)
         r = torch.empty(T, N, device=dev)
         states[0] = s0
         sim.reset(states[0])
-        depth, lidar = sim.render()
+        depth, lidar = sim.render(hits=hits_of(0) if store_hits else None)
         for t in range(T):
             pol.act(states[t], self.targets, depth, lidar, out=actions[t])
-            o = sim.step(actions[t])
+            o = sim.step(actions[t], hits=hits_of(t + 1) if store_hits and t + 1 < T else None)
             r[t], done[t] = o["r_ctrl"], o["done"]
             depth, lidar = o["depth"], o["lidar"]
             states[t + 1] = sim.get_state()
         loss = float((g_r[:T] * r).sum())
         g_s = torch.zeros(N, 13, device=dev)
         g_dep = g_lid = hits = None
-        hit_buf = sim.hit_buffers() if Rc or Rl else None
+        hit_buf = sim.hit_buffers() if (Rc or Rl) and not store_hits else None
         scratch = torch.empty(N, 4, device=dev)
         pol.grads(reset=True)
         for t in range(T - 1, -1, -1):
             g_a, g_st = sim.step_backward(states[t], actions[t], done[t], g_s, g_r[t], g_dep, g_lid, hits=hits)
             sim.set_state(states[t])
-            depth, lidar = sim.render(hits=hit_buf)
-            hits = hit_buf
+            if store_hits:
+                hits = hits_of(t)
+                depth, lidar = sim.render_from_hits(hits)
+            else:
+                depth, lidar = sim.render(hits=hit_buf)
+                hits = hit_buf
             pol.act(states[t], self.targets, depth, lidar, out=scratch)
             g_dep = torch.empty(N, Rc, device=dev) if Rc else None
             g_lid = torch.empty(N, Rl, device=dev) if Rl else None

@@ -112,6 +112,7 @@ def test_null_pointers(lib):
     assert lib.sim_set_gate_index(None, None, None) == -2
     assert lib.sim_last_status(None, None, None) == -2
     assert lib.sim_render_taped(None, None, None, None, None, None) == -2
+    assert lib.sim_render_hits(None, None, None, None, None, None) == -2
     assert lib.sim_step_backward_taped(None, None, None, None, None, None, None, None, None, None, None, None,
                                        None) == -2
 
@@ -132,6 +133,15 @@ def test_graph_and_profiling_null_pointers(lib):
     assert lib.sim_graph_launch(None, None) == -2
     assert lib.sim_graph_kernels(None, None) == -2
     assert lib.sim_graph_destroy(None) == 0
+
+
+def test_rollout_io_layout_matches_header():
+    src = open(os.path.join(ROOT, "include", "diffsim.h")).read()
+    body = src[src.index("typedef struct sim_rollout_io {"):src.index("} sim_rollout_io;")]
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    n = sum(len(d.split(",")) for d in re.findall(r"\*\s*([^;]+);", body))
+    assert ctypes.sizeof(binding.SimRolloutIO) == 8 * n
+    assert [f for f, _ in binding.SimRolloutIO._fields_][-2:] == ["hits_cam", "hits_lidar"]
 
 
 def test_graph_io_layout_matches_header():

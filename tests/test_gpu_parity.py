@@ -206,6 +206,35 @@ def test_step_backward_with_recorded_hits_matches_recast(pair):
         with pytest.raises(RuntimeError):  # a cotangent without its sensor's hits
             sim.step_backward(s_t, a2, o["done"], g_sn, g_r, g_d, g_l, hits=(None, hits[1]))
 
+
+def test_render_from_hits_matches_render(pair):
+    """sim_render_hits rebuilds a state's depth / LiDAR from the hit ids that
+    sim_step_ex or sim_render_taped recorded for it, equal to a full render
+    bit for bit (every primitive kind, misses, clamps, origins inside)."""
+    p = pair.p
+    if p["cam"] is None and p["lidar"] is None:
+        pytest.skip("no sensor")
+    sim = Simulator(p, pair.inp)
+    sim.reset(dev(pair.inp["s0"]))
+    for t in range(3):
+        hits = sim.hit_buffers()
+        o = sim.step(pair.act[t], hits=hits)
+        depth, lidar = sim.render_from_hits(hits)
+        for got, ref in ((depth, o["depth"]), (lidar, o["lidar"])):
+            if ref is not None:
+                assert torch.equal(got, ref), t
+        d2, l2 = sim.render()
+        for got, ref in ((d2, o["depth"]), (l2, o["lidar"])):
+            if ref is not None:
+                assert torch.equal(got, ref), t
+        h2 = sim.hit_buffers()
+        sim.render(hits=h2)
+        for a, b in zip(hits, h2):
+            if a is not None:
+                assert torch.equal(a, b)
+    torch.cuda.synchronize()
+    assert sim.status() == 0
+
 def test_culling_is_result_preserving(pair):
     p = pair.p
     if p["cam"] is None and p["lidar"] is None:

@@ -98,7 +98,9 @@ def test_closed_loop_gradient_matches_oracle():
     g_r = synth.cotangents(p, seed=9)["g_r"]
     cl = ClosedLoop(p, inp)
     cl.pol.set_params(flat)
-    L, g, rec = cl.gradient(dev(inp["s0"]), dev(g_r))
+    L, g, rec = cl.gradient(dev(inp["s0"]), dev(g_r), store_hits=True)
+    L2, g2, _ = cl.gradient(dev(inp["s0"]), dev(g_r), store_hits=False)
+    assert L2 == L and np.array_equal(g, g2)
     Lo, go, reco = PO.closed_loop(oracle.Oracle(p, inp), PO.split(p, flat), inp["s0"], g_r)
     print("closed loop: loss %.6f vs %.6f, max |da| %.2e" % (L, Lo, np.abs(host(rec["actions"]) - reco["actions"]).max()))
     assert abs(L - Lo) <= 1e-3 * abs(Lo)
@@ -123,3 +125,6 @@ def test_closed_loop_full_width_observation():
     assert cl.pol.status() == 0 and cl.sim.status() == 0
     L2, g2, rec2 = cl.gradient(dev(inp["s0"]), g_r)
     assert L2 == L and np.array_equal(g, g2)  # deterministic
+    # kept hits (observations rebuilt from them) vs re-rendering: bit for bit
+    L3, g3, _ = cl.gradient(dev(inp["s0"]), g_r, store_hits=not cl.stored_hits)
+    assert L3 == L and np.array_equal(g, g3)
