@@ -510,7 +510,7 @@ __global__ void __launch_bounds__(256, TAPE ? 4 : 3) k_render_vjp(const Args a) 
 // (cut by a reset), reward -> state before reset and action, dynamics ->
 // previous state.
 template <bool EXT>
-__global__ void __launch_bounds__(128) k_physics_bwd(const Args a) {
+__global__ void __launch_bounds__(128, EXT ? 4 : 5) k_physics_bwd(const Args a) {
     extern __shared__ __align__(16) float segm[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int env = blockIdx.x * (blockDim.x >> 5) + wid;
