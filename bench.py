@@ -35,9 +35,14 @@ METRIC = "env-steps/s (fwd+adjoint, with depth) at 16k envs vs roofline; Grays/s
 UNIT = "env-steps/s"
 # launch configuration timed by the bench (and used by the full-size parity test)
 BENCH_EXEC = dict(ckpt_every=16, tape_hits=1, cull=1)
-# algorithmic FP32 operations of one ray-primitive test:
-# sphere: b = d.oc (5), disc = b^2 - C (2), can-beat test (3); box: 6 slab
-# products, 6 per-axis min/max, 4 entry/exit min/max
+# algorithmic work of one ray-primitive test after the per-origin list entry,
+# in FP32-pipe instructions (an FMA counts once): sphere 6 (3 for b = d.oc,
+# 1 for b^2 - C, 1 subtraction, 1 min / select; the square root of a hit
+# runs on the SFU), box 14 (6 slab products, 6 per-axis min / max, the
+# entry max and exit min).  The same tests in FLOP (an FMA counts twice):
+# sphere 10, box 16.
+OPS_SPHERE_TEST = 6
+OPS_BOX_TEST = 14
 FLOP_SPHERE_TEST = 10
 FLOP_BOX_TEST = 16
 
@@ -81,9 +86,9 @@ def source_hash():
     return h.hexdigest()[:16]
 
 
-def peak_fp32_tflops(num_sms, sm_mhz):
-    # FP32 FMA issue: 128 lanes per SM, 2 FLOP per FMA
-    return 2.0 * 128 * num_sms * sm_mhz * 1e6 / 1e12
+def peak_fp32_tinst(num_sms, sm_mhz):
+    # FP32-pipe issue: 128 lanes per SM, one instruction per lane and cycle
+    return 128.0 * num_sms * sm_mhz * 1e6 / 1e12
 
 
 def config_of(p, extra=None):
@@ -329,10 +334,11 @@ def run_ours(args, rank, world):
         return 0
     # roofline of the dominant kernel: k_render (FP32 ray casting), per launch
     props = torch.cuda.get_device_properties(dev)
+    ops = OPS_SPHERE_TEST * cnt["sphere_tests"] + OPS_BOX_TEST * cnt["box_tests"]
     flop = FLOP_SPHERE_TEST * cnt["sphere_tests"] + FLOP_BOX_TEST * cnt["box_tests"]
     render_ms = kt["render"][0] / max(kt["render"][1], 1)
-    achieved = flop / (render_ms / 1e3) / 1e12
-    peak = peak_fp32_tflops(props.multi_processor_count, 2032.0)
+    achieved = ops / (render_ms / 1e3) / 1e12
+    peak = peak_fp32_tinst(props.multi_processor_count, 2032.0)
     traffic = None
     tfile = os.path.join(ROOT, "profiles", "traffic.txt")
     if os.path.exists(tfile):
@@ -341,13 +347,18 @@ def run_ours(args, rank, world):
                 and "render_bytes_per_launch" in tj:
             traffic = float(tj["render_bytes_per_launch"])
     per_kernel = {k: {"ms_per_launch": v[0] / max(v[1], 1), "launches": v[1]} for k, v in kt.items()}
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tinst/s",
                 "frac": achieved / peak, "traffic": traffic,
                 "kernel": "k_render (ray casting of all T steps)", "kernel_ms": render_ms,
-                "peak_basis": "FP32 FMA issue, %d SMs x 128 lanes x 2 x 2032 MHz (derived, not measured)"
-                % props.multi_processor_count,
+                "peak_basis": "FP32-pipe issue, %d SMs x 128 lanes x 2032 MHz, one instruction (an FMA counts "
+                              "once) per lane and cycle (derived, not measured)" % props.multi_processor_count,
+                "work_basis": "per test after culling: sphere %d, box %d FP32-pipe instructions"
+                              % (OPS_SPHERE_TEST, OPS_BOX_TEST),
                 "tests_per_launch": cnt["sphere_tests"] + cnt["box_tests"],
-                "flop_per_launch": flop, "kernels": per_kernel}
+                "sphere_tests_per_launch": cnt["sphere_tests"], "box_tests_per_launch": cnt["box_tests"],
+                "ops_per_launch": ops, "flop_per_launch": flop,
+                "tflops": flop / (render_ms / 1e3) / 1e12, "frac_flop": flop / (render_ms / 1e3) / 1e12 / (2 * peak),
+                "kernels": per_kernel}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
