@@ -117,3 +117,36 @@ def test_uneven_maps_long_horizon_ckpt():
     sa, ss = grad_spread(pr.orc, p, pr.inp, rec, g_r, g_d)
     compare_grads(p, host(ga), ga_o, bad, "g_a", spread=sa)
     compare_grads(p, host(gs), gs_o, bad, "g_s0", spread=ss)
+
+
+def test_foreign_hit_ids_stay_in_bounds():
+    """Hit buffers that do not belong to the state (arbitrary int16 ids):
+    the images rebuilt from them read the maximum range for ids outside the
+    map, 0 for -2, and stay finite; the step adjoint gathering them ignores
+    ids outside the map and reports no error."""
+    p = synth.params(model="rigid", n_env=12, horizon=3, cam=(12, 8, 90.0, 10.0), lidar=(4, 32, -15.0, 15.0, 10.0),
+                     map_counts=[(6, 3, 2, 2), (4, 2, 0, 0)], n_maps=2, obst_lo=(-6, -6, -3), obst_hi=(6, 6, 3))
+    inp = synth.make_inputs(p, seed=4)
+    sim = Simulator(p, inp)
+    sim.reset(dev(inp["s0"]))
+    rng = np.random.default_rng(9)
+    hits = tuple(torch.as_tensor(rng.integers(-32768, 32768, (sim.NM, R)), dtype=torch.int16, device="cuda")
+                 for R in (sim.Rc, sim.Rl))
+    depth, lidar = sim.render_from_hits(hits)
+    torch.cuda.synchronize()
+    counts = np.diff(inp["sph_off"]) + np.diff(inp["box_off"]) + np.diff(inp["cyl_off"]) + np.diff(inp["gate_off"])
+    n_of_agent = counts[inp["env_map"]].repeat(p["n_agent"])[:, None]
+    for img, h, rng_max in ((depth, hits[0], p["cam"][3]), (lidar, hits[1], p["lidar"][4])):
+        v, ids = host(img), host(h).astype(np.int64)
+        assert np.isfinite(v).all() and (v <= rng_max).all()
+        assert (v[(ids < -2) | (ids == -1) | (ids >= n_of_agent)] == np.float32(rng_max)).all()
+        assert (v[ids == -2] == 0).all()
+    a = dev(inp["actions"][0])
+    s_t = sim.get_state().clone()
+    o = sim.step(a)
+    g = torch.ones(sim.NM, device="cuda")
+    ga, gs = sim.step_backward(s_t, a, o["done"], torch.zeros(sim.NM, sim.D, device="cuda"), g,
+                               torch.ones(sim.NM, sim.Rc, device="cuda"), torch.ones(sim.NM, sim.Rl, device="cuda"),
+                               hits=hits)
+    torch.cuda.synchronize()
+    assert sim.status() in (0, 1)  # a foreign hit may give a non-finite gradient (flagged), never a fault
