@@ -130,7 +130,7 @@ def cpu_rate(p, inp, target_s):
     import oracle
     n = max(1, min(8, p["n_env"]))
     dt, steps = oracle_sample(p, inp, n)
-    while dt < 0.3 * target_s and n < p["n_env"]:
+    while dt < 0.7 * target_s and n < p["n_env"]:
         n = min(p["n_env"], max(n + 1, int(n * min(8.0, target_s / max(dt, 1e-3)))))
         dt, steps = oracle_sample(p, inp, n)
     return steps / dt, n, dt, oracle.max_threads()
