@@ -469,9 +469,31 @@ int run_physics_bwd(sim_handle* h, const Args& a, cudaStream_t st) {
     return launch_kernel(h, SIM_KERNEL_PHYSICS_BWD, st, [&] { return ds::launch_physics_bwd(a, st); });
 }
 
+// Ray parts per (step, agent, sensor) item of the forward render: when an
+// environment's T x M x S items are fewer than the CTA's warps, each sensor's
+// chunks are split into parts, the warps' worth of parts shared among the
+// sensors in proportion to their chunk counts (every part builds its own
+// list, so no more parts than warps).
+void set_render_parts(const sim_handle* h, Args& a) {
+    int nch[ds::MAX_SENSORS] = {0, 0}, tot = 0;
+    for (int s = 0; s < h->S; ++s) tot += nch[s] = std::max(1, (h->sen[s].R + 32 * h->rpt - 1) / (32 * h->rpt));
+    const int items = a.T * h->M;
+    const int want = (h->nw + items - 1) / items;  // parts per (step, agent) over all sensors
+    for (int s = 0; s < ds::MAX_SENSORS; ++s) a.rparts[s] = 1;
+    if (want <= h->S) return;
+    int left = want;
+    for (int s = 0; s < h->S; ++s) {
+        const int q = s + 1 < h->S ? std::max(1, (int)std::lround((double)want * nch[s] / tot)) : left;
+        a.rparts[s] = std::max(1, std::min(q, nch[s]));
+        left -= a.rparts[s];
+        if (left < h->S - s - 1) left = h->S - s - 1;
+    }
+}
+
 // which: 0 render, 1 render adjoint (rollout), 2 render adjoint re-casting
 // (step), 3 render adjoint gathering caller-supplied hit ids (step)
 int run_render(sim_handle* h, int which, Args& a, cudaStream_t st) {
+    if (which == 0) set_render_parts(h, a);
     const ds::Smem& sm = which == 0 ? h->sm_r : (which == 1 ? h->sm_rv : (which == 2 ? h->sm_rvs : h->sm_rvt));
     const int grid = which == 0 ? h->grid_r : (which == 1 ? h->grid_rv : (which == 2 ? h->grid_rvs : h->grid_rvt));
     a.sm = sm;

@@ -77,7 +77,8 @@ struct Args {
     const uint8_t* done_rd;     // adjoint: [T][NM] done flags of the forward pass
     float* poses;               // [T][NM][12] sensor pose per step (origin, row-major R)
     float* gposes;              // [T][NM][parts][12] cotangent of the poses, per ray part
-    int parts;                  // ray parts per (step, agent) item of the render kernels
+    int parts;                  // ray parts per (step, agent) item of the render adjoint
+    int rparts[MAX_SENSORS];    // forward render: ray parts per (step, agent, sensor) item
     // racing (task 1) and IMU
     int* gate_k;                // [NM] each agent's next gate, read and advanced
     int16_t* gate_tape;         // [T][NM] gate targeted during step t (internal)

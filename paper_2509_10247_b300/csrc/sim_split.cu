@@ -247,11 +247,11 @@ __global__ void __launch_bounds__(256, 4) k_render(const Args a) {
     __syncthreads();
     uint32_t phase = 0;
     // items: (step, agent, sensor, part); a sensor's chunks are split into
-    // up to `parts` consecutive ranges so that short horizons still give
-    // every warp of the CTA work
+    // rparts consecutive ranges so that short horizons still give every warp
+    // of the CTA work
     const int nch0 = (a.sen[0].R + 32 * RPT - 1) / (32 * RPT);
     const int nch1 = S > 1 ? (a.sen[1].R + 32 * RPT - 1) / (32 * RPT) : 0;
-    const int P0 = S > 0 ? min(a.parts, max(nch0, 1)) : 0, P1 = S > 1 ? min(a.parts, max(nch1, 1)) : 0;
+    const int P0 = S > 0 ? min(a.rparts[0], max(nch0, 1)) : 0, P1 = S > 1 ? min(a.rparts[1], max(nch1, 1)) : 0;
     const int per_tm = P0 + P1;
     const int per_env = a.T * M * per_tm;
     for (;;) {
