@@ -232,7 +232,57 @@ __global__ void __launch_bounds__(128) k_physics(const Args a) {
 // environment's map is staged once into shared memory; its T x M x S items
 // (step, agent, sensor) are taken by warps from a CTA ticket.  A warp culls
 // the map into its private list and sweeps all rays of the item.
+// Rays of chunks [c0, c1) of one (step, agent, sensor) item against its
+// cull list L (meta: its counts): cast, count, write depth / range and the
+// hit tape.  One full warp.
 template <int RPT, bool EXTRA>
+__device__ __forceinline__ void render_chunks(const Args& a, const WList& L, const int4& meta, const LCap& cap,
+                                              const Sensor& sen, const float* R, int c0, int c1, size_t base,
+                                              unsigned long long* s_cnt) {
+    const int lane = threadIdx.x & 31;
+    for (int ch = c0; ch < c1; ++ch) {
+        float dx[RPT], dy[RPT], dz[RPT], tb[RPT];
+        int bi[RPT];
+        item_rays<RPT>(sen, R, ch, lane, dx, dy, dz, tb);
+#pragma unroll
+        for (int r = 0; r < RPT; ++r) bi[r] = -1;
+        int4 nsub = make_int4(meta.x, meta.y, meta.w & 0xffff, meta.w >> 16);
+        if (meta.z < 0) {
+            if (a.cull > 1 && sen.cone) {
+                nsub = chunk_slots<EXTRA>(L, meta, cap, sen, a.cull, ch, R);
+                cast_sub<RPT, EXTRA>(L, nsub, cap, dx, dy, dz, tb, bi);
+            } else {
+                cast_list<RPT, EXTRA>(L, meta, cap, dx, dy, dz, tb, bi);
+            }
+        }
+        if (a.counters && lane == 0) {
+            const unsigned long long nr = (unsigned long long)min(32 * RPT, sen.R - ch * 32 * RPT);
+            if (meta.z < 0) {
+                atomicAdd(&s_cnt[0], nr * (unsigned long long)nsub.x);
+                atomicAdd(&s_cnt[1], nr * (unsigned long long)(nsub.y + nsub.z + nsub.w));
+            }
+            atomicAdd(&s_cnt[2], nr);
+        }
+#pragma unroll
+        for (int r = 0; r < RPT; ++r) {
+            const int j = ch * 32 * RPT + r * 32 + lane;
+            if (j >= sen.R) continue;
+            const int ray = out_index(sen, j);
+            float v;
+            int id;
+            if (meta.z >= 0) { v = 0.f; id = -2; }  // origin inside a primitive: no ray cotangent
+            else if (bi[r] < 0) { v = sen.range; id = -1; }
+            else {
+                v = fminf(sen.kind == 0 ? tb[r] * __ldg(&sen.dir[j].w) : tb[r], sen.range);
+                id = L.id[bi[r]];
+            }
+            if (sen.out) sen.out[base + ray] = v;
+            if (sen.tape) sen.tape[base + ray] = (int16_t)id;
+        }
+    }
+}
+
+template <int RPT, bool EXTRA, bool COOP>
 __global__ void __launch_bounds__(256, 4) k_render(const Args a) {
     extern __shared__ __align__(16) unsigned char sm[];
     __shared__ int s_env, s_flag, s_item;
@@ -254,6 +304,11 @@ __global__ void __launch_bounds__(256, 4) k_render(const Args a) {
     const int P0 = S > 0 ? min(a.rparts[0], max(nch0, 1)) : 0, P1 = S > 1 ? min(a.rparts[1], max(nch1, 1)) : 0;
     const int per_tm = P0 + P1;
     const int per_env = a.T * M * per_tm;
+    // few (step, agent, sensor) lists split into parts: each list is built
+    // once per environment, by its own warp, and shared by the warps that
+    // cast its parts (each keeps its chunk sub-lists in its own region)
+    const int nlists = a.T * M * S;
+    const bool coop = COOP && per_tm > S && nlists <= NW;
     for (;;) {
         if (threadIdx.x == 0) {
             s_env = atomicAdd(a.work, 1);
@@ -267,6 +322,22 @@ __global__ void __launch_bounds__(256, 4) k_render(const Args a) {
         const MapView mv = map_view(a, map, prim);
         if (!stage_map(a, sm, map, mv, phase, &s_flag)) return;
         prep_boxes(sm, a, mv.ns, mv.nb);
+        if (coop) {
+            if (warp < nlists) {
+                const int tm = warp / S, si = warp - tm * S, t = tm / M, m = tm - t * M;
+                const Sensor& sen = a.sen[si];
+                if (sen.out || sen.tape) {
+                    const size_t ti = (size_t)t * NM + env * M + m;
+                    float o[3], R[9];
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) o[k] = a.poses[ti * 12 + k];
+#pragma unroll
+                    for (int k = 0; k < 9; ++k) R[k] = a.poses[ti * 12 + 3 + k];
+                    warp_build_list<EXTRA, true>(mv, o, R, sen, a.cull, L, cap);
+                }
+            }
+            __syncthreads();
+        }
         for (int it = warp; it < per_env; it = next_item(&s_item, lane)) {
             const int tm = div_small(it, per_tm), r = it - tm * per_tm;
             const int t = div_small(tm, M), m = tm - t * M;
@@ -280,48 +351,17 @@ __global__ void __launch_bounds__(256, 4) k_render(const Args a) {
             for (int k = 0; k < 3; ++k) o[k] = a.poses[ti * 12 + k];
 #pragma unroll
             for (int k = 0; k < 9; ++k) R[k] = a.poses[ti * 12 + 3 + k];
-            const int4 meta = warp_build_list<EXTRA, true>(mv, o, R, sen, a.cull, L, cap);
             const size_t base = ti * sen.R;
-            for (int ch = c0; ch < c1; ++ch) {
-                float dx[RPT], dy[RPT], dz[RPT], tb[RPT];
-                int bi[RPT];
-                item_rays<RPT>(sen, R, ch, lane, dx, dy, dz, tb);
-#pragma unroll
-                for (int r = 0; r < RPT; ++r) bi[r] = -1;
-                int4 nsub = make_int4(meta.x, meta.y, meta.w & 0xffff, meta.w >> 16);
-                if (meta.z < 0) {
-                    if (a.cull > 1 && sen.cone) {
-                        nsub = chunk_slots<EXTRA>(L, meta, cap, sen, a.cull, ch, R);
-                        cast_sub<RPT, EXTRA>(L, nsub, cap, dx, dy, dz, tb, bi);
-                    } else {
-                        cast_list<RPT, EXTRA>(L, meta, cap, dx, dy, dz, tb, bi);
-                    }
-                }
-                if (a.counters && lane == 0) {
-                    const unsigned long long nr = (unsigned long long)min(32 * RPT, sen.R - ch * 32 * RPT);
-                    if (meta.z < 0) {
-                        atomicAdd(&s_cnt[0], nr * (unsigned long long)nsub.x);
-                        atomicAdd(&s_cnt[1], nr * (unsigned long long)(nsub.y + nsub.z + nsub.w));
-                    }
-                    atomicAdd(&s_cnt[2], nr);
-                }
-#pragma unroll
-                for (int r = 0; r < RPT; ++r) {
-                    const int j = ch * 32 * RPT + r * 32 + lane;
-                    if (j >= sen.R) continue;
-                    const int ray = out_index(sen, j);
-                    float v;
-                    int id;
-                    if (meta.z >= 0) { v = 0.f; id = -2; }  // origin inside a primitive: no ray cotangent
-                    else if (bi[r] < 0) { v = sen.range; id = -1; }
-                    else {
-                        v = fminf(sen.kind == 0 ? tb[r] * __ldg(&sen.dir[j].w) : tb[r], sen.range);
-                        id = L.id[bi[r]];
-                    }
-                    if (sen.out) sen.out[base + ray] = v;
-                    if (sen.tape) sen.tape[base + ray] = (int16_t)id;
-                }
+            int4 meta;
+            WList Lv = L;
+            if (coop) {  // the item's list, built by warp (tm * S + si) in this environment's first phase
+                Lv = wlist_at(sm + a.sm.wlist + (size_t)(tm * S + si) * a.sm.wstride, cap);
+                Lv.sub = L.sub;
+                meta = *Lv.meta;
+            } else {
+                meta = warp_build_list<EXTRA, true>(mv, o, R, sen, a.cull, L, cap);
             }
+            render_chunks<RPT, EXTRA>(a, Lv, meta, cap, sen, R, c0, c1, base, s_cnt);
             __syncwarp();
         }
         if (threadIdx.x == 0) s_cnt[3] += (unsigned long long)(a.T);
@@ -705,7 +745,13 @@ static cudaError_t render_rpt(bool vjp, bool launch, const Args& a, int grid, in
     if (vjp && (a.sen[0].tape || (a.S > 1 && a.sen[1].tape)))  // taped hit ids: one kernel for every RPT
         return render_launch(k_render_vjp<1, true, EXTRA>, launch, a, grid, block, smem, st, occ);
     if (vjp) return render_launch(k_render_vjp<RPT, false, EXTRA>, launch, a, grid, block, smem, st, occ);
-    return render_launch(k_render<RPT, EXTRA>, launch, a, grid, block, smem, st, occ);
+    // shared lists for split items: compiled for the cone-culling default of
+    // 4 rays per thread only (the other shapes keep one list per item)
+    if constexpr (RPT == 4) {
+        const bool coop = a.rparts[0] + (a.S > 1 ? a.rparts[1] : 0) > a.S && a.T * a.M * a.S <= block / 32;
+        if (coop && launch) return render_launch(k_render<RPT, EXTRA, true>, launch, a, grid, block, smem, st, occ);
+    }
+    return render_launch(k_render<RPT, EXTRA, false>, launch, a, grid, block, smem, st, occ);
 }
 
 template <bool EXTRA>
