@@ -34,7 +34,7 @@ WORKLOAD = "swarm_16384env_8agent_8maps_depth16x9"
 METRIC = "env-steps/s (fwd+adjoint, with depth) at 16k envs vs roofline; Grays/s"
 UNIT = "env-steps/s"
 # launch configuration timed by the bench (and used by the full-size parity test)
-BENCH_EXEC = dict(ckpt_every=16, tape_hits=1, cull=1)
+BENCH_EXEC = dict(ckpt_every=4, tape_hits=1, cull=1)
 # algorithmic work of one ray-primitive test after the per-origin list entry,
 # in FP32-pipe instructions (an FMA counts once): sphere 6 (3 for b = d.oc,
 # 1 for b^2 - C, 1 subtraction, 1 min / select; the square root of a hit

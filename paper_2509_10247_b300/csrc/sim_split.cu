@@ -90,6 +90,44 @@ __device__ __forceinline__ void nearest_obstacle(const MapView& mv, int M, const
     id = __shfl_sync(0xffffffffu, bid, src);
 }
 
+// The same search by one lane for its own position over the whole map (the
+// lanes of a warp may belong to different environments).
+__device__ __forceinline__ void nearest_obstacle_lane(const MapView& mv, const float* q, float& sd, int& id) {
+    float best = CUDART_INF_F;
+    int bid = -1;
+    const int ns = mv.ns, nb = mv.nb, np = mv.count();
+    for (int k = 0; k < ns; ++k) {
+        const float d = sdf_sphere(mv.prim[k], q);
+        if (d < best) { best = d; bid = k; }
+    }
+    for (int j = 0; j < nb; ++j) {
+        const float d = sdf_box_lohi(mv.box(j)[0], mv.box(j)[1], q);
+        if (d < best) { best = d; bid = ns + j; }
+    }
+    for (int c = ns + nb; c < np; ++c) {
+        const float d = sdf_prim(mv, c, q);
+        if (d < best) { best = d; bid = c; }
+    }
+    sd = best;
+    id = bid;
+}
+
+__host__ __device__ inline int pow2_ceil(int m) {
+    int p = 1;
+    while (p < m) p <<= 1;
+    return p;
+}
+
+// Environments per warp of the physics adjoint: the warp's lanes form groups
+// of pow2_ceil(M) lanes, one environment per group and a lane per agent, as
+// many groups as fit in 32 lanes and in 96 KiB of segment states.
+__host__ __device__ inline int phys_bwd_envs_per_warp(int K, int M) {
+    const size_t per_env = (size_t)(K + 1) * M * 16 * sizeof(float);
+    int E = 32 / pow2_ceil(M);
+    while (E > 1 && (size_t)E * per_env > 96 * 1024) E >>= 1;
+    return E;
+}
+
 // ----------------------------------------------------------- forward physics
 // One warp per environment.  render_only: write the pose of the current
 // state at step 0 and return.
@@ -553,14 +591,18 @@ template <bool EXT>
 __global__ void __launch_bounds__(128, EXT ? 4 : 5) k_physics_bwd(const Args a) {
     extern __shared__ __align__(16) float segm[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int env = blockIdx.x * (blockDim.x >> 5) + wid;
-    if (env >= a.N) return;
     const int M = a.M, D = a.c.D, A = a.c.A, NM = a.NM;
-    float* seg = segm + (size_t)wid * (a.K + 1) * M * 16;
+    const int Mp = pow2_ceil(M), E = phys_bwd_envs_per_warp(a.K, M);
+    const int grp = lane / Mp, agent = lane - grp * Mp, gbase = grp * Mp;
+    const int env0 = (blockIdx.x * (blockDim.x >> 5) + wid) * E;
+    if (env0 >= a.N) return;
+    const bool live = grp < E && env0 + grp < a.N;
+    const int env = live ? env0 + grp : env0;  // idle groups read a valid environment, write nothing
+    float* seg = segm + ((size_t)wid * E + (grp < E ? grp : 0)) * (a.K + 1) * M * 16;
     const int map = a.env_map[env];
     const MapView mv = map_view(a, map, a.prims + a.map_off[map]);
-    const bool on = lane < M;
-    const int i = env * M + (on ? lane : 0);
+    const bool on = live && agent < M;
+    const int i = env * M + (on ? agent : 0);
     const float drag = a.drag_env ? a.drag_env[env] : a.c.drag;
     const float lam = a.lam_env ? a.lam_env[env] : a.c.lam;
     float g[16];
@@ -574,7 +616,7 @@ __global__ void __launch_bounds__(128, EXT ? 4 : 5) k_physics_bwd(const Args a) 
         int kp = a.ckpt_k ? a.ckpt_k[(size_t)sg * a.N + env] : 0;
         if (on)
 #pragma unroll
-            for (int k = 0; k < 16; ++k) seg[(0 * M + lane) * 16 + k] = s[k];
+            for (int k = 0; k < 16; ++k) seg[(0 * M + agent) * 16 + k] = s[k];
         for (int t = t0; t < t1; ++t) {
             const bool dn = a.done_rd[(size_t)t * NM + env * M] != 0;
             float act[4], sp[16];
@@ -587,7 +629,7 @@ __global__ void __launch_bounds__(128, EXT ? 4 : 5) k_physics_bwd(const Args a) 
             for (int k = 0; k < 16; ++k) s[k] = sp[k];
             if (on)
 #pragma unroll
-                for (int k = 0; k < 16; ++k) seg[((t - t0 + 1) * M + lane) * 16 + k] = s[k];
+                for (int k = 0; k < 16; ++k) seg[((t - t0 + 1) * M + agent) * 16 + k] = s[k];
         }
         __syncwarp();
         for (int t = t1 - 1; t >= t0; --t) {
@@ -596,8 +638,8 @@ __global__ void __launch_bounds__(128, EXT ? 4 : 5) k_physics_bwd(const Args a) 
             float s0[16], s1[16], act[4];
 #pragma unroll
             for (int k = 0; k < 16; ++k) {
-                s0[k] = on ? seg[((t - t0) * M + lane) * 16 + k] : 0.f;
-                s1[k] = on ? seg[((t - t0 + 1) * M + lane) * 16 + k] : 0.f;
+                s0[k] = on ? seg[((t - t0) * M + agent) * 16 + k] : 0.f;
+                s1[k] = on ? seg[((t - t0 + 1) * M + agent) * 16 + k] : 0.f;
             }
             if (!on && a.c.model == MODEL_RIGID) { s0[3] = 1.f; s1[3] = 1.f; }
             if (!on && a.c.model == MODEL_SIMPLE) { s0[6] = s0[10] = s0[14] = 1.f; s1[6] = s1[10] = s1[14] = 1.f; }
@@ -622,7 +664,8 @@ __global__ void __launch_bounds__(128, EXT ? 4 : 5) k_physics_bwd(const Args a) 
             if (a.sdf_tape) bid = on ? a.sdf_tape[o] : -1;
             else {
                 float sd;
-                nearest_obstacle(mv, M, sp, sd, bid);
+                if (E > 1) nearest_obstacle_lane(mv, sp, sd, bid);
+                else nearest_obstacle(mv, M, sp, sd, bid);
             }
             const float gr = (on && a.g_r) ? a.g_r[o] : 0.f;
             if (on) {
@@ -663,9 +706,11 @@ __global__ void __launch_bounds__(128, EXT ? 4 : 5) k_physics_bwd(const Args a) 
                 for (int k = 0; k < 4; ++k) ga[k] += -2.f * a.c.w_act * gr * act[k];
             }
             for (int n = 0; n < M; ++n) {
-                const float px = __shfl_sync(0xffffffffu, sp[0], n), py = __shfl_sync(0xffffffffu, sp[1], n),
-                            pz = __shfl_sync(0xffffffffu, sp[2], n), grn = __shfl_sync(0xffffffffu, gr, n);
-                if (n == lane || !on) continue;
+                const float px = __shfl_sync(0xffffffffu, sp[0], gbase + n),
+                            py = __shfl_sync(0xffffffffu, sp[1], gbase + n),
+                            pz = __shfl_sync(0xffffffffu, sp[2], gbase + n),
+                            grn = __shfl_sync(0xffffffffu, gr, gbase + n);
+                if (n == agent || !on) continue;
                 const float dd[3] = {sp[0] - px, sp[1] - py, sp[2] - pz};
                 const float dij = sqrtf(dot3(dd, dd));
                 const float sv = relu(a.c.d_agent - dij);
@@ -707,7 +752,7 @@ cudaError_t launch_physics(const Args& a, cudaStream_t st) {
 
 // Warps per CTA of the physics adjoint and its dynamic shared memory.
 void physics_bwd_shape(int K, int M, int* warps, size_t* smem) {
-    const size_t per = (size_t)(K + 1) * M * 16 * sizeof(float);
+    const size_t per = (size_t)phys_bwd_envs_per_warp(K, M) * (K + 1) * M * 16 * sizeof(float);
     int w = kPhysWarps;
     while (w > 1 && (size_t)w * per > 96 * 1024) --w;
     *warps = w;
@@ -722,8 +767,9 @@ cudaError_t launch_physics_bwd(const Args& a, cudaStream_t st) {
     cudaError_t e = cudaFuncSetAttribute(ext ? k_physics_bwd<true> : k_physics_bwd<false>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    if (ext) k_physics_bwd<true><<<(a.N + w - 1) / w, 32 * w, smem, st>>>(a);
-    else k_physics_bwd<false><<<(a.N + w - 1) / w, 32 * w, smem, st>>>(a);
+    const int per_cta = w * phys_bwd_envs_per_warp(a.K, a.M);
+    if (ext) k_physics_bwd<true><<<(a.N + per_cta - 1) / per_cta, 32 * w, smem, st>>>(a);
+    else k_physics_bwd<false><<<(a.N + per_cta - 1) / per_cta, 32 * w, smem, st>>>(a);
     return cudaGetLastError();
 }
 
