@@ -129,19 +129,27 @@ __host__ __device__ inline int phys_bwd_envs_per_warp(int K, int M) {
 }
 
 // ----------------------------------------------------------- forward physics
-// One warp per environment.  render_only: write the pose of the current
-// state at step 0 and return.
+// A warp holds 32 / pow2_ceil(M) environments, a lane group per environment
+// and a lane per agent; environments are taken in the work order (grouped
+// by map, so a warp's groups scan maps of one size).  render_only: write the
+// pose of the current state at step 0 and return.
 // EXT: the racing task or the IMU readout is on (else their code is compiled out).
 template <bool EXT>
 __global__ void __launch_bounds__(128) k_physics(const Args a) {
     const int lane = threadIdx.x & 31;
-    const int env = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (env >= a.N) return;
     const int M = a.M, D = a.c.D, A = a.c.A, NM = a.NM;
+    const int Mp = pow2_ceil(M), E = 32 / Mp;
+    const int grp = lane / Mp, agent = lane - grp * Mp, gbase = grp * Mp;
+    const unsigned gmask = Mp == 32 ? 0xffffffffu : ((1u << Mp) - 1u) << gbase;
+    const int q0 = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * E;
+    if (q0 >= a.N) return;
+    const bool live = q0 + grp < a.N;
+    const int q = live ? q0 + grp : q0;
+    const int env = a.order ? a.order[q] : q;  // idle groups read a valid environment, write nothing
     const int map = a.env_map[env];
     const MapView mv = map_view(a, map, a.prims + a.map_off[map]);
-    const bool on = lane < M;
-    const int i = env * M + (on ? lane : 0);
+    const bool on = live && agent < M;
+    const int i = env * M + (on ? agent : 0);
     const float drag = a.drag_env ? a.drag_env[env] : a.c.drag;
     const float lam = a.lam_env ? a.lam_env[env] : a.c.lam;
     float s[16];
@@ -165,7 +173,7 @@ __global__ void __launch_bounds__(128) k_physics(const Args a) {
 #pragma unroll
                 for (int k = 0; k < 16; ++k)
                     if (k < D) a.ckpt[((size_t)c * NM + i) * D + k] = s[k];
-            if (lane == 0) a.ckpt_k[(size_t)c * a.N + env] = kpool;
+            if (live && agent == 0) a.ckpt_k[(size_t)c * a.N + env] = kpool;
         }
         float act[4], sp[16];
 #pragma unroll
@@ -173,23 +181,25 @@ __global__ void __launch_bounds__(128) k_physics(const Args a) {
         step_agent(a.c, drag, lam, s, act, sp);
         float sd;
         int bid;
-        nearest_obstacle(mv, M, sp, sd, bid);
+        if (E > 1) nearest_obstacle_lane(mv, sp, sd, bid);
+        else nearest_obstacle(mv, M, sp, sd, bid);
         // collisions and the dense / sparse rewards (Sec. III-C, III-E)
         bool col = sd < a.c.r_quad;
 #pragma unroll
         for (int k = 0; k < 3; ++k) col = col || sp[k] < a.c.blo[k] || sp[k] > a.c.bhi[k];
         float pair = 0.f;
         for (int n = 0; n < M; ++n) {
-            const float px = __shfl_sync(0xffffffffu, sp[0], n), py = __shfl_sync(0xffffffffu, sp[1], n),
-                        pz = __shfl_sync(0xffffffffu, sp[2], n);
-            if (n == lane) continue;
+            const float px = __shfl_sync(0xffffffffu, sp[0], gbase + n),
+                        py = __shfl_sync(0xffffffffu, sp[1], gbase + n),
+                        pz = __shfl_sync(0xffffffffu, sp[2], gbase + n);
+            if (n == agent) continue;
             const float dd[3] = {sp[0] - px, sp[1] - py, sp[2] - pz};
             const float dij = sqrtf(dot3(dd, dd));
             col = col || dij < a.c.d_agent;
             const float sv = relu(a.c.d_agent - dij);
             pair += sv * sv;
         }
-        const bool dn = a.c.terminate && __ballot_sync(0xffffffffu, on && col) != 0u;
+        const bool dn = a.c.terminate && (__ballot_sync(0xffffffffu, on && col) & gmask) != 0u;
         if (on) {
             const float ob = (a.c.w_obs != 0.f && sd < CUDART_INF_F) ? relu(a.c.d_safe - sd) : 0.f;
             float aa = 0.f;
@@ -258,7 +268,7 @@ __global__ void __launch_bounds__(128) k_physics(const Args a) {
 #pragma unroll
         for (int k = 0; k < 16; ++k)
             if (k < D) a.state[(size_t)i * D + k] = s[k];
-    if (lane == 0 && a.pool_k) a.pool_k[env] = kpool;
+    if (live && agent == 0 && a.pool_k) a.pool_k[env] = kpool;
     if (racing && on) a.gate_k[i] = gk;
     if (imu && a.imu_noise && on)
 #pragma unroll
@@ -744,7 +754,10 @@ __global__ void __launch_bounds__(128, EXT ? 4 : 5) k_physics_bwd(const Args a) 
 constexpr int kPhysWarps = 4;
 
 cudaError_t launch_physics(const Args& a, cudaStream_t st) {
-    const int blocks = (a.N + kPhysWarps - 1) / kPhysWarps;
+    int Mp = 1;
+    while (Mp < a.M) Mp <<= 1;
+    const int per_cta = kPhysWarps * (32 / Mp);
+    const int blocks = (a.N + per_cta - 1) / per_cta;
     if (a.c.task == 1 || a.imu) k_physics<true><<<blocks, 32 * kPhysWarps, 0, st>>>(a);
     else k_physics<false><<<blocks, 32 * kPhysWarps, 0, st>>>(a);
     return cudaGetLastError();
