@@ -355,6 +355,35 @@ int oc_pose(const oc_config *c, const double *s, double *o, double *R)
     return flags;
 }
 
+/* Conditioning of the sensor attitude at state s (Sec. III-B): the factor by
+ * which FP32 rounding of the state (and of the arithmetic) is amplified in
+ * the body axes, relative to a well-conditioned rotation.  Rigid body and
+ * simplified quadrotor: 1 (the rotation is the state).  Point mass: x_B is
+ * the heading vector h with its z_B component removed, normalised; rounding h
+ * and z_B moves that difference by ~eps |h|, so x_B turns by ~eps |h| /
+ * |h - (h.z_B) z_B|: the factor is |h| / |h_perp| (>= 1), of the vector the
+ * rule actually uses (the heading, else the world-axis fallback). */
+static double pose_kappa(const oc_config *c, const double *s)
+{
+    if (c->model != OC_PM && c->model != OC_PMD) return 1.0;
+    const double *a = s + 6, *e = s + 9;
+    double z[3] = {0.0, 0.0, 1.0};
+    double na = norm3(a);
+    if (na >= 1e-6) { z[0] = a[0] / na; z[1] = a[1] / na; z[2] = a[2] / na; }
+    double cand[3][3] = {{e[0], e[1], 0.0}, {1.0, 0.0, 0.0}, {0.0, 1.0, 0.0}};
+    for (int k = 0; k < 3; ++k) {
+        const double *h = cand[k];
+        double hz = dot3(h, z), hp[3];
+        for (int i = 0; i < 3; ++i) hp[i] = h[i] - hz * z[i];
+        double nh = norm3(hp);
+        if (nh >= 1e-6 || k == 2) {
+            double r = norm3(h) / (nh > 0.0 ? nh : 1e-300);
+            return r > 1.0 ? r : 1.0;
+        }
+    }
+    return 1.0;
+}
+
 /* ------------------------------------------------------- sensors (Sec. III-B) */
 
 /* Depth-camera rays in the body frame: pinhole looking along +x_B, image
@@ -726,8 +755,10 @@ static double prim_sdf(const map_t *m, int id, const double *p)
 /* Slab-type decisions of primitive id that are near their thresholds for
  * the ray: entry and exit close (grazing), or two candidate entry times
  * close (the entry face, or for a gate whether the entry is inside the
- * opening, may change in FP32).  Returns amb bits: 1|2 value, 2 gradient. */
-static int prim_amb(const map_t *m, int id, const double *o, const double *d, double reach)
+ * opening, may change in FP32).  kdir (>= 1) scales the margins that come
+ * from the ray direction's FP32 error (the pose's attitude conditioning).
+ * Returns amb bits: 1|2 value, 2 gradient. */
+static int prim_amb(const map_t *m, int id, const double *o, const double *d, double reach, double kdir)
 {
     int flags = 0;
     if (fabs(prim_sdf(m, id, o)) < AMB_INSIDE) flags |= 3;
@@ -737,7 +768,7 @@ static int prim_amb(const map_t *m, int id, const double *o, const double *d, do
         double C = dot3(oc, oc) - sp[3] * sp[3];
         double b = dot3(d, oc);
         double disc = b * b - C;
-        if (b > 0.0 && b - sqrt(fabs(disc)) < reach && fabs(disc) < AMB_DISC * (b * b > 1.0 ? b * b : 1.0))
+        if (b > 0.0 && b - sqrt(fabs(disc)) < reach && fabs(disc) < kdir * AMB_DISC * (b * b > 1.0 ? b * b : 1.0))
             flags |= 3;
         return flags;
     }
@@ -753,7 +784,7 @@ static int prim_amb(const map_t *m, int id, const double *o, const double *d, do
             if (lo > tn) tn = lo;
             if (hi < tf) tf = hi;
         }
-        if (ok && tn > 0.0 && tn < reach && fabs(tf - tn) < AMB_SLAB) flags |= 3;
+        if (ok && tn > 0.0 && tn < reach && fabs(tf - tn) < kdir * AMB_SLAB) flags |= 3;
         return flags;
     }
     k -= m->nb;
@@ -769,7 +800,7 @@ static int prim_amb(const map_t *m, int id, const double *o, const double *d, do
             double disc = b * b - a * cc;
             double sq = sqrt(fabs(disc));
             /* grazing the side: the two roots (nearly) coincide */
-            if ((-b - sq) / a < reach && -b + sq > 0.0 && fabs(disc) < AMB_DISC * (b * b > a ? b * b : a))
+            if ((-b - sq) / a < reach && -b + sq > 0.0 && fabs(disc) < kdir * AMB_DISC * (b * b > a ? b * b : a))
                 flags |= 3;
             if (disc >= 0.0) { e[ne++] = (-b - sq) / a; e[ne++] = (-b + sq) / a; }
         }
@@ -794,7 +825,7 @@ static int prim_amb(const map_t *m, int id, const double *o, const double *d, do
     for (int i = 0; i < ne; ++i)
         for (int j = i + 1; j < ne; ++j) {
             double lo = e[i] < e[j] ? e[i] : e[j];
-            if (lo > 0.0 && lo < reach && fabs(e[i] - e[j]) < AMB_EDGE * (lo > 1.0 ? lo : 1.0)) flags |= 3;
+            if (lo > 0.0 && lo < reach && fabs(e[i] - e[j]) < kdir * AMB_EDGE * (lo > 1.0 ? lo : 1.0)) flags |= 3;
         }
     return flags;
 }
@@ -805,8 +836,14 @@ static int prim_amb(const map_t *m, int id, const double *o, const double *d, do
  * length: bit 0 a value decision near its threshold (grazing, origin near a
  * surface), bit 1 a gradient decision near its threshold (second hit, range
  * clamp, box edge), bit 2 a value ill-conditioned in FP32, bit 3 a gradient
- * ill-conditioned under FP32 trajectory drift (near-grazing incidence). */
-static double cast_ray(const double *o, const double *d, const map_t *m, int *hit, double tclamp, int *amb)
+ * ill-conditioned under FP32 trajectory drift (near-grazing incidence), bit
+ * 4 a gradient ill-conditioned under FP32 rounding of the pose alone (no
+ * drift).  kdir (>= 1) is the attitude's conditioning at this pose: how much
+ * the FP32 error of the body axes exceeds that of a well-conditioned
+ * rotation (pose_kappa); it scales every margin that the ray direction's
+ * error sets. */
+static double cast_ray(const double *o, const double *d, const map_t *m, int *hit, double tclamp, int *amb,
+                       double kdir)
 {
     double best = OC_INF, second = OC_INF;
     int id = -1, flags = 0, aux = -1;
@@ -819,11 +856,11 @@ static double cast_ray(const double *o, const double *d, const map_t *m, int *hi
     }
     /* near-degenerate decisions that could change the value in FP32 */
     double reach = (best < tclamp ? best : tclamp) + 1e-2;
-    for (int k = 0; k < np; ++k) flags |= prim_amb(m, k, o, d, reach);
+    for (int k = 0; k < np; ++k) flags |= prim_amb(m, k, o, d, reach, kdir);
     /* gradient-only ambiguities: second hit close, range clamp, grazing,
      * entry through a box edge */
     if (best < OC_INF) {
-        if (second - best < AMB_GAP) flags |= 2;
+        if (second - best < kdir * AMB_GAP) flags |= 2;
         if (fabs(best - tclamp) < AMB_RANGE) flags |= 2;
         double n[3];
         if (best > 0.0 && best < tclamp && prim_normal(m, id, o, d, best, aux, n)) {
@@ -837,20 +874,25 @@ static double cast_ray(const double *o, const double *d, const map_t *m, int *hi
                     tl[i] = t1 < t2 ? t1 : t2;
                 }
                 for (int i = 0; i < 3; ++i)
-                    if (i != aux && fabs(tl[i] - best) < AMB_EDGE * (best > 1.0 ? best : 1.0)) flags |= 2;
+                    if (i != aux && fabs(tl[i] - best) < kdir * AMB_EDGE * (best > 1.0 ? best : 1.0)) flags |= 2;
             }
             double nd = fabs(dot3(n, d));
             if (nd < AMB_GRAZE) flags |= 8;
             /* gradient -n/(n.d) of a curved hit turns by ~ dp/(r |n.d|) when
              * the trajectory drifts by dp (FP32 rollout): flag above 3e-4 */
-            if (id < m->ns && DRIFT_POS / (m->sph[4 * id + 3] * nd) > 3e-4) flags |= 8;
-            if (id >= m->ns + m->nb && id < m->ns + m->nb + m->nc && aux == 0 &&
-                DRIFT_POS / (m->cyl[5 * (id - m->ns - m->nb) + 2] * nd) > 3e-4)
-                flags |= 8;
-            /* ill-conditioned value: rounding the direction (COND_DIR per
-             * component) and origin (COND_ORG) to FP32 moves the hit by
-             * (COND_DIR t + COND_ORG) / |n.d|; flag above half the tolerance */
-            if ((COND_DIR * best + COND_ORG) / nd > COND_MAX) flags |= 4 | 8;
+            double rc = 0.0;  /* radius of curvature of a curved hit, 0 if flat */
+            if (id < m->ns) rc = m->sph[4 * id + 3];
+            if (id >= m->ns + m->nb && id < m->ns + m->nb + m->nc && aux == 0) rc = m->cyl[5 * (id - m->ns - m->nb) + 2];
+            if (rc > 0.0 && DRIFT_POS / (rc * nd) > 3e-4) flags |= 8;
+            /* rounding the pose to FP32 (direction COND_DIR kdir per
+             * component, origin COND_ORG) moves the hit by dp = (COND_DIR kdir
+             * t + COND_ORG) / |n.d|: the value is ill-conditioned when dp
+             * exceeds half the depth tolerance; the gradient when its relative
+             * change, dp / (r |n.d|) on a curved surface and COND_DIR kdir /
+             * |n.d| on any, exceeds the gradient tolerance (1e-3) */
+            double dp = (COND_DIR * kdir * best + COND_ORG) / nd;
+            if (dp > COND_MAX) flags |= 4 | 8;
+            if ((rc > 0.0 && dp / (rc * nd) > 1e-3) || COND_DIR * kdir / nd > 1e-3) flags |= 16;
         }
     }
     *hit = id;
@@ -956,13 +998,14 @@ static void render_agent(const ctx_t *x, int env, const double *s, double *depth
     map_of(x, env, &mp);
     double o[3], R[9];
     int pf = oc_pose(x->c, s, o, R);
+    double kdir = pose_kappa(x->c, s);
     for (int r = 0; r < x->Rc; ++r) {
         const double *db = x->cam_dir + 3 * r;
         double d[3];
         for (int i = 0; i < 3; ++i) d[i] = R[3 * i] * db[0] + R[3 * i + 1] * db[1] + R[3 * i + 2] * db[2];
         int id, amb;
         double tcl = x->c->cam_range / x->cam_fac[r];
-        double t = cast_ray(o, d, &mp, &id, tcl, &amb);
+        double t = cast_ray(o, d, &mp, &id, tcl, &amb, kdir);
         double z = t * x->cam_fac[r];
         if (depth) depth[r] = z < x->c->cam_range ? z : x->c->cam_range;
         hc[r] = id;
@@ -973,7 +1016,7 @@ static void render_agent(const ctx_t *x, int env, const double *s, double *depth
         double d[3];
         for (int i = 0; i < 3; ++i) d[i] = R[3 * i] * db[0] + R[3 * i + 1] * db[1] + R[3 * i + 2] * db[2];
         int id, amb;
-        double t = cast_ray(o, d, &mp, &id, x->c->lid_range, &amb);
+        double t = cast_ray(o, d, &mp, &id, x->c->lid_range, &amb, kdir);
         if (lidar) lidar[r] = t < x->c->lid_range ? t : x->c->lid_range;
         hl[r] = id;
         al[r] = (uint8_t)(amb | ((pf & 4) ? 3 : 0));
