@@ -70,7 +70,7 @@ enum {
 enum { SIM_MODEL_POINT_MASS = 0, SIM_MODEL_RIGID = 1, SIM_MODEL_POINT_MASS_DISCRETE = 2, SIM_MODEL_SIMPLE = 3 };
 
 /* Status bits accumulated on the device (sim_last_status). */
-enum { SIM_STATUS_NAN = 1, SIM_STATUS_TIMEOUT = 2 };
+enum { SIM_STATUS_NAN = 1, SIM_STATUS_TIMEOUT = 2, SIM_STATUS_MAP_CAPACITY = 4 };
 
 /* Simulation parameters.  Paper symbols: Eq. 3 (lam, drag), Eq. 1 (mass,
  * inertia J, drag_body D), Sec. III-B (sensors), Sec. III-C/D/E (task). */
@@ -377,15 +377,26 @@ int sim_counters(sim_handle *h, uint64_t *out, int32_t reset);
  *   actions  DEVICE [NM][A]; outputs depth, lidar, r_ctrl, r_goal, done as
  *            in sim_step (any may be NULL); pool_k DEVICE [N] reset counters
  *            (read and advanced; NULL: entry 0 and no counting)
- * The first call on a device looks up the scratch address on that device;
- * make it before any stream capture.  Every call rewrites the scratch, so
- * calls that overlap on the GPU (other streams, other threads) race; order
- * them on one stream.  Returns SIM_OK or a SIM_ERR_* code. */
+ *   status   DEVICE int32 (nullable): receives this call's SIM_STATUS_* bits
+ *            once the step has run on `stream` (no host synchronisation):
+ *            SIM_STATUS_NAN a non-finite state, SIM_STATUS_TIMEOUT a bounded
+ *            wait for the map copy gave up (that environment was skipped),
+ *            SIM_STATUS_MAP_CAPACITY a map with more spheres or boxes than
+ *            ns_max / nb_max (checked on the device before staging; the
+ *            environments of that map are left untouched: outputs unwritten,
+ *            state unchanged).  Read it before relying on the outputs.
+ * The first call on a device looks up the scratch address on that device
+ * (again whenever the device's context has changed, e.g. after
+ * cudaDeviceReset); make it before any stream capture.  Every call rewrites
+ * the scratch, so calls that overlap on the GPU (other streams, other
+ * threads) race; order them on one stream.  Returns SIM_OK or a SIM_ERR_*
+ * code. */
 int sim_step_static(const sim_config *cfg, const float *prims, const int32_t *map_off,
                     const int32_t *map_ns, const int32_t *map_nb, int32_t ns_max, int32_t nb_max,
                     const int32_t *env_map, const float *targets, const float *pool, float *state,
                     const float *actions, float *depth, float *lidar, float *r_ctrl,
-                    int8_t *r_goal, uint8_t *done, int32_t *pool_k, sim_stream_t stream);
+                    int8_t *r_goal, uint8_t *done, int32_t *pool_k, int32_t *status,
+                    sim_stream_t stream);
 
 /* Launch shape chosen for this handle: warps per CTA, rays per thread,
  * grid size of the rollout kernel and its dynamic shared memory (bytes). */

@@ -353,13 +353,15 @@ def sim_launch_info(h):
 
 def sim_step_static(cfg, prims, map_off, map_ns, map_nb, ns_max, nb_max, env_map, targets, pool,
                     state, actions, depth=None, lidar=None, r_ctrl=None, r_goal=None, done=None,
-                    pool_k=None, stream=None):
+                    pool_k=None, status=None, stream=None):
     """One step without any device allocation by the library (all buffers are
-    the caller's device tensors; see include/diffsim.h)."""
+    the caller's device tensors; status: an int32 device tensor of one
+    element that receives the call's SIM_STATUS_* bits; see include/diffsim.h)."""
     _ck(lib().sim_step_static(C.byref(cfg), _ptr(prims), _ptr(map_off), _ptr(map_ns), _ptr(map_nb),
                               _i(ns_max), _i(nb_max), _ptr(env_map), _ptr(targets), _ptr(pool),
                               _ptr(state), _ptr(actions), _ptr(depth), _ptr(lidar), _ptr(r_ctrl),
-                              _ptr(r_goal), _ptr(done), _ptr(pool_k), _stream(stream)), "sim_step_static")
+                              _ptr(r_goal), _ptr(done), _ptr(pool_k), _ptr(status), _stream(stream)),
+        "sim_step_static")
 
 
 def sim_profile(h, on=True):

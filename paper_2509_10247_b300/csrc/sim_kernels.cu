@@ -94,6 +94,15 @@ __global__ void __launch_bounds__(256, 3) k_rollout(const Args a) {
         const int env = a.order ? a.order[q] : q;
         const int map = a.env_map[env];
         const MapView mv = map_view(a, map, prim);
+        // the shared-memory map block and cull lists are sized by the
+        // capacities the caller gave: a larger map is flagged and its
+        // environment left untouched (outputs unwritten, state unchanged)
+        if (mv.ns > a.ns_max || mv.nb > a.nb_max || mv.nc > a.nc_max || mv.ng > a.ng_max || mv.ns < 0 ||
+            mv.nb < 0) {
+            if (threadIdx.x == 0) atomicOr(a.status, 4);
+            __syncthreads();
+            continue;
+        }
         for (int i = threadIdx.x; i < M * 16; i += blockDim.x) {
             const int m = i >> 4, k = i & 15;
             st[i] = k < D ? a.state[(size_t)(env * M + m) * D + k] : 0.f;

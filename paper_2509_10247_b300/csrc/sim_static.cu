@@ -10,6 +10,8 @@
 #include <cstring>
 #include <mutex>
 
+#include <cuda.h>
+
 #include "diffsim.h"
 #include "sim_kernels.cuh"
 
@@ -30,13 +32,52 @@ static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
+// Per device ordinal: the scratch address and the id of the context it was
+// looked up in.  A device's context can be torn down and made again
+// (cudaDeviceReset), which reloads the module at a new address; the context
+// id tells the cached address apart from a stale one.
 unsigned char* g_ptr[kMaxDevices] = {nullptr};
+unsigned long long g_ctx[kMaxDevices] = {0};
 
-// Device address of g_scratch on the current device, looked up once per device.
+using CtxGetCurrent = CUresult (*)(CUcontext*);
+using CtxGetId = CUresult (*)(CUcontext, unsigned long long*);
+CtxGetCurrent g_get_ctx = nullptr;
+CtxGetId g_get_id = nullptr;
+bool g_looked_up = false;
+
+// Id of the calling thread's current context, 0 if none or unknown.  The
+// driver functions come through the runtime's entry-point query, so the
+// library needs no link against the driver library.
+unsigned long long current_ctx_id() {
+    if (!g_looked_up) {
+        g_looked_up = true;
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            g_get_ctx = reinterpret_cast<CtxGetCurrent>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            g_get_id = reinterpret_cast<CtxGetId>(f);
+        cudaGetLastError();
+    }
+    if (!g_get_ctx || !g_get_id) return 0;
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (g_get_ctx(&ctx) != CUDA_SUCCESS || !ctx) return 0;
+    if (g_get_id(ctx, &id) != CUDA_SUCCESS) return 0;
+    return id;
+}
+
+// Device address of g_scratch on the current device: looked up once per
+// device and context (again after the device's context was reset; on every
+// call if the context id cannot be read).
 int scratch_ptr(int dev, unsigned char** out) {
     if (dev < 0 || dev >= kMaxDevices) return SIM_ERR_UNSUPPORTED;
     std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_ptr[dev]) {
+    const unsigned long long id = current_ctx_id();
+    if (!g_ptr[dev] || id == 0 || id != g_ctx[dev]) {
         void* p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
         if (e != cudaSuccess) {
@@ -44,6 +85,7 @@ int scratch_ptr(int dev, unsigned char** out) {
             return SIM_ERR_CUDA;
         }
         g_ptr[dev] = static_cast<unsigned char*>(p);
+        g_ctx[dev] = current_ctx_id();  // the lookup made the device's context current
     }
     *out = g_ptr[dev];
     return SIM_OK;
@@ -100,7 +142,7 @@ extern "C" int sim_step_static(const sim_config* cfg, const float* prims, const 
                                const int32_t* map_ns, const int32_t* map_nb, int32_t ns_max, int32_t nb_max,
                                const int32_t* env_map, const float* targets, const float* pool, float* state,
                                const float* actions, float* depth, float* lidar, float* r_ctrl, int8_t* r_goal,
-                               uint8_t* done, int32_t* pool_k, sim_stream_t stream) {
+                               uint8_t* done, int32_t* pool_k, int32_t* status, sim_stream_t stream) {
     if (!cfg || !map_off || !map_ns || !map_nb || !env_map || !targets || !state || !actions)
         return SIM_ERR_NULL_PTR;
     if (bad_cfg(cfg)) return SIM_ERR_INVALID_ARG;
@@ -212,5 +254,8 @@ extern "C" int sim_step_static(const sim_config* cfg, const float* prims, const 
         cudaGetLastError();
         return SIM_ERR_CUDA;
     }
+    // this call's status word (the control words were cleared above)
+    if (status && cudaMemcpyAsync(status, a.status, sizeof(int32_t), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+        return SIM_ERR_CUDA;
     return SIM_OK;
 }

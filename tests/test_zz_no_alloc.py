@@ -71,9 +71,11 @@ def test_static_step_matches_sim_step_twice(name, kw):
         r = torch.empty(NM, device=dev)
         g = torch.empty(NM, dtype=torch.int8, device=dev)
         d = torch.empty(NM, dtype=torch.uint8, device=dev)
+        status = torch.full((1,), -1, dtype=torch.int32, device=dev)
         binding.sim_step_static(cfg, prims, off, ns, nb, ns_max, nb_max, env_map, targets, pool, state,
-                                act[t], depth, lidar, r, g, d, pool_k)
+                                act[t], depth, lidar, r, g, d, pool_k, status=status)
         torch.cuda.synchronize()
+        assert int(status.item()) == 0, t
         s_ref, o_ref = ref[t]
         assert torch.all((state - s_ref).abs() <= STATE_TF * s_ref.abs().clamp(min=1.0)), t
         assert torch.all((r - o_ref["r_ctrl"]).abs() <= 1e-6 * o_ref["r_ctrl"].abs().clamp(min=1.0)), t
@@ -82,6 +84,47 @@ def test_static_step_matches_sim_step_twice(name, kw):
             assert torch.all((depth - o_ref["depth"]).abs() <= DEPTH_TOL), t
         if Rl:
             assert torch.all((lidar - o_ref["lidar"]).abs() <= DEPTH_TOL), t
+    sim.close()
+
+
+def test_static_step_flags_understated_map_capacity():
+    """ns_max / nb_max size the kernel's shared-memory map block and cull
+    lists; a map with more primitives is caught on the device before it is
+    staged: SIM_STATUS_MAP_CAPACITY is reported and that map's environments
+    are left untouched, while the others step as sim_step does."""
+    dev = torch.device("cuda", 0)
+    p = synth.preset("swarm_16384env_8agent_8maps_depth16x9", n_env=24, horizon=1)
+    inp = synth.make_inputs(p, seed=4)
+    f32 = lambda x: torch.as_tensor(np.asarray(x, np.float32), device=dev).contiguous()
+    act = f32(inp["actions"])
+    sim = Simulator(p, inp, device=dev)
+    sim.reset(f32(inp["s0"]))
+    o_ref = sim.step(act[0])
+    s_ref = sim.get_state()
+    prims, off, ns, nb, ns_max, nb_max = device_scene(inp, dev)
+    n_s = np.diff(inp["sph_off"])
+    big = int(np.argmax(n_s))
+    cap = int(np.sort(n_s)[-2])  # below the largest map's sphere count only
+    assert cap < n_s[big]
+    cfg = binding.make_config(p)
+    env_map = torch.as_tensor(inp["env_map"], device=dev)
+    state = f32(inp["s0"])
+    s_before = state.clone()
+    NM = p["n_env"] * p["n_agent"]
+    r = torch.full((NM,), 7.0, device=dev)
+    status = torch.zeros(1, dtype=torch.int32, device=dev)
+    binding.sim_step_static(cfg, prims, off, ns, nb, cap, nb_max, env_map, f32(inp["targets"]), f32(inp["pool"]),
+                            state, act[0], None, None, r, None, None, None, status=status)
+    torch.cuda.synchronize()
+    assert int(status.item()) == 4  # SIM_STATUS_MAP_CAPACITY
+    skipped = np.repeat(inp["env_map"] == big, p["n_agent"])
+    sk = torch.as_tensor(skipped, device=dev)
+    assert skipped.any() and (~skipped).any()
+    assert torch.equal(state[sk], s_before[sk])
+    assert torch.all(r[sk] == 7.0)
+    kept = ~sk
+    assert torch.all((state[kept] - s_ref[kept]).abs() <= STATE_TF * s_ref[kept].abs().clamp(min=1.0))
+    assert torch.all((r[kept] - o_ref["r_ctrl"][kept]).abs() <= 1e-6 * o_ref["r_ctrl"][kept].abs().clamp(min=1.0))
     sim.close()
 
 
