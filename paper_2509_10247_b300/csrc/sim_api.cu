@@ -198,8 +198,8 @@ int validate(const sim_config* c) {
 size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 
 // Shared memory of a render CTA: the map block, one cull list per warp, the
-// TMA barrier.
-ds::Smem layout_render(const sim_handle* h, bool lists) {
+// adjoint's hit queue per warp, the TMA barrier.
+ds::Smem layout_render(const sim_handle* h, bool lists, bool queues) {
     ds::Smem s{};
     size_t o = 0;
     s.prim = 0;
@@ -208,6 +208,8 @@ ds::Smem layout_render(const sim_handle* h, bool lists) {
     s.wlist = (int)o;
     s.wstride = (int)ds::wlist_bytes(cap);
     if (lists) o += (size_t)h->nw * s.wstride;
+    s.vq = (int)o;
+    if (queues) o += (size_t)h->nw * ds::VQ_BYTES;
     s.mbar = (int)o;
     o += 16;
     s.total = (int)o;
@@ -359,13 +361,14 @@ int configure_launch(sim_handle* h) {
         if (rc) return rc;
     }
     h->cull_mode = cull;
-    h->sm_r = layout_render(h, h->S > 0);
-    h->sm_rv = layout_render(h, h->S > 0 && !h->tape);
-    h->sm_rvs = layout_render(h, h->S > 0);
-    h->sm_rvt = layout_render(h, false);
+    h->sm_r = layout_render(h, h->S > 0, false);
+    h->sm_rv = layout_render(h, h->S > 0 && !h->tape, h->S > 0);
+    h->sm_rvs = layout_render(h, h->S > 0, h->S > 0);
+    h->sm_rvt = layout_render(h, false, h->S > 0);
     int maxsm = 0;
     CK(cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
-    if (h->sm_r.total > maxsm || h->sm_rv.total > maxsm) return SIM_ERR_SIZE;
+    if (h->sm_r.total > maxsm || h->sm_rv.total > maxsm || h->sm_rvs.total > maxsm || h->sm_rvt.total > maxsm)
+        return SIM_ERR_SIZE;
     int w;
     size_t segb;
     ds::physics_bwd_shape(h->K, h->M, &w, &segb);
@@ -494,13 +497,13 @@ void set_render_parts(const sim_handle* h, Args& a) {
 // (step), 3 render adjoint gathering caller-supplied hit ids (step)
 int run_render(sim_handle* h, int which, Args& a, cudaStream_t st) {
     if (which == 0) set_render_parts(h, a);
-    const ds::Smem& sm = which == 0 ? h->sm_r : (which == 1 ? h->sm_rv : (which == 2 ? h->sm_rvs : h->sm_rvt));
+    const ds::Smem* sm = which == 0 ? &h->sm_r : (which == 1 ? &h->sm_rv : (which == 2 ? &h->sm_rvs : &h->sm_rvt));
     const int grid = which == 0 ? h->grid_r : (which == 1 ? h->grid_rv : (which == 2 ? h->grid_rvs : h->grid_rvt));
-    a.sm = sm;
+    a.sm = *sm;
     CK(cudaMemsetAsync(h->d_work, 0, sizeof(int), st));
     int occ = 0;
     return launch_kernel(h, which == 0 ? SIM_KERNEL_RENDER : SIM_KERNEL_RENDER_VJP, st, [&] {
-        return ds::render_call(which != 0, true, h->rpt, a, grid, 32 * h->nw, sm.total, st, &occ);
+        return ds::render_call(which != 0, true, h->rpt, a, grid, 32 * h->nw, sm->total, st, &occ);
     });
 }
 

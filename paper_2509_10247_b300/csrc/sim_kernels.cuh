@@ -7,6 +7,13 @@ namespace ds {
 
 constexpr int MAX_SENSORS = 2;
 
+// Hit queue of one warp of the render adjoint: VQ_CAP entries of (ray slot,
+// sensor) word, output cotangent and primitive id; VQ_FLUSH blocks of 32
+// rays at most between flushes.
+constexpr int VQ_FLUSH = 8;
+constexpr int VQ_CAP = 32 * VQ_FLUSH;
+constexpr int VQ_BYTES = VQ_CAP * 10;
+
 // Capacities of a cull list (the largest per-map counts of each kind).
 struct LCap {
     int ns, nb, nc, ng;
@@ -48,6 +55,7 @@ struct Smem {
     int mbar;    // uint64 mbarrier
     int wlist;   // render kernels: first per-warp cull list
     int wstride; // render kernels: bytes per warp list
+    int vq;      // render adjoint: first per-warp hit queue (VQ_BYTES each)
     int total;
 };
 

@@ -465,10 +465,81 @@ cudaError_t launch_render_hits(const Args& a, int grid, cudaStream_t st) {
 }
 
 // ---------------------------------------------------------- render adjoint
-// One warp per (step, agent) item: the cotangents of all its rays (every
-// sensor) reduce, in a fixed order, to the pose cotangent gposes[t][i] =
-// (d/d origin [3], d/d R [9]).  Zero when the step terminated (the state was
-// replaced).  Hit ids come from the rollout's tape or are re-cast.
+// Per-warp queue of the hit rays of one (step, agent, part) item.  Rays are
+// pushed in increasing slot order, 32 slots (a block) at a time (a ballot
+// per kind keeps the lane order); spheres fill the queue from the front, the
+// other kinds from the back.  The queue is flushed after every VQ_FLUSH
+// blocks of a sensor and at the end of each sensor; flushing hands entry q
+// of a kind to lane q mod 32, so the ray VJPs run on full warps without
+// divergence between primitive kinds, and each lane's partial sums follow
+// one fixed order that depends only on the set of hit rays: the taped and
+// the re-casting adjoints, which find the same hits, agree bit for bit.
+struct HitQueue {
+    uint32_t* key;  // [VQ_CAP] ray slot * 2 + sensor
+    float* g;       // [VQ_CAP] output cotangent of the ray
+    short* id;      // [VQ_CAP] primitive id
+    int ns, nr;     // sphere entries from the front, other kinds from the back
+    int nblk;       // blocks pushed since the last flush
+};
+
+__device__ __forceinline__ HitQueue hit_queue(unsigned char* sm, const Args& a, int warp) {
+    HitQueue q;
+    q.key = reinterpret_cast<uint32_t*>(sm + a.sm.vq + (size_t)warp * VQ_BYTES);
+    q.g = reinterpret_cast<float*>(q.key + VQ_CAP);
+    q.id = reinterpret_cast<short*>(q.g + VQ_CAP);
+    q.ns = q.nr = q.nblk = 0;
+    return q;
+}
+
+// Push the lane's ray of a block of 32 consecutive slots (valid: a hit with
+// a non-zero cotangent).  Every lane of the warp calls it.
+__device__ __forceinline__ void hq_push(HitQueue& q, bool valid, int ns, int si, int j, int id, float g) {
+    const int lane = threadIdx.x & 31;
+    const unsigned below = (1u << lane) - 1u;
+    const bool hs = valid && id < ns, hr = valid && id >= ns;
+    const unsigned bs = __ballot_sync(0xffffffffu, hs), br = __ballot_sync(0xffffffffu, hr);
+    if (hs || hr) {
+        const int p = hs ? q.ns + __popc(bs & below) : VQ_CAP - 1 - (q.nr + __popc(br & below));
+        q.key[p] = ((uint32_t)j << 1) | (uint32_t)si;
+        q.g[p] = g;
+        q.id[p] = (short)id;
+    }
+    q.ns += __popc(bs);
+    q.nr += __popc(br);
+    ++q.nblk;
+}
+
+// Ray VJPs of every queued entry, accumulated into the lane's go / gR.
+template <bool EXTRA>
+__device__ __forceinline__ void hq_flush(HitQueue& q, const Args& a, const MapView& mv, const float* o,
+                                         const float* R, float* go, float* gR) {
+    const int lane = threadIdx.x & 31;
+    __syncwarp();
+    for (int k = lane; k < q.ns; k += 32) {
+        const uint32_t key = q.key[k];
+        const Sensor& sen = a.sen[key & 1u];
+        float d[3];
+        const float4 db = ray_dir(sen, R, (int)(key >> 1), d);
+        ray_vjp<EXTRA>(mv, q.id[k], o, d[0], d[1], d[2], db, sen, q.g[k], go, gR);
+    }
+    for (int k = lane; k < q.nr; k += 32) {
+        const int p = VQ_CAP - 1 - k;
+        const uint32_t key = q.key[p];
+        const Sensor& sen = a.sen[key & 1u];
+        float d[3];
+        const float4 db = ray_dir(sen, R, (int)(key >> 1), d);
+        ray_vjp<EXTRA>(mv, q.id[p], o, d[0], d[1], d[2], db, sen, q.g[p], go, gR);
+    }
+    __syncwarp();
+    q.ns = q.nr = q.nblk = 0;
+}
+
+// One warp per (step, agent, part) item: the cotangents of all its rays
+// (every sensor) reduce, in a fixed order, to the pose cotangent
+// gposes[t][i] = (d/d origin [3], d/d R [9]).  Zero when the step terminated
+// (the state was replaced).  Hit ids come from the rollout's tape or are
+// re-cast; the hit rays are queued (HitQueue) and their VJPs run on full
+// warps.
 template <int RPT, bool TAPE, bool EXTRA>
 __global__ void __launch_bounds__(256, TAPE ? 4 : 3) k_render_vjp(const Args a) {
     extern __shared__ __align__(16) unsigned char sm[];
@@ -480,13 +551,13 @@ __global__ void __launch_bounds__(256, TAPE ? 4 : 3) k_render_vjp(const Args a) 
     const LCap cap = cap_of(a);
     WList L;
     if (recast) L = wlist_at(sm + a.sm.wlist + (size_t)warp * a.sm.wstride, cap);
+    HitQueue hq = hit_queue(sm, a, warp);
     if (threadIdx.x == 0) mbar_init(reinterpret_cast<uint64_t*>(sm + a.sm.mbar));
     __syncthreads();
     uint32_t phase = 0;
     // items: (step, agent, part); part p takes the slots [32 w0, 32 w1) of
     // every sensor, w0 = p W / P, w1 = (p + 1) W / P with W = ceil(R / 32)
-    // (the same slots for every rays-per-thread setting, so taped and
-    // re-cast gradients agree bit for bit)
+    // (the same slots for every rays-per-thread setting)
     const int P = a.parts;
     const int per_env = a.T * M * P;
     for (;;) {
@@ -502,6 +573,7 @@ __global__ void __launch_bounds__(256, TAPE ? 4 : 3) k_render_vjp(const Args a) 
         const MapView mv = map_view(a, map, prim);
         if (!stage_map(a, sm, map, mv, phase, &s_flag)) return;
         prep_boxes(sm, a, mv.ns, mv.nb);
+        const int nprim = mv.count();
         for (int it = warp; it < per_env; it = next_item(&s_item, lane)) {
             const int tm = div_small(it, P), part = it - tm * P;
             const int t = div_small(tm, M), m = tm - t * M;
@@ -522,35 +594,35 @@ __global__ void __launch_bounds__(256, TAPE ? 4 : 3) k_render_vjp(const Args a) 
                     const size_t base = ti * sen.R;
                     const int W32 = (sen.R + 31) / 32;
                     const int j0 = 32 * (part * W32 / P), j1 = min(sen.R, 32 * ((part + 1) * W32 / P));
+                    if (j0 >= j1) continue;
                     if (TAPE) {
-                        // taped hit ids: rays in slot order j = j0 + lane, + 32, ...
-                        // the next ray's hit id and cotangent are in flight while
-                        // the current one is processed
-                        int jn = j0 + lane;
-                        int idn = -1;
-                        float gn = 0.f;
-                        if (jn < j1) {
-                            const int ray = out_index(sen, jn);
-                            idn = sen.tape[base + ray];
-                            gn = sen.gout[base + ray];
-                        }
-                        while (jn < j1) {
-                            const int j = jn, id = idn;
-                            const float gv = gn;
-                            jn += 32;
-                            if (jn < j1) {
-                                const int ray = out_index(sen, jn);
-                                idn = sen.tape[base + ray];
-                                gn = sen.gout[base + ray];
+                        // taped hit ids: rounds of VQ_FLUSH blocks whose ids and
+                        // cotangents are loaded together (many loads in flight)
+                        for (int b0 = j0; b0 < j1; b0 += 32 * VQ_FLUSH) {
+                            int idv[VQ_FLUSH];
+                            float gv[VQ_FLUSH];
+#pragma unroll
+                            for (int u = 0; u < VQ_FLUSH; ++u) {
+                                const int j = b0 + 32 * u + lane;
+                                idv[u] = -1;
+                                gv[u] = 0.f;
+                                if (j < j1) {
+                                    const int ray = out_index(sen, j);
+                                    idv[u] = sen.tape[base + ray];
+                                    gv[u] = sen.gout[base + ray];
+                                }
                             }
-                            if (id < 0) continue;
-                            float d[3];
-                            const float4 db = ray_dir(sen, R, j, d);
-                            ray_vjp<EXTRA>(mv, id, o, d[0], d[1], d[2], db, sen, gv, go, gR);
+#pragma unroll
+                            for (int u = 0; u < VQ_FLUSH; ++u) {
+                                if (b0 + 32 * u >= j1) break;
+                                const int id = idv[u];
+                                hq_push(hq, id >= 0 && id < nprim && gv[u] != 0.f, mv.ns, si, b0 + 32 * u + lane, id,
+                                        gv[u]);
+                            }
+                            hq_flush<EXTRA>(hq, a, mv, o, R, go, gR);
                         }
                         continue;
                     }
-                    if (j0 >= j1) continue;
                     const int4 meta = warp_build_list<EXTRA, true>(mv, o, R, sen, a.cull, L, cap);
                     const int chb = j0 / (32 * RPT), che = (j1 + 32 * RPT - 1) / (32 * RPT);
                     for (int ch = chb; ch < che; ++ch) {
@@ -567,14 +639,21 @@ __global__ void __launch_bounds__(256, TAPE ? 4 : 3) k_render_vjp(const Args a) 
                                 cast_list<RPT, EXTRA>(L, meta, cap, dx, dy, dz, tb, bi);
                             }
                         }
+                        // the blocks of the part's slots, in order; a flush
+                        // after every VQ_FLUSH of them, as in the taped gather
 #pragma unroll
                         for (int r = 0; r < RPT; ++r) {
-                            const int j = ch * 32 * RPT + r * 32 + lane;
-                            if (j < j0 || j >= j1 || meta.z >= 0 || bi[r] < 0) continue;
-                            ray_vjp<EXTRA>(mv, L.id[bi[r]], o, dx[r], dy[r], dz[r], __ldg(sen.dir + j), sen,
-                                    sen.gout[base + out_index(sen, j)], go, gR);
+                            const int jb = ch * 32 * RPT + r * 32, j = jb + lane;
+                            if (jb >= j1) break;
+                            if (jb < j0) continue;
+                            const bool hit = j < j1 && meta.z < 0 && bi[r] >= 0;
+                            const int id = hit ? L.id[bi[r]] : -1;
+                            const float g = hit ? sen.gout[base + out_index(sen, j)] : 0.f;
+                            hq_push(hq, hit && g != 0.f, mv.ns, si, j, id, g);
+                            if (hq.nblk == VQ_FLUSH) hq_flush<EXTRA>(hq, a, mv, o, R, go, gR);
                         }
                     }
+                    hq_flush<EXTRA>(hq, a, mv, o, R, go, gR);
                     __syncwarp();
                 }
             }
