@@ -63,6 +63,8 @@ def parse():
     ap.add_argument("--policy-only", action="store_true",
                     help="closed-loop workload: time the policy's act and backward on rendered observations only")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--ref-seconds", type=float, default=5.0,
+                    help="reference arm: oracle seconds per step (the sample size follows)")
     ap.add_argument("--n-env", type=int, default=None,
                     help="override the number of environments (profiling on a smaller case)")
     return ap.parse_args()
@@ -89,6 +91,24 @@ def source_hash():
 def peak_fp32_tinst(num_sms, sm_mhz):
     # FP32-pipe issue: 128 lanes per SM, one instruction per lane and cycle
     return 128.0 * num_sms * sm_mhz * 1e6 / 1e12
+
+
+def measured_peaks():
+    """The measured HBM and bf16 peaks (MEASURED_PEAKS.json), else the
+    recipe's fallback figures; returns (dict, basis)."""
+    f = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(f):
+        return json.load(open(f)), "measured (MEASURED_PEAKS.json)"
+    return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0}, "fallback"
+
+
+def render_vjp_bytes(NM, T, R, parts):
+    """Algorithmic DRAM bytes of one taped render-adjoint launch: per ray its
+    hit id (2 B) and output cotangent (4 B); per (step, agent) item its pose
+    (48 B) and done flag (1 B); per item part the pose cotangent written
+    (48 B)."""
+    items = T * NM
+    return items * R * 6 + items * (48 + 1) + items * parts * 48
 
 
 def config_of(p, extra=None):
@@ -189,10 +209,9 @@ def run_reference(args, rank, world):
     inp = synth.make_inputs(p, seed=args.seed)
     import oracle
     oracle.build()
-    # size the per-step sample to about 2 s of CPU work
-    n = max(1, min(8, p["n_env"]))
-    dt, _ = oracle_sample(p, inp, n)
-    n = int(max(1, min(p["n_env"], n * 2.0 / max(dt, 1e-3))))
+    # size the per-step sample like the CPU baseline: enough environments
+    # (all maps, every host core busy) for about --ref-seconds of oracle work
+    _, n, _, _ = cpu_rate(p, inp, args.ref_seconds)
     for _ in range(args.warmup):
         oracle_sample(p, inp, n)
     times = []
@@ -332,13 +351,18 @@ def run_ours(args, rank, world):
 
     if rank != 0:
         return 0
-    # roofline of the dominant kernel: k_render (FP32 ray casting), per launch
+    # roofline of the dominant kernel: k_render (FP32 ray casting), per launch;
+    # the FP32 peak is measured on this GPU right after the timed region
+    from paper_2509_10247_b300.binding import sim_fp32_issue_rate
     props = torch.cuda.get_device_properties(dev)
+    fma_s, ffma2_s = sim_fp32_issue_rate(dev)
     ops = OPS_SPHERE_TEST * cnt["sphere_tests"] + OPS_BOX_TEST * cnt["box_tests"]
     flop = FLOP_SPHERE_TEST * cnt["sphere_tests"] + FLOP_BOX_TEST * cnt["box_tests"]
     render_ms = kt["render"][0] / max(kt["render"][1], 1)
     achieved = ops / (render_ms / 1e3) / 1e12
-    peak = peak_fp32_tinst(props.multi_processor_count, 2032.0)
+    peak = max(fma_s, ffma2_s) / 1e12
+    sm_mhz = (ck or {}).get("sm_mhz") or 2032.0
+    peak_derived = peak_fp32_tinst(props.multi_processor_count, sm_mhz)
     traffic = None
     tfile = os.path.join(ROOT, "profiles", "traffic.txt")
     if os.path.exists(tfile):
@@ -350,8 +374,12 @@ def run_ours(args, rank, world):
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tinst/s",
                 "frac": achieved / peak, "traffic": traffic,
                 "kernel": "k_render (ray casting of all T steps)", "kernel_ms": render_ms,
-                "peak_basis": "FP32-pipe issue, %d SMs x 128 lanes x 2032 MHz, one instruction (an FMA counts "
-                              "once) per lane and cycle (derived, not measured)" % props.multi_processor_count,
+                "peak_basis": "measured: FP32 multiply-adds per second of this GPU (sim_fp32_issue_rate, "
+                              "scalar %.2f T/s, packed pairs %.2f T/s; the larger), right after the timed region"
+                              % (fma_s / 1e12, ffma2_s / 1e12),
+                "peak_derived_at_sampled_clock": peak_derived,
+                "derived_basis": "%d SMs x 128 FP32 lanes x %.0f MHz (median SM clock sampled in the timed "
+                                 "region)" % (props.multi_processor_count, sm_mhz),
                 "work_basis": "per test after culling: sphere %d, box %d FP32-pipe instructions"
                               % (OPS_SPHERE_TEST, OPS_BOX_TEST),
                 "tests_per_launch": cnt["sphere_tests"] + cnt["box_tests"],
@@ -359,16 +387,29 @@ def run_ours(args, rank, world):
                 "ops_per_launch": ops, "flop_per_launch": flop,
                 "tflops": flop / (render_ms / 1e3) / 1e12, "frac_flop": flop / (render_ms / 1e3) / 1e12 / (2 * peak),
                 "kernels": per_kernel}
+    # second roofline: the ray adjoint (taped: reads hit ids and cotangents, HBM)
+    vjp_ms = kt["render_vjp"][0] / max(kt["render_vjp"][1], 1)
+    pk, pk_basis = measured_peaks()
+    # the library splits a rollout adjoint's items into ceil(8 / (T M)) ray parts (at most 8)
+    parts = min(8, max(1, -(-8 // (T * p["n_agent"]))))
+    vjp_b = render_vjp_bytes(NM, T, Rc + sim.Rl, parts)
+    roofline_vjp = {"bound": "hbm", "achieved": vjp_b / (vjp_ms / 1e3) / 1e9, "peak": pk["hbm_gbs"],
+                    "unit": "GB/s", "frac": vjp_b / (vjp_ms / 1e3) / 1e9 / pk["hbm_gbs"], "traffic": None,
+                    "kernel": "k_render_vjp (taped ray adjoint of all T steps)", "kernel_ms": vjp_ms,
+                    "bytes_per_launch": vjp_b, "peak_basis": pk_basis,
+                    "work_basis": "per ray 2 B hit id + 4 B cotangent; per (step, agent) 48 B pose + 1 B done; "
+                                  "per item part 48 B pose cotangent written"}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": config_of(p, {"l2": "inputs larger than L2: %.1f GB depth written and %.1f GB "
-                                          "depth cotangent read per step" % (4e-9 * T * NM * Rc,
-                                                                            4e-9 * T * NM * Rc),
-                                    "exec": BENCH_EXEC}),
+            "config": config_of(p),
+            "l2": "inputs larger than L2: %.1f GB depth written and %.1f GB depth cotangent read per step"
+                  % (4e-9 * T * NM * Rc, 4e-9 * T * NM * Rc),
+            "exec": BENCH_EXEC,
             "grays_per_s": grays, "agent_steps_per_s": value * p["n_agent"],
             "fwd_ms": fwd_ms, "bwd_ms": bwd_ms,
-            "roofline": roofline, "gpu_launches": launches, "clocks": ck, "graph": graph}
+            "roofline": roofline, "roofline_render_vjp": roofline_vjp,
+            "gpu_launches": launches, "clocks": ck, "graph": graph}
     # end to end: host actions and initial state in, rewards and action gradients out
     if not args.no_e2e:
         line["e2e"] = run_e2e(args, sim, inp, dev, g_r, g_d, out, g_a, g_s0, p)
@@ -649,7 +690,11 @@ def run_e2e(args, sim, inp, dev, g_r, g_d, out, g_a, g_s0, p):
     return {"value": p["n_env"] * T * args.steps / (ms / 1e3), "unit": UNIT,
             "h2d_bytes_per_step": h2d_b, "d2h_bytes_per_step": d2h_b,
             "what": "pinned host actions + initial state in; rewards + action gradients out, on a copy "
-                    "stream double-buffered against the compute; reward/depth cotangents device-resident"}
+                    "stream double-buffered against the compute",
+            "device_resident": "the depth images written by the rollout (%.1f GB per step) and the reward "
+                               "and depth cotangents read by the adjoint (%.1f GB per step) stay on the device, "
+                               "as for a policy that consumes depth on the GPU; they are not copied"
+                               % (4e-9 * T * NM * sim.Rc, 4e-9 * T * NM * (sim.Rc + 1))}
 
 
 def main():

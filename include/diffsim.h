@@ -346,11 +346,36 @@ int sim_step_backward_taped(sim_handle *h, const float *s_t, const float *a_t,
  * per_env is reserved and must be NULL. */
 int sim_last_status(sim_handle *h, int32_t *status, int32_t *per_env);
 
+/* sim_set_wait_limit: polls > 0 limits the first wait of every render and
+ * rollout CTA of h (the wait for its map's bulk copy) to that many
+ * non-blocking polls; 0 (the default) restores the full bounded wait.  The
+ * paper has no counterpart: this exercises the failure path of the bounded
+ * device waits.  A wait that runs out sets SIM_STATUS_TIMEOUT; the CTA then
+ * waits (fully bounded) for its copy in flight and stops, so the launch's
+ * outputs are incomplete and sim_last_status returns SIM_ERR_TIMEOUT, while
+ * the handle and the CUDA context stay usable.  SIM_ERR_INVALID_ARG for
+ * polls < 0. */
+int sim_set_wait_limit(sim_handle *h, int32_t polls);
+
 /* Work counters accumulated by the forward kernels since the last reset:
  * out[0] ray-sphere tests, out[1] ray-box tests (both after field-of-view
  * culling), out[2] rays cast, out[3] environment steps.  Synchronises the
  * last stream.  reset != 0 zeroes the counters after reading. */
 int sim_counters(sim_handle *h, uint64_t *out, int32_t reset);
+
+/* sim_fp32_issue_rate: measures this GPU's FP32 multiply-add rate, the
+ * denominator of the ray cast's roofline (the paper has no counterpart: a
+ * measurement utility).  Runs a grid of 8 CTAs of 256 threads per SM, each
+ * thread 8 independent FMA chains, timed with CUDA events on `stream` (the
+ * call synchronises it); the fastest of three passes after a warm-up.
+ *   scratch        DEVICE float[scratch_floats] that receives the chains'
+ *                  sums (>= 2048 * SM count floats, else SIM_ERR_SIZE)
+ *   fma_per_s      HOST out: scalar FMAs per second (one FP32-pipe
+ *                  instruction per lane and FMA)
+ *   ffma2_per_s    HOST out (nullable): FMAs per second issued as packed
+ *                  pairs (one instruction per lane, two FMAs) */
+int sim_fp32_issue_rate(float *scratch, int64_t scratch_floats, double *fma_per_s, double *ffma2_per_s,
+                        sim_stream_t stream);
 
 /* Bytes of the library's static device scratch used by sim_step_static. */
 #define SIM_STATIC_SCRATCH_BYTES (256 * 1024)

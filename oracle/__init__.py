@@ -13,6 +13,8 @@ Parity status of each oracle function (what pins it, see tests/test_oracle_*):
   ray casting (Sec. III-B)     closed-form hits, wall z-depth, SDF marching
   collisions and rewards       hand-computed cases
   adjoint (Eq. 5)              central finite differences of ``loss``
+  culling work count           brute-force counts of hand-placed cases
+                               (tests/test_oracle_cull.py)
 """
 from __future__ import annotations
 
@@ -273,6 +275,16 @@ class Oracle:
         return lib().oc_loss(C.byref(self.cfg), C.byref(self.scene), _p(_c64(s0)),
                              _p(_c64(actions)), _p(_c64(g_r)), _p(gd), _p(gl), _p(gs), _p(gi),
                              _p(gk, _pi), _p(_c64(imu_noise)), _p(_c64(imu_bias)))
+
+    def cull_counts(self, s):
+        """Post-cull work of one render of states s [NM, D] under the
+        frustum culling rule (see oc_cull_counts): dict of sphere_tests,
+        other_tests (boxes, cylinders, gates), rays, and ambiguous (tests
+        that near-threshold decisions could move)."""
+        s = _c64(s).reshape(self.NM, self.D)
+        out = np.zeros(4)
+        lib().oc_cull_counts(C.byref(self.cfg), C.byref(self.scene), _p(s), _p(out))
+        return dict(sphere_tests=int(out[0]), other_tests=int(out[1]), rays=int(out[2]), ambiguous=int(out[3]))
 
     def render(self, s):
         """Sensor outputs of states s [NM, D]: (depth, lidar, hit_cam, hit_lid, amb_cam, amb_lid)."""

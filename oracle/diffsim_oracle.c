@@ -1041,6 +1041,132 @@ int oc_render(const oc_config *c, const oc_scene *sc, const double *s, double *d
     return 0;
 }
 
+/* ---------------------------------------------------- culling work count */
+
+/* Bounding sphere (centre cb, radius) of primitive id of a map. */
+static double prim_bound(const map_t *m, int id, double *cb)
+{
+    if (id < m->ns) {
+        for (int i = 0; i < 3; ++i) cb[i] = m->sph[4 * id + i];
+        return m->sph[4 * id + 3];
+    }
+    id -= m->ns;
+    if (id < m->nb) {
+        const double *b = m->box + 6 * id;
+        double h2 = 0.0;
+        for (int i = 0; i < 3; ++i) {
+            cb[i] = 0.5 * (b[i] + b[3 + i]);
+            double h = 0.5 * (b[3 + i] - b[i]);
+            h2 += h * h;
+        }
+        return sqrt(h2);
+    }
+    id -= m->nb;
+    if (id < m->nc) {
+        const double *cy = m->cyl + 5 * id;
+        double hz = 0.5 * (cy[4] - cy[3]);
+        cb[0] = cy[0]; cb[1] = cy[1]; cb[2] = 0.5 * (cy[3] + cy[4]);
+        return sqrt(hz * hz + cy[2] * cy[2]);
+    }
+    const double *g = m->gate + 7 * (id - m->nc);
+    double W = g[4] + g[5];
+    for (int i = 0; i < 3; ++i) cb[i] = g[i];
+    return sqrt(g[6] * g[6] + 2.0 * W * W);
+}
+
+/* Post-cull work of one render of the states s [NM][D] (Sec. III-B: each
+ * sensor's rays are cast only against the primitives that its field of view
+ * can reach).  The culling rule counted here is the one the CUDA path applies
+ * with frustum culling (cull mode 1), restated in double precision from its
+ * definition: a primitive is kept for an agent's sensor when its bounding
+ * sphere (centre c, radius rho, relative position oc = c - o) either holds
+ * the origin (|oc| <= rho + 1e-3) or lies within reach (|oc| - rho <= L +
+ * 1e-3, L the longest unclamped ray: range / cos of the corner ray for the
+ * camera, the range for the LiDAR) and meets the sensor's field of view with
+ * a 1e-3 m margin: for the camera the four side planes of the pinhole
+ * frustum (body frame, signed distance of the centre >= -(rho + 1e-3)); for
+ * the LiDAR the elevation band widened by 1e-3 rad and by the sphere's
+ * angular radius.  An agent whose origin lies in a primitive casts no test.
+ * out[0] ray-sphere tests, out[1] tests of the other kinds, out[2] rays,
+ * out[3] a bound on the tests that decisions within 1e-6 of a threshold (in
+ * double precision) could move. */
+int oc_cull_counts(const oc_config *c, const oc_scene *sc, const double *s, double *out)
+{
+    ctx_t x;
+    ctx_init(&x, c, sc);
+    const int M = c->n_agent;
+    const double mg = 1e-3, eps = 1e-6;
+    double th = tan(0.5 * c->cam_hfov), tv = th * (double)c->cam_h / (double)(c->cam_w > 0 ? c->cam_w : 1);
+    double uc = (1.0 - 1.0 / (c->cam_w > 0 ? c->cam_w : 1)) * th, vc = (1.0 - 1.0 / (c->cam_h > 0 ? c->cam_h : 1)) * tv;
+    double cam_len = c->cam_range * sqrt(1.0 + uc * uc + vc * vc);
+    double c2 = 1.0 / sqrt(1.0 + th * th), c3 = 1.0 / sqrt(1.0 + tv * tv);
+    for (int k = 0; k < 4; ++k) out[k] = 0.0;
+    for (int i = 0; i < x.NM; ++i) {
+        map_t mp;
+        map_of(&x, i / M, &mp);
+        double o[3], R[9];
+        oc_pose(c, s + (size_t)i * x.D, o, R);
+        const int np = map_count(&mp);
+        /* origin inside a primitive (closed sets), and how close to a surface */
+        int inside = 0;
+        double near_surf = OC_INF;
+        for (int k = 0; k < np; ++k) {
+            double d = prim_sdf(&mp, k, o);
+            if (d <= 0.0) inside = 1;
+            if (fabs(d) < near_surf) near_surf = fabs(d);
+        }
+        for (int sen = 0; sen < 2; ++sen) {
+            const int R_s = sen == 0 ? x.Rc : x.Rl;
+            if (R_s == 0) continue;
+            out[2] += R_s;
+            const double len = sen == 0 ? cam_len : c->lid_range;
+            long ks = 0, ko = 0, amb = 0;
+            for (int k = 0; k < np; ++k) {
+                double cb[3], oc[3], bx[3];
+                double rho = prim_bound(&mp, k, cb);
+                for (int j = 0; j < 3; ++j) oc[j] = cb[j] - o[j];
+                for (int j = 0; j < 3; ++j) bx[j] = R[j] * oc[0] + R[3 + j] * oc[1] + R[6 + j] * oc[2];
+                double L2 = dot3(oc, oc), r = rho + mg, rout = len + mg + rho;
+                int near = L2 <= r * r, far = L2 > rout * rout, keep;
+                int a = fabs(L2 - r * r) < eps * (L2 > 1.0 ? L2 : 1.0) || fabs(L2 - rout * rout) < eps * (L2 > 1.0 ? L2 : 1.0);
+                if (sen == 0) {
+                    double f[4] = {th * c2 * bx[0] - c2 * bx[1], th * c2 * bx[0] + c2 * bx[1],
+                                   tv * c3 * bx[0] - c3 * bx[2], tv * c3 * bx[0] + c3 * bx[2]};
+                    int in = 1;
+                    for (int q = 0; q < 4; ++q) {
+                        if (f[q] < -r) in = 0;
+                        if (fabs(f[q] + r) < eps * (1.0 + sqrt(L2))) a = 1;
+                    }
+                    keep = near || (!far && in);
+                } else {
+                    double L = sqrt(L2);
+                    if (near) keep = 1;
+                    else if (far) keep = 0;
+                    else {
+                        double el = asin(clamp1(bx[2] / L)), del = asin(r / L < 1.0 ? r / L : 1.0);
+                        double lo = c->lid_elev_lo - mg, hi = c->lid_elev_hi + mg;
+                        keep = el - del <= hi && el + del >= lo;
+                        if (fabs(el - del - hi) < eps || fabs(el + del - lo) < eps) a = 1;
+                    }
+                }
+                if (keep) {
+                    if (k < mp.ns) ++ks;
+                    else ++ko;
+                }
+                amb += a;
+            }
+            if (inside) {
+                ks = ko = 0;
+            }
+            out[0] += (double)R_s * ks;
+            out[1] += (double)R_s * ko;
+            out[3] += (double)R_s * (near_surf < eps ? np : amb);
+        }
+    }
+    ctx_free(&x);
+    return 0;
+}
+
 /* ------------------------------------------------------------------ IMU */
 
 /* IMU readout of one agent after a step (Sec. III-B), noise-free: the

@@ -38,7 +38,8 @@ SYMBOLS = ["sim_version", "sim_strerror", "sim_state_dim", "sim_action_dim", "si
            "sim_launch_info", "sim_counters", "sim_step_static", "sim_profile", "sim_kernel_times",
            "sim_graph_create", "sim_graph_launch", "sim_graph_kernels", "sim_graph_destroy",
            "sim_set_scene_ex", "sim_get_gate_index", "sim_set_gate_index", "sim_rollout_ex",
-           "sim_step_ex", "sim_backward_ex", "sim_render_taped", "sim_step_backward_taped", "sim_render_hits"]
+           "sim_step_ex", "sim_backward_ex", "sim_render_taped", "sim_step_backward_taped", "sim_render_hits",
+           "sim_fp32_issue_rate", "sim_set_wait_limit"]
 
 # flight tasks (Sec. III-C)
 TASKS = {"reach": 0, "racing": 1}
@@ -339,6 +340,10 @@ def sim_last_status(h):
     return st.value
 
 
+def sim_set_wait_limit(h, polls):
+    _ck(lib().sim_set_wait_limit(h, _i(polls)), "sim_set_wait_limit")
+
+
 def sim_counters(h, reset=True):
     v = (C.c_uint64 * 4)()
     _ck(lib().sim_counters(h, v, _i(1 if reset else 0)), "sim_counters")
@@ -362,6 +367,18 @@ def sim_step_static(cfg, prims, map_off, map_ns, map_nb, ns_max, nb_max, env_map
                               _ptr(state), _ptr(actions), _ptr(depth), _ptr(lidar), _ptr(r_ctrl),
                               _ptr(r_goal), _ptr(done), _ptr(pool_k), _ptr(status), _stream(stream)),
         "sim_step_static")
+
+
+def sim_fp32_issue_rate(device=None, stream=None):
+    """Measured FMAs per second of this GPU: (scalar, packed pairs)."""
+    dev = torch.device("cuda") if device is None else torch.device(device)
+    n = torch.cuda.get_device_properties(dev).multi_processor_count * 2048
+    scratch = torch.empty(n, dtype=torch.float32, device=dev)
+    a, b = C.c_double(), C.c_double()
+    with torch.cuda.device(dev):
+        _ck(lib().sim_fp32_issue_rate(_ptr(scratch), C.c_int64(n), C.byref(a), C.byref(b), _stream(stream)),
+            "sim_fp32_issue_rate")
+    return a.value, b.value
 
 
 def sim_profile(h, on=True):
@@ -575,6 +592,9 @@ class Simulator:
 
     def launch_info(self):
         return sim_launch_info(self.h)
+
+    def set_wait_limit(self, polls):
+        sim_set_wait_limit(self.h, polls)
 
     def counters(self, reset=True):
         return sim_counters(self.h, reset)

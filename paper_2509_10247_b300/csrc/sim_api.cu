@@ -79,6 +79,7 @@ struct sim_handle {
     // ray parts per render item of a rollout and of a single step: enough
     // items per environment for 8 warps (a function of T and M only)
     int parts_roll = 1, parts_one = 1;
+    int wait_polls = 0;  // sim_set_wait_limit
     ds::Smem sm_r{}, sm_rv{}, sm_rvs{}, sm_rvt{};
     // kernel launches per kind; while profiling, one CUDA event pair per launch
     bool profiling = false, capturing = false, ev_overflow = false;
@@ -420,6 +421,7 @@ Args base_args(const sim_handle* h) {
     a.drag_env = h->d_drag; a.lam_env = h->d_lam;
     a.state = h->d_state; a.pool_k = h->d_pool_k;
     a.work = h->d_work; a.status = h->d_status;
+    a.wait_polls = h->wait_polls;
     a.counters = h->d_counters;
     a.parts = h->parts_roll;
     return a;
@@ -1142,6 +1144,13 @@ int sim_last_status(sim_handle* h, int32_t* status, int32_t* per_env) {
     *status = v;
     if (v & SIM_STATUS_TIMEOUT) return SIM_ERR_TIMEOUT;
     if (v & SIM_STATUS_NAN) return SIM_ERR_NAN;
+    return SIM_OK;
+}
+
+int sim_set_wait_limit(sim_handle* h, int32_t polls) {
+    if (!h) return SIM_ERR_NULL_PTR;
+    if (polls < 0) return SIM_ERR_INVALID_ARG;
+    h->wait_polls = polls;
     return SIM_OK;
 }
 

@@ -96,6 +96,7 @@ struct Args {
     const float* g_imu;         // adjoint: [T][NM][6] cotangent of the readout or nullptr
     // control
     int* work; int* status;
+    int wait_polls;             // > 0: poll limit of the map copy's wait (tests of the timeout path)
     unsigned long long* counters;  // [4]: sphere tests, box / cylinder / gate tests, rays, env-steps (nullable)
 };
 
@@ -140,6 +141,27 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase) {
         if (mbar_try(bar, phase)) return true;
         if (i > 64) __nanosleep(256);
     }
+    return false;
+}
+
+// Non-blocking test of the mbarrier phase.
+__device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t phase) {
+    uint32_t ok;
+    asm volatile(
+        "{ .reg .pred p; mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(phase)
+        : "memory");
+    return ok != 0;
+}
+
+// The first wait of a CTA: polls > 0 limits it to that many non-blocking
+// tests (a host-set limit that lets a test make the wait run out); 0 waits
+// as mbar_wait does.
+__device__ __forceinline__ bool mbar_wait_first(uint64_t* bar, uint32_t phase, int polls) {
+    if (polls <= 0) return mbar_wait(bar, phase);
+    for (int i = 0; i < polls; ++i)
+        if (mbar_test(bar, phase)) return true;
     return false;
 }
 

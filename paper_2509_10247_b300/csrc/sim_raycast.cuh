@@ -707,7 +707,7 @@ __device__ inline bool stage_map(const Args& a, unsigned char* sm, int map, cons
     if (bytes == 0) return true;
     if (threadIdx.x == 0) {
         bulk_load(sm + a.sm.prim, a.prims + a.map_off[map], bytes, bar);
-        bool ok = mbar_wait(bar, phase);
+        bool ok = mbar_wait_first(bar, phase, a.wait_polls);
         if (!ok) {
             atomicOr(a.status, 2);
             mbar_wait(bar, phase);  // give the copy in flight a second bounded chance

@@ -22,7 +22,7 @@ def lib():
 def declared_functions(header="diffsim.h", prefix="sim_"):
     src = open(os.path.join(ROOT, "include", header)).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(%s[a-z_]+)\s*\(" % prefix, src)))
+    return sorted(set(re.findall(r"\b(%s[a-z0-9_]+)\s*\(" % prefix, src)))
 
 
 def test_every_declared_symbol_is_exported(lib):

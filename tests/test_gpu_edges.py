@@ -150,3 +150,38 @@ def test_foreign_hit_ids_stay_in_bounds():
                                hits=hits)
     torch.cuda.synchronize()
     assert sim.status() in (0, 1)  # a foreign hit may give a non-finite gradient (flagged), never a fault
+
+
+def test_bounded_wait_that_runs_out_is_reported_and_the_handle_recovers():
+    """The first wait of every render CTA (for its map's bulk copy) limited
+    to one non-blocking poll runs out before the copy lands: the kernels set
+    SIM_STATUS_TIMEOUT, wait (bounded) for the copy in flight and stop, no
+    hang and no fault; with the limit lifted the same handle reproduces the
+    reference rollout and adjoint bit for bit."""
+    p = synth.preset("swarm_16384env_8agent_8maps_depth16x9", n_env=64, horizon=4)
+    inp = synth.make_inputs(p, seed=3)
+    sim = Simulator(p, inp)
+    s0, act = dev(inp["s0"]), dev(inp["actions"])
+    g_r = dev(synth.cotangents(p, seed=4)["g_r"])
+
+    def run():
+        sim.reset(s0)
+        o = sim.rollout(act)
+        ga, gs = sim.backward(g_r)
+        torch.cuda.synchronize()
+        return {k: (None if v is None else v.clone()) for k, v in o.items()}, ga.clone(), gs.clone()
+
+    ref = run()
+    assert sim.status() == 0
+    sim.set_wait_limit(1)
+    run()
+    assert sim.status() & 2  # SIM_STATUS_TIMEOUT
+    sim.set_wait_limit(0)
+    again = run()
+    assert sim.status() == 0
+    for k in ("r_ctrl", "r_goal", "done", "depth"):
+        assert torch.equal(ref[0][k], again[0][k]), k
+    assert torch.equal(ref[1], again[1]) and torch.equal(ref[2], again[2])
+    with pytest.raises(SimError):
+        sim.set_wait_limit(-1)
+    sim.close()

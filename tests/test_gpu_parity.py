@@ -387,3 +387,29 @@ def test_step_adjoint_chain_matches_rollout_adjoint(pair):
     scale = ga.abs().max().item()
     assert (g_chain - ga).abs().max().item() <= 1e-5 * max(scale, 1.0)
     assert (s.grad - gs).abs().max().item() <= 1e-5 * max(gs.abs().max().item(), 1.0)
+
+
+def test_cull_counters_match_oracle_count(pair):
+    """The render kernel's own post-cull test counters (the work the
+    roofline credits) against the oracle's independent count of the same
+    frustum rule at the same states: equal, up to the tests that decisions
+    within 1e-6 of a threshold could move (none in most cases)."""
+    p = pair.p
+    if p["cam"] is None and p["lidar"] is None:
+        pytest.skip("no sensor")
+    sim = Simulator(p, pair.inp, cull=1)
+    T = pair.rec["r_ctrl"].shape[0]
+    exact = 0
+    for t in sorted(set([0, T // 2, T])):
+        s32 = pair.rec["states"][t].astype(np.float32).astype(np.float64)
+        sim.reset(dev(s32))
+        sim.counters(reset=True)
+        sim.render()
+        c = sim.counters(reset=True)
+        oc = pair.orc.cull_counts(s32)
+        assert c["rays"] == oc["rays"], (t, c, oc)
+        diff = abs(c["sphere_tests"] - oc["sphere_tests"]) + abs(c["box_tests"] - oc["other_tests"])
+        assert diff <= oc["ambiguous"], (t, c, oc)
+        exact += diff == 0
+    assert exact >= 1
+    sim.close()
