@@ -127,7 +127,11 @@ typedef struct sim_config {
        (rad/s), and the standard deviation per sqrt(s) of their bias random
        walks; all >= 0 */
     float imu_noise[2], imu_walk[2];
-    int32_t reserved[1];     /* must be 0 */
+    int32_t cast_mode;       /* execution: 0 thread per ray (each lane sweeps the cull list for
+                                its rays); 1 warp per ray (the lanes split the list and a
+                                warp-level min-reduction picks the nearest hit; maps of spheres
+                                and boxes only, others cast thread per ray).  Same results bit
+                                for bit */
 } sim_config;
 
 /* Flight tasks. */

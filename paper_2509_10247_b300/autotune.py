@@ -1,9 +1,10 @@
 """Launch-shape autotuner of the render kernels.
 
-Every candidate launch configuration (rays per thread, warps per CTA,
-culling mode, hit tape on / off) computes the same values bit for bit: the
-ray order of the minimum and every arithmetic step are fixed, only the work
-split changes.  So a candidate is admitted only if its rollout outputs and
+Every candidate execution configuration (rays per thread, warps per CTA,
+culling mode, thread-per-ray or warp-per-ray casting, hit tape on / off,
+checkpoint interval of the adjoint) computes the same values bit for bit:
+the ray order of the minimum and every arithmetic step are fixed, only the
+work split changes.  So a candidate is admitted only if its rollout outputs and
 adjoint gradients are bitwise equal to those of the library's default
 configuration (the one the parity tests hold against the FP64 oracle); among
 the admitted ones the fastest reset + rollout + adjoint, timed in process with
@@ -18,7 +19,7 @@ import json
 import os
 import statistics
 
-EXEC_FIELDS = ("rays_per_thread", "warps_per_cta", "cull", "tape_hits")
+EXEC_FIELDS = ("rays_per_thread", "warps_per_cta", "cull", "tape_hits", "cast_mode", "ckpt_every")
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "diffsim_b300", "autotune.json")
 
 
@@ -43,13 +44,24 @@ def workload_key(p, inp):
 
 
 def candidates(p):
-    """Execution fields to try (rays per thread 0 lets the library choose)."""
+    """Render launch shapes to try (rays per thread 0 lets the library
+    choose): thread per ray over culling mode, warps per CTA and rays per
+    thread; warp per ray (the lanes split each cull list and a warp-level
+    min-reduction picks the nearest hit) on the frustum-culled lists."""
     out = []
     for cull in (1, 2):
         for nw in (4, 8):
             for rpt in (0, 1, 2, 3, 4, 5, 6, 8):
-                out.append(dict(rays_per_thread=rpt, warps_per_cta=nw, cull=cull, tape_hits=-1))
+                out.append(dict(rays_per_thread=rpt, warps_per_cta=nw, cull=cull, tape_hits=-1, cast_mode=0))
+    for rpt in (0, 4):
+        out.append(dict(rays_per_thread=rpt, warps_per_cta=8, cull=1, tape_hits=-1, cast_mode=1))
     return out
+
+
+def ckpt_candidates(p):
+    """Checkpoint intervals of the adjoint to try with the best render shape."""
+    T = p["horizon"]
+    return sorted({k for k in (1, 2, 4, 8, 16, T) if 1 <= k <= T})
 
 
 def load_cache(path=None):
@@ -137,11 +149,15 @@ def _equal(a, b):
     return bool(torch.equal(a, b))
 
 
-def tune(p, inp, device="cuda", cands=None, reps=3, path=None, force=False, runner=None, gpu_name=None):
+def tune(p, inp, device="cuda", cands=None, reps=3, path=None, force=False, runner=None, gpu_name=None,
+         ckpts=None):
     """Best execution fields for workload (p, inp) on this GPU, from the cache
-    unless `force`.  Returns the cache entry: {'exec', 'ms', 'default_ms',
-    'tried', 'admitted'}.  `runner(exec) -> (ms, outputs)` and `gpu_name`
-    replace the GPU measurement (host-logic tests)."""
+    unless `force`.  Two stages: the render shapes (`cands`, default
+    candidates(p)) at the workload's checkpoint interval, then the checkpoint
+    intervals (`ckpts`, default ckpt_candidates(p); [] skips the stage) with
+    the best shape.  Returns the cache entry: {'exec', 'ms', 'default_ms',
+    'tried', 'admitted', 'rejected'}.  `runner(exec) -> (ms, outputs)` and
+    `gpu_name` replace the GPU measurement (host-logic tests)."""
     if gpu_name is None:
         import torch
         gpu_name = torch.cuda.get_device_name(torch.device(device))
@@ -151,18 +167,30 @@ def tune(p, inp, device="cuda", cands=None, reps=3, path=None, force=False, runn
         if hit is not None:
             return hit
     run = runner or _Runner(p, inp, device, reps)
-    ref_ms, ref = run(dict(rays_per_thread=0, warps_per_cta=0, cull=-1, tape_hits=-1))
+    default = dict(rays_per_thread=0, warps_per_cta=0, cull=-1, tape_hits=-1, cast_mode=0,
+                   ckpt_every=p.get("ckpt_every", 16))
+    ref_ms, ref = run(default)
     if ref is None:
         raise RuntimeError("the default configuration failed on this workload")
     results = []
-    for ex in (cands or candidates(p)):
+
+    def trial(ex):
         ms, outs = run(ex)
         ok = outs is not None and len(outs) == len(ref) and all(_equal(a, b) for a, b in zip(outs, ref))
         results.append({"exec": ex, "ms": ms, "ok": ok})
+
+    for ex in (cands or candidates(p)):
+        trial(dict(ex, ckpt_every=ex.get("ckpt_every", default["ckpt_every"])))
     best = select(results)
-    entry = {"exec": best["exec"] if best else dict(rays_per_thread=0, warps_per_cta=0, cull=-1, tape_hits=-1),
+    base = dict(best["exec"]) if best else dict(default)
+    for k in (ckpt_candidates(p) if ckpts is None else ckpts):
+        if k != base["ckpt_every"]:
+            trial(dict(base, ckpt_every=k))
+    best = select(results)
+    entry = {"exec": best["exec"] if best else default,
              "ms": best["ms"] if best else ref_ms, "default_ms": ref_ms,
              "tried": len(results), "admitted": sum(r["ok"] for r in results),
-             "rejected": [r["exec"] for r in results if not r["ok"]]}
+             "rejected": [r["exec"] for r in results if not r["ok"]],
+             "results": [{"exec": r["exec"], "ms": r["ms"], "ok": r["ok"]} for r in results]}
     store_cache(key, entry, path)
     return entry

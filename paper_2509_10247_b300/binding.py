@@ -68,7 +68,7 @@ class SimConfig(C.Structure):
         ("terminate", _i), ("pool_size", _i),
         ("ckpt_every", _i), ("tape_hits", _i), ("cull", _i), ("warps_per_cta", _i),
         ("rays_per_thread", _i), ("ctas_per_sm", _i),
-        ("task", _i), ("imu_noise", _f * 2), ("imu_walk", _f * 2), ("reserved", _i * 1),
+        ("task", _i), ("imu_noise", _f * 2), ("imu_walk", _f * 2), ("cast_mode", _i),
     ]
 
 
@@ -172,6 +172,7 @@ def make_config(p, **ex):
     c.warps_per_cta = ex.get("warps_per_cta", 0)
     c.rays_per_thread = ex.get("rays_per_thread", 0)
     c.ctas_per_sm = ex.get("ctas_per_sm", 0)
+    c.cast_mode = ex.get("cast_mode", 0)
     c.task = TASKS[p.get("task", "reach")]
     for k in range(2):
         c.imu_noise[k] = p.get("imu_noise", (0.0, 0.0))[k]

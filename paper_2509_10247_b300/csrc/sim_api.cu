@@ -192,7 +192,7 @@ int validate(const sim_config* c) {
         if (!(c->imu_noise[i] >= 0.f) || !(c->imu_walk[i] >= 0.f) || !std::isfinite(c->imu_noise[i]) ||
             !std::isfinite(c->imu_walk[i]))
             return SIM_ERR_INVALID_ARG;
-    if (c->reserved[0] != 0) return SIM_ERR_INVALID_ARG;
+    if (c->cast_mode < 0 || c->cast_mode > 1) return SIM_ERR_INVALID_ARG;
     return SIM_OK;
 }
 
@@ -244,6 +244,7 @@ int grid_of(sim_handle* h, bool vjp, bool tape, const ds::Smem& sm, int* grid) {
     static int16_t tape_marker;  // selects the taped-adjoint kernel; never dereferenced here
     dummy.sen[0].tape = tape ? &tape_marker : nullptr;
     dummy.nc_max = h->nc_max;  // selects the kernels with cylinders and gates
+    dummy.cast_mode = h->cfg.cast_mode;
     dummy.ng_max = h->ng_max;
     CK(ds::render_call(vjp, false, h->rpt, dummy, 0, 32 * h->nw, sm.total, nullptr, &occ));
     if (occ < 1) return SIM_ERR_UNSUPPORTED;
@@ -402,6 +403,7 @@ Args base_args(const sim_handle* h) {
     for (int i = 0; i < 2; ++i) { a.c.imu_noise[i] = c.imu_noise[i]; a.c.imu_walk[i] = c.imu_walk[i]; }
     a.N = h->N; a.M = h->M; a.NM = h->NM; a.T = h->T; a.K = h->K; a.S = h->S;
     a.ns_max = h->ns_max; a.nb_max = h->nb_max; a.cull = h->cull_mode;
+    a.cast_mode = h->cfg.cast_mode;
     a.nc_max = h->nc_max; a.ng_max = h->ng_max;
     for (int s = 0; s < ds::MAX_SENSORS; ++s) {
         a.sen[s] = h->sen[s];

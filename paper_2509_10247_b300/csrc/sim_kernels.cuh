@@ -63,6 +63,7 @@ struct Args {
     Phys c;
     int N, M, NM, T, K, S;      // envs, agents/env, agents, steps, checkpoint interval, sensors
     int ns_max, nb_max, cull;
+    int cast_mode;              // 0 thread per ray, 1 warp per ray (spheres and boxes)
     int nc_max, ng_max;         // largest cylinder and gate counts of a map
     int render_only;            // forward: only render the current state (no dynamics)
     Sensor sen[MAX_SENSORS];

@@ -518,6 +518,50 @@ __device__ __forceinline__ void cast_list(const WList& L, const int4& meta, cons
     if (EXTRA && meta.w) cast_rest<RPT>(L, cap, meta.w & 0xffff, meta.w >> 16, false, dx, dy, dz, tb, bi);
 }
 
+// Warp per ray: the lanes split the (sub-)list and every ray of the chunk is
+// cast by the whole warp in turn, each lane testing its share of the
+// entries (spheres: slots lane, lane + 32, ...; then boxes) with the same
+// tests as cast_list, a warp-level min-reduction of (t, slot) picking the
+// nearest hit and, among equal distances, the lowest slot: the result of the
+// per-lane sweep in slot order, bit for bit.  The ray's direction and start
+// distance come from the lane that holds it, and its best goes back there.
+// Spheres and boxes only.
+template <int RPT>
+__device__ inline void cast_warp_per_ray(const WList& L, const int4& n, const LCap& cap, bool sub, const float* dx,
+                                         const float* dy, const float* dz, float* tb, int* bi) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) {
+        for (int l = 0; l < 32; ++l) {
+            const float rx = __shfl_sync(0xffffffffu, dx[r], l), ry = __shfl_sync(0xffffffffu, dy[r], l);
+            const float rz = __shfl_sync(0xffffffffu, dz[r], l), t0 = __shfl_sync(0xffffffffu, tb[r], l);
+            float best = t0;
+            int slot = -1;
+            for (int j = lane; j < n.x; j += 32) {
+                const int k = sub ? L.sub[j] : j;
+                const float4 e = L.sph[k];
+                const float v = fmaf(rx, e.x, fmaf(ry, e.y, fmaf(rz, e.z, e.w)));
+                if (v >= 0.f) {
+                    const float t = sphere_near_root(e, L.sx[k].x, v, rx, ry, rz);
+                    if (t < best) { best = t; slot = k; }
+                }
+            }
+            if (n.y > 0) {
+                const float ix = safe_rcp(rx), iy = safe_rcp(ry), iz = safe_rcp(rz);
+                for (int j = lane; j < n.y; j += 32) {
+                    const int k = sub ? L.sub[cap.ns + j] : j;
+                    box_test(L.box[2 * k], L.box[2 * k + 1], ix, iy, iz, cap.ns + k, best, slot);
+                }
+            }
+            warp_argmin(best, slot);
+            if (lane == l) {
+                tb[r] = best;
+                bi[r] = slot;
+            }
+        }
+    }
+}
+
 // Second-level cull for one chunk of rays whose body directions lie in the
 // cone (axis cone.xyz, cos = cone.w, sin = sn); aw = R axis in the world.  A
 // sphere (or the bounding sphere of a box, cylinder or gate) at oc with

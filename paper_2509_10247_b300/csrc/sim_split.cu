@@ -283,7 +283,7 @@ __global__ void __launch_bounds__(128) k_physics(const Args a) {
 // Rays of chunks [c0, c1) of one (step, agent, sensor) item against its
 // cull list L (meta: its counts): cast, count, write depth / range and the
 // hit tape.  One full warp.
-template <int RPT, bool EXTRA>
+template <int RPT, bool EXTRA, bool CASTW = false>
 __device__ __forceinline__ void render_chunks(const Args& a, const WList& L, const int4& meta, const LCap& cap,
                                               const Sensor& sen, const float* R, int c0, int c1, size_t base,
                                               unsigned long long* s_cnt) {
@@ -296,7 +296,11 @@ __device__ __forceinline__ void render_chunks(const Args& a, const WList& L, con
         for (int r = 0; r < RPT; ++r) bi[r] = -1;
         int4 nsub = make_int4(meta.x, meta.y, meta.w & 0xffff, meta.w >> 16);
         if (meta.z < 0) {
-            if (a.cull > 1 && sen.cone) {
+            if (CASTW) {
+                const bool sub = a.cull > 1 && sen.cone;
+                if (sub) nsub = chunk_slots<EXTRA>(L, meta, cap, sen, a.cull, ch, R);
+                cast_warp_per_ray<RPT>(L, nsub, cap, sub, dx, dy, dz, tb, bi);
+            } else if (a.cull > 1 && sen.cone) {
                 nsub = chunk_slots<EXTRA>(L, meta, cap, sen, a.cull, ch, R);
                 cast_sub<RPT, EXTRA>(L, nsub, cap, dx, dy, dz, tb, bi);
             } else {
@@ -330,7 +334,9 @@ __device__ __forceinline__ void render_chunks(const Args& a, const WList& L, con
     }
 }
 
-template <int RPT, bool EXTRA, bool COOP>
+// CASTW: warp per ray (cast_mode 1, maps of spheres and boxes), compiled apart
+// so that the thread-per-ray kernels keep their registers.
+template <int RPT, bool EXTRA, bool COOP, bool CASTW = false>
 __global__ void __launch_bounds__(256, 4) k_render(const Args a) {
     extern __shared__ __align__(16) unsigned char sm[];
     __shared__ int s_env, s_flag, s_item;
@@ -409,7 +415,7 @@ __global__ void __launch_bounds__(256, 4) k_render(const Args a) {
             } else {
                 meta = warp_build_list<EXTRA, true>(mv, o, R, sen, a.cull, L, cap);
             }
-            render_chunks<RPT, EXTRA>(a, Lv, meta, cap, sen, R, c0, c1, base, s_cnt);
+            render_chunks<RPT, EXTRA, CASTW>(a, Lv, meta, cap, sen, R, c0, c1, base, s_cnt);
             __syncwarp();
         }
         if (threadIdx.x == 0) s_cnt[3] += (unsigned long long)(a.T);
@@ -885,6 +891,9 @@ static cudaError_t render_rpt(bool vjp, bool launch, const Args& a, int grid, in
     if (vjp) return render_launch(k_render_vjp<RPT, false, EXTRA>, launch, a, grid, block, smem, st, occ);
     // shared lists for split items: compiled for the cone-culling default of
     // 4 rays per thread only (the other shapes keep one list per item)
+    if constexpr (!EXTRA) {  // warp per ray (one list per item)
+        if (a.cast_mode == 1) return render_launch(k_render<RPT, false, false, true>, launch, a, grid, block, smem, st, occ);
+    }
     if constexpr (RPT == 4) {
         const bool coop = a.rparts[0] + (a.S > 1 ? a.rparts[1] : 0) > a.S && a.T * a.M * a.S <= block / 32;
         if (coop && launch) return render_launch(k_render<RPT, EXTRA, true>, launch, a, grid, block, smem, st, occ);

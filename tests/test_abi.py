@@ -78,9 +78,9 @@ def test_create_rejects_bad_config(lib, field, value, code):
     assert rc == code and h is None
 
 
-def test_create_rejects_reserved_and_rigid_params(lib):
+def test_create_rejects_bad_cast_mode_and_rigid_params(lib):
     cfg = binding.make_config(synth.preset("pointmass_64env_depth16x9_10sph"))
-    cfg.reserved[0] = 1
+    cfg.cast_mode = 2
     assert _create_rc(lib, cfg)[0] == -1
     cfg = binding.make_config(synth.preset("pointmass_64env_depth16x9_10sph"))
     cfg.task = 2
