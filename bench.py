@@ -417,8 +417,12 @@ def run_ours(args, rank, world):
             "l2": "inputs larger than L2: %.1f GB depth written and %.1f GB depth cotangent read per step"
                   % (4e-9 * T * NM * Rc, 4e-9 * T * NM * Rc),
             "exec": exec_,
-            "autotune": None if tuned is None else {k: tuned[k] for k in ("tried", "admitted", "ms", "default_ms",
-                                                                          "seconds")},
+            "autotune": None if tuned is None else dict(
+                {k: tuned[k] for k in ("tried", "admitted", "ms", "default_ms", "seconds")},
+                best_thread_per_ray_ms=min([r["ms"] for r in tuned.get("results", [])
+                                            if r["ok"] and r["ms"] and not r["exec"].get("cast_mode")], default=None),
+                best_warp_per_ray_ms=min([r["ms"] for r in tuned.get("results", [])
+                                          if r["ok"] and r["ms"] and r["exec"].get("cast_mode") == 1], default=None)),
             "grays_per_s": grays, "agent_steps_per_s": value * p["n_agent"],
             "fwd_ms": fwd_ms, "bwd_ms": bwd_ms,
             "roofline": roofline, "roofline_render_vjp": roofline_vjp,

@@ -121,7 +121,8 @@ def test_autotune_admits_candidates_and_runs(tmp_path):
     cands = [dict(rays_per_thread=r, warps_per_cta=w, cull=c, tape_hits=-1)
              for r, w, c in ((1, 8, 1), (5, 8, 2), (3, 4, 1), (8, 4, 2))]
     e = autotune.tune(p, inp, cands=cands, path=str(tmp_path / "t.json"), reps=1)
-    assert e["tried"] == 4 and e["admitted"] == 4, e
+    # four render shapes, then the checkpoint intervals around the best one
+    assert e["tried"] >= 4 and e["admitted"] == e["tried"], e
     sim = Simulator(p, inp, **e["exec"])
     sim.reset(dev(inp["s0"]))
     sim.rollout(dev(inp["actions"]))

@@ -288,8 +288,9 @@ def test_steps_equal_rollout(pair):
 
 
 def test_launch_shape_variants_agree(pair):
-    """Rays per thread, warps per CTA and culling mode change only the work
-    split: outputs and adjoint gradients agree bit for bit."""
+    """Rays per thread, warps per CTA, culling mode and thread- or
+    warp-per-ray casting change only the work split: outputs and adjoint
+    gradients agree bit for bit."""
     p = pair.p
     if p["cam"] is None:
         pytest.skip("no camera")
@@ -299,7 +300,8 @@ def test_launch_shape_variants_agree(pair):
     g_l = dev(cot["g_lidar"]) if "g_lidar" in cot else None
     ref = None
     for ex in (dict(), dict(rays_per_thread=1), dict(rays_per_thread=3, warps_per_cta=4),
-               dict(rays_per_thread=8, cull=2), dict(rays_per_thread=2, cull=1, tape_hits=0)):
+               dict(rays_per_thread=8, cull=2), dict(rays_per_thread=2, cull=1, tape_hits=0),
+               dict(cast_mode=1), dict(cast_mode=1, cull=2, rays_per_thread=4), dict(cast_mode=1, cull=0)):
         s2 = Simulator(p, pair.inp, **ex)
         s2.reset(dev(pair.inp["s0"]))
         o2 = s2.rollout(pair.act)
