@@ -604,15 +604,20 @@ def run_closed_loop(args, rank, world):
                           "workload": CLOSED_LOOP_WORKLOAD, "act_ms": act_ms,
                           "backward_ms": e0.elapsed_time(e1) / reps, "reps": reps}))
         return
+    K = p.get("ckpt_every", 16)
+    torch.cuda.synchronize()
+    torch.cuda.reset_peak_memory_stats(dev)
+    base_mem = torch.cuda.memory_allocated(dev)
     clocks = Clocks(local)
     e0, e1 = ev(), ev()
     e0.record()
     for _ in range(args.steps):
-        L, g, rec = cl.gradient(s0, g_r)
+        L, g, rec = cl.gradient(s0, g_r, ckpt_every=K)
     e1.record()
     torch.cuda.synchronize()
     ck = clocks.stop()
     ms = e0.elapsed_time(e1) / args.steps
+    peak_gb = (torch.cuda.max_memory_allocated(dev) - base_mem) / 1e9
     if cl.sim.status() != 0 or cl.pol.status() != 0:
         raise RuntimeError("device status flagged in the closed loop")
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) \
@@ -622,8 +627,12 @@ def run_closed_loop(args, rank, world):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "dtype": "f32 simulator, bf16 policy (fp32 accumulate)", "data": "synthetic",
             "config": {"n_env": N, "horizon": T, "policy": "%d -> 256 -> 4" % F, "obstacles": 256,
-                       "backward_observations": "rebuilt from the forward's stored hit ids (%.0f GB)"
-                       % (cl.hits_bytes(T) / 1e9) if cl.stored_hits else "re-rendered"},
+                       "ckpt_every": K,
+                       "backward": "checkpoints (state, reset counters) every %d steps; each segment replayed "
+                                   "in the backward pass, its observations rebuilt from the replay's hit ids "
+                                   "(%.1f GB per segment)" % (K, cl.hits_bytes(K + 1) / 1e9)},
+            "peak_gb_per_gradient": peak_gb,
+            "simulator_workspace_gb": cl.sim.workspace_bytes() / 1e9,
             "loss": L, "grad_norm": float(np.linalg.norm(g)),
             "policy_act_ms": act_ms,
             "roofline": {"bound": "tensor", "achieved": gemm_flop / (act_ms / 1e3) / 1e12,

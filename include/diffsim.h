@@ -226,6 +226,13 @@ int sim_reset(sim_handle *h, const float *state0, sim_stream_t stream);
 int sim_get_state(const sim_handle *h, float *dst, sim_stream_t stream);
 int sim_set_state(sim_handle *h, const float *src, sim_stream_t stream);
 
+/* Copy the per-environment reset counters to / from a DEVICE int32 [N]: the
+ * k of the pool entry (k mod P) the environment takes at its next reset
+ * (Sec. IV-A resets; sim_reset zeroes them).  With sim_get/set_state they
+ * make a checkpoint from which steps replay bit for bit. */
+int sim_get_reset_counters(const sim_handle *h, int32_t *dst, sim_stream_t stream);
+int sim_set_reset_counters(sim_handle *h, const int32_t *src, sim_stream_t stream);
+
 /* Sensor outputs of the current state (the initial observation): depth
  * [NM][Rc] and lidar [NM][Rl], DEVICE, either NULL to skip. */
 int sim_render(sim_handle *h, float *depth, float *lidar, sim_stream_t stream);

@@ -39,7 +39,7 @@ SYMBOLS = ["sim_version", "sim_strerror", "sim_state_dim", "sim_action_dim", "si
            "sim_graph_create", "sim_graph_launch", "sim_graph_kernels", "sim_graph_destroy",
            "sim_set_scene_ex", "sim_get_gate_index", "sim_set_gate_index", "sim_rollout_ex",
            "sim_step_ex", "sim_backward_ex", "sim_render_taped", "sim_step_backward_taped", "sim_render_hits",
-           "sim_fp32_issue_rate", "sim_set_wait_limit"]
+           "sim_fp32_issue_rate", "sim_set_wait_limit", "sim_get_reset_counters", "sim_set_reset_counters"]
 
 # flight tasks (Sec. III-C)
 TASKS = {"reach": 0, "racing": 1}
@@ -291,6 +291,14 @@ def sim_set_state(h, src, stream=None):
     _ck(lib().sim_set_state(h, _ptr(src), _stream(stream)), "sim_set_state")
 
 
+def sim_get_reset_counters(h, dst, stream=None):
+    _ck(lib().sim_get_reset_counters(h, _ptr(dst), _stream(stream)), "sim_get_reset_counters")
+
+
+def sim_set_reset_counters(h, src, stream=None):
+    _ck(lib().sim_set_reset_counters(h, _ptr(src), _stream(stream)), "sim_set_reset_counters")
+
+
 def sim_render(h, depth=None, lidar=None, stream=None):
     _ck(lib().sim_render(h, _ptr(depth), _ptr(lidar), _stream(stream)), "sim_render")
 
@@ -495,6 +503,14 @@ class Simulator:
 
     def set_state(self, s):
         sim_set_state(self.h, s.contiguous())
+
+    def get_reset_counters(self):
+        out = self._empty(self.N, dtype=torch.int32)
+        sim_get_reset_counters(self.h, out)
+        return out
+
+    def set_reset_counters(self, k):
+        sim_set_reset_counters(self.h, k.to(device=self.device, dtype=torch.int32).contiguous())
 
     def render(self, hits=None):
         """Depth and LiDAR of the current state.  hits: None, or a pair of

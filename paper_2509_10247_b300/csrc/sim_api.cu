@@ -945,6 +945,21 @@ int sim_set_state(sim_handle* h, const float* src, sim_stream_t stream) {
     return SIM_OK;
 }
 
+int sim_get_reset_counters(const sim_handle* h, int32_t* dst, sim_stream_t stream) {
+    if (!h || !dst) return SIM_ERR_NULL_PTR;
+    CK(cudaMemcpyAsync(dst, h->d_pool_k, (size_t)h->N * sizeof(int), cudaMemcpyDeviceToDevice,
+                       (cudaStream_t)stream));
+    return SIM_OK;
+}
+
+int sim_set_reset_counters(sim_handle* h, const int32_t* src, sim_stream_t stream) {
+    if (!h || !src) return SIM_ERR_NULL_PTR;
+    CK(cudaMemcpyAsync(h->d_pool_k, src, (size_t)h->N * sizeof(int), cudaMemcpyDeviceToDevice,
+                       (cudaStream_t)stream));
+    h->have_rollout = false;
+    return SIM_OK;
+}
+
 int sim_render_taped(sim_handle* h, float* depth, float* lidar, int16_t* hits_cam, int16_t* hits_lidar,
                      sim_stream_t stream) {
     if (!h) return SIM_ERR_NULL_PTR;

@@ -102,21 +102,28 @@ class ClosedLoop:
     """A policy flying the simulator: at each step the policy maps the
     agents' states and rendered depth / LiDAR to actions, the simulator steps
     and renders the next observation.  gradient() returns the loss
-    L = sum_t <g_r[t], r_ctrl[t]> and dL/d(policy parameters) by
-    backpropagation through time: states are kept per step; going back, each
-    step's observation is re-rendered and the policy's forward re-run (both
+    L = sum_t <g_r[t], r_ctrl[t]> (reported; the gradient is driven by the
+    reward cotangent g_r alone) and dL/d(policy parameters) by
+    backpropagation through time (Eq. 5): going back, each step's
+    observation is rebuilt and the policy's forward re-run (both
     deterministic), then the simulator's step adjoint (sim_step_backward)
     gives the action cotangent, the policy's backward pass the parameter
     gradient and the observation cotangent, whose depth / LiDAR part feeds
     the previous step's adjoint and whose state part joins the state
     cotangent.  The last step's observation feeds no action, so its adjoint
-    has no ray term.  Rays are cast once per step: the forward pass records
-    every ray's hit primitive (2 bytes per ray and step, kept when it fits in
-    free device memory; store_hits forces either way), the backward pass
-    rebuilds each observation from its hits (sim_render_hits, bit for bit)
-    and the adjoint of step t - 1 gathers the hits of state t.  Without the
-    stored hits the backward pass re-renders state t, recording its hits
-    for that adjoint.  Rigid-body agents, one per environment."""
+    has no ray term.
+
+    Memory: with ckpt_every = K > 0 (the workload's, 16 for the closed-loop
+    configuration) the forward pass keeps only a checkpoint (state and reset
+    counters) every K steps; the backward pass replays each segment of K
+    steps from its checkpoint, recording its states, actions and every ray's
+    hit primitive (2 bytes per ray), and runs the segment's adjoint from
+    them: observations rebuilt from the hits (sim_render_hits, bit for bit)
+    and the step adjoints gathering them.  With K = 0 every state is kept
+    and the hits of all T steps too when they fit in free device memory
+    (store_hits forces either way; without them each observation is
+    re-rendered).  Both give the same gradient bit for bit.  Rigid-body
+    agents, one per environment."""
 
     def __init__(self, p, inp, device="cuda", **ex):
         assert p["model"] == "rigid" and p["n_agent"] == 1
@@ -125,14 +132,45 @@ class ClosedLoop:
         self.sim = Simulator(p, inp, device=self.device, **ex)
         self.pol = Policy.for_workload(p, device=self.device)
         self.targets = torch.as_tensor(inp["targets"], dtype=torch.float32, device=self.device)
+        self.stored_hits = False
 
     def hits_bytes(self, T=None):
         T = self.p["horizon"] if T is None else T
         return 2 * T * self.p["n_env"] * (self.sim.Rc + self.sim.Rl)
 
-    def gradient(self, s0, g_r, T=None, store_hits=None):
-        sim, pol, dev = self.sim, self.pol, self.device
+    def _tape(self, n):
+        N, Rc, Rl, dev = self.p["n_env"], self.sim.Rc, self.sim.Rl, self.device
+        tape = (torch.empty(n, N, Rc, dtype=torch.int16, device=dev) if Rc else None,
+                torch.empty(n, N, Rl, dtype=torch.int16, device=dev) if Rl else None)
+        return lambda t: tuple(None if x is None else x[t] for x in tape)
+
+    def gradient(self, s0, g_r, T=None, store_hits=None, ckpt_every=None):
         T = self.p["horizon"] if T is None else T
+        K = self.p.get("ckpt_every", 16) if ckpt_every is None else ckpt_every
+        if 0 < K < T:
+            return self._gradient_segments(s0, g_r, T, K)
+        return self._gradient_stored(s0, g_r, T, store_hits)
+
+    def _backward_step(self, t, state, action, done, g_s, g_r_t, g_obs, hits_next, hits_t, scratch, render_hits):
+        """Adjoint of step t and of the policy's action at state t; returns
+        (state cotangent at t, observation cotangent of state t)."""
+        sim, pol, dev = self.sim, self.pol, self.device
+        N, Rc, Rl = self.p["n_env"], sim.Rc, sim.Rl
+        g_dep, g_lid = g_obs
+        g_a, g_st = sim.step_backward(state, action, done, g_s, g_r_t, g_dep, g_lid, hits=hits_next)
+        sim.set_state(state)
+        if render_hits:
+            depth, lidar = sim.render_from_hits(hits_t)
+        else:
+            depth, lidar = sim.render(hits=hits_t)
+        pol.act(state, self.targets, depth, lidar, out=scratch)
+        g_dep = torch.empty(N, Rc, device=dev) if Rc else None
+        g_lid = torch.empty(N, Rl, device=dev) if Rl else None
+        pol.backward(g_a, g_st, g_dep, g_lid)
+        return g_st, (g_dep, g_lid)
+
+    def _gradient_stored(self, s0, g_r, T, store_hits):
+        sim, pol, dev = self.sim, self.pol, self.device
         N = self.p["n_env"]
         Rc, Rl = sim.Rc, sim.Rl
         if not (Rc or Rl):
@@ -140,10 +178,7 @@ class ClosedLoop:
         elif store_hits is None:
             store_hits = self.hits_bytes(T) + (24 << 30) < torch.cuda.mem_get_info(dev)[0]
         self.stored_hits = store_hits
-        if store_hits:
-            tape = (torch.empty(T, N, Rc, dtype=torch.int16, device=dev) if Rc else None,
-                    torch.empty(T, N, Rl, dtype=torch.int16, device=dev) if Rl else None)
-            hits_of = lambda t: tuple(None if x is None else x[t] for x in tape)
+        hits_of = self._tape(T) if store_hits else None
         states = torch.empty(T + 1, N, 13, device=dev)
         actions = torch.empty(T, N, 4, device=dev)
         done = torch.empty(T, N, dtype=torch.uint8, device=dev)
@@ -159,22 +194,65 @@ class ClosedLoop:
             states[t + 1] = sim.get_state()
         loss = float((g_r[:T] * r).sum())
         g_s = torch.zeros(N, 13, device=dev)
-        g_dep = g_lid = hits = None
+        g_obs, hits = (None, None), None
         hit_buf = sim.hit_buffers() if (Rc or Rl) and not store_hits else None
         scratch = torch.empty(N, 4, device=dev)
         pol.grads(reset=True)
         for t in range(T - 1, -1, -1):
-            g_a, g_st = sim.step_backward(states[t], actions[t], done[t], g_s, g_r[t], g_dep, g_lid, hits=hits)
-            sim.set_state(states[t])
-            if store_hits:
-                hits = hits_of(t)
-                depth, lidar = sim.render_from_hits(hits)
-            else:
-                depth, lidar = sim.render(hits=hit_buf)
-                hits = hit_buf
-            pol.act(states[t], self.targets, depth, lidar, out=scratch)
-            g_dep = torch.empty(N, Rc, device=dev) if Rc else None
-            g_lid = torch.empty(N, Rl, device=dev) if Rl else None
-            pol.backward(g_a, g_st, g_dep, g_lid)
-            g_s = g_st
+            h_t = hits_of(t) if store_hits else hit_buf
+            g_s, g_obs = self._backward_step(t, states[t], actions[t], done[t], g_s, g_r[t], g_obs, hits, h_t,
+                                             scratch, store_hits)
+            hits = h_t
         return loss, pol.grads(reset=True), dict(states=states, actions=actions, done=done, r_ctrl=r)
+
+    def _gradient_segments(self, s0, g_r, T, K):
+        sim, pol, dev = self.sim, self.pol, self.device
+        N = self.p["n_env"]
+        nseg = (T + K - 1) // K
+        self.stored_hits = False
+        ck_s = torch.empty(nseg, N, 13, device=dev)
+        ck_k = torch.empty(nseg, N, dtype=torch.int32, device=dev)
+        r = torch.empty(T, N, device=dev)
+        done_all = torch.empty(T, N, dtype=torch.uint8, device=dev)
+        act = torch.empty(N, 4, device=dev)
+        sim.reset(s0)
+        state = s0.contiguous()
+        depth, lidar = sim.render()
+        for t in range(T):
+            if t % K == 0:
+                ck_s[t // K] = state
+                ck_k[t // K] = sim.get_reset_counters()
+            pol.act(state, self.targets, depth, lidar, out=act)
+            o = sim.step(act)
+            r[t], done_all[t] = o["r_ctrl"], o["done"]
+            depth, lidar = o["depth"], o["lidar"]
+            state = sim.get_state()
+        loss = float((g_r[:T] * r).sum())
+        # the backward pass, segment by segment, from the last
+        states = torch.empty(K + 1, N, 13, device=dev)
+        actions = torch.empty(K, N, 4, device=dev)
+        done = torch.empty(K, N, dtype=torch.uint8, device=dev)
+        hits_of = self._tape(K + 1) if (sim.Rc or sim.Rl) else (lambda i: (None, None))
+        g_s = torch.zeros(N, 13, device=dev)
+        g_obs = (None, None)
+        scratch = torch.empty(N, 4, device=dev)
+        pol.grads(reset=True)
+        for seg in range(nseg - 1, -1, -1):
+            t0 = seg * K
+            n = min(T, t0 + K) - t0
+            sim.set_state(ck_s[seg])
+            sim.set_reset_counters(ck_k[seg])
+            states[0] = ck_s[seg]
+            depth, lidar = sim.render(hits=hits_of(0))
+            for i in range(n):
+                pol.act(states[i], self.targets, depth, lidar, out=actions[i])
+                o = sim.step(actions[i], hits=hits_of(i + 1))
+                done[i] = o["done"]
+                depth, lidar = o["depth"], o["lidar"]
+                states[i + 1] = sim.get_state()
+            for i in range(n - 1, -1, -1):
+                t = t0 + i
+                hits_next = hits_of(i + 1) if g_obs[0] is not None or g_obs[1] is not None else None
+                g_s, g_obs = self._backward_step(t, states[i], actions[i], done[i], g_s, g_r[t], g_obs, hits_next,
+                                                 hits_of(i), scratch, True)
+        return loss, pol.grads(reset=True), dict(r_ctrl=r, done=done_all, checkpoints=ck_s)

@@ -128,3 +128,23 @@ def test_closed_loop_full_width_observation():
     # kept hits (observations rebuilt from them) vs re-rendering: bit for bit
     L3, g3, _ = cl.gradient(dev(inp["s0"]), g_r, store_hits=not cl.stored_hits)
     assert L3 == L and np.array_equal(g, g3)
+
+
+def test_closed_loop_checkpointed_segments_match_stored_states():
+    """Checkpoints every K steps (state and reset counters) and the replay of
+    each segment in the backward pass give the stored-trajectory gradient bit
+    for bit, for K dividing T or not, with collisions that reset agents."""
+    p = _tiny(n_env=64, horizon=7, terminate=1, bound_lo=(-np.inf, -np.inf, 0.7),
+              bound_hi=(np.inf, np.inf, 1.3))
+    inp = synth.make_inputs(p, seed=21)
+    cl = ClosedLoop(p, inp)
+    cl.pol.set_params(synth.policy_init(p, seed=22))
+    g_r = dev(synth.cotangents(p, seed=23)["g_r"])
+    s0 = dev(inp["s0"])
+    L0, g0, rec0 = cl.gradient(s0, g_r, ckpt_every=0, store_hits=True)
+    assert int(rec0["done"].sum()) > 0  # resets happen inside segments
+    for K in (1, 2, 3, 4):
+        L, g, rec = cl.gradient(s0, g_r, ckpt_every=K)
+        assert L == L0 and np.array_equal(g, g0), K
+        assert torch.equal(rec["done"], rec0["done"])
+    assert cl.sim.status() == 0 and cl.pol.status() == 0
