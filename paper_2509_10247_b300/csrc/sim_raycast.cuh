@@ -794,8 +794,9 @@ __device__ __forceinline__ MapView map_view(const Args& a, int map, const float4
 // direction, folded into the rotation cotangent gR += g_d (x) d_B.  Zero for a
 // miss, a clamped output or an origin inside the primitive.  With the hit
 // point's outward normal n: dt/do = -n / (n.d), dt/dd = -t n / (n.d).
-// Quotients by the hardware approximation (a few ulp: the gradient's bar is
-// 1e-3 relative).
+// Quotients and the box's slab reciprocals by the hardware approximation (a
+// few ulp: the gradient's bar is 1e-3 relative; an entry face that a few ulp
+// could change is an edge entry, whose gradient is ambiguous anyway).
 template <bool EXTRA>
 __device__ __forceinline__ void ray_vjp(const MapView& mv, int id, const float* o, float dx, float dy, float dz,
                                         const float4& db, const Sensor& sen, float g, float* go, float* gR) {
@@ -824,7 +825,7 @@ __device__ __forceinline__ void ray_vjp(const MapView& mv, int id, const float* 
         float tl[3];
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            const float iv = safe_rcp(d[k]);
+            const float iv = __fdividef(1.f, fabsf(d[k]) < 1e-20f ? copysignf(1e-20f, d[k]) : d[k]);
             tl[k] = fmaf(-h[k], fabsf(iv), c[k] * iv);
         }
         // entry axis: the largest entry time, lowest axis on ties (selects,

@@ -481,7 +481,7 @@ cudaError_t launch_render_hits(const Args& a, int grid, cudaStream_t st) {
 // one fixed order that depends only on the set of hit rays: the taped and
 // the re-casting adjoints, which find the same hits, agree bit for bit.
 struct HitQueue {
-    uint32_t* key;  // [VQ_CAP] ray slot * 2 + sensor
+    int* slot;      // [VQ_CAP] ray slot in the sensor's table
     float* g;       // [VQ_CAP] output cotangent of the ray
     short* id;      // [VQ_CAP] primitive id
     int ns, nr;     // sphere entries from the front, other kinds from the back
@@ -490,8 +490,8 @@ struct HitQueue {
 
 __device__ __forceinline__ HitQueue hit_queue(unsigned char* sm, const Args& a, int warp) {
     HitQueue q;
-    q.key = reinterpret_cast<uint32_t*>(sm + a.sm.vq + (size_t)warp * VQ_BYTES);
-    q.g = reinterpret_cast<float*>(q.key + VQ_CAP);
+    q.slot = reinterpret_cast<int*>(sm + a.sm.vq + (size_t)warp * VQ_BYTES);
+    q.g = reinterpret_cast<float*>(q.slot + VQ_CAP);
     q.id = reinterpret_cast<short*>(q.g + VQ_CAP);
     q.ns = q.nr = q.nblk = 0;
     return q;
@@ -499,14 +499,14 @@ __device__ __forceinline__ HitQueue hit_queue(unsigned char* sm, const Args& a, 
 
 // Push the lane's ray of a block of 32 consecutive slots (valid: a hit with
 // a non-zero cotangent).  Every lane of the warp calls it.
-__device__ __forceinline__ void hq_push(HitQueue& q, bool valid, int ns, int si, int j, int id, float g) {
+__device__ __forceinline__ void hq_push(HitQueue& q, bool valid, int ns, int j, int id, float g) {
     const int lane = threadIdx.x & 31;
     const unsigned below = (1u << lane) - 1u;
     const bool hs = valid && id < ns, hr = valid && id >= ns;
     const unsigned bs = __ballot_sync(0xffffffffu, hs), br = __ballot_sync(0xffffffffu, hr);
     if (hs || hr) {
         const int p = hs ? q.ns + __popc(bs & below) : VQ_CAP - 1 - (q.nr + __popc(br & below));
-        q.key[p] = ((uint32_t)j << 1) | (uint32_t)si;
+        q.slot[p] = j;
         q.g[p] = g;
         q.id[p] = (short)id;
     }
@@ -515,25 +515,22 @@ __device__ __forceinline__ void hq_push(HitQueue& q, bool valid, int ns, int si,
     ++q.nblk;
 }
 
-// Ray VJPs of every queued entry, accumulated into the lane's go / gR.
+// Ray VJPs of every queued entry (all of sensor sen: a flush never spans
+// two sensors), accumulated into the lane's go / gR.
 template <bool EXTRA>
-__device__ __forceinline__ void hq_flush(HitQueue& q, const Args& a, const MapView& mv, const float* o,
+__device__ __forceinline__ void hq_flush(HitQueue& q, const Sensor& sen, const MapView& mv, const float* o,
                                          const float* R, float* go, float* gR) {
     const int lane = threadIdx.x & 31;
     __syncwarp();
     for (int k = lane; k < q.ns; k += 32) {
-        const uint32_t key = q.key[k];
-        const Sensor& sen = a.sen[key & 1u];
         float d[3];
-        const float4 db = ray_dir(sen, R, (int)(key >> 1), d);
+        const float4 db = ray_dir(sen, R, q.slot[k], d);
         ray_vjp<EXTRA>(mv, q.id[k], o, d[0], d[1], d[2], db, sen, q.g[k], go, gR);
     }
     for (int k = lane; k < q.nr; k += 32) {
         const int p = VQ_CAP - 1 - k;
-        const uint32_t key = q.key[p];
-        const Sensor& sen = a.sen[key & 1u];
         float d[3];
-        const float4 db = ray_dir(sen, R, (int)(key >> 1), d);
+        const float4 db = ray_dir(sen, R, q.slot[p], d);
         ray_vjp<EXTRA>(mv, q.id[p], o, d[0], d[1], d[2], db, sen, q.g[p], go, gR);
     }
     __syncwarp();
@@ -599,7 +596,8 @@ __global__ void __launch_bounds__(256, TAPE ? 4 : 3) k_render_vjp(const Args a) 
                     if (!sen.gout || (TAPE && !sen.tape)) continue;
                     const size_t base = ti * sen.R;
                     const int W32 = (sen.R + 31) / 32;
-                    const int j0 = 32 * (part * W32 / P), j1 = min(sen.R, 32 * ((part + 1) * W32 / P));
+                    const int j0 = P == 1 ? 0 : 32 * (part * W32 / P);
+                    const int j1 = P == 1 ? sen.R : min(sen.R, 32 * ((part + 1) * W32 / P));
                     if (j0 >= j1) continue;
                     if (TAPE) {
                         // taped hit ids: rounds of VQ_FLUSH blocks whose ids and
@@ -612,7 +610,7 @@ __global__ void __launch_bounds__(256, TAPE ? 4 : 3) k_render_vjp(const Args a) 
                                 const int j = b0 + 32 * u + lane;
                                 idv[u] = -1;
                                 gv[u] = 0.f;
-                                if (j < j1) {
+                                if (b0 + 32 * u < j1 && j < j1) {  // the first test is the warp's
                                     const int ray = out_index(sen, j);
                                     idv[u] = sen.tape[base + ray];
                                     gv[u] = sen.gout[base + ray];
@@ -622,10 +620,9 @@ __global__ void __launch_bounds__(256, TAPE ? 4 : 3) k_render_vjp(const Args a) 
                             for (int u = 0; u < VQ_FLUSH; ++u) {
                                 if (b0 + 32 * u >= j1) break;
                                 const int id = idv[u];
-                                hq_push(hq, id >= 0 && id < nprim && gv[u] != 0.f, mv.ns, si, b0 + 32 * u + lane, id,
-                                        gv[u]);
+                                hq_push(hq, id >= 0 && id < nprim && gv[u] != 0.f, mv.ns, b0 + 32 * u + lane, id, gv[u]);
                             }
-                            hq_flush<EXTRA>(hq, a, mv, o, R, go, gR);
+                            hq_flush<EXTRA>(hq, sen, mv, o, R, go, gR);
                         }
                         continue;
                     }
@@ -655,11 +652,11 @@ __global__ void __launch_bounds__(256, TAPE ? 4 : 3) k_render_vjp(const Args a) 
                             const bool hit = j < j1 && meta.z < 0 && bi[r] >= 0;
                             const int id = hit ? L.id[bi[r]] : -1;
                             const float g = hit ? sen.gout[base + out_index(sen, j)] : 0.f;
-                            hq_push(hq, hit && g != 0.f, mv.ns, si, j, id, g);
-                            if (hq.nblk == VQ_FLUSH) hq_flush<EXTRA>(hq, a, mv, o, R, go, gR);
+                            hq_push(hq, hit && g != 0.f, mv.ns, j, id, g);
+                            if (hq.nblk == VQ_FLUSH) hq_flush<EXTRA>(hq, sen, mv, o, R, go, gR);
                         }
                     }
-                    hq_flush<EXTRA>(hq, a, mv, o, R, go, gR);
+                    hq_flush<EXTRA>(hq, sen, mv, o, R, go, gR);
                     __syncwarp();
                 }
             }
