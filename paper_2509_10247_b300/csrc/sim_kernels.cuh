@@ -7,12 +7,13 @@ namespace ds {
 
 constexpr int MAX_SENSORS = 2;
 
-// Hit queue of one warp of the render adjoint: VQ_CAP entries of (ray slot,
-// sensor) word, output cotangent and primitive id; VQ_FLUSH blocks of 32
-// rays at most between flushes.
-constexpr int VQ_FLUSH = 8;
-constexpr int VQ_CAP = 32 * VQ_FLUSH;
-constexpr int VQ_BYTES = VQ_CAP * 10;
+// Hit queues of one warp of the render adjoint: two half-warp queues of
+// VQ_CAP entries (ray slot, output cotangent, primitive id); VQ_FLUSH blocks
+// of 16 rays at most between flushes.
+constexpr int VQ_FLUSH = 16;
+constexpr int VQ_CAP = 16 * VQ_FLUSH;
+constexpr int VQ_BYTES = 2 * VQ_CAP * 10;
+static_assert(VQ_FLUSH % 4 == 0, "the taped adjoint gathers rounds of 4 blocks between flushes");
 
 // Capacities of a cull list (the largest per-map counts of each kind).
 struct LCap {

@@ -471,15 +471,19 @@ cudaError_t launch_render_hits(const Args& a, int grid, cudaStream_t st) {
 }
 
 // ---------------------------------------------------------- render adjoint
-// Per-warp queue of the hit rays of one (step, agent, part) item.  Rays are
-// pushed in increasing slot order, 32 slots (a block) at a time (a ballot
-// per kind keeps the lane order); spheres fill the queue from the front, the
-// other kinds from the back.  The queue is flushed after every VQ_FLUSH
-// blocks of a sensor and at the end of each sensor; flushing hands entry q
-// of a kind to lane q mod 32, so the ray VJPs run on full warps without
-// divergence between primitive kinds, and each lane's partial sums follow
-// one fixed order that depends only on the set of hit rays: the taped and
-// the re-casting adjoints, which find the same hits, agree bit for bit.
+// The ray adjoint works in half warps: 16 virtual lanes per (step, agent,
+// part) item.  A taped adjoint warp holds two items, one per half; the
+// re-casting adjoint (which needs the whole warp to cull and cast) one item,
+// whose VJPs then run on the first half.  Per item, hit rays are queued in
+// increasing slot order, 16 slots (a block) at a time (a ballot per kind
+// keeps the lane order), spheres from the front of the half's queue and the
+// other kinds from the back; the queue is flushed after every VQ_FLUSH
+// blocks of a sensor and at the end of each sensor, entry q of a kind going
+// to virtual lane q mod 16, so the ray VJPs run on full half warps without
+// divergence between primitive kinds.  Each virtual lane's partial sums
+// follow one fixed order that depends only on the set of hit rays, and the
+// 16 lanes reduce in a fixed tree: the taped and the re-casting adjoints,
+// which find the same hits, agree bit for bit.
 struct HitQueue {
     int* slot;      // [VQ_CAP] ray slot in the sensor's table
     float* g;       // [VQ_CAP] output cotangent of the ray
@@ -488,23 +492,27 @@ struct HitQueue {
     int nblk;       // blocks pushed since the last flush
 };
 
-__device__ __forceinline__ HitQueue hit_queue(unsigned char* sm, const Args& a, int warp) {
+// Queue `h` (0 or 1) of the warp.
+__device__ __forceinline__ HitQueue hit_queue(unsigned char* sm, const Args& a, int warp, int h) {
     HitQueue q;
-    q.slot = reinterpret_cast<int*>(sm + a.sm.vq + (size_t)warp * VQ_BYTES);
+    unsigned char* base = sm + a.sm.vq + (size_t)warp * VQ_BYTES + (size_t)h * (VQ_CAP * 10);
+    q.slot = reinterpret_cast<int*>(base);
     q.g = reinterpret_cast<float*>(q.slot + VQ_CAP);
     q.id = reinterpret_cast<short*>(q.g + VQ_CAP);
     q.ns = q.nr = q.nblk = 0;
     return q;
 }
 
-// Push the lane's ray of a block of 32 consecutive slots (valid: a hit with
-// a non-zero cotangent).  Every lane of the warp calls it.
-__device__ __forceinline__ void hq_push(HitQueue& q, bool valid, int ns, int j, int id, float g) {
+// Push the rays of the 16-slot block held by half `src` (its lanes' valid:
+// a hit with a non-zero cotangent) into q.  Every lane of the warp calls it;
+// the lanes whose q is the pushed queue keep its counters.
+__device__ __forceinline__ void hq_push(HitQueue& q, int src, bool valid, int ns, int j, int id, float g) {
     const int lane = threadIdx.x & 31;
+    const unsigned hmask = 0xffffu << (16 * src);
     const unsigned below = (1u << lane) - 1u;
     const bool hs = valid && id < ns, hr = valid && id >= ns;
-    const unsigned bs = __ballot_sync(0xffffffffu, hs), br = __ballot_sync(0xffffffffu, hr);
-    if (hs || hr) {
+    const unsigned bs = __ballot_sync(0xffffffffu, hs) & hmask, br = __ballot_sync(0xffffffffu, hr) & hmask;
+    if ((lane >> 4) == src && (hs || hr)) {
         const int p = hs ? q.ns + __popc(bs & below) : VQ_CAP - 1 - (q.nr + __popc(br & below));
         q.slot[p] = j;
         q.g[p] = g;
@@ -515,54 +523,90 @@ __device__ __forceinline__ void hq_push(HitQueue& q, bool valid, int ns, int j, 
     ++q.nblk;
 }
 
-// Ray VJPs of every queued entry (all of sensor sen: a flush never spans
-// two sensors), accumulated into the lane's go / gR.
+// Ray VJPs of every entry of q (all of sensor sen: a flush never spans two
+// sensors) on the lanes with `active`, virtual lane lane & 15, accumulated
+// into the lane's go / gR; the lanes with `reset` empty their queue.  Every
+// lane of the warp calls it.
 template <bool EXTRA>
-__device__ __forceinline__ void hq_flush(HitQueue& q, const Sensor& sen, const MapView& mv, const float* o,
-                                         const float* R, float* go, float* gR) {
-    const int lane = threadIdx.x & 31;
+__device__ __forceinline__ void hq_flush(HitQueue& q, bool active, bool reset, const Sensor& sen,
+                                         const MapView& mv, const float* o, const float* R, float* go,
+                                         float* gR) {
+    const int vl = threadIdx.x & 15;
     __syncwarp();
-    for (int k = lane; k < q.ns; k += 32) {
-        float d[3];
-        const float4 db = ray_dir(sen, R, q.slot[k], d);
-        ray_vjp<EXTRA>(mv, q.id[k], o, d[0], d[1], d[2], db, sen, q.g[k], go, gR);
-    }
-    for (int k = lane; k < q.nr; k += 32) {
-        const int p = VQ_CAP - 1 - k;
-        float d[3];
-        const float4 db = ray_dir(sen, R, q.slot[p], d);
-        ray_vjp<EXTRA>(mv, q.id[p], o, d[0], d[1], d[2], db, sen, q.g[p], go, gR);
+    if (active) {
+        for (int k = vl; k < q.ns; k += 16) {
+            float d[3];
+            const float4 db = ray_dir(sen, R, q.slot[k], d);
+            ray_vjp<EXTRA>(mv, q.id[k], o, d[0], d[1], d[2], db, sen, q.g[k], go, gR);
+        }
+        for (int k = vl; k < q.nr; k += 16) {
+            const int p = VQ_CAP - 1 - k;
+            float d[3];
+            const float4 db = ray_dir(sen, R, q.slot[p], d);
+            ray_vjp<EXTRA>(mv, q.id[p], o, d[0], d[1], d[2], db, sen, q.g[p], go, gR);
+        }
     }
     __syncwarp();
-    q.ns = q.nr = q.nblk = 0;
+    if (reset) q.ns = q.nr = q.nblk = 0;
 }
 
-// One warp per (step, agent, part) item: the cotangents of all its rays
-// (every sensor) reduce, in a fixed order, to the pose cotangent
-// gposes[t][i] = (d/d origin [3], d/d R [9]).  Zero when the step terminated
-// (the state was replaced).  Hit ids come from the rollout's tape or are
-// re-cast; the hit rays are queued (HitQueue) and their VJPs run on full
-// warps.
+// Sum of 12 per-lane values over each half warp in a fixed tree (reduce-
+// scatter through shuffles of distance 8, 4, 2, 1): virtual lane v (lane &
+// 15) receives the half's total of value v (meaningful below 12).
+__device__ __forceinline__ float half_sum12(const float* v) {
+    const int vl = threadIdx.x & 15;
+    float a[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) a[k] = k < 12 ? v[k] : 0.f;
+#pragma unroll
+    for (int w = 8; w >= 1; w >>= 1) {
+        const bool hi = (vl & w) != 0;
+#pragma unroll
+        for (int k = 0; k < w; ++k) {
+            const float send = hi ? a[k] : a[k + w];
+            a[k] = (hi ? a[k + w] : a[k]) + __shfl_xor_sync(0xffffffffu, send, w);
+        }
+    }
+    return a[0];
+}
+
+// Slot range [j0, j1) of part `part` of P in a sensor of R rays: 32-slot
+// blocks split evenly among the parts (the same for every launch shape).
+__device__ __forceinline__ void part_range(int R, int part, int P, int& j0, int& j1) {
+    if (P == 1) {
+        j0 = 0;
+        j1 = R;
+        return;
+    }
+    const int W32 = (R + 31) / 32;
+    j0 = 32 * (part * W32 / P);
+    j1 = min(R, 32 * ((part + 1) * W32 / P));
+}
+
+// (step, agent, part) items reduce, in a fixed order, to the pose cotangent
+// gposes[t][i][part] = (d/d origin [3], d/d R [9]); zero when the step
+// terminated (the state was replaced).  TAPE: hit ids from the rollout's
+// tape, two items per warp (one per half); else re-cast, one item per warp.
 template <int RPT, bool TAPE, bool EXTRA>
 __global__ void __launch_bounds__(256, TAPE ? 4 : 3) k_render_vjp(const Args a) {
     extern __shared__ __align__(16) unsigned char sm[];
     __shared__ int s_env, s_flag, s_item;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, NW = blockDim.x >> 5;
+    const int half = lane >> 4, vl = lane & 15;
     const int M = a.M, S = a.S, NM = a.NM;
     const float4* prim = reinterpret_cast<const float4*>(sm + a.sm.prim);
     constexpr bool recast = !TAPE;
     const LCap cap = cap_of(a);
     WList L;
     if (recast) L = wlist_at(sm + a.sm.wlist + (size_t)warp * a.sm.wstride, cap);
-    HitQueue hq = hit_queue(sm, a, warp);
+    HitQueue hq = hit_queue(sm, a, warp, TAPE ? half : 0);
     if (threadIdx.x == 0) mbar_init(reinterpret_cast<uint64_t*>(sm + a.sm.mbar));
     __syncthreads();
     uint32_t phase = 0;
-    // items: (step, agent, part); part p takes the slots [32 w0, 32 w1) of
-    // every sensor, w0 = p W / P, w1 = (p + 1) W / P with W = ceil(R / 32)
-    // (the same slots for every rays-per-thread setting)
     const int P = a.parts;
     const int per_env = a.T * M * P;
+    const int per_warp = TAPE ? 2 : 1;                   // items per warp
+    const int tasks = (per_env + per_warp - 1) / per_warp;
     for (;;) {
         if (threadIdx.x == 0) {
             s_env = atomicAdd(a.work, 1);
@@ -577,15 +621,18 @@ __global__ void __launch_bounds__(256, TAPE ? 4 : 3) k_render_vjp(const Args a) 
         if (!stage_map(a, sm, map, mv, phase, &s_flag)) return;
         prep_boxes(sm, a, mv.ns, mv.nb);
         const int nprim = mv.count();
-        for (int it = warp; it < per_env; it = next_item(&s_item, lane)) {
-            const int tm = div_small(it, P), part = it - tm * P;
+        for (int task = warp; task < tasks; task = next_item(&s_item, lane)) {
+            const int it = TAPE ? 2 * task + half : task;  // this lane's item
+            const bool has = it < per_env;
+            const int itc = has ? it : per_env - 1;
+            const int tm = div_small(itc, P), part = itc - tm * P;
             const int t = div_small(tm, M), m = tm - t * M;
             const size_t ti = (size_t)t * NM + env * M + m;
-            const bool dn = a.done_rd[(size_t)t * NM + env * M] != 0;
+            const bool live = has && a.done_rd[(size_t)t * NM + env * M] == 0;
             float go[3] = {0.f, 0.f, 0.f}, gR[9];
 #pragma unroll
             for (int k = 0; k < 9; ++k) gR[k] = 0.f;
-            if (!dn) {
+            if (__any_sync(0xffffffffu, live)) {
                 float o[3], R[9];
 #pragma unroll
                 for (int k = 0; k < 3; ++k) o[k] = a.poses[ti * 12 + k];
@@ -595,37 +642,61 @@ __global__ void __launch_bounds__(256, TAPE ? 4 : 3) k_render_vjp(const Args a) 
                     const Sensor& sen = a.sen[si];
                     if (!sen.gout || (TAPE && !sen.tape)) continue;
                     const size_t base = ti * sen.R;
-                    const int W32 = (sen.R + 31) / 32;
-                    const int j0 = P == 1 ? 0 : 32 * (part * W32 / P);
-                    const int j1 = P == 1 ? sen.R : min(sen.R, 32 * ((part + 1) * W32 / P));
-                    if (j0 >= j1) continue;
+                    int j0, j1;
+                    part_range(sen.R, part, P, j0, j1);
+                    if (!live) j1 = j0;  // a terminated step or no item: no block
                     if (TAPE) {
-                        // taped hit ids: rounds of VQ_FLUSH blocks whose ids and
-                        // cotangents are loaded together (many loads in flight)
-                        for (int b0 = j0; b0 < j1; b0 += 32 * VQ_FLUSH) {
-                            int idv[VQ_FLUSH];
-                            float gv[VQ_FLUSH];
+                        // blocks of 16 slots per half, both halves in step, in
+                        // rounds of 4 whose hit ids and cotangents are loaded
+                        // together (more loads in flight; 8 spills); a half past
+                        // its range pushes nothing and counts no block.  Rounds
+                        // start at the sensor's first block and 4 divides
+                        // VQ_FLUSH, so the flush after every VQ_FLUSH blocks
+                        // falls at a round's end.
+                        const int nb = (j1 - j0 + 15) >> 4;
+                        const int nb_w = max(nb, __shfl_xor_sync(0xffffffffu, nb, 16));
+                        const unsigned hm = 0xffffu << (16 * half), below = (1u << lane) - 1u;
+                        for (int k0 = 0; k0 < nb_w; k0 += 4) {
+                            int idv[4];
+                            float gv[4];
 #pragma unroll
-                            for (int u = 0; u < VQ_FLUSH; ++u) {
-                                const int j = b0 + 32 * u + lane;
+                            for (int u = 0; u < 4; ++u) {
+                                const int j = j0 + 16 * (k0 + u) + vl;
                                 idv[u] = -1;
                                 gv[u] = 0.f;
-                                if (b0 + 32 * u < j1 && j < j1) {  // the first test is the warp's
+                                if (k0 + u < nb_w && j < j1) {  // the first test is the warp's
                                     const int ray = out_index(sen, j);
                                     idv[u] = sen.tape[base + ray];
                                     gv[u] = sen.gout[base + ray];
                                 }
                             }
 #pragma unroll
-                            for (int u = 0; u < VQ_FLUSH; ++u) {
-                                if (b0 + 32 * u >= j1) break;
-                                const int id = idv[u];
-                                hq_push(hq, id >= 0 && id < nprim && gv[u] != 0.f, mv.ns, b0 + 32 * u + lane, id, gv[u]);
+                            for (int u = 0; u < 4; ++u) {
+                                if (k0 + u >= nb_w) break;
+                                const int j = j0 + 16 * (k0 + u) + vl, id = idv[u];
+                                const bool v = j < j1 && id >= 0 && id < nprim && gv[u] != 0.f;
+                                const unsigned bs = __ballot_sync(0xffffffffu, v && id < mv.ns);
+                                const unsigned br = __ballot_sync(0xffffffffu, v && id >= mv.ns);
+                                if (v) {
+                                    const int p = id < mv.ns ? hq.ns + __popc(bs & hm & below)
+                                                             : VQ_CAP - 1 - (hq.nr + __popc(br & hm & below));
+                                    hq.slot[p] = j;
+                                    hq.g[p] = gv[u];
+                                    hq.id[p] = (short)id;
+                                }
+                                if (k0 + u < nb) {
+                                    hq.ns += __popc(bs & hm);
+                                    hq.nr += __popc(br & hm);
+                                    ++hq.nblk;
+                                }
                             }
-                            hq_flush<EXTRA>(hq, sen, mv, o, R, go, gR);
+                            const bool full = hq.nblk == VQ_FLUSH;
+                            if (__any_sync(0xffffffffu, full)) hq_flush<EXTRA>(hq, full, full, sen, mv, o, R, go, gR);
                         }
+                        hq_flush<EXTRA>(hq, true, true, sen, mv, o, R, go, gR);
                         continue;
                     }
+                    if (__all_sync(0xffffffffu, j0 >= j1)) continue;
                     const int4 meta = warp_build_list<EXTRA, true>(mv, o, R, sen, a.cull, L, cap);
                     const int chb = j0 / (32 * RPT), che = (j1 + 32 * RPT - 1) / (32 * RPT);
                     for (int ch = chb; ch < che; ++ch) {
@@ -642,8 +713,8 @@ __global__ void __launch_bounds__(256, TAPE ? 4 : 3) k_render_vjp(const Args a) 
                                 cast_list<RPT, EXTRA>(L, meta, cap, dx, dy, dz, tb, bi);
                             }
                         }
-                        // the blocks of the part's slots, in order; a flush
-                        // after every VQ_FLUSH of them, as in the taped gather
+                        // each 32-slot row: its two 16-slot blocks in order, as
+                        // the taped gather pushes them; VJPs on the first half
 #pragma unroll
                         for (int r = 0; r < RPT; ++r) {
                             const int jb = ch * 32 * RPT + r * 32, j = jb + lane;
@@ -652,11 +723,14 @@ __global__ void __launch_bounds__(256, TAPE ? 4 : 3) k_render_vjp(const Args a) 
                             const bool hit = j < j1 && meta.z < 0 && bi[r] >= 0;
                             const int id = hit ? L.id[bi[r]] : -1;
                             const float g = hit ? sen.gout[base + out_index(sen, j)] : 0.f;
-                            hq_push(hq, hit && g != 0.f, mv.ns, j, id, g);
-                            if (hq.nblk == VQ_FLUSH) hq_flush<EXTRA>(hq, sen, mv, o, R, go, gR);
+                            for (int src = 0; src < 2; ++src) {
+                                if (jb + 16 * src >= j1) break;
+                                hq_push(hq, src, hit && g != 0.f, mv.ns, j, id, g);
+                                if (hq.nblk == VQ_FLUSH) hq_flush<EXTRA>(hq, half == 0, true, sen, mv, o, R, go, gR);
+                            }
                         }
                     }
-                    hq_flush<EXTRA>(hq, sen, mv, o, R, go, gR);
+                    hq_flush<EXTRA>(hq, half == 0, true, sen, mv, o, R, go, gR);
                     __syncwarp();
                 }
             }
@@ -665,8 +739,8 @@ __global__ void __launch_bounds__(256, TAPE ? 4 : 3) k_render_vjp(const Args a) 
             for (int k = 0; k < 3; ++k) v12[k] = go[k];
 #pragma unroll
             for (int k = 0; k < 9; ++k) v12[3 + k] = gR[k];
-            const float tot = warp_sum12(v12);
-            if (!(lane & 1) && (lane >> 1) < 12) a.gposes[(ti * P + part) * 12 + (lane >> 1)] = tot;
+            const float tot = half_sum12(v12);
+            if (has && vl < 12 && (TAPE || half == 0)) a.gposes[(ti * P + part) * 12 + vl] = tot;
         }
         __syncthreads();
     }
