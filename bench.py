@@ -374,13 +374,13 @@ def run_ours(args, rank, world):
     peak = max(fma_s, ffma2_s) / 1e12
     sm_mhz = (ck or {}).get("sm_mhz") or 2032.0
     peak_derived = peak_fp32_tinst(props.multi_processor_count, sm_mhz)
-    traffic = None
+    traffic = traffic_vjp = None
     tfile = os.path.join(ROOT, "profiles", "traffic.txt")
     if os.path.exists(tfile):
         tj = dict(l.split(": ", 1) for l in open(tfile).read().splitlines() if ": " in l and not l.startswith("#"))
-        if tj.get("source_hash") == source_hash() and tj.get("workload") == p["name"] \
-                and "render_bytes_per_launch" in tj:
-            traffic = float(tj["render_bytes_per_launch"])
+        if tj.get("source_hash") == source_hash() and tj.get("workload") == p["name"]:
+            traffic = float(tj["render_bytes_per_launch"]) if "render_bytes_per_launch" in tj else None
+            traffic_vjp = float(tj["render_vjp_bytes_per_launch"]) if "render_vjp_bytes_per_launch" in tj else None
     per_kernel = {k: {"ms_per_launch": v[0] / max(v[1], 1), "launches": v[1]} for k, v in kt.items()}
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tinst/s",
                 "frac": achieved / peak, "traffic": traffic,
@@ -405,7 +405,7 @@ def run_ours(args, rank, world):
     parts = min(8, max(1, -(-8 // (T * p["n_agent"]))))
     vjp_b = render_vjp_bytes(NM, T, Rc + sim.Rl, parts)
     roofline_vjp = {"bound": "hbm", "achieved": vjp_b / (vjp_ms / 1e3) / 1e9, "peak": pk["hbm_gbs"],
-                    "unit": "GB/s", "frac": vjp_b / (vjp_ms / 1e3) / 1e9 / pk["hbm_gbs"], "traffic": None,
+                    "unit": "GB/s", "frac": vjp_b / (vjp_ms / 1e3) / 1e9 / pk["hbm_gbs"], "traffic": traffic_vjp,
                     "kernel": "k_render_vjp (taped ray adjoint of all T steps)", "kernel_ms": vjp_ms,
                     "bytes_per_launch": vjp_b, "peak_basis": pk_basis,
                     "work_basis": "per ray 2 B hit id + 4 B cotangent; per (step, agent) 48 B pose + 1 B done; "
