@@ -760,10 +760,14 @@ __global__ void __launch_bounds__(128, EXT ? 4 : 5) k_physics_bwd(const Args a) 
     const int M = a.M, D = a.c.D, A = a.c.A, NM = a.NM;
     const int Mp = pow2_ceil(M), E = phys_bwd_envs_per_warp(a.K, M);
     const int grp = lane / Mp, agent = lane - grp * Mp, gbase = grp * Mp;
-    const int env0 = (blockIdx.x * (blockDim.x >> 5) + wid) * E;
-    if (env0 >= a.N) return;
-    const bool live = grp < E && env0 + grp < a.N;
-    const int env = live ? env0 + grp : env0;  // idle groups read a valid environment, write nothing
+    // environments in the work order (grouped by map, as in the forward: a
+    // warp's groups scan maps of one size when the nearest obstacles are
+    // recomputed); checkpoints and tapes are indexed by environment
+    const int q0 = (blockIdx.x * (blockDim.x >> 5) + wid) * E;
+    if (q0 >= a.N) return;
+    const bool live = grp < E && q0 + grp < a.N;
+    const int qq = live ? q0 + grp : q0;
+    const int env = a.order ? a.order[qq] : qq;  // idle groups read a valid environment, write nothing
     float* seg = segm + ((size_t)wid * E + (grp < E ? grp : 0)) * (a.K + 1) * M * 16;
     const int map = a.env_map[env];
     const MapView mv = map_view(a, map, a.prims + a.map_off[map]);
