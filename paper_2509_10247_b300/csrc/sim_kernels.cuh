@@ -7,6 +7,12 @@ namespace ds {
 
 constexpr int MAX_SENSORS = 2;
 
+// A compile-time index (selects a sensor's body in the render kernels).
+template <int V>
+struct Idx {
+    static constexpr int value = V;
+};
+
 // Hit queues of one warp of the render adjoint: two half-warp queues of
 // VQ_CAP entries (ray slot, output cotangent, primitive id); VQ_FLUSH blocks
 // of 16 rays at most between flushes.
@@ -218,7 +224,7 @@ __device__ __forceinline__ bool cull_keep(const CullK& s, const float* R, const 
         const float hx = s.c0c2 * bx, vx = s.c1c3 * bx;
         const bool in = (fmaf(-s.c2, by, hx) >= -r) & (fmaf(s.c2, by, hx) >= -r) & (fmaf(-s.c3, bz, vx) >= -r) &
                         (fmaf(s.c3, bz, vx) >= -r);
-        return near | (!far & in);
+        return !far & in;  // |oc| <= r passes every plane through the origin
     }
     if (near) return true;
     if (far) return false;

@@ -103,9 +103,15 @@ __device__ __forceinline__ void box_rel(const float4& bl, const float4& bh, cons
     h[2] = 0.5f * (bh.z - bl.z);
 }
 
-// Correctly rounded reciprocal of a direction component kept away from 0.
+// Reciprocal of a direction component kept away from 0: the hardware
+// approximation (one MUFU operation, at most 1 ulp from the exact value;
+// |d| >= 1e-20 keeps operand and result normal, so flushing denormals
+// changes nothing).
 __device__ __forceinline__ float safe_rcp(float d) {
-    return __frcp_rn(fabsf(d) < 1e-20f ? copysignf(1e-20f, d) : d);
+    const float x = fabsf(d) < 1e-20f ? copysignf(1e-20f, d) : d;
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
 }
 
 // Origin-relative list entries of the four kinds (o: sensor origin).  The
@@ -180,12 +186,9 @@ __device__ inline int4 warp_build_list(const MapView& mv, const float* o, const 
     // contains the origin), so the inside test runs in pass 2.
     for (int base = 0; base < ns; base += 32) {
         const int k = base + lane;
-        bool keep = false;
-        if (k < ns) {
-            const float4 sp = prim[k];
-            const float oc[3] = {sp.x - o[0], sp.y - o[1], sp.z - o[2]};
-            keep = !cull || cull_keep(ck, R, oc, sp.w);
-        }
+        const float4 sp = prim[min(k, ns - 1)];
+        const float oc[3] = {sp.x - o[0], sp.y - o[1], sp.z - o[2]};
+        const bool keep = k < ns && (!cull || cull_keep(ck, R, oc, sp.w));
         const unsigned bal = __ballot_sync(0xffffffffu, keep);
         if (keep) L.id[cnt + __popc(bal & below)] = (short)k;
         cnt += __popc(bal);
@@ -202,21 +205,18 @@ __device__ inline int4 warp_build_list(const MapView& mv, const float* o, const 
     }
     cnt = 0;
     for (int base = 0; base < nb; base += 32) {
-        const int k = base + lane;
-        bool keep = false;
-        if (k < nb) {
-            const float4 bl = prim[ns + 2 * k];
-            float c[3], rho;
-            if (PREP) {  // staged as (centre, radius), (half extents, 0)
-                c[0] = bl.x - o[0]; c[1] = bl.y - o[1]; c[2] = bl.z - o[2];
-                rho = bl.w;
-            } else {
-                float h[3];
-                box_rel(bl, prim[ns + 2 * k + 1], o, c, h);
-                rho = sqrtf(dot3(h, h));
-            }
-            keep = !cull || cull_keep(ck, R, c, rho);
+        const int k = base + lane, kc = min(k, nb - 1);
+        const float4 bl = prim[ns + 2 * kc];
+        float c[3], rho;
+        if (PREP) {  // staged as (centre, radius), (half extents, 0)
+            c[0] = bl.x - o[0]; c[1] = bl.y - o[1]; c[2] = bl.z - o[2];
+            rho = bl.w;
+        } else {
+            float h[3];
+            box_rel(bl, prim[ns + 2 * kc + 1], o, c, h);
+            rho = sqrtf(dot3(h, h));
         }
+        const bool keep = k < nb && (!cull || cull_keep(ck, R, c, rho));
         const unsigned bal = __ballot_sync(0xffffffffu, keep);
         if (keep) L.id[cap.ns + cnt + __popc(bal & below)] = (short)(ns + k);
         cnt += __popc(bal);
@@ -305,7 +305,14 @@ __device__ __forceinline__ void box_test(const float4& c, const float4& h, float
     const float mx = c.x * ix, my = c.y * iy, mz = c.z * iz;
     const float tn = max3f(fmaf(-h.x, fabsf(ix), mx), fmaf(-h.y, fabsf(iy), my), fmaf(-h.z, fabsf(iz), mz));
     const float tf = min3f(fmaf(h.x, fabsf(ix), mx), fmaf(h.y, fabsf(iy), my), fmaf(h.z, fabsf(iz), mz));
-    if (tn <= tf && __float_as_uint(tn) < __float_as_uint(tb)) { tb = tn; bi = slot; }
+    // predicated moves: the update costs two issue slots and no branch
+    asm("{\n\t.reg .pred p, q;\n\t"
+        "setp.le.f32 p, %2, %3;\n\t"
+        "setp.lt.and.u32 q, %4, %5, p;\n\t"
+        "@q mov.b32 %0, %2;\n\t"
+        "@q mov.b32 %1, %6;\n\t}"
+        : "+f"(tb), "+r"(bi)
+        : "f"(tn), "f"(tf), "r"(__float_as_uint(tn)), "r"(__float_as_uint(tb)), "r"(slot));
 }
 
 // Vertical capped cylinder (list entry c0 = axis centre - o and bounding

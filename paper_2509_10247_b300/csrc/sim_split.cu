@@ -288,6 +288,8 @@ __device__ __forceinline__ void render_chunks(const Args& a, const WList& L, con
                                               const Sensor& sen, const float* R, int c0, int c1, size_t base,
                                               unsigned long long* s_cnt) {
     const int lane = threadIdx.x & 31;
+    float* const outp = sen.out ? sen.out + base : nullptr;
+    int16_t* const tapep = sen.tape ? sen.tape + base : nullptr;
     for (int ch = c0; ch < c1; ++ch) {
         float dx[RPT], dy[RPT], dz[RPT], tb[RPT];
         int bi[RPT];
@@ -328,8 +330,8 @@ __device__ __forceinline__ void render_chunks(const Args& a, const WList& L, con
                 v = fminf(sen.kind == 0 ? tb[r] * __ldg(&sen.dir[j].w) : tb[r], sen.range);
                 id = L.id[bi[r]];
             }
-            if (sen.out) sen.out[base + ray] = v;
-            if (sen.tape) sen.tape[base + ray] = (int16_t)id;
+            if (outp) outp[ray] = v;
+            if (tapep) tapep[ray] = (int16_t)id;
         }
     }
 }
@@ -397,25 +399,31 @@ __global__ void __launch_bounds__(256, 4) k_render(const Args a) {
             const int t = div_small(tm, M), m = tm - t * M;
             const int si = r < P0 ? 0 : 1, part = si ? r - P0 : r, np = si ? P1 : P0, nchs = si ? nch1 : nch0;
             const int c0 = div_small(part * nchs, np), c1 = div_small((part + 1) * nchs, np);
-            const Sensor& sen = a.sen[si];
-            if (!sen.out && !sen.tape) continue;
-            const size_t ti = (size_t)t * NM + env * M + m;
-            float o[3], R[9];
+            // one body per sensor index, known at compile time: the sensor's
+            // fields are then kernel-parameter operands
+            auto item = [&](auto sic) {
+                const Sensor& sen = a.sen[decltype(sic)::value];
+                if (!sen.out && !sen.tape) return;
+                const size_t ti = (size_t)t * NM + env * M + m;
+                float o[3], R[9];
 #pragma unroll
-            for (int k = 0; k < 3; ++k) o[k] = a.poses[ti * 12 + k];
+                for (int k = 0; k < 3; ++k) o[k] = a.poses[ti * 12 + k];
 #pragma unroll
-            for (int k = 0; k < 9; ++k) R[k] = a.poses[ti * 12 + 3 + k];
-            const size_t base = ti * sen.R;
-            int4 meta;
-            WList Lv = L;
-            if (coop) {  // the item's list, built by warp (tm * S + si) in this environment's first phase
-                Lv = wlist_at(sm + a.sm.wlist + (size_t)(tm * S + si) * a.sm.wstride, cap);
-                Lv.sub = L.sub;
-                meta = *Lv.meta;
-            } else {
-                meta = warp_build_list<EXTRA, true>(mv, o, R, sen, a.cull, L, cap);
-            }
-            render_chunks<RPT, EXTRA, CASTW>(a, Lv, meta, cap, sen, R, c0, c1, base, s_cnt);
+                for (int k = 0; k < 9; ++k) R[k] = a.poses[ti * 12 + 3 + k];
+                const size_t base = ti * sen.R;
+                int4 meta;
+                WList Lv = L;
+                if (coop) {  // the item's list, built by warp (tm * S + si) in this environment's first phase
+                    Lv = wlist_at(sm + a.sm.wlist + (size_t)(tm * S + si) * a.sm.wstride, cap);
+                    Lv.sub = L.sub;
+                    meta = *Lv.meta;
+                } else {
+                    meta = warp_build_list<EXTRA, true>(mv, o, R, sen, a.cull, L, cap);
+                }
+                render_chunks<RPT, EXTRA, CASTW>(a, Lv, meta, cap, sen, R, c0, c1, base, s_cnt);
+            };
+            if (si == 0) item(Idx<0>{});
+            else item(Idx<1>{});
             __syncwarp();
         }
         if (threadIdx.x == 0) s_cnt[3] += (unsigned long long)(a.T);
@@ -638,9 +646,11 @@ __global__ void __launch_bounds__(256, TAPE ? 4 : 3) k_render_vjp(const Args a) 
                 for (int k = 0; k < 3; ++k) o[k] = a.poses[ti * 12 + k];
 #pragma unroll
                 for (int k = 0; k < 9; ++k) R[k] = a.poses[ti * 12 + 3 + k];
-                for (int si = 0; si < S; ++si) {
-                    const Sensor& sen = a.sen[si];
-                    if (!sen.gout || (TAPE && !sen.tape)) continue;
+                // one body per sensor index, known at compile time: the
+                // sensor's fields are then kernel-parameter operands
+                auto sensor = [&](auto sic) {
+                    const Sensor& sen = a.sen[decltype(sic)::value];
+                    if (!sen.gout || (TAPE && !sen.tape)) return;
                     const size_t base = ti * sen.R;
                     int j0, j1;
                     part_range(sen.R, part, P, j0, j1);
@@ -648,14 +658,16 @@ __global__ void __launch_bounds__(256, TAPE ? 4 : 3) k_render_vjp(const Args a) 
                     if (TAPE) {
                         // blocks of 16 slots per half, both halves in step, in
                         // rounds of 4 whose hit ids and cotangents are loaded
-                        // together (more loads in flight; 8 spills); a half past
-                        // its range pushes nothing and counts no block.  Rounds
-                        // start at the sensor's first block and 4 divides
-                        // VQ_FLUSH, so the flush after every VQ_FLUSH blocks
-                        // falls at a round's end.
+                        // together; a half past its range pushes nothing.  The
+                        // queue is flushed after every VQ_FLUSH blocks of the
+                        // half's range (4 divides VQ_FLUSH, so at a round's
+                        // end) and at the sensor's end, as the re-casting
+                        // adjoint flushes.
                         const int nb = (j1 - j0 + 15) >> 4;
                         const int nb_w = max(nb, __shfl_xor_sync(0xffffffffu, nb, 16));
-                        const unsigned hm = 0xffffu << (16 * half), below = (1u << lane) - 1u;
+                        const unsigned hm = 0xffffu << (16 * half), bl = ((1u << lane) - 1u) & hm;
+                        const int16_t* const tp = sen.tape + base;
+                        const float* const gp = sen.gout + base;
                         for (int k0 = 0; k0 < nb_w; k0 += 4) {
                             int idv[4];
                             float gv[4];
@@ -664,39 +676,35 @@ __global__ void __launch_bounds__(256, TAPE ? 4 : 3) k_render_vjp(const Args a) 
                                 const int j = j0 + 16 * (k0 + u) + vl;
                                 idv[u] = -1;
                                 gv[u] = 0.f;
-                                if (k0 + u < nb_w && j < j1) {  // the first test is the warp's
+                                if (j < j1) {
                                     const int ray = out_index(sen, j);
-                                    idv[u] = sen.tape[base + ray];
-                                    gv[u] = sen.gout[base + ray];
+                                    idv[u] = tp[ray];
+                                    gv[u] = gp[ray];
                                 }
                             }
 #pragma unroll
                             for (int u = 0; u < 4; ++u) {
-                                if (k0 + u >= nb_w) break;
-                                const int j = j0 + 16 * (k0 + u) + vl, id = idv[u];
-                                const bool v = j < j1 && id >= 0 && id < nprim && gv[u] != 0.f;
-                                const unsigned bs = __ballot_sync(0xffffffffu, v && id < mv.ns);
-                                const unsigned br = __ballot_sync(0xffffffffu, v && id >= mv.ns);
+                                if (k0 + u >= nb_w) break;  // the same on every lane
+                                const int id = idv[u];
+                                const bool v = (unsigned)id < (unsigned)nprim && gv[u] != 0.f, sph = id < mv.ns;
+                                const unsigned bv = __ballot_sync(0xffffffffu, v);
+                                const unsigned bs = __ballot_sync(0xffffffffu, v && sph), br = bv & ~bs;
                                 if (v) {
-                                    const int p = id < mv.ns ? hq.ns + __popc(bs & hm & below)
-                                                             : VQ_CAP - 1 - (hq.nr + __popc(br & hm & below));
-                                    hq.slot[p] = j;
+                                    const int p = sph ? hq.ns + __popc(bs & bl) : VQ_CAP - 1 - (hq.nr + __popc(br & bl));
+                                    hq.slot[p] = j0 + 16 * (k0 + u) + vl;
                                     hq.g[p] = gv[u];
                                     hq.id[p] = (short)id;
                                 }
-                                if (k0 + u < nb) {
-                                    hq.ns += __popc(bs & hm);
-                                    hq.nr += __popc(br & hm);
-                                    ++hq.nblk;
-                                }
+                                hq.ns += __popc(bs & hm);
+                                hq.nr += __popc(br & hm);
                             }
-                            const bool full = hq.nblk == VQ_FLUSH;
+                            const bool full = k0 + 4 <= nb && (k0 + 4) % VQ_FLUSH == 0;
                             if (__any_sync(0xffffffffu, full)) hq_flush<EXTRA>(hq, full, full, sen, mv, o, R, go, gR);
                         }
                         hq_flush<EXTRA>(hq, true, true, sen, mv, o, R, go, gR);
-                        continue;
+                        return;
                     }
-                    if (__all_sync(0xffffffffu, j0 >= j1)) continue;
+                    if (__all_sync(0xffffffffu, j0 >= j1)) return;
                     const int4 meta = warp_build_list<EXTRA, true>(mv, o, R, sen, a.cull, L, cap);
                     const int chb = j0 / (32 * RPT), che = (j1 + 32 * RPT - 1) / (32 * RPT);
                     for (int ch = chb; ch < che; ++ch) {
@@ -732,7 +740,9 @@ __global__ void __launch_bounds__(256, TAPE ? 4 : 3) k_render_vjp(const Args a) 
                     }
                     hq_flush<EXTRA>(hq, half == 0, true, sen, mv, o, R, go, gR);
                     __syncwarp();
-                }
+                };
+                sensor(Idx<0>{});
+                if (S > 1) sensor(Idx<1>{});
             }
             float v12[12];
 #pragma unroll
