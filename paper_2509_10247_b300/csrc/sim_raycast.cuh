@@ -804,50 +804,87 @@ __device__ __forceinline__ MapView map_view(const Args& a, int map, const float4
 // Quotients and the box's slab reciprocals by the hardware approximation (a
 // few ulp: the gradient's bar is 1e-3 relative; an entry face that a few ulp
 // could change is an edge entry, whose gradient is ambiguous anyway).
+
+// The part shared by every kind: hit distance t, outward normal n.
+__device__ __forceinline__ void ray_vjp_tail(float t, const float* n, const float* d, const float4& db,
+                                             const Sensor& sen, float g, float* go, float* gR) {
+    const float fac = sen.kind == 0 ? db.w : 1.f;
+    if (t * fac >= sen.range) return;
+    const float nd = dot3(n, d);
+    const float gt = __fdividef(g * fac, nd);
+    const float db3[3] = {db.x, db.y, db.z};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        go[k] -= gt * n[k];
+        const float gdk = -gt * t * n[k];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) gR[3 * k + j] += gdk * db3[j];
+    }
+}
+
+// Sphere id of the map (the caller has checked the id and g != 0).
+__device__ __forceinline__ void ray_vjp_sphere(const MapView& mv, int id, const float* o, const float* d,
+                                               const float4& db, const Sensor& sen, float g, float* go, float* gR) {
+    const float4 s = mv.prim[id];
+    const float oc[3] = {s.x - o[0], s.y - o[1], s.z - o[2]};
+    const float r2 = s.w * s.w;
+    const float C = dot3(oc, oc) - r2;
+    if (C <= 0.f) return;
+    const float b = dot3(d, oc);
+    const float f[3] = {fmaf(-b, d[0], oc[0]), fmaf(-b, d[1], oc[1]), fmaf(-b, d[2], oc[2])};
+    const float d2 = fmaxf(r2 - dot3(f, f), 0.f);
+    const float t = __fdividef(C, b + sqrt_approx(d2));
+    const float ir = __fdividef(1.f, s.w);
+    float n[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) n[k] = (t * d[k] - oc[k]) * ir;
+    ray_vjp_tail(t, n, d, db, sen, g, go, gR);
+}
+
+// Box b of the map, staged as (centre, radius), (half extents, 0) (the
+// caller has checked the id and g != 0).
+__device__ __forceinline__ void ray_vjp_box(const MapView& mv, int b, const float* o, const float* d,
+                                            const float4& db, const Sensor& sen, float g, float* go, float* gR) {
+    const float4 bc = mv.prim[mv.ns + 2 * b], bh = mv.prim[mv.ns + 2 * b + 1];
+    const float c[3] = {bc.x - o[0], bc.y - o[1], bc.z - o[2]}, h[3] = {bh.x, bh.y, bh.z};
+    float tl[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float iv = __fdividef(1.f, fabsf(d[k]) < 1e-20f ? copysignf(1e-20f, d[k]) : d[k]);
+        tl[k] = fmaf(-h[k], fabsf(iv), c[k] * iv);
+    }
+    // entry axis: the largest entry time, lowest axis on ties (selects, no
+    // runtime-indexed arrays)
+    const bool x1 = tl[1] > tl[0];
+    const float t01 = x1 ? tl[1] : tl[0];
+    const bool x2 = tl[2] > t01;
+    const float t = x2 ? tl[2] : t01;
+    if (!(t > 0.f)) return;
+    const int ax = x2 ? 2 : (x1 ? 1 : 0);
+    float n[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) n[k] = k == ax ? (d[k] > 0.f ? -1.f : 1.f) : 0.f;
+    ray_vjp_tail(t, n, d, db, sen, g, go, gR);
+}
+
+// Any kind, by primitive id (spheres, boxes, then cylinders and gates).
 template <bool EXTRA>
 __device__ __forceinline__ void ray_vjp(const MapView& mv, int id, const float* o, float dx, float dy, float dz,
                                         const float4& db, const Sensor& sen, float g, float* go, float* gR) {
     if (id < 0 || id >= mv.count() || g == 0.f) return;  // miss (or an id foreign to the map)
-    const float4* prim = mv.prim;
     const int ns = mv.ns;
     const float d[3] = {dx, dy, dz};
-    float t, n[3];
     if (id < ns) {
-        const float4 s = prim[id];
-        const float oc[3] = {s.x - o[0], s.y - o[1], s.z - o[2]};
-        const float r2 = s.w * s.w;
-        const float C = dot3(oc, oc) - r2;
-        if (C <= 0.f) return;
-        const float b = dot3(d, oc);
-        const float f[3] = {fmaf(-b, d[0], oc[0]), fmaf(-b, d[1], oc[1]), fmaf(-b, d[2], oc[2])};
-        const float d2 = fmaxf(r2 - dot3(f, f), 0.f);
-        t = __fdividef(C, b + sqrt_approx(d2));
-        const float ir = __fdividef(1.f, s.w);
-#pragma unroll
-        for (int k = 0; k < 3; ++k) n[k] = (t * d[k] - oc[k]) * ir;
-    } else if (id < ns + mv.nb) {
-        const int b = id - ns;
-        const float4 bc = prim[ns + 2 * b], bh = prim[ns + 2 * b + 1];  // staged (centre, radius), (half, 0)
-        const float c[3] = {bc.x - o[0], bc.y - o[1], bc.z - o[2]}, h[3] = {bh.x, bh.y, bh.z};
-        float tl[3];
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            const float iv = __fdividef(1.f, fabsf(d[k]) < 1e-20f ? copysignf(1e-20f, d[k]) : d[k]);
-            tl[k] = fmaf(-h[k], fabsf(iv), c[k] * iv);
-        }
-        // entry axis: the largest entry time, lowest axis on ties (selects,
-        // no runtime-indexed arrays)
-        const bool x1 = tl[1] > tl[0];
-        const float t01 = x1 ? tl[1] : tl[0];
-        const bool x2 = tl[2] > t01;
-        t = x2 ? tl[2] : t01;
-        if (!(t > 0.f)) return;
-        const int ax = x2 ? 2 : (x1 ? 1 : 0);
-#pragma unroll
-        for (int k = 0; k < 3; ++k) n[k] = k == ax ? (d[k] > 0.f ? -1.f : 1.f) : 0.f;
-    } else if (!EXTRA) {
+        ray_vjp_sphere(mv, id, o, d, db, sen, g, go, gR);
         return;
-    } else if (id < ns + mv.nb + mv.nc) {
+    }
+    if (id < ns + mv.nb) {
+        ray_vjp_box(mv, id - ns, o, d, db, sen, g, go, gR);
+        return;
+    }
+    if (!EXTRA) return;
+    float t, n[3];
+    if (id < ns + mv.nb + mv.nc) {
         const float4 a0 = mv.cyl(id - ns - mv.nb)[0], a1 = mv.cyl(id - ns - mv.nb)[1];
         const float hz = 0.5f * (a1.y - a1.x);
         const float4 c0 = make_float4(a0.x - o[0], a0.y - o[1], 0.5f * (a1.x + a1.y) - o[2], 0.f);
@@ -891,18 +928,7 @@ __device__ __forceinline__ void ray_vjp(const MapView& mv, int id, const float* 
         n[1] = k == 0 ? sg * a1.y : (k == 1 ? sg * a1.x : 0.f);
         n[2] = k == 2 ? sg : 0.f;
     }
-    const float fac = sen.kind == 0 ? db.w : 1.f;
-    if (t * fac >= sen.range) return;
-    const float nd = dot3(n, d);
-    const float gt = __fdividef(g * fac, nd);
-    const float db3[3] = {db.x, db.y, db.z};
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        go[k] -= gt * n[k];
-        const float gdk = -gt * t * n[k];
-#pragma unroll
-        for (int j = 0; j < 3; ++j) gR[3 * k + j] += gdk * db3[j];
-    }
+    ray_vjp_tail(t, n, d, db, sen, g, go, gR);
 }
 
 }  // namespace ds

@@ -542,16 +542,19 @@ __device__ __forceinline__ void hq_flush(HitQueue& q, bool active, bool reset, c
     const int vl = threadIdx.x & 15;
     __syncwarp();
     if (active) {
+        // queued ids are in range and their cotangents non-zero: the kind of
+        // each part of the queue is known, no dispatch on the id
         for (int k = vl; k < q.ns; k += 16) {
             float d[3];
             const float4 db = ray_dir(sen, R, q.slot[k], d);
-            ray_vjp<EXTRA>(mv, q.id[k], o, d[0], d[1], d[2], db, sen, q.g[k], go, gR);
+            ray_vjp_sphere(mv, q.id[k], o, d, db, sen, q.g[k], go, gR);
         }
         for (int k = vl; k < q.nr; k += 16) {
             const int p = VQ_CAP - 1 - k;
             float d[3];
             const float4 db = ray_dir(sen, R, q.slot[p], d);
-            ray_vjp<EXTRA>(mv, q.id[p], o, d[0], d[1], d[2], db, sen, q.g[p], go, gR);
+            if (EXTRA) ray_vjp<EXTRA>(mv, q.id[p], o, d[0], d[1], d[2], db, sen, q.g[p], go, gR);
+            else ray_vjp_box(mv, q.id[p] - mv.ns, o, d, db, sen, q.g[p], go, gR);
         }
     }
     __syncwarp();
