@@ -179,30 +179,30 @@ __device__ inline int4 warp_build_list(const MapView& mv, const float* o, const 
     const CullK ck = cull_consts(sen);
     int inside = INT_MAX, cnt = 0;
     const unsigned below = (1u << lane) - 1u;
-    // Two passes per kind.  Pass 1 tests every primitive's bounding sphere
-    // against the field of view and appends the kept ids in index order;
-    // pass 2 builds the origin-relative entries of the kept ones only.  A
-    // primitive containing the origin is always kept (its bounding sphere
-    // contains the origin), so the inside test runs in pass 2.
+    // One pass per kind: every primitive's bounding sphere is tested against
+    // the field of view, and the kept ones get their origin-relative entry
+    // at their place in index order (ballot compaction).  A primitive that
+    // contains the origin is always kept (its bounding sphere contains the
+    // origin and so meets every side plane through it), so the inside test
+    // runs on kept primitives only.
     for (int base = 0; base < ns; base += 32) {
         const int k = base + lane;
         const float4 sp = prim[min(k, ns - 1)];
         const float oc[3] = {sp.x - o[0], sp.y - o[1], sp.z - o[2]};
         const bool keep = k < ns && (!cull || cull_keep(ck, R, oc, sp.w));
         const unsigned bal = __ballot_sync(0xffffffffu, keep);
-        if (keep) L.id[cnt + __popc(bal & below)] = (short)k;
+        if (keep) {
+            const int j = cnt + __popc(bal & below);
+            float4 e;
+            float2 x;
+            if (sphere_list_entry(sp, o, e, x)) inside = min(inside, k);
+            L.sph[j] = e;
+            L.sx[j] = x;
+            L.id[j] = (short)k;
+        }
         cnt += __popc(bal);
     }
     const int nsk = cnt;
-    __syncwarp();
-    for (int j = lane; j < nsk; j += 32) {
-        const int k = L.id[j];
-        float4 e;
-        float2 x;
-        if (sphere_list_entry(prim[k], o, e, x)) inside = min(inside, k);
-        L.sph[j] = e;
-        L.sx[j] = x;
-    }
     cnt = 0;
     for (int base = 0; base < nb; base += 32) {
         const int k = base + lane, kc = min(k, nb - 1);
@@ -218,35 +218,32 @@ __device__ inline int4 warp_build_list(const MapView& mv, const float* o, const 
         }
         const bool keep = k < nb && (!cull || cull_keep(ck, R, c, rho));
         const unsigned bal = __ballot_sync(0xffffffffu, keep);
-        if (keep) L.id[cap.ns + cnt + __popc(bal & below)] = (short)(ns + k);
+        if (keep) {
+            const int j = cnt + __popc(bal & below);
+            const float4 bh = prim[ns + 2 * k + 1];
+            float h[3];
+            if (PREP) {
+                h[0] = bh.x; h[1] = bh.y; h[2] = bh.z;
+                if (fabsf(c[0]) <= h[0] && fabsf(c[1]) <= h[1] && fabsf(c[2]) <= h[2]) inside = min(inside, ns + k);
+            } else {
+                if (bl.x <= o[0] && bh.x >= o[0] && bl.y <= o[1] && bh.y >= o[1] && bl.z <= o[2] && bh.z >= o[2])
+                    inside = min(inside, ns + k);
+                float cc[3];
+                box_rel(bl, bh, o, cc, h);
+            }
+            // the bounding tangent serves only the chunk cones (cull > 1)
+            float tw = -1e30f;
+            if (cull > 1) {
+                const float cb = dot3(c, c) - rho * rho;
+                if (cb > 0.f) tw = sqrtf(cb);
+            }
+            L.box[2 * j] = make_float4(c[0], c[1], c[2], tw);
+            L.box[2 * j + 1] = make_float4(h[0], h[1], h[2], rho);
+            L.id[cap.ns + j] = (short)(ns + k);
+        }
         cnt += __popc(bal);
     }
     const int nbk = cnt;
-    __syncwarp();
-    for (int j = lane; j < nbk; j += 32) {
-        const int k = L.id[cap.ns + j] - ns;
-        const float4 bl = prim[ns + 2 * k], bh = prim[ns + 2 * k + 1];
-        float c[3], h[3], rho;
-        if (PREP) {
-            c[0] = bl.x - o[0]; c[1] = bl.y - o[1]; c[2] = bl.z - o[2];
-            h[0] = bh.x; h[1] = bh.y; h[2] = bh.z;
-            rho = bl.w;
-            if (fabsf(c[0]) <= h[0] && fabsf(c[1]) <= h[1] && fabsf(c[2]) <= h[2]) inside = min(inside, ns + k);
-        } else {
-            if (bl.x <= o[0] && bh.x >= o[0] && bl.y <= o[1] && bh.y >= o[1] && bl.z <= o[2] && bh.z >= o[2])
-                inside = min(inside, ns + k);
-            box_rel(bl, bh, o, c, h);
-            rho = sqrtf(dot3(h, h));
-        }
-        // the bounding tangent serves only the chunk cones (cull > 1)
-        float tw = -1e30f;
-        if (cull > 1) {
-            const float cb = dot3(c, c) - rho * rho;
-            if (cb > 0.f) tw = sqrtf(cb);
-        }
-        L.box[2 * j] = make_float4(c[0], c[1], c[2], tw);
-        L.box[2 * j + 1] = make_float4(h[0], h[1], h[2], rho);
-    }
     int nck = 0, ngk = 0;
     for (int base = 0; EXTRA && base < mv.nc; base += 32) {
         const int k = base + lane;
