@@ -374,6 +374,13 @@ int sim_set_wait_limit(sim_handle *h, int32_t polls);
  * last stream.  reset != 0 zeroes the counters after reading. */
 int sim_counters(sim_handle *h, uint64_t *out, int32_t reset);
 
+/* Whether the forward kernels of h count their work (on != 0, the default)
+ * into the counters that sim_counters reads; with 0 they skip the counting
+ * atomics (a few shared-memory atomics per 32 x rays-per-thread ray slots),
+ * for timing runs that take the counts from a separate counted pass.  Takes
+ * effect at the next launch; SIM_ERR_NULL_PTR for a null handle. */
+int sim_set_counting(sim_handle *h, int32_t on);
+
 /* sim_fp32_issue_rate: measures this GPU's FP32 multiply-add rate, the
  * denominator of the ray cast's roofline (the paper has no counterpart: a
  * measurement utility).  Runs a grid of 8 CTAs of 256 threads per SM, each

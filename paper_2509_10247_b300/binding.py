@@ -35,7 +35,7 @@ SYMBOLS = ["sim_version", "sim_strerror", "sim_state_dim", "sim_action_dim", "si
            "sim_destroy", "sim_workspace_bytes", "sim_set_scene", "sim_set_pool",
            "sim_set_env_params", "sim_reset", "sim_get_state", "sim_set_state", "sim_render",
            "sim_step", "sim_rollout", "sim_backward", "sim_step_backward", "sim_last_status",
-           "sim_launch_info", "sim_counters", "sim_step_static", "sim_profile", "sim_kernel_times",
+           "sim_launch_info", "sim_counters", "sim_set_counting", "sim_step_static", "sim_profile", "sim_kernel_times",
            "sim_graph_create", "sim_graph_launch", "sim_graph_kernels", "sim_graph_destroy",
            "sim_set_scene_ex", "sim_get_gate_index", "sim_set_gate_index", "sim_rollout_ex",
            "sim_step_ex", "sim_backward_ex", "sim_render_taped", "sim_step_backward_taped", "sim_render_hits",
@@ -353,6 +353,10 @@ def sim_set_wait_limit(h, polls):
     _ck(lib().sim_set_wait_limit(h, _i(polls)), "sim_set_wait_limit")
 
 
+def sim_set_counting(h, on=True):
+    _ck(lib().sim_set_counting(h, _i(1 if on else 0)), "sim_set_counting")
+
+
 def sim_counters(h, reset=True):
     v = (C.c_uint64 * 4)()
     _ck(lib().sim_counters(h, v, _i(1 if reset else 0)), "sim_counters")
@@ -615,6 +619,10 @@ class Simulator:
 
     def counters(self, reset=True):
         return sim_counters(self.h, reset)
+
+    def set_counting(self, on=True):
+        """Whether the forward kernels count their work (default on)."""
+        sim_set_counting(self.h, on)
 
     def workspace_bytes(self):
         return sim_workspace_bytes(self.h)

@@ -80,6 +80,7 @@ struct sim_handle {
     // items per environment for 8 warps (a function of T and M only)
     int parts_roll = 1, parts_one = 1;
     int wait_polls = 0;  // sim_set_wait_limit
+    int counting = 1;    // sim_set_counting
     ds::Smem sm_r{}, sm_rv{}, sm_rvs{}, sm_rvt{};
     // kernel launches per kind; while profiling, one CUDA event pair per launch
     bool profiling = false, capturing = false, ev_overflow = false;
@@ -424,7 +425,7 @@ Args base_args(const sim_handle* h) {
     a.state = h->d_state; a.pool_k = h->d_pool_k;
     a.work = h->d_work; a.status = h->d_status;
     a.wait_polls = h->wait_polls;
-    a.counters = h->d_counters;
+    a.counters = h->counting ? h->d_counters : nullptr;
     a.parts = h->parts_roll;
     return a;
 }
@@ -1168,6 +1169,12 @@ int sim_set_wait_limit(sim_handle* h, int32_t polls) {
     if (!h) return SIM_ERR_NULL_PTR;
     if (polls < 0) return SIM_ERR_INVALID_ARG;
     h->wait_polls = polls;
+    return SIM_OK;
+}
+
+int sim_set_counting(sim_handle* h, int32_t on) {
+    if (!h) return SIM_ERR_NULL_PTR;
+    h->counting = on != 0;
     return SIM_OK;
 }
 

@@ -701,6 +701,16 @@ __device__ __forceinline__ void item_rays(const Sensor& sen, const float* R, int
     }
 }
 
+// Pose (origin, rotation) of a 12-float record: three 16-byte loads (the
+// pose arrays are 16-byte aligned and records 48 bytes apart).
+__device__ __forceinline__ void load_pose(const float* p, float* o, float* R) {
+    const float4* q = reinterpret_cast<const float4*>(p);
+    const float4 a = __ldg(q), b = __ldg(q + 1), c = __ldg(q + 2);
+    o[0] = a.x; o[1] = a.y; o[2] = a.z;
+    R[0] = a.w; R[1] = b.x; R[2] = b.y; R[3] = b.z; R[4] = b.w;
+    R[5] = c.x; R[6] = c.y; R[7] = c.z; R[8] = c.w;
+}
+
 // World direction of table slot j.
 __device__ __forceinline__ float4 ray_dir(const Sensor& sen, const float* R, int j, float* d) {
     const float4 db = __ldg(sen.dir + j);

@@ -385,20 +385,18 @@ __global__ void __launch_bounds__(256, 4) k_render(const Args a) {
                 if (sen.out || sen.tape) {
                     const size_t ti = (size_t)t * NM + env * M + m;
                     float o[3], R[9];
-#pragma unroll
-                    for (int k = 0; k < 3; ++k) o[k] = a.poses[ti * 12 + k];
-#pragma unroll
-                    for (int k = 0; k < 9; ++k) R[k] = a.poses[ti * 12 + 3 + k];
+                    load_pose(a.poses + ti * 12, o, R);
                     warp_build_list<EXTRA, true>(mv, o, R, sen, a.cull, L, cap);
                 }
             }
             __syncthreads();
         }
+        const int lgM = (M & (M - 1)) == 0 ? __ffs(M) - 1 : -1;  // M a power of two: shifts
         for (int it = warp; it < per_env; it = next_item(&s_item, lane)) {
-            const int tm = div_small(it, per_tm), r = it - tm * per_tm;
-            const int t = div_small(tm, M), m = tm - t * M;
+            const int tm = per_tm == 1 ? it : div_small(it, per_tm), r = it - tm * per_tm;
+            const int t = lgM >= 0 ? tm >> lgM : div_small(tm, M), m = tm - t * M;
             const int si = r < P0 ? 0 : 1, part = si ? r - P0 : r, np = si ? P1 : P0, nchs = si ? nch1 : nch0;
-            const int c0 = div_small(part * nchs, np), c1 = div_small((part + 1) * nchs, np);
+            const int c0 = np == 1 ? 0 : div_small(part * nchs, np), c1 = np == 1 ? nchs : div_small((part + 1) * nchs, np);
             // one body per sensor index, known at compile time: the sensor's
             // fields are then kernel-parameter operands
             auto item = [&](auto sic) {
@@ -406,10 +404,7 @@ __global__ void __launch_bounds__(256, 4) k_render(const Args a) {
                 if (!sen.out && !sen.tape) return;
                 const size_t ti = (size_t)t * NM + env * M + m;
                 float o[3], R[9];
-#pragma unroll
-                for (int k = 0; k < 3; ++k) o[k] = a.poses[ti * 12 + k];
-#pragma unroll
-                for (int k = 0; k < 9; ++k) R[k] = a.poses[ti * 12 + 3 + k];
+                load_pose(a.poses + ti * 12, o, R);
                 const size_t base = ti * sen.R;
                 int4 meta;
                 WList Lv = L;
@@ -645,10 +640,7 @@ __global__ void __launch_bounds__(256, TAPE ? 4 : 3) k_render_vjp(const Args a) 
             for (int k = 0; k < 9; ++k) gR[k] = 0.f;
             if (__any_sync(0xffffffffu, live)) {
                 float o[3], R[9];
-#pragma unroll
-                for (int k = 0; k < 3; ++k) o[k] = a.poses[ti * 12 + k];
-#pragma unroll
-                for (int k = 0; k < 9; ++k) R[k] = a.poses[ti * 12 + 3 + k];
+                load_pose(a.poses + ti * 12, o, R);
                 // one body per sensor index, known at compile time: the
                 // sensor's fields are then kernel-parameter operands
                 auto sensor = [&](auto sic) {
