@@ -13,12 +13,14 @@ struct Idx {
     static constexpr int value = V;
 };
 
-// Hit queues of one warp of the render adjoint: two half-warp queues of
-// VQ_CAP entries (ray slot, output cotangent, primitive id); VQ_FLUSH blocks
-// of 16 rays at most between flushes.
+// Hit queues of one warp of the render adjoint: one per group of VL lanes
+// (an item each), VQ_CAP entries (ray slot, output cotangent, primitive id);
+// VQ_FLUSH blocks of VL rays at most between flushes.
+constexpr int VL = 8;
+constexpr int VQ_PER_WARP = 32 / VL;
 constexpr int VQ_FLUSH = 16;
-constexpr int VQ_CAP = 16 * VQ_FLUSH;
-constexpr int VQ_BYTES = 2 * VQ_CAP * 10;
+constexpr int VQ_CAP = VL * VQ_FLUSH;
+constexpr int VQ_BYTES = VQ_PER_WARP * VQ_CAP * 10;
 static_assert(VQ_FLUSH % 4 == 0, "the taped adjoint gathers rounds of 4 blocks between flushes");
 
 // Capacities of a cull list (the largest per-map counts of each kind).

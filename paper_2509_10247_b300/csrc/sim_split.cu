@@ -474,19 +474,19 @@ cudaError_t launch_render_hits(const Args& a, int grid, cudaStream_t st) {
 }
 
 // ---------------------------------------------------------- render adjoint
-// The ray adjoint works in half warps: 16 virtual lanes per (step, agent,
-// part) item.  A taped adjoint warp holds two items, one per half; the
-// re-casting adjoint (which needs the whole warp to cull and cast) one item,
-// whose VJPs then run on the first half.  Per item, hit rays are queued in
-// increasing slot order, 16 slots (a block) at a time (a ballot per kind
-// keeps the lane order), spheres from the front of the half's queue and the
-// other kinds from the back; the queue is flushed after every VQ_FLUSH
-// blocks of a sensor and at the end of each sensor, entry q of a kind going
-// to virtual lane q mod 16, so the ray VJPs run on full half warps without
-// divergence between primitive kinds.  Each virtual lane's partial sums
-// follow one fixed order that depends only on the set of hit rays, and the
-// 16 lanes reduce in a fixed tree: the taped and the re-casting adjoints,
-// which find the same hits, agree bit for bit.
+// The ray adjoint works in groups of VL = 8 virtual lanes per (step, agent,
+// part) item.  A taped adjoint warp holds four items, one per lane group;
+// the re-casting adjoint (which needs the whole warp to cull and cast) one
+// item, whose VJPs then run on the first group.  Per item, hit rays are
+// queued in increasing slot order, VL slots (a block) at a time (a ballot
+// per kind keeps the lane order), spheres from the front of the group's
+// queue and the other kinds from the back; the queue is flushed after every
+// VQ_FLUSH blocks of a sensor and at the end of each sensor, entry q of a
+// kind going to virtual lane q mod VL, so the ray VJPs run on full groups
+// without divergence between primitive kinds.  Each virtual lane's partial
+// sums follow one fixed order that depends only on the set of hit rays, and
+// the VL lanes reduce in a fixed tree: the taped and the re-casting
+// adjoints, which find the same hits, agree bit for bit.
 struct HitQueue {
     int* slot;      // [VQ_CAP] ray slot in the sensor's table
     float* g;       // [VQ_CAP] output cotangent of the ray
@@ -495,7 +495,7 @@ struct HitQueue {
     int nblk;       // blocks pushed since the last flush
 };
 
-// Queue `h` (0 or 1) of the warp.
+// Queue `h` (0 .. VQ_PER_WARP - 1) of the warp.
 __device__ __forceinline__ HitQueue hit_queue(unsigned char* sm, const Args& a, int warp, int h) {
     HitQueue q;
     unsigned char* base = sm + a.sm.vq + (size_t)warp * VQ_BYTES + (size_t)h * (VQ_CAP * 10);
@@ -506,16 +506,16 @@ __device__ __forceinline__ HitQueue hit_queue(unsigned char* sm, const Args& a, 
     return q;
 }
 
-// Push the rays of the 16-slot block held by half `src` (its lanes' valid:
-// a hit with a non-zero cotangent) into q.  Every lane of the warp calls it;
-// the lanes whose q is the pushed queue keep its counters.
+// Push the rays of the VL-slot block held by lane group `src` (its lanes'
+// valid: a hit with a non-zero cotangent) into q.  Every lane of the warp
+// calls it; the lanes whose q is the pushed queue keep its counters.
 __device__ __forceinline__ void hq_push(HitQueue& q, int src, bool valid, int ns, int j, int id, float g) {
     const int lane = threadIdx.x & 31;
-    const unsigned hmask = 0xffffu << (16 * src);
+    const unsigned gmask = ((1u << VL) - 1u) << (VL * src);
     const unsigned below = (1u << lane) - 1u;
     const bool hs = valid && id < ns, hr = valid && id >= ns;
-    const unsigned bs = __ballot_sync(0xffffffffu, hs) & hmask, br = __ballot_sync(0xffffffffu, hr) & hmask;
-    if ((lane >> 4) == src && (hs || hr)) {
+    const unsigned bs = __ballot_sync(0xffffffffu, hs) & gmask, br = __ballot_sync(0xffffffffu, hr) & gmask;
+    if (lane / VL == src && (hs || hr)) {
         const int p = hs ? q.ns + __popc(bs & below) : VQ_CAP - 1 - (q.nr + __popc(br & below));
         q.slot[p] = j;
         q.g[p] = g;
@@ -527,24 +527,24 @@ __device__ __forceinline__ void hq_push(HitQueue& q, int src, bool valid, int ns
 }
 
 // Ray VJPs of every entry of q (all of sensor sen: a flush never spans two
-// sensors) on the lanes with `active`, virtual lane lane & 15, accumulated
+// sensors) on the lanes with `active`, virtual lane lane % VL, accumulated
 // into the lane's go / gR; the lanes with `reset` empty their queue.  Every
 // lane of the warp calls it.
 template <bool EXTRA>
 __device__ __forceinline__ void hq_flush(HitQueue& q, bool active, bool reset, const Sensor& sen,
                                          const MapView& mv, const float* o, const float* R, float* go,
                                          float* gR) {
-    const int vl = threadIdx.x & 15;
+    const int vl = threadIdx.x % VL;
     __syncwarp();
     if (active) {
         // queued ids are in range and their cotangents non-zero: the kind of
         // each part of the queue is known, no dispatch on the id
-        for (int k = vl; k < q.ns; k += 16) {
+        for (int k = vl; k < q.ns; k += VL) {
             float d[3];
             const float4 db = ray_dir(sen, R, q.slot[k], d);
             ray_vjp_sphere(mv, q.id[k], o, d, db, sen, q.g[k], go, gR);
         }
-        for (int k = vl; k < q.nr; k += 16) {
+        for (int k = vl; k < q.nr; k += VL) {
             const int p = VQ_CAP - 1 - k;
             float d[3];
             const float4 db = ray_dir(sen, R, q.slot[p], d);
@@ -556,24 +556,25 @@ __device__ __forceinline__ void hq_flush(HitQueue& q, bool active, bool reset, c
     if (reset) q.ns = q.nr = q.nblk = 0;
 }
 
-// Sum of 12 per-lane values over each half warp in a fixed tree (reduce-
-// scatter through shuffles of distance 8, 4, 2, 1): virtual lane v (lane &
-// 15) receives the half's total of value v (meaningful below 12).
-__device__ __forceinline__ float half_sum12(const float* v) {
-    const int vl = threadIdx.x & 15;
+// Sum of 12 per-lane values over each group of VL = 8 lanes in a fixed tree
+// (reduce-scatter through shuffles of distance 4, 2, 1 on 16 value slots):
+// virtual lane v (lane % 8) receives the group's totals of values 2v and
+// 2v + 1 (meaningful below 12).
+__device__ __forceinline__ float2 group_sum12(const float* v) {
+    const int vl = threadIdx.x % VL;
     float a[16];
 #pragma unroll
     for (int k = 0; k < 16; ++k) a[k] = k < 12 ? v[k] : 0.f;
 #pragma unroll
-    for (int w = 8; w >= 1; w >>= 1) {
+    for (int w = 4, h = 8; w >= 1; w >>= 1, h >>= 1) {
         const bool hi = (vl & w) != 0;
 #pragma unroll
-        for (int k = 0; k < w; ++k) {
-            const float send = hi ? a[k] : a[k + w];
-            a[k] = (hi ? a[k + w] : a[k]) + __shfl_xor_sync(0xffffffffu, send, w);
+        for (int k = 0; k < h; ++k) {
+            const float send = hi ? a[k] : a[k + h];
+            a[k] = (hi ? a[k + h] : a[k]) + __shfl_xor_sync(0xffffffffu, send, w);
         }
     }
-    return a[0];
+    return make_float2(a[0], a[1]);
 }
 
 // Slot range [j0, j1) of part `part` of P in a sensor of R rays: 32-slot
@@ -592,26 +593,28 @@ __device__ __forceinline__ void part_range(int R, int part, int P, int& j0, int&
 // (step, agent, part) items reduce, in a fixed order, to the pose cotangent
 // gposes[t][i][part] = (d/d origin [3], d/d R [9]); zero when the step
 // terminated (the state was replaced).  TAPE: hit ids from the rollout's
-// tape, two items per warp (one per half); else re-cast, one item per warp.
+// tape, VQ_PER_WARP items per warp (one per lane group); else re-cast, one
+// item per warp.
 template <int RPT, bool TAPE, bool EXTRA>
 __global__ void __launch_bounds__(256, TAPE ? 4 : 3) k_render_vjp(const Args a) {
     extern __shared__ __align__(16) unsigned char sm[];
     __shared__ int s_env, s_flag, s_item;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, NW = blockDim.x >> 5;
-    const int half = lane >> 4, vl = lane & 15;
+    const int grp = lane / VL, vl = lane % VL;
     const int M = a.M, S = a.S, NM = a.NM;
     const float4* prim = reinterpret_cast<const float4*>(sm + a.sm.prim);
     constexpr bool recast = !TAPE;
     const LCap cap = cap_of(a);
     WList L;
     if (recast) L = wlist_at(sm + a.sm.wlist + (size_t)warp * a.sm.wstride, cap);
-    HitQueue hq = hit_queue(sm, a, warp, TAPE ? half : 0);
+    HitQueue hq = hit_queue(sm, a, warp, TAPE ? grp : 0);
     if (threadIdx.x == 0) mbar_init(reinterpret_cast<uint64_t*>(sm + a.sm.mbar));
     __syncthreads();
     uint32_t phase = 0;
     const int P = a.parts;
     const int per_env = a.T * M * P;
-    const int per_warp = TAPE ? 2 : 1;                   // items per warp
+    const int per_warp = TAPE ? VQ_PER_WARP : 1;         // items per warp
+    const int lgM = (M & (M - 1)) == 0 ? __ffs(M) - 1 : -1;  // M a power of two: shifts
     const int tasks = (per_env + per_warp - 1) / per_warp;
     for (;;) {
         if (threadIdx.x == 0) {
@@ -628,11 +631,11 @@ __global__ void __launch_bounds__(256, TAPE ? 4 : 3) k_render_vjp(const Args a) 
         prep_boxes(sm, a, mv.ns, mv.nb);
         const int nprim = mv.count();
         for (int task = warp; task < tasks; task = next_item(&s_item, lane)) {
-            const int it = TAPE ? 2 * task + half : task;  // this lane's item
+            const int it = TAPE ? VQ_PER_WARP * task + grp : task;  // this lane's item
             const bool has = it < per_env;
             const int itc = has ? it : per_env - 1;
-            const int tm = div_small(itc, P), part = itc - tm * P;
-            const int t = div_small(tm, M), m = tm - t * M;
+            const int tm = P == 1 ? itc : div_small(itc, P), part = itc - tm * P;
+            const int t = lgM >= 0 ? tm >> lgM : div_small(tm, M), m = tm - t * M;
             const size_t ti = (size_t)t * NM + env * M + m;
             const bool live = has && a.done_rd[(size_t)t * NM + env * M] == 0;
             float go[3] = {0.f, 0.f, 0.f}, gR[9];
@@ -651,16 +654,18 @@ __global__ void __launch_bounds__(256, TAPE ? 4 : 3) k_render_vjp(const Args a) 
                     part_range(sen.R, part, P, j0, j1);
                     if (!live) j1 = j0;  // a terminated step or no item: no block
                     if (TAPE) {
-                        // blocks of 16 slots per half, both halves in step, in
+                        // blocks of VL slots per group, all groups in step, in
                         // rounds of 4 whose hit ids and cotangents are loaded
-                        // together; a half past its range pushes nothing.  The
-                        // queue is flushed after every VQ_FLUSH blocks of the
-                        // half's range (4 divides VQ_FLUSH, so at a round's
-                        // end) and at the sensor's end, as the re-casting
-                        // adjoint flushes.
-                        const int nb = (j1 - j0 + 15) >> 4;
-                        const int nb_w = max(nb, __shfl_xor_sync(0xffffffffu, nb, 16));
-                        const unsigned hm = 0xffffu << (16 * half), bl = ((1u << lane) - 1u) & hm;
+                        // together; a group past its range pushes nothing.
+                        // The queue is flushed after every VQ_FLUSH blocks of
+                        // the group's range (4 divides VQ_FLUSH, so at a
+                        // round's end) and at the sensor's end, as the
+                        // re-casting adjoint flushes.
+                        const int nb = (j1 - j0 + VL - 1) / VL;
+                        int nb_w = nb;
+#pragma unroll
+                        for (int w = VL; w < 32; w <<= 1) nb_w = max(nb_w, __shfl_xor_sync(0xffffffffu, nb_w, w));
+                        const unsigned hm = ((1u << VL) - 1u) << (VL * grp), bl = ((1u << lane) - 1u) & hm;
                         const int16_t* const tp = sen.tape + base;
                         const float* const gp = sen.gout + base;
                         for (int k0 = 0; k0 < nb_w; k0 += 4) {
@@ -668,7 +673,7 @@ __global__ void __launch_bounds__(256, TAPE ? 4 : 3) k_render_vjp(const Args a) 
                             float gv[4];
 #pragma unroll
                             for (int u = 0; u < 4; ++u) {
-                                const int j = j0 + 16 * (k0 + u) + vl;
+                                const int j = j0 + VL * (k0 + u) + vl;
                                 idv[u] = -1;
                                 gv[u] = 0.f;
                                 if (j < j1) {
@@ -686,7 +691,7 @@ __global__ void __launch_bounds__(256, TAPE ? 4 : 3) k_render_vjp(const Args a) 
                                 const unsigned bs = __ballot_sync(0xffffffffu, v && sph), br = bv & ~bs;
                                 if (v) {
                                     const int p = sph ? hq.ns + __popc(bs & bl) : VQ_CAP - 1 - (hq.nr + __popc(br & bl));
-                                    hq.slot[p] = j0 + 16 * (k0 + u) + vl;
+                                    hq.slot[p] = j0 + VL * (k0 + u) + vl;
                                     hq.g[p] = gv[u];
                                     hq.id[p] = (short)id;
                                 }
@@ -716,8 +721,8 @@ __global__ void __launch_bounds__(256, TAPE ? 4 : 3) k_render_vjp(const Args a) 
                                 cast_list<RPT, EXTRA>(L, meta, cap, dx, dy, dz, tb, bi);
                             }
                         }
-                        // each 32-slot row: its two 16-slot blocks in order, as
-                        // the taped gather pushes them; VJPs on the first half
+                        // each 32-slot row: its VL-slot blocks in order, as
+                        // the taped gather pushes them; VJPs on the first group
 #pragma unroll
                         for (int r = 0; r < RPT; ++r) {
                             const int jb = ch * 32 * RPT + r * 32, j = jb + lane;
@@ -726,14 +731,14 @@ __global__ void __launch_bounds__(256, TAPE ? 4 : 3) k_render_vjp(const Args a) 
                             const bool hit = j < j1 && meta.z < 0 && bi[r] >= 0;
                             const int id = hit ? L.id[bi[r]] : -1;
                             const float g = hit ? sen.gout[base + out_index(sen, j)] : 0.f;
-                            for (int src = 0; src < 2; ++src) {
-                                if (jb + 16 * src >= j1) break;
+                            for (int src = 0; src < VQ_PER_WARP; ++src) {
+                                if (jb + VL * src >= j1) break;
                                 hq_push(hq, src, hit && g != 0.f, mv.ns, j, id, g);
-                                if (hq.nblk == VQ_FLUSH) hq_flush<EXTRA>(hq, half == 0, true, sen, mv, o, R, go, gR);
+                                if (hq.nblk == VQ_FLUSH) hq_flush<EXTRA>(hq, grp == 0, true, sen, mv, o, R, go, gR);
                             }
                         }
                     }
-                    hq_flush<EXTRA>(hq, half == 0, true, sen, mv, o, R, go, gR);
+                    hq_flush<EXTRA>(hq, grp == 0, true, sen, mv, o, R, go, gR);
                     __syncwarp();
                 };
                 sensor(Idx<0>{});
@@ -744,8 +749,9 @@ __global__ void __launch_bounds__(256, TAPE ? 4 : 3) k_render_vjp(const Args a) 
             for (int k = 0; k < 3; ++k) v12[k] = go[k];
 #pragma unroll
             for (int k = 0; k < 9; ++k) v12[3 + k] = gR[k];
-            const float tot = half_sum12(v12);
-            if (has && vl < 12 && (TAPE || half == 0)) a.gposes[(ti * P + part) * 12 + vl] = tot;
+            const float2 tot = group_sum12(v12);
+            if (has && vl < 6 && (TAPE || grp == 0))
+                *reinterpret_cast<float2*>(a.gposes + (ti * P + part) * 12 + 2 * vl) = tot;
         }
         __syncthreads();
     }

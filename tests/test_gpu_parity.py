@@ -414,4 +414,17 @@ def test_cull_counters_match_oracle_count(pair):
         assert diff <= oc["ambiguous"], (t, c, oc)
         exact += diff == 0
     assert exact >= 1
+    # counting off: the same images, no counts
+    s32 = pair.rec["states"][0].astype(np.float32).astype(np.float64)
+    sim.reset(dev(s32))
+    d_on = sim.render()
+    sim.counters(reset=True)
+    sim.set_counting(False)
+    d_off = sim.render()
+    c = sim.counters(reset=True)
+    assert c["sphere_tests"] == 0 and c["box_tests"] == 0 and c["rays"] == 0, c
+    for x, y in zip(d_on, d_off):
+        if x is not None:
+            assert torch.equal(x, y)
+    sim.set_counting(True)
     sim.close()
