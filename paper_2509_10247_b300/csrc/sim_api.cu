@@ -667,8 +667,13 @@ int sim_create(const sim_config* cfg, sim_handle** out) {
         h->img_h[s] = cfg->lid_ch;
         h->sen[s++].tmax = h->d_lid_tmax;
     }
-    h->parts_roll = std::min(8, std::max(1, (8 + h->T * h->M - 1) / (h->T * h->M)));
-    h->parts_one = std::min(8, std::max(1, (8 + h->M - 1) / h->M));
+    // ray-adjoint items per environment: enough for every lane group of a
+    // CTA of 8 warps (VQ_PER_WARP items per warp) when the horizon and the
+    // agents give fewer (step, agent) items; fixed, so that every launch
+    // shape splits the rays alike and gives the same sums
+    const int want = ds::VQ_PER_WARP * 8;
+    h->parts_roll = std::min(want, std::max(1, (want + h->T * h->M - 1) / (h->T * h->M)));
+    h->parts_one = std::min(want, std::max(1, (want + h->M - 1) / h->M));
     const size_t tape_bytes = (size_t)h->T * h->NM * (h->Rc + h->Rl) * 2;
     h->tape = cfg->tape_hits == 1 || (cfg->tape_hits == -1 && tape_bytes <= (size_t(8) << 30));
     if (h->S == 0) h->tape = false;

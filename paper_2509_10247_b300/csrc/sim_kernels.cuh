@@ -7,12 +7,6 @@ namespace ds {
 
 constexpr int MAX_SENSORS = 2;
 
-// A compile-time index (selects a sensor's body in the render kernels).
-template <int V>
-struct Idx {
-    static constexpr int value = V;
-};
-
 // Hit queues of one warp of the render adjoint: one per group of VL lanes
 // (an item each), VQ_CAP entries (ray slot, output cotangent, primitive id);
 // VQ_FLUSH blocks of VL rays at most between flushes.

@@ -338,7 +338,9 @@ __device__ __forceinline__ void render_chunks(const Args& a, const WList& L, con
 
 // CASTW: warp per ray (cast_mode 1, maps of spheres and boxes), compiled apart
 // so that the thread-per-ray kernels keep their registers.
-template <int RPT, bool EXTRA, bool COOP, bool CASTW = false>
+// ONE: a single sensor (index 0, known at compile time: its fields are
+// kernel-parameter operands instead of loads indexed by the item's sensor).
+template <int RPT, bool EXTRA, bool COOP, bool CASTW = false, bool ONE = false>
 __global__ void __launch_bounds__(256, 4) k_render(const Args a) {
     extern __shared__ __align__(16) unsigned char sm[];
     __shared__ int s_env, s_flag, s_item;
@@ -397,10 +399,7 @@ __global__ void __launch_bounds__(256, 4) k_render(const Args a) {
             const int t = lgM >= 0 ? tm >> lgM : div_small(tm, M), m = tm - t * M;
             const int si = r < P0 ? 0 : 1, part = si ? r - P0 : r, np = si ? P1 : P0, nchs = si ? nch1 : nch0;
             const int c0 = np == 1 ? 0 : div_small(part * nchs, np), c1 = np == 1 ? nchs : div_small((part + 1) * nchs, np);
-            // one body per sensor index, known at compile time: the sensor's
-            // fields are then kernel-parameter operands
-            auto item = [&](auto sic) {
-                const Sensor& sen = a.sen[decltype(sic)::value];
+            auto item = [&](const Sensor& sen) {
                 if (!sen.out && !sen.tape) return;
                 const size_t ti = (size_t)t * NM + env * M + m;
                 float o[3], R[9];
@@ -417,8 +416,8 @@ __global__ void __launch_bounds__(256, 4) k_render(const Args a) {
                 }
                 render_chunks<RPT, EXTRA, CASTW>(a, Lv, meta, cap, sen, R, c0, c1, base, s_cnt);
             };
-            if (si == 0) item(Idx<0>{});
-            else item(Idx<1>{});
+            if (ONE) item(a.sen[0]);
+            else item(a.sen[si]);
             __syncwarp();
         }
         if (threadIdx.x == 0) s_cnt[3] += (unsigned long long)(a.T);
@@ -595,7 +594,8 @@ __device__ __forceinline__ void part_range(int R, int part, int P, int& j0, int&
 // terminated (the state was replaced).  TAPE: hit ids from the rollout's
 // tape, VQ_PER_WARP items per warp (one per lane group); else re-cast, one
 // item per warp.
-template <int RPT, bool TAPE, bool EXTRA>
+// ONE: a single sensor, as for k_render.
+template <int RPT, bool TAPE, bool EXTRA, bool ONE = false>
 __global__ void __launch_bounds__(256, TAPE ? 4 : 3) k_render_vjp(const Args a) {
     extern __shared__ __align__(16) unsigned char sm[];
     __shared__ int s_env, s_flag, s_item;
@@ -644,10 +644,7 @@ __global__ void __launch_bounds__(256, TAPE ? 4 : 3) k_render_vjp(const Args a) 
             if (__any_sync(0xffffffffu, live)) {
                 float o[3], R[9];
                 load_pose(a.poses + ti * 12, o, R);
-                // one body per sensor index, known at compile time: the
-                // sensor's fields are then kernel-parameter operands
-                auto sensor = [&](auto sic) {
-                    const Sensor& sen = a.sen[decltype(sic)::value];
+                auto sensor = [&](const Sensor& sen) {
                     if (!sen.gout || (TAPE && !sen.tape)) return;
                     const size_t base = ti * sen.R;
                     int j0, j1;
@@ -741,8 +738,9 @@ __global__ void __launch_bounds__(256, TAPE ? 4 : 3) k_render_vjp(const Args a) 
                     hq_flush<EXTRA>(hq, grp == 0, true, sen, mv, o, R, go, gR);
                     __syncwarp();
                 };
-                sensor(Idx<0>{});
-                if (S > 1) sensor(Idx<1>{});
+                if (ONE) sensor(a.sen[0]);
+                else
+                    for (int si = 0; si < S; ++si) sensor(a.sen[si]);
             }
             float v12[12];
 #pragma unroll
@@ -972,8 +970,11 @@ static cudaError_t render_launch(K kernel, bool launch, const Args& a, int grid,
 template <int RPT, bool EXTRA>
 static cudaError_t render_rpt(bool vjp, bool launch, const Args& a, int grid, int block, size_t smem,
                               cudaStream_t st, int* occ) {
-    if (vjp && (a.sen[0].tape || (a.S > 1 && a.sen[1].tape)))  // taped hit ids: one kernel for every RPT
+    const bool one = a.S == 1;
+    if (vjp && (a.sen[0].tape || (a.S > 1 && a.sen[1].tape))) {  // taped hit ids: one kernel for every RPT
+        if (one) return render_launch(k_render_vjp<1, true, EXTRA, true>, launch, a, grid, block, smem, st, occ);
         return render_launch(k_render_vjp<1, true, EXTRA>, launch, a, grid, block, smem, st, occ);
+    }
     if (vjp) return render_launch(k_render_vjp<RPT, false, EXTRA>, launch, a, grid, block, smem, st, occ);
     // shared lists for split items: compiled for the cone-culling default of
     // 4 rays per thread only (the other shapes keep one list per item)
@@ -984,6 +985,7 @@ static cudaError_t render_rpt(bool vjp, bool launch, const Args& a, int grid, in
         const bool coop = a.rparts[0] + (a.S > 1 ? a.rparts[1] : 0) > a.S && a.T * a.M * a.S <= block / 32;
         if (coop && launch) return render_launch(k_render<RPT, EXTRA, true>, launch, a, grid, block, smem, st, occ);
     }
+    if (one) return render_launch(k_render<RPT, EXTRA, false, false, true>, launch, a, grid, block, smem, st, occ);
     return render_launch(k_render<RPT, EXTRA, false>, launch, a, grid, block, smem, st, occ);
 }
 
